@@ -1,0 +1,201 @@
+"""FP64 CPU oracle of the relativistic PIC cycle -- test infrastructure only.
+
+Only ``tests/``, ``__graft_entry__.smoke()`` and the CPU-baseline leg of
+``bench.py`` may import this package.  The product library
+(``paper_1503_02464_gb300``) never imports, links or calls it, and the two
+share no code: the oracle is plain C (``pic_oracle.c``) compiled with gcc and
+driven through ctypes from here.
+
+What the oracle computes (section 2 of the PICCANTE paper, with the readings
+listed in ``pic_oracle.c``): gather of the Yee-staggered fields with the
+shape function, Boris push and leap-frog move in global FP64 coordinates,
+Esirkepov charge-conserving deposition, Yee FDTD split into half B steps, and
+FP64 diagnostics.  Particles are the paper's seven doubles (§3.3).
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+import sys
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "pic_oracle.c")
+_LIB = os.path.join(_HERE, "_build", "libpic_oracle.so")
+
+EX, EY, EZ, BX, BY, BZ, JX, JY, JZ, RHO = range(10)
+FIELD_NAMES = ["Ex", "Ey", "Ez", "Bx", "By", "Bz", "Jx", "Jy", "Jz", "rho"]
+
+_lib = None
+
+
+def build(force: bool = False) -> str:
+    """Compile the oracle with gcc (no GPU, no CUDA)."""
+    os.makedirs(os.path.dirname(_LIB), exist_ok=True)
+    if not force and os.path.exists(_LIB) and os.path.getmtime(_LIB) >= os.path.getmtime(_SRC):
+        return _LIB
+    tmp = _LIB + f".tmp{os.getpid()}"
+    cmd = ["gcc", "-O2", "-fPIC", "-shared", "-std=c99", "-ffp-contract=off", "-o", tmp, _SRC, "-lm"]
+    subprocess.run(cmd, check=True)
+    os.replace(tmp, _LIB)
+    return _LIB
+
+
+def _load():
+    global _lib
+    if _lib is not None:
+        return _lib
+    lib = ctypes.CDLL(build())
+    vp, dp, ip = ctypes.c_void_p, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int)
+    u32p = ctypes.POINTER(ctypes.c_uint32)
+    lib.oracle_create.restype = vp
+    lib.oracle_create.argtypes = [ctypes.c_int, ip, dp, ctypes.c_double, ctypes.c_int]
+    lib.oracle_destroy.argtypes = [vp]
+    lib.oracle_add_species.restype = ctypes.c_int
+    lib.oracle_add_species.argtypes = [vp, ctypes.c_double, ctypes.c_double, ctypes.c_long] + [dp] * 7 + [u32p]
+    lib.oracle_num_particles.restype = ctypes.c_long
+    lib.oracle_num_particles.argtypes = [vp, ctypes.c_int]
+    lib.oracle_get_particles.restype = ctypes.c_long
+    lib.oracle_get_particles.argtypes = [vp, ctypes.c_int, dp, u32p]
+    lib.oracle_get_field.argtypes = [vp, ctypes.c_int, dp]
+    lib.oracle_set_field.argtypes = [vp, ctypes.c_int, dp]
+    lib.oracle_step.argtypes = [vp, ctypes.c_int]
+    lib.oracle_field_step.argtypes = [vp, ctypes.c_int]
+    lib.oracle_step_count.restype = ctypes.c_long
+    lib.oracle_step_count.argtypes = [vp]
+    lib.oracle_shape.restype = ctypes.c_double
+    lib.oracle_shape.argtypes = [ctypes.c_int, ctypes.c_double]
+    lib.oracle_boris.argtypes = [ctypes.c_double, ctypes.c_double, ctypes.c_double, dp, dp, dp]
+    lib.oracle_gather_point.argtypes = [vp, ctypes.c_double, ctypes.c_double, ctypes.c_double, dp, dp]
+    lib.oracle_deposit_move.argtypes = [vp, ctypes.c_double, ctypes.c_double, dp, dp, ctypes.c_double]
+    lib.oracle_compute_rho.argtypes = [vp]
+    lib.oracle_neutralize.argtypes = [vp]
+    lib.oracle_diag.argtypes = [vp, dp]
+    if hasattr(lib, "oracle_set_boundary"):
+        lib.oracle_set_boundary.argtypes = [vp, ctypes.c_int]
+    if hasattr(lib, "oracle_set_laser"):
+        lib.oracle_set_laser.argtypes = [vp, ctypes.c_int] + [ctypes.c_double] * 5 + [ctypes.c_int]
+    _lib = lib
+    return lib
+
+
+def _dp(a: np.ndarray):
+    return a.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+
+
+def _f64(a) -> np.ndarray:
+    return np.ascontiguousarray(a, dtype=np.float64)
+
+
+def shape(order: int, xi: float) -> float:
+    """Shape function value (1 = CIC, 2 = TSC) at distance xi in cells."""
+    return _load().oracle_shape(order, float(xi))
+
+
+def boris(q: float, m: float, dt: float, E, B, p) -> np.ndarray:
+    """One Boris momentum update of p (= m u) in fields E, B (§2 eq. 3)."""
+    E, B, p = _f64(E).copy(), _f64(B).copy(), _f64(p).copy()
+    _load().oracle_boris(q, m, dt, _dp(E), _dp(B), _dp(p))
+    return p
+
+
+class OracleSim:
+    """One simulation held by the C oracle.
+
+    ``dims`` is 2 or 3, ``n`` the cells per axis, ``d`` the cell sizes (c/omega
+    units), ``dt`` the time step and ``order`` the shape order (1 CIC, 2 TSC).
+    Fields are returned as numpy arrays shaped (nz, ny, nx).
+    """
+
+    def __init__(self, dims, n, d, dt, order):
+        lib = _load()
+        n3 = list(n) + [1] * (3 - len(n))
+        d3 = list(d) + [1.0] * (3 - len(d))
+        if dims == 2:
+            n3[2], d3[2] = 1, 1.0
+        self.dims, self.n, self.d, self.dt, self.order = dims, tuple(n3), tuple(d3), dt, order
+        ni = (ctypes.c_int * 3)(*n3)
+        dd = (ctypes.c_double * 3)(*d3)
+        self._h = lib.oracle_create(dims, ni, dd, float(dt), int(order))
+        self._keep = []
+
+    def close(self):
+        if self._h:
+            _load().oracle_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    @property
+    def shape3(self):
+        return (self.n[2], self.n[1], self.n[0])
+
+    def add_species(self, q, m, x, y, z, ux, uy, uz, w, ids=None) -> int:
+        n = len(x)
+        arrs = [_f64(a) for a in (x, y, z if z is not None else np.zeros(n), ux, uy, uz, w)]
+        ids = np.ascontiguousarray(ids if ids is not None else np.arange(n), dtype=np.uint32)
+        return _load().oracle_add_species(
+            self._h, float(q), float(m), n, *[_dp(a) for a in arrs],
+            ids.ctypes.data_as(ctypes.POINTER(ctypes.c_uint32)))
+
+    def add_particles(self, parts: dict, q: float, m: float) -> int:
+        return self.add_species(q, m, parts["x"], parts["y"], parts.get("z"), parts["ux"], parts["uy"],
+                                parts["uz"], parts["w"], parts.get("id"))
+
+    def step(self, n: int = 1):
+        _load().oracle_step(self._h, int(n))
+
+    def field_step(self, n: int = 1):
+        _load().oracle_field_step(self._h, int(n))
+
+    def get_field(self, which: int) -> np.ndarray:
+        out = np.empty(self.shape3, dtype=np.float64)
+        _load().oracle_get_field(self._h, which, _dp(out))
+        return out
+
+    def set_field(self, which: int, arr):
+        a = _f64(np.broadcast_to(arr, self.shape3))
+        _load().oracle_set_field(self._h, which, _dp(a))
+
+    def rho(self) -> np.ndarray:
+        _load().oracle_compute_rho(self._h)
+        return self.get_field(RHO)
+
+    def neutralize(self):
+        _load().oracle_neutralize(self._h)
+
+    def particles(self, species: int = 0) -> dict:
+        lib = _load()
+        n = lib.oracle_num_particles(self._h, species)
+        out = np.empty((max(n, 1), 7), dtype=np.float64)
+        ids = np.empty(max(n, 1), dtype=np.uint32)
+        lib.oracle_get_particles(self._h, species, _dp(out), ids.ctypes.data_as(ctypes.POINTER(ctypes.c_uint32)))
+        out, ids = out[:n], ids[:n]
+        return {"x": out[:, 0], "y": out[:, 1], "z": out[:, 2], "ux": out[:, 3], "uy": out[:, 4],
+                "uz": out[:, 5], "w": out[:, 6], "id": ids}
+
+    def gather(self, x, y, z=0.0):
+        E = np.zeros(3)
+        B = np.zeros(3)
+        _load().oracle_gather_point(self._h, float(x), float(y), float(z), _dp(E), _dp(B))
+        return E, B
+
+    def deposit_move(self, q, w, r0, r1, vz=0.0):
+        r0, r1 = _f64(r0), _f64(r1)
+        _load().oracle_deposit_move(self._h, float(q), float(w), _dp(r0), _dp(r1), float(vz))
+
+    def diag(self) -> dict:
+        out = np.zeros(8)
+        _load().oracle_diag(self._h, _dp(out))
+        return {"energy_field": out[0], "energy_kinetic": out[1], "charge": out[2], "gauss_max": out[3],
+                "n_alive": int(out[4]), "energy_e": out[5], "energy_b": out[6]}
+
+    @property
+    def step_count(self) -> int:
+        return _load().oracle_step_count(self._h)

@@ -1,0 +1,584 @@
+/*
+ * pic_oracle.c -- plain, slow FP64 CPU oracle of the relativistic PIC cycle.
+ *
+ * TEST INFRASTRUCTURE ONLY.  It is loaded by tests/, by
+ * __graft_entry__.smoke() and by bench.py's CPU-baseline leg; the product
+ * library never links, calls or includes it, and it shares no code with the
+ * CUDA path.
+ *
+ * What it computes follows section 2 of "Optimising PICCANTE -- an Open
+ * Source Particle-in-Cell Code for Advanced Simulations on Tier-0 Systems":
+ *   - normalised units with c = 1, v = p / sqrt(p^2 + m^2)        (§2, eq. 1)
+ *   - macro-particles with a compact positive shape g              (§2, eq. 2)
+ *   - equations of motion dp/dt = q(E + v x B), dr/dt = v          (§2, eq. 3)
+ *   - current density J = sum q v g(r - r_n)                       (§2, eq. 4)
+ *   - Maxwell curl equations dE/dt = curl B - J, dB/dt = -curl E   (§2)
+ *   - force = g-weighted average of the grid fields                (§2)
+ *   - leap-frog + Boris pusher, FDTD on the Yee lattice            (§2, refs [8],[9])
+ *   - particle record of seven doubles (x,y,z,px,py,pz,w)          (§3.3)
+ * The paper leaves the continuity-preserving deposit, the boundary
+ * conditions and the laser source unstated (§2); the readings taken here are:
+ *   - Esirkepov's charge-conserving current (Comput. Phys. Commun. 135, 2001)
+ *   - periodic boundaries; absorbing x walls with a first-order Mur
+ *     condition and an incoming laser wave at x = 0.
+ *
+ * Data layout (deliberately unlike the GPU path): particles are an array of
+ * structs holding global positions in physical units and momenta p = m u;
+ * every field component is a full nx*ny*nz array of doubles, index
+ * i + nx*(j + ny*k).  Staggering (Yee): Ex(i+1/2,j,k) Ey(i,j+1/2,k)
+ * Ez(i,j,k+1/2) Bx(i,j+1/2,k+1/2) By(i+1/2,j,k+1/2) Bz(i+1/2,j+1/2,k); J sits
+ * with E; rho at nodes (i,j,k).  In 2D (2D3V) nz = 1 and nothing depends on z.
+ * Shape sums run over a generous window of nodes and every weight is taken
+ * from the shape function itself, so zero weights simply drop out.
+ */
+#include <math.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+
+#define ORC_EX 0
+#define ORC_EY 1
+#define ORC_EZ 2
+#define ORC_BX 3
+#define ORC_BY 4
+#define ORC_BZ 5
+#define ORC_JX 6
+#define ORC_JY 7
+#define ORC_JZ 8
+#define ORC_RHO 9
+#define ORC_NFIELD 10
+
+typedef struct {
+  double x, y, z;    /* global position, physical units            */
+  double px, py, pz; /* momentum p = m u (u = gamma v), §2 eq. 1   */
+  double w;          /* weight: density carried by the particle    */
+  uint32_t id;
+  int alive;
+} orc_particle;
+
+typedef struct {
+  double q, m;
+  long n;
+  orc_particle *p;
+} orc_species;
+
+typedef struct {
+  int dims;
+  int n[3];
+  double d[3];
+  double dt;
+  int order;
+  long ncell;
+  double *f[ORC_NFIELD]; /* E, B, J, and a scratch rho */
+  double *rho_bg;        /* immobile background charge density (nodes) */
+  int nsp;
+  orc_species sp[8];
+  long step;
+  /* x boundaries: 0 periodic, 1 absorbing (first-order Mur) */
+  int absorb_x;
+  /* laser entering through x = 0 (section on boundary readings) */
+  int laser_on;
+  double a0, waist, duration, yc, zc;
+  int pol; /* 1: E along y, 2: E along z */
+  double *mur_prev; /* previous boundary samples kept by the Mur condition */
+} orc_sim;
+
+/* ------------------------------------------------------------------ */
+/* Shape functions (§2: g compact and positive).                       */
+/* order 1: cloud-in-cell (linear B-spline); order 2: triangular-      */
+/* shaped cloud (quadratic B-spline).  xi is measured in cells.        */
+/* ------------------------------------------------------------------ */
+double oracle_shape(int order, double xi) {
+  double a = fabs(xi);
+  if (order == 1) return a < 1.0 ? 1.0 - a : 0.0;
+  if (a <= 0.5) return 0.75 - a * a;
+  if (a < 1.5) {
+    double b = 1.5 - a;
+    return 0.5 * b * b;
+  }
+  return 0.0;
+}
+
+static long wrapi(long i, int n) {
+  long r = i % n;
+  return r < 0 ? r + n : r;
+}
+
+static long idx(const orc_sim *s, long i, long j, long k) {
+  return wrapi(i, s->n[0]) + (long)s->n[0] * (wrapi(j, s->n[1]) + (long)s->n[1] * wrapi(k, s->n[2]));
+}
+
+/* ------------------------------------------------------------------ */
+/* Creation / teardown                                                 */
+/* ------------------------------------------------------------------ */
+void *oracle_create(int dims, const int *n, const double *d, double dt, int order) {
+  orc_sim *s = (orc_sim *)calloc(1, sizeof(orc_sim));
+  s->dims = dims;
+  for (int a = 0; a < 3; ++a) {
+    s->n[a] = n[a];
+    s->d[a] = d[a];
+  }
+  if (dims == 2) {
+    s->n[2] = 1;
+    if (s->d[2] <= 0) s->d[2] = 1.0;
+  }
+  s->dt = dt;
+  s->order = order;
+  s->ncell = (long)s->n[0] * s->n[1] * s->n[2];
+  for (int c = 0; c < ORC_NFIELD; ++c) s->f[c] = (double *)calloc(s->ncell, sizeof(double));
+  s->rho_bg = (double *)calloc(s->ncell, sizeof(double));
+  s->mur_prev = (double *)calloc(8 * (size_t)s->n[1] * s->n[2], sizeof(double));
+  return s;
+}
+
+void oracle_destroy(void *h) {
+  orc_sim *s = (orc_sim *)h;
+  if (!s) return;
+  for (int c = 0; c < ORC_NFIELD; ++c) free(s->f[c]);
+  free(s->rho_bg);
+  free(s->mur_prev);
+  for (int i = 0; i < s->nsp; ++i) free(s->sp[i].p);
+  free(s);
+}
+
+/* Species are given momenta as u = p/m (the generator's convention); the
+ * oracle stores p = m u, the paper's variable (§2 eq. 1, §3.3). */
+int oracle_add_species(void *h, double q, double m, long n, const double *x, const double *y,
+                       const double *z, const double *ux, const double *uy, const double *uz,
+                       const double *w, const uint32_t *id) {
+  orc_sim *s = (orc_sim *)h;
+  if (s->nsp >= 8) return -1;
+  orc_species *sp = &s->sp[s->nsp];
+  sp->q = q;
+  sp->m = m;
+  sp->n = n;
+  sp->p = (orc_particle *)calloc(n > 0 ? n : 1, sizeof(orc_particle));
+  for (long i = 0; i < n; ++i) {
+    orc_particle *p = &sp->p[i];
+    p->x = x[i];
+    p->y = y[i];
+    p->z = (s->dims == 3) ? z[i] : 0.0;
+    p->px = m * ux[i];
+    p->py = m * uy[i];
+    p->pz = m * uz[i];
+    p->w = w[i];
+    p->id = id ? id[i] : (uint32_t)i;
+    p->alive = 1;
+  }
+  return s->nsp++;
+}
+
+long oracle_num_particles(void *h, int isp) {
+  orc_sim *s = (orc_sim *)h;
+  long c = 0;
+  for (long i = 0; i < s->sp[isp].n; ++i) c += s->sp[isp].p[i].alive;
+  return c;
+}
+
+/* Output: for each live particle, x y z ux uy uz w (u = p/m). */
+long oracle_get_particles(void *h, int isp, double *out7, uint32_t *id) {
+  orc_sim *s = (orc_sim *)h;
+  orc_species *sp = &s->sp[isp];
+  long c = 0;
+  for (long i = 0; i < sp->n; ++i) {
+    orc_particle *p = &sp->p[i];
+    if (!p->alive) continue;
+    double *o = out7 + 7 * c;
+    o[0] = p->x;
+    o[1] = p->y;
+    o[2] = p->z;
+    o[3] = p->px / sp->m;
+    o[4] = p->py / sp->m;
+    o[5] = p->pz / sp->m;
+    o[6] = p->w;
+    id[c] = p->id;
+    ++c;
+  }
+  return c;
+}
+
+void oracle_get_field(void *h, int which, double *out) {
+  orc_sim *s = (orc_sim *)h;
+  memcpy(out, s->f[which], sizeof(double) * s->ncell);
+}
+
+void oracle_set_field(void *h, int which, const double *in) {
+  orc_sim *s = (orc_sim *)h;
+  memcpy(s->f[which], in, sizeof(double) * s->ncell);
+}
+
+long oracle_step_count(void *h) { return ((orc_sim *)h)->step; }
+
+/* ------------------------------------------------------------------ */
+/* Field gather (§2: "spatial average of the EM fields weighted with   */
+/* g").  Each component is sampled with the shape centred on the       */
+/* particle, using that component's own Yee location; stag[a] is 0 for */
+/* an integer position and 0.5 for a half-integer one along axis a.    */
+/* ------------------------------------------------------------------ */
+static double gather_component(const orc_sim *s, const double *F, const double X[3], const double stag[3]) {
+  int o = s->order;
+  if (s->dims == 2) {
+    double sum = 0.0;
+    long i0 = (long)floor(X[0] - stag[0]), j0 = (long)floor(X[1] - stag[1]);
+    for (long j = j0 - 2; j <= j0 + 3; ++j) {
+      double sy = oracle_shape(o, X[1] - stag[1] - (double)j);
+      if (sy == 0.0) continue;
+      for (long i = i0 - 2; i <= i0 + 3; ++i) {
+        double sx = oracle_shape(o, X[0] - stag[0] - (double)i);
+        if (sx == 0.0) continue;
+        sum += F[idx(s, i, j, 0)] * sx * sy;
+      }
+    }
+    return sum;
+  }
+  double sum = 0.0;
+  long i0 = (long)floor(X[0] - stag[0]), j0 = (long)floor(X[1] - stag[1]), k0 = (long)floor(X[2] - stag[2]);
+  for (long k = k0 - 2; k <= k0 + 3; ++k) {
+    double sz = oracle_shape(o, X[2] - stag[2] - (double)k);
+    if (sz == 0.0) continue;
+    for (long j = j0 - 2; j <= j0 + 3; ++j) {
+      double sy = oracle_shape(o, X[1] - stag[1] - (double)j);
+      if (sy == 0.0) continue;
+      for (long i = i0 - 2; i <= i0 + 3; ++i) {
+        double sx = oracle_shape(o, X[0] - stag[0] - (double)i);
+        if (sx == 0.0) continue;
+        sum += F[idx(s, i, j, k)] * sx * sy * sz;
+      }
+    }
+  }
+  return sum;
+}
+
+/* Yee locations of the six components (in cells). */
+static const double STAG_E[3][3] = {{0.5, 0, 0}, {0, 0.5, 0}, {0, 0, 0.5}};
+static const double STAG_B[3][3] = {{0, 0.5, 0.5}, {0.5, 0, 0.5}, {0.5, 0.5, 0}};
+
+static void gather_at(const orc_sim *s, double x, double y, double z, double E[3], double B[3]) {
+  double X[3] = {x / s->d[0], y / s->d[1], s->dims == 3 ? z / s->d[2] : 0.0};
+  for (int c = 0; c < 3; ++c) {
+    E[c] = gather_component(s, s->f[ORC_EX + c], X, STAG_E[c]);
+    B[c] = gather_component(s, s->f[ORC_BX + c], X, STAG_B[c]);
+  }
+}
+
+void oracle_gather_point(void *h, double x, double y, double z, double *E, double *B) {
+  gather_at((orc_sim *)h, x, y, z, E, B);
+}
+
+/* ------------------------------------------------------------------ */
+/* Boris pusher in the paper's variables (§2 eq. 3, ref [8]):           */
+/* half electric kick, magnetic rotation, half electric kick.  Written */
+/* for momentum p with gamma m = sqrt(p^2 + m^2).                      */
+/* ------------------------------------------------------------------ */
+void oracle_boris(double q, double m, double dt, const double *E, const double *B, double *p) {
+  double h = 0.5 * q * dt;
+  double pm[3] = {p[0] + h * E[0], p[1] + h * E[1], p[2] + h * E[2]};
+  double gm = sqrt(pm[0] * pm[0] + pm[1] * pm[1] + pm[2] * pm[2] + m * m); /* gamma * m */
+  double t[3] = {h * B[0] / gm, h * B[1] / gm, h * B[2] / gm};
+  double t2 = t[0] * t[0] + t[1] * t[1] + t[2] * t[2];
+  double sv[3] = {2.0 * t[0] / (1.0 + t2), 2.0 * t[1] / (1.0 + t2), 2.0 * t[2] / (1.0 + t2)};
+  double pp[3] = {pm[0] + (pm[1] * t[2] - pm[2] * t[1]), pm[1] + (pm[2] * t[0] - pm[0] * t[2]),
+                  pm[2] + (pm[0] * t[1] - pm[1] * t[0])};
+  double pl[3] = {pm[0] + (pp[1] * sv[2] - pp[2] * sv[1]), pm[1] + (pp[2] * sv[0] - pp[0] * sv[2]),
+                  pm[2] + (pp[0] * sv[1] - pp[1] * sv[0])};
+  p[0] = pl[0] + h * E[0];
+  p[1] = pl[1] + h * E[1];
+  p[2] = pl[2] + h * E[2];
+}
+
+/* ------------------------------------------------------------------ */
+/* Esirkepov charge-conserving current for one particle moving from    */
+/* X0 to X1 (positions in cells, unwrapped).  With S0, S1 the shapes   */
+/* at the two positions and DS = S1 - S0 on a common run of nodes:     */
+/*  3D: Wx = DSx (S0y S0z + DSy S0z/2 + S0y DSz/2 + DSy DSz/3), cyclic  */
+/*      for Wy, Wz; Jx(i+1/2) - Jx(i-1/2) = -q w (dx/dt) Wx(i), the run */
+/*      starting from zero below the stencil.                          */
+/*  2D: Wx = DSx (S0y + DSy/2), Wy = DSy (S0x + DSx/2) with the same    */
+/*      running sums; Jz(i,j) += q w vz (S0x S0y + DSx S0y/2 +          */
+/*      S0x DSy/2 + DSx DSy/3).                                         */
+/* This makes (rho1 - rho0)/dt + div J = 0 with rho = sum q w S (§2     */
+/* eq. 4 and the continuity requirement stated in §2).                 */
+/* ------------------------------------------------------------------ */
+#define ORC_SW 10
+static void esirkepov(orc_sim *s, double q, double w, const double X0[3], const double X1[3], double vz) {
+  int o = s->order;
+  int na = s->dims;
+  long lo[3] = {0, 0, 0};
+  int wdt[3] = {1, 1, 1};
+  double S0[3][ORC_SW], S1[3][ORC_SW], DS[3][ORC_SW];
+  for (int a = 0; a < na; ++a) {
+    double mn = X0[a] < X1[a] ? X0[a] : X1[a];
+    double mx = X0[a] < X1[a] ? X1[a] : X0[a];
+    lo[a] = (long)floor(mn) - 2;
+    wdt[a] = (int)((long)floor(mx) + 3 - lo[a] + 1);
+    if (wdt[a] > ORC_SW) wdt[a] = ORC_SW; /* moves of more than a cell are outside CFL */
+    for (int i = 0; i < wdt[a]; ++i) {
+      S0[a][i] = oracle_shape(o, (double)(lo[a] + i) - X0[a]);
+      S1[a][i] = oracle_shape(o, (double)(lo[a] + i) - X1[a]);
+      DS[a][i] = S1[a][i] - S0[a][i];
+    }
+  }
+  double *Jx = s->f[ORC_JX], *Jy = s->f[ORC_JY], *Jz = s->f[ORC_JZ];
+  double cx = -q * w * s->d[0] / s->dt, cy = -q * w * s->d[1] / s->dt, cz = -q * w * s->d[2] / s->dt;
+  if (s->dims == 2) {
+    for (int j = 0; j < wdt[1]; ++j) {
+      double acc = 0.0;
+      for (int i = 0; i < wdt[0]; ++i) {
+        acc += DS[0][i] * (S0[1][j] + 0.5 * DS[1][j]);
+        Jx[idx(s, lo[0] + i, lo[1] + j, 0)] += cx * acc;
+      }
+    }
+    for (int i = 0; i < wdt[0]; ++i) {
+      double acc = 0.0;
+      for (int j = 0; j < wdt[1]; ++j) {
+        acc += DS[1][j] * (S0[0][i] + 0.5 * DS[0][i]);
+        Jy[idx(s, lo[0] + i, lo[1] + j, 0)] += cy * acc;
+      }
+    }
+    for (int j = 0; j < wdt[1]; ++j)
+      for (int i = 0; i < wdt[0]; ++i) {
+        double sm = S0[0][i] * S0[1][j] + 0.5 * DS[0][i] * S0[1][j] + 0.5 * S0[0][i] * DS[1][j] +
+                    DS[0][i] * DS[1][j] / 3.0;
+        Jz[idx(s, lo[0] + i, lo[1] + j, 0)] += q * w * vz * sm;
+      }
+    return;
+  }
+  /* 3D */
+  for (int k = 0; k < wdt[2]; ++k)
+    for (int j = 0; j < wdt[1]; ++j) {
+      double acc = 0.0;
+      for (int i = 0; i < wdt[0]; ++i) {
+        acc += DS[0][i] * (S0[1][j] * S0[2][k] + 0.5 * DS[1][j] * S0[2][k] + 0.5 * S0[1][j] * DS[2][k] +
+                           DS[1][j] * DS[2][k] / 3.0);
+        Jx[idx(s, lo[0] + i, lo[1] + j, lo[2] + k)] += cx * acc;
+      }
+    }
+  for (int k = 0; k < wdt[2]; ++k)
+    for (int i = 0; i < wdt[0]; ++i) {
+      double acc = 0.0;
+      for (int j = 0; j < wdt[1]; ++j) {
+        acc += DS[1][j] * (S0[2][k] * S0[0][i] + 0.5 * DS[2][k] * S0[0][i] + 0.5 * S0[2][k] * DS[0][i] +
+                           DS[2][k] * DS[0][i] / 3.0);
+        Jy[idx(s, lo[0] + i, lo[1] + j, lo[2] + k)] += cy * acc;
+      }
+    }
+  for (int j = 0; j < wdt[1]; ++j)
+    for (int i = 0; i < wdt[0]; ++i) {
+      double acc = 0.0;
+      for (int k = 0; k < wdt[2]; ++k) {
+        acc += DS[2][k] * (S0[0][i] * S0[1][j] + 0.5 * DS[0][i] * S0[1][j] + 0.5 * S0[0][i] * DS[1][j] +
+                           DS[0][i] * DS[1][j] / 3.0);
+        Jz[idx(s, lo[0] + i, lo[1] + j, lo[2] + k)] += cz * acc;
+      }
+    }
+}
+
+/* Deposit the current of one move from global positions r0 to r1. */
+void oracle_deposit_move(void *h, double q, double w, const double *r0, const double *r1, double vz) {
+  orc_sim *s = (orc_sim *)h;
+  double X0[3] = {r0[0] / s->d[0], r0[1] / s->d[1], s->dims == 3 ? r0[2] / s->d[2] : 0.0};
+  double X1[3] = {r1[0] / s->d[0], r1[1] / s->d[1], s->dims == 3 ? r1[2] / s->d[2] : 0.0};
+  esirkepov(s, q, w, X0, X1, vz);
+}
+
+/* ------------------------------------------------------------------ */
+/* Yee FDTD (§2, ref [9]), split so that B is known at integer times:  */
+/*   B^{n+1/2} = B^n - dt/2 curl E^n                                   */
+/*   E^{n+1}   = E^n + dt (curl B^{n+1/2} - J^{n+1/2})                 */
+/*   B^{n+1}   = B^{n+1/2} - dt/2 curl E^{n+1}                         */
+/* Differences wrap periodically; with nz = 1 every z difference is    */
+/* zero, which is the 2D case.                                         */
+/* ------------------------------------------------------------------ */
+static void yee_b(orc_sim *s, double h) {
+  double *Ex = s->f[ORC_EX], *Ey = s->f[ORC_EY], *Ez = s->f[ORC_EZ];
+  double *Bx = s->f[ORC_BX], *By = s->f[ORC_BY], *Bz = s->f[ORC_BZ];
+  double dx = s->d[0], dy = s->d[1], dz = s->d[2];
+  for (long k = 0; k < s->n[2]; ++k)
+    for (long j = 0; j < s->n[1]; ++j)
+      for (long i = 0; i < s->n[0]; ++i) {
+        long c = idx(s, i, j, k);
+        /* curl E at the B locations */
+        double cx = (Ez[idx(s, i, j + 1, k)] - Ez[c]) / dy - (Ey[idx(s, i, j, k + 1)] - Ey[c]) / dz;
+        double cy = (Ex[idx(s, i, j, k + 1)] - Ex[c]) / dz - (Ez[idx(s, i + 1, j, k)] - Ez[c]) / dx;
+        double cz = (Ey[idx(s, i + 1, j, k)] - Ey[c]) / dx - (Ex[idx(s, i, j + 1, k)] - Ex[c]) / dy;
+        Bx[c] -= h * cx;
+        By[c] -= h * cy;
+        Bz[c] -= h * cz;
+      }
+}
+
+static void yee_e(orc_sim *s, double h) {
+  double *Ex = s->f[ORC_EX], *Ey = s->f[ORC_EY], *Ez = s->f[ORC_EZ];
+  double *Bx = s->f[ORC_BX], *By = s->f[ORC_BY], *Bz = s->f[ORC_BZ];
+  double *Jx = s->f[ORC_JX], *Jy = s->f[ORC_JY], *Jz = s->f[ORC_JZ];
+  double dx = s->d[0], dy = s->d[1], dz = s->d[2];
+  for (long k = 0; k < s->n[2]; ++k)
+    for (long j = 0; j < s->n[1]; ++j)
+      for (long i = 0; i < s->n[0]; ++i) {
+        long c = idx(s, i, j, k);
+        /* curl B at the E locations */
+        double cx = (Bz[c] - Bz[idx(s, i, j - 1, k)]) / dy - (By[c] - By[idx(s, i, j, k - 1)]) / dz;
+        double cy = (Bx[c] - Bx[idx(s, i, j, k - 1)]) / dz - (Bz[c] - Bz[idx(s, i - 1, j, k)]) / dx;
+        double cz = (By[c] - By[idx(s, i - 1, j, k)]) / dx - (Bx[c] - Bx[idx(s, i, j - 1, k)]) / dy;
+        Ex[c] += h * (cx - Jx[c]);
+        Ey[c] += h * (cy - Jy[c]);
+        Ez[c] += h * (cz - Jz[c]);
+      }
+}
+
+/* Field-only update, exposed for the Yee dispersion and Courant pins. */
+void oracle_field_step(void *h, int nsteps) {
+  orc_sim *s = (orc_sim *)h;
+  for (int t = 0; t < nsteps; ++t) {
+    yee_b(s, 0.5 * s->dt);
+    yee_e(s, s->dt);
+    yee_b(s, 0.5 * s->dt);
+  }
+}
+
+/* ------------------------------------------------------------------ */
+/* One PIC cycle: gather -> Boris -> move -> deposit, then Yee.        */
+/* ------------------------------------------------------------------ */
+void oracle_step(void *h, int nsteps) {
+  orc_sim *s = (orc_sim *)h;
+  double L[3] = {s->n[0] * s->d[0], s->n[1] * s->d[1], s->n[2] * s->d[2]};
+  for (int t = 0; t < nsteps; ++t) {
+    memset(s->f[ORC_JX], 0, sizeof(double) * s->ncell);
+    memset(s->f[ORC_JY], 0, sizeof(double) * s->ncell);
+    memset(s->f[ORC_JZ], 0, sizeof(double) * s->ncell);
+    for (int isp = 0; isp < s->nsp; ++isp) {
+      orc_species *sp = &s->sp[isp];
+      for (long ip = 0; ip < sp->n; ++ip) {
+        orc_particle *p = &sp->p[ip];
+        if (!p->alive) continue;
+        double E[3], B[3];
+        gather_at(s, p->x, p->y, p->z, E, B);
+        double mom[3] = {p->px, p->py, p->pz};
+        oracle_boris(sp->q, sp->m, s->dt, E, B, mom);
+        p->px = mom[0];
+        p->py = mom[1];
+        p->pz = mom[2];
+        double gm = sqrt(mom[0] * mom[0] + mom[1] * mom[1] + mom[2] * mom[2] + sp->m * sp->m);
+        double v[3] = {mom[0] / gm, mom[1] / gm, mom[2] / gm}; /* §2 eq. 1 */
+        double r0[3] = {p->x, p->y, p->z};
+        double r1[3] = {p->x + s->dt * v[0], p->y + s->dt * v[1], s->dims == 3 ? p->z + s->dt * v[2] : 0.0};
+        double X0[3] = {r0[0] / s->d[0], r0[1] / s->d[1], r0[2] / s->d[2]};
+        double X1[3] = {r1[0] / s->d[0], r1[1] / s->d[1], r1[2] / s->d[2]};
+        esirkepov(s, sp->q, p->w, X0, X1, v[2]);
+        /* periodic wrap of the stored position */
+        for (int a = 0; a < s->dims; ++a) {
+          if (r1[a] >= L[a]) r1[a] -= L[a];
+          else if (r1[a] < 0.0) r1[a] += L[a];
+        }
+        p->x = r1[0];
+        p->y = r1[1];
+        p->z = r1[2];
+      }
+    }
+    yee_b(s, 0.5 * s->dt);
+    yee_e(s, s->dt);
+    yee_b(s, 0.5 * s->dt);
+    s->step++;
+  }
+}
+
+/* ------------------------------------------------------------------ */
+/* Charge density at the nodes: rho = sum q w S (+ background), §2.    */
+/* ------------------------------------------------------------------ */
+static void deposit_rho(orc_sim *s, double *rho) {
+  int o = s->order;
+  memcpy(rho, s->rho_bg, sizeof(double) * s->ncell);
+  for (int isp = 0; isp < s->nsp; ++isp) {
+    orc_species *sp = &s->sp[isp];
+    for (long ip = 0; ip < sp->n; ++ip) {
+      orc_particle *p = &sp->p[ip];
+      if (!p->alive) continue;
+      double X[3] = {p->x / s->d[0], p->y / s->d[1], s->dims == 3 ? p->z / s->d[2] : 0.0};
+      long i0 = (long)floor(X[0]), j0 = (long)floor(X[1]), k0 = (long)floor(X[2]);
+      long kr = s->dims == 3 ? 2 : 0;
+      for (long k = k0 - kr; k <= k0 + kr + (s->dims == 3); ++k) {
+        double sz = s->dims == 3 ? oracle_shape(o, X[2] - (double)k) : 1.0;
+        if (sz == 0.0) continue;
+        for (long j = j0 - 2; j <= j0 + 3; ++j) {
+          double sy = oracle_shape(o, X[1] - (double)j);
+          if (sy == 0.0) continue;
+          for (long i = i0 - 2; i <= i0 + 3; ++i) {
+            double sx = oracle_shape(o, X[0] - (double)i);
+            if (sx == 0.0) continue;
+            rho[idx(s, i, j, k)] += sp->q * p->w * sx * sy * sz;
+          }
+        }
+      }
+    }
+  }
+}
+
+/* rho of the particles (+ background) into the scratch rho field. */
+void oracle_compute_rho(void *h) {
+  orc_sim *s = (orc_sim *)h;
+  deposit_rho(s, s->f[ORC_RHO]);
+}
+
+/* Immobile neutralising background: rho_bg = -rho of the current particles. */
+void oracle_neutralize(void *h) {
+  orc_sim *s = (orc_sim *)h;
+  memset(s->rho_bg, 0, sizeof(double) * s->ncell);
+  double *tmp = (double *)calloc(s->ncell, sizeof(double));
+  deposit_rho(s, tmp);
+  for (long c = 0; c < s->ncell; ++c) s->rho_bg[c] = -tmp[c];
+  free(tmp);
+}
+
+/* ------------------------------------------------------------------ */
+/* Diagnostics in FP64.  out[0] field energy 1/2 sum(E^2+B^2) dV,       */
+/* out[1] kinetic energy sum w dV (sqrt(p^2+m^2) - m) at the stored    */
+/* momenta, out[2] total charge sum rho dV (incl. background),         */
+/* out[3] max |div E - rho|, out[4] live particle count,               */
+/* out[5] electric part, out[6] magnetic part of the field energy.     */
+/* ------------------------------------------------------------------ */
+void oracle_diag(void *h, double *out) {
+  orc_sim *s = (orc_sim *)h;
+  double dV = s->d[0] * s->d[1] * (s->dims == 3 ? s->d[2] : 1.0);
+  double ue = 0, ub = 0;
+  for (long c = 0; c < s->ncell; ++c) {
+    for (int a = 0; a < 3; ++a) {
+      ue += s->f[ORC_EX + a][c] * s->f[ORC_EX + a][c];
+      ub += s->f[ORC_BX + a][c] * s->f[ORC_BX + a][c];
+    }
+  }
+  ue *= 0.5 * dV;
+  ub *= 0.5 * dV;
+  double uk = 0;
+  long nalive = 0;
+  for (int isp = 0; isp < s->nsp; ++isp) {
+    orc_species *sp = &s->sp[isp];
+    for (long ip = 0; ip < sp->n; ++ip) {
+      orc_particle *p = &sp->p[ip];
+      if (!p->alive) continue;
+      double gm = sqrt(p->px * p->px + p->py * p->py + p->pz * p->pz + sp->m * sp->m);
+      uk += p->w * dV * (gm - sp->m);
+      ++nalive;
+    }
+  }
+  double *rho = s->f[ORC_RHO];
+  deposit_rho(s, rho);
+  double q = 0, gmax = 0;
+  for (long k = 0; k < s->n[2]; ++k)
+    for (long j = 0; j < s->n[1]; ++j)
+      for (long i = 0; i < s->n[0]; ++i) {
+        long c = idx(s, i, j, k);
+        q += rho[c] * dV;
+        double div = (s->f[ORC_EX][c] - s->f[ORC_EX][idx(s, i - 1, j, k)]) / s->d[0] +
+                     (s->f[ORC_EY][c] - s->f[ORC_EY][idx(s, i, j - 1, k)]) / s->d[1] +
+                     (s->f[ORC_EZ][c] - s->f[ORC_EZ][idx(s, i, j, k - 1)]) / s->d[2];
+        double r = fabs(div - rho[c]);
+        if (r > gmax) gmax = r;
+      }
+  out[0] = ue + ub;
+  out[1] = uk;
+  out[2] = q;
+  out[3] = gmax;
+  out[4] = (double)nalive;
+  out[5] = ue;
+  out[6] = ub;
+}

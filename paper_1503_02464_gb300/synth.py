@@ -1,0 +1,181 @@
+"""Seeded synthetic inputs shared by the CUDA path, the tests and the bench.
+
+This module holds none of the PIC method's arithmetic: it only draws
+particle positions and momenta and names the workload presets.  Both the
+CUDA library and the CPU oracle are fed from it, so their inputs are
+identical bit for bit.
+
+Random numbers come from Philox4x64-10 (Salmon et al., SC'11) through
+numpy's counter-based ``Philox`` bit generator.  Particle ``g`` (global
+index = cell * ppc + slot, cells in row-major order i + nx*(j + ny*k)) owns
+the two Philox blocks with counters 2g and 2g+1, i.e. eight raw 64-bit
+draws, so any subset of cells can be regenerated on its own (this is what
+the sampled full-size parity tests rely on).  Draws -> uniforms in (0, 1)
+with 53 random bits; normals by the Box-Muller transform.
+
+Workload recipe (section 2 of the paper states the model; the sizes below are
+the synthetic stand-ins for its laser-plasma and thermal-plasma runs):
+positions uniform inside each cell, ``ppc`` particles per cell, momenta
+u = gamma v drawn per component from N(0, u_th) (cold beams/targets have
+u_th = 0), weight w = density / ppc, ids = global index.
+"""
+from __future__ import annotations
+
+import math
+from dataclasses import dataclass, field
+from typing import Optional, Sequence
+
+import numpy as np
+
+TWO_PI = 2.0 * math.pi
+
+
+def philox_uniforms(seed: int, first: int, count: int) -> np.ndarray:
+    """(count, 8) uniforms in (0,1) for particles first .. first+count-1."""
+    if count <= 0:
+        return np.zeros((0, 8))
+    bg = np.random.Philox(key=int(seed), counter=2 * int(first))
+    raw = bg.random_raw(8 * int(count)).reshape(count, 8)
+    return ((raw >> np.uint64(11)).astype(np.float64) + 0.5) * (1.0 / 9007199254740992.0)
+
+
+def _normals(u1, u2):
+    r = np.sqrt(-2.0 * np.log(u1))
+    return r * np.cos(TWO_PI * u2), r * np.sin(TWO_PI * u2)
+
+
+def particles_for_cells(cells: np.ndarray, grid: Sequence[int], d: Sequence[float], ppc: int,
+                        u_th: float, w: np.ndarray | float, seed: int, dims: int,
+                        drift: Sequence[float] = (0.0, 0.0, 0.0)) -> dict:
+    """Particles of the given cells (row-major linear indices).
+
+    Returns global positions (physical units), momenta u, weights and ids.
+    ``w`` is a scalar or an array with one weight per listed cell.
+    """
+    cells = np.asarray(cells, dtype=np.int64)
+    nx, ny = int(grid[0]), int(grid[1])
+    n = cells.size * ppc
+    gidx = (cells[:, None] * ppc + np.arange(ppc)[None, :]).reshape(-1)
+    # draws are contiguous per run of consecutive cells; fetch run by run
+    u = np.empty((n, 8))
+    if cells.size:
+        breaks = np.nonzero(np.diff(cells) != 1)[0] + 1
+        starts = np.concatenate([[0], breaks])
+        ends = np.concatenate([breaks, [cells.size]])
+        for s, e in zip(starts, ends):
+            u[s * ppc:e * ppc] = philox_uniforms(seed, int(cells[s]) * ppc, int(e - s) * ppc)
+    cc = np.repeat(cells, ppc)
+    i = cc % nx
+    j = (cc // nx) % ny
+    k = cc // (nx * ny)
+    x = (i + u[:, 0]) * d[0]
+    y = (j + u[:, 1]) * d[1]
+    z = (k + u[:, 2]) * d[2] if dims == 3 else np.zeros(n)
+    n0, n1 = _normals(u[:, 3], u[:, 4])
+    n2, _ = _normals(u[:, 5], u[:, 6])
+    ux = u_th * n0 + drift[0]
+    uy = u_th * n1 + drift[1]
+    uz = u_th * n2 + drift[2]
+    wa = np.broadcast_to(np.asarray(w, dtype=np.float64), cells.shape)
+    ww = np.repeat(wa, ppc) / ppc
+    return {"x": x, "y": y, "z": z, "ux": ux, "uy": uy, "uz": uz, "w": np.ascontiguousarray(ww),
+            "id": gidx.astype(np.uint32)}
+
+
+@dataclass
+class Species:
+    name: str
+    q: float
+    m: float
+    ppc: int
+    u_th: float
+    density: float = 1.0
+    # columns [x0, x1) holding the species (None = whole box)
+    x_range: Optional[tuple] = None
+    seed_offset: int = 0
+
+
+@dataclass
+class Workload:
+    """A named synthetic configuration (grid, time step, shape, species)."""
+    name: str
+    dims: int
+    n: tuple
+    d: tuple
+    dt: float
+    order: int
+    steps: int
+    seed: int
+    species: list = field(default_factory=list)
+    sort_every: int = 20
+    absorbing_x: bool = False
+    laser: Optional[dict] = None
+    neutralize: bool = True
+
+    @property
+    def ncells(self) -> int:
+        return int(np.prod(self.n[:self.dims]))
+
+    def species_cells(self, sp: Species) -> np.ndarray:
+        nx, ny = self.n[0], self.n[1]
+        nz = self.n[2] if self.dims == 3 else 1
+        if sp.x_range is None:
+            return np.arange(nx * ny * nz, dtype=np.int64)
+        i = np.arange(sp.x_range[0], sp.x_range[1])
+        jk = np.arange(ny * nz)
+        return (i[None, :] + nx * jk[:, None]).reshape(-1)
+
+    def n_particles(self) -> int:
+        return sum(int(self.species_cells(s).size) * s.ppc for s in self.species)
+
+    def particles(self, isp: int, cells: Optional[np.ndarray] = None) -> dict:
+        sp = self.species[isp]
+        if cells is None:
+            cells = self.species_cells(sp)
+        return particles_for_cells(cells, self.n, self.d, sp.ppc, sp.u_th, sp.density,
+                                   self.seed * 1000 + sp.seed_offset, self.dims)
+
+
+def courant_limit(d: Sequence[float], dims: int) -> float:
+    """Largest stable Yee time step (c = 1): (sum 1/dx_i^2)^(-1/2)."""
+    return 1.0 / math.sqrt(sum(1.0 / (x * x) for x in d[:dims]))
+
+
+def preset(name: str) -> Workload:
+    """The synthetic workloads (sizes of the paper's laser/thermal plasma runs)."""
+    lam = TWO_PI  # laser wavelength in c/omega_0 units
+    if name == "thermal2d_64":
+        # 2D3V periodic plasma 64x64, dx=dy=0.05, dt=0.035, 16 ppc, u_th=0.01, CIC
+        return Workload(name, 2, (64, 64, 1), (0.05, 0.05, 1.0), 0.035, 1, 100, 1001,
+                        [Species("electron", -1.0, 1.0, 16, 0.01)])
+    if name == "thermal3d_256":
+        # 3D3V periodic thermal plasma 256^3, 8 ppc, u_th=0.05, TSC, sort every 20
+        return Workload(name, 3, (256, 256, 256), (0.05, 0.05, 0.05), 0.028, 2, 50, 1003,
+                        [Species("electron", -1.0, 1.0, 8, 0.05)])
+    if name == "laser_slab2d":
+        d = 0.02 * lam
+        dt = 0.9 * courant_limit((d, d), 2)
+        return Workload(name, 2, (2048, 1024, 1), (d, d, 1.0), dt, 2, 2000, 1002,
+                        [Species("electron", -1.0, 1.0, 64, 0.0, 40.0, (1024, 1064), 0),
+                         Species("proton", 1.0, 1836.0, 64, 0.0, 40.0, (1024, 1064), 1)],
+                        absorbing_x=True, neutralize=False,
+                        laser={"a0": 3.0, "waist": 3 * lam, "duration": 10 * lam, "pol": 1})
+    if name == "laser_foil3d":
+        d = 0.03 * lam
+        dt = 0.9 * courant_limit((d, d, d), 3)
+        return Workload(name, 3, (512, 256, 256), (d, d, d), dt, 2, 1000, 1004,
+                        [Species("electron", -1.0, 1.0, 27, 0.0, 50.0, (256, 276), 0),
+                         Species("proton", 1.0, 1836.0, 27, 0.0, 50.0, (256, 276), 1)],
+                        absorbing_x=True, neutralize=False,
+                        laser={"a0": 10.0, "waist": 2 * lam, "duration": 8 * lam, "pol": 1})
+    raise KeyError(name)
+
+
+def small(dims: int, n: tuple, order: int, ppc: int, u_th: float, seed: int, dt_frac: float = 0.95,
+          d: float = 0.05) -> Workload:
+    """A small periodic thermal plasma for parity tests."""
+    dd = (d, d, d if dims == 3 else 1.0)
+    dt = dt_frac * courant_limit(dd, dims)
+    nn = tuple(n) + (1,) * (3 - len(n))
+    return Workload(f"small{dims}d", dims, nn, dd, dt, order, 10, seed,
+                    [Species("electron", -1.0, 1.0, ppc, u_th)])
