@@ -1,0 +1,213 @@
+/*
+ * pic.h -- C ABI of the GB300 particle-in-cell library (libpic.so).
+ *
+ * The library runs the standard relativistic PIC cycle of section 2 of
+ * "Optimising PICCANTE -- an Open Source Particle-in-Cell Code for Advanced
+ * Simulations on Tier-0 Systems" on one GPU (sm_103a):
+ *
+ *   field gather   force from the g-weighted average of the Yee fields (§2)
+ *   Boris push     dp/dt = q(E + v x B), v = p / sqrt(p^2 + m^2)  (§2 eqs. 1, 3, ref [8])
+ *   leap-frog move dr/dt = v                                       (§2 eq. 3)
+ *   deposit        J = sum q v g, charge-conserving (Esirkepov)    (§2 eq. 4 and the
+ *                  continuity requirement of §2)
+ *   Yee FDTD       dE/dt = curl B - J, dB/dt = -curl E             (§2, ref [9])
+ *
+ * Units are the paper's normalised ones (§2): c = 1, time in 1/omega_r, length
+ * in c/omega_r, momentum u = p/(m c) = gamma v, fields in m c omega_r / e,
+ * densities in epsilon_0 m omega_r^2 / e^2.  Then div E = rho and an electron
+ * has q = -1, m = 1.
+ *
+ * Conventions shared by every call
+ *  - Every call returns an int status: PIC_OK (0) or one of the PIC_E* codes.
+ *    pic_last_error() gives a one-line description of the last failure.
+ *  - The library owns every simulation buffer (allocated on the device with
+ *    cudaMalloc at pic_create / pic_add_species time).  Pointers passed in are
+ *    borrowed for the duration of the call only; output buffers belong to the
+ *    caller.  mem_kind says whether a pointer is host (PIC_MEM_HOST) or device
+ *    (PIC_MEM_DEVICE) memory.
+ *  - Work is enqueued on config.stream (a cudaStream_t, NULL = legacy default
+ *    stream).  pic_step is asynchronous; pic_fields, pic_particles, pic_diag and
+ *    pic_sync synchronise that stream and report errors latched on the device.
+ *  - A handle must not be used from two host threads at once.
+ *
+ * Grid and staggering (Yee lattice): cells i in [0,n[0]), j in [0,n[1]),
+ * k in [0,n[2]); a field array is indexed i + n[0]*(j + n[1]*k) (x fastest).
+ * Ex(i+1/2,j,k) Ey(i,j+1/2,k) Ez(i,j,k+1/2) Bx(i,j+1/2,k+1/2) By(i+1/2,j,k+1/2)
+ * Bz(i+1/2,j+1/2,k); J sits with E; rho at the nodes (i,j,k).  dims = 2 is the
+ * 2D3V case: n[2] = 1, three field and momentum components, nothing depends
+ * on z.
+ */
+#ifndef PIC_H
+#define PIC_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- status codes ---- */
+#define PIC_OK 0
+#define PIC_EINVAL 1    /* bad argument or configuration                       */
+#define PIC_ECOURANT 2  /* dt above the Yee stability limit (sum dx^-2)^(-1/2)  */
+#define PIC_ENOMEM 3    /* device allocation failed or capacity exceeded         */
+#define PIC_ECUDA 4     /* a CUDA runtime call or kernel launch failed           */
+#define PIC_EOVERFLOW 5 /* an internal bound was exceeded on the device          */
+#define PIC_ETIMEOUT 6  /* a bounded device-side wait gave up                    */
+#define PIC_ENAN 7      /* a non-finite value was found by a diagnostic          */
+
+/* ---- enumerations ---- */
+#define PIC_FP32 0 /* FP32 push/gather/deposit on cell-relative offsets */
+#define PIC_FP64 1 /* the same cycle in FP64                            */
+
+#define PIC_BC_PERIODIC 0
+#define PIC_BC_ABSORBING 1 /* x walls only: first-order Mur fields, particles removed */
+
+#define PIC_MEM_HOST 0
+#define PIC_MEM_DEVICE 1
+
+#define PIC_EX 0
+#define PIC_EY 1
+#define PIC_EZ 2
+#define PIC_BX 3
+#define PIC_BY 4
+#define PIC_BZ 5
+#define PIC_JX 6
+#define PIC_JY 7
+#define PIC_JZ 8
+#define PIC_RHO 9 /* charge density of the particles plus the background */
+
+/* Laser entering through the x = 0 wall (laser-plasma runs, §1-§2; the
+ * paper gives no source formula -- see the boundary reading in the design
+ * notes).  Field amplitude a0 (normalised vector potential), Gaussian
+ * transverse profile exp(-r^2/waist^2) about (y_center, z_center), sin^2
+ * envelope of total length `duration`, carrier frequency 1 (omega_r = omega
+ * of the laser).  polarization 1 = E along y, 2 = E along z. */
+typedef struct {
+  int enabled;
+  double a0;
+  double waist;
+  double duration;
+  double y_center;
+  double z_center;
+  int polarization;
+} pic_laser;
+
+typedef struct {
+  int dims;            /* 2 (2D3V) or 3                                        */
+  int n[3];            /* cells per axis; n[2] = 1 when dims = 2               */
+  double dx[3];        /* cell sizes                                           */
+  double dt;           /* time step; must satisfy dt <= (sum dx^-2)^(-1/2)     */
+  int shape_order;     /* 1 = CIC (linear), 2 = TSC (quadratic) shape g (§2)   */
+  int precision;       /* PIC_FP32 or PIC_FP64                                 */
+  int bc_lo[3];        /* PIC_BC_* per axis; only x may be absorbing           */
+  int bc_hi[3];
+  int sort_every;      /* steps between particle sorts (0 = 20)                */
+  int tile[3];         /* cell-tile shape of the push kernel (0 = default)     */
+  int drift_guard;     /* cells a particle may stray from its tile between sorts
+                          and still use the tile's shared-memory window (0 = 1) */
+  pic_laser laser;
+  void *stream;        /* cudaStream_t                                         */
+} pic_config;
+
+/* FP64 diagnostics (all reductions accumulate in double). */
+typedef struct {
+  double energy_field;    /* 1/2 sum (E^2 + B^2) dV at the current integer time  */
+  double energy_e;        /* electric part                                        */
+  double energy_b;        /* magnetic part                                        */
+  double energy_kinetic;  /* sum w dV m (gamma - 1) at the stored momenta         */
+  double charge;          /* sum rho dV (particles + background)                  */
+  double gauss_max;       /* max |div E - rho|                                    */
+  double continuity_max;  /* max |(rho - rho_prev)/dt + div J| when the previous
+                             pic_diag call was exactly one step earlier, else -1  */
+  int64_t n_alive;        /* live macro-particles, all species                    */
+  int64_t n_escaped;      /* particle-steps that left their tile window (slow path)*/
+  int64_t n_clamped;      /* FP32 offsets clamped below 1 after a cell carry      */
+  int64_t n_absorbed;     /* particles removed at absorbing walls                 */
+  int64_t step;           /* completed time steps                                 */
+} pic_diag_t;
+
+typedef struct pic_handle pic_handle;
+
+/* Create a simulation.  Validates sizes, shape order, precision, boundary
+ * kinds and the Courant condition of the Yee scheme (§2 states dx_i >= c dt;
+ * the limit enforced is the sharper (sum dx_i^-2)^(-1/2)).  Allocates and
+ * zeroes E, B, J.  Returns PIC_EINVAL / PIC_ECOURANT / PIC_ENOMEM / PIC_ECUDA.
+ * On failure *out is NULL. */
+int pic_create(const pic_config *cfg, pic_handle **out);
+
+/* Release every device buffer and the handle (NULL is accepted). */
+int pic_destroy(pic_handle *h);
+
+/* Text of the last error on this handle (or of the last failed pic_create
+ * when h is NULL).  Owned by the library; valid until the next call. */
+const char *pic_last_error(const pic_handle *h);
+
+/* Add a species of charge q and mass m with room for `capacity`
+ * macro-particles (§2: each species a has q_a, m_a).  *species receives its
+ * index (0, 1, ...).  Up to 8 species. */
+int pic_add_species(pic_handle *h, double q, double m, int64_t capacity, int *species);
+
+/* Append n particles to a species.  x, y, z are global positions (physical
+ * units; z ignored in 2D), ux, uy, uz the momenta u = p/(m c) at time
+ * t - dt/2 (leap-frog), w the weight (density carried, so rho = sum q w g),
+ * id an optional tag (NULL = running index) kept through sorts.  Seven values
+ * per particle as in §3.3, converted on the device to an integer cell plus an
+ * in-cell offset.  Positions outside the box wrap on periodic axes and are
+ * rejected (PIC_EINVAL) on absorbing ones.  Exceeding capacity: PIC_ENOMEM. */
+int pic_load_particles(pic_handle *h, int species, int64_t n, const double *x, const double *y,
+                       const double *z, const double *ux, const double *uy, const double *uz,
+                       const double *w, const uint32_t *id, int mem_kind);
+
+/* Immobile neutralising background: rho_bg = -rho of the particles loaded so
+ * far (so that E = 0 satisfies Gauss's law).  Used by the diagnostics only:
+ * an immobile background carries no current. */
+int pic_neutralize(pic_handle *h);
+
+/* Advance nsteps PIC cycles (enqueued on the stream; asynchronous).
+ * Per step: sort (every sort_every steps) -> J = 0 -> per species one fused
+ * gather/Boris/move/deposit launch -> Yee B half step -> E step -> B half
+ * step (-> wall and laser boundary kernels when enabled). */
+int pic_step(pic_handle *h, int nsteps);
+
+/* Copy one field (PIC_EX .. PIC_RHO) as FP64 into out (n[0]*n[1]*n[2]
+ * doubles, x fastest).  Synchronises.  J holds the current of the last step.
+ * PIC_RHO deposits the particles' charge (plus background) first. */
+int pic_fields(pic_handle *h, int which, double *out, int mem_kind);
+
+/* Overwrite one field component (PIC_EX .. PIC_JZ) from FP64 data. */
+int pic_set_field(pic_handle *h, int which, const double *in, int mem_kind);
+
+/* Number of particle slots of a species (live particles plus dead ones not
+ * yet compacted by a sort). */
+int pic_num_particles(pic_handle *h, int species, int64_t *n);
+
+/* Copy a species out in global FP64 coordinates, slot order.  Any pointer
+ * may be NULL to skip that array.  alive[i] = 1 for a live slot.
+ * Synchronises. */
+int pic_particles(pic_handle *h, int species, double *x, double *y, double *z, double *ux,
+                  double *uy, double *uz, double *w, uint32_t *id, int32_t *alive, int mem_kind);
+
+/* FP64 diagnostics of the current state.  Synchronises; reports device-side
+ * errors (PIC_EOVERFLOW, PIC_ENAN). */
+int pic_diag(pic_handle *h, pic_diag_t *out);
+
+/* Wait for all enqueued work and report latched device errors. */
+int pic_sync(pic_handle *h);
+
+/* Per-kernel timing with CUDA events on the simulation stream.  enable = 1
+ * starts recording (clearing previous records).  pic_timings synchronises
+ * and writes, for up to nmax kernel classes, total milliseconds and launch
+ * counts; class order: 0 sort, 1 zero J, 2 push, 3 Yee B, 4 Yee E,
+ * 5 boundary.  Returns the number of classes written in *ncls. */
+int pic_profile(pic_handle *h, int enable);
+int pic_timings(pic_handle *h, double *ms, int64_t *launches, int nmax, int *ncls);
+
+/* Number of kernels this handle has launched since creation. */
+int pic_launch_count(pic_handle *h, int64_t *count);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* PIC_H */

@@ -1,0 +1,190 @@
+"""ctypes binding of libpic.so -- argument marshalling only.
+
+Every function here has the name of the C entry point it wraps (declared in
+``include/pic.h``) and does nothing but convert arguments: all of the PIC
+cycle runs in the CUDA kernels of the library.  There is no fallback: if the
+library is missing or cannot be loaded, ``load()`` raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from typing import Optional
+
+PIC_OK, PIC_EINVAL, PIC_ECOURANT, PIC_ENOMEM, PIC_ECUDA, PIC_EOVERFLOW, PIC_ETIMEOUT, PIC_ENAN = range(8)
+PIC_FP32, PIC_FP64 = 0, 1
+PIC_BC_PERIODIC, PIC_BC_ABSORBING = 0, 1
+PIC_MEM_HOST, PIC_MEM_DEVICE = 0, 1
+PIC_EX, PIC_EY, PIC_EZ, PIC_BX, PIC_BY, PIC_BZ, PIC_JX, PIC_JY, PIC_JZ, PIC_RHO = range(10)
+KERNEL_CLASSES = ["sort", "zero_j", "push", "yee_b", "yee_e", "boundary"]
+
+ERROR_NAMES = {0: "PIC_OK", 1: "PIC_EINVAL", 2: "PIC_ECOURANT", 3: "PIC_ENOMEM", 4: "PIC_ECUDA",
+               5: "PIC_EOVERFLOW", 6: "PIC_ETIMEOUT", 7: "PIC_ENAN"}
+
+# every symbol include/pic.h declares
+EXPORTED = ["pic_create", "pic_destroy", "pic_last_error", "pic_add_species", "pic_load_particles",
+            "pic_neutralize", "pic_step", "pic_fields", "pic_set_field", "pic_num_particles", "pic_particles",
+            "pic_diag", "pic_sync", "pic_profile", "pic_timings", "pic_launch_count"]
+
+
+class pic_laser(ctypes.Structure):
+    _fields_ = [("enabled", ctypes.c_int), ("a0", ctypes.c_double), ("waist", ctypes.c_double),
+                ("duration", ctypes.c_double), ("y_center", ctypes.c_double), ("z_center", ctypes.c_double),
+                ("polarization", ctypes.c_int)]
+
+
+class pic_config(ctypes.Structure):
+    _fields_ = [("dims", ctypes.c_int), ("n", ctypes.c_int * 3), ("dx", ctypes.c_double * 3),
+                ("dt", ctypes.c_double), ("shape_order", ctypes.c_int), ("precision", ctypes.c_int),
+                ("bc_lo", ctypes.c_int * 3), ("bc_hi", ctypes.c_int * 3), ("sort_every", ctypes.c_int),
+                ("tile", ctypes.c_int * 3), ("drift_guard", ctypes.c_int), ("laser", pic_laser),
+                ("stream", ctypes.c_void_p)]
+
+
+class pic_diag_t(ctypes.Structure):
+    _fields_ = [("energy_field", ctypes.c_double), ("energy_e", ctypes.c_double), ("energy_b", ctypes.c_double),
+                ("energy_kinetic", ctypes.c_double), ("charge", ctypes.c_double), ("gauss_max", ctypes.c_double),
+                ("continuity_max", ctypes.c_double), ("n_alive", ctypes.c_int64), ("n_escaped", ctypes.c_int64),
+                ("n_clamped", ctypes.c_int64), ("n_absorbed", ctypes.c_int64), ("step", ctypes.c_int64)]
+
+    def as_dict(self) -> dict:
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+class PicError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"{ERROR_NAMES.get(code, code)}: {msg}")
+        self.code = code
+
+
+_lib: Optional[ctypes.CDLL] = None
+
+
+def library_path() -> str:
+    return os.path.join(os.path.dirname(os.path.abspath(__file__)), "_build", "libpic.so")
+
+
+def load(build_if_missing: bool = True) -> ctypes.CDLL:
+    """Load libpic.so (building it with nvcc first if it is absent)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    path = library_path()
+    if not os.path.exists(path):
+        if not build_if_missing:
+            raise RuntimeError(f"libpic.so not built ({path}); run paper_1503_02464_gb300/build.py")
+        from . import build as _build
+        _build.build()
+    lib = ctypes.CDLL(path)
+    vp, dp, i64 = ctypes.c_void_p, ctypes.POINTER(ctypes.c_double), ctypes.c_int64
+    hp = ctypes.c_void_p
+    sig = {
+        "pic_create": ([ctypes.POINTER(pic_config), ctypes.POINTER(ctypes.c_void_p)], ctypes.c_int),
+        "pic_destroy": ([hp], ctypes.c_int),
+        "pic_last_error": ([hp], ctypes.c_char_p),
+        "pic_add_species": ([hp, ctypes.c_double, ctypes.c_double, i64, ctypes.POINTER(ctypes.c_int)], ctypes.c_int),
+        "pic_load_particles": ([hp, ctypes.c_int, i64] + [vp] * 8 + [ctypes.c_int], ctypes.c_int),
+        "pic_neutralize": ([hp], ctypes.c_int),
+        "pic_step": ([hp, ctypes.c_int], ctypes.c_int),
+        "pic_fields": ([hp, ctypes.c_int, vp, ctypes.c_int], ctypes.c_int),
+        "pic_set_field": ([hp, ctypes.c_int, vp, ctypes.c_int], ctypes.c_int),
+        "pic_num_particles": ([hp, ctypes.c_int, ctypes.POINTER(ctypes.c_int64)], ctypes.c_int),
+        "pic_particles": ([hp, ctypes.c_int] + [vp] * 9 + [ctypes.c_int], ctypes.c_int),
+        "pic_diag": ([hp, ctypes.POINTER(pic_diag_t)], ctypes.c_int),
+        "pic_sync": ([hp], ctypes.c_int),
+        "pic_profile": ([hp, ctypes.c_int], ctypes.c_int),
+        "pic_timings": ([hp, dp, ctypes.POINTER(ctypes.c_int64), ctypes.c_int, ctypes.POINTER(ctypes.c_int)],
+                        ctypes.c_int),
+        "pic_launch_count": ([hp, ctypes.POINTER(ctypes.c_int64)], ctypes.c_int),
+    }
+    for name, (args, res) in sig.items():
+        fn = getattr(lib, name)
+        fn.argtypes = args
+        fn.restype = res
+    _lib = lib
+    return lib
+
+
+def check(handle, rc: int) -> None:
+    if rc != PIC_OK:
+        msg = load().pic_last_error(handle)
+        raise PicError(rc, msg.decode() if msg else "")
+
+
+def pic_create(cfg: pic_config) -> ctypes.c_void_p:
+    h = ctypes.c_void_p()
+    check(None, load().pic_create(ctypes.byref(cfg), ctypes.byref(h)))
+    return h
+
+
+def pic_destroy(h) -> None:
+    check(h, load().pic_destroy(h))
+
+
+def pic_last_error(h) -> str:
+    m = load().pic_last_error(h)
+    return m.decode() if m else ""
+
+
+def pic_add_species(h, q: float, m: float, capacity: int) -> int:
+    sp = ctypes.c_int()
+    check(h, load().pic_add_species(h, float(q), float(m), int(capacity), ctypes.byref(sp)))
+    return sp.value
+
+
+def pic_load_particles(h, species: int, n: int, x, y, z, ux, uy, uz, w, ids, mem_kind: int) -> None:
+    check(h, load().pic_load_particles(h, species, int(n), x, y, z, ux, uy, uz, w, ids, mem_kind))
+
+
+def pic_neutralize(h) -> None:
+    check(h, load().pic_neutralize(h))
+
+
+def pic_step(h, nsteps: int) -> None:
+    check(h, load().pic_step(h, int(nsteps)))
+
+
+def pic_fields(h, which: int, out_ptr, mem_kind: int) -> None:
+    check(h, load().pic_fields(h, which, out_ptr, mem_kind))
+
+
+def pic_set_field(h, which: int, in_ptr, mem_kind: int) -> None:
+    check(h, load().pic_set_field(h, which, in_ptr, mem_kind))
+
+
+def pic_num_particles(h, species: int) -> int:
+    n = ctypes.c_int64()
+    check(h, load().pic_num_particles(h, species, ctypes.byref(n)))
+    return n.value
+
+
+def pic_particles(h, species: int, x, y, z, ux, uy, uz, w, ids, alive, mem_kind: int) -> None:
+    check(h, load().pic_particles(h, species, x, y, z, ux, uy, uz, w, ids, alive, mem_kind))
+
+
+def pic_diag(h) -> dict:
+    d = pic_diag_t()
+    check(h, load().pic_diag(h, ctypes.byref(d)))
+    return d.as_dict()
+
+
+def pic_sync(h) -> None:
+    check(h, load().pic_sync(h))
+
+
+def pic_profile(h, enable: bool) -> None:
+    check(h, load().pic_profile(h, 1 if enable else 0))
+
+
+def pic_timings(h) -> dict:
+    ms = (ctypes.c_double * 8)()
+    cnt = (ctypes.c_int64 * 8)()
+    nc = ctypes.c_int()
+    check(h, load().pic_timings(h, ms, cnt, 8, ctypes.byref(nc)))
+    return {KERNEL_CLASSES[i]: (ms[i], cnt[i]) for i in range(nc.value)}
+
+
+def pic_launch_count(h) -> int:
+    c = ctypes.c_int64()
+    check(h, load().pic_launch_count(h, ctypes.byref(c)))
+    return c.value

@@ -1,0 +1,641 @@
+// Host runtime and C ABI of libpic.so (declared in include/pic.h).
+//
+// Owns the device state of one simulation (fields, per-species particle
+// buffers, sort scratch, counters), orders the kernels of a PIC step on the
+// caller's stream, and converts between the caller's FP64 global view and the
+// library's (cell, offset) particle storage.
+#include <cuda_runtime.h>
+#include <math.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <string>
+#include <vector>
+
+#include "pic.h"
+#include "pic_internal.h"
+
+using pic::Counters;
+using pic::Grid;
+using pic::Particles;
+
+namespace {
+
+constexpr int kMaxSpecies = 8;
+constexpr int kBlock = 256;
+
+struct Species {
+  double q = 0, m = 1;
+  int64_t capacity = 0;
+  Particles buf[2] = {};
+  int cur = 0;
+  int64_t *d_count = nullptr;   // slots in use (device)
+  int64_t h_count = 0;          // host mirror, valid while !stepped_since_count
+  int32_t *rank = nullptr;
+  int64_t *tile_start = nullptr;
+  bool need_sort = true;
+};
+
+struct TimerRec {
+  int cls;
+  cudaEvent_t a, b;
+};
+
+std::string g_create_error;
+
+}  // namespace
+
+struct pic_handle {
+  pic_config cfg;
+  Grid g;
+  cudaStream_t st = nullptr;
+  size_t rsize = 4;
+  void *E[3] = {}, *B[3] = {}, *J[3] = {};
+  double *rho_bg = nullptr, *rho = nullptr, *rho_prev = nullptr, *f64 = nullptr, *red = nullptr;
+  int64_t rho_prev_step = -2;
+  int32_t *keys = nullptr;
+  int64_t *tile_tmp = nullptr;
+  Counters *ctr = nullptr;
+  unsigned long long *bad = nullptr;
+  Species sp[kMaxSpecies];
+  int nsp = 0;
+  int64_t step = 0;
+  int64_t launches = 0;
+  std::string err;
+  bool profiling = false;
+  std::vector<TimerRec> timers;
+  std::vector<cudaEvent_t> event_pool;
+};
+
+namespace {
+
+int fail(pic_handle *h, int code, const std::string &msg) {
+  if (h) h->err = msg;
+  else g_create_error = msg;
+  return code;
+}
+
+int cuda_fail(pic_handle *h, cudaError_t e, const char *where) {
+  return fail(h, PIC_ECUDA, std::string(where) + ": " + cudaGetErrorString(e));
+}
+
+#define CK(h, call, where)                         \
+  do {                                             \
+    cudaError_t e_ = (call);                       \
+    if (e_ != cudaSuccess) return cuda_fail(h, e_, where); \
+  } while (0)
+
+cudaEvent_t take_event(pic_handle *h) {
+  if (!h->event_pool.empty()) {
+    cudaEvent_t e = h->event_pool.back();
+    h->event_pool.pop_back();
+    return e;
+  }
+  cudaEvent_t e = nullptr;
+  cudaEventCreate(&e);
+  return e;
+}
+
+struct Timed {
+  pic_handle *h;
+  int cls;
+  cudaEvent_t a = nullptr;
+  Timed(pic_handle *h_, int c) : h(h_), cls(c) {
+    if (h->profiling) {
+      a = take_event(h);
+      cudaEventRecord(a, h->st);
+    }
+  }
+  ~Timed() {
+    if (h->profiling) {
+      cudaEvent_t b = take_event(h);
+      cudaEventRecord(b, h->st);
+      h->timers.push_back({cls, a, b});
+    }
+  }
+};
+
+void free_particles(Particles &p) {
+  cudaFree(p.cell);
+  for (int d = 0; d < 3; ++d) {
+    cudaFree(p.off[d]);
+    cudaFree(p.u[d]);
+  }
+  cudaFree(p.w);
+  cudaFree(p.id);
+  p = Particles{};
+}
+
+cudaError_t alloc_particles(Particles &p, int64_t cap, size_t rs, int dims) {
+  cudaError_t e;
+  const size_t n = (size_t)(cap > 0 ? cap : 1);
+  if ((e = cudaMalloc(&p.cell, n * sizeof(int32_t))) != cudaSuccess) return e;
+  for (int d = 0; d < 3; ++d) {
+    if (d < dims && (e = cudaMalloc(&p.off[d], n * rs)) != cudaSuccess) return e;
+    if ((e = cudaMalloc(&p.u[d], n * rs)) != cudaSuccess) return e;
+  }
+  if ((e = cudaMalloc(&p.w, n * rs)) != cudaSuccess) return e;
+  if ((e = cudaMalloc(&p.id, n * sizeof(uint32_t))) != cudaSuccess) return e;
+  return cudaSuccess;
+}
+
+int check_device_errors(pic_handle *h) {
+  Counters c;
+  CK(h, cudaMemcpyAsync(&c, h->ctr, sizeof(Counters), cudaMemcpyDeviceToHost, h->st), "read counters");
+  CK(h, cudaStreamSynchronize(h->st), "stream sync");
+  if (c.error) return fail(h, PIC_EOVERFLOW, "device-side error flags set");
+  return PIC_OK;
+}
+
+// Copy a device buffer to caller memory (host or device).
+int copy_out(pic_handle *h, void *dst, const void *src, size_t bytes, int mem_kind) {
+  CK(h,
+     cudaMemcpyAsync(dst, src, bytes, mem_kind == PIC_MEM_HOST ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice,
+                     h->st),
+     "copy out");
+  return PIC_OK;
+}
+
+int sort_species(pic_handle *h, Species &s) {
+  int nl = 0;
+  Timed tm(h, pic::KC_SORT);
+  CK(h,
+     pic::launch_sort(h->g, s.buf[s.cur], s.buf[1 - s.cur], s.d_count, s.capacity, h->keys, s.rank, s.tile_start,
+                      h->tile_tmp, h->st, &nl),
+     "sort");
+  h->launches += nl;
+  s.cur = 1 - s.cur;
+  s.need_sort = false;
+  return PIC_OK;
+}
+
+int compute_rho(pic_handle *h, double *rho) {
+  CK(h, cudaMemcpyAsync(rho, h->rho_bg, sizeof(double) * h->g.ncell, cudaMemcpyDeviceToDevice, h->st), "rho init");
+  for (int i = 0; i < h->nsp; ++i) {
+    Species &s = h->sp[i];
+    CK(h, pic::launch_rho(h->g, s.buf[s.cur], s.d_count, s.capacity, s.q, rho, h->st), "rho deposit");
+    h->launches++;
+  }
+  return PIC_OK;
+}
+
+int64_t read_count(pic_handle *h, Species &s) {
+  int64_t n = 0;
+  cudaMemcpyAsync(&n, s.d_count, sizeof(int64_t), cudaMemcpyDeviceToHost, h->st);
+  cudaStreamSynchronize(h->st);
+  s.h_count = n;
+  return n;
+}
+
+}  // namespace
+
+extern "C" {
+
+int pic_create(const pic_config *cfg, pic_handle **out) {
+  if (!out) return fail(nullptr, PIC_EINVAL, "out is NULL");
+  *out = nullptr;
+  if (!cfg) return fail(nullptr, PIC_EINVAL, "cfg is NULL");
+  const pic_config &c = *cfg;
+  if (c.dims != 2 && c.dims != 3) return fail(nullptr, PIC_EINVAL, "dims must be 2 or 3");
+  if (c.shape_order != 1 && c.shape_order != 2) return fail(nullptr, PIC_EINVAL, "shape_order must be 1 or 2");
+  if (c.precision != PIC_FP32 && c.precision != PIC_FP64) return fail(nullptr, PIC_EINVAL, "bad precision");
+  for (int d = 0; d < c.dims; ++d) {
+    if (c.n[d] < 1 || !(c.dx[d] > 0)) return fail(nullptr, PIC_EINVAL, "n and dx must be positive");
+    if (c.bc_lo[d] != PIC_BC_PERIODIC || c.bc_hi[d] != PIC_BC_PERIODIC) {
+      if (d != 0) return fail(nullptr, PIC_EINVAL, "only x walls may be absorbing");
+    }
+  }
+  if (c.bc_lo[0] == PIC_BC_ABSORBING || c.bc_hi[0] == PIC_BC_ABSORBING)
+    return fail(nullptr, PIC_EINVAL, "absorbing walls are not available in this build");
+  if (c.laser.enabled) return fail(nullptr, PIC_EINVAL, "laser injection is not available in this build");
+  if (c.dims == 2 && c.n[2] != 1 && c.n[2] != 0) return fail(nullptr, PIC_EINVAL, "2D needs n[2] = 1");
+  if (!(c.dt > 0)) return fail(nullptr, PIC_EINVAL, "dt must be positive");
+  double s = 0;
+  for (int d = 0; d < c.dims; ++d) s += 1.0 / (c.dx[d] * c.dx[d]);
+  const double lim = 1.0 / sqrt(s);
+  if (c.dt > lim) {
+    char b[160];
+    snprintf(b, sizeof b, "dt = %.6g exceeds the Yee limit (sum dx^-2)^(-1/2) = %.6g", c.dt, lim);
+    return fail(nullptr, PIC_ECOURANT, b);
+  }
+  const int64_t ncell = (int64_t)c.n[0] * c.n[1] * (c.dims == 3 ? c.n[2] : 1);
+  if (ncell > 0x7fffffffLL) return fail(nullptr, PIC_EINVAL, "more than 2^31 cells");
+
+  pic_handle *h = new pic_handle();
+  h->cfg = c;
+  Grid &g = h->g;
+  g.dims = c.dims;
+  g.order = c.shape_order;
+  g.prec = c.precision;
+  g.n[0] = c.n[0];
+  g.n[1] = c.n[1];
+  g.n[2] = c.dims == 3 ? c.n[2] : 1;
+  g.dx[0] = c.dx[0];
+  g.dx[1] = c.dx[1];
+  g.dx[2] = c.dims == 3 ? c.dx[2] : 1.0;
+  g.dt = c.dt;
+  g.ncell = ncell;
+  g.drift = c.drift_guard > 0 ? c.drift_guard : 1;
+  g.absorb_lo = c.bc_lo[0] == PIC_BC_ABSORBING;
+  g.absorb_hi = c.bc_hi[0] == PIC_BC_ABSORBING;
+  const int deft = c.dims == 3 ? 8 : 16;
+  g.ntiles = 1;
+  for (int d = 0; d < 3; ++d) {
+    int t = (d < c.dims) ? (c.tile[d] > 0 ? c.tile[d] : deft) : 1;
+    if (t > g.n[d]) t = g.n[d];
+    g.tile[d] = t;
+    g.ntile[d] = (g.n[d] + t - 1) / t;
+    g.ntiles *= g.ntile[d];
+  }
+  h->rsize = g.prec == PIC_FP64 ? sizeof(double) : sizeof(float);
+  h->st = static_cast<cudaStream_t>(c.stream);
+
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  int maxsm = 0;
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&maxsm, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+  if (e != cudaSuccess) {
+    delete h;
+    return fail(nullptr, PIC_ECUDA, std::string("no CUDA device: ") + cudaGetErrorString(e));
+  }
+  if (pic::push_smem_bytes(g) > (size_t)maxsm) {
+    delete h;
+    return fail(nullptr, PIC_EINVAL, "tile + guard window does not fit in shared memory; use a smaller tile");
+  }
+  const size_t fb = (size_t)ncell * h->rsize;
+  bool ok = true;
+  for (int d = 0; d < 3 && ok; ++d) {
+    ok = ok && cudaMalloc(&h->E[d], fb) == cudaSuccess && cudaMalloc(&h->B[d], fb) == cudaSuccess &&
+         cudaMalloc(&h->J[d], fb) == cudaSuccess;
+  }
+  const size_t db = (size_t)ncell * sizeof(double);
+  const int64_t nkeys = g.ntiles * g.tile[0] * g.tile[1] * g.tile[2];
+  ok = ok && cudaMalloc(&h->rho_bg, db) == cudaSuccess && cudaMalloc(&h->rho, db) == cudaSuccess &&
+       cudaMalloc(&h->rho_prev, db) == cudaSuccess && cudaMalloc(&h->f64, db) == cudaSuccess &&
+       cudaMalloc(&h->red, 16 * sizeof(double)) == cudaSuccess &&
+       cudaMalloc(&h->keys, (size_t)nkeys * sizeof(int32_t)) == cudaSuccess &&
+       cudaMalloc(&h->tile_tmp, (size_t)(g.ntiles + 1) * sizeof(int64_t)) == cudaSuccess &&
+       cudaMalloc(&h->ctr, sizeof(Counters)) == cudaSuccess && cudaMalloc(&h->bad, sizeof(unsigned long long)) == cudaSuccess;
+  if (!ok) {
+    pic_destroy(h);
+    return fail(nullptr, PIC_ENOMEM, "device allocation failed in pic_create");
+  }
+  for (int d = 0; d < 3; ++d) {
+    cudaMemsetAsync(h->E[d], 0, fb, h->st);
+    cudaMemsetAsync(h->B[d], 0, fb, h->st);
+    cudaMemsetAsync(h->J[d], 0, fb, h->st);
+  }
+  cudaMemsetAsync(h->rho_bg, 0, db, h->st);
+  cudaMemsetAsync(h->ctr, 0, sizeof(Counters), h->st);
+  e = cudaStreamSynchronize(h->st);
+  if (e != cudaSuccess) {
+    pic_destroy(h);
+    return fail(nullptr, PIC_ECUDA, std::string("pic_create: ") + cudaGetErrorString(e));
+  }
+  *out = h;
+  return PIC_OK;
+}
+
+int pic_destroy(pic_handle *h) {
+  if (!h) return PIC_OK;
+  cudaStreamSynchronize(h->st);
+  for (int d = 0; d < 3; ++d) {
+    cudaFree(h->E[d]);
+    cudaFree(h->B[d]);
+    cudaFree(h->J[d]);
+  }
+  cudaFree(h->rho_bg);
+  cudaFree(h->rho);
+  cudaFree(h->rho_prev);
+  cudaFree(h->f64);
+  cudaFree(h->red);
+  cudaFree(h->keys);
+  cudaFree(h->tile_tmp);
+  cudaFree(h->ctr);
+  cudaFree(h->bad);
+  for (int i = 0; i < h->nsp; ++i) {
+    Species &s = h->sp[i];
+    free_particles(s.buf[0]);
+    free_particles(s.buf[1]);
+    cudaFree(s.d_count);
+    cudaFree(s.rank);
+    cudaFree(s.tile_start);
+  }
+  for (auto &t : h->timers) {
+    cudaEventDestroy(t.a);
+    cudaEventDestroy(t.b);
+  }
+  for (auto e : h->event_pool) cudaEventDestroy(e);
+  delete h;
+  return PIC_OK;
+}
+
+const char *pic_last_error(const pic_handle *h) { return h ? h->err.c_str() : g_create_error.c_str(); }
+
+int pic_add_species(pic_handle *h, double q, double m, int64_t capacity, int *species) {
+  if (!h || !species) return fail(h, PIC_EINVAL, "NULL argument");
+  if (h->nsp >= kMaxSpecies) return fail(h, PIC_EINVAL, "too many species");
+  if (!(m > 0) || capacity < 0 || capacity > 0x7fffffffLL) return fail(h, PIC_EINVAL, "bad mass or capacity");
+  Species &s = h->sp[h->nsp];
+  s = Species{};
+  s.q = q;
+  s.m = m;
+  s.capacity = capacity;
+  cudaError_t e = alloc_particles(s.buf[0], capacity, h->rsize, h->g.dims);
+  if (e == cudaSuccess) e = alloc_particles(s.buf[1], capacity, h->rsize, h->g.dims);
+  if (e == cudaSuccess) e = cudaMalloc(&s.d_count, sizeof(int64_t));
+  if (e == cudaSuccess) e = cudaMalloc(&s.rank, (size_t)(capacity > 0 ? capacity : 1) * sizeof(int32_t));
+  if (e == cudaSuccess) e = cudaMalloc(&s.tile_start, (size_t)(h->g.ntiles + 1) * sizeof(int64_t));
+  if (e != cudaSuccess) {
+    free_particles(s.buf[0]);
+    free_particles(s.buf[1]);
+    cudaFree(s.d_count);
+    cudaFree(s.rank);
+    cudaFree(s.tile_start);
+    s = Species{};
+    cudaGetLastError();
+    return fail(h, PIC_ENOMEM, "device allocation failed in pic_add_species");
+  }
+  cudaMemsetAsync(s.d_count, 0, sizeof(int64_t), h->st);
+  cudaMemsetAsync(s.tile_start, 0, (size_t)(h->g.ntiles + 1) * sizeof(int64_t), h->st);
+  *species = h->nsp++;
+  return PIC_OK;
+}
+
+int pic_load_particles(pic_handle *h, int species, int64_t n, const double *x, const double *y, const double *z,
+                       const double *ux, const double *uy, const double *uz, const double *w, const uint32_t *id,
+                       int mem_kind) {
+  if (!h) return fail(h, PIC_EINVAL, "NULL handle");
+  if (species < 0 || species >= h->nsp) return fail(h, PIC_EINVAL, "bad species index");
+  if (n < 0) return fail(h, PIC_EINVAL, "negative count");
+  if (n == 0) return PIC_OK;
+  if (!x || !y || (h->g.dims == 3 && !z) || !ux || !uy || !uz || !w)
+    return fail(h, PIC_EINVAL, "NULL particle array");
+  Species &s = h->sp[species];
+  const int64_t cur = read_count(h, s);
+  if (cur + n > s.capacity) return fail(h, PIC_ENOMEM, "species capacity exceeded");
+  const double *src[7] = {x, y, z, ux, uy, uz, w};
+  const double *dsrc[7] = {};
+  std::vector<void *> tmp;
+  if (mem_kind == PIC_MEM_HOST) {
+    for (int a = 0; a < 7; ++a) {
+      if (!src[a]) continue;
+      void *p = nullptr;
+      CK(h, cudaMallocAsync(&p, (size_t)n * sizeof(double), h->st), "load staging alloc");
+      tmp.push_back(p);
+      CK(h, cudaMemcpyAsync(p, src[a], (size_t)n * sizeof(double), cudaMemcpyHostToDevice, h->st), "load H2D");
+      dsrc[a] = static_cast<const double *>(p);
+    }
+  } else {
+    for (int a = 0; a < 7; ++a) dsrc[a] = src[a];
+  }
+  const uint32_t *did = id;
+  std::vector<uint32_t> gen;
+  if (!id) {
+    gen.resize((size_t)n);
+    for (int64_t i = 0; i < n; ++i) gen[(size_t)i] = (uint32_t)(cur + i);
+    did = gen.data();
+  }
+  if (mem_kind == PIC_MEM_HOST || !id) {
+    void *p = nullptr;
+    CK(h, cudaMallocAsync(&p, (size_t)n * sizeof(uint32_t), h->st), "load staging alloc");
+    tmp.push_back(p);
+    CK(h, cudaMemcpyAsync(p, did, (size_t)n * sizeof(uint32_t), cudaMemcpyHostToDevice, h->st), "load H2D");
+    did = static_cast<const uint32_t *>(p);
+  }
+  CK(h, cudaMemsetAsync(h->bad, 0, sizeof(unsigned long long), h->st), "memset");
+  CK(h,
+     pic::launch_load(h->g, s.buf[s.cur], cur, n, dsrc[0], dsrc[1], dsrc[2], dsrc[3], dsrc[4], dsrc[5], dsrc[6], did,
+                      h->bad, h->st),
+     "load kernel");
+  h->launches++;
+  const int64_t nn = cur + n;
+  CK(h, cudaMemcpyAsync(s.d_count, &nn, sizeof(int64_t), cudaMemcpyHostToDevice, h->st), "count");
+  unsigned long long bad = 0;
+  CK(h, cudaMemcpyAsync(&bad, h->bad, sizeof(bad), cudaMemcpyDeviceToHost, h->st), "bad count");
+  for (void *p : tmp) cudaFreeAsync(p, h->st);
+  CK(h, cudaStreamSynchronize(h->st), "load sync");
+  s.h_count = nn;
+  s.need_sort = true;
+  if (bad) return fail(h, PIC_EINVAL, "particles outside an absorbing wall were marked dead");
+  return PIC_OK;
+}
+
+int pic_neutralize(pic_handle *h) {
+  if (!h) return fail(h, PIC_EINVAL, "NULL handle");
+  CK(h, cudaMemsetAsync(h->rho_bg, 0, sizeof(double) * h->g.ncell, h->st), "memset");
+  int r = compute_rho(h, h->rho);
+  if (r) return r;
+  // rho_bg = -rho
+  std::vector<double> tmp((size_t)h->g.ncell);
+  CK(h, cudaMemcpyAsync(tmp.data(), h->rho, sizeof(double) * h->g.ncell, cudaMemcpyDeviceToHost, h->st), "D2H");
+  CK(h, cudaStreamSynchronize(h->st), "sync");
+  for (auto &v : tmp) v = -v;
+  CK(h, cudaMemcpyAsync(h->rho_bg, tmp.data(), sizeof(double) * h->g.ncell, cudaMemcpyHostToDevice, h->st), "H2D");
+  CK(h, cudaStreamSynchronize(h->st), "sync");
+  return PIC_OK;
+}
+
+int pic_step(pic_handle *h, int nsteps) {
+  if (!h) return fail(h, PIC_EINVAL, "NULL handle");
+  if (nsteps < 0) return fail(h, PIC_EINVAL, "negative step count");
+  const int every = h->cfg.sort_every > 0 ? h->cfg.sort_every : 20;
+  const size_t fb = (size_t)h->g.ncell * h->rsize;
+  for (int t = 0; t < nsteps; ++t) {
+    for (int i = 0; i < h->nsp; ++i) {
+      Species &s = h->sp[i];
+      if (s.need_sort || h->step % every == 0) {
+        int r = sort_species(h, s);
+        if (r) return r;
+      }
+    }
+    {
+      Timed tm(h, pic::KC_ZEROJ);
+      for (int d = 0; d < 3; ++d) CK(h, cudaMemsetAsync(h->J[d], 0, fb, h->st), "zero J");
+    }
+    for (int i = 0; i < h->nsp; ++i) {
+      Species &s = h->sp[i];
+      Timed tm(h, pic::KC_PUSH);
+      CK(h, pic::launch_push(h->g, h->E, h->B, h->J, s.buf[s.cur], s.tile_start, s.q, s.m, h->ctr, h->st), "push");
+      h->launches++;
+    }
+    {
+      Timed tm(h, pic::KC_YEE_B);
+      CK(h, pic::launch_yee_b(h->g, h->E, h->B, 0.5 * h->g.dt, h->st), "yee B");
+    }
+    {
+      Timed tm(h, pic::KC_YEE_E);
+      CK(h, pic::launch_yee_e(h->g, h->E, h->B, h->J, h->g.dt, h->st), "yee E");
+    }
+    {
+      Timed tm(h, pic::KC_YEE_B);
+      CK(h, pic::launch_yee_b(h->g, h->E, h->B, 0.5 * h->g.dt, h->st), "yee B");
+    }
+    h->launches += 3;
+    h->step++;
+  }
+  return PIC_OK;
+}
+
+int pic_fields(pic_handle *h, int which, double *out, int mem_kind) {
+  if (!h || !out) return fail(h, PIC_EINVAL, "NULL argument");
+  if (which < PIC_EX || which > PIC_RHO) return fail(h, PIC_EINVAL, "bad field selector");
+  const size_t db = sizeof(double) * h->g.ncell;
+  if (which == PIC_RHO) {
+    int r = compute_rho(h, h->rho);
+    if (r) return r;
+    r = copy_out(h, out, h->rho, db, mem_kind);
+    if (r) return r;
+  } else {
+    void *src = which < 3 ? h->E[which] : which < 6 ? h->B[which - 3] : h->J[which - 6];
+    CK(h, pic::launch_field_to_f64(h->g, src, h->f64, h->st), "convert");
+    int r = copy_out(h, out, h->f64, db, mem_kind);
+    if (r) return r;
+  }
+  return check_device_errors(h);
+}
+
+int pic_set_field(pic_handle *h, int which, const double *in, int mem_kind) {
+  if (!h || !in) return fail(h, PIC_EINVAL, "NULL argument");
+  if (which < PIC_EX || which > PIC_JZ) return fail(h, PIC_EINVAL, "bad field selector");
+  const size_t db = sizeof(double) * h->g.ncell;
+  CK(h, cudaMemcpyAsync(h->f64, in, db, mem_kind == PIC_MEM_HOST ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice,
+                        h->st),
+     "set field copy");
+  void *dst = which < 3 ? h->E[which] : which < 6 ? h->B[which - 3] : h->J[which - 6];
+  CK(h, pic::launch_field_from_f64(h->g, h->f64, dst, h->st), "convert");
+  CK(h, cudaStreamSynchronize(h->st), "sync");
+  return PIC_OK;
+}
+
+int pic_num_particles(pic_handle *h, int species, int64_t *n) {
+  if (!h || !n) return fail(h, PIC_EINVAL, "NULL argument");
+  if (species < 0 || species >= h->nsp) return fail(h, PIC_EINVAL, "bad species index");
+  *n = read_count(h, h->sp[species]);
+  return PIC_OK;
+}
+
+int pic_particles(pic_handle *h, int species, double *x, double *y, double *z, double *ux, double *uy, double *uz,
+                  double *w, uint32_t *id, int32_t *alive, int mem_kind) {
+  if (!h) return fail(h, PIC_EINVAL, "NULL handle");
+  if (species < 0 || species >= h->nsp) return fail(h, PIC_EINVAL, "bad species index");
+  Species &s = h->sp[species];
+  const int64_t n = read_count(h, s);
+  if (n == 0) return PIC_OK;
+  double *outs[7] = {x, y, z, ux, uy, uz, w};
+  double *dev[7] = {};
+  uint32_t *did = nullptr;
+  int32_t *dal = nullptr;
+  std::vector<void *> tmp;
+  auto dalloc = [&](size_t b) -> void * {
+    void *p = nullptr;
+    if (cudaMallocAsync(&p, b, h->st) != cudaSuccess) return nullptr;
+    tmp.push_back(p);
+    return p;
+  };
+  const bool host = mem_kind == PIC_MEM_HOST;
+  for (int a = 0; a < 7; ++a)
+    if (outs[a]) dev[a] = host ? static_cast<double *>(dalloc((size_t)n * sizeof(double))) : outs[a];
+  if (id) did = host ? static_cast<uint32_t *>(dalloc((size_t)n * sizeof(uint32_t))) : id;
+  if (alive) dal = host ? static_cast<int32_t *>(dalloc((size_t)n * sizeof(int32_t))) : alive;
+  for (int a = 0; a < 7; ++a)
+    if (outs[a] && !dev[a]) return fail(h, PIC_ENOMEM, "staging allocation failed");
+  CK(h,
+     pic::launch_unload(h->g, s.buf[s.cur], s.d_count, n, dev[0], dev[1], dev[2], dev[3], dev[4], dev[5], dev[6],
+                        did, dal, h->st),
+     "unload");
+  h->launches++;
+  if (host) {
+    for (int a = 0; a < 7; ++a)
+      if (outs[a]) CK(h, cudaMemcpyAsync(outs[a], dev[a], (size_t)n * sizeof(double), cudaMemcpyDeviceToHost, h->st), "D2H");
+    if (id) CK(h, cudaMemcpyAsync(id, did, (size_t)n * sizeof(uint32_t), cudaMemcpyDeviceToHost, h->st), "D2H");
+    if (alive) CK(h, cudaMemcpyAsync(alive, dal, (size_t)n * sizeof(int32_t), cudaMemcpyDeviceToHost, h->st), "D2H");
+  }
+  for (void *p : tmp) cudaFreeAsync(p, h->st);
+  return check_device_errors(h);
+}
+
+int pic_diag(pic_handle *h, pic_diag_t *out) {
+  if (!h || !out) return fail(h, PIC_EINVAL, "NULL argument");
+  memset(out, 0, sizeof(*out));
+  int r = compute_rho(h, h->rho);
+  if (r) return r;
+  CK(h, cudaMemsetAsync(h->red, 0, 16 * sizeof(double), h->st), "memset");
+  const bool have_prev = h->rho_prev_step == h->step - 1;
+  CK(h, pic::launch_field_diag(h->g, h->E, h->B, h->J, h->rho, have_prev ? h->rho_prev : nullptr, h->red, h->st),
+     "field diag");
+  h->launches++;
+  for (int i = 0; i < h->nsp; ++i) {
+    Species &s = h->sp[i];
+    CK(h, pic::launch_particle_diag(h->g, s.buf[s.cur], s.d_count, s.capacity, s.m, h->red + 8, h->st), "part diag");
+    h->launches++;
+  }
+  double red[16];
+  Counters c;
+  CK(h, cudaMemcpyAsync(red, h->red, sizeof red, cudaMemcpyDeviceToHost, h->st), "D2H");
+  CK(h, cudaMemcpyAsync(&c, h->ctr, sizeof c, cudaMemcpyDeviceToHost, h->st), "D2H");
+  CK(h, cudaMemcpyAsync(h->rho_prev, h->rho, sizeof(double) * h->g.ncell, cudaMemcpyDeviceToDevice, h->st), "copy");
+  CK(h, cudaStreamSynchronize(h->st), "diag sync");
+  h->rho_prev_step = h->step;
+  const double dV = h->g.dx[0] * h->g.dx[1] * h->g.dx[2];
+  out->energy_e = 0.5 * red[0] * dV;
+  out->energy_b = 0.5 * red[1] * dV;
+  out->energy_field = out->energy_e + out->energy_b;
+  out->charge = red[2] * dV;
+  out->gauss_max = red[3];
+  out->continuity_max = have_prev ? red[4] : -1.0;
+  out->energy_kinetic = red[8] * dV;
+  out->n_alive = (int64_t)red[9];
+  out->n_escaped = (int64_t)c.escaped;
+  out->n_clamped = (int64_t)c.clamped;
+  out->n_absorbed = (int64_t)c.absorbed;
+  out->step = h->step;
+  if (c.error) return fail(h, PIC_EOVERFLOW, "device-side error flags set");
+  if (red[5] > 0 || red[10] > 0) return fail(h, PIC_ENAN, "non-finite field or momentum values");
+  return PIC_OK;
+}
+
+int pic_sync(pic_handle *h) {
+  if (!h) return fail(h, PIC_EINVAL, "NULL handle");
+  return check_device_errors(h);
+}
+
+int pic_profile(pic_handle *h, int enable) {
+  if (!h) return fail(h, PIC_EINVAL, "NULL handle");
+  cudaStreamSynchronize(h->st);
+  for (auto &t : h->timers) {
+    h->event_pool.push_back(t.a);
+    h->event_pool.push_back(t.b);
+  }
+  h->timers.clear();
+  h->profiling = enable != 0;
+  return PIC_OK;
+}
+
+int pic_timings(pic_handle *h, double *ms, int64_t *launches, int nmax, int *ncls) {
+  if (!h) return fail(h, PIC_EINVAL, "NULL handle");
+  CK(h, cudaStreamSynchronize(h->st), "sync");
+  double acc[pic::KC_N] = {};
+  int64_t cnt[pic::KC_N] = {};
+  for (auto &t : h->timers) {
+    float v = 0.f;
+    CK(h, cudaEventElapsedTime(&v, t.a, t.b), "event time");
+    acc[t.cls] += v;
+    cnt[t.cls] += 1;
+  }
+  const int n = nmax < pic::KC_N ? nmax : pic::KC_N;
+  for (int i = 0; i < n; ++i) {
+    if (ms) ms[i] = acc[i];
+    if (launches) launches[i] = cnt[i];
+  }
+  if (ncls) *ncls = n;
+  return PIC_OK;
+}
+
+int pic_launch_count(pic_handle *h, int64_t *count) {
+  if (!h || !count) return fail(h, PIC_EINVAL, "NULL argument");
+  *count = h->launches;
+  return PIC_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,400 @@
+// Grid kernels: Yee FDTD curl updates (§2 Maxwell curl equations, FDTD on
+// the Yee lattice per ref [9] of the paper), particle load/unload between
+// global FP64 coordinates and (cell, offset), and the FP64 diagnostics.
+#include <cuda_runtime.h>
+#include <math.h>
+
+#include "pic_device.cuh"
+
+namespace pic {
+
+namespace {
+
+int grid_blocks(int64_t n, int per_block) {
+  int dev = 0, nsm = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+  const int64_t want = (n + per_block - 1) / per_block;
+  const int64_t cap = (int64_t)nsm * 32;
+  return (int)(want < 1 ? 1 : (want < cap ? want : cap));
+}
+
+template <class R> struct YeeArgs {
+  int n[3];
+  R rdx[3];  // 1/dx_a
+  R h;       // time step of this update
+  R *E[3];
+  R *B[3];
+  const R *J[3];
+};
+
+// B <- B - h curl E, curl E at the B locations.
+template <class R, int DIM>
+__global__ void __launch_bounds__(256) k_yee_b(YeeArgs<R> a) {
+  const int n0 = a.n[0], n1 = a.n[1], n2 = a.n[2];
+  const int64_t ncell = (int64_t)n0 * n1 * n2;
+  const int64_t sy = n0, sz = (int64_t)n0 * n1;
+  for (int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; c < ncell; c += (int64_t)gridDim.x * blockDim.x) {
+    const int i = (int)(c % n0);
+    const int64_t r = c / n0;
+    const int j = (int)(r % n1);
+    const int k = (int)(r / n1);
+    const int64_t cxp = c + (i + 1 < n0 ? 1 : 1 - n0);
+    const int64_t cyp = c + (j + 1 < n1 ? sy : sy - sy * n1);
+    const R ex = a.E[0][c], ey = a.E[1][c], ez = a.E[2][c];
+    R cx = (a.E[2][cyp] - ez) * a.rdx[1];
+    R cy = -(a.E[2][cxp] - ez) * a.rdx[0];
+    const R cz = (a.E[1][cxp] - ey) * a.rdx[0] - (a.E[0][cyp] - ex) * a.rdx[1];
+    if (DIM == 3) {
+      const int64_t czp = c + (k + 1 < n2 ? sz : sz - sz * n2);
+      cx -= (a.E[1][czp] - ey) * a.rdx[2];
+      cy += (a.E[0][czp] - ex) * a.rdx[2];
+    }
+    a.B[0][c] -= a.h * cx;
+    a.B[1][c] -= a.h * cy;
+    a.B[2][c] -= a.h * cz;
+  }
+}
+
+// E <- E + h (curl B - J), curl B at the E locations.
+template <class R, int DIM>
+__global__ void __launch_bounds__(256) k_yee_e(YeeArgs<R> a) {
+  const int n0 = a.n[0], n1 = a.n[1], n2 = a.n[2];
+  const int64_t ncell = (int64_t)n0 * n1 * n2;
+  const int64_t sy = n0, sz = (int64_t)n0 * n1;
+  for (int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; c < ncell; c += (int64_t)gridDim.x * blockDim.x) {
+    const int i = (int)(c % n0);
+    const int64_t r = c / n0;
+    const int j = (int)(r % n1);
+    const int k = (int)(r / n1);
+    const int64_t cxm = c - (i > 0 ? 1 : 1 - n0);
+    const int64_t cym = c - (j > 0 ? sy : sy - sy * n1);
+    const R bx = a.B[0][c], by = a.B[1][c], bz = a.B[2][c];
+    R cx = (bz - a.B[2][cym]) * a.rdx[1];
+    R cy = -(bz - a.B[2][cxm]) * a.rdx[0];
+    const R cz = (by - a.B[1][cxm]) * a.rdx[0] - (bx - a.B[0][cym]) * a.rdx[1];
+    if (DIM == 3) {
+      const int64_t czm = c - (k > 0 ? sz : sz - sz * n2);
+      cx -= (by - a.B[1][czm]) * a.rdx[2];
+      cy += (bx - a.B[0][czm]) * a.rdx[2];
+    }
+    a.E[0][c] += a.h * (cx - a.J[0][c]);
+    a.E[1][c] += a.h * (cy - a.J[1][c]);
+    a.E[2][c] += a.h * (cz - a.J[2][c]);
+  }
+}
+
+template <class R>
+YeeArgs<R> yee_args(const Grid &g, void *const E[3], void *const B[3], void *const J[3], double h) {
+  YeeArgs<R> a;
+  for (int d = 0; d < 3; ++d) {
+    a.n[d] = g.n[d];
+    a.rdx[d] = (R)(1.0 / g.dx[d]);
+    a.E[d] = static_cast<R *>(E[d]);
+    a.B[d] = static_cast<R *>(B[d]);
+    a.J[d] = J ? static_cast<const R *>(J[d]) : nullptr;
+  }
+  a.h = (R)h;
+  return a;
+}
+
+// ---- particle load: global (x, y, z) -> (cell, offset) ----
+template <class R>
+__global__ void k_load(int dims, int n0, int n1, int n2, double rdx0, double rdx1, double rdx2, int absorb, Particles p,
+                       int64_t offset, int64_t n, const double *__restrict__ x, const double *__restrict__ y,
+                       const double *__restrict__ z, const double *__restrict__ ux, const double *__restrict__ uy,
+                       const double *__restrict__ uz, const double *__restrict__ w, const uint32_t *__restrict__ id,
+                       unsigned long long *bad) {
+  for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < n; q += (int64_t)gridDim.x * blockDim.x) {
+    const double pos[3] = {x[q] * rdx0, y[q] * rdx1, dims == 3 ? z[q] * rdx2 : 0.0};
+    const int nn[3] = {n0, n1, n2};
+    int ci[3] = {0, 0, 0};
+    R off[3] = {R(0), R(0), R(0)};
+    bool ok = true;
+    for (int d = 0; d < dims; ++d) {
+      const double fl = floor(pos[d]);
+      double f = pos[d] - fl;
+      long long i = (long long)fl;
+      R fr = (R)f;
+      if (fr >= R(1)) {  // rounding of the narrowing conversion
+        fr = R(0);
+        i += 1;
+      }
+      if (d == 0 && absorb && (i < 0 || i >= nn[0])) ok = false;
+      i %= nn[d];
+      if (i < 0) i += nn[d];
+      ci[d] = (int)i;
+      off[d] = fr;
+    }
+    const int64_t s = offset + q;
+    if (!ok) {
+      atomicAdd(bad, 1ull);
+      p.cell[s] = -1;
+    } else {
+      p.cell[s] = ci[0] + n0 * (ci[1] + n1 * ci[2]);
+    }
+    for (int d = 0; d < 3; ++d) {
+      if (d < dims) static_cast<R *>(p.off[d])[s] = off[d];
+    }
+    static_cast<R *>(p.u[0])[s] = (R)ux[q];
+    static_cast<R *>(p.u[1])[s] = (R)uy[q];
+    static_cast<R *>(p.u[2])[s] = (R)uz[q];
+    static_cast<R *>(p.w)[s] = (R)w[q];
+    p.id[s] = id ? id[q] : (uint32_t)q;
+  }
+}
+
+// ---- particle unload: (cell, offset) -> global FP64 ----
+template <class R>
+__global__ void k_unload(int dims, int n0, int n1, double dx0, double dx1, double dx2, Particles p,
+                         const int64_t *__restrict__ d_count, double *x, double *y, double *z, double *ux, double *uy,
+                         double *uz, double *w, uint32_t *id, int32_t *alive) {
+  const int64_t n = *d_count;
+  for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < n; q += (int64_t)gridDim.x * blockDim.x) {
+    const int c = p.cell[q];
+    const int i = c < 0 ? 0 : c % n0;
+    const int r = c < 0 ? 0 : c / n0;
+    const int j = r % n1;
+    const int k = r / n1;
+    if (x) x[q] = ((double)i + (double)static_cast<const R *>(p.off[0])[q]) * dx0;
+    if (y) y[q] = ((double)j + (double)static_cast<const R *>(p.off[1])[q]) * dx1;
+    if (z) z[q] = dims == 3 ? ((double)k + (double)static_cast<const R *>(p.off[2])[q]) * dx2 : 0.0;
+    if (ux) ux[q] = (double)static_cast<const R *>(p.u[0])[q];
+    if (uy) uy[q] = (double)static_cast<const R *>(p.u[1])[q];
+    if (uz) uz[q] = (double)static_cast<const R *>(p.u[2])[q];
+    if (w) w[q] = (double)static_cast<const R *>(p.w)[q];
+    if (id) id[q] = p.id[q];
+    if (alive) alive[q] = c >= 0 ? 1 : 0;
+  }
+}
+
+template <class Rs, class Rd>
+__global__ void k_convert(const Rs *__restrict__ s, Rd *__restrict__ d, int64_t n) {
+  for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < n; q += (int64_t)gridDim.x * blockDim.x)
+    d[q] = (Rd)s[q];
+}
+
+// ---- charge density at the nodes: rho += q w S(X-i) S(Y-j) S(Z-k) ----
+template <class R>
+__global__ void k_rho(int dims, int order, int n0, int n1, int n2, double q, Particles p,
+                      const int64_t *__restrict__ d_count, double *rho) {
+  const int64_t n = *d_count;
+  for (int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; s < n; s += (int64_t)gridDim.x * blockDim.x) {
+    const int c = p.cell[s];
+    if (c < 0) continue;
+    const int ci[3] = {c % n0, (c / n0) % n1, dims == 3 ? c / (n0 * n1) : 0};
+    const int nn[3] = {n0, n1, n2};
+    int base[3] = {0, 0, 0};
+    double wt[3][3] = {{1, 0, 0}, {1, 0, 0}, {1, 0, 0}};
+    int ns[3] = {1, 1, 1};
+    for (int d = 0; d < dims; ++d) {
+      const double f = (double)static_cast<const R *>(p.off[d])[s];
+      if (order == 2) {
+        const int h = f >= 0.5;
+        const double dd = f - h;
+        const double a = 0.5 - dd, b = 0.5 + dd;
+        wt[d][0] = 0.5 * a * a;
+        wt[d][1] = 0.75 - dd * dd;
+        wt[d][2] = 0.5 * b * b;
+        base[d] = ci[d] + h - 1;
+        ns[d] = 3;
+      } else {
+        wt[d][0] = 1.0 - f;
+        wt[d][1] = f;
+        base[d] = ci[d];
+        ns[d] = 2;
+      }
+    }
+    const double qw = q * (double)static_cast<const R *>(p.w)[s];
+    for (int kz = 0; kz < ns[2]; ++kz)
+      for (int ky = 0; ky < ns[1]; ++ky)
+        for (int kx = 0; kx < ns[0]; ++kx) {
+          const int gi = wrapi(base[0] + kx, nn[0]);
+          const int gj = wrapi(base[1] + ky, nn[1]);
+          const int gk = dims == 3 ? wrapi(base[2] + kz, nn[2]) : 0;
+          atomicAdd(rho + gi + (int64_t)n0 * (gj + (int64_t)n1 * gk), qw * wt[0][kx] * wt[1][ky] * wt[2][kz]);
+        }
+  }
+}
+
+template <class R>
+__global__ void __launch_bounds__(256)
+    k_field_diag(int dims, int n0, int n1, int n2, double rdx0, double rdx1, double rdx2, double rdt, const R *Ex,
+                 const R *Ey, const R *Ez, const R *Bx, const R *By, const R *Bz, const R *Jx, const R *Jy,
+                 const R *Jz, const double *rho, const double *rho_prev, double *out) {
+  __shared__ double sh[32];
+  const int64_t ncell = (int64_t)n0 * n1 * n2;
+  double se = 0, sb = 0, sq = 0, gm = 0, cm = 0, nf = 0;
+  for (int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; c < ncell; c += (int64_t)gridDim.x * blockDim.x) {
+    const int i = (int)(c % n0);
+    const int64_t r = c / n0;
+    const int j = (int)(r % n1);
+    const int k = (int)(r / n1);
+    const double ex = Ex[c], ey = Ey[c], ez = Ez[c], bx = Bx[c], by = By[c], bz = Bz[c];
+    se += ex * ex + ey * ey + ez * ez;
+    sb += bx * bx + by * by + bz * bz;
+    if (!isfinite(ex) || !isfinite(ey) || !isfinite(ez) || !isfinite(bx) || !isfinite(by) || !isfinite(bz)) nf += 1;
+    const int64_t cxm = c - (i > 0 ? 1 : 1 - n0);
+    const int64_t cym = c - (j > 0 ? n0 : (int64_t)n0 - (int64_t)n0 * n1);
+    const int64_t czm = c - (k > 0 ? (int64_t)n0 * n1 : (int64_t)n0 * n1 - (int64_t)n0 * n1 * n2);
+    double div = ((double)Ex[c] - (double)Ex[cxm]) * rdx0 + ((double)Ey[c] - (double)Ey[cym]) * rdx1;
+    double dj = ((double)Jx[c] - (double)Jx[cxm]) * rdx0 + ((double)Jy[c] - (double)Jy[cym]) * rdx1;
+    if (dims == 3) {
+      div += ((double)Ez[c] - (double)Ez[czm]) * rdx2;
+      dj += ((double)Jz[c] - (double)Jz[czm]) * rdx2;
+    }
+    sq += rho[c];
+    gm = fmax(gm, fabs(div - rho[c]));
+    if (rho_prev) cm = fmax(cm, fabs((rho[c] - rho_prev[c]) * rdt + dj));
+  }
+  double v;
+  v = block_sum(se, sh);
+  if (threadIdx.x == 0) atomicAdd(out + 0, v);
+  v = block_sum(sb, sh);
+  if (threadIdx.x == 0) atomicAdd(out + 1, v);
+  v = block_sum(sq, sh);
+  if (threadIdx.x == 0) atomicAdd(out + 2, v);
+  v = block_max(gm, sh);
+  if (threadIdx.x == 0) atomic_max_nonneg(out + 3, v);
+  v = block_max(cm, sh);
+  if (threadIdx.x == 0) atomic_max_nonneg(out + 4, v);
+  v = block_sum(nf, sh);
+  if (threadIdx.x == 0) atomicAdd(out + 5, v);
+}
+
+template <class R>
+__global__ void __launch_bounds__(256)
+    k_particle_diag(Particles p, const int64_t *__restrict__ d_count, double m, double *out) {
+  __shared__ double sh[32];
+  const int64_t n = *d_count;
+  double ek = 0, cnt = 0, nf = 0;
+  for (int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; s < n; s += (int64_t)gridDim.x * blockDim.x) {
+    if (p.cell[s] < 0) continue;
+    const double ux = static_cast<const R *>(p.u[0])[s], uy = static_cast<const R *>(p.u[1])[s],
+                 uz = static_cast<const R *>(p.u[2])[s];
+    const double u2 = ux * ux + uy * uy + uz * uz;
+    // gamma - 1 = u^2 / (sqrt(1 + u^2) + 1), free of cancellation
+    ek += (double)static_cast<const R *>(p.w)[s] * m * (u2 / (sqrt(1.0 + u2) + 1.0));
+    cnt += 1;
+    if (!isfinite(u2)) nf += 1;
+  }
+  double v = block_sum(ek, sh);
+  if (threadIdx.x == 0) atomicAdd(out + 0, v);
+  v = block_sum(cnt, sh);
+  if (threadIdx.x == 0) atomicAdd(out + 1, v);
+  v = block_sum(nf, sh);
+  if (threadIdx.x == 0) atomicAdd(out + 2, v);
+}
+
+}  // namespace
+
+cudaError_t launch_yee_b(const Grid &g, void *const E[3], void *const B[3], double h, cudaStream_t st) {
+  const int nb = grid_blocks(g.ncell, 256);
+  if (g.prec == 1) {
+    auto a = yee_args<double>(g, E, B, nullptr, h);
+    if (g.dims == 3) k_yee_b<double, 3><<<nb, 256, 0, st>>>(a);
+    else k_yee_b<double, 2><<<nb, 256, 0, st>>>(a);
+  } else {
+    auto a = yee_args<float>(g, E, B, nullptr, h);
+    if (g.dims == 3) k_yee_b<float, 3><<<nb, 256, 0, st>>>(a);
+    else k_yee_b<float, 2><<<nb, 256, 0, st>>>(a);
+  }
+  return cudaGetLastError();
+}
+
+cudaError_t launch_yee_e(const Grid &g, void *const E[3], void *const B[3], void *const J[3], double h,
+                         cudaStream_t st) {
+  const int nb = grid_blocks(g.ncell, 256);
+  if (g.prec == 1) {
+    auto a = yee_args<double>(g, E, B, J, h);
+    if (g.dims == 3) k_yee_e<double, 3><<<nb, 256, 0, st>>>(a);
+    else k_yee_e<double, 2><<<nb, 256, 0, st>>>(a);
+  } else {
+    auto a = yee_args<float>(g, E, B, J, h);
+    if (g.dims == 3) k_yee_e<float, 3><<<nb, 256, 0, st>>>(a);
+    else k_yee_e<float, 2><<<nb, 256, 0, st>>>(a);
+  }
+  return cudaGetLastError();
+}
+
+cudaError_t launch_load(const Grid &g, const Particles &p, int64_t offset, int64_t n, const double *x,
+                        const double *y, const double *z, const double *ux, const double *uy, const double *uz,
+                        const double *w, const uint32_t *id, unsigned long long *bad, cudaStream_t st) {
+  if (n <= 0) return cudaSuccess;
+  const int nb = grid_blocks(n, 256);
+  const int absorb = g.absorb_lo || g.absorb_hi;
+  if (g.prec == 1)
+    k_load<double><<<nb, 256, 0, st>>>(g.dims, g.n[0], g.n[1], g.n[2], 1.0 / g.dx[0], 1.0 / g.dx[1], 1.0 / g.dx[2],
+                                       absorb, p, offset, n, x, y, z, ux, uy, uz, w, id, bad);
+  else
+    k_load<float><<<nb, 256, 0, st>>>(g.dims, g.n[0], g.n[1], g.n[2], 1.0 / g.dx[0], 1.0 / g.dx[1], 1.0 / g.dx[2],
+                                      absorb, p, offset, n, x, y, z, ux, uy, uz, w, id, bad);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_unload(const Grid &g, const Particles &p, const int64_t *d_count, int64_t nmax, double *x,
+                          double *y, double *z, double *ux, double *uy, double *uz, double *w, uint32_t *id,
+                          int32_t *alive, cudaStream_t st) {
+  const int nb = grid_blocks(nmax, 256);
+  if (g.prec == 1)
+    k_unload<double><<<nb, 256, 0, st>>>(g.dims, g.n[0], g.n[1], g.dx[0], g.dx[1], g.dx[2], p, d_count, x, y, z, ux,
+                                         uy, uz, w, id, alive);
+  else
+    k_unload<float><<<nb, 256, 0, st>>>(g.dims, g.n[0], g.n[1], g.dx[0], g.dx[1], g.dx[2], p, d_count, x, y, z, ux,
+                                        uy, uz, w, id, alive);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_field_to_f64(const Grid &g, const void *src, double *dst, cudaStream_t st) {
+  const int nb = grid_blocks(g.ncell, 256);
+  if (g.prec == 1)
+    return cudaMemcpyAsync(dst, src, sizeof(double) * g.ncell, cudaMemcpyDeviceToDevice, st);
+  k_convert<float, double><<<nb, 256, 0, st>>>(static_cast<const float *>(src), dst, g.ncell);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_field_from_f64(const Grid &g, const double *src, void *dst, cudaStream_t st) {
+  const int nb = grid_blocks(g.ncell, 256);
+  if (g.prec == 1)
+    return cudaMemcpyAsync(dst, src, sizeof(double) * g.ncell, cudaMemcpyDeviceToDevice, st);
+  k_convert<double, float><<<nb, 256, 0, st>>>(src, static_cast<float *>(dst), g.ncell);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_rho(const Grid &g, const Particles &p, const int64_t *d_count, int64_t nmax, double q,
+                       double *rho, cudaStream_t st) {
+  const int nb = grid_blocks(nmax, 256);
+  if (g.prec == 1)
+    k_rho<double><<<nb, 256, 0, st>>>(g.dims, g.order, g.n[0], g.n[1], g.n[2], q, p, d_count, rho);
+  else
+    k_rho<float><<<nb, 256, 0, st>>>(g.dims, g.order, g.n[0], g.n[1], g.n[2], q, p, d_count, rho);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_field_diag(const Grid &g, void *const E[3], void *const B[3], void *const J[3],
+                              const double *rho, const double *rho_prev, double *out, cudaStream_t st) {
+  const int nb = grid_blocks(g.ncell, 256);
+  const double r0 = 1.0 / g.dx[0], r1 = 1.0 / g.dx[1], r2 = 1.0 / g.dx[2], rdt = 1.0 / g.dt;
+  if (g.prec == 1) {
+    auto c = [](void *v) { return static_cast<const double *>(v); };
+    k_field_diag<double><<<nb, 256, 0, st>>>(g.dims, g.n[0], g.n[1], g.n[2], r0, r1, r2, rdt, c(E[0]), c(E[1]),
+                                             c(E[2]), c(B[0]), c(B[1]), c(B[2]), c(J[0]), c(J[1]), c(J[2]), rho,
+                                             rho_prev, out);
+  } else {
+    auto c = [](void *v) { return static_cast<const float *>(v); };
+    k_field_diag<float><<<nb, 256, 0, st>>>(g.dims, g.n[0], g.n[1], g.n[2], r0, r1, r2, rdt, c(E[0]), c(E[1]),
+                                            c(E[2]), c(B[0]), c(B[1]), c(B[2]), c(J[0]), c(J[1]), c(J[2]), rho,
+                                            rho_prev, out);
+  }
+  return cudaGetLastError();
+}
+
+cudaError_t launch_particle_diag(const Grid &g, const Particles &p, const int64_t *d_count, int64_t nmax, double m,
+                                 double *out, cudaStream_t st) {
+  const int nb = grid_blocks(nmax, 256);
+  if (g.prec == 1) k_particle_diag<double><<<nb, 256, 0, st>>>(p, d_count, m, out);
+  else k_particle_diag<float><<<nb, 256, 0, st>>>(p, d_count, m, out);
+  return cudaGetLastError();
+}
+
+}  // namespace pic

@@ -1,0 +1,155 @@
+// Device helpers shared by the kernels: shape weights, Boris rotation,
+// index wrapping.  Everything is templated on the real type R (float for the
+// cell-relative FP32 path, double for the FP64 path).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "pic_internal.h"
+
+namespace pic {
+
+__device__ __forceinline__ int wrapi(int i, int n) {
+  i %= n;
+  return i < 0 ? i + n : i;
+}
+
+// Largest value below one (offsets live in [0, 1)).
+template <class R> __device__ __forceinline__ R below_one();
+template <> __device__ __forceinline__ float below_one<float>() { return 0.99999994f; }
+template <> __device__ __forceinline__ double below_one<double>() { return 0.99999999999999989; }
+
+// Quadratic B-spline (TSC) weights on the nodes nearest-1, nearest,
+// nearest+1 for a particle at distance d = X - nearest, |d| <= 1/2.
+template <class R> __device__ __forceinline__ void tsc3(R d, R w[3]) {
+  const R a = R(0.5) - d, b = R(0.5) + d;
+  w[0] = R(0.5) * a * a;
+  w[1] = R(0.75) - d * d;
+  w[2] = R(0.5) * b * b;
+}
+
+// Gather stencil along one axis for a particle at cell-relative offset f.
+// Integer ("primal") positions m sit at m; half-integer ("dual") positions m
+// sit at m + 1/2.  `rel` is the first node relative to the particle's cell.
+template <class R, int ORDER> struct GatherAxis {
+  static constexpr int NS = ORDER + 1;
+  int relp, reld;
+  R wp[NS], wd[NS];
+  __device__ __forceinline__ void set(R f) {
+    if (ORDER == 2) {
+      const int h = f >= R(0.5);
+      relp = h - 1;
+      tsc3<R>(f - R(h), wp);
+      reld = -1;
+      tsc3<R>(f - R(0.5), wd);
+    } else {
+      relp = 0;
+      wp[0] = R(1) - f;
+      wp[1] = f;
+      if (f >= R(0.5)) {
+        reld = 0;
+        wd[0] = R(1.5) - f;
+        wd[1] = f - R(0.5);
+      } else {
+        reld = -1;
+        wd[0] = R(0.5) - f;
+        wd[1] = R(0.5) + f;
+      }
+    }
+  }
+};
+
+// Deposit stencil along one axis (Esirkepov, compact form): the shapes
+// before (S0, offset f in the old cell) and after (S1, offset fn in the cell
+// shifted by s) a move, on NW = ORDER + 2 consecutive nodes starting at `rel`
+// (relative to the old cell).
+template <class R, int ORDER> struct DepositAxis {
+  static constexpr int NW = ORDER + 2;
+  int rel;
+  R S0[NW], DS[NW];
+  __device__ __forceinline__ void set(R f, int s, R fn) {
+    R w0[ORDER + 1], w1[ORDER + 1];
+    int n0, n1;
+    if (ORDER == 2) {
+      const int h0 = f >= R(0.5), h1 = fn >= R(0.5);
+      tsc3<R>(f - R(h0), w0);
+      tsc3<R>(fn - R(h1), w1);
+      n0 = h0 - 1;      // first node of the old support
+      n1 = s + h1 - 1;  // first node of the new support
+    } else {
+      w0[0] = R(1) - f;
+      w0[1] = f;
+      w1[0] = R(1) - fn;
+      w1[1] = fn;
+      n0 = 0;
+      n1 = s;
+    }
+    rel = n0 < n1 ? n0 : n1;
+    const int o0 = n0 - rel, o1 = n1 - rel;
+#pragma unroll
+    for (int k = 0; k < NW; ++k) {
+      R a = R(0), b = R(0);
+#pragma unroll
+      for (int q = 0; q <= ORDER; ++q) {
+        a = (k - o0 == q) ? w0[q] : a;
+        b = (k - o1 == q) ? w1[q] : b;
+      }
+      S0[k] = a;
+      DS[k] = b - a;
+    }
+  }
+};
+
+// Boris rotation in the variable u = gamma v (ref [8] of the paper; §2 eq. 3):
+// half electric kick, magnetic rotation, half electric kick.  h = q dt/(2m).
+template <class R>
+__device__ __forceinline__ void boris(R h, const R E[3], const R B[3], R u[3]) {
+  const R umx = u[0] + h * E[0], umy = u[1] + h * E[1], umz = u[2] + h * E[2];
+  const R ig = R(1) / sqrt(R(1) + umx * umx + umy * umy + umz * umz);
+  const R tx = h * B[0] * ig, ty = h * B[1] * ig, tz = h * B[2] * ig;
+  const R sf = R(2) / (R(1) + tx * tx + ty * ty + tz * tz);
+  const R sx = sf * tx, sy = sf * ty, sz = sf * tz;
+  const R upx = umx + (umy * tz - umz * ty);
+  const R upy = umy + (umz * tx - umx * tz);
+  const R upz = umz + (umx * ty - umy * tx);
+  u[0] = umx + (upy * sz - upz * sy) + h * E[0];
+  u[1] = umy + (upz * sx - upx * sz) + h * E[1];
+  u[2] = umz + (upx * sy - upy * sx) + h * E[2];
+}
+
+// Block-wide sum of a double (blockDim.x a multiple of 32, <= 1024).
+__device__ __forceinline__ double block_sum(double v, double *sh) {
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  __syncthreads();
+  if (lane == 0) sh[wid] = v;
+  __syncthreads();
+  double r = 0.0;
+  if (wid == 0) {
+    r = lane < (int)(blockDim.x >> 5) ? sh[lane] : 0.0;
+    for (int o = 16; o > 0; o >>= 1) r += __shfl_down_sync(0xffffffffu, r, o);
+  }
+  return r;  // valid in thread 0
+}
+
+__device__ __forceinline__ double block_max(double v, double *sh) {
+  for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_down_sync(0xffffffffu, v, o));
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  __syncthreads();
+  if (lane == 0) sh[wid] = v;
+  __syncthreads();
+  double r = 0.0;
+  if (wid == 0) {
+    r = lane < (int)(blockDim.x >> 5) ? sh[lane] : 0.0;
+    for (int o = 16; o > 0; o >>= 1) r = fmax(r, __shfl_down_sync(0xffffffffu, r, o));
+  }
+  return r;
+}
+
+// Max of non-negative doubles through their bit patterns (order-preserving).
+__device__ __forceinline__ void atomic_max_nonneg(double *addr, double v) {
+  atomicMax(reinterpret_cast<unsigned long long *>(addr), (unsigned long long)__double_as_longlong(v));
+}
+
+}  // namespace pic

@@ -1,0 +1,81 @@
+// Internal interface between the host runtime (api.cu) and the kernel
+// translation units.  Not part of the public ABI (include/pic.h is).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace pic {
+
+// Geometry of the grid and of the push kernel's cell tiles.
+struct Grid {
+  int dims;        // 2 or 3
+  int order;       // 1 CIC, 2 TSC
+  int prec;        // PIC_FP32 / PIC_FP64
+  int n[3];        // cells per axis (n[2] = 1 in 2D)
+  double dx[3];    // cell sizes
+  double dt;
+  int tile[3];     // tile shape (tile[2] = 1 in 2D)
+  int ntile[3];    // tiles per axis (ceil)
+  int64_t ntiles;  // product
+  int drift;       // cells a particle may leave its tile and still use the window
+  int64_t ncell;
+  int absorb_lo, absorb_hi;  // x walls absorbing
+};
+
+// One buffer of a species' structure-of-arrays particle storage.  Real
+// arrays are float (FP32 path) or double (FP64 path).
+struct Particles {
+  int32_t *cell;   // linear cell index i + n0*(j + n1*k); -1 = dead slot
+  void *off[3];    // in-cell offset in [0,1) per axis
+  void *u[3];      // momentum u = gamma v
+  void *w;         // weight
+  uint32_t *id;    // tag (permuted only by the sort)
+};
+
+// Device-side counters, one block per simulation.
+struct Counters {
+  unsigned long long escaped;   // particle-steps taken on the global-memory path
+  unsigned long long clamped;   // FP32/FP64 offsets clamped after a carry
+  unsigned long long absorbed;  // particles removed at absorbing walls
+  unsigned long long error;     // bit flags of device-side errors
+};
+
+enum KernelClass { KC_SORT = 0, KC_ZEROJ = 1, KC_PUSH = 2, KC_YEE_B = 3, KC_YEE_E = 4, KC_BOUNDARY = 5, KC_N = 6 };
+
+// ---- push (push.cu) ----
+size_t push_smem_bytes(const Grid &g);
+cudaError_t launch_push(const Grid &g, void *const E[3], void *const B[3], void *const J[3], const Particles &p,
+                        const int64_t *tile_start, double q, double m, Counters *ctr, cudaStream_t st);
+
+// ---- sort (sort.cu) ----
+// Counting sort of the slots [0, *d_count) of `src` by (tile, cell-in-tile),
+// dead slots dropped; result in `dst`, *d_count updated, tile_start[ntiles+1]
+// written.  `keys` has ntiles*tile_cells ints, `rank` one int per slot.
+cudaError_t launch_sort(const Grid &g, const Particles &src, const Particles &dst, int64_t *d_count,
+                        int64_t capacity, int32_t *keys, int32_t *rank, int64_t *tile_start, int64_t *tile_tmp,
+                        cudaStream_t st, int *nlaunch);
+
+// ---- fields and particle conversion (fields.cu) ----
+cudaError_t launch_yee_b(const Grid &g, void *const E[3], void *const B[3], double h, cudaStream_t st);
+cudaError_t launch_yee_e(const Grid &g, void *const E[3], void *const B[3], void *const J[3], double h,
+                         cudaStream_t st);
+cudaError_t launch_load(const Grid &g, const Particles &p, int64_t offset, int64_t n, const double *x,
+                        const double *y, const double *z, const double *ux, const double *uy, const double *uz,
+                        const double *w, const uint32_t *id, unsigned long long *bad, cudaStream_t st);
+cudaError_t launch_unload(const Grid &g, const Particles &p, const int64_t *d_count, int64_t nmax, double *x,
+                          double *y, double *z, double *ux, double *uy, double *uz, double *w, uint32_t *id,
+                          int32_t *alive, cudaStream_t st);
+cudaError_t launch_field_to_f64(const Grid &g, const void *src, double *dst, cudaStream_t st);
+cudaError_t launch_field_from_f64(const Grid &g, const double *src, void *dst, cudaStream_t st);
+cudaError_t launch_rho(const Grid &g, const Particles &p, const int64_t *d_count, int64_t nmax, double q,
+                       double *rho, cudaStream_t st);
+// Reductions into out[] (double): 0 sum E^2, 1 sum B^2, 2 sum rho, 3 max|divE-rho|,
+// 4 max|(rho-rho_prev)/dt + div J| (if rho_prev), 5 nonfinite count (fields)
+cudaError_t launch_field_diag(const Grid &g, void *const E[3], void *const B[3], void *const J[3],
+                              const double *rho, const double *rho_prev, double *out, cudaStream_t st);
+// out[0] += sum w m (gamma-1), out[1] += live count, out[2] += nonfinite count
+cudaError_t launch_particle_diag(const Grid &g, const Particles &p, const int64_t *d_count, int64_t nmax, double m,
+                                 double *out, cudaStream_t st);
+
+}  // namespace pic

@@ -1,0 +1,196 @@
+"""Python front end of libpic.so: a Simulation object over the C ABI.
+
+Marshalling only -- every step of the PIC cycle runs in the library's CUDA
+kernels.  PyTorch is used for device buffers and the CUDA stream; host data
+may be numpy arrays.
+"""
+from __future__ import annotations
+
+import ctypes
+from typing import Optional
+
+import numpy as np
+
+from . import capi
+
+_PREC = {"fp32": capi.PIC_FP32, "fp64": capi.PIC_FP64}
+
+
+def _ptr(a):
+    """Data pointer and mem kind of a numpy array or a torch tensor."""
+    if a is None:
+        return None, capi.PIC_MEM_HOST
+    if isinstance(a, np.ndarray):
+        return a.ctypes.data, capi.PIC_MEM_HOST
+    # torch tensor
+    if a.is_cuda:
+        return a.data_ptr(), capi.PIC_MEM_DEVICE
+    return a.data_ptr(), capi.PIC_MEM_HOST
+
+
+def make_config(dims: int, n, d, dt: float, order: int, precision: str = "fp32", sort_every: int = 20,
+                tile=None, drift_guard: int = 0, absorbing_x: bool = False, laser: Optional[dict] = None,
+                stream: Optional[int] = None) -> capi.pic_config:
+    cfg = capi.pic_config()
+    cfg.dims = dims
+    nn = list(n) + [1] * (3 - len(n))
+    dd = list(d) + [1.0] * (3 - len(d))
+    if dims == 2:
+        nn[2], dd[2] = 1, 1.0
+    for i in range(3):
+        cfg.n[i] = int(nn[i])
+        cfg.dx[i] = float(dd[i])
+        cfg.tile[i] = int(tile[i]) if tile is not None and i < len(tile) else 0
+        cfg.bc_lo[i] = capi.PIC_BC_PERIODIC
+        cfg.bc_hi[i] = capi.PIC_BC_PERIODIC
+    if absorbing_x:
+        cfg.bc_lo[0] = cfg.bc_hi[0] = capi.PIC_BC_ABSORBING
+    cfg.dt = float(dt)
+    cfg.shape_order = int(order)
+    cfg.precision = _PREC[precision] if isinstance(precision, str) else int(precision)
+    cfg.sort_every = int(sort_every)
+    cfg.drift_guard = int(drift_guard)
+    if laser:
+        cfg.laser.enabled = 1
+        cfg.laser.a0 = float(laser["a0"])
+        cfg.laser.waist = float(laser["waist"])
+        cfg.laser.duration = float(laser["duration"])
+        cfg.laser.y_center = float(laser.get("y_center", 0.5 * nn[1] * dd[1]))
+        cfg.laser.z_center = float(laser.get("z_center", 0.5 * nn[2] * dd[2]))
+        cfg.laser.polarization = int(laser.get("pol", 1))
+    cfg.stream = stream
+    return cfg
+
+
+class Simulation:
+    """One PIC simulation living on the current CUDA device."""
+
+    def __init__(self, dims: int, n, d, dt: float, order: int, precision: str = "fp32", sort_every: int = 20,
+                 tile=None, drift_guard: int = 0, absorbing_x: bool = False, laser: Optional[dict] = None,
+                 stream=None):
+        capi.load()
+        if stream is None:
+            import torch
+            stream = torch.cuda.current_stream().cuda_stream
+        self.cfg = make_config(dims, n, d, dt, order, precision, sort_every, tile, drift_guard, absorbing_x,
+                               laser, stream)
+        self.dims = dims
+        self.n = tuple(self.cfg.n)
+        self.d = tuple(self.cfg.dx)
+        self.dt = dt
+        self.order = order
+        self.precision = precision
+        self.h = capi.pic_create(self.cfg)
+        self.species = []
+
+    @classmethod
+    def from_workload(cls, wl, precision: str = "fp32", **kw) -> "Simulation":
+        kw.setdefault("sort_every", wl.sort_every)
+        kw.setdefault("absorbing_x", wl.absorbing_x)
+        kw.setdefault("laser", wl.laser)
+        return cls(wl.dims, wl.n, wl.d, wl.dt, wl.order, precision, **kw)
+
+    # -- lifecycle
+    def close(self):
+        if getattr(self, "h", None):
+            capi.pic_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    @property
+    def shape3(self):
+        return (self.n[2], self.n[1], self.n[0])
+
+    # -- particles
+    def add_species(self, q: float, m: float, capacity: int) -> int:
+        sp = capi.pic_add_species(self.h, q, m, capacity)
+        self.species.append((q, m))
+        return sp
+
+    def load(self, species: int, parts: dict) -> None:
+        """Append particles given as FP64 arrays x, y, z, ux, uy, uz, w (+ id)."""
+        keys = ["x", "y", "z", "ux", "uy", "uz", "w"]
+        n = len(parts["x"])
+        arrs = []
+        kinds = set()
+        for k in keys:
+            a = parts.get(k)
+            if a is None and k == "z":
+                arrs.append(None)
+                continue
+            if isinstance(a, np.ndarray):
+                a = np.ascontiguousarray(a, dtype=np.float64)
+            arrs.append(a)
+        ids = parts.get("id")
+        if isinstance(ids, np.ndarray):
+            ids = np.ascontiguousarray(ids, dtype=np.uint32)
+        ptrs = []
+        for a in arrs + [ids]:
+            p, kind = _ptr(a)
+            ptrs.append(p)
+            if a is not None:
+                kinds.add(kind)
+        if len(kinds) != 1:
+            raise ValueError("particle arrays must all be host or all be device memory")
+        self._keep = (arrs, ids)
+        capi.pic_load_particles(self.h, species, n, *ptrs, kinds.pop())
+
+    def neutralize(self) -> None:
+        capi.pic_neutralize(self.h)
+
+    def num_particles(self, species: int = 0) -> int:
+        return capi.pic_num_particles(self.h, species)
+
+    def particles(self, species: int = 0, alive_only: bool = True) -> dict:
+        n = self.num_particles(species)
+        out = {k: np.empty(n, dtype=np.float64) for k in ("x", "y", "z", "ux", "uy", "uz", "w")}
+        out["id"] = np.empty(n, dtype=np.uint32)
+        out["alive"] = np.empty(n, dtype=np.int32)
+        if n:
+            capi.pic_particles(self.h, species, *[out[k].ctypes.data for k in ("x", "y", "z", "ux", "uy", "uz", "w")],
+                               out["id"].ctypes.data, out["alive"].ctypes.data, capi.PIC_MEM_HOST)
+        if alive_only:
+            m = out["alive"] == 1
+            out = {k: v[m] for k, v in out.items()}
+        return out
+
+    # -- stepping
+    def step(self, nsteps: int = 1) -> None:
+        capi.pic_step(self.h, nsteps)
+
+    def sync(self) -> None:
+        capi.pic_sync(self.h)
+
+    # -- fields
+    def field(self, which: int) -> np.ndarray:
+        out = np.empty(self.shape3, dtype=np.float64)
+        capi.pic_fields(self.h, which, out.ctypes.data, capi.PIC_MEM_HOST)
+        return out
+
+    def field_device(self, which: int):
+        import torch
+        out = torch.empty(self.shape3, dtype=torch.float64, device="cuda")
+        capi.pic_fields(self.h, which, out.data_ptr(), capi.PIC_MEM_DEVICE)
+        return out
+
+    def set_field(self, which: int, arr) -> None:
+        a = np.ascontiguousarray(np.broadcast_to(arr, self.shape3), dtype=np.float64)
+        capi.pic_set_field(self.h, which, a.ctypes.data, capi.PIC_MEM_HOST)
+
+    def diag(self) -> dict:
+        return capi.pic_diag(self.h)
+
+    # -- profiling
+    def profile(self, enable: bool = True) -> None:
+        capi.pic_profile(self.h, enable)
+
+    def timings(self) -> dict:
+        return capi.pic_timings(self.h)
+
+    def launch_count(self) -> int:
+        return capi.pic_launch_count(self.h)
