@@ -1,0 +1,388 @@
+"""Throughput benchmark of the GB300 PIC hot path.
+
+Default workload: the 3D3V periodic thermal plasma, 256^3 cells, 8 electrons
+per cell (134,217,728 macro-particles), u_th = 0.05, TSC shape, dx = 0.05,
+dt = 0.028, FP32 cell-relative push/deposit, particle sort every 20 steps.
+One "step" is one full PIC cycle (sort when due, J reset, fused
+gather/Boris/move/Esirkepov kernel, three Yee updates).  Metric:
+particle-steps/s = live particles x steps / time.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl gpu|reference]
+
+Prints one JSON line (rank 0).  Under torchrun with N > 1 every rank runs an
+independent replica of the workload on its own GPU (the path has no exchange
+step on one GPU; see the design notes), times are max-reduced over ranks and
+`value` is the aggregate over all ranks.
+
+`--impl reference` times the FP64 CPU oracle instead (the only other place
+this script runs it), on a bounded sub-box of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+from paper_1503_02464_gb300 import synth  # noqa: E402
+
+WORKLOAD = "thermal3d_256"
+# algorithmic bytes of the fused push kernel (FP32, 3D): per particle it
+# reads cell(4) + offset(12) + u(12) + w(4) and writes cell(4) + offset(12) +
+# u(12) = 60 B; per cell it reads E, B (24 B) once and adds J (12 B read +
+# 12 B write) once = 48 B.
+PUSH_BYTES_PER_PARTICLE = {"fp32": 60, "fp64": 4 + 24 + 24 + 8 + 4 + 24 + 24}
+PUSH_BYTES_PER_CELL = {"fp32": 48, "fp64": 96}
+
+
+def _peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            p = json.load(f)
+        return float(p["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi sampling of SM clocks and throttle reasons during a region."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        try:
+            os.makedirs(os.path.join(ROOT, "gpurun_out"), exist_ok=True)
+            self.path = os.path.join(ROOT, "gpurun_out", f"clocks_{os.getpid()}.csv")
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self) -> dict:
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.f.close()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# --------------------------------------------------------------------------- CPU oracle arm
+def oracle_sample_workload(wl, ncell_axis: int):
+    """A periodic sub-box of the workload with the same cell size, dt, shape,
+    density, temperature and particles per cell."""
+    n = (ncell_axis,) * wl.dims + (1,) * (3 - wl.dims)
+    return synth.Workload(wl.name + f"_sample{ncell_axis}", wl.dims, n, wl.d, wl.dt, wl.order, wl.steps,
+                          wl.seed, wl.species, wl.sort_every)
+
+
+def time_oracle(wl, nsteps: int, warmup: int = 0):
+    import oracle
+    o = oracle.OracleSim(wl.dims, wl.n, wl.d, wl.dt, wl.order)
+    npart = 0
+    for isp, sp in enumerate(wl.species):
+        p = wl.particles(isp)
+        o.add_particles(p, sp.q, sp.m)
+        npart += len(p["x"])
+    o.neutralize()
+    if warmup:
+        o.step(warmup)
+    times = []
+    for _ in range(nsteps):
+        t0 = time.perf_counter()
+        o.step(1)
+        times.append(time.perf_counter() - t0)
+    o.close()
+    return npart, times
+
+
+def run_reference(args, rank: int, world: int):
+    if rank != 0:
+        return
+    wl = synth.preset(args.workload)
+    sample = oracle_sample_workload(wl, 32 if wl.dims == 3 else 256)
+    npart, times = time_oracle(sample, args.steps, args.warmup)
+    tot = sum(times)
+    value = npart * len(times) / tot
+    desc = (f"FP64 C oracle, single thread, periodic {'x'.join(map(str, sample.n[:sample.dims]))} sub-box of "
+            f"{wl.name} ({npart} particles, same dx, dt, ppc, u_th, shape), {len(times)} steps")
+    line = {"impl": "reference", "metric": "particle-steps/s", "value": value, "unit": "particle-steps/s",
+            "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * tot / len(times),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": wl.name, "sample": "x".join(map(str, sample.n[:sample.dims])),
+                       "particles": npart},
+            "cpu_baseline": {"value": value, "unit": "particle-steps/s", "cores": 1, "kind": "oracle",
+                             "sample": desc},
+            "e2e": {"value": value, "unit": "particle-steps/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+# --------------------------------------------------------------------------- GPU arm
+def _dist_setup(args):
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+def _barrier_max(world, value: float) -> float:
+    if world == 1:
+        return value
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([value], dtype=torch.float64, device="cuda")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def _barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def generate(wl, isp, nproc):
+    return synth.SharedParticles(wl, isp, nproc=nproc)
+
+
+def run_gpu(args, rank: int, world: int, local: int):
+    import torch
+    from paper_1503_02464_gb300 import capi
+    from paper_1503_02464_gb300.sim import Simulation
+
+    wl = synth.preset(args.workload)
+    if world > 1:
+        wl.seed += 7919 * rank  # independent replica per rank
+    # host inputs first (spawned pool, before the first CUDA call)
+    t_gen = time.perf_counter()
+    host = [generate(wl, isp, args.nproc) for isp in range(len(wl.species))]
+    t_gen = time.perf_counter() - t_gen
+
+    torch.cuda.set_device(local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    capi.load()
+    stream = torch.cuda.current_stream()
+    npart = sum(h.n for h in host)
+    ncell = wl.ncells
+
+    def make_sim(precision):
+        return Simulation.from_workload(wl, precision=precision, stream=stream.cuda_stream)
+
+    def load_device(sim):
+        for isp, (sp, h) in enumerate(zip(wl.species, host)):
+            s = sim.add_species(sp.q, sp.m, h.n)
+            dev = {k: torch.from_numpy(v).to("cuda") for k, v in h.arrays.items()}
+            sim.load(s, dev)
+            del dev
+        if wl.neutralize:
+            sim.neutralize()
+
+    def timed_steps(sim, k):
+        """K steps between device events on the simulation's stream."""
+        _barrier(world)
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        sim.step(k)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        _barrier(world)
+        return e0.elapsed_time(e1) / 1e3
+
+    results = {}
+    # ---------------- FP32 device-resident run (the headline value)
+    sim = make_sim(args.precision)
+    load_device(sim)
+    sim.step(args.warmup)
+    torch.cuda.synchronize()
+    l0 = sim.launch_count()
+    sim.profile(True)
+    clocks = ClockSampler(local)
+    clocks.start()
+    dt_s = timed_steps(sim, args.steps)
+    clk = clocks.stop()
+    tim = sim.timings()
+    launches = sim.launch_count() - l0
+    d = sim.diag()
+    sim.profile(False)
+    dt_max = _barrier_max(world, dt_s)
+    push_ms, push_n = tim["push"]
+    results["main"] = dict(dt=dt_max, tim=tim, launches=launches, diag=d, clocks=clk)
+    sim.close()
+    del sim
+    torch.cuda.synchronize()
+
+    # ---------------- FP64 path on the same workload (fewer steps)
+    fp64 = None
+    if args.fp64_steps > 0:
+        sim = make_sim("fp64")
+        load_device(sim)
+        sim.step(min(args.warmup, 3))
+        sim.profile(True)
+        dt64 = _barrier_max(world, timed_steps(sim, args.fp64_steps))
+        t64 = sim.timings()
+        sim.profile(False)
+        sim.close()
+        del sim
+        p64_ms, p64_n = t64["push"]
+        fp64 = {"value": world * npart * args.fp64_steps / dt64, "unit": "particle-steps/s",
+                "ms_per_step": 1e3 * dt64 / args.fp64_steps, "steps": args.fp64_steps,
+                "push_ms_per_launch": p64_ms / max(p64_n, 1)}
+        torch.cuda.synchronize()
+
+    # ---------------- end to end through the C ABI with host buffers
+    e2e = None
+    if not args.no_e2e:
+        cudart = torch.cuda.cudart()
+        regs = []
+        for h in host:
+            for v in h.arrays.values():
+                if v.nbytes:
+                    rc = cudart.cudaHostRegister(v.ctypes.data, v.nbytes, 0)
+                    if int(rc) == 0:
+                        regs.append(v.ctypes.data)
+        sim = make_sim(args.precision)
+        for sp, h in zip(wl.species, host):
+            sim.add_species(sp.q, sp.m, h.n)
+        Ex = np.empty(sim.shape3, dtype=np.float64)
+        torch.cuda.synchronize()
+        _barrier(world)
+        t0 = time.perf_counter()
+        for isp, h in enumerate(host):
+            sim.load(isp, h.arrays)           # pinned host -> device inside the call
+        if wl.neutralize:
+            sim.neutralize()
+        for _ in range(args.steps):
+            sim.step(1)
+            dg = sim.diag()                   # FP64 diagnostics read back every step
+        sim.sync()
+        t1 = time.perf_counter()
+        _barrier(world)
+        e2e_s = _barrier_max(world, t1 - t0)
+        sim.close()
+        del sim
+        for ptr in regs:
+            cudart.cudaHostUnregister(ptr)
+        h2d = sum(sum(v.nbytes for v in h.arrays.values()) for h in host)
+        d2h = 12 * 8
+        e2e = {"value": world * npart * args.steps / e2e_s, "unit": "particle-steps/s",
+               "h2d_bytes_per_step": int(h2d / args.steps), "d2h_bytes_per_step": d2h,
+               "pinned": len(regs) == sum(len(h.arrays) for h in host),
+               "note": "load from pinned host + per-step pic_step + pic_diag read-back, wall clock"}
+
+    # ---------------- CPU oracle baseline (rank 0, N = 1 only)
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        sample = oracle_sample_workload(wl, 32)
+        n_o, ts = time_oracle(sample, args.cpu_steps)
+        cpu = {"value": n_o * len(ts) / sum(ts), "unit": "particle-steps/s", "cores": 1, "kind": "oracle",
+               "sample": f"FP64 C oracle, 1 thread, periodic 32^3 sub-box of {wl.name} ({n_o} particles, "
+                         f"same dx/dt/ppc/u_th/TSC), {len(ts)} steps, {sum(ts):.1f} s"}
+
+    for h in host:
+        h.close()
+
+    if rank != 0:
+        return
+    r = results["main"]
+    value = world * npart * args.steps / r["dt"]
+    peak, peak_kind = _peaks()
+    push_avg_s = push_ms / max(push_n, 1) / 1e3
+    alg_bytes = npart * PUSH_BYTES_PER_PARTICLE[args.precision] + ncell * PUSH_BYTES_PER_CELL[args.precision]
+    achieved = alg_bytes / push_avg_s / 1e9
+    tim_out = {k: {"ms_total": v[0], "launches": v[1]} for k, v in r["tim"].items() if v[1]}
+    line = {
+        "metric": "particle-steps/s", "value": value, "unit": "particle-steps/s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * r["dt"] / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f32" if args.precision == "fp32" else "f64", "data": "synthetic",
+        "config": {"workload": f"{wl.name}: 3D3V periodic thermal plasma 256^3 cells, 8 ppc, "
+                               f"{npart} electrons, u_th=0.05, TSC, dx=0.05, dt=0.028, sort every 20",
+                   "particles": npart, "cells": ncell, "precision": args.precision,
+                   "l2": "inputs larger than L2 (particle arrays > 4 GB, fields 0.6 GB)",
+                   "parallelism": "replicas" if world > 1 else "single GPU"},
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                     "traffic": None, "kernel": "k_push (fused gather/Boris/move/Esirkepov)",
+                     "peak_kind": f"{peak_kind} HBM copy bandwidth",
+                     "bytes_per_launch": alg_bytes, "ms_per_launch": push_avg_s * 1e3},
+        "kernel_times": tim_out,
+        "gpu_launches": int(r["launches"]),
+        "clocks": r["clocks"],
+        "diag_after": {k: r["diag"][k] for k in ("energy_field", "energy_kinetic", "n_alive", "n_escaped",
+                                                   "gauss_max")},
+        "setup_s": {"generate": t_gen},
+    }
+    if fp64 is not None:
+        line["fp64"] = fp64
+    if e2e is not None:
+        line["e2e"] = e2e
+    if cpu is not None:
+        line["cpu_baseline"] = cpu
+    print(json.dumps(line), flush=True)
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=40)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="gpu", choices=["gpu", "reference"])
+    ap.add_argument("--workload", default=WORKLOAD)
+    ap.add_argument("--precision", default="fp32", choices=["fp32", "fp64"])
+    ap.add_argument("--fp64-steps", type=int, default=10)
+    ap.add_argument("--cpu-steps", type=int, default=3)
+    ap.add_argument("--nproc", type=int, default=0)
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    world, rank, local = _dist_setup(args)
+    if args.impl == "reference":
+        run_reference(args, rank, world)
+        return
+    run_gpu(args, rank, world, local)
+
+
+if __name__ == "__main__":
+    main()

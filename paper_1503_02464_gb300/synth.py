@@ -152,6 +152,10 @@ def preset(name: str) -> Workload:
         # 3D3V periodic thermal plasma 256^3, 8 ppc, u_th=0.05, TSC, sort every 20
         return Workload(name, 3, (256, 256, 256), (0.05, 0.05, 0.05), 0.028, 2, 50, 1003,
                         [Species("electron", -1.0, 1.0, 8, 0.05)])
+    if name == "thermal3d_128":
+        # the same plasma on a 128^3 grid (16.8M particles): profiling size
+        return Workload(name, 3, (128, 128, 128), (0.05, 0.05, 0.05), 0.028, 2, 50, 1003,
+                        [Species("electron", -1.0, 1.0, 8, 0.05)])
     if name == "laser_slab2d":
         d = 0.02 * lam
         dt = 0.9 * courant_limit((d, d), 2)
@@ -179,3 +183,66 @@ def small(dims: int, n: tuple, order: int, ppc: int, u_th: float, seed: int, dt_
     nn = tuple(n) + (1,) * (3 - len(n))
     return Workload(f"small{dims}d", dims, nn, dd, dt, order, 10, seed,
                     [Species("electron", -1.0, 1.0, ppc, u_th)])
+
+
+# ---------------------------------------------------------------------------
+# Parallel generation into file-backed shared arrays (large workloads)
+# ---------------------------------------------------------------------------
+_FIELDS = (("x", np.float64), ("y", np.float64), ("z", np.float64), ("ux", np.float64), ("uy", np.float64),
+           ("uz", np.float64), ("w", np.float64), ("id", np.uint32))
+
+
+def _fill_chunk(args):
+    wl, isp, c0, c1, paths, n_total = args
+    sp = wl.species[isp]
+    cells = wl.species_cells(sp)[c0:c1]
+    p = wl.particles(isp, cells)
+    for (key, dt), path in zip(_FIELDS, paths):
+        arr = np.memmap(path, dtype=dt, mode="r+", shape=(n_total,))
+        arr[c0 * sp.ppc:c1 * sp.ppc] = p[key]
+        arr.flush()
+        del arr
+    return c1 - c0
+
+
+class SharedParticles:
+    """Particle arrays of one species in memory-mapped temporary files, filled
+    by a pool of worker processes (spawned, so it is safe after CUDA has
+    started).  ``arrays`` maps x, y, z, ux, uy, uz, w, id to numpy views."""
+
+    def __init__(self, wl: Workload, isp: int, nproc: int = 0, chunk_cells: int = 65536):
+        import multiprocessing as mp
+        import os
+        import tempfile
+        sp = wl.species[isp]
+        ncells = int(wl.species_cells(sp).size)
+        self.n = ncells * sp.ppc
+        self._dir = tempfile.mkdtemp(prefix="picsynth_")
+        self.paths = [os.path.join(self._dir, key + ".bin") for key, _ in _FIELDS]
+        for (key, dt), path in zip(_FIELDS, self.paths):
+            with open(path, "wb") as f:
+                f.truncate(max(self.n, 1) * np.dtype(dt).itemsize)
+        jobs = [(wl, isp, c, min(c + chunk_cells, ncells), self.paths, self.n) for c in range(0, ncells, chunk_cells)]
+        nproc = nproc or min(16, os.cpu_count() or 1)
+        if nproc <= 1 or len(jobs) == 1:
+            for j in jobs:
+                _fill_chunk(j)
+        else:
+            with mp.get_context("spawn").Pool(nproc) as pool:
+                for _ in pool.imap_unordered(_fill_chunk, jobs):
+                    pass
+        self.arrays = {key: np.memmap(path, dtype=dt, mode="r+", shape=(max(self.n, 1),))[:self.n]
+                       for (key, dt), path in zip(_FIELDS, self.paths)}
+
+    def close(self):
+        import shutil
+        self.arrays = {}
+        if getattr(self, "_dir", None):
+            shutil.rmtree(self._dir, ignore_errors=True)
+            self._dir = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
