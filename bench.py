@@ -335,8 +335,11 @@ def run_gpu(args, rank: int, world: int, local: int):
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * r["dt"] / args.steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": "f32" if args.precision == "fp32" else "f64", "data": "synthetic",
-        "config": {"workload": f"{wl.name}: 3D3V periodic thermal plasma 256^3 cells, 8 ppc, "
-                               f"{npart} electrons, u_th=0.05, TSC, dx=0.05, dt=0.028, sort every 20",
+        "config": {"workload": f"{wl.name}: {wl.dims}D3V periodic thermal plasma "
+                               f"{'x'.join(map(str, wl.n[:wl.dims]))} cells, {wl.species[0].ppc} ppc, "
+                               f"{npart} electrons, u_th={wl.species[0].u_th}, "
+                               f"{'TSC' if wl.order == 2 else 'CIC'}, dx={wl.d[0]}, dt={wl.dt}, "
+                               f"sort every {wl.sort_every}",
                    "particles": npart, "cells": ncell, "precision": args.precision,
                    "l2": "inputs larger than L2 (particle arrays > 4 GB, fields 0.6 GB)",
                    "parallelism": "replicas" if world > 1 else "single GPU"},
