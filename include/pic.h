@@ -206,6 +206,26 @@ int pic_timings(pic_handle *h, double *ms, int64_t *launches, int nmax, int *ncl
 /* Number of kernels this handle has launched since creation. */
 int pic_launch_count(pic_handle *h, int64_t *count);
 
+/* FP64 field energies without any device allocation.  The paper has no
+ * counterpart: this is a library service for callers that must not call
+ * cudaMalloc/cudaFree (which can synchronise the device), e.g. code embedded
+ * in an application whose device memory belongs to its own pool or fixed
+ * budget, or code running on a host-callback or latency-critical thread.
+ * Computes out[0] = 1/2 sum(Ex^2+Ey^2+Ez^2) dV and out[1] = 1/2 sum(Bx^2+
+ * By^2+Bz^2) dV -- pic_diag's energy_e and energy_b -- over ncell cells of the
+ * caller's device arrays E[0..2], B[0..2] (float for PIC_FP32, double for
+ * PIC_FP64), summed in a fixed order (bitwise reproducible).  out (2 doubles)
+ * is host (the call then synchronises the stream) or device memory
+ * (asynchronous) per mem_kind.  Scratch lives in a static device array of
+ * 32 KB that every GPU loading the library keeps until exit; ncell above
+ * 33,554,432 is rejected with PIC_EINVAL.  All calls share that array, so
+ * calls that overlap on the GPU race.  The first call on each device looks up
+ * the array's device address (it must run with that device current, and
+ * before any stream capture).  Errors: PIC_EINVAL, PIC_ECUDA; text via
+ * pic_last_error(NULL). */
+int pic_field_energy_noalloc(int precision, const void *const E[3], const void *const B[3], int64_t ncell,
+                             double cell_volume, double *out, int mem_kind, void *stream);
+
 #ifdef __cplusplus
 }
 #endif

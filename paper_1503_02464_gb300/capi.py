@@ -24,7 +24,7 @@ ERROR_NAMES = {0: "PIC_OK", 1: "PIC_EINVAL", 2: "PIC_ECOURANT", 3: "PIC_ENOMEM",
 # every symbol include/pic.h declares
 EXPORTED = ["pic_create", "pic_destroy", "pic_last_error", "pic_add_species", "pic_load_particles",
             "pic_neutralize", "pic_step", "pic_fields", "pic_set_field", "pic_num_particles", "pic_particles",
-            "pic_diag", "pic_sync", "pic_profile", "pic_timings", "pic_launch_count"]
+            "pic_diag", "pic_sync", "pic_profile", "pic_timings", "pic_launch_count", "pic_field_energy_noalloc"]
 
 
 class pic_laser(ctypes.Structure):
@@ -96,6 +96,8 @@ def load(build_if_missing: bool = True) -> ctypes.CDLL:
         "pic_timings": ([hp, dp, ctypes.POINTER(ctypes.c_int64), ctypes.c_int, ctypes.POINTER(ctypes.c_int)],
                         ctypes.c_int),
         "pic_launch_count": ([hp, ctypes.POINTER(ctypes.c_int64)], ctypes.c_int),
+        "pic_field_energy_noalloc": ([ctypes.c_int, ctypes.c_void_p * 3, ctypes.c_void_p * 3, i64, ctypes.c_double,
+                                      vp, ctypes.c_int, vp], ctypes.c_int),
     }
     for name, (args, res) in sig.items():
         fn = getattr(lib, name)
@@ -188,3 +190,12 @@ def pic_launch_count(h) -> int:
     c = ctypes.c_int64()
     check(h, load().pic_launch_count(h, ctypes.byref(c)))
     return c.value
+
+
+def pic_field_energy_noalloc(precision: int, E_ptrs, B_ptrs, ncell: int, cell_volume: float, out_ptr,
+                             mem_kind: int, stream) -> None:
+    """FP64 field energies (electric, magnetic) using no device allocation."""
+    e = (ctypes.c_void_p * 3)(*E_ptrs)
+    b = (ctypes.c_void_p * 3)(*B_ptrs)
+    check(None, load().pic_field_energy_noalloc(int(precision), e, b, int(ncell), float(cell_volume), out_ptr,
+                                                int(mem_kind), stream))

@@ -189,6 +189,10 @@ int64_t read_count(pic_handle *h, Species &s) {
 
 }  // namespace
 
+namespace pic {
+void set_global_error(const std::string &msg) { g_create_error = msg; }
+}  // namespace pic
+
 extern "C" {
 
 int pic_create(const pic_config *cfg, pic_handle **out) {

@@ -5,6 +5,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <string>
+
 namespace pic {
 
 // Geometry of the grid and of the push kernel's cell tiles.
@@ -40,6 +42,9 @@ struct Counters {
   unsigned long long absorbed;  // particles removed at absorbing walls
   unsigned long long error;     // bit flags of device-side errors
 };
+
+// Error text reported by pic_last_error(NULL) (entry points without a handle).
+void set_global_error(const std::string &msg);
 
 enum KernelClass { KC_SORT = 0, KC_ZEROJ = 1, KC_PUSH = 2, KC_YEE_B = 3, KC_YEE_E = 4, KC_BOUNDARY = 5, KC_N = 6 };
 
