@@ -26,7 +26,8 @@ constexpr int kBlock = 256;
 
 struct Species {
   double q = 0, m = 1;
-  int64_t capacity = 0;
+  int64_t capacity = 0;         // particles the caller may load
+  int64_t slots = 0;            // allocated slots: capacity + tile padding
   Particles buf[2] = {};
   int cur = 0;
   int64_t *d_count = nullptr;   // slots in use (device)
@@ -55,6 +56,7 @@ struct pic_handle {
   int64_t rho_prev_step = -2;
   int32_t *keys = nullptr;
   int64_t *tile_tmp = nullptr;
+  unsigned long long *esc_count = nullptr;
   Counters *ctr = nullptr;
   unsigned long long *bad = nullptr;
   Species sp[kMaxSpecies];
@@ -160,7 +162,7 @@ int sort_species(pic_handle *h, Species &s) {
   int nl = 0;
   Timed tm(h, pic::KC_SORT);
   CK(h,
-     pic::launch_sort(h->g, s.buf[s.cur], s.buf[1 - s.cur], s.d_count, s.capacity, h->keys, s.rank, s.tile_start,
+     pic::launch_sort(h->g, s.buf[s.cur], s.buf[1 - s.cur], s.d_count, s.slots, h->keys, s.rank, s.tile_start,
                       h->tile_tmp, h->st, &nl),
      "sort");
   h->launches += nl;
@@ -173,7 +175,7 @@ int compute_rho(pic_handle *h, double *rho) {
   CK(h, cudaMemcpyAsync(rho, h->rho_bg, sizeof(double) * h->g.ncell, cudaMemcpyDeviceToDevice, h->st), "rho init");
   for (int i = 0; i < h->nsp; ++i) {
     Species &s = h->sp[i];
-    CK(h, pic::launch_rho(h->g, s.buf[s.cur], s.d_count, s.capacity, s.q, rho, h->st), "rho deposit");
+    CK(h, pic::launch_rho(h->g, s.buf[s.cur], s.d_count, s.slots, s.q, rho, h->st), "rho deposit");
     h->launches++;
   }
   return PIC_OK;
@@ -223,7 +225,14 @@ int pic_create(const pic_config *cfg, pic_handle **out) {
     return fail(nullptr, PIC_ECOURANT, b);
   }
   const int64_t ncell = (int64_t)c.n[0] * c.n[1] * (c.dims == 3 ? c.n[2] : 1);
-  if (ncell > 0x7fffffffLL) return fail(nullptr, PIC_EINVAL, "more than 2^31 cells");
+  if (ncell >= (1LL << 30)) return fail(nullptr, PIC_EINVAL, "2^30 cells or more");
+  int ctile[3];
+  pic::push_tile_shape(c.dims, ctile);
+  for (int d = 0; d < c.dims; ++d)
+    if (c.tile[d] != 0 && c.tile[d] != ctile[d])
+      return fail(nullptr, PIC_EINVAL, "tile must be 0 (default) or the compiled tile shape (8x8x8 in 3D, 16x16 in 2D)");
+  if (c.drift_guard != 0 && c.drift_guard != 1)
+    return fail(nullptr, PIC_EINVAL, "drift_guard must be 0 or 1 (the compiled drift allowance)");
 
   pic_handle *h = new pic_handle();
   h->cfg = c;
@@ -239,14 +248,12 @@ int pic_create(const pic_config *cfg, pic_handle **out) {
   g.dx[2] = c.dims == 3 ? c.dx[2] : 1.0;
   g.dt = c.dt;
   g.ncell = ncell;
-  g.drift = c.drift_guard > 0 ? c.drift_guard : 1;
+  g.drift = 1;
   g.absorb_lo = c.bc_lo[0] == PIC_BC_ABSORBING;
   g.absorb_hi = c.bc_hi[0] == PIC_BC_ABSORBING;
-  const int deft = c.dims == 3 ? 8 : 16;
   g.ntiles = 1;
   for (int d = 0; d < 3; ++d) {
-    int t = (d < c.dims) ? (c.tile[d] > 0 ? c.tile[d] : deft) : 1;
-    if (t > g.n[d]) t = g.n[d];
+    const int t = ctile[d];
     g.tile[d] = t;
     g.ntile[d] = (g.n[d] + t - 1) / t;
     g.ntiles *= g.ntile[d];
@@ -279,7 +286,8 @@ int pic_create(const pic_config *cfg, pic_handle **out) {
        cudaMalloc(&h->red, 16 * sizeof(double)) == cudaSuccess &&
        cudaMalloc(&h->keys, (size_t)nkeys * sizeof(int32_t)) == cudaSuccess &&
        cudaMalloc(&h->tile_tmp, (size_t)(g.ntiles + 1) * sizeof(int64_t)) == cudaSuccess &&
-       cudaMalloc(&h->ctr, sizeof(Counters)) == cudaSuccess && cudaMalloc(&h->bad, sizeof(unsigned long long)) == cudaSuccess;
+       cudaMalloc(&h->ctr, sizeof(Counters)) == cudaSuccess && cudaMalloc(&h->bad, sizeof(unsigned long long)) == cudaSuccess &&
+       cudaMalloc(&h->esc_count, sizeof(unsigned long long)) == cudaSuccess;
   if (!ok) {
     pic_destroy(h);
     return fail(nullptr, PIC_ENOMEM, "device allocation failed in pic_create");
@@ -317,6 +325,7 @@ int pic_destroy(pic_handle *h) {
   cudaFree(h->tile_tmp);
   cudaFree(h->ctr);
   cudaFree(h->bad);
+  cudaFree(h->esc_count);
   for (int i = 0; i < h->nsp; ++i) {
     Species &s = h->sp[i];
     free_particles(s.buf[0]);
@@ -345,10 +354,12 @@ int pic_add_species(pic_handle *h, double q, double m, int64_t capacity, int *sp
   s.q = q;
   s.m = m;
   s.capacity = capacity;
-  cudaError_t e = alloc_particles(s.buf[0], capacity, h->rsize, h->g.dims);
-  if (e == cudaSuccess) e = alloc_particles(s.buf[1], capacity, h->rsize, h->g.dims);
+  s.slots = capacity + (pic::kTilePad - 1) * h->g.ntiles;
+  if (s.slots > 0x7fffffffLL) return fail(h, PIC_EINVAL, "capacity plus tile padding exceeds 2^31 slots");
+  cudaError_t e = alloc_particles(s.buf[0], s.slots, h->rsize, h->g.dims);
+  if (e == cudaSuccess) e = alloc_particles(s.buf[1], s.slots, h->rsize, h->g.dims);
   if (e == cudaSuccess) e = cudaMalloc(&s.d_count, sizeof(int64_t));
-  if (e == cudaSuccess) e = cudaMalloc(&s.rank, (size_t)(capacity > 0 ? capacity : 1) * sizeof(int32_t));
+  if (e == cudaSuccess) e = cudaMalloc(&s.rank, (size_t)(s.slots > 0 ? s.slots : 1) * sizeof(int32_t));
   if (e == cudaSuccess) e = cudaMalloc(&s.tile_start, (size_t)(h->g.ntiles + 1) * sizeof(int64_t));
   if (e != cudaSuccess) {
     free_particles(s.buf[0]);
@@ -460,8 +471,12 @@ int pic_step(pic_handle *h, int nsteps) {
     for (int i = 0; i < h->nsp; ++i) {
       Species &s = h->sp[i];
       Timed tm(h, pic::KC_PUSH);
-      CK(h, pic::launch_push(h->g, h->E, h->B, h->J, s.buf[s.cur], s.tile_start, s.q, s.m, h->ctr, h->st), "push");
-      h->launches++;
+      int nl = 0;
+      CK(h,
+         pic::launch_push(h->g, h->E, h->B, h->J, s.buf[s.cur], s.tile_start, s.rank, h->esc_count, s.q, s.m, h->ctr,
+                          h->st, &nl),
+         "push");
+      h->launches += nl;
     }
     {
       Timed tm(h, pic::KC_YEE_B);
@@ -571,7 +586,7 @@ int pic_diag(pic_handle *h, pic_diag_t *out) {
   h->launches++;
   for (int i = 0; i < h->nsp; ++i) {
     Species &s = h->sp[i];
-    CK(h, pic::launch_particle_diag(h->g, s.buf[s.cur], s.d_count, s.capacity, s.m, h->red + 8, h->st), "part diag");
+    CK(h, pic::launch_particle_diag(h->g, s.buf[s.cur], s.d_count, s.slots, s.m, h->red + 8, h->st), "part diag");
     h->launches++;
   }
   double red[16];

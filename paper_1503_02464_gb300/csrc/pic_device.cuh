@@ -86,17 +86,29 @@ template <class R, int ORDER> struct DepositAxis {
       n1 = s;
     }
     rel = n0 < n1 ? n0 : n1;
-    const int o0 = n0 - rel, o1 = n1 - rel;
+    // each support starts at offset 0 or 1 inside the NW-node run; pad the
+    // weights with a zero on either side and pick the window
+    R p0[NW + 1], p1[NW + 1];
+    p0[0] = p1[0] = R(0);
+    p0[NW] = p1[NW] = R(0);
+#pragma unroll
+    for (int q = 0; q <= ORDER; ++q) {
+      p0[q + 1] = w0[q];
+      p1[q + 1] = w1[q];
+    }
+    const bool o0 = n0 != rel, o1 = n1 != rel;
 #pragma unroll
     for (int k = 0; k < NW; ++k) {
-      R a = R(0), b = R(0);
+      S0[k] = o0 ? p0[k] : p0[k + 1];
+      DS[k] = (o1 ? p1[k] : p1[k + 1]) - S0[k];
+    }
+  }
+  __device__ __forceinline__ void zero() {
+    rel = 0;
 #pragma unroll
-      for (int q = 0; q <= ORDER; ++q) {
-        a = (k - o0 == q) ? w0[q] : a;
-        b = (k - o1 == q) ? w1[q] : b;
-      }
-      S0[k] = a;
-      DS[k] = b - a;
+    for (int k = 0; k < NW; ++k) {
+      S0[k] = R(0);
+      DS[k] = R(0);
     }
   }
 };

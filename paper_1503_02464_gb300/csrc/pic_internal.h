@@ -46,17 +46,26 @@ struct Counters {
 // Error text reported by pic_last_error(NULL) (entry points without a handle).
 void set_global_error(const std::string &msg);
 
+constexpr int kTilePad = 4;
+
 enum KernelClass { KC_SORT = 0, KC_ZEROJ = 1, KC_PUSH = 2, KC_YEE_B = 3, KC_YEE_E = 4, KC_BOUNDARY = 5, KC_N = 6 };
 
 // ---- push (push.cu) ----
+// Tile shape compiled into the push kernel (8x8x8 in 3D, 16x16 in 2D); the
+// drift allowance is one cell.
+void push_tile_shape(int dims, int tile[3]);
 size_t push_smem_bytes(const Grid &g);
+// Tile kernel + escape kernel.  esc_list (one int per slot) and esc_count are
+// scratch for particles deferred to the escape kernel.
 cudaError_t launch_push(const Grid &g, void *const E[3], void *const B[3], void *const J[3], const Particles &p,
-                        const int64_t *tile_start, double q, double m, Counters *ctr, cudaStream_t st);
+                        const int64_t *tile_start, int32_t *esc_list, unsigned long long *esc_count, double q,
+                        double m, Counters *ctr, cudaStream_t st, int *nlaunch);
 
 // ---- sort (sort.cu) ----
 // Counting sort of the slots [0, *d_count) of `src` by (tile, cell-in-tile),
 // dead slots dropped; result in `dst`, *d_count updated, tile_start[ntiles+1]
-// written.  `keys` has ntiles*tile_cells ints, `rank` one int per slot.
+// written.  Each tile's run is padded with dead slots to a multiple of
+// kTilePad.  `keys` has ntiles*tile_cells ints, `rank` one int per slot.
 cudaError_t launch_sort(const Grid &g, const Particles &src, const Particles &dst, int64_t *d_count,
                         int64_t capacity, int32_t *keys, int32_t *rank, int64_t *tile_start, int64_t *tile_tmp,
                         cudaStream_t st, int *nlaunch);

@@ -3,15 +3,21 @@
 // ref [8], the charge-conserving deposit for the continuity requirement it
 // states in §2).
 //
-// One thread block owns one cell tile.  Particles are kept sorted by tile
-// (then by cell), so the block's particles are a contiguous slot range.  The
-// block stages E and B of the tile plus guard cells in shared memory,
-// accumulates J of the tile plus guard in shared memory with shared atomics,
-// then adds its J window to the global J with one atomic per non-zero value.
-// A particle that has drifted further than `drift` cells outside its tile
-// since the last sort takes the same arithmetic on global memory instead
-// (gather from the global arrays, global atomics), so results never depend on
-// the window size.
+// One thread block owns one cell tile (8x8x8 in 3D, 16x16 in 2D).  The sort
+// keeps each tile's particles in one contiguous, 4-aligned slot range.  The
+// block stages E and B of the tile plus guard cells in shared memory and
+// accumulates J of the tile plus guard with shared-memory atomics, then adds
+// its J window to the global J (one atomic per non-zero value).
+//
+// Particles stream through a 256-slot shared staging chunk: loaded and stored
+// with coalesced accesses in slot order, but processed in a permuted order
+// that gives the 32 lanes of a warp particles eight slots apart.  Slots are
+// cell-sorted, so lanes then sit in different cells and their shared atomics
+// hit different addresses and banks.
+//
+// A particle that has drifted more than D = 1 cell outside its tile since the
+// last sort is not handled here: its slot is appended to an escape list and
+// k_push_escaped applies the same arithmetic on global memory afterwards.
 #include <cuda_runtime.h>
 
 #include "pic_device.cuh"
@@ -20,11 +26,50 @@ namespace pic {
 
 namespace {
 
+constexpr int kThreads = 256;
+constexpr int32_t kEscFlag = 0x40000000;  // set in `cell` while a particle waits for the escape kernel
+
+// Compile-time tile and window geometry.
+template <int DIM, int ORDER> struct Geo {
+  static constexpr int TX = DIM == 3 ? 8 : 16;
+  static constexpr int TY = DIM == 3 ? 8 : 16;
+  static constexpr int TZ = DIM == 3 ? 8 : 1;
+  static constexpr int D = 1;  // drift allowance (cells)
+  static constexpr int LOE = 1, HIE = ORDER == 2 ? 2 : 1;  // gather reach below / above the cell
+  static constexpr int LOJ = ORDER == 2 ? 2 : 1, HIJ = ORDER == 2 ? 3 : 2;  // deposit reach
+  static constexpr int EX = TX + 2 * D + LOE + HIE;
+  static constexpr int EY = TY + 2 * D + LOE + HIE;
+  static constexpr int EZ = DIM == 3 ? TZ + 2 * D + LOE + HIE : 1;
+  static constexpr int JX = TX + 2 * D + LOJ + HIJ;
+  static constexpr int JY = TY + 2 * D + LOJ + HIJ;
+  static constexpr int JZ = DIM == 3 ? TZ + 2 * D + LOJ + HIJ : 1;
+  static constexpr int EN = EX * EY * EZ;
+  static constexpr int JN = JX * JY * JZ;
+  static constexpr int NS = ORDER + 1;  // gather stencil width
+  static constexpr int NW = ORDER + 2;  // deposit stencil width
+};
+
+// Division by a runtime constant (Granlund-Montgomery): q = (umulhi(n,m) + n) >> l.
+struct FastDiv {
+  uint32_t m, l;
+  __device__ __forceinline__ uint32_t div(uint32_t n) const {
+    return (uint32_t)(((uint64_t)__umulhi(n, m) + n) >> l);
+  }
+};
+
+FastDiv make_fastdiv(uint32_t d) {
+  FastDiv f;
+  uint32_t l = 0;
+  while ((1ull << l) < d) ++l;
+  f.l = l;
+  f.m = (uint32_t)(((1ull << 32) * ((1ull << l) - d)) / d + 1);
+  return f;
+}
+
 template <class R> struct PushArgs {
   int n[3];
-  int tile[3];
-  int ntile[3];
-  int drift;
+  int ntile[2];
+  FastDiv dn0, dn1;
   const R *E[3];
   const R *B[3];
   R *J[3];
@@ -33,6 +78,8 @@ template <class R> struct PushArgs {
   R *u[3];
   const R *w;
   const int64_t *tile_start;
+  int32_t *esc_list;                // slots deferred to k_push_escaped
+  unsigned long long *esc_count;
   R qmh;      // q dt / (2 m)
   R dtdx[3];  // dt / dx_a
   R jfac[3];  // -q dx_a / dt  (Esirkepov running-sum scale, times w)
@@ -40,71 +87,38 @@ template <class R> struct PushArgs {
   Counters *ctr;
 };
 
-// margins of the E/B window and of the J window below / above a particle's cell
-template <int ORDER> struct Margins {
-  static constexpr int LOE = 1;
-  static constexpr int HIE = ORDER == 2 ? 2 : 1;
-  static constexpr int LOJ = ORDER == 2 ? 2 : 1;
-  static constexpr int HIJ = ORDER == 2 ? 3 : 2;
-};
+template <class R> __device__ __forceinline__ R inv_sqrt(R x);
+template <> __device__ __forceinline__ float inv_sqrt<float>(float x) { return rsqrtf(x); }
+template <> __device__ __forceinline__ double inv_sqrt<double>(double x) { return 1.0 / sqrt(x); }
 
-// Weighted sum of one field component over the gather stencil.  ix/iy/iz are
-// per-axis address offsets (already multiplied by the strides).
-template <class R, int NS, int DIM>
-__device__ __forceinline__ R gsum(const R *__restrict__ F, const int *ix, const R *wx, const int *iy, const R *wy,
-                                  const int *iz, const R *wz) {
+// Weighted sum of one field component over the gather stencil; the stencil
+// offsets are compile-time (row stride SY, plane stride SZ).
+template <class R, int NS, int DIM, int SY, int SZ>
+__device__ __forceinline__ R gsum(const R *__restrict__ F, const R *wx, const R *wy, const R *wz) {
   R acc = R(0);
-  if (DIM == 3) {
 #pragma unroll
-    for (int c = 0; c < NS; ++c) {
-      R accb = R(0);
-#pragma unroll
-      for (int b = 0; b < NS; ++b) {
-        const R *row = F + iz[c] + iy[b];
-        R ra = R(0);
-#pragma unroll
-        for (int a = 0; a < NS; ++a) ra += row[ix[a]] * wx[a];
-        accb += ra * wy[b];
-      }
-      acc += accb * wz[c];
-    }
-  } else {
+  for (int c = 0; c < (DIM == 3 ? NS : 1); ++c) {
+    R accb = R(0);
 #pragma unroll
     for (int b = 0; b < NS; ++b) {
-      const R *row = F + iy[b];
-      R ra = R(0);
+      const R *row = F + c * SZ + b * SY;
+      R ra = row[0] * wx[0];
 #pragma unroll
-      for (int a = 0; a < NS; ++a) ra += row[ix[a]] * wx[a];
-      acc += ra * wy[b];
+      for (int a = 1; a < NS; ++a) ra += row[a] * wx[a];
+      accb += ra * wy[b];
     }
+    acc += DIM == 3 ? accb * wz[c] : accb;
   }
   return acc;
 }
 
-// Gather E and B.  Each component uses its own Yee location: primal (p) or
-// dual (d) stencil per axis.
-template <class R, int ORDER, int DIM>
-__device__ __forceinline__ void gather6(const R *const F[6], const GatherAxis<R, ORDER> ga[3], const int ixp[],
-                                        const int ixd[], const int iyp[], const int iyd[], const int izp[],
-                                        const int izd[], R E[3], R B[3]) {
-  constexpr int NS = ORDER + 1;
-  const GatherAxis<R, ORDER> &gx = ga[0], &gy = ga[1], &gz = ga[2];
-  E[0] = gsum<R, NS, DIM>(F[0], ixd, gx.wd, iyp, gy.wp, izp, gz.wp);
-  E[1] = gsum<R, NS, DIM>(F[1], ixp, gx.wp, iyd, gy.wd, izp, gz.wp);
-  E[2] = gsum<R, NS, DIM>(F[2], ixp, gx.wp, iyp, gy.wp, izd, gz.wd);
-  B[0] = gsum<R, NS, DIM>(F[3], ixp, gx.wp, iyd, gy.wd, izd, gz.wd);
-  B[1] = gsum<R, NS, DIM>(F[4], ixd, gx.wd, iyp, gy.wp, izd, gz.wd);
-  B[2] = gsum<R, NS, DIM>(F[5], ixd, gx.wd, iyd, gy.wd, izp, gz.wp);
-}
-
-// Esirkepov deposit of one move into J (shared window or global arrays).
-// jx/jy/jz: per-axis address offsets of the NW stencil nodes.
-template <class R, int ORDER, int DIM>
-__device__ __forceinline__ void deposit(R *const J[3], const DepositAxis<R, ORDER> da[3], const int jx[],
-                                        const int jy[], const int jz[], R cx, R cy, R cz, R qwvz) {
+// Esirkepov deposit into a J window with compile-time strides.
+// base: window index of the stencil's first node; P*: scaled running sums.
+template <class R, int ORDER, int DIM, int SY, int SZ, int JN, bool SHARED>
+__device__ __forceinline__ void deposit_win(R *__restrict__ J, int base, const DepositAxis<R, ORDER> &X,
+                                            const DepositAxis<R, ORDER> &Y, const DepositAxis<R, ORDER> &Z, R cx,
+                                            R cy, R cz, R qwvz) {
   constexpr int NW = ORDER + 2;
-  const DepositAxis<R, ORDER> &X = da[0], &Y = da[1], &Z = da[2];
-  // running sums of DS along each axis (the last one is zero)
   R Px[NW - 1], Py[NW - 1], Pz[NW - 1];
   {
     R a = R(0), b = R(0), c = R(0);
@@ -118,34 +132,40 @@ __device__ __forceinline__ void deposit(R *const J[3], const DepositAxis<R, ORDE
       Pz[k] = cz * c;
     }
   }
+  R *Jx = J + base, *Jy = J + JN + base, *Jz = J + 2 * JN + base;
   if (DIM == 3) {
-    // Jx(i+1/2, j, k): Px[i] * (S0y S0z + DSy S0z/2 + S0y DSz/2 + DSy DSz/3)
+    // Jx(i+1/2,j,k) += Px[i] (S0y S0z + DSy S0z/2 + S0y DSz/2 + DSy DSz/3), cyclic for y, z
+    R hz[NW], tz[NW], hx[NW], tx[NW];
+#pragma unroll
+    for (int k = 0; k < NW; ++k) {
+      hz[k] = Z.S0[k] + R(0.5) * Z.DS[k];
+      tz[k] = R(0.5) * Z.S0[k] + Z.DS[k] * R(1.0 / 3.0);
+      hx[k] = X.S0[k] + R(0.5) * X.DS[k];
+      tx[k] = R(0.5) * X.S0[k] + X.DS[k] * R(1.0 / 3.0);
+    }
 #pragma unroll
     for (int c = 0; c < NW; ++c)
 #pragma unroll
       for (int b = 0; b < NW; ++b) {
-        const R br = Y.S0[b] * (Z.S0[c] + R(0.5) * Z.DS[c]) + Y.DS[b] * (R(0.5) * Z.S0[c] + Z.DS[c] * R(1.0 / 3.0));
-        R *row = J[0] + jz[c] + jy[b];
+        const R br = Y.S0[b] * hz[c] + Y.DS[b] * tz[c];
 #pragma unroll
-        for (int a = 0; a < NW - 1; ++a) atomicAdd(row + jx[a], Px[a] * br);
+        for (int a = 0; a < NW - 1; ++a) atomicAdd(Jx + c * SZ + b * SY + a, Px[a] * br);
       }
 #pragma unroll
     for (int c = 0; c < NW; ++c)
 #pragma unroll
       for (int a = 0; a < NW; ++a) {
-        const R br = Z.S0[c] * (X.S0[a] + R(0.5) * X.DS[a]) + Z.DS[c] * (R(0.5) * X.S0[a] + X.DS[a] * R(1.0 / 3.0));
-        R *col = J[1] + jz[c] + jx[a];
+        const R br = Z.S0[c] * hx[a] + Z.DS[c] * tx[a];
 #pragma unroll
-        for (int b = 0; b < NW - 1; ++b) atomicAdd(col + jy[b], Py[b] * br);
+        for (int b = 0; b < NW - 1; ++b) atomicAdd(Jy + c * SZ + b * SY + a, Py[b] * br);
       }
 #pragma unroll
     for (int b = 0; b < NW; ++b)
 #pragma unroll
       for (int a = 0; a < NW; ++a) {
         const R br = X.S0[a] * (Y.S0[b] + R(0.5) * Y.DS[b]) + X.DS[a] * (R(0.5) * Y.S0[b] + Y.DS[b] * R(1.0 / 3.0));
-        R *col = J[2] + jy[b] + jx[a];
 #pragma unroll
-        for (int c = 0; c < NW - 1; ++c) atomicAdd(col + jz[c], Pz[c] * br);
+        for (int c = 0; c < NW - 1; ++c) atomicAdd(Jz + c * SZ + b * SY + a, Pz[c] * br);
       }
   } else {
     // 2D3V: Jx = Px (S0y + DSy/2), Jy = Py (S0x + DSx/2),
@@ -153,280 +173,372 @@ __device__ __forceinline__ void deposit(R *const J[3], const DepositAxis<R, ORDE
 #pragma unroll
     for (int b = 0; b < NW; ++b) {
       const R by = Y.S0[b] + R(0.5) * Y.DS[b];
-      R *row = J[0] + jy[b];
+      const R ty = R(0.5) * Y.S0[b] + Y.DS[b] * R(1.0 / 3.0);
 #pragma unroll
-      for (int a = 0; a < NW - 1; ++a) atomicAdd(row + jx[a], Px[a] * by);
+      for (int a = 0; a < NW - 1; ++a) atomicAdd(Jx + b * SY + a, Px[a] * by);
+#pragma unroll
+      for (int a = 0; a < NW; ++a) atomicAdd(Jz + b * SY + a, qwvz * (X.S0[a] * by + X.DS[a] * ty));
     }
 #pragma unroll
     for (int a = 0; a < NW; ++a) {
       const R bx = X.S0[a] + R(0.5) * X.DS[a];
-      R *col = J[1] + jx[a];
 #pragma unroll
-      for (int b = 0; b < NW - 1; ++b) atomicAdd(col + jy[b], Py[b] * bx);
-    }
-#pragma unroll
-    for (int b = 0; b < NW; ++b) {
-      const R s0 = Y.S0[b] + R(0.5) * Y.DS[b];
-      const R s1 = R(0.5) * Y.S0[b] + Y.DS[b] * R(1.0 / 3.0);
-      R *row = J[2] + jy[b];
-#pragma unroll
-      for (int a = 0; a < NW; ++a) {
-        const R v = qwvz * (X.S0[a] * s0 + X.DS[a] * s1);
-        atomicAdd(row + jx[a], v);
-      }
+      for (int b = 0; b < NW - 1; ++b) atomicAdd(Jy + b * SY + a, Py[b] * bx);
     }
   }
 }
 
-template <class R, int DIM, int ORDER>
-__global__ void __launch_bounds__(256) k_push(const PushArgs<R> a) {
-  using M = Margins<ORDER>;
-  constexpr int NS = ORDER + 1;
-  constexpr int NW = ORDER + 2;
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  R *sm = reinterpret_cast<R *>(smem_raw);
-  __shared__ unsigned int s_esc, s_clamp;
-
-  const int64_t t = blockIdx.x;
-  const int64_t pb = a.tile_start[t], pe = a.tile_start[t + 1];
-  if (pb >= pe) return;
-
-  const int D = a.drift;
-  int t0[3], ew[3], jw[3];
-  {
-    int tt = (int)t;
-    const int tx = tt % a.ntile[0];
-    tt /= a.ntile[0];
-    const int ty = tt % a.ntile[1];
-    const int tz = tt / a.ntile[1];
-    t0[0] = tx * a.tile[0];
-    t0[1] = ty * a.tile[1];
-    t0[2] = tz * a.tile[2];
-  }
+// The per-particle physics shared by the tile kernel and the escape kernel:
+// given gathered E, B, advance u, move, and build the deposit stencils.
+template <class R, int ORDER, int DIM>
+__device__ __forceinline__ void push_move(const PushArgs<R> &a, R u[3], const R E[3], const R B[3], const R f[3],
+                                          R fn[3], int s[3], R &ig, unsigned &clamp) {
+  boris<R>(a.qmh, E, B, u);
+  ig = inv_sqrt<R>(R(1) + u[0] * u[0] + u[1] * u[1] + u[2] * u[2]);
 #pragma unroll
   for (int d = 0; d < 3; ++d) {
-    const bool act = d < DIM;
-    ew[d] = act ? a.tile[d] + 2 * D + M::LOE + M::HIE : 1;
-    jw[d] = act ? a.tile[d] + 2 * D + M::LOJ + M::HIJ : 1;
+    fn[d] = R(0);
+    s[d] = 0;
   }
-  const int ebN = ew[0] * ew[1] * ew[2];
-  const int jN = jw[0] * jw[1] * jw[2];
-  R *sF[6];
 #pragma unroll
-  for (int c = 0; c < 6; ++c) sF[c] = sm + c * ebN;
-  R *sJ[3];
-#pragma unroll
-  for (int c = 0; c < 3; ++c) sJ[c] = sm + 6 * ebN + c * jN;
+  for (int d = 0; d < DIM; ++d) {
+    R x = f[d] + a.dtdx[d] * u[d] * ig;
+    const int sh = (x >= R(1)) ? 1 : ((x < R(0)) ? -1 : 0);
+    x -= R(sh);
+    if (x >= R(1)) {
+      x = below_one<R>();
+      ++clamp;
+    }
+    if (x < R(0)) {
+      x = R(0);
+      ++clamp;
+    }
+    fn[d] = x;
+    s[d] = sh;
+  }
+}
 
-  // stage E, B of the tile + guard (periodic wrap of global indices)
-  for (int q = threadIdx.x; q < ebN; q += blockDim.x) {
-    const int x = q % ew[0];
-    const int r = q / ew[0];
-    const int y = r % ew[1];
-    const int z = r / ew[1];
-    const int gi = wrapi(t0[0] - D - M::LOE + x, a.n[0]);
-    const int gj = DIM >= 2 ? wrapi(t0[1] - D - M::LOE + y, a.n[1]) : 0;
-    const int gk = DIM == 3 ? wrapi(t0[2] - D - M::LOE + z, a.n[2]) : 0;
+template <class R, int DIM, int ORDER>
+__global__ void __launch_bounds__(kThreads, sizeof(R) == 4 ? 2 : 1) k_push(const PushArgs<R> a) {
+  using G = Geo<DIM, ORDER>;
+  constexpr int NS = G::NS;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  R *sF = reinterpret_cast<R *>(smem_raw);    // 6 * EN: Ex Ey Ez Bx By Bz
+  R *sJ = sF + 6 * G::EN;                     // 3 * JN: Jx Jy Jz
+  R *sOff = sJ + 3 * G::JN;                   // DIM x 256
+  R *sU = sOff + DIM * kThreads;              // 3 x 256
+  R *sW = sU + 3 * kThreads;                  // 256
+  int32_t *sCell = reinterpret_cast<int32_t *>(sW + kThreads);  // 256
+  __shared__ unsigned int s_clamp;
+
+  const int t = blockIdx.x;
+  const int64_t pb = a.tile_start[t], pe = a.tile_start[t + 1];
+  if (pb >= pe) return;
+  const int tid = threadIdx.x;
+  int t0[3];
+  {
+    const int tx = t % a.ntile[0];
+    const int r = t / a.ntile[0];
+    t0[0] = tx * G::TX;
+    t0[1] = (r % a.ntile[1]) * G::TY;
+    t0[2] = (r / a.ntile[1]) * G::TZ;
+  }
+
+  // ---- stage E, B of the tile + guard (periodic wrap of global indices) ----
+  for (int q = tid; q < G::EN; q += kThreads) {
+    const int x = q % G::EX;
+    const int y = (q / G::EX) % G::EY;
+    const int z = q / (G::EX * G::EY);
+    const int gi = wrapi(t0[0] - G::D - G::LOE + x, a.n[0]);
+    const int gj = wrapi(t0[1] - G::D - G::LOE + y, a.n[1]);
+    const int gk = DIM == 3 ? wrapi(t0[2] - G::D - G::LOE + z, a.n[2]) : 0;
     const int64_t g = gi + (int64_t)a.n[0] * (gj + (int64_t)a.n[1] * gk);
 #pragma unroll
     for (int c = 0; c < 3; ++c) {
-      sF[c][q] = a.E[c][g];
-      sF[3 + c][q] = a.B[c][g];
+      sF[c * G::EN + q] = a.E[c][g];
+      sF[(3 + c) * G::EN + q] = a.B[c][g];
     }
   }
-  for (int q = threadIdx.x; q < 3 * jN; q += blockDim.x) sJ[0][q] = R(0);
-  if (threadIdx.x == 0) {
-    s_esc = 0;
-    s_clamp = 0;
-  }
+  for (int q = tid; q < 3 * G::JN; q += kThreads) sJ[q] = R(0);
+  if (tid == 0) s_clamp = 0;
   __syncthreads();
 
-  const R *F6s[6] = {sF[0], sF[1], sF[2], sF[3], sF[4], sF[5]};
-  const R *F6g[6] = {a.E[0], a.E[1], a.E[2], a.B[0], a.B[1], a.B[2]};
-  unsigned int my_esc = 0, my_clamp = 0;
+  // lane-spreading permutation of the 256 staging slots (bijective; the
+  // eight warps' lanes land on 32 distinct banks)
+  const int lane = tid & 31, warp = tid >> 5;
+  const int e = 8 * lane + ((warp + (lane >> 2)) & 7);
+  unsigned my_clamp = 0;
 
-  for (int64_t pi = pb + threadIdx.x; pi < pe; pi += blockDim.x) {
-    const int c = a.cell[pi];
-    if (c < 0) continue;
-    int ci[3];
-    ci[0] = c % a.n[0];
-    {
-      const int r = c / a.n[0];
-      ci[1] = r % a.n[1];
-      ci[2] = DIM == 3 ? r / a.n[1] : 0;
-    }
-    int l[3] = {0, 0, 0};
-    bool inw = true;
+  for (int64_t c0 = pb; c0 < pe; c0 += kThreads) {
+    const int cn = (int)(pe - c0 < kThreads ? pe - c0 : kThreads);
+    // coalesced load of the chunk, slot order
+    if (tid < cn) {
+      const int64_t p = c0 + tid;
+      sCell[tid] = a.cell[p];
 #pragma unroll
-    for (int d = 0; d < DIM; ++d) {
-      int dl = ci[d] - t0[d];
-      if (dl > a.tile[d] - 1 + D) dl -= a.n[d];
-      if (dl < -D) dl += a.n[d];
-      l[d] = dl;
-      inw = inw && dl >= -D && dl <= a.tile[d] - 1 + D;
-    }
-    R f[3], u[3];
+      for (int d = 0; d < DIM; ++d) sOff[d * kThreads + tid] = a.off[d][p];
 #pragma unroll
-    for (int d = 0; d < 3; ++d) {
-      f[d] = d < DIM ? a.off[d][pi] : R(0);
-      u[d] = a.u[d][pi];
+      for (int d = 0; d < 3; ++d) sU[d * kThreads + tid] = a.u[d][p];
+      sW[tid] = a.w[p];
     }
-    const R wq = a.w[pi];
+    __syncthreads();
+    if (e < cn) {
+      const int c = sCell[e];
+      if (c >= 0) {
+        // decode the cell and its position relative to the tile
+        const uint32_t r0 = a.dn0.div((uint32_t)c);
+        int ci[3];
+        ci[0] = c - (int)r0 * a.n[0];
+        if (DIM == 3) {
+          const uint32_t r1 = a.dn1.div(r0);
+          ci[1] = (int)r0 - (int)r1 * a.n[1];
+          ci[2] = (int)r1;
+        } else {
+          ci[1] = (int)r0;
+          ci[2] = 0;
+        }
+        int l[3] = {0, 0, 0};
+        bool inw = true;
+        constexpr int TT[3] = {G::TX, G::TY, G::TZ};
+#pragma unroll
+        for (int d = 0; d < DIM; ++d) {
+          int dl = ci[d] - t0[d];
+          if (dl > TT[d] - 1 + G::D) dl -= a.n[d];
+          if (dl < -G::D) dl += a.n[d];
+          l[d] = dl;
+          inw = inw && dl >= -G::D && dl <= TT[d] - 1 + G::D;
+        }
+        if (!inw) {
+          // defer to k_push_escaped (state left untouched)
+          sCell[e] = c | kEscFlag;
+          const unsigned long long slot = atomicAdd(a.esc_count, 1ull);
+          a.esc_list[slot] = (int32_t)(c0 + e);
+        } else {
+          R f[3], u[3];
+#pragma unroll
+          for (int d = 0; d < 3; ++d) {
+            f[d] = d < DIM ? sOff[d * kThreads + e] : R(0);
+            u[d] = sU[d * kThreads + e];
+          }
+          // ---- gather (§2: g-weighted average of the grid fields) ----
+          GatherAxis<R, ORDER> gx, gy, gz;
+          gx.set(f[0]);
+          gy.set(f[1]);
+          gz.set(f[2]);
+          constexpr int oE = G::D + G::LOE;
+          const int xp = l[0] + gx.relp + oE, xd = l[0] + gx.reld + oE;
+          const int yp = (l[1] + gy.relp + oE) * G::EX, yd = (l[1] + gy.reld + oE) * G::EX;
+          const int zp = DIM == 3 ? (l[2] + gz.relp + oE) * G::EX * G::EY : 0;
+          const int zd = DIM == 3 ? (l[2] + gz.reld + oE) * G::EX * G::EY : 0;
+          constexpr int SY = G::EX, SZ = G::EX * G::EY;
+          R E[3], B[3];
+          E[0] = gsum<R, NS, DIM, SY, SZ>(sF + 0 * G::EN + xd + yp + zp, gx.wd, gy.wp, gz.wp);
+          E[1] = gsum<R, NS, DIM, SY, SZ>(sF + 1 * G::EN + xp + yd + zp, gx.wp, gy.wd, gz.wp);
+          E[2] = gsum<R, NS, DIM, SY, SZ>(sF + 2 * G::EN + xp + yp + zd, gx.wp, gy.wp, gz.wd);
+          B[0] = gsum<R, NS, DIM, SY, SZ>(sF + 3 * G::EN + xp + yd + zd, gx.wp, gy.wd, gz.wd);
+          B[1] = gsum<R, NS, DIM, SY, SZ>(sF + 4 * G::EN + xd + yp + zd, gx.wd, gy.wp, gz.wd);
+          B[2] = gsum<R, NS, DIM, SY, SZ>(sF + 5 * G::EN + xd + yd + zp, gx.wd, gy.wd, gz.wp);
 
-    // ---- gather (§2: g-weighted average of the grid fields) ----
-    GatherAxis<R, ORDER> ga[3];
-#pragma unroll
-    for (int d = 0; d < 3; ++d) ga[d].set(f[d]);
-    R E[3], B[3];
-    int ixp[NS], ixd[NS], iyp[NS], iyd[NS], izp[NS], izd[NS];
-    if (inw) {
-      const int o = D + M::LOE;
-#pragma unroll
-      for (int k = 0; k < NS; ++k) {
-        ixp[k] = l[0] + ga[0].relp + k + o;
-        ixd[k] = l[0] + ga[0].reld + k + o;
-        iyp[k] = (l[1] + ga[1].relp + k + o) * ew[0];
-        iyd[k] = (l[1] + ga[1].reld + k + o) * ew[0];
-        izp[k] = DIM == 3 ? (l[2] + ga[2].relp + k + o) * ew[0] * ew[1] : 0;
-        izd[k] = DIM == 3 ? (l[2] + ga[2].reld + k + o) * ew[0] * ew[1] : 0;
-      }
-      gather6<R, ORDER, DIM>(F6s, ga, ixp, ixd, iyp, iyd, izp, izd, E, B);
-    } else {
-      const int sy = a.n[0];
-      const int sz = a.n[0] * a.n[1];
-#pragma unroll
-      for (int k = 0; k < NS; ++k) {
-        ixp[k] = wrapi(ci[0] + ga[0].relp + k, a.n[0]);
-        ixd[k] = wrapi(ci[0] + ga[0].reld + k, a.n[0]);
-        iyp[k] = wrapi(ci[1] + ga[1].relp + k, a.n[1]) * sy;
-        iyd[k] = wrapi(ci[1] + ga[1].reld + k, a.n[1]) * sy;
-        izp[k] = DIM == 3 ? wrapi(ci[2] + ga[2].relp + k, a.n[2]) * sz : 0;
-        izd[k] = DIM == 3 ? wrapi(ci[2] + ga[2].reld + k, a.n[2]) * sz : 0;
-      }
-      gather6<R, ORDER, DIM>(F6g, ga, ixp, ixd, iyp, iyd, izp, izd, E, B);
-    }
+          // ---- Boris push (§2 eq. 3) and leap-frog move ----
+          R fn[3], ig;
+          int s[3];
+          push_move<R, ORDER, DIM>(a, u, E, B, f, fn, s, ig, my_clamp);
 
-    // ---- Boris push (§2 eq. 3) ----
-    boris<R>(a.qmh, E, B, u);
+          // ---- Esirkepov deposit (§2 eq. 4 + continuity) ----
+          DepositAxis<R, ORDER> dx, dy, dz;
+          dx.set(f[0], s[0], fn[0]);
+          dy.set(f[1], s[1], fn[1]);
+          if (DIM == 3) dz.set(f[2], s[2], fn[2]);
+          else dz.zero();
+          const R wq = sW[e];
+          constexpr int oJ = G::D + G::LOJ;
+          const int jb = (l[0] + dx.rel + oJ) + (l[1] + dy.rel + oJ) * G::JX +
+                         (DIM == 3 ? (l[2] + dz.rel + oJ) * G::JX * G::JY : 0);
+          deposit_win<R, ORDER, DIM, G::JX, G::JX * G::JY, G::JN, true>(
+              sJ, jb, dx, dy, dz, a.jfac[0] * wq, a.jfac[1] * wq, a.jfac[2] * wq, a.qz * wq * u[2] * ig);
 
-    // ---- leap-frog move with integer cell carry ----
-    const R ig = R(1) / sqrt(R(1) + u[0] * u[0] + u[1] * u[1] + u[2] * u[2]);
-    R fn[3] = {R(0), R(0), R(0)};
-    int s[3] = {0, 0, 0};
+          // ---- new state back into the staging slot ----
+          int nc = c;
+          {
+            int i0 = ci[0] + s[0];
+            nc += s[0] + (i0 < 0 ? a.n[0] : (i0 >= a.n[0] ? -a.n[0] : 0));
+            const int i1 = ci[1] + s[1];
+            nc += (s[1] + (i1 < 0 ? a.n[1] : (i1 >= a.n[1] ? -a.n[1] : 0))) * a.n[0];
+            if (DIM == 3) {
+              const int i2 = ci[2] + s[2];
+              nc += (s[2] + (i2 < 0 ? a.n[2] : (i2 >= a.n[2] ? -a.n[2] : 0))) * a.n[0] * a.n[1];
+            }
+          }
+          sCell[e] = nc;
 #pragma unroll
-    for (int d = 0; d < DIM; ++d) {
-      R x = f[d] + a.dtdx[d] * u[d] * ig;
-      const int sh = (x >= R(1)) ? 1 : ((x < R(0)) ? -1 : 0);
-      x -= R(sh);
-      if (x >= R(1)) {
-        x = below_one<R>();
-        ++my_clamp;
-      }
-      if (x < R(0)) {
-        x = R(0);
-        ++my_clamp;
-      }
-      fn[d] = x;
-      s[d] = sh;
-    }
-
-    // ---- Esirkepov deposit (§2 eq. 4 + continuity) ----
-    DepositAxis<R, ORDER> da[3];
+          for (int d = 0; d < DIM; ++d) sOff[d * kThreads + e] = fn[d];
 #pragma unroll
-    for (int d = 0; d < 3; ++d) {
-      if (d < DIM) {
-        da[d].set(f[d], s[d], fn[d]);
-      } else {
-        // 2D: no z extent; a unit weight on the single layer keeps the 3D
-        // formulas unused.
-        da[d].rel = 0;
-#pragma unroll
-        for (int k = 0; k < NW; ++k) {
-          da[d].S0[k] = R(0);
-          da[d].DS[k] = R(0);
+          for (int d = 0; d < 3; ++d) sU[d * kThreads + e] = u[d];
         }
       }
     }
-    const R cx = a.jfac[0] * wq, cy = a.jfac[1] * wq, cz = a.jfac[2] * wq;
-    const R qwvz = a.qz * wq * u[2] * ig;
-    int jx[NW], jy[NW], jz[NW];
-    if (inw) {
-      const int o = D + M::LOJ;
+    __syncthreads();
+    // coalesced store of the chunk (w is unchanged)
+    if (tid < cn) {
+      const int64_t p = c0 + tid;
+      a.cell[p] = sCell[tid];
 #pragma unroll
-      for (int k = 0; k < NW; ++k) {
-        jx[k] = l[0] + da[0].rel + k + o;
-        jy[k] = (l[1] + da[1].rel + k + o) * jw[0];
-        jz[k] = DIM == 3 ? (l[2] + da[2].rel + k + o) * jw[0] * jw[1] : 0;
-      }
-      deposit<R, ORDER, DIM>(sJ, da, jx, jy, jz, cx, cy, cz, qwvz);
-    } else {
-      ++my_esc;
-      const int sy = a.n[0];
-      const int sz = a.n[0] * a.n[1];
+      for (int d = 0; d < DIM; ++d) a.off[d][p] = sOff[d * kThreads + tid];
 #pragma unroll
-      for (int k = 0; k < NW; ++k) {
-        jx[k] = wrapi(ci[0] + da[0].rel + k, a.n[0]);
-        jy[k] = wrapi(ci[1] + da[1].rel + k, a.n[1]) * sy;
-        jz[k] = DIM == 3 ? wrapi(ci[2] + da[2].rel + k, a.n[2]) * sz : 0;
-      }
-      deposit<R, ORDER, DIM>(a.J, da, jx, jy, jz, cx, cy, cz, qwvz);
+      for (int d = 0; d < 3; ++d) a.u[d][p] = sU[d * kThreads + tid];
     }
-
-    // ---- store the new state ----
-    int nc[3] = {ci[0], ci[1], ci[2]};
-#pragma unroll
-    for (int d = 0; d < DIM; ++d) nc[d] = wrapi(ci[d] + s[d], a.n[d]);
-    a.cell[pi] = nc[0] + a.n[0] * (nc[1] + a.n[1] * nc[2]);
-#pragma unroll
-    for (int d = 0; d < DIM; ++d) a.off[d][pi] = fn[d];
-#pragma unroll
-    for (int d = 0; d < 3; ++d) a.u[d][pi] = u[d];
   }
 
-  if (my_esc) atomicAdd(&s_esc, my_esc);
   if (my_clamp) atomicAdd(&s_clamp, my_clamp);
   __syncthreads();
 
   // ---- flush the J window into global J ----
-  for (int q = threadIdx.x; q < jN; q += blockDim.x) {
-    const int x = q % jw[0];
-    const int r = q / jw[0];
-    const int y = r % jw[1];
-    const int z = r / jw[1];
-    const int gi = wrapi(t0[0] - D - M::LOJ + x, a.n[0]);
-    const int gj = wrapi(t0[1] - D - M::LOJ + y, a.n[1]);
-    const int gk = DIM == 3 ? wrapi(t0[2] - D - M::LOJ + z, a.n[2]) : 0;
+  for (int q = tid; q < G::JN; q += kThreads) {
+    const int x = q % G::JX;
+    const int y = (q / G::JX) % G::JY;
+    const int z = q / (G::JX * G::JY);
+    const int gi = wrapi(t0[0] - G::D - G::LOJ + x, a.n[0]);
+    const int gj = wrapi(t0[1] - G::D - G::LOJ + y, a.n[1]);
+    const int gk = DIM == 3 ? wrapi(t0[2] - G::D - G::LOJ + z, a.n[2]) : 0;
     const int64_t g = gi + (int64_t)a.n[0] * (gj + (int64_t)a.n[1] * gk);
 #pragma unroll
     for (int c = 0; c < 3; ++c) {
-      const R v = sJ[c][q];
+      const R v = sJ[c * G::JN + q];
       if (v != R(0)) atomicAdd(a.J[c] + g, v);
     }
   }
-  if (threadIdx.x == 0) {
-    if (s_esc) atomicAdd(&a.ctr->escaped, (unsigned long long)s_esc);
-    if (s_clamp) atomicAdd(&a.ctr->clamped, (unsigned long long)s_clamp);
-  }
+  if (tid == 0 && s_clamp) atomicAdd(&a.ctr->clamped, (unsigned long long)s_clamp);
 }
 
-template <int ORDER> size_t window_bytes(const Grid &g, size_t rsize) {
-  using M = Margins<ORDER>;
-  size_t ebN = 1, jN = 1;
-  for (int d = 0; d < g.dims; ++d) {
-    ebN *= (size_t)(g.tile[d] + 2 * g.drift + M::LOE + M::HIE);
-    jN *= (size_t)(g.tile[d] + 2 * g.drift + M::LOJ + M::HIJ);
+// Particles deferred by the tile kernel: the same gather / Boris / move /
+// Esirkepov arithmetic, reading E, B from and adding J to global memory with
+// periodic index wrapping.
+template <class R, int DIM, int ORDER>
+__global__ void __launch_bounds__(kThreads) k_push_escaped(const PushArgs<R> a) {
+  constexpr int NS = ORDER + 1;
+  constexpr int NW = ORDER + 2;
+  const unsigned long long nesc = *a.esc_count;
+  unsigned my_clamp = 0;
+  for (unsigned long long q = blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x; q < nesc;
+       q += (unsigned long long)gridDim.x * blockDim.x) {
+    const int64_t p = a.esc_list[q];
+    const int c = a.cell[p] & ~kEscFlag;
+    int ci[3];
+    ci[0] = c % a.n[0];
+    ci[1] = (c / a.n[0]) % a.n[1];
+    ci[2] = DIM == 3 ? c / (a.n[0] * a.n[1]) : 0;
+    R f[3], u[3];
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+      f[d] = d < DIM ? a.off[d][p] : R(0);
+      u[d] = a.u[d][p];
+    }
+    GatherAxis<R, ORDER> ga[3];
+#pragma unroll
+    for (int d = 0; d < 3; ++d) ga[d].set(f[d]);
+    const int64_t sy = a.n[0], sz = (int64_t)a.n[0] * a.n[1];
+    auto fetch = [&](const R *F, const bool dual[3]) {
+      R acc = R(0);
+      for (int cz = 0; cz < (DIM == 3 ? NS : 1); ++cz) {
+        const int kz = DIM == 3 ? wrapi(ci[2] + (dual[2] ? ga[2].reld : ga[2].relp) + cz, a.n[2]) : 0;
+        const R wz = DIM == 3 ? (dual[2] ? ga[2].wd[cz] : ga[2].wp[cz]) : R(1);
+        for (int by = 0; by < NS; ++by) {
+          const int ky = wrapi(ci[1] + (dual[1] ? ga[1].reld : ga[1].relp) + by, a.n[1]);
+          const R wy = dual[1] ? ga[1].wd[by] : ga[1].wp[by];
+          for (int ax = 0; ax < NS; ++ax) {
+            const int kx = wrapi(ci[0] + (dual[0] ? ga[0].reld : ga[0].relp) + ax, a.n[0]);
+            const R wx = dual[0] ? ga[0].wd[ax] : ga[0].wp[ax];
+            acc += F[kx + sy * ky + sz * kz] * (wx * wy * wz);
+          }
+        }
+      }
+      return acc;
+    };
+    const bool sE[3][3] = {{true, false, false}, {false, true, false}, {false, false, true}};
+    const bool sB[3][3] = {{false, true, true}, {true, false, true}, {true, true, false}};
+    R E[3], B[3];
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+      E[k] = fetch(a.E[k], sE[k]);
+      B[k] = fetch(a.B[k], sB[k]);
+    }
+    R fn[3], ig;
+    int s[3];
+    push_move<R, ORDER, DIM>(a, u, E, B, f, fn, s, ig, my_clamp);
+    DepositAxis<R, ORDER> da[3];
+    da[0].set(f[0], s[0], fn[0]);
+    da[1].set(f[1], s[1], fn[1]);
+    if (DIM == 3) da[2].set(f[2], s[2], fn[2]);
+    else da[2].zero();
+    const R wq = a.w[p];
+    // global Esirkepov with wrapped node indices
+    R P[3][NW - 1];
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+      R run = R(0);
+      for (int k = 0; k < NW - 1; ++k) {
+        run += da[d].DS[k];
+        P[d][k] = a.jfac[d] * wq * run;
+      }
+    }
+    int gx[NW], gy[NW], gz[NW];
+    for (int k = 0; k < NW; ++k) {
+      gx[k] = wrapi(ci[0] + da[0].rel + k, a.n[0]);
+      gy[k] = wrapi(ci[1] + da[1].rel + k, a.n[1]);
+      gz[k] = DIM == 3 ? wrapi(ci[2] + da[2].rel + k, a.n[2]) : 0;
+    }
+    const DepositAxis<R, ORDER> &X = da[0], &Y = da[1], &Z = da[2];
+    if (DIM == 3) {
+      for (int cz = 0; cz < NW; ++cz)
+        for (int by = 0; by < NW; ++by)
+          for (int ax = 0; ax < NW; ++ax) {
+            const int64_t g = gx[ax] + sy * gy[by] + sz * gz[cz];
+            const R bx = Y.S0[by] * (Z.S0[cz] + R(0.5) * Z.DS[cz]) + Y.DS[by] * (R(0.5) * Z.S0[cz] + Z.DS[cz] * R(1.0 / 3.0));
+            const R byy = Z.S0[cz] * (X.S0[ax] + R(0.5) * X.DS[ax]) + Z.DS[cz] * (R(0.5) * X.S0[ax] + X.DS[ax] * R(1.0 / 3.0));
+            const R bz = X.S0[ax] * (Y.S0[by] + R(0.5) * Y.DS[by]) + X.DS[ax] * (R(0.5) * Y.S0[by] + Y.DS[by] * R(1.0 / 3.0));
+            if (ax < NW - 1) atomicAdd(a.J[0] + g, P[0][ax] * bx);
+            if (by < NW - 1) atomicAdd(a.J[1] + g, P[1][by] * byy);
+            if (cz < NW - 1) atomicAdd(a.J[2] + g, P[2][cz] * bz);
+          }
+    } else {
+      const R qwvz = a.qz * wq * u[2] * ig;
+      for (int by = 0; by < NW; ++by)
+        for (int ax = 0; ax < NW; ++ax) {
+          const int64_t g = gx[ax] + sy * gy[by];
+          const R hy = Y.S0[by] + R(0.5) * Y.DS[by];
+          const R ty = R(0.5) * Y.S0[by] + Y.DS[by] * R(1.0 / 3.0);
+          const R hx = X.S0[ax] + R(0.5) * X.DS[ax];
+          if (ax < NW - 1) atomicAdd(a.J[0] + g, P[0][ax] * hy);
+          if (by < NW - 1) atomicAdd(a.J[1] + g, P[1][by] * hx);
+          atomicAdd(a.J[2] + g, qwvz * (X.S0[ax] * hy + X.DS[ax] * ty));
+        }
+    }
+    int nc[3] = {ci[0], ci[1], ci[2]};
+#pragma unroll
+    for (int d = 0; d < DIM; ++d) nc[d] = wrapi(ci[d] + s[d], a.n[d]);
+    a.cell[p] = nc[0] + a.n[0] * (nc[1] + a.n[1] * nc[2]);
+#pragma unroll
+    for (int d = 0; d < DIM; ++d) a.off[d][p] = fn[d];
+#pragma unroll
+    for (int d = 0; d < 3; ++d) a.u[d][p] = u[d];
   }
-  return (6 * ebN + 3 * jN) * rsize;
+  if (my_clamp) atomicAdd(&a.ctr->clamped, (unsigned long long)my_clamp);
+  // escaped particle-steps are counted by the host-visible counter
+  if (blockIdx.x == 0 && threadIdx.x == 0 && nesc) atomicAdd(&a.ctr->escaped, nesc);
+}
+
+template <class R, int DIM, int ORDER> constexpr size_t smem_bytes() {
+  using G = Geo<DIM, ORDER>;
+  return (size_t)(6 * G::EN + 3 * G::JN + (DIM + 4) * kThreads) * sizeof(R) + kThreads * sizeof(int32_t);
 }
 
 template <class R, int DIM, int ORDER>
 cudaError_t launch_t(const Grid &g, void *const E[3], void *const B[3], void *const J[3], const Particles &p,
-                     const int64_t *tile_start, double q, double m, Counters *ctr, cudaStream_t st) {
+                     const int64_t *tile_start, int32_t *esc_list, unsigned long long *esc_count, double q, double m,
+                     Counters *ctr, cudaStream_t st, int *nlaunch) {
   PushArgs<R> a;
   for (int d = 0; d < 3; ++d) {
     a.n[d] = g.n[d];
-    a.tile[d] = g.tile[d];
-    a.ntile[d] = g.ntile[d];
     a.E[d] = static_cast<const R *>(E[d]);
     a.B[d] = static_cast<const R *>(B[d]);
     a.J[d] = static_cast<R *>(J[d]);
@@ -435,43 +547,76 @@ cudaError_t launch_t(const Grid &g, void *const E[3], void *const B[3], void *co
     a.dtdx[d] = (R)(g.dt / g.dx[d]);
     a.jfac[d] = (R)(-q * g.dx[d] / g.dt);
   }
-  a.drift = g.drift;
+  a.ntile[0] = g.ntile[0];
+  a.ntile[1] = g.ntile[1];
+  a.dn0 = make_fastdiv((uint32_t)g.n[0]);
+  a.dn1 = make_fastdiv((uint32_t)g.n[1]);
   a.cell = p.cell;
   a.w = static_cast<const R *>(p.w);
   a.tile_start = tile_start;
+  a.esc_list = esc_list;
+  a.esc_count = esc_count;
   a.qmh = (R)(q * g.dt / (2.0 * m));
   a.qz = (R)q;
   a.ctr = ctr;
-  const size_t smem = window_bytes<ORDER>(g, sizeof(R));
+  constexpr size_t smem = smem_bytes<R, DIM, ORDER>();
   auto fn = k_push<R, DIM, ORDER>;
   cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   if (g.ntiles > 0x7fffffff) return cudaErrorInvalidValue;
-  fn<<<(unsigned)g.ntiles, 256, smem, st>>>(a);
+  e = cudaMemsetAsync(esc_count, 0, sizeof(unsigned long long), st);
+  if (e != cudaSuccess) return e;
+  fn<<<(unsigned)g.ntiles, kThreads, smem, st>>>(a);
+  int dev = 0, nsm = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+  k_push_escaped<R, DIM, ORDER><<<nsm, kThreads, 0, st>>>(a);
+  if (nlaunch) *nlaunch = 2;
   return cudaGetLastError();
 }
 
 }  // namespace
 
+// Tile shape compiled into the push kernel for a given dimensionality.
+void push_tile_shape(int dims, int tile[3]) {
+  tile[0] = dims == 3 ? Geo<3, 2>::TX : Geo<2, 2>::TX;
+  tile[1] = dims == 3 ? Geo<3, 2>::TY : Geo<2, 2>::TY;
+  tile[2] = dims == 3 ? Geo<3, 2>::TZ : 1;
+}
+
 size_t push_smem_bytes(const Grid &g) {
-  const size_t rs = g.prec == 1 ? sizeof(double) : sizeof(float);
-  return g.order == 2 ? window_bytes<2>(g, rs) : window_bytes<1>(g, rs);
+  const int key = (g.prec == 1 ? 100 : 0) + g.dims * 10 + g.order;
+  switch (key) {
+    case 21: return smem_bytes<float, 2, 1>();
+    case 22: return smem_bytes<float, 2, 2>();
+    case 31: return smem_bytes<float, 3, 1>();
+    case 32: return smem_bytes<float, 3, 2>();
+    case 121: return smem_bytes<double, 2, 1>();
+    case 122: return smem_bytes<double, 2, 2>();
+    case 131: return smem_bytes<double, 3, 1>();
+    case 132: return smem_bytes<double, 3, 2>();
+    default: return 0;
+  }
 }
 
 cudaError_t launch_push(const Grid &g, void *const E[3], void *const B[3], void *const J[3], const Particles &p,
-                        const int64_t *tile_start, double q, double m, Counters *ctr, cudaStream_t st) {
+                        const int64_t *tile_start, int32_t *esc_list, unsigned long long *esc_count, double q,
+                        double m, Counters *ctr, cudaStream_t st, int *nlaunch) {
   const int key = (g.prec == 1 ? 100 : 0) + g.dims * 10 + g.order;
+#define PIC_PUSH_CASE(K, R, D, O) \
+  case K: return launch_t<R, D, O>(g, E, B, J, p, tile_start, esc_list, esc_count, q, m, ctr, st, nlaunch);
   switch (key) {
-    case 21: return launch_t<float, 2, 1>(g, E, B, J, p, tile_start, q, m, ctr, st);
-    case 22: return launch_t<float, 2, 2>(g, E, B, J, p, tile_start, q, m, ctr, st);
-    case 31: return launch_t<float, 3, 1>(g, E, B, J, p, tile_start, q, m, ctr, st);
-    case 32: return launch_t<float, 3, 2>(g, E, B, J, p, tile_start, q, m, ctr, st);
-    case 121: return launch_t<double, 2, 1>(g, E, B, J, p, tile_start, q, m, ctr, st);
-    case 122: return launch_t<double, 2, 2>(g, E, B, J, p, tile_start, q, m, ctr, st);
-    case 131: return launch_t<double, 3, 1>(g, E, B, J, p, tile_start, q, m, ctr, st);
-    case 132: return launch_t<double, 3, 2>(g, E, B, J, p, tile_start, q, m, ctr, st);
+    PIC_PUSH_CASE(21, float, 2, 1)
+    PIC_PUSH_CASE(22, float, 2, 2)
+    PIC_PUSH_CASE(31, float, 3, 1)
+    PIC_PUSH_CASE(32, float, 3, 2)
+    PIC_PUSH_CASE(121, double, 2, 1)
+    PIC_PUSH_CASE(122, double, 2, 2)
+    PIC_PUSH_CASE(131, double, 3, 1)
+    PIC_PUSH_CASE(132, double, 3, 2)
     default: return cudaErrorInvalidValue;
   }
+#undef PIC_PUSH_CASE
 }
 
 }  // namespace pic

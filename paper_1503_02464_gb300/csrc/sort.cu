@@ -66,7 +66,7 @@ __global__ void k_tile_sum(const int32_t *__restrict__ count, int64_t ntiles, in
   int64_t s = 0;
   for (int i = lane; i < tc; i += 32) s += c[i];
   for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
-  if (lane == 0) tsum[t] = s;
+  if (lane == 0) tsum[t] = (s + kTilePad - 1) / kTilePad * kTilePad;  // padded run length
 }
 
 // single block exclusive scan of ntiles values -> tile_start[0..ntiles]
@@ -99,8 +99,10 @@ __global__ void k_scan_tiles(const int64_t *__restrict__ tsum, int64_t ntiles, i
   }
 }
 
-// one warp per tile: count[key] <- absolute start slot of the key
-__global__ void k_offsets(int32_t *__restrict__ count, int64_t ntiles, int tc, const int64_t *__restrict__ tile_start) {
+// one warp per tile: count[key] <- absolute start slot of the key; the
+// tile's padding slots in the destination are marked dead
+__global__ void k_offsets(int32_t *__restrict__ count, int64_t ntiles, int tc, const int64_t *__restrict__ tile_start,
+                          int32_t *__restrict__ dst_cell) {
   const int64_t t = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
   const int lane = threadIdx.x & 31;
   if (t >= ntiles) return;
@@ -117,6 +119,7 @@ __global__ void k_offsets(int32_t *__restrict__ count, int64_t ntiles, int tc, c
     if (i < tc) c[i] = (int32_t)(run + incl - v);
     run += __shfl_sync(0xffffffffu, incl, 31);
   }
+  if (run + lane < tile_start[t + 1]) dst_cell[run + lane] = -1;
 }
 
 template <class R>
@@ -168,7 +171,7 @@ cudaError_t launch_sort(const Grid &g, const Particles &src, const Particles &ds
   e = cudaMemcpyAsync(tile_tmp + g.ntiles, d_count, sizeof(int64_t), cudaMemcpyDeviceToDevice, st);
   if (e != cudaSuccess) return e;
   k_scan_tiles<<<1, 1024, 0, st>>>(tile_tmp, g.ntiles, tile_start, d_count);
-  k_offsets<<<wb, 256, 0, st>>>(keys, g.ntiles, km.tc, tile_start);
+  k_offsets<<<wb, 256, 0, st>>>(keys, g.ntiles, km.tc, tile_start, dst.cell);
   if (g.prec == 1)
     k_scatter<double><<<nb, 256, 0, st>>>(km, g.dims, src, dst, tile_tmp + g.ntiles, keys, rank);
   else

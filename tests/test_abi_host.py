@@ -42,15 +42,17 @@ def test_every_declared_symbol_exported(lib):
 
 def _cfg(**kw):
     from paper_1503_02464_gb300.sim import make_config
-    base = dict(dims=3, n=(8, 8, 8), d=(0.1, 0.1, 0.1), dt=0.05, order=2)
+    base = dict(dims=3, n=(8, 8, 8), d=(0.1, 0.1, 0.1), dt=0.05, order=2, tile=None)
     base.update(kw)
-    return make_config(base["dims"], base["n"], base["d"], base["dt"], base["order"])
+    return make_config(base["dims"], base["n"], base["d"], base["dt"], base["order"], tile=base["tile"])
 
 
 @pytest.mark.parametrize("kw,code", [
     (dict(dims=4), 1), (dict(order=3), 1), (dict(dt=-1.0), 1),
     (dict(dt=0.0578), 2),           # 3D Yee limit for dx = 0.1 is 0.057735
     (dict(dims=2, n=(8, 8), d=(0.1, 0.1), dt=0.0708), 2),  # 2D limit 0.070711
+    (dict(tile=(4, 4, 4)), 1),      # only the compiled tile shape
+    (dict(n=(1024, 1024, 1024)), 1),  # 2^30 cells
 ])
 def test_create_rejects_bad_config(lib, kw, code):
     from paper_1503_02464_gb300 import capi

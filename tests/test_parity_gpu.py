@@ -92,13 +92,14 @@ def test_tiny_brute_force(dims, order, npart):
         assert du <= FP64_TOL_PER_STEP * step and dx <= 1e-10
 
 
-def test_escape_path_fp64():
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+def test_escape_path(precision):
     """Hot plasma, no re-sorting: particles leave their tile windows and take
     the global-memory path; results still match the oracle."""
-    wl = _wl(3, 2, (16, 16, 8), 2, 0.8, 99)
+    wl = _wl(3, 2, (24, 16, 16), 2, 0.8, 99)
     parts = [wl.particles(0)]
     o = build_oracle(wl, parts)
-    s = build_gpu(wl, parts, "fp64", tile=(4, 4, 4), sort_every=1000, drift_guard=1)
+    s = build_gpu(wl, parts, precision, sort_every=1000)
     for step in range(1, 9):
         o.step(1)
         s.step(1)
@@ -106,9 +107,11 @@ def test_escape_path_fp64():
     du, dx = compare_particles(o, s, wl)
     d = s.diag()
     assert d["n_escaped"] > 0
+    tol = FP64_TOL_PER_STEP * 8 if precision == "fp64" else FP32_TOL
     for k, v in fe.items():
-        assert v <= FP64_TOL_PER_STEP * 8, (k, v)
-    assert du <= FP64_TOL_PER_STEP * 8
+        if precision == "fp64" or not k.startswith("J"):
+            assert v <= tol, (k, v)
+    assert du <= tol
 
 
 def test_thermal2d_64_full_fp64():
