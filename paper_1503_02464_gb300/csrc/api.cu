@@ -34,6 +34,7 @@ struct Species {
   int64_t h_count = 0;          // host mirror, valid while !stepped_since_count
   int32_t *rank = nullptr;
   int64_t *tile_start = nullptr;
+  void *wmax = nullptr;         // max |w| (float or double), raised by every load
   bool need_sort = true;
 };
 
@@ -230,7 +231,7 @@ int pic_create(const pic_config *cfg, pic_handle **out) {
   pic::push_tile_shape(c.dims, ctile);
   for (int d = 0; d < c.dims; ++d)
     if (c.tile[d] != 0 && c.tile[d] != ctile[d])
-      return fail(nullptr, PIC_EINVAL, "tile must be 0 (default) or the compiled tile shape (8x8x8 in 3D, 16x16 in 2D)");
+      return fail(nullptr, PIC_EINVAL, "tile must be 0 (default) or the compiled tile shape (8x8x4 in 3D, 16x16 in 2D)");
   if (c.drift_guard != 0 && c.drift_guard != 1)
     return fail(nullptr, PIC_EINVAL, "drift_guard must be 0 or 1 (the compiled drift allowance)");
 
@@ -333,6 +334,7 @@ int pic_destroy(pic_handle *h) {
     cudaFree(s.d_count);
     cudaFree(s.rank);
     cudaFree(s.tile_start);
+    cudaFree(s.wmax);
   }
   for (auto &t : h->timers) {
     cudaEventDestroy(t.a);
@@ -361,18 +363,21 @@ int pic_add_species(pic_handle *h, double q, double m, int64_t capacity, int *sp
   if (e == cudaSuccess) e = cudaMalloc(&s.d_count, sizeof(int64_t));
   if (e == cudaSuccess) e = cudaMalloc(&s.rank, (size_t)(s.slots > 0 ? s.slots : 1) * sizeof(int32_t));
   if (e == cudaSuccess) e = cudaMalloc(&s.tile_start, (size_t)(h->g.ntiles + 1) * sizeof(int64_t));
+  if (e == cudaSuccess) e = cudaMalloc(&s.wmax, sizeof(double));
   if (e != cudaSuccess) {
     free_particles(s.buf[0]);
     free_particles(s.buf[1]);
     cudaFree(s.d_count);
     cudaFree(s.rank);
     cudaFree(s.tile_start);
+    cudaFree(s.wmax);
     s = Species{};
     cudaGetLastError();
     return fail(h, PIC_ENOMEM, "device allocation failed in pic_add_species");
   }
   cudaMemsetAsync(s.d_count, 0, sizeof(int64_t), h->st);
   cudaMemsetAsync(s.tile_start, 0, (size_t)(h->g.ntiles + 1) * sizeof(int64_t), h->st);
+  cudaMemsetAsync(s.wmax, 0, sizeof(double), h->st);
   *species = h->nsp++;
   return PIC_OK;
 }
@@ -421,7 +426,7 @@ int pic_load_particles(pic_handle *h, int species, int64_t n, const double *x, c
   CK(h, cudaMemsetAsync(h->bad, 0, sizeof(unsigned long long), h->st), "memset");
   CK(h,
      pic::launch_load(h->g, s.buf[s.cur], cur, n, dsrc[0], dsrc[1], dsrc[2], dsrc[3], dsrc[4], dsrc[5], dsrc[6], did,
-                      h->bad, h->st),
+                      h->bad, s.wmax, h->st),
      "load kernel");
   h->launches++;
   const int64_t nn = cur + n;
@@ -473,8 +478,8 @@ int pic_step(pic_handle *h, int nsteps) {
       Timed tm(h, pic::KC_PUSH);
       int nl = 0;
       CK(h,
-         pic::launch_push(h->g, h->E, h->B, h->J, s.buf[s.cur], s.tile_start, s.rank, h->esc_count, s.q, s.m, h->ctr,
-                          h->st, &nl),
+         pic::launch_push(h->g, h->E, h->B, h->J, s.buf[s.cur], s.tile_start, s.wmax, s.rank, h->esc_count, s.q,
+                          s.m, h->ctr, h->st, &nl),
          "push");
       h->launches += nl;
     }

@@ -104,7 +104,7 @@ __global__ void k_load(int dims, int n0, int n1, int n2, double rdx0, double rdx
                        int64_t offset, int64_t n, const double *__restrict__ x, const double *__restrict__ y,
                        const double *__restrict__ z, const double *__restrict__ ux, const double *__restrict__ uy,
                        const double *__restrict__ uz, const double *__restrict__ w, const uint32_t *__restrict__ id,
-                       unsigned long long *bad) {
+                       unsigned long long *bad, R *wmax) {
   for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < n; q += (int64_t)gridDim.x * blockDim.x) {
     const double pos[3] = {x[q] * rdx0, y[q] * rdx1, dims == 3 ? z[q] * rdx2 : 0.0};
     const int nn[3] = {n0, n1, n2};
@@ -141,6 +141,12 @@ __global__ void k_load(int dims, int n0, int n1, int n2, double rdx0, double rdx
     static_cast<R *>(p.u[2])[s] = (R)uz[q];
     static_cast<R *>(p.w)[s] = (R)w[q];
     p.id[s] = id ? id[q] : (uint32_t)q;
+    // max |w| through the order-preserving bit pattern of a non-negative value
+    const R aw = fabs((R)w[q]);
+    if (sizeof(R) == 4)
+      atomicMax(reinterpret_cast<unsigned int *>(wmax), __float_as_uint((float)aw));
+    else
+      atomicMax(reinterpret_cast<unsigned long long *>(wmax), (unsigned long long)__double_as_longlong((double)aw));
   }
 }
 
@@ -319,16 +325,18 @@ cudaError_t launch_yee_e(const Grid &g, void *const E[3], void *const B[3], void
 
 cudaError_t launch_load(const Grid &g, const Particles &p, int64_t offset, int64_t n, const double *x,
                         const double *y, const double *z, const double *ux, const double *uy, const double *uz,
-                        const double *w, const uint32_t *id, unsigned long long *bad, cudaStream_t st) {
+                        const double *w, const uint32_t *id, unsigned long long *bad, void *wmax, cudaStream_t st) {
   if (n <= 0) return cudaSuccess;
   const int nb = grid_blocks(n, 256);
   const int absorb = g.absorb_lo || g.absorb_hi;
   if (g.prec == 1)
     k_load<double><<<nb, 256, 0, st>>>(g.dims, g.n[0], g.n[1], g.n[2], 1.0 / g.dx[0], 1.0 / g.dx[1], 1.0 / g.dx[2],
-                                       absorb, p, offset, n, x, y, z, ux, uy, uz, w, id, bad);
+                                       absorb, p, offset, n, x, y, z, ux, uy, uz, w, id, bad,
+                                       static_cast<double *>(wmax));
   else
     k_load<float><<<nb, 256, 0, st>>>(g.dims, g.n[0], g.n[1], g.n[2], 1.0 / g.dx[0], 1.0 / g.dx[1], 1.0 / g.dx[2],
-                                      absorb, p, offset, n, x, y, z, ux, uy, uz, w, id, bad);
+                                      absorb, p, offset, n, x, y, z, ux, uy, uz, w, id, bad,
+                                      static_cast<float *>(wmax));
   return cudaGetLastError();
 }
 

@@ -51,15 +51,17 @@ constexpr int kTilePad = 4;
 enum KernelClass { KC_SORT = 0, KC_ZEROJ = 1, KC_PUSH = 2, KC_YEE_B = 3, KC_YEE_E = 4, KC_BOUNDARY = 5, KC_N = 6 };
 
 // ---- push (push.cu) ----
-// Tile shape compiled into the push kernel (8x8x8 in 3D, 16x16 in 2D); the
+// Tile shape compiled into the push kernel (8x8x4 in 3D, 16x16 in 2D); the
 // drift allowance is one cell.
 void push_tile_shape(int dims, int tile[3]);
 size_t push_smem_bytes(const Grid &g);
-// Tile kernel + escape kernel.  esc_list (one int per slot) and esc_count are
+// Tile kernel + escape kernel.  wmax: device pointer to max |w| of the
+// species (float or double).  esc_list (one int per slot) and esc_count are
 // scratch for particles deferred to the escape kernel.
 cudaError_t launch_push(const Grid &g, void *const E[3], void *const B[3], void *const J[3], const Particles &p,
-                        const int64_t *tile_start, int32_t *esc_list, unsigned long long *esc_count, double q,
-                        double m, Counters *ctr, cudaStream_t st, int *nlaunch);
+                        const int64_t *tile_start, const void *wmax, int32_t *esc_list,
+                        unsigned long long *esc_count, double q, double m, Counters *ctr, cudaStream_t st,
+                        int *nlaunch);
 
 // ---- sort (sort.cu) ----
 // Counting sort of the slots [0, *d_count) of `src` by (tile, cell-in-tile),
@@ -74,9 +76,11 @@ cudaError_t launch_sort(const Grid &g, const Particles &src, const Particles &ds
 cudaError_t launch_yee_b(const Grid &g, void *const E[3], void *const B[3], double h, cudaStream_t st);
 cudaError_t launch_yee_e(const Grid &g, void *const E[3], void *const B[3], void *const J[3], double h,
                          cudaStream_t st);
+// Load n particles into slots [offset, offset+n); *wmax (float or double,
+// matching the precision) is raised to max |w| of the loaded weights.
 cudaError_t launch_load(const Grid &g, const Particles &p, int64_t offset, int64_t n, const double *x,
                         const double *y, const double *z, const double *ux, const double *uy, const double *uz,
-                        const double *w, const uint32_t *id, unsigned long long *bad, cudaStream_t st);
+                        const double *w, const uint32_t *id, unsigned long long *bad, void *wmax, cudaStream_t st);
 cudaError_t launch_unload(const Grid &g, const Particles &p, const int64_t *d_count, int64_t nmax, double *x,
                           double *y, double *z, double *ux, double *uy, double *uz, double *w, uint32_t *id,
                           int32_t *alive, cudaStream_t st);

@@ -33,7 +33,7 @@ constexpr int32_t kEscFlag = 0x40000000;  // set in `cell` while a particle wait
 template <int DIM, int ORDER> struct Geo {
   static constexpr int TX = DIM == 3 ? 8 : 16;
   static constexpr int TY = DIM == 3 ? 8 : 16;
-  static constexpr int TZ = DIM == 3 ? 8 : 1;
+  static constexpr int TZ = DIM == 3 ? 4 : 1;
   static constexpr int D = 1;  // drift allowance (cells)
   static constexpr int LOE = 1, HIE = ORDER == 2 ? 2 : 1;  // gather reach below / above the cell
   static constexpr int LOJ = ORDER == 2 ? 2 : 1, HIJ = ORDER == 2 ? 3 : 2;  // deposit reach
@@ -78,6 +78,8 @@ template <class R> struct PushArgs {
   R *u[3];
   const R *w;
   const int64_t *tile_start;
+  const R *wmax;                    // max |w| of the species (device)
+  double qabs;                      // |q|
   int32_t *esc_list;                // slots deferred to k_push_escaped
   unsigned long long *esc_count;
   R qmh;      // q dt / (2 m)
@@ -112,18 +114,62 @@ __device__ __forceinline__ R gsum(const R *__restrict__ F, const R *wx, const R 
   return acc;
 }
 
-// Esirkepov deposit into a J window with compile-time strides.
-// base: window index of the stencil's first node; P*: scaled running sums.
-template <class R, int ORDER, int DIM, int SY, int SZ, int JN, bool SHARED>
-__device__ __forceinline__ void deposit_win(R *__restrict__ J, int base, const DepositAxis<R, ORDER> &X,
+// Shared-memory J window in fixed point.  Floating-point shared atomics are
+// compare-and-swap loops costing several shared-memory wavefronts each;
+// integer shared atomics are single native operations.  A contribution v is
+// stored as the integer X = rint(v * 2^K); FP32 runs keep X in two 32-bit
+// words (low 16 bits summed as unsigned, the rest summed signed), FP64 runs
+// in one 64-bit word.  Integer sums are exact and independent of order.  K is
+// chosen per tile from a bound on |J| at any node: every Esirkepov
+// contribution satisfies |v| <= |q w v_particle| < |q w|, so
+// |J_node| <= Q = |q| * max|w| * (particles of the tile), and K keeps Q * 2^K
+// below 2^46 (FP32: hi word and 16-bit lo sums of up to 65,536 terms fit) or
+// 2^61 (FP64).
+template <class R> struct WinAcc;
+template <> struct WinAcc<float> {
+  int *w;       // [3][2][JN]: per component lo words, then hi words
+  int jn;
+  float scale;  // 2^K
+  static constexpr int kLimitLog2 = 46;
+  __device__ __forceinline__ void add(int comp, int idx, float v) const {
+    if (v != 0.f) {
+      const long long X = __float2ll_rn(v * scale);
+      int *b = w + comp * 2 * jn + idx;
+      atomicAdd(b, (int)(X & 0xFFFF));
+      atomicAdd(b + jn, (int)(X >> 16));
+    }
+  }
+  __device__ __forceinline__ double get(int comp, int idx) const {
+    const int *b = w + comp * 2 * jn + idx;
+    return ((double)b[jn] * 65536.0 + (double)(unsigned)b[0]) / (double)scale;
+  }
+};
+template <> struct WinAcc<double> {
+  unsigned long long *w;  // [3][JN]
+  int jn;
+  double scale;
+  static constexpr int kLimitLog2 = 61;
+  __device__ __forceinline__ void add(int comp, int idx, double v) const {
+    if (v != 0.0) atomicAdd(w + comp * jn + idx, (unsigned long long)__double2ll_rn(v * scale));
+  }
+  __device__ __forceinline__ double get(int comp, int idx) const {
+    return (double)(long long)w[comp * jn + idx] / scale;
+  }
+};
+
+// Esirkepov deposit into the shared J window (compile-time strides).
+// base: window index of the stencil's first node.
+template <class R, int ORDER, int DIM, int SY, int SZ>
+__device__ __forceinline__ void deposit_win(const WinAcc<R> &acc, int base, const DepositAxis<R, ORDER> &X,
                                             const DepositAxis<R, ORDER> &Y, const DepositAxis<R, ORDER> &Z, R cx,
                                             R cy, R cz, R qwvz) {
   constexpr int NW = ORDER + 2;
-  R Px[NW - 1], Py[NW - 1], Pz[NW - 1];
+  constexpr int M = NW - 1;
+  R Px[M], Py[M], Pz[M];
   {
     R a = R(0), b = R(0), c = R(0);
 #pragma unroll
-    for (int k = 0; k < NW - 1; ++k) {
+    for (int k = 0; k < M; ++k) {
       a += X.DS[k];
       b += Y.DS[k];
       c += Z.DS[k];
@@ -132,7 +178,6 @@ __device__ __forceinline__ void deposit_win(R *__restrict__ J, int base, const D
       Pz[k] = cz * c;
     }
   }
-  R *Jx = J + base, *Jy = J + JN + base, *Jz = J + 2 * JN + base;
   if (DIM == 3) {
     // Jx(i+1/2,j,k) += Px[i] (S0y S0z + DSy S0z/2 + S0y DSz/2 + DSy DSz/3), cyclic for y, z
     R hz[NW], tz[NW], hx[NW], tx[NW];
@@ -149,7 +194,7 @@ __device__ __forceinline__ void deposit_win(R *__restrict__ J, int base, const D
       for (int b = 0; b < NW; ++b) {
         const R br = Y.S0[b] * hz[c] + Y.DS[b] * tz[c];
 #pragma unroll
-        for (int a = 0; a < NW - 1; ++a) atomicAdd(Jx + c * SZ + b * SY + a, Px[a] * br);
+        for (int a = 0; a < M; ++a) acc.add(0, base + c * SZ + b * SY + a, Px[a] * br);
       }
 #pragma unroll
     for (int c = 0; c < NW; ++c)
@@ -157,33 +202,36 @@ __device__ __forceinline__ void deposit_win(R *__restrict__ J, int base, const D
       for (int a = 0; a < NW; ++a) {
         const R br = Z.S0[c] * hx[a] + Z.DS[c] * tx[a];
 #pragma unroll
-        for (int b = 0; b < NW - 1; ++b) atomicAdd(Jy + c * SZ + b * SY + a, Py[b] * br);
+        for (int b = 0; b < M; ++b) acc.add(1, base + c * SZ + b * SY + a, Py[b] * br);
       }
 #pragma unroll
-    for (int b = 0; b < NW; ++b)
+    for (int b = 0; b < NW; ++b) {
+      const R hy = Y.S0[b] + R(0.5) * Y.DS[b];
+      const R ty = R(0.5) * Y.S0[b] + Y.DS[b] * R(1.0 / 3.0);
 #pragma unroll
       for (int a = 0; a < NW; ++a) {
-        const R br = X.S0[a] * (Y.S0[b] + R(0.5) * Y.DS[b]) + X.DS[a] * (R(0.5) * Y.S0[b] + Y.DS[b] * R(1.0 / 3.0));
+        const R br = X.S0[a] * hy + X.DS[a] * ty;
 #pragma unroll
-        for (int c = 0; c < NW - 1; ++c) atomicAdd(Jz + c * SZ + b * SY + a, Pz[c] * br);
+        for (int c = 0; c < M; ++c) acc.add(2, base + c * SZ + b * SY + a, Pz[c] * br);
       }
+    }
   } else {
     // 2D3V: Jx = Px (S0y + DSy/2), Jy = Py (S0x + DSx/2),
     //       Jz = q w vz (S0x S0y + DSx S0y/2 + S0x DSy/2 + DSx DSy/3)
 #pragma unroll
     for (int b = 0; b < NW; ++b) {
-      const R by = Y.S0[b] + R(0.5) * Y.DS[b];
+      const R hy = Y.S0[b] + R(0.5) * Y.DS[b];
       const R ty = R(0.5) * Y.S0[b] + Y.DS[b] * R(1.0 / 3.0);
 #pragma unroll
-      for (int a = 0; a < NW - 1; ++a) atomicAdd(Jx + b * SY + a, Px[a] * by);
+      for (int a = 0; a < M; ++a) acc.add(0, base + b * SY + a, Px[a] * hy);
 #pragma unroll
-      for (int a = 0; a < NW; ++a) atomicAdd(Jz + b * SY + a, qwvz * (X.S0[a] * by + X.DS[a] * ty));
+      for (int a = 0; a < NW; ++a) acc.add(2, base + b * SY + a, qwvz * (X.S0[a] * hy + X.DS[a] * ty));
     }
 #pragma unroll
     for (int a = 0; a < NW; ++a) {
-      const R bx = X.S0[a] + R(0.5) * X.DS[a];
+      const R hx = X.S0[a] + R(0.5) * X.DS[a];
 #pragma unroll
-      for (int b = 0; b < NW - 1; ++b) atomicAdd(Jy + b * SY + a, Py[b] * bx);
+      for (int b = 0; b < M; ++b) acc.add(1, base + b * SY + a, Py[b] * hx);
     }
   }
 }
@@ -224,12 +272,14 @@ __global__ void __launch_bounds__(kThreads, sizeof(R) == 4 ? 2 : 1) k_push(const
   constexpr int NS = G::NS;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   R *sF = reinterpret_cast<R *>(smem_raw);    // 6 * EN: Ex Ey Ez Bx By Bz
-  R *sJ = sF + 6 * G::EN;                     // 3 * JN: Jx Jy Jz
-  R *sOff = sJ + 3 * G::JN;                   // DIM x 256
+  // J window: 24 bytes per node (3 components x 8 bytes of fixed point)
+  unsigned char *sJraw = smem_raw + 6 * G::EN * sizeof(R);
+  R *sOff = reinterpret_cast<R *>(sJraw + 24 * G::JN);  // DIM x 256
   R *sU = sOff + DIM * kThreads;              // 3 x 256
   R *sW = sU + 3 * kThreads;                  // 256
   int32_t *sCell = reinterpret_cast<int32_t *>(sW + kThreads);  // 256
   __shared__ unsigned int s_clamp;
+  __shared__ double s_scale;
 
   const int t = blockIdx.x;
   const int64_t pb = a.tile_start[t], pe = a.tile_start[t + 1];
@@ -259,9 +309,22 @@ __global__ void __launch_bounds__(kThreads, sizeof(R) == 4 ? 2 : 1) k_push(const
       sF[(3 + c) * G::EN + q] = a.B[c][g];
     }
   }
-  for (int q = tid; q < 3 * G::JN; q += kThreads) sJ[q] = R(0);
-  if (tid == 0) s_clamp = 0;
+  for (int q = tid; q < 6 * G::JN; q += kThreads) reinterpret_cast<int *>(sJraw)[q] = 0;
+  if (tid == 0) {
+    s_clamp = 0;
+    // fixed-point scale 2^K with |q| max|w| n_tile 2^K < 2^limit
+    const double Q = a.qabs * (double)*a.wmax * (double)(pe - pb);
+    int e2 = 0;
+    if (Q > 0.0) frexp(Q, &e2);
+    int K = Q > 0.0 ? WinAcc<R>::kLimitLog2 - e2 : 100;
+    K = K > 100 ? 100 : (K < -100 ? -100 : K);
+    s_scale = ldexp(1.0, K);
+  }
   __syncthreads();
+  WinAcc<R> acc;
+  acc.w = reinterpret_cast<decltype(acc.w)>(sJraw);
+  acc.jn = G::JN;
+  acc.scale = (R)s_scale;
 
   // lane-spreading permutation of the 256 staging slots (bijective; the
   // eight warps' lanes land on 32 distinct banks)
@@ -354,8 +417,8 @@ __global__ void __launch_bounds__(kThreads, sizeof(R) == 4 ? 2 : 1) k_push(const
           constexpr int oJ = G::D + G::LOJ;
           const int jb = (l[0] + dx.rel + oJ) + (l[1] + dy.rel + oJ) * G::JX +
                          (DIM == 3 ? (l[2] + dz.rel + oJ) * G::JX * G::JY : 0);
-          deposit_win<R, ORDER, DIM, G::JX, G::JX * G::JY, G::JN, true>(
-              sJ, jb, dx, dy, dz, a.jfac[0] * wq, a.jfac[1] * wq, a.jfac[2] * wq, a.qz * wq * u[2] * ig);
+          deposit_win<R, ORDER, DIM, G::JX, G::JX * G::JY>(acc, jb, dx, dy, dz, a.jfac[0] * wq, a.jfac[1] * wq,
+                                                            a.jfac[2] * wq, a.qz * wq * u[2] * ig);
 
           // ---- new state back into the staging slot ----
           int nc = c;
@@ -403,8 +466,8 @@ __global__ void __launch_bounds__(kThreads, sizeof(R) == 4 ? 2 : 1) k_push(const
     const int64_t g = gi + (int64_t)a.n[0] * (gj + (int64_t)a.n[1] * gk);
 #pragma unroll
     for (int c = 0; c < 3; ++c) {
-      const R v = sJ[c * G::JN + q];
-      if (v != R(0)) atomicAdd(a.J[c] + g, v);
+      const double v = acc.get(c, q);
+      if (v != 0.0) atomicAdd(a.J[c] + g, (R)v);
     }
   }
   if (tid == 0 && s_clamp) atomicAdd(&a.ctr->clamped, (unsigned long long)s_clamp);
@@ -529,14 +592,16 @@ __global__ void __launch_bounds__(kThreads) k_push_escaped(const PushArgs<R> a) 
 
 template <class R, int DIM, int ORDER> constexpr size_t smem_bytes() {
   using G = Geo<DIM, ORDER>;
-  return (size_t)(6 * G::EN + 3 * G::JN + (DIM + 4) * kThreads) * sizeof(R) + kThreads * sizeof(int32_t);
+  return (size_t)(6 * G::EN + (DIM + 4) * kThreads) * sizeof(R) + 24 * (size_t)G::JN + kThreads * sizeof(int32_t);
 }
 
 template <class R, int DIM, int ORDER>
 cudaError_t launch_t(const Grid &g, void *const E[3], void *const B[3], void *const J[3], const Particles &p,
-                     const int64_t *tile_start, int32_t *esc_list, unsigned long long *esc_count, double q, double m,
-                     Counters *ctr, cudaStream_t st, int *nlaunch) {
+                     const int64_t *tile_start, const void *wmax, int32_t *esc_list, unsigned long long *esc_count,
+                     double q, double m, Counters *ctr, cudaStream_t st, int *nlaunch) {
   PushArgs<R> a;
+  a.wmax = static_cast<const R *>(wmax);
+  a.qabs = q < 0 ? -q : q;
   for (int d = 0; d < 3; ++d) {
     a.n[d] = g.n[d];
     a.E[d] = static_cast<const R *>(E[d]);
@@ -600,11 +665,12 @@ size_t push_smem_bytes(const Grid &g) {
 }
 
 cudaError_t launch_push(const Grid &g, void *const E[3], void *const B[3], void *const J[3], const Particles &p,
-                        const int64_t *tile_start, int32_t *esc_list, unsigned long long *esc_count, double q,
-                        double m, Counters *ctr, cudaStream_t st, int *nlaunch) {
+                        const int64_t *tile_start, const void *wmax, int32_t *esc_list,
+                        unsigned long long *esc_count, double q, double m, Counters *ctr, cudaStream_t st,
+                        int *nlaunch) {
   const int key = (g.prec == 1 ? 100 : 0) + g.dims * 10 + g.order;
 #define PIC_PUSH_CASE(K, R, D, O) \
-  case K: return launch_t<R, D, O>(g, E, B, J, p, tile_start, esc_list, esc_count, q, m, ctr, st, nlaunch);
+  case K: return launch_t<R, D, O>(g, E, B, J, p, tile_start, wmax, esc_list, esc_count, q, m, ctr, st, nlaunch);
   switch (key) {
     PIC_PUSH_CASE(21, float, 2, 1)
     PIC_PUSH_CASE(22, float, 2, 2)

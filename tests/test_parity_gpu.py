@@ -26,8 +26,8 @@ CASES = [
     # dims, order, grid, tile, ppc, u_th  (grids not multiples of the tile: ragged tiles)
     (2, 1, (40, 24), (16, 16), 4, 0.2),
     (2, 2, (40, 24), (16, 16), 4, 0.2),
-    (3, 1, (12, 10, 9), (8, 8, 8), 3, 0.2),
-    (3, 2, (12, 10, 9), (8, 8, 8), 3, 0.2),
+    (3, 1, (12, 10, 9), None, 3, 0.2),
+    (3, 2, (12, 10, 9), None, 3, 0.2),
 ]
 
 
