@@ -116,45 +116,56 @@ __device__ __forceinline__ R gsum(const R *__restrict__ F, const R *wx, const R 
 
 // Shared-memory J window in fixed point.  Floating-point shared atomics are
 // compare-and-swap loops costing several shared-memory wavefronts each;
-// integer shared atomics are single native operations.  A contribution v is
-// stored as the integer X = rint(v * 2^K); FP32 runs keep X in two 32-bit
-// words (low 16 bits summed as unsigned, the rest summed signed), FP64 runs
-// in one 64-bit word.  Integer sums are exact and independent of order.  K is
-// chosen per tile from a bound on |J| at any node: every Esirkepov
-// contribution satisfies |v| <= |q w v_particle| < |q w|, so
-// |J_node| <= Q = |q| * max|w| * (particles of the tile), and K keeps Q * 2^K
-// below 2^46 (FP32: hi word and 16-bit lo sums of up to 65,536 terms fit) or
-// 2^61 (FP64).
+// integer shared atomics are single native operations, and integer sums are
+// exact and independent of order.  A contribution v becomes the integer
+// X = rint(v * 2^K).  K is chosen per tile from a bound on |J| at any node:
+// every Esirkepov contribution satisfies |v| <= |q w v_particle| < |q w|, so
+// |J_node| <= Q = |q| * max|w| * (particles of the tile), and 2^K keeps
+// Q * 2^K below 2^kLimitLog2.
+//
+// FP32: X is kept as two signed 32-bit words, X = hi * 2^16 + lo with
+// |lo| <= 2^15, both found with FP32 adds only (adding 1.5 * 2^23 rounds a
+// float of magnitude below 2^22 to an integer held in its low mantissa bits),
+// because float-to-64-bit conversions run on the slow FP64 pipe.  With
+// |X| < 2^37 the hi sums cannot overflow, and the lo sums cannot overflow for
+// fewer than 65,536 contributions per node.  FP64: one 64-bit word, exact
+// modulo 2^64 with |X| < 2^61.
 template <class R> struct WinAcc;
 template <> struct WinAcc<float> {
   int *w;       // [3][2][JN]: per component lo words, then hi words
   int jn;
   float scale;  // 2^K
-  static constexpr int kLimitLog2 = 46;
+  float unit;   // 2^-K
+  static constexpr int kLimitLog2 = 37;
+  static constexpr float kMagic = 12582912.0f;  // 1.5 * 2^23
   __device__ __forceinline__ void add(int comp, int idx, float v) const {
     if (v != 0.f) {
-      const long long X = __float2ll_rn(v * scale);
+      const float x = v * scale;
+      const float yh = fmaf(x, 1.0f / 65536.0f, kMagic);  // rint(x / 2^16) + magic
+      const float hf = yh - kMagic;
+      const int hi = __float_as_int(yh) - __float_as_int(kMagic);
+      const float lf = fmaf(-hf, 65536.0f, x);            // exact, |lf| <= 2^15
+      const int lo = __float_as_int(lf + kMagic) - __float_as_int(kMagic);
       int *b = w + comp * 2 * jn + idx;
-      atomicAdd(b, (int)(X & 0xFFFF));
-      atomicAdd(b + jn, (int)(X >> 16));
+      atomicAdd(b, lo);
+      atomicAdd(b + jn, hi);
     }
   }
-  __device__ __forceinline__ double get(int comp, int idx) const {
+  __device__ __forceinline__ float get(int comp, int idx) const {
     const int *b = w + comp * 2 * jn + idx;
-    return ((double)b[jn] * 65536.0 + (double)(unsigned)b[0]) / (double)scale;
+    return fmaf((float)b[jn], 65536.0f * unit, (float)b[0] * unit);
   }
 };
 template <> struct WinAcc<double> {
   unsigned long long *w;  // [3][JN]
   int jn;
   double scale;
+  double unit;
   static constexpr int kLimitLog2 = 61;
   __device__ __forceinline__ void add(int comp, int idx, double v) const {
     if (v != 0.0) atomicAdd(w + comp * jn + idx, (unsigned long long)__double2ll_rn(v * scale));
   }
-  __device__ __forceinline__ double get(int comp, int idx) const {
-    return (double)(long long)w[comp * jn + idx] / scale;
-  }
+  __device__ __forceinline__ double get(int comp, int idx) const { return (double)(long long)w[comp * jn + idx] * unit; }
 };
 
 // Esirkepov deposit into the shared J window (compile-time strides).
@@ -325,6 +336,7 @@ __global__ void __launch_bounds__(kThreads, sizeof(R) == 4 ? 2 : 1) k_push(const
   acc.w = reinterpret_cast<decltype(acc.w)>(sJraw);
   acc.jn = G::JN;
   acc.scale = (R)s_scale;
+  acc.unit = (R)(1.0 / s_scale);
 
   // lane-spreading permutation of the 256 staging slots (bijective; the
   // eight warps' lanes land on 32 distinct banks)
@@ -466,8 +478,8 @@ __global__ void __launch_bounds__(kThreads, sizeof(R) == 4 ? 2 : 1) k_push(const
     const int64_t g = gi + (int64_t)a.n[0] * (gj + (int64_t)a.n[1] * gk);
 #pragma unroll
     for (int c = 0; c < 3; ++c) {
-      const double v = acc.get(c, q);
-      if (v != 0.0) atomicAdd(a.J[c] + g, (R)v);
+      const R v = acc.get(c, q);
+      if (v != R(0)) atomicAdd(a.J[c] + g, v);
     }
   }
   if (tid == 0 && s_clamp) atomicAdd(&a.ctr->clamped, (unsigned long long)s_clamp);
