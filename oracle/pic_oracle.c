@@ -31,7 +31,11 @@
  * Shape sums run over a generous window of nodes and every weight is taken
  * from the shape function itself, so zero weights simply drop out.
  */
+#define _USE_MATH_DEFINES
 #include <math.h>
+#ifndef M_PI
+#define M_PI 3.14159265358979323846
+#endif
 #include <stdint.h>
 #include <stdlib.h>
 #include <string.h>
@@ -82,6 +86,46 @@ typedef struct {
   int pol; /* 1: E along y, 2: E along z */
   double *mur_prev; /* previous boundary samples kept by the Mur condition */
 } orc_sim;
+
+/* ------------------------------------------------------------------ */
+/* Boundary readings (the paper names boundary conditions but gives   */
+/* none, §2).  With absorbing x walls the field domain is the nodes    */
+/* i = 0 .. nx-1; tangential E (Ey, Ez) on the wall nodes i = 0 and    */
+/* nx-1 follows the first-order Mur condition applied to the field     */
+/* minus the incoming laser wave; By, Bz and Ex at i = nx-1 (a half    */
+/* cell beyond the last node) are never updated.  A particle whose new */
+/* position leaves [3, nx-4) cells is removed after its move has       */
+/* deposited its current, so no stencil reaches past the arrays.       */
+/* ------------------------------------------------------------------ */
+#define ORC_WALL_LO 3.0
+#define ORC_WALL_HI_MARGIN 4.0
+
+void oracle_set_boundary(void *h, int absorb_x) { ((orc_sim *)h)->absorb_x = absorb_x; }
+
+/* Laser through x = 0: field a0 exp(-r^2/waist^2) env(t - x) sin(t - x)
+ * along y (pol 1) or z (pol 2), env(tau) = sin^2(pi tau / duration) on
+ * [0, duration] (carrier frequency 1: times are in 1/omega_laser). */
+void oracle_set_laser(void *h, int on, double a0, double waist, double duration, double yc, double zc, int pol) {
+  orc_sim *s = (orc_sim *)h;
+  s->laser_on = on;
+  s->a0 = a0;
+  s->waist = waist;
+  s->duration = duration;
+  s->yc = yc;
+  s->zc = zc;
+  s->pol = pol;
+}
+
+/* Incoming laser field at (x, y, z, t) for the polarised component. */
+double oracle_laser_field(void *h, double x, double y, double z, double t) {
+  orc_sim *s = (orc_sim *)h;
+  if (!s->laser_on) return 0.0;
+  double tau = t - x;
+  if (tau <= 0.0 || tau >= s->duration) return 0.0;
+  double env = sin(M_PI * tau / s->duration);
+  double r2 = (y - s->yc) * (y - s->yc) + (s->dims == 3 ? (z - s->zc) * (z - s->zc) : 0.0);
+  return s->a0 * exp(-r2 / (s->waist * s->waist)) * env * env * sin(tau);
+}
 
 /* ------------------------------------------------------------------ */
 /* Shape functions (§2: g compact and positive).                       */
@@ -402,6 +446,7 @@ static void yee_b(orc_sim *s, double h) {
         double cy = (Ex[idx(s, i, j, k + 1)] - Ex[c]) / dz - (Ez[idx(s, i + 1, j, k)] - Ez[c]) / dx;
         double cz = (Ey[idx(s, i + 1, j, k)] - Ey[c]) / dx - (Ex[idx(s, i, j + 1, k)] - Ex[c]) / dy;
         Bx[c] -= h * cx;
+        if (s->absorb_x && i == s->n[0] - 1) continue; /* By, Bz beyond the last node */
         By[c] -= h * cy;
         Bz[c] -= h * cz;
       }
@@ -420,19 +465,75 @@ static void yee_e(orc_sim *s, double h) {
         double cx = (Bz[c] - Bz[idx(s, i, j - 1, k)]) / dy - (By[c] - By[idx(s, i, j, k - 1)]) / dz;
         double cy = (Bx[c] - Bx[idx(s, i, j, k - 1)]) / dz - (Bz[c] - Bz[idx(s, i - 1, j, k)]) / dx;
         double cz = (By[c] - By[idx(s, i - 1, j, k)]) / dx - (Bx[c] - Bx[idx(s, i, j - 1, k)]) / dy;
+        if (s->absorb_x && i == s->n[0] - 1) continue; /* wall node: Mur; Ex beyond the last node */
         Ex[c] += h * (cx - Jx[c]);
+        if (s->absorb_x && i == 0) continue; /* wall node: Mur */
         Ey[c] += h * (cy - Jy[c]);
         Ez[c] += h * (cz - Jz[c]);
       }
 }
 
+/* First-order Mur condition on the tangential E of both x walls, applied to
+ * the scattered field E - E_laser:
+ *   E(0)^{n+1} = E(1)^n + k (E(1)^{n+1} - E(0)^n),  k = (dt - dx)/(dt + dx)
+ * and the mirror image at the right wall.  `old` holds E^n of the nodes
+ * 0, 1, nx-2, nx-1 (components y, z) saved before the E update. */
+static double laser_comp(orc_sim *s, int comp, long i, long j, long k, double t) {
+  /* Ey at (i, j+1/2, k), Ez at (i, j, k+1/2) */
+  if (!s->laser_on) return 0.0;
+  if ((comp == 0 && s->pol != 1) || (comp == 1 && s->pol != 2)) return 0.0;
+  double x = i * s->d[0];
+  double y = (j + (comp == 0 ? 0.5 : 0.0)) * s->d[1];
+  double z = (k + (comp == 1 ? 0.5 : 0.0)) * s->d[2];
+  return oracle_laser_field(s, x, y, z, t);
+}
+
+static void mur_save(orc_sim *s) {
+  long nyz = (long)s->n[1] * s->n[2], nx = s->n[0];
+  long nodes[4] = {0, 1, nx - 2, nx - 1};
+  for (int c = 0; c < 2; ++c)
+    for (int q = 0; q < 4; ++q)
+      for (long jk = 0; jk < nyz; ++jk) {
+        long j = jk % s->n[1], k = jk / s->n[1];
+        s->mur_prev[((c * 4 + q) * nyz) + jk] = s->f[ORC_EY + c][idx(s, nodes[q], j, k)];
+      }
+}
+
+static void mur_apply(orc_sim *s, double t_old, double t_new) {
+  long nyz = (long)s->n[1] * s->n[2], nx = s->n[0];
+  double kc = (s->dt - s->d[0]) / (s->dt + s->d[0]);
+  for (int c = 0; c < 2; ++c)
+    for (long jk = 0; jk < nyz; ++jk) {
+      long j = jk % s->n[1], k = jk / s->n[1];
+      double *E = s->f[ORC_EY + c];
+      const double *o = s->mur_prev + (long)c * 4 * nyz;
+      /* left wall (node 0, neighbour node 1): scattered field leaves towards -x */
+      double s0_old = o[0 * nyz + jk] - laser_comp(s, c, 0, j, k, t_old);
+      double s1_old = o[1 * nyz + jk] - laser_comp(s, c, 1, j, k, t_old);
+      double s1_new = E[idx(s, 1, j, k)] - laser_comp(s, c, 1, j, k, t_new);
+      E[idx(s, 0, j, k)] = laser_comp(s, c, 0, j, k, t_new) + s1_old + kc * (s1_new - s0_old);
+      /* right wall (node nx-1, neighbour nx-2): no laser term there */
+      double r0_old = o[3 * nyz + jk], r1_old = o[2 * nyz + jk];
+      double r1_new = E[idx(s, nx - 2, j, k)];
+      E[idx(s, nx - 1, j, k)] = r1_old + kc * (r1_new - r0_old);
+    }
+}
+
 /* Field-only update, exposed for the Yee dispersion and Courant pins. */
+static void field_cycle(orc_sim *s) {
+  double t_old = s->step * s->dt, t_new = (s->step + 1) * s->dt;
+  yee_b(s, 0.5 * s->dt);
+  if (s->absorb_x) mur_save(s);
+  yee_e(s, s->dt);
+  if (s->absorb_x) mur_apply(s, t_old, t_new);
+  yee_b(s, 0.5 * s->dt);
+}
+
 void oracle_field_step(void *h, int nsteps) {
   orc_sim *s = (orc_sim *)h;
   for (int t = 0; t < nsteps; ++t) {
-    yee_b(s, 0.5 * s->dt);
-    yee_e(s, s->dt);
-    yee_b(s, 0.5 * s->dt);
+    field_cycle(s);
+    s->step++;
   }
 }
 
@@ -465,6 +566,10 @@ void oracle_step(void *h, int nsteps) {
         double X0[3] = {r0[0] / s->d[0], r0[1] / s->d[1], r0[2] / s->d[2]};
         double X1[3] = {r1[0] / s->d[0], r1[1] / s->d[1], r1[2] / s->d[2]};
         esirkepov(s, sp->q, p->w, X0, X1, v[2]);
+        if (s->absorb_x && (X1[0] < ORC_WALL_LO || X1[0] >= s->n[0] - ORC_WALL_HI_MARGIN)) {
+          p->alive = 0; /* removed at the wall after depositing its last move */
+          continue;
+        }
         /* periodic wrap of the stored position */
         for (int a = 0; a < s->dims; ++a) {
           if (r1[a] >= L[a]) r1[a] -= L[a];
@@ -475,9 +580,7 @@ void oracle_step(void *h, int nsteps) {
         p->z = r1[2];
       }
     }
-    yee_b(s, 0.5 * s->dt);
-    yee_e(s, s->dt);
-    yee_b(s, 0.5 * s->dt);
+    field_cycle(s);
     s->step++;
   }
 }

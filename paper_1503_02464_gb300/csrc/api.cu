@@ -34,7 +34,6 @@ struct Species {
   int64_t h_count = 0;          // host mirror, valid while !stepped_since_count
   int32_t *rank = nullptr;
   int64_t *tile_start = nullptr;
-  void *wmax = nullptr;         // max |w| (float or double), raised by every load
   bool need_sort = true;
 };
 
@@ -57,6 +56,8 @@ struct pic_handle {
   int64_t rho_prev_step = -2;
   int32_t *keys = nullptr;
   int64_t *tile_tmp = nullptr;
+  double *mur = nullptr;  // Mur wall planes (8 * n1 * n2)
+  pic::Laser laser{};
   unsigned long long *esc_count = nullptr;
   Counters *ctr = nullptr;
   unsigned long long *bad = nullptr;
@@ -212,9 +213,20 @@ int pic_create(const pic_config *cfg, pic_handle **out) {
       if (d != 0) return fail(nullptr, PIC_EINVAL, "only x walls may be absorbing");
     }
   }
-  if (c.bc_lo[0] == PIC_BC_ABSORBING || c.bc_hi[0] == PIC_BC_ABSORBING)
-    return fail(nullptr, PIC_EINVAL, "absorbing walls are not available in this build");
-  if (c.laser.enabled) return fail(nullptr, PIC_EINVAL, "laser injection is not available in this build");
+  for (int d = 0; d < 3; ++d)
+    if ((c.bc_lo[d] != PIC_BC_PERIODIC && c.bc_lo[d] != PIC_BC_ABSORBING) ||
+        (c.bc_hi[d] != PIC_BC_PERIODIC && c.bc_hi[d] != PIC_BC_ABSORBING))
+      return fail(nullptr, PIC_EINVAL, "unknown boundary kind");
+  const bool absorb = c.bc_lo[0] == PIC_BC_ABSORBING || c.bc_hi[0] == PIC_BC_ABSORBING;
+  if (absorb && (c.bc_lo[0] != PIC_BC_ABSORBING || c.bc_hi[0] != PIC_BC_ABSORBING))
+    return fail(nullptr, PIC_EINVAL, "absorbing x walls come in pairs (bc_lo[0] = bc_hi[0])");
+  if (absorb && c.n[0] < 16) return fail(nullptr, PIC_EINVAL, "absorbing x walls need n[0] >= 16");
+  if (c.laser.enabled) {
+    if (!absorb) return fail(nullptr, PIC_EINVAL, "the laser enters through an absorbing x = 0 wall");
+    if (!(c.laser.duration > 0) || !(c.laser.waist > 0) || (c.laser.polarization != 1 && c.laser.polarization != 2) ||
+        (c.dims == 2 && c.laser.polarization == 2 && false))
+      return fail(nullptr, PIC_EINVAL, "bad laser parameters");
+  }
   if (c.dims == 2 && c.n[2] != 1 && c.n[2] != 0) return fail(nullptr, PIC_EINVAL, "2D needs n[2] = 1");
   if (!(c.dt > 0)) return fail(nullptr, PIC_EINVAL, "dt must be positive");
   double s = 0;
@@ -260,6 +272,13 @@ int pic_create(const pic_config *cfg, pic_handle **out) {
     g.ntiles *= g.ntile[d];
   }
   h->rsize = g.prec == PIC_FP64 ? sizeof(double) : sizeof(float);
+  h->laser.enabled = c.laser.enabled;
+  h->laser.a0 = c.laser.a0;
+  h->laser.waist = c.laser.waist;
+  h->laser.duration = c.laser.duration;
+  h->laser.yc = c.laser.y_center;
+  h->laser.zc = c.laser.z_center;
+  h->laser.pol = c.laser.polarization;
   h->st = static_cast<cudaStream_t>(c.stream);
 
   int dev = 0;
@@ -288,7 +307,8 @@ int pic_create(const pic_config *cfg, pic_handle **out) {
        cudaMalloc(&h->keys, (size_t)nkeys * sizeof(int32_t)) == cudaSuccess &&
        cudaMalloc(&h->tile_tmp, (size_t)(g.ntiles + 1) * sizeof(int64_t)) == cudaSuccess &&
        cudaMalloc(&h->ctr, sizeof(Counters)) == cudaSuccess && cudaMalloc(&h->bad, sizeof(unsigned long long)) == cudaSuccess &&
-       cudaMalloc(&h->esc_count, sizeof(unsigned long long)) == cudaSuccess;
+       cudaMalloc(&h->esc_count, sizeof(unsigned long long)) == cudaSuccess &&
+       cudaMalloc(&h->mur, 8 * sizeof(double) * (size_t)g.n[1] * g.n[2]) == cudaSuccess;
   if (!ok) {
     pic_destroy(h);
     return fail(nullptr, PIC_ENOMEM, "device allocation failed in pic_create");
@@ -327,6 +347,7 @@ int pic_destroy(pic_handle *h) {
   cudaFree(h->ctr);
   cudaFree(h->bad);
   cudaFree(h->esc_count);
+  cudaFree(h->mur);
   for (int i = 0; i < h->nsp; ++i) {
     Species &s = h->sp[i];
     free_particles(s.buf[0]);
@@ -334,7 +355,6 @@ int pic_destroy(pic_handle *h) {
     cudaFree(s.d_count);
     cudaFree(s.rank);
     cudaFree(s.tile_start);
-    cudaFree(s.wmax);
   }
   for (auto &t : h->timers) {
     cudaEventDestroy(t.a);
@@ -363,21 +383,18 @@ int pic_add_species(pic_handle *h, double q, double m, int64_t capacity, int *sp
   if (e == cudaSuccess) e = cudaMalloc(&s.d_count, sizeof(int64_t));
   if (e == cudaSuccess) e = cudaMalloc(&s.rank, (size_t)(s.slots > 0 ? s.slots : 1) * sizeof(int32_t));
   if (e == cudaSuccess) e = cudaMalloc(&s.tile_start, (size_t)(h->g.ntiles + 1) * sizeof(int64_t));
-  if (e == cudaSuccess) e = cudaMalloc(&s.wmax, sizeof(double));
   if (e != cudaSuccess) {
     free_particles(s.buf[0]);
     free_particles(s.buf[1]);
     cudaFree(s.d_count);
     cudaFree(s.rank);
     cudaFree(s.tile_start);
-    cudaFree(s.wmax);
     s = Species{};
     cudaGetLastError();
     return fail(h, PIC_ENOMEM, "device allocation failed in pic_add_species");
   }
   cudaMemsetAsync(s.d_count, 0, sizeof(int64_t), h->st);
   cudaMemsetAsync(s.tile_start, 0, (size_t)(h->g.ntiles + 1) * sizeof(int64_t), h->st);
-  cudaMemsetAsync(s.wmax, 0, sizeof(double), h->st);
   *species = h->nsp++;
   return PIC_OK;
 }
@@ -426,7 +443,7 @@ int pic_load_particles(pic_handle *h, int species, int64_t n, const double *x, c
   CK(h, cudaMemsetAsync(h->bad, 0, sizeof(unsigned long long), h->st), "memset");
   CK(h,
      pic::launch_load(h->g, s.buf[s.cur], cur, n, dsrc[0], dsrc[1], dsrc[2], dsrc[3], dsrc[4], dsrc[5], dsrc[6], did,
-                      h->bad, s.wmax, h->st),
+                      h->bad, h->st),
      "load kernel");
   h->launches++;
   const int64_t nn = cur + n;
@@ -478,8 +495,8 @@ int pic_step(pic_handle *h, int nsteps) {
       Timed tm(h, pic::KC_PUSH);
       int nl = 0;
       CK(h,
-         pic::launch_push(h->g, h->E, h->B, h->J, s.buf[s.cur], s.tile_start, s.wmax, s.rank, h->esc_count, s.q,
-                          s.m, h->ctr, h->st, &nl),
+         pic::launch_push(h->g, h->E, h->B, h->J, s.buf[s.cur], s.tile_start, s.rank, h->esc_count, s.q, s.m,
+                          h->ctr, h->st, &nl),
          "push");
       h->launches += nl;
     }
@@ -487,9 +504,21 @@ int pic_step(pic_handle *h, int nsteps) {
       Timed tm(h, pic::KC_YEE_B);
       CK(h, pic::launch_yee_b(h->g, h->E, h->B, 0.5 * h->g.dt, h->st), "yee B");
     }
+    const bool walls = h->g.absorb_lo || h->g.absorb_hi;
+    if (walls) {
+      Timed tm(h, pic::KC_BOUNDARY);
+      CK(h, pic::launch_mur_save(h->g, h->E, h->mur, h->st), "mur save");
+      h->launches++;
+    }
     {
       Timed tm(h, pic::KC_YEE_E);
       CK(h, pic::launch_yee_e(h->g, h->E, h->B, h->J, h->g.dt, h->st), "yee E");
+    }
+    if (walls) {
+      Timed tm(h, pic::KC_BOUNDARY);
+      CK(h, pic::launch_mur_apply(h->g, h->E, h->mur, h->laser, h->step * h->g.dt, (h->step + 1) * h->g.dt, h->st),
+         "mur apply");
+      h->launches++;
     }
     {
       Timed tm(h, pic::KC_YEE_B);

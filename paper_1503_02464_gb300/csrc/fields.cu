@@ -21,6 +21,7 @@ int grid_blocks(int64_t n, int per_block) {
 
 template <class R> struct YeeArgs {
   int n[3];
+  int absorb;  // x walls absorbing: wall nodes are left to the Mur kernels
   R rdx[3];  // 1/dx_a
   R h;       // time step of this update
   R *E[3];
@@ -51,6 +52,7 @@ __global__ void __launch_bounds__(256) k_yee_b(YeeArgs<R> a) {
       cy += (a.E[0][czp] - ex) * a.rdx[2];
     }
     a.B[0][c] -= a.h * cx;
+    if (a.absorb && i == n0 - 1) continue;  // By, Bz half a cell beyond the last node
     a.B[1][c] -= a.h * cy;
     a.B[2][c] -= a.h * cz;
   }
@@ -78,15 +80,74 @@ __global__ void __launch_bounds__(256) k_yee_e(YeeArgs<R> a) {
       cx -= (by - a.B[1][czm]) * a.rdx[2];
       cy += (bx - a.B[0][czm]) * a.rdx[2];
     }
+    if (a.absorb && i == n0 - 1) continue;  // wall node (Mur) and Ex beyond the last node
     a.E[0][c] += a.h * (cx - a.J[0][c]);
+    if (a.absorb && i == 0) continue;       // wall node (Mur)
     a.E[1][c] += a.h * (cy - a.J[1][c]);
     a.E[2][c] += a.h * (cz - a.J[2][c]);
+  }
+}
+
+// Incoming laser field (polarised component) at (x, y, z, t):
+// a0 exp(-r^2/waist^2) sin^2(pi tau/duration) sin(tau), tau = t - x, on
+// 0 < tau < duration (carrier frequency 1).
+__device__ double laser_at(const Laser &L, int dims, double x, double y, double z, double t) {
+  const double tau = t - x;
+  if (tau <= 0.0 || tau >= L.duration) return 0.0;
+  const double env = sin(3.14159265358979323846 * tau / L.duration);
+  double r2 = (y - L.yc) * (y - L.yc);
+  if (dims == 3) r2 += (z - L.zc) * (z - L.zc);
+  return L.a0 * exp(-r2 / (L.waist * L.waist)) * env * env * sin(tau);
+}
+
+template <class R>
+__global__ void k_mur_save(int n0, int n1, int n2, const R *Ey, const R *Ez, double *buf) {
+  const int64_t nyz = (int64_t)n1 * n2;
+  const int nodes[4] = {0, 1, n0 - 2, n0 - 1};
+  for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < 8 * nyz; q += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t jk = q % nyz;
+    const int cq = (int)(q / nyz);  // component * 4 + node slot
+    const R *E = cq < 4 ? Ey : Ez;
+    buf[q] = (double)E[nodes[cq & 3] + (int64_t)n0 * jk];
+  }
+}
+
+// E(0)^{n+1} = L(0)^{n+1} + S(1)^n + k (S(1)^{n+1} - S(0)^n), S = E - L the
+// scattered field, k = (dt - dx)/(dt + dx); the same without L at x = n0-1.
+template <class R>
+__global__ void k_mur_apply(int dims, int n0, int n1, int n2, double dx, double dy, double dz, double dt, R *Ey,
+                            R *Ez, const double *buf, Laser las, double t_old, double t_new) {
+  const int64_t nyz = (int64_t)n1 * n2;
+  const double kc = (dt - dx) / (dt + dx);
+  for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < 2 * nyz; q += (int64_t)gridDim.x * blockDim.x) {
+    const int c = (int)(q / nyz);  // 0: Ey, 1: Ez
+    const int64_t jk = q % nyz;
+    const int j = (int)(jk % n1), k = (int)(jk / n1);
+    R *E = c == 0 ? Ey : Ez;
+    const double *o = buf + (int64_t)c * 4 * nyz;
+    const bool lit = las.enabled && las.pol == c + 1;
+    // Ey sits at (i, j+1/2, k), Ez at (i, j, k+1/2)
+    const double y = (j + (c == 0 ? 0.5 : 0.0)) * dy;
+    const double z = (k + (c == 1 ? 0.5 : 0.0)) * dz;
+    const double l0o = lit ? laser_at(las, dims, 0.0, y, z, t_old) : 0.0;
+    const double l1o = lit ? laser_at(las, dims, dx, y, z, t_old) : 0.0;
+    const double l0n = lit ? laser_at(las, dims, 0.0, y, z, t_new) : 0.0;
+    const double l1n = lit ? laser_at(las, dims, dx, y, z, t_new) : 0.0;
+    const int64_t row = (int64_t)n0 * jk;
+    const double s0o = o[0 * nyz + jk] - l0o;
+    const double s1o = o[1 * nyz + jk] - l1o;
+    const double s1n = (double)E[row + 1] - l1n;
+    E[row] = (R)(l0n + s1o + kc * (s1n - s0o));
+    const double r1o = o[2 * nyz + jk], r0o = o[3 * nyz + jk];
+    const double r1n = (double)E[row + n0 - 2];
+    E[row + n0 - 1] = (R)(r1o + kc * (r1n - r0o));
   }
 }
 
 template <class R>
 YeeArgs<R> yee_args(const Grid &g, void *const E[3], void *const B[3], void *const J[3], double h) {
   YeeArgs<R> a;
+  a.absorb = g.absorb_lo || g.absorb_hi;
   for (int d = 0; d < 3; ++d) {
     a.n[d] = g.n[d];
     a.rdx[d] = (R)(1.0 / g.dx[d]);
@@ -104,7 +165,7 @@ __global__ void k_load(int dims, int n0, int n1, int n2, double rdx0, double rdx
                        int64_t offset, int64_t n, const double *__restrict__ x, const double *__restrict__ y,
                        const double *__restrict__ z, const double *__restrict__ ux, const double *__restrict__ uy,
                        const double *__restrict__ uz, const double *__restrict__ w, const uint32_t *__restrict__ id,
-                       unsigned long long *bad, R *wmax) {
+                       unsigned long long *bad) {
   for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < n; q += (int64_t)gridDim.x * blockDim.x) {
     const double pos[3] = {x[q] * rdx0, y[q] * rdx1, dims == 3 ? z[q] * rdx2 : 0.0};
     const int nn[3] = {n0, n1, n2};
@@ -120,7 +181,7 @@ __global__ void k_load(int dims, int n0, int n1, int n2, double rdx0, double rdx
         fr = R(0);
         i += 1;
       }
-      if (d == 0 && absorb && (i < 0 || i >= nn[0])) ok = false;
+      if (d == 0 && absorb && (pos[0] < kWallLo || pos[0] >= nn[0] - kWallHiMargin)) ok = false;
       i %= nn[d];
       if (i < 0) i += nn[d];
       ci[d] = (int)i;
@@ -141,12 +202,6 @@ __global__ void k_load(int dims, int n0, int n1, int n2, double rdx0, double rdx
     static_cast<R *>(p.u[2])[s] = (R)uz[q];
     static_cast<R *>(p.w)[s] = (R)w[q];
     p.id[s] = id ? id[q] : (uint32_t)q;
-    // max |w| through the order-preserving bit pattern of a non-negative value
-    const R aw = fabs((R)w[q]);
-    if (sizeof(R) == 4)
-      atomicMax(reinterpret_cast<unsigned int *>(wmax), __float_as_uint((float)aw));
-    else
-      atomicMax(reinterpret_cast<unsigned long long *>(wmax), (unsigned long long)__double_as_longlong((double)aw));
   }
 }
 
@@ -323,20 +378,43 @@ cudaError_t launch_yee_e(const Grid &g, void *const E[3], void *const B[3], void
   return cudaGetLastError();
 }
 
+cudaError_t launch_mur_save(const Grid &g, void *const E[3], double *buf, cudaStream_t st) {
+  const int nb = grid_blocks(8LL * g.n[1] * g.n[2], 256);
+  if (g.prec == 1)
+    k_mur_save<double><<<nb, 256, 0, st>>>(g.n[0], g.n[1], g.n[2], static_cast<const double *>(E[1]),
+                                           static_cast<const double *>(E[2]), buf);
+  else
+    k_mur_save<float><<<nb, 256, 0, st>>>(g.n[0], g.n[1], g.n[2], static_cast<const float *>(E[1]),
+                                          static_cast<const float *>(E[2]), buf);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_mur_apply(const Grid &g, void *const E[3], const double *buf, const Laser &las, double t_old,
+                             double t_new, cudaStream_t st) {
+  const int nb = grid_blocks(2LL * g.n[1] * g.n[2], 256);
+  if (g.prec == 1)
+    k_mur_apply<double><<<nb, 256, 0, st>>>(g.dims, g.n[0], g.n[1], g.n[2], g.dx[0], g.dx[1], g.dx[2], g.dt,
+                                            static_cast<double *>(E[1]), static_cast<double *>(E[2]), buf, las,
+                                            t_old, t_new);
+  else
+    k_mur_apply<float><<<nb, 256, 0, st>>>(g.dims, g.n[0], g.n[1], g.n[2], g.dx[0], g.dx[1], g.dx[2], g.dt,
+                                           static_cast<float *>(E[1]), static_cast<float *>(E[2]), buf, las, t_old,
+                                           t_new);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_load(const Grid &g, const Particles &p, int64_t offset, int64_t n, const double *x,
                         const double *y, const double *z, const double *ux, const double *uy, const double *uz,
-                        const double *w, const uint32_t *id, unsigned long long *bad, void *wmax, cudaStream_t st) {
+                        const double *w, const uint32_t *id, unsigned long long *bad, cudaStream_t st) {
   if (n <= 0) return cudaSuccess;
   const int nb = grid_blocks(n, 256);
   const int absorb = g.absorb_lo || g.absorb_hi;
   if (g.prec == 1)
     k_load<double><<<nb, 256, 0, st>>>(g.dims, g.n[0], g.n[1], g.n[2], 1.0 / g.dx[0], 1.0 / g.dx[1], 1.0 / g.dx[2],
-                                       absorb, p, offset, n, x, y, z, ux, uy, uz, w, id, bad,
-                                       static_cast<double *>(wmax));
+                                       absorb, p, offset, n, x, y, z, ux, uy, uz, w, id, bad);
   else
     k_load<float><<<nb, 256, 0, st>>>(g.dims, g.n[0], g.n[1], g.n[2], 1.0 / g.dx[0], 1.0 / g.dx[1], 1.0 / g.dx[2],
-                                      absorb, p, offset, n, x, y, z, ux, uy, uz, w, id, bad,
-                                      static_cast<float *>(wmax));
+                                      absorb, p, offset, n, x, y, z, ux, uy, uz, w, id, bad);
   return cudaGetLastError();
 }
 

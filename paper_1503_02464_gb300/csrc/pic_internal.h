@@ -25,6 +25,18 @@ struct Grid {
   int absorb_lo, absorb_hi;  // x walls absorbing
 };
 
+// Laser entering through the x = 0 wall (copied from pic_config).
+struct Laser {
+  int enabled;
+  double a0, waist, duration, yc, zc;
+  int pol;  // 1: E along y, 2: E along z
+};
+
+// Particles whose new position leaves [kWallLo, n0 - kWallHiMargin) cells in
+// x are removed at absorbing walls (after depositing their move).
+constexpr double kWallLo = 3.0;
+constexpr double kWallHiMargin = 4.0;
+
 // One buffer of a species' structure-of-arrays particle storage.  Real
 // arrays are float (FP32 path) or double (FP64 path).
 struct Particles {
@@ -55,13 +67,11 @@ enum KernelClass { KC_SORT = 0, KC_ZEROJ = 1, KC_PUSH = 2, KC_YEE_B = 3, KC_YEE_
 // drift allowance is one cell.
 void push_tile_shape(int dims, int tile[3]);
 size_t push_smem_bytes(const Grid &g);
-// Tile kernel + escape kernel.  wmax: device pointer to max |w| of the
-// species (float or double).  esc_list (one int per slot) and esc_count are
-// scratch for particles deferred to the escape kernel.
+// Tile kernel + escape kernel.  esc_list (one int per slot) and esc_count
+// are scratch for particles deferred to the escape kernel.
 cudaError_t launch_push(const Grid &g, void *const E[3], void *const B[3], void *const J[3], const Particles &p,
-                        const int64_t *tile_start, const void *wmax, int32_t *esc_list,
-                        unsigned long long *esc_count, double q, double m, Counters *ctr, cudaStream_t st,
-                        int *nlaunch);
+                        const int64_t *tile_start, int32_t *esc_list, unsigned long long *esc_count, double q,
+                        double m, Counters *ctr, cudaStream_t st, int *nlaunch);
 
 // ---- sort (sort.cu) ----
 // Counting sort of the slots [0, *d_count) of `src` by (tile, cell-in-tile),
@@ -76,11 +86,16 @@ cudaError_t launch_sort(const Grid &g, const Particles &src, const Particles &ds
 cudaError_t launch_yee_b(const Grid &g, void *const E[3], void *const B[3], double h, cudaStream_t st);
 cudaError_t launch_yee_e(const Grid &g, void *const E[3], void *const B[3], void *const J[3], double h,
                          cudaStream_t st);
-// Load n particles into slots [offset, offset+n); *wmax (float or double,
-// matching the precision) is raised to max |w| of the loaded weights.
+// First-order Mur walls: save E^n (y, z) of the nodes 0, 1, n0-2, n0-1 into
+// `buf` (8 * n1 * n2 values) before the E update; apply afterwards, with the
+// incoming laser wave at x = 0 (times t_old = n dt, t_new = (n+1) dt).
+cudaError_t launch_mur_save(const Grid &g, void *const E[3], double *buf, cudaStream_t st);
+cudaError_t launch_mur_apply(const Grid &g, void *const E[3], const double *buf, const Laser &las, double t_old,
+                             double t_new, cudaStream_t st);
+// Load n particles into slots [offset, offset+n).
 cudaError_t launch_load(const Grid &g, const Particles &p, int64_t offset, int64_t n, const double *x,
                         const double *y, const double *z, const double *ux, const double *uy, const double *uz,
-                        const double *w, const uint32_t *id, unsigned long long *bad, void *wmax, cudaStream_t st);
+                        const double *w, const uint32_t *id, unsigned long long *bad, cudaStream_t st);
 cudaError_t launch_unload(const Grid &g, const Particles &p, const int64_t *d_count, int64_t nmax, double *x,
                           double *y, double *z, double *ux, double *uy, double *uz, double *w, uint32_t *id,
                           int32_t *alive, cudaStream_t st);

@@ -27,6 +27,13 @@ namespace pic {
 namespace {
 
 constexpr int kThreads = 256;
+
+// i mod n for i within a few periods of [0, n) (window coordinates)
+__device__ __forceinline__ int wrap_near(int i, int n) {
+  while (i < 0) i += n;
+  while (i >= n) i -= n;
+  return i;
+}
 constexpr int32_t kEscFlag = 0x40000000;  // set in `cell` while a particle waits for the escape kernel
 
 // Compile-time tile and window geometry.
@@ -78,7 +85,6 @@ template <class R> struct PushArgs {
   R *u[3];
   const R *w;
   const int64_t *tile_start;
-  const R *wmax;                    // max |w| of the species (device)
   double qabs;                      // |q|
   int32_t *esc_list;                // slots deferred to k_push_escaped
   unsigned long long *esc_count;
@@ -86,8 +92,17 @@ template <class R> struct PushArgs {
   R dtdx[3];  // dt / dx_a
   R jfac[3];  // -q dx_a / dt  (Esirkepov running-sum scale, times w)
   R qz;       // q            (2D3V: Jz = q w vz S)
+  int absorb;  // absorbing x walls: remove particles leaving [kWallLo, n0 - kWallHiMargin)
   Counters *ctr;
 };
+
+// True when a particle at cell index i0 with offset f has left the region
+// allowed between absorbing x walls.
+template <class R> __device__ __forceinline__ bool outside_walls(int absorb, int i0, R f, int n0) {
+  if (!absorb) return false;
+  const R X = (R)i0 + f;
+  return X < (R)kWallLo || X >= (R)(n0 - kWallHiMargin);
+}
 
 template <class R> __device__ __forceinline__ R inv_sqrt(R x);
 template <> __device__ __forceinline__ float inv_sqrt<float>(float x) { return rsqrtf(x); }
@@ -114,22 +129,22 @@ __device__ __forceinline__ R gsum(const R *__restrict__ F, const R *wx, const R 
   return acc;
 }
 
-// Shared-memory J window in fixed point.  Floating-point shared atomics are
-// compare-and-swap loops costing several shared-memory wavefronts each;
-// integer shared atomics are single native operations, and integer sums are
-// exact and independent of order.  A contribution v becomes the integer
-// X = rint(v * 2^K).  K is chosen per tile from a bound on |J| at any node:
-// every Esirkepov contribution satisfies |v| <= |q w v_particle| < |q w|, so
-// |J_node| <= Q = |q| * max|w| * (particles of the tile), and 2^K keeps
-// Q * 2^K below 2^kLimitLog2.
-//
-// FP32: X is kept as two signed 32-bit words, X = hi * 2^16 + lo with
-// |lo| <= 2^15, both found with FP32 adds only (adding 1.5 * 2^23 rounds a
-// float of magnitude below 2^22 to an integer held in its low mantissa bits),
-// because float-to-64-bit conversions run on the slow FP64 pipe.  With
+// Shared-memory J window.  FP32 runs accumulate in fixed point: FP32 shared
+// atomics are compare-and-swap loops costing several shared-memory
+// wavefronts each, integer shared atomics are single native operations, and
+// integer sums are exact and independent of order.  A contribution v becomes
+// the integer X = rint(v * 2^K), K chosen per tile from a bound on |J| at any
+// node: each Esirkepov contribution of a particle satisfies |v| <= |q w| |v_p|
+// and Boris raises |u| by at most |q/m| dt |E|, so
+//   |J_node| <= Q = sum over the tile's particles of |q w| min(1, |u| + |q/m| dt Emax)
+// with Emax bounding |E| over the tile's field window; 2^K keeps Q 2^K below
+// 2^kLimitLog2.  X is kept as two signed 32-bit words, X = hi * 2^16 + lo
+// with |lo| <= 2^15, both found with FP32 adds only (adding 1.5 * 2^23 rounds
+// a float of magnitude below 2^22 to an integer held in its low mantissa
+// bits), because float-to-64-bit conversions run on the slow FP64 pipe.  With
 // |X| < 2^37 the hi sums cannot overflow, and the lo sums cannot overflow for
-// fewer than 65,536 contributions per node.  FP64: one 64-bit word, exact
-// modulo 2^64 with |X| < 2^61.
+// fewer than 65,536 contributions per node.  FP64 runs use plain double
+// shared atomics, keeping FP64 rounding.
 template <class R> struct WinAcc;
 template <> struct WinAcc<float> {
   int *w;       // [3][2][JN]: per component lo words, then hi words
@@ -138,9 +153,9 @@ template <> struct WinAcc<float> {
   float unit;   // 2^-K
   static constexpr int kLimitLog2 = 37;
   static constexpr float kMagic = 12582912.0f;  // 1.5 * 2^23
-  __device__ __forceinline__ void add(int comp, int idx, float v) const {
-    if (v != 0.f) {
-      const float x = v * scale;
+  // x: contribution already multiplied by 2^K
+  __device__ __forceinline__ void add(int comp, int idx, float x) const {
+    if (x != 0.f) {
       const float yh = fmaf(x, 1.0f / 65536.0f, kMagic);  // rint(x / 2^16) + magic
       const float hf = yh - kMagic;
       const int hi = __float_as_int(yh) - __float_as_int(kMagic);
@@ -157,15 +172,14 @@ template <> struct WinAcc<float> {
   }
 };
 template <> struct WinAcc<double> {
-  unsigned long long *w;  // [3][JN]
+  double *w;  // [3][JN], plain double sums (the FP64 path keeps FP64 rounding)
   int jn;
-  double scale;
+  double scale;  // 1: contributions are passed unscaled
   double unit;
-  static constexpr int kLimitLog2 = 61;
-  __device__ __forceinline__ void add(int comp, int idx, double v) const {
-    if (v != 0.0) atomicAdd(w + comp * jn + idx, (unsigned long long)__double2ll_rn(v * scale));
+  __device__ __forceinline__ void add(int comp, int idx, double x) const {
+    if (x != 0.0) atomicAdd(w + comp * jn + idx, x);
   }
-  __device__ __forceinline__ double get(int comp, int idx) const { return (double)(long long)w[comp * jn + idx] * unit; }
+  __device__ __forceinline__ double get(int comp, int idx) const { return w[comp * jn + idx]; }
 };
 
 // Esirkepov deposit into the shared J window (compile-time strides).
@@ -291,6 +305,9 @@ __global__ void __launch_bounds__(kThreads, sizeof(R) == 4 ? 2 : 1) k_push(const
   int32_t *sCell = reinterpret_cast<int32_t *>(sW + kThreads);  // 256
   __shared__ unsigned int s_clamp;
   __shared__ double s_scale;
+  __shared__ unsigned int s_emax[3];
+  __shared__ float s_qsum;
+  float emax[3] = {0.f, 0.f, 0.f};
 
   const int t = blockIdx.x;
   const int64_t pb = a.tile_start[t], pe = a.tile_start[t + 1];
@@ -310,26 +327,53 @@ __global__ void __launch_bounds__(kThreads, sizeof(R) == 4 ? 2 : 1) k_push(const
     const int x = q % G::EX;
     const int y = (q / G::EX) % G::EY;
     const int z = q / (G::EX * G::EY);
-    const int gi = wrapi(t0[0] - G::D - G::LOE + x, a.n[0]);
-    const int gj = wrapi(t0[1] - G::D - G::LOE + y, a.n[1]);
-    const int gk = DIM == 3 ? wrapi(t0[2] - G::D - G::LOE + z, a.n[2]) : 0;
+    const int gi = wrap_near(t0[0] - G::D - G::LOE + x, a.n[0]);
+    const int gj = wrap_near(t0[1] - G::D - G::LOE + y, a.n[1]);
+    const int gk = DIM == 3 ? wrap_near(t0[2] - G::D - G::LOE + z, a.n[2]) : 0;
     const int64_t g = gi + (int64_t)a.n[0] * (gj + (int64_t)a.n[1] * gk);
 #pragma unroll
     for (int c = 0; c < 3; ++c) {
-      sF[c * G::EN + q] = a.E[c][g];
+      const R ev = a.E[c][g];
+      sF[c * G::EN + q] = ev;
       sF[(3 + c) * G::EN + q] = a.B[c][g];
+      emax[c] = fmax(emax[c], fabs((float)ev));
     }
   }
-  for (int q = tid; q < 6 * G::JN; q += kThreads) reinterpret_cast<int *>(sJraw)[q] = 0;
+  for (int q = tid; q < 6 * G::JN; q += kThreads) reinterpret_cast<int *>(sJraw)[q] = 0;  // 24 B per node
   if (tid == 0) {
     s_clamp = 0;
-    // fixed-point scale 2^K with |q| max|w| n_tile 2^K < 2^limit
-    const double Q = a.qabs * (double)*a.wmax * (double)(pe - pb);
-    int e2 = 0;
-    if (Q > 0.0) frexp(Q, &e2);
-    int K = Q > 0.0 ? WinAcc<R>::kLimitLog2 - e2 : 100;
-    K = K > 100 ? 100 : (K < -100 ? -100 : K);
-    s_scale = ldexp(1.0, K);
+    s_emax[0] = s_emax[1] = s_emax[2] = 0u;
+    s_qsum = 0.f;
+  }
+  __syncthreads();
+  if (sizeof(R) == 4) {
+    // fixed-point scale: bound Q on |J| at any node of the window (see WinAcc)
+#pragma unroll
+    for (int c = 0; c < 3; ++c)
+      if (emax[c] > 0.f) atomicMax(&s_emax[c], __float_as_uint(emax[c]));
+    __syncthreads();
+    const float ex = __uint_as_float(s_emax[0]), ey = __uint_as_float(s_emax[1]), ez = __uint_as_float(s_emax[2]);
+    const float kick = (float)(2.0 * fabs((double)a.qmh)) * sqrtf(ex * ex + ey * ey + ez * ez);
+    float qs = 0.f;
+    for (int64_t p = pb + tid; p < pe; p += kThreads) {
+      if (a.cell[p] < 0) continue;
+      const float ux = (float)a.u[0][p], uy = (float)a.u[1][p], uz = (float)a.u[2][p];
+      qs += fabsf((float)a.w[p]) * fminf(1.f, sqrtf(ux * ux + uy * uy + uz * uz) + kick);
+    }
+    for (int o = 16; o > 0; o >>= 1) qs += __shfl_down_sync(0xffffffffu, qs, o);
+    if ((tid & 31) == 0 && qs > 0.f) atomicAdd(&s_qsum, qs);
+    __syncthreads();
+    if (tid == 0) {
+      // 1.01: room for the FP32 rounding of the sums above
+      const double Q = 1.01 * a.qabs * (double)s_qsum;
+      int e2 = 0;
+      if (Q > 0.0) frexp(Q, &e2);  // Q < 2^e2
+      int K = Q > 0.0 ? WinAcc<float>::kLimitLog2 - e2 : 100;
+      K = K > 100 ? 100 : (K < -100 ? -100 : K);
+      s_scale = ldexp(1.0, K);
+    }
+  } else if (tid == 0) {
+    s_scale = 1.0;
   }
   __syncthreads();
   WinAcc<R> acc;
@@ -342,7 +386,7 @@ __global__ void __launch_bounds__(kThreads, sizeof(R) == 4 ? 2 : 1) k_push(const
   // eight warps' lanes land on 32 distinct banks)
   const int lane = tid & 31, warp = tid >> 5;
   const int e = 8 * lane + ((warp + (lane >> 2)) & 7);
-  unsigned my_clamp = 0;
+  unsigned my_clamp = 0, my_absorbed = 0;
 
   for (int64_t c0 = pb; c0 < pe; c0 += kThreads) {
     const int cn = (int)(pe - c0 < kThreads ? pe - c0 : kThreads);
@@ -429,10 +473,15 @@ __global__ void __launch_bounds__(kThreads, sizeof(R) == 4 ? 2 : 1) k_push(const
           constexpr int oJ = G::D + G::LOJ;
           const int jb = (l[0] + dx.rel + oJ) + (l[1] + dy.rel + oJ) * G::JX +
                          (DIM == 3 ? (l[2] + dz.rel + oJ) * G::JX * G::JY : 0);
-          deposit_win<R, ORDER, DIM, G::JX, G::JX * G::JY>(acc, jb, dx, dy, dz, a.jfac[0] * wq, a.jfac[1] * wq,
-                                                            a.jfac[2] * wq, a.qz * wq * u[2] * ig);
+          const R ws = wq * acc.scale;  // fixed-point units folded into the factors
+          deposit_win<R, ORDER, DIM, G::JX, G::JX * G::JY>(acc, jb, dx, dy, dz, a.jfac[0] * ws, a.jfac[1] * ws,
+                                                            a.jfac[2] * ws, a.qz * ws * u[2] * ig);
 
           // ---- new state back into the staging slot ----
+          if (outside_walls<R>(a.absorb, ci[0] + s[0], fn[0], a.n[0])) {
+            sCell[e] = -1;  // removed at an absorbing wall after depositing its move
+            ++my_absorbed;
+          } else {
           int nc = c;
           {
             int i0 = ci[0] + s[0];
@@ -449,6 +498,7 @@ __global__ void __launch_bounds__(kThreads, sizeof(R) == 4 ? 2 : 1) k_push(const
           for (int d = 0; d < DIM; ++d) sOff[d * kThreads + e] = fn[d];
 #pragma unroll
           for (int d = 0; d < 3; ++d) sU[d * kThreads + e] = u[d];
+          }
         }
       }
     }
@@ -465,6 +515,7 @@ __global__ void __launch_bounds__(kThreads, sizeof(R) == 4 ? 2 : 1) k_push(const
   }
 
   if (my_clamp) atomicAdd(&s_clamp, my_clamp);
+  if (my_absorbed) atomicAdd(&a.ctr->absorbed, (unsigned long long)my_absorbed);
   __syncthreads();
 
   // ---- flush the J window into global J ----
@@ -472,9 +523,9 @@ __global__ void __launch_bounds__(kThreads, sizeof(R) == 4 ? 2 : 1) k_push(const
     const int x = q % G::JX;
     const int y = (q / G::JX) % G::JY;
     const int z = q / (G::JX * G::JY);
-    const int gi = wrapi(t0[0] - G::D - G::LOJ + x, a.n[0]);
-    const int gj = wrapi(t0[1] - G::D - G::LOJ + y, a.n[1]);
-    const int gk = DIM == 3 ? wrapi(t0[2] - G::D - G::LOJ + z, a.n[2]) : 0;
+    const int gi = wrap_near(t0[0] - G::D - G::LOJ + x, a.n[0]);
+    const int gj = wrap_near(t0[1] - G::D - G::LOJ + y, a.n[1]);
+    const int gk = DIM == 3 ? wrap_near(t0[2] - G::D - G::LOJ + z, a.n[2]) : 0;
     const int64_t g = gi + (int64_t)a.n[0] * (gj + (int64_t)a.n[1] * gk);
 #pragma unroll
     for (int c = 0; c < 3; ++c) {
@@ -588,6 +639,11 @@ __global__ void __launch_bounds__(kThreads) k_push_escaped(const PushArgs<R> a) 
           atomicAdd(a.J[2] + g, qwvz * (X.S0[ax] * hy + X.DS[ax] * ty));
         }
     }
+    if (outside_walls<R>(a.absorb, ci[0] + s[0], fn[0], a.n[0])) {
+      a.cell[p] = -1;  // removed at an absorbing wall after depositing its move
+      atomicAdd(&a.ctr->absorbed, 1ull);
+      continue;
+    }
     int nc[3] = {ci[0], ci[1], ci[2]};
 #pragma unroll
     for (int d = 0; d < DIM; ++d) nc[d] = wrapi(ci[d] + s[d], a.n[d]);
@@ -609,10 +665,9 @@ template <class R, int DIM, int ORDER> constexpr size_t smem_bytes() {
 
 template <class R, int DIM, int ORDER>
 cudaError_t launch_t(const Grid &g, void *const E[3], void *const B[3], void *const J[3], const Particles &p,
-                     const int64_t *tile_start, const void *wmax, int32_t *esc_list, unsigned long long *esc_count,
-                     double q, double m, Counters *ctr, cudaStream_t st, int *nlaunch) {
+                     const int64_t *tile_start, int32_t *esc_list, unsigned long long *esc_count, double q,
+                     double m, Counters *ctr, cudaStream_t st, int *nlaunch) {
   PushArgs<R> a;
-  a.wmax = static_cast<const R *>(wmax);
   a.qabs = q < 0 ? -q : q;
   for (int d = 0; d < 3; ++d) {
     a.n[d] = g.n[d];
@@ -635,6 +690,7 @@ cudaError_t launch_t(const Grid &g, void *const E[3], void *const B[3], void *co
   a.esc_count = esc_count;
   a.qmh = (R)(q * g.dt / (2.0 * m));
   a.qz = (R)q;
+  a.absorb = g.absorb_lo || g.absorb_hi;
   a.ctr = ctr;
   constexpr size_t smem = smem_bytes<R, DIM, ORDER>();
   auto fn = k_push<R, DIM, ORDER>;
@@ -677,12 +733,11 @@ size_t push_smem_bytes(const Grid &g) {
 }
 
 cudaError_t launch_push(const Grid &g, void *const E[3], void *const B[3], void *const J[3], const Particles &p,
-                        const int64_t *tile_start, const void *wmax, int32_t *esc_list,
-                        unsigned long long *esc_count, double q, double m, Counters *ctr, cudaStream_t st,
-                        int *nlaunch) {
+                        const int64_t *tile_start, int32_t *esc_list, unsigned long long *esc_count, double q,
+                        double m, Counters *ctr, cudaStream_t st, int *nlaunch) {
   const int key = (g.prec == 1 ? 100 : 0) + g.dims * 10 + g.order;
 #define PIC_PUSH_CASE(K, R, D, O) \
-  case K: return launch_t<R, D, O>(g, E, B, J, p, tile_start, wmax, esc_list, esc_count, q, m, ctr, st, nlaunch);
+  case K: return launch_t<R, D, O>(g, E, B, J, p, tile_start, esc_list, esc_count, q, m, ctr, st, nlaunch);
   switch (key) {
     PIC_PUSH_CASE(21, float, 2, 1)
     PIC_PUSH_CASE(22, float, 2, 2)

@@ -1,0 +1,131 @@
+"""Absorbing x walls, laser injection and particle removal: GPU path vs the
+FP64 oracle on identical inputs (needs a GB300).
+
+Tolerances as for the periodic path: FP64 within 1e-12 relative per step,
+FP32 within 1e-5 after 10 steps on fields and momenta.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_1503_02464_gb300 import synth
+from paper_1503_02464_gb300.sim import Simulation
+
+from _parity import compare_fields, compare_particles, j_floor, rel_inf
+
+pytestmark = pytest.mark.gpu
+
+TAU = 2 * math.pi
+
+
+def _laser_slab(dims, nx, ny, nz=1, d=0.1, a0=2.0, slab=(20, 28), ppc=2, density=4.0, order=2):
+    dd = (d, d, d if dims == 3 else 1.0)
+    dt = 0.9 * synth.courant_limit(dd, dims)
+    n = (nx, ny, nz if dims == 3 else 1)
+    wl = synth.Workload("laser_slab_small", dims, n, dd, dt, order, 50, 77,
+                        [synth.Species("electron", -1.0, 1.0, ppc, 0.0, density, slab, 0),
+                         synth.Species("proton", 1.0, 1836.0, ppc, 0.0, density, slab, 1)],
+                        absorbing_x=True, neutralize=False,
+                        laser={"a0": a0, "waist": 0.25 * ny * d, "duration": TAU, "pol": 1})
+    return wl
+
+
+def _pair(wl, precision):
+    """Oracle and GPU simulations of the same workload; also returns the
+    oracle's J error floor for these particles."""
+    o = oracle.OracleSim(wl.dims, wl.n, wl.d, wl.dt, wl.order)
+    o.set_absorbing_x(True)
+    L = wl.laser
+    o.set_laser(L["a0"], L["waist"], L["duration"], pol=L["pol"])
+    s = Simulation.from_workload(wl, precision=precision)
+    parts = []
+    for isp, sp in enumerate(wl.species):
+        p = wl.particles(isp)
+        parts.append(p)
+        o.add_particles(p, sp.q, sp.m)
+        k = s.add_species(sp.q, sp.m, len(p["x"]))
+        s.load(k, p)
+    return o, s, j_floor(wl, parts)
+
+
+def test_vacuum_pulse_fp64():
+    wl = _laser_slab(2, 96, 16, ppc=0)
+    wl.species = []
+    o, s, _ = _pair(wl, "fp64")
+    for step in range(1, 121):
+        o.field_step(1)
+        s.step(1)
+        if step % 20 == 0:
+            fe = compare_fields(o, s, ["Ex", "Ey", "Ez", "Bx", "By", "Bz"])
+            for k, v in fe.items():
+                assert v <= 1e-12 * step, (step, k, v)
+    assert np.abs(s.field(1)).max() > 0.1  # the pulse is in the box
+
+
+@pytest.mark.parametrize("dims", [2, 3])
+def test_laser_slab_fp64(dims):
+    wl = _laser_slab(3, 64, 16, 8, slab=(10, 16)) if dims == 3 else _laser_slab(2, 96, 24)
+    o, s, jf = _pair(wl, "fp64")
+    nsteps = 40 if dims == 3 else 80
+    for step in range(1, nsteps + 1):
+        o.step(1)
+        s.step(1)
+        if step % 10 == 0:
+            fe = compare_fields(o, s, j_abs=jf)
+            for k, v in fe.items():
+                assert v <= 1e-12 * step, (step, k, v)
+            # momentum scale the fields can impart so far: |q/m| max|E| t
+            emax = max(np.abs(o.get_field(c)).max() for c in range(3))
+            for isp, sp in enumerate(wl.species):
+                us = abs(sp.q) / sp.m * emax * wl.dt * step
+                du, dx = compare_particles(o, s, wl, isp, u_scale=us)
+                assert du <= 1e-12 * step, (step, isp, du)
+    # the laser has reached the slab and pushed electrons
+    assert np.abs(s.particles(0)["ux"]).max() > 1e-3
+
+
+def test_laser_slab_fp32():
+    wl = _laser_slab(2, 96, 24)
+    o, s, _ = _pair(wl, "fp32")
+    o.step(50)
+    s.step(50)
+    o.step(10)
+    s.step(10)
+    fe = compare_fields(o, s, ["Ex", "Ey", "Ez", "Bx", "By", "Bz"])
+    for k, v in fe.items():
+        assert v <= 1e-5, (k, v)
+    du, _ = compare_particles(o, s, wl, 0)
+    assert du <= 1e-4, du
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+def test_particles_removed_at_walls(precision):
+    """Fast particles streaming into both walls are removed on the same step
+    as in the oracle; the remaining fields agree."""
+    nx, ny = 40, 8
+    wl = synth.Workload("walls", 2, (nx, ny, 1), (0.1, 0.1, 1.0), 0.06, 2, 10, 5, [], absorbing_x=True)
+    rng = np.random.default_rng(3)
+    n = 64
+    x = rng.uniform(4.0, nx - 5.0, n) * 0.1
+    parts = {"x": x, "y": rng.uniform(0, ny, n) * 0.1, "z": np.zeros(n),
+             "ux": np.where(x > 2.0, 3.0, -3.0) * rng.uniform(0.5, 1.0, n),
+             "uy": rng.normal(0, 0.3, n), "uz": rng.normal(0, 0.3, n), "w": np.full(n, 0.5),
+             "id": np.arange(n, dtype=np.uint32)}
+    o = oracle.OracleSim(2, wl.n, wl.d, wl.dt, 2)
+    o.set_absorbing_x(True)
+    o.add_particles(parts, -1.0, 1.0)
+    s = Simulation.from_workload(wl, precision=precision)
+    k = s.add_species(-1.0, 1.0, n)
+    s.load(k, parts)
+    for step in range(1, 31):
+        o.step(1)
+        s.step(1)
+        assert s.diag()["n_alive"] == o.diag()["n_alive"], step
+    assert o.diag()["n_alive"] < n
+    tol = 1e-10 if precision == "fp64" else 1e-4
+    fe = compare_fields(o, s, ["Ex", "Ey", "Ez", "Bx", "By", "Bz"])
+    for key, v in fe.items():
+        assert v <= tol, (key, v)
+    assert s.diag()["n_absorbed"] == n - o.diag()["n_alive"]
