@@ -43,6 +43,10 @@ WORKLOAD = "thermal3d_256"
 # 12 B write) once = 48 B.
 PUSH_BYTES_PER_PARTICLE = {"fp32": 60, "fp64": 4 + 24 + 24 + 8 + 4 + 24 + 24}
 PUSH_BYTES_PER_CELL = {"fp32": 48, "fp64": 96}
+# DRAM bytes (read + write) per particle of one push launch, from the ncu
+# capture summarised in profiles/k_push_thermal3d_128.md (128^3 case of the
+# same kernel, scaled by the particle count); None once the kernel changes.
+PUSH_TRAFFIC_PER_PARTICLE = {"fp32": 62.7}
 
 
 def _peaks():
@@ -344,7 +348,8 @@ def run_gpu(args, rank: int, world: int, local: int):
                    "l2": "inputs larger than L2 (particle arrays > 4 GB, fields 0.6 GB)",
                    "parallelism": "replicas" if world > 1 else "single GPU"},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-                     "traffic": None, "kernel": "k_push (fused gather/Boris/move/Esirkepov)",
+                     "traffic": (PUSH_TRAFFIC_PER_PARTICLE.get(args.precision) or 0) * npart or None,
+                     "kernel": "k_push (fused gather/Boris/move/Esirkepov)",
                      "peak_kind": f"{peak_kind} HBM copy bandwidth",
                      "bytes_per_launch": alg_bytes, "ms_per_launch": push_avg_s * 1e3},
         "kernel_times": tim_out,
