@@ -273,6 +273,30 @@ def run_gpu(args, rank: int, world: int, local: int):
                 "push_ms_per_launch": p64_ms / max(p64_n, 1)}
         torch.cuda.synchronize()
 
+    # ---------------- adjoint / forward time of the differentiable run
+    adjoint = None
+    if not args.no_adjoint and rank == 0:
+        from paper_1503_02464_gb300 import diff
+        run = diff.SlabRun(precision="fp32")
+        prof = run.default_profile()
+        for rep in range(2):  # the first repetition warms up
+            sim = diff.build_sim(run, 2.0, prof)
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            F = diff.run_forward(run, sim)
+            torch.cuda.synchronize()
+            t1 = time.perf_counter()
+            da0, dprof = diff.backward_gradients(run, sim)
+            torch.cuda.synchronize()
+            t2 = time.perf_counter()
+            sim.close()
+        adjoint = {"workload": f"2D3V laser slab {run.nx}x{run.ny}, {run.ppc} ppc ({run.nx * run.ny * run.ppc} "
+                               f"electron slots), TSC, {run.steps} steps, checkpoint every {run.segment}, FP32 "
+                               f"forward/adjoint, FP64 gradients",
+                   "forward_s": t1 - t0, "backward_s": t2 - t1, "ratio": (t2 - t1) / (t1 - t0),
+                   "note": "backward includes re-running every segment with the tape on",
+                   "objective": F, "dF_da0": da0}
+
     # ---------------- end to end through the C ABI with host buffers
     e2e = None
     if not args.no_e2e:
@@ -363,6 +387,8 @@ def run_gpu(args, rank: int, world: int, local: int):
         line["fp64"] = fp64
     if e2e is not None:
         line["e2e"] = e2e
+    if adjoint is not None:
+        line["adjoint"] = adjoint
     if cpu is not None:
         line["cpu_baseline"] = cpu
     print(json.dumps(line), flush=True)
@@ -384,6 +410,7 @@ def main():
     ap.add_argument("--nproc", type=int, default=0)
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-adjoint", action="store_true")
     args = ap.parse_args()
     world, rank, local = _dist_setup(args)
     if args.impl == "reference":

@@ -206,6 +206,48 @@ int pic_timings(pic_handle *h, double *ms, int64_t *launches, int nmax, int *ncl
 /* Number of kernels this handle has launched since creation. */
 int pic_launch_count(pic_handle *h, int64_t *count);
 
+/* ---- differentiable runs (2D3V, TSC) ----------------------------------
+ * Reverse-mode gradients of an objective with respect to the laser
+ * amplitude a0 and the particle weights w (hence an initial density
+ * profile): hand-written adjoint kernels of the Yee update and its Mur
+ * walls with the laser source, of the gather, the Boris push, the move and
+ * the Esirkepov deposit (the transposes of the §2 step), FP32 or FP64 like
+ * the forward, with the gradients accumulated in FP64.  A reverse sweep
+ * needs the forward states of the steps it reverses: take checkpoints during
+ * the forward run, and before reversing a segment restore its checkpoint and
+ * re-run it with the tape on.  Checkpoints and tapes hold every species
+ * added so far; add all species first. */
+
+/* Save (restore) the full state -- fields, particles of every species, step
+ * count -- in slot `slot` (0..4096; device memory allocated on first use).
+ * pic_restore marks the species for a sort at the next step. */
+int pic_checkpoint(pic_handle *h, int slot);
+int pic_restore(pic_handle *h, int slot);
+
+/* Record the state at the start of each of the next nsteps calls to the
+ * step loop (after its sort), for pic_adjoint_step.  nsteps = 0 stops. */
+int pic_tape_begin(pic_handle *h, int nsteps);
+
+/* Allocate (first call) and zero the adjoint state: field adjoints, and per
+ * species particle adjoints indexed by particle id (ids must be below
+ * id_capacity), the FP64 weight gradients and dF/da0.  PIC_EINVAL unless
+ * dims = 2 and shape_order = 2. */
+int pic_adjoint_begin(pic_handle *h, int64_t id_capacity);
+
+/* Objective F = sum over live particles of `species` whose x cell column is
+ * in [col_lo, col_hi) of w dV m (gamma - 1) at the current state (FP64),
+ * written to *F; seeds the adjoint with dF/du and dF/dw. */
+int pic_adjoint_seed_kinetic(pic_handle *h, int species, int col_lo, int col_hi, double *F);
+
+/* Reverse the last nsteps recorded steps (most recent first), accumulating
+ * dF/da0 and dF/dw.  PIC_EINVAL if fewer steps are on the tape. */
+int pic_adjoint_step(pic_handle *h, int nsteps);
+
+/* Copy dF/da0 (one double, may be NULL) and dF/dw of `species` indexed by
+ * particle id (id_capacity doubles, may be NULL) to host or device memory.
+ * Synchronises. */
+int pic_grad(pic_handle *h, double *d_a0, int species, double *d_w, int mem_kind);
+
 /* FP64 field energies without any device allocation.  The paper has no
  * counterpart: this is a library service for callers that must not call
  * cudaMalloc/cudaFree (which can synchronise the device), e.g. code embedded

@@ -24,7 +24,9 @@ ERROR_NAMES = {0: "PIC_OK", 1: "PIC_EINVAL", 2: "PIC_ECOURANT", 3: "PIC_ENOMEM",
 # every symbol include/pic.h declares
 EXPORTED = ["pic_create", "pic_destroy", "pic_last_error", "pic_add_species", "pic_load_particles",
             "pic_neutralize", "pic_step", "pic_fields", "pic_set_field", "pic_num_particles", "pic_particles",
-            "pic_diag", "pic_sync", "pic_profile", "pic_timings", "pic_launch_count", "pic_field_energy_noalloc"]
+            "pic_diag", "pic_sync", "pic_profile", "pic_timings", "pic_launch_count", "pic_checkpoint",
+            "pic_restore", "pic_tape_begin", "pic_adjoint_begin", "pic_adjoint_seed_kinetic", "pic_adjoint_step",
+            "pic_grad", "pic_field_energy_noalloc"]
 
 
 class pic_laser(ctypes.Structure):
@@ -96,6 +98,13 @@ def load(build_if_missing: bool = True) -> ctypes.CDLL:
         "pic_timings": ([hp, dp, ctypes.POINTER(ctypes.c_int64), ctypes.c_int, ctypes.POINTER(ctypes.c_int)],
                         ctypes.c_int),
         "pic_launch_count": ([hp, ctypes.POINTER(ctypes.c_int64)], ctypes.c_int),
+        "pic_checkpoint": ([hp, ctypes.c_int], ctypes.c_int),
+        "pic_restore": ([hp, ctypes.c_int], ctypes.c_int),
+        "pic_tape_begin": ([hp, ctypes.c_int], ctypes.c_int),
+        "pic_adjoint_begin": ([hp, i64], ctypes.c_int),
+        "pic_adjoint_seed_kinetic": ([hp, ctypes.c_int, ctypes.c_int, ctypes.c_int, dp], ctypes.c_int),
+        "pic_adjoint_step": ([hp, ctypes.c_int], ctypes.c_int),
+        "pic_grad": ([hp, dp, ctypes.c_int, vp, ctypes.c_int], ctypes.c_int),
         "pic_field_energy_noalloc": ([ctypes.c_int, ctypes.c_void_p * 3, ctypes.c_void_p * 3, i64, ctypes.c_double,
                                       vp, ctypes.c_int, vp], ctypes.c_int),
     }
@@ -184,6 +193,38 @@ def pic_timings(h) -> dict:
     nc = ctypes.c_int()
     check(h, load().pic_timings(h, ms, cnt, 8, ctypes.byref(nc)))
     return {KERNEL_CLASSES[i]: (ms[i], cnt[i]) for i in range(nc.value)}
+
+
+def pic_checkpoint(h, slot: int) -> None:
+    check(h, load().pic_checkpoint(h, int(slot)))
+
+
+def pic_restore(h, slot: int) -> None:
+    check(h, load().pic_restore(h, int(slot)))
+
+
+def pic_tape_begin(h, nsteps: int) -> None:
+    check(h, load().pic_tape_begin(h, int(nsteps)))
+
+
+def pic_adjoint_begin(h, id_capacity: int) -> None:
+    check(h, load().pic_adjoint_begin(h, int(id_capacity)))
+
+
+def pic_adjoint_seed_kinetic(h, species: int, col_lo: int, col_hi: int) -> float:
+    F = ctypes.c_double()
+    check(h, load().pic_adjoint_seed_kinetic(h, int(species), int(col_lo), int(col_hi), ctypes.byref(F)))
+    return F.value
+
+
+def pic_adjoint_step(h, nsteps: int) -> None:
+    check(h, load().pic_adjoint_step(h, int(nsteps)))
+
+
+def pic_grad(h, species: int, dw_ptr, mem_kind: int) -> float:
+    d_a0 = ctypes.c_double()
+    check(h, load().pic_grad(h, ctypes.byref(d_a0), int(species), dw_ptr, int(mem_kind)))
+    return d_a0.value
 
 
 def pic_launch_count(h) -> int:

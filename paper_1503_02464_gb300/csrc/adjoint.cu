@@ -1,0 +1,715 @@
+// Reverse-mode (adjoint) kernels of the PIC step, for gradients of an
+// objective with respect to the laser amplitude and the particle weights
+// (hence the initial density profile).
+//
+// Forward step n (what is being differentiated, §2 of the paper):
+//   gather F = G(x^n; E^n, B^n) -> Boris u^{n+1/2} -> move x^{n+1}
+//   -> Esirkepov J(x^n, x^{n+1}, w) -> B half / E (+ Mur walls, laser) / B half.
+// Reverse step n, given the adjoints of the state after the step:
+//   R5  adj_yee_b   lamE -= dt/2 C_B (M_B lamB)       (transpose of B half 2)
+//   R4  adj_mur     transpose of the Mur wall update; dF/da0 accumulates
+//   R3  adj_yee_e   lamJ = -dt M_E lamE; lamB += dt C_E (M_E lamE); + wall terms
+//   R1  adj_yee_b   lamE -= dt/2 C_B (M_B lamB)       (transpose of B half 1)
+//   P   adj_push    per particle: deposit^T, move^T, Boris^T, gather^T
+// with C_B = C_E^T the Yee curls (curl B at E points, curl E at B points)
+// and M_B, M_E masks of the rows the forward updated.  Particle adjoints are
+// indexed by particle id; weight gradients accumulate in FP64.
+#include <cuda_runtime.h>
+
+#include "pic_device.cuh"
+
+namespace pic {
+
+namespace {
+
+int nblocks(int64_t n) {
+  int dev = 0, nsm = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+  const int64_t want = (n + 255) / 256;
+  const int64_t cap = (int64_t)nsm * 32;
+  return (int)(want < 1 ? 1 : (want < cap ? want : cap));
+}
+
+struct GridIdx {
+  int n0, n1, n2;
+  __device__ __forceinline__ void ijk(int64_t c, int &i, int &j, int &k) const {
+    i = (int)(c % n0);
+    const int64_t r = c / n0;
+    j = (int)(r % n1);
+    k = (int)(r / n1);
+  }
+};
+
+// ---------------------------------------------------------------- fields
+// lamE -= h * curl_at_E(M_B lamB): the transpose of "B -= h curl_at_B(E)"
+// over the rows the forward updated (By, Bz of the last x cell are not
+// updated when the x walls absorb).
+template <class R, int DIM>
+__global__ void __launch_bounds__(256)
+    k_adj_yee_b(GridIdx g, int absorb, R rdx, R rdy, R rdz, R h, R *lE0, R *lE1, R *lE2, const R *lB0, const R *lB1,
+                const R *lB2) {
+  const int64_t ncell = (int64_t)g.n0 * g.n1 * g.n2;
+  const int64_t sy = g.n0, sz = (int64_t)g.n0 * g.n1;
+  for (int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; c < ncell; c += (int64_t)gridDim.x * blockDim.x) {
+    int i, j, k;
+    g.ijk(c, i, j, k);
+    const int64_t cxm = c - (i > 0 ? 1 : 1 - g.n0);
+    const int64_t cym = c - (j > 0 ? sy : sy - sy * g.n1);
+    const bool mx0 = absorb && i == g.n0 - 1;        // row (i) of By, Bz masked
+    const bool mxm = absorb && (i == 0);             // row (i-1) wraps to the last x cell
+    const R bx = lB0[c], by = mx0 ? R(0) : lB1[c], bz = mx0 ? R(0) : lB2[c];
+    const R bzym = mx0 ? R(0) : lB2[cym];
+    const R byxm = mxm ? R(0) : lB1[cxm], bzxm = mxm ? R(0) : lB2[cxm];
+    const R bxym = lB0[cym];
+    R cx = (bz - bzym) * rdy;
+    R cy = -(bz - bzxm) * rdx;
+    const R cz = (by - byxm) * rdx - (bx - bxym) * rdy;
+    if (DIM == 3) {
+      const int64_t czm = c - (k > 0 ? sz : sz - sz * g.n2);
+      const R byzm = mx0 ? R(0) : lB1[czm];
+      cx -= (by - byzm) * rdz;
+      cy += (bx - lB0[czm]) * rdz;
+    }
+    lE0[c] -= h * cx;
+    lE1[c] -= h * cy;
+    lE2[c] -= h * cz;
+  }
+}
+
+// lamJ = -h M_E lamE ; lamB += h * curl_at_B(M_E lamE): the transpose of
+// "E += h (curl_at_E(B) - J)" over the updated rows (with absorbing walls:
+// Ex of the last x cell, Ey and Ez of the first and last x cells are not).
+template <class R, int DIM>
+__global__ void __launch_bounds__(256)
+    k_adj_yee_e(GridIdx g, int absorb, R rdx, R rdy, R rdz, R h, const R *lE0, const R *lE1, const R *lE2, R *lB0,
+                R *lB1, R *lB2, R *lJ0, R *lJ1, R *lJ2) {
+  const int64_t ncell = (int64_t)g.n0 * g.n1 * g.n2;
+  const int64_t sy = g.n0, sz = (int64_t)g.n0 * g.n1;
+  auto mex = [&](int i) { return absorb && i == g.n0 - 1; };
+  auto meyz = [&](int i) { return absorb && (i == 0 || i == g.n0 - 1); };
+  for (int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; c < ncell; c += (int64_t)gridDim.x * blockDim.x) {
+    int i, j, k;
+    g.ijk(c, i, j, k);
+    const int ip = i + 1 < g.n0 ? i + 1 : 0;
+    const int64_t cxp = c + (i + 1 < g.n0 ? 1 : 1 - g.n0);
+    const int64_t cyp = c + (j + 1 < g.n1 ? sy : sy - sy * g.n1);
+    const R ex = mex(i) ? R(0) : lE0[c], ey = meyz(i) ? R(0) : lE1[c], ez = meyz(i) ? R(0) : lE2[c];
+    lJ0[c] = -h * ex;
+    lJ1[c] = -h * ey;
+    lJ2[c] = -h * ez;
+    const R ezyp = meyz(i) ? R(0) : lE2[cyp];
+    const R ezxp = meyz(ip) ? R(0) : lE2[cxp];
+    const R eyxp = meyz(ip) ? R(0) : lE1[cxp];
+    const R exyp = mex(i) ? R(0) : lE0[cyp];
+    R cx = (ezyp - ez) * rdy;
+    R cy = -(ezxp - ez) * rdx;
+    const R cz = (eyxp - ey) * rdx - (exyp - ex) * rdy;
+    if (DIM == 3) {
+      const int64_t czp = c + (k + 1 < g.n2 ? sz : sz - sz * g.n2);
+      const R eyzp = meyz(i) ? R(0) : lE1[czp];
+      const R exzp = mex(i) ? R(0) : lE0[czp];
+      cx -= (eyzp - ey) * rdz;
+      cy += (exzp - ex) * rdz;
+    }
+    lB0[c] += h * cx;
+    lB1[c] += h * cy;
+    lB2[c] += h * cz;
+  }
+}
+
+__device__ double laser_unit(const Laser &L, int dims, double x, double y, double z, double t) {
+  const double tau = t - x;
+  if (tau <= 0.0 || tau >= L.duration) return 0.0;
+  const double env = sin(3.14159265358979323846 * tau / L.duration);
+  double r2 = (y - L.yc) * (y - L.yc);
+  if (dims == 3) r2 += (z - L.zc) * (z - L.zc);
+  return exp(-r2 / (L.waist * L.waist)) * env * env * sin(tau);
+}
+
+// Transpose of the Mur wall update (tangential components y, z):
+//   E0' = L0n + S1o + k (S1n - S0o),  S = E - L     (left wall, laser)
+//   Ez' = E(n0-2)o + k (E(n0-2)n - E(n0-1)o)      (right wall)
+// g = lamE(wall) is consumed (the wall value was overwritten), k g goes to
+// the neighbour at the new time, and g, -k g are kept in `pend` for the old
+// time (added after R3).  dF/da0 += g dE0'/da0 (the laser terms over a0).
+template <class R>
+__global__ void k_adj_mur(int dims, int n0, int n1, int n2, double dx, double dy, double dz, double dt, R *lEy,
+                          R *lEz, double *pend, Laser las, double t_old, double t_new, double *da0) {
+  __shared__ double sh[32];
+  const int64_t nyz = (int64_t)n1 * n2;
+  const double kc = (dt - dx) / (dt + dx);
+  double acc = 0.0;
+  for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < 2 * nyz; q += (int64_t)gridDim.x * blockDim.x) {
+    const int c = (int)(q / nyz);
+    const int64_t jk = q % nyz;
+    const int j = (int)(jk % n1), k = (int)(jk / n1);
+    R *E = c == 0 ? lEy : lEz;
+    double *pd = pend + (int64_t)c * 4 * nyz;  // slots: node 0, 1, n0-2, n0-1
+    const int64_t row = (int64_t)n0 * jk;
+    const double g0 = (double)E[row];
+    E[row] = R(0);
+    E[row + 1] += (R)(kc * g0);
+    pd[0 * nyz + jk] = -kc * g0;
+    pd[1 * nyz + jk] = g0;
+    if (las.enabled && las.pol == c + 1) {
+      const double y = (j + (c == 0 ? 0.5 : 0.0)) * dy, z = (k + (c == 1 ? 0.5 : 0.0)) * dz;
+      const double l0n = laser_unit(las, dims, 0.0, y, z, t_new), l1o = laser_unit(las, dims, dx, y, z, t_old);
+      const double l1n = laser_unit(las, dims, dx, y, z, t_new), l0o = laser_unit(las, dims, 0.0, y, z, t_old);
+      acc += g0 * (l0n - l1o - kc * l1n + kc * l0o);
+    }
+    const double gr = (double)E[row + n0 - 1];
+    E[row + n0 - 1] = R(0);
+    E[row + n0 - 2] += (R)(kc * gr);
+    pd[2 * nyz + jk] = gr;
+    pd[3 * nyz + jk] = -kc * gr;
+  }
+  const double v = block_sum(acc, sh);
+  if (threadIdx.x == 0 && v != 0.0) atomicAdd(da0, v);
+}
+
+template <class R>
+__global__ void k_adj_mur_pend(int n0, int n1, int n2, R *lEy, R *lEz, const double *pend) {
+  const int64_t nyz = (int64_t)n1 * n2;
+  const int nodes[4] = {0, 1, n0 - 2, n0 - 1};
+  for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < 2 * nyz; q += (int64_t)gridDim.x * blockDim.x) {
+    const int c = (int)(q / nyz);
+    const int64_t jk = q % nyz;
+    R *E = c == 0 ? lEy : lEz;
+    const double *pd = pend + (int64_t)c * 4 * nyz;
+    const int64_t row = (int64_t)n0 * jk;
+#pragma unroll
+    for (int s = 0; s < 4; ++s) E[row + nodes[s]] += (R)pd[s * nyz + jk];
+  }
+}
+
+// ---------------------------------------------------------------- particles
+// TSC weights and their derivatives w.r.t. the particle coordinate.
+template <class R> __device__ __forceinline__ void tsc3d(R d, R w[3], R dw[3]) {
+  const R a = R(0.5) - d, b = R(0.5) + d;
+  w[0] = R(0.5) * a * a;
+  w[1] = R(0.75) - d * d;
+  w[2] = R(0.5) * b * b;
+  dw[0] = -a;
+  dw[1] = R(-2) * d;
+  dw[2] = b;
+}
+
+// Gather stencil (TSC) with derivatives: primal nodes rel_p.., dual rel_d..
+template <class R> struct GAxisD {
+  int relp, reld;
+  R wp[3], wd[3], dwp[3], dwd[3];
+  __device__ __forceinline__ void set(R f) {
+    const int h = f >= R(0.5);
+    relp = h - 1;
+    tsc3d<R>(f - R(h), wp, dwp);
+    reld = -1;
+    tsc3d<R>(f - R(0.5), wd, dwd);
+  }
+};
+
+// Deposit stencil (TSC, 4 nodes) with derivatives of S0 w.r.t. f and of S1
+// w.r.t. the new offset fn.
+template <class R> struct DAxisD {
+  int rel;
+  R S0[4], S1[4], dS0[4], dS1[4];
+  __device__ __forceinline__ void set(R f, int s, R fn) {
+    R w0[3], w1[3], d0[3], d1[3];
+    const int h0 = f >= R(0.5), h1 = fn >= R(0.5);
+    tsc3d<R>(f - R(h0), w0, d0);
+    tsc3d<R>(fn - R(h1), w1, d1);
+    const int n0 = h0 - 1, n1 = s + h1 - 1;
+    rel = n0 < n1 ? n0 : n1;
+    const int o0 = n0 - rel, o1 = n1 - rel;
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      const int q0 = k - o0, q1 = k - o1;
+      S0[k] = (q0 >= 0 && q0 < 3) ? w0[q0 < 3 ? q0 : 0] : R(0);
+      dS0[k] = (q0 >= 0 && q0 < 3) ? d0[q0 < 3 ? q0 : 0] : R(0);
+      S1[k] = (q1 >= 0 && q1 < 3) ? w1[q1 < 3 ? q1 : 0] : R(0);
+      dS1[k] = (q1 >= 0 && q1 < 3) ? d1[q1 < 3 ? q1 : 0] : R(0);
+    }
+  }
+};
+
+template <class R> struct AdjPushArgs {
+  int n[3];
+  int absorb;
+  // tape: particle state at the start of the step and the fields E^n, B^n
+  const int32_t *cell;
+  const R *off[3];
+  const R *u[3];
+  const R *w;
+  const uint32_t *id;
+  const int64_t *d_count;  // slots in use (device)
+  const R *E[3];
+  const R *B[3];
+  // adjoints
+  const R *lJ[3];
+  R *lE[3];
+  R *lB[3];
+  R *lx[3];   // by id: adjoint of the position (cells)
+  R *lu[3];   // by id: adjoint of u
+  double *lw;  // by id: dF/dw accumulated
+  int64_t id_cap;
+  unsigned long long *err;
+  R qmh, dtdx[3], cxu[3], q;
+};
+
+// The move's 1/gamma exactly as the forward push computes it.
+template <class R> __device__ __forceinline__ R inv_sqrt_fwd(R x);
+template <> __device__ __forceinline__ float inv_sqrt_fwd<float>(float x) { return rsqrtf(x); }
+template <> __device__ __forceinline__ double inv_sqrt_fwd<double>(double x) { return 1.0 / sqrt(x); }
+
+// Per-particle adjoint of gather -> Boris -> move -> Esirkepov (2D3V, TSC).
+template <class R>
+__global__ void __launch_bounds__(256) k_adj_push2d(const AdjPushArgs<R> a) {
+  const int n0 = a.n[0], n1 = a.n[1];
+  const int64_t nslots = *a.d_count;
+  for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < nslots; p += (int64_t)gridDim.x * blockDim.x) {
+    const int c = a.cell[p];
+    if (c < 0) continue;
+    const uint32_t pid = a.id[p];
+    if ((int64_t)pid >= a.id_cap) {
+      atomicOr(a.err, 1ull);  // id outside the adjoint arrays: skipped, reported
+      continue;
+    }
+    const int i0 = c % n0, j0 = c / n0;
+    const R f[2] = {a.off[0][p], a.off[1][p]};
+    const R u0[3] = {a.u[0][p], a.u[1][p], a.u[2][p]};
+    const R wq = a.w[p];
+    // ---- forward recomputation: gather
+    GAxisD<R> gx, gy;
+    gx.set(f[0]);
+    gy.set(f[1]);
+    int ixp[3], ixd[3], iyp[3], iyd[3];
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+      ixp[k] = wrapi(i0 + gx.relp + k, n0);
+      ixd[k] = wrapi(i0 + gx.reld + k, n0);
+      iyp[k] = wrapi(j0 + gy.relp + k, n1) * n0;
+      iyd[k] = wrapi(j0 + gy.reld + k, n1) * n0;
+    }
+    // component c: (dual x?, dual y?) for Ex Ey Ez Bx By Bz
+    const bool dx_[6] = {true, false, false, false, true, true};
+    const bool dy_[6] = {false, true, false, true, false, true};
+    R F[6], dFx[6], dFy[6];
+#pragma unroll
+    for (int cc = 0; cc < 6; ++cc) {
+      const R *G = cc < 3 ? a.E[cc] : a.B[cc - 3];
+      const int *ix = dx_[cc] ? ixd : ixp;
+      const int *iy = dy_[cc] ? iyd : iyp;
+      const R *wx = dx_[cc] ? gx.wd : gx.wp, *dwx = dx_[cc] ? gx.dwd : gx.dwp;
+      const R *wy = dy_[cc] ? gy.wd : gy.wp, *dwy = dy_[cc] ? gy.dwd : gy.dwp;
+      R s = 0, sx = 0, sy = 0;
+#pragma unroll
+      for (int b = 0; b < 3; ++b)
+#pragma unroll
+        for (int aa = 0; aa < 3; ++aa) {
+          const R v = G[ix[aa] + iy[b]];
+          s += v * wx[aa] * wy[b];
+          sx += v * dwx[aa] * wy[b];
+          sy += v * wx[aa] * dwy[b];
+        }
+      F[cc] = s;
+      dFx[cc] = sx;
+      dFy[cc] = sy;
+    }
+    // Boris (forward values kept for the transpose)
+    const R h = a.qmh;
+    R um[3], t[3], sv[3], up[3], uo[3];
+#pragma unroll
+    for (int d = 0; d < 3; ++d) um[d] = u0[d] + h * F[d];
+    const R gm = sqrt(R(1) + um[0] * um[0] + um[1] * um[1] + um[2] * um[2]);
+#pragma unroll
+    for (int d = 0; d < 3; ++d) t[d] = h * F[3 + d] / gm;
+    const R t2 = t[0] * t[0] + t[1] * t[1] + t[2] * t[2];
+    const R den = R(1) + t2;
+#pragma unroll
+    for (int d = 0; d < 3; ++d) sv[d] = R(2) * t[d] / den;
+    up[0] = um[0] + (um[1] * t[2] - um[2] * t[1]);
+    up[1] = um[1] + (um[2] * t[0] - um[0] * t[2]);
+    up[2] = um[2] + (um[0] * t[1] - um[1] * t[0]);
+    uo[0] = um[0] + (up[1] * sv[2] - up[2] * sv[1]) + h * F[0];
+    uo[1] = um[1] + (up[2] * sv[0] - up[0] * sv[2]) + h * F[1];
+    uo[2] = um[2] + (up[0] * sv[1] - up[1] * sv[0]) + h * F[2];
+    // move
+    const R ig = inv_sqrt_fwd<R>(R(1) + uo[0] * uo[0] + uo[1] * uo[1] + uo[2] * uo[2]);
+    R fn[2];
+    int sh[2];
+#pragma unroll
+    for (int d = 0; d < 2; ++d) {
+      R x = f[d] + a.dtdx[d] * uo[d] * ig;
+      const int s = (x >= R(1)) ? 1 : ((x < R(0)) ? -1 : 0);
+      x -= R(s);
+      if (x >= R(1)) x = below_one<R>();
+      if (x < R(0)) x = R(0);
+      fn[d] = x;
+      sh[d] = s;
+    }
+    const R vz = uo[2] * ig;
+    DAxisD<R> X, Y;
+    X.set(f[0], sh[0], fn[0]);
+    Y.set(f[1], sh[1], fn[1]);
+
+    // ---- deposit^T: gather lamJ on the deposit stencil
+    int jx[4], jy[4];
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      jx[k] = wrapi(i0 + X.rel + k, n0);
+      jy[k] = wrapi(j0 + Y.rel + k, n1) * n0;
+    }
+    R Px[3], Py[3];
+    {
+      R sx = 0, sy = 0;
+#pragma unroll
+      for (int k = 0; k < 3; ++k) {
+        sx += X.S1[k] - X.S0[k];
+        sy += Y.S1[k] - Y.S0[k];
+        Px[k] = sx;
+        Py[k] = sy;
+      }
+    }
+    R Hx[4], Hy[4];
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      Hx[k] = R(0.5) * (X.S0[k] + X.S1[k]);
+      Hy[k] = R(0.5) * (Y.S0[k] + Y.S1[k]);
+    }
+    // Jx: Gx[a] = sum_b Ax[a][b] Hy[b], Ky[b] = sum_a Ax[a][b] Px[a]
+    R Gx[3] = {0, 0, 0}, Ky[4] = {0, 0, 0, 0};
+    R Gy[3] = {0, 0, 0}, Kx[4] = {0, 0, 0, 0};
+    R Zx0[4] = {0, 0, 0, 0}, Zx1[4] = {0, 0, 0, 0}, Zy0[4] = {0, 0, 0, 0}, Zy1[4] = {0, 0, 0, 0};
+#pragma unroll
+    for (int b = 0; b < 4; ++b)
+#pragma unroll
+      for (int aa = 0; aa < 4; ++aa) {
+        const int64_t node = jx[aa] + jy[b];
+        if (aa < 3) {
+          const R Ax = a.lJ[0][node];
+          Gx[aa] += Ax * Hy[b];
+          Ky[b] += Ax * Px[aa];
+        }
+        if (b < 3) {
+          const R Ay = a.lJ[1][node];
+          Gy[b] += Ay * Hx[aa];
+          Kx[aa] += Ay * Py[b];
+        }
+        const R Az = a.lJ[2][node];
+        Zx0[aa] += Az * Y.S0[b];
+        Zx1[aa] += Az * Y.S1[b];
+        Zy0[b] += Az * X.S0[aa];
+        Zy1[b] += Az * X.S1[aa];
+      }
+    const R cx = a.cxu[0] * wq, cy = a.cxu[1] * wq, qw = a.q * wq;
+    // suffix sums R[k] = sum_{a>=k, a<3} G[a]
+    R Rx[4], Ry[4];
+    Rx[3] = 0;
+    Ry[3] = 0;
+#pragma unroll
+    for (int k = 2; k >= 0; --k) {
+      Rx[k] = Rx[k + 1] + Gx[k];
+      Ry[k] = Ry[k + 1] + Gy[k];
+    }
+    R Tz = 0;
+    R dS0x[4], dS1x[4], dS0y[4], dS1y[4];  // dL/dS
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      Tz += (X.S0[k] * Zx0[k] + X.S1[k] * Zx1[k]) * R(1.0 / 3.0) + (X.S0[k] * Zx1[k] + X.S1[k] * Zx0[k]) * R(1.0 / 6.0);
+      dS1x[k] = cx * Rx[k] + R(0.5) * cy * Kx[k] + qw * vz * (Zx1[k] * R(1.0 / 3.0) + Zx0[k] * R(1.0 / 6.0));
+      dS0x[k] = -cx * Rx[k] + R(0.5) * cy * Kx[k] + qw * vz * (Zx0[k] * R(1.0 / 3.0) + Zx1[k] * R(1.0 / 6.0));
+      dS1y[k] = cy * Ry[k] + R(0.5) * cx * Ky[k] + qw * vz * (Zy1[k] * R(1.0 / 3.0) + Zy0[k] * R(1.0 / 6.0));
+      dS0y[k] = -cy * Ry[k] + R(0.5) * cx * Ky[k] + qw * vz * (Zy0[k] * R(1.0 / 3.0) + Zy1[k] * R(1.0 / 6.0));
+    }
+    // dL/dw (contributions are linear in w)
+    double dLw = 0.0;
+    {
+      R gxp = 0, gyp = 0;
+#pragma unroll
+      for (int k = 0; k < 3; ++k) {
+        gxp += Gx[k] * Px[k];
+        gyp += Gy[k] * Py[k];
+      }
+      dLw = (double)(a.cxu[0] * gxp + a.cxu[1] * gyp + a.q * vz * Tz);
+    }
+    const R lvz = qw * Tz;  // dL/dvz
+    R lf_old[2] = {0, 0}, lf_new[2] = {0, 0};
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      lf_old[0] += dS0x[k] * X.dS0[k];
+      lf_new[0] += dS1x[k] * X.dS1[k];
+      lf_old[1] += dS0y[k] * Y.dS0[k];
+      lf_new[1] += dS1y[k] * Y.dS1[k];
+    }
+
+    // ---- move^T: x' = x + D(u+), vz = u+_z / gamma
+    R lX[2], lD[3];
+#pragma unroll
+    for (int d = 0; d < 2; ++d) {
+      const R lfut = a.lx[d][pid];
+      lD[d] = (lfut + lf_new[d]) * a.dtdx[d];
+      lX[d] = lfut + lf_new[d] + lf_old[d];
+    }
+    lD[2] = lvz;
+    R lu[3];
+    {
+      const R ud = (uo[0] * lD[0] + uo[1] * lD[1] + uo[2] * lD[2]) * ig * ig;
+#pragma unroll
+      for (int d = 0; d < 3; ++d) lu[d] = a.lu[d][pid] + (lD[d] - uo[d] * ud) * ig;
+    }
+
+    // ---- Boris^T
+    R lF[6];
+#pragma unroll
+    for (int d = 0; d < 3; ++d) lF[d] = h * lu[d];  // u_out = u+' + h E
+    // u+' = um + up x sv
+    R lum[3] = {lu[0], lu[1], lu[2]};
+    R lup[3], lsv[3];
+    // lambda_up = sv x lu ; lambda_sv = lu x up
+    lup[0] = sv[1] * lu[2] - sv[2] * lu[1];
+    lup[1] = sv[2] * lu[0] - sv[0] * lu[2];
+    lup[2] = sv[0] * lu[1] - sv[1] * lu[0];
+    lsv[0] = lu[1] * up[2] - lu[2] * up[1];
+    lsv[1] = lu[2] * up[0] - lu[0] * up[2];
+    lsv[2] = lu[0] * up[1] - lu[1] * up[0];
+    // sv = 2 t / (1 + t^2)
+    R lt[3];
+    {
+      const R tl = t[0] * lsv[0] + t[1] * lsv[1] + t[2] * lsv[2];
+#pragma unroll
+      for (int d = 0; d < 3; ++d) lt[d] = R(2) / den * lsv[d] - R(4) * t[d] * tl / (den * den);
+    }
+    // up = um + um x t: lambda_um += lup + t x lup ; lambda_t += lup x um
+#pragma unroll
+    for (int d = 0; d < 3; ++d) lum[d] += lup[d];
+    lum[0] += t[1] * lup[2] - t[2] * lup[1];
+    lum[1] += t[2] * lup[0] - t[0] * lup[2];
+    lum[2] += t[0] * lup[1] - t[1] * lup[0];
+    lt[0] += lup[1] * um[2] - lup[2] * um[1];
+    lt[1] += lup[2] * um[0] - lup[0] * um[2];
+    lt[2] += lup[0] * um[1] - lup[1] * um[0];
+    // t = h B / gm
+    R lgm = 0;
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+      lF[3 + d] = h / gm * lt[d];
+      lgm -= h * F[3 + d] / (gm * gm) * lt[d];
+    }
+    // gm = sqrt(1 + um^2)
+#pragma unroll
+    for (int d = 0; d < 3; ++d) lum[d] += lgm * um[d] / gm;
+    // um = u + h E
+    R lu0[3];
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+      lu0[d] = lum[d];
+      lF[d] += h * lum[d];
+    }
+
+    // ---- gather^T: scatter lamF into lamE, lamB; position derivative
+#pragma unroll
+    for (int cc = 0; cc < 6; ++cc) {
+      lX[0] += lF[cc] * dFx[cc];
+      lX[1] += lF[cc] * dFy[cc];
+      if (lF[cc] == R(0)) continue;
+      R *G = cc < 3 ? a.lE[cc] : a.lB[cc - 3];
+      const int *ix = dx_[cc] ? ixd : ixp;
+      const int *iy = dy_[cc] ? iyd : iyp;
+      const R *wx = dx_[cc] ? gx.wd : gx.wp;
+      const R *wy = dy_[cc] ? gy.wd : gy.wp;
+#pragma unroll
+      for (int b = 0; b < 3; ++b)
+#pragma unroll
+        for (int aa = 0; aa < 3; ++aa) atomicAdd(G + ix[aa] + iy[b], lF[cc] * wx[aa] * wy[b]);
+    }
+
+    // ---- new adjoint state (time n), weight gradient
+    a.lx[0][pid] = lX[0];
+    a.lx[1][pid] = lX[1];
+#pragma unroll
+    for (int d = 0; d < 3; ++d) a.lu[d][pid] = lu0[d];
+    a.lw[pid] += dLw;
+  }
+}
+
+// Objective F = sum over live particles with x column in [c_lo, c_hi) of
+// w dV m (gamma - 1); seeds lam_u = w dV m u / gamma and dF/dw directly.
+template <class R>
+__global__ void k_adj_seed(int n0, const int32_t *cell, const R *u0, const R *u1, const R *u2, const R *w,
+                           const uint32_t *id, const int64_t *d_count, int c_lo, int c_hi, double dVm, R *lu0, R *lu1,
+                           R *lu2, double *lw, double *F, int64_t id_cap, unsigned long long *err) {
+  __shared__ double sh[32];
+  double acc = 0.0;
+  const int64_t nslots = *d_count;
+  for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < nslots; p += (int64_t)gridDim.x * blockDim.x) {
+    const int c = cell[p];
+    if (c < 0) continue;
+    const int col = c % n0;
+    if (col < c_lo || col >= c_hi) continue;
+    const double ux = u0[p], uy = u1[p], uz = u2[p];
+    const double g = sqrt(1.0 + ux * ux + uy * uy + uz * uz);
+    const double ww = w[p];
+    const uint32_t k = id[p];
+    if ((int64_t)k >= id_cap) {
+      atomicOr(err, 1ull);
+      continue;
+    }
+    acc += ww * dVm * (g - 1.0);
+    lw[k] += dVm * (g - 1.0);
+    lu0[k] += (R)(ww * dVm * ux / g);
+    lu1[k] += (R)(ww * dVm * uy / g);
+    lu2[k] += (R)(ww * dVm * uz / g);
+  }
+  const double v = block_sum(acc, sh);
+  if (threadIdx.x == 0 && v != 0.0) atomicAdd(F, v);
+}
+
+template <class R> GridIdx gidx(const Grid &g) { return GridIdx{g.n[0], g.n[1], g.n[2]}; }
+
+}  // namespace
+
+cudaError_t launch_adj_yee_b(const Grid &g, void *const lE[3], void *const lB[3], double h, cudaStream_t st) {
+  const int nb = nblocks(g.ncell);
+  const int absorb = g.absorb_lo || g.absorb_hi;
+  if (g.prec == 1) {
+    auto E = [&](int c) { return static_cast<double *>(lE[c]); };
+    auto B = [&](int c) { return static_cast<const double *>(lB[c]); };
+    if (g.dims == 3)
+      k_adj_yee_b<double, 3><<<nb, 256, 0, st>>>(gidx<double>(g), absorb, 1.0 / g.dx[0], 1.0 / g.dx[1], 1.0 / g.dx[2],
+                                                 h, E(0), E(1), E(2), B(0), B(1), B(2));
+    else
+      k_adj_yee_b<double, 2><<<nb, 256, 0, st>>>(gidx<double>(g), absorb, 1.0 / g.dx[0], 1.0 / g.dx[1], 1.0 / g.dx[2],
+                                                 h, E(0), E(1), E(2), B(0), B(1), B(2));
+  } else {
+    auto E = [&](int c) { return static_cast<float *>(lE[c]); };
+    auto B = [&](int c) { return static_cast<const float *>(lB[c]); };
+    if (g.dims == 3)
+      k_adj_yee_b<float, 3><<<nb, 256, 0, st>>>(gidx<float>(g), absorb, (float)(1.0 / g.dx[0]), (float)(1.0 / g.dx[1]),
+                                                (float)(1.0 / g.dx[2]), (float)h, E(0), E(1), E(2), B(0), B(1), B(2));
+    else
+      k_adj_yee_b<float, 2><<<nb, 256, 0, st>>>(gidx<float>(g), absorb, (float)(1.0 / g.dx[0]), (float)(1.0 / g.dx[1]),
+                                                (float)(1.0 / g.dx[2]), (float)h, E(0), E(1), E(2), B(0), B(1), B(2));
+  }
+  return cudaGetLastError();
+}
+
+cudaError_t launch_adj_yee_e(const Grid &g, void *const lE[3], void *const lB[3], void *const lJ[3], double h,
+                             cudaStream_t st) {
+  const int nb = nblocks(g.ncell);
+  const int absorb = g.absorb_lo || g.absorb_hi;
+  if (g.prec == 1) {
+    auto E = [&](int c) { return static_cast<const double *>(lE[c]); };
+    auto B = [&](int c) { return static_cast<double *>(lB[c]); };
+    auto J = [&](int c) { return static_cast<double *>(lJ[c]); };
+    if (g.dims == 3)
+      k_adj_yee_e<double, 3><<<nb, 256, 0, st>>>(gidx<double>(g), absorb, 1.0 / g.dx[0], 1.0 / g.dx[1], 1.0 / g.dx[2],
+                                                 h, E(0), E(1), E(2), B(0), B(1), B(2), J(0), J(1), J(2));
+    else
+      k_adj_yee_e<double, 2><<<nb, 256, 0, st>>>(gidx<double>(g), absorb, 1.0 / g.dx[0], 1.0 / g.dx[1], 1.0 / g.dx[2],
+                                                 h, E(0), E(1), E(2), B(0), B(1), B(2), J(0), J(1), J(2));
+  } else {
+    auto E = [&](int c) { return static_cast<const float *>(lE[c]); };
+    auto B = [&](int c) { return static_cast<float *>(lB[c]); };
+    auto J = [&](int c) { return static_cast<float *>(lJ[c]); };
+    const float r0 = (float)(1.0 / g.dx[0]), r1 = (float)(1.0 / g.dx[1]), r2 = (float)(1.0 / g.dx[2]);
+    if (g.dims == 3)
+      k_adj_yee_e<float, 3><<<nb, 256, 0, st>>>(gidx<float>(g), absorb, r0, r1, r2, (float)h, E(0), E(1), E(2), B(0),
+                                                B(1), B(2), J(0), J(1), J(2));
+    else
+      k_adj_yee_e<float, 2><<<nb, 256, 0, st>>>(gidx<float>(g), absorb, r0, r1, r2, (float)h, E(0), E(1), E(2), B(0),
+                                                B(1), B(2), J(0), J(1), J(2));
+  }
+  return cudaGetLastError();
+}
+
+cudaError_t launch_adj_mur(const Grid &g, void *const lE[3], double *pend, const Laser &las, double t_old,
+                           double t_new, double *da0, cudaStream_t st) {
+  const int nb = nblocks(2LL * g.n[1] * g.n[2]);
+  if (g.prec == 1)
+    k_adj_mur<double><<<nb, 256, 0, st>>>(g.dims, g.n[0], g.n[1], g.n[2], g.dx[0], g.dx[1], g.dx[2], g.dt,
+                                          static_cast<double *>(lE[1]), static_cast<double *>(lE[2]), pend, las, t_old,
+                                          t_new, da0);
+  else
+    k_adj_mur<float><<<nb, 256, 0, st>>>(g.dims, g.n[0], g.n[1], g.n[2], g.dx[0], g.dx[1], g.dx[2], g.dt,
+                                         static_cast<float *>(lE[1]), static_cast<float *>(lE[2]), pend, las, t_old,
+                                         t_new, da0);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_adj_mur_pend(const Grid &g, void *const lE[3], const double *pend, cudaStream_t st) {
+  const int nb = nblocks(2LL * g.n[1] * g.n[2]);
+  if (g.prec == 1)
+    k_adj_mur_pend<double><<<nb, 256, 0, st>>>(g.n[0], g.n[1], g.n[2], static_cast<double *>(lE[1]),
+                                               static_cast<double *>(lE[2]), pend);
+  else
+    k_adj_mur_pend<float><<<nb, 256, 0, st>>>(g.n[0], g.n[1], g.n[2], static_cast<float *>(lE[1]),
+                                              static_cast<float *>(lE[2]), pend);
+  return cudaGetLastError();
+}
+
+template <class R>
+static cudaError_t adj_push_t(const Grid &g, const Particles &tp, const int64_t *d_count, int64_t nmax,
+                              void *const E[3], void *const B[3],
+                              void *const lJ[3], void *const lE[3], void *const lB[3], void *const lx[3],
+                              void *const lu[3], double *lw, int64_t id_cap, unsigned long long *err, double q,
+                              double m, cudaStream_t st) {
+  AdjPushArgs<R> a;
+  for (int d = 0; d < 3; ++d) {
+    a.n[d] = g.n[d];
+    a.off[d] = static_cast<const R *>(tp.off[d]);
+    a.u[d] = static_cast<const R *>(tp.u[d]);
+    a.E[d] = static_cast<const R *>(E[d]);
+    a.B[d] = static_cast<const R *>(B[d]);
+    a.lJ[d] = static_cast<const R *>(lJ[d]);
+    a.lE[d] = static_cast<R *>(lE[d]);
+    a.lB[d] = static_cast<R *>(lB[d]);
+    a.lx[d] = static_cast<R *>(lx[d]);
+    a.lu[d] = static_cast<R *>(lu[d]);
+    a.dtdx[d] = (R)(g.dt / g.dx[d]);
+    a.cxu[d] = (R)(-q * g.dx[d] / g.dt);
+  }
+  a.absorb = g.absorb_lo || g.absorb_hi;
+  a.cell = tp.cell;
+  a.w = static_cast<const R *>(tp.w);
+  a.id = tp.id;
+  a.d_count = d_count;
+  a.lw = lw;
+  a.id_cap = id_cap;
+  a.err = err;
+  a.qmh = (R)(q * g.dt / (2.0 * m));
+  a.q = (R)q;
+  k_adj_push2d<R><<<nblocks(nmax), 256, 0, st>>>(a);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_adj_push(const Grid &g, const Particles &tp, const int64_t *d_count, int64_t nmax,
+                            void *const E[3], void *const B[3], void *const lJ[3], void *const lE[3],
+                            void *const lB[3], void *const lx[3], void *const lu[3], double *lw, int64_t id_cap,
+                            unsigned long long *err, double q, double m, cudaStream_t st) {
+  if (g.dims != 2 || g.order != 2) return cudaErrorInvalidValue;
+  if (nmax <= 0) return cudaSuccess;
+  if (g.prec == 1)
+    return adj_push_t<double>(g, tp, d_count, nmax, E, B, lJ, lE, lB, lx, lu, lw, id_cap, err, q, m, st);
+  return adj_push_t<float>(g, tp, d_count, nmax, E, B, lJ, lE, lB, lx, lu, lw, id_cap, err, q, m, st);
+}
+
+cudaError_t launch_adj_seed(const Grid &g, const Particles &p, const int64_t *d_count, int64_t nmax, int c_lo,
+                            int c_hi, double dVm, void *const lu[3], double *lw, double *F, int64_t id_cap,
+                            unsigned long long *err, cudaStream_t st) {
+  if (nmax <= 0) return cudaSuccess;
+  const int nb = nblocks(nmax);
+  if (g.prec == 1) {
+    auto U = [&](int d) { return static_cast<const double *>(p.u[d]); };
+    auto L = [&](int d) { return static_cast<double *>(lu[d]); };
+    k_adj_seed<double><<<nb, 256, 0, st>>>(g.n[0], p.cell, U(0), U(1), U(2), static_cast<const double *>(p.w), p.id,
+                                           d_count, c_lo, c_hi, dVm, L(0), L(1), L(2), lw, F, id_cap, err);
+  } else {
+    auto U = [&](int d) { return static_cast<const float *>(p.u[d]); };
+    auto L = [&](int d) { return static_cast<float *>(lu[d]); };
+    k_adj_seed<float><<<nb, 256, 0, st>>>(g.n[0], p.cell, U(0), U(1), U(2), static_cast<const float *>(p.w), p.id,
+                                          d_count, c_lo, c_hi, dVm, L(0), L(1), L(2), lw, F, id_cap, err);
+  }
+  return cudaGetLastError();
+}
+
+}  // namespace pic

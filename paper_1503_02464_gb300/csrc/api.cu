@@ -42,6 +42,28 @@ struct TimerRec {
   cudaEvent_t a, b;
 };
 
+// Device copy of one species' particle state (and its slot count).
+struct PCopy {
+  Particles p{};
+  int64_t *count = nullptr;
+};
+
+// Full simulation state at a step boundary (checkpoint) or at the start of a
+// recorded step after its sort (tape entry).
+struct Snapshot {
+  PCopy sp[kMaxSpecies];
+  void *E[3] = {}, *B[3] = {};
+  int64_t step = -1;
+  int nsp = 0;  // species the buffers were sized for
+  bool allocated = false;
+};
+
+// Adjoint arrays of one species, indexed by particle id.
+struct SpeciesAdjoint {
+  void *lx[3] = {}, *lu[3] = {};
+  double *lw = nullptr;
+};
+
 std::string g_create_error;
 
 }  // namespace
@@ -69,6 +91,17 @@ struct pic_handle {
   bool profiling = false;
   std::vector<TimerRec> timers;
   std::vector<cudaEvent_t> event_pool;
+  // differentiable runs
+  std::vector<Snapshot> ckpt;
+  std::vector<Snapshot> tape;
+  int tape_len = 0;
+  bool taping = false;
+  bool adj_ready = false;
+  int64_t id_cap = 0;
+  void *lE[3] = {}, *lB[3] = {}, *lJ[3] = {};
+  double *pend = nullptr, *da0 = nullptr, *objF = nullptr;
+  unsigned long long *adj_err = nullptr;
+  SpeciesAdjoint adj[kMaxSpecies];
 };
 
 namespace {
@@ -189,6 +222,94 @@ int64_t read_count(pic_handle *h, Species &s) {
   cudaStreamSynchronize(h->st);
   s.h_count = n;
   return n;
+}
+
+void free_snapshot(Snapshot &sn);
+
+cudaError_t alloc_snapshot(pic_handle *h, Snapshot &sn) {
+  if (sn.allocated && sn.nsp == h->nsp) return cudaSuccess;
+  if (sn.allocated) free_snapshot(sn);
+  const size_t fb = (size_t)h->g.ncell * h->rsize;
+  cudaError_t e = cudaSuccess;
+  for (int d = 0; d < 3 && e == cudaSuccess; ++d) {
+    e = cudaMalloc(&sn.E[d], fb);
+    if (e == cudaSuccess) e = cudaMalloc(&sn.B[d], fb);
+  }
+  for (int i = 0; i < h->nsp && e == cudaSuccess; ++i) {
+    e = alloc_particles(sn.sp[i].p, h->sp[i].slots, h->rsize, h->g.dims);
+    if (e == cudaSuccess) e = cudaMalloc(&sn.sp[i].count, sizeof(int64_t));
+  }
+  sn.allocated = e == cudaSuccess;
+  sn.nsp = h->nsp;
+  return e;
+}
+
+void free_snapshot(Snapshot &sn) {
+  for (int d = 0; d < 3; ++d) {
+    cudaFree(sn.E[d]);
+    cudaFree(sn.B[d]);
+  }
+  for (int i = 0; i < kMaxSpecies; ++i) {
+    free_particles(sn.sp[i].p);
+    cudaFree(sn.sp[i].count);
+  }
+  sn = Snapshot{};
+}
+
+cudaError_t copy_particles(pic_handle *h, const Particles &dst, int64_t *dcount, const Particles &src,
+                           const int64_t *scount, int64_t slots) {
+  const size_t n = (size_t)slots;
+  const size_t rs = h->rsize;
+  cudaError_t e = cudaMemcpyAsync(dst.cell, src.cell, n * sizeof(int32_t), cudaMemcpyDeviceToDevice, h->st);
+  for (int d = 0; d < 3 && e == cudaSuccess; ++d) {
+    if (d < h->g.dims) e = cudaMemcpyAsync(dst.off[d], src.off[d], n * rs, cudaMemcpyDeviceToDevice, h->st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(dst.u[d], src.u[d], n * rs, cudaMemcpyDeviceToDevice, h->st);
+  }
+  if (e == cudaSuccess) e = cudaMemcpyAsync(dst.w, src.w, n * rs, cudaMemcpyDeviceToDevice, h->st);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(dst.id, src.id, n * sizeof(uint32_t), cudaMemcpyDeviceToDevice, h->st);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(dcount, scount, sizeof(int64_t), cudaMemcpyDeviceToDevice, h->st);
+  return e;
+}
+
+// Copy the live state (current particle buffers, E, B, step) into sn.
+cudaError_t save_snapshot(pic_handle *h, Snapshot &sn) {
+  cudaError_t e = alloc_snapshot(h, sn);
+  const size_t fb = (size_t)h->g.ncell * h->rsize;
+  for (int d = 0; d < 3 && e == cudaSuccess; ++d) {
+    e = cudaMemcpyAsync(sn.E[d], h->E[d], fb, cudaMemcpyDeviceToDevice, h->st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(sn.B[d], h->B[d], fb, cudaMemcpyDeviceToDevice, h->st);
+  }
+  for (int i = 0; i < h->nsp && e == cudaSuccess; ++i) {
+    Species &s = h->sp[i];
+    e = copy_particles(h, sn.sp[i].p, sn.sp[i].count, s.buf[s.cur], s.d_count, s.slots);
+  }
+  sn.step = h->step;
+  return e;
+}
+
+void free_adjoint(pic_handle *h) {
+  for (int d = 0; d < 3; ++d) {
+    cudaFree(h->lE[d]);
+    cudaFree(h->lB[d]);
+    cudaFree(h->lJ[d]);
+    h->lE[d] = h->lB[d] = h->lJ[d] = nullptr;
+  }
+  cudaFree(h->pend);
+  cudaFree(h->da0);
+  cudaFree(h->objF);
+  cudaFree(h->adj_err);
+  h->pend = h->da0 = h->objF = nullptr;
+  h->adj_err = nullptr;
+  for (int i = 0; i < kMaxSpecies; ++i) {
+    for (int d = 0; d < 3; ++d) {
+      cudaFree(h->adj[i].lx[d]);
+      cudaFree(h->adj[i].lu[d]);
+    }
+    cudaFree(h->adj[i].lw);
+    h->adj[i] = SpeciesAdjoint{};
+  }
+  h->adj_ready = false;
+  h->id_cap = 0;
 }
 
 }  // namespace
@@ -361,6 +482,9 @@ int pic_destroy(pic_handle *h) {
     cudaEventDestroy(t.b);
   }
   for (auto e : h->event_pool) cudaEventDestroy(e);
+  for (auto &sn : h->ckpt) free_snapshot(sn);
+  for (auto &sn : h->tape) free_snapshot(sn);
+  free_adjoint(h);
   delete h;
   return PIC_OK;
 }
@@ -485,6 +609,13 @@ int pic_step(pic_handle *h, int nsteps) {
         int r = sort_species(h, s);
         if (r) return r;
       }
+    }
+    if (h->taping) {
+      if (h->tape_len < (int)h->tape.size()) {
+        CK(h, save_snapshot(h, h->tape[h->tape_len]), "tape record");
+        h->tape_len++;
+      }
+      if (h->tape_len >= (int)h->tape.size()) h->taping = false;
     }
     {
       Timed tm(h, pic::KC_ZEROJ);
@@ -682,6 +813,167 @@ int pic_timings(pic_handle *h, double *ms, int64_t *launches, int nmax, int *ncl
     if (launches) launches[i] = cnt[i];
   }
   if (ncls) *ncls = n;
+  return PIC_OK;
+}
+
+int pic_checkpoint(pic_handle *h, int slot) {
+  if (!h || slot < 0 || slot > 4096) return fail(h, PIC_EINVAL, "bad checkpoint slot");
+  if ((int)h->ckpt.size() <= slot) h->ckpt.resize(slot + 1);
+  cudaError_t e = save_snapshot(h, h->ckpt[slot]);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return e == cudaErrorMemoryAllocation ? fail(h, PIC_ENOMEM, "checkpoint allocation failed")
+                                          : cuda_fail(h, e, "checkpoint");
+  }
+  return PIC_OK;
+}
+
+int pic_restore(pic_handle *h, int slot) {
+  if (!h || slot < 0 || slot >= (int)h->ckpt.size() || !h->ckpt[slot].allocated)
+    return fail(h, PIC_EINVAL, "no such checkpoint");
+  Snapshot &sn = h->ckpt[slot];
+  const size_t fb = (size_t)h->g.ncell * h->rsize;
+  for (int d = 0; d < 3; ++d) {
+    CK(h, cudaMemcpyAsync(h->E[d], sn.E[d], fb, cudaMemcpyDeviceToDevice, h->st), "restore");
+    CK(h, cudaMemcpyAsync(h->B[d], sn.B[d], fb, cudaMemcpyDeviceToDevice, h->st), "restore");
+  }
+  for (int i = 0; i < h->nsp; ++i) {
+    Species &s = h->sp[i];
+    CK(h, copy_particles(h, s.buf[s.cur], s.d_count, sn.sp[i].p, sn.sp[i].count, s.slots), "restore");
+    s.need_sort = true;
+  }
+  h->step = sn.step;
+  return PIC_OK;
+}
+
+int pic_tape_begin(pic_handle *h, int nsteps) {
+  if (!h || nsteps < 0 || nsteps > 100000) return fail(h, PIC_EINVAL, "bad tape length");
+  while ((int)h->tape.size() > nsteps) {
+    free_snapshot(h->tape.back());
+    h->tape.pop_back();
+  }
+  h->tape.resize(nsteps);
+  for (int k = 0; k < nsteps; ++k) {
+    cudaError_t e = alloc_snapshot(h, h->tape[k]);
+    if (e != cudaSuccess) {
+      cudaGetLastError();
+      return fail(h, PIC_ENOMEM, "tape allocation failed");
+    }
+  }
+  h->tape_len = 0;
+  h->taping = nsteps > 0;
+  return PIC_OK;
+}
+
+int pic_adjoint_begin(pic_handle *h, int64_t id_capacity) {
+  if (!h) return fail(h, PIC_EINVAL, "NULL handle");
+  if (h->g.dims != 2 || h->g.order != 2)
+    return fail(h, PIC_EINVAL, "adjoint kernels exist for 2D3V with the TSC shape only");
+  if (id_capacity <= 0 || id_capacity > 0x7fffffffLL) return fail(h, PIC_EINVAL, "bad id capacity");
+  if (!h->adj_ready || h->id_cap != id_capacity) {
+    free_adjoint(h);
+    const size_t fb = (size_t)h->g.ncell * h->rsize;
+    const size_t ib = (size_t)id_capacity * h->rsize;
+    bool ok = true;
+    for (int d = 0; d < 3 && ok; ++d)
+      ok = cudaMalloc(&h->lE[d], fb) == cudaSuccess && cudaMalloc(&h->lB[d], fb) == cudaSuccess &&
+           cudaMalloc(&h->lJ[d], fb) == cudaSuccess;
+    ok = ok && cudaMalloc(&h->pend, 8 * sizeof(double) * (size_t)h->g.n[1] * h->g.n[2]) == cudaSuccess &&
+         cudaMalloc(&h->da0, sizeof(double)) == cudaSuccess && cudaMalloc(&h->objF, sizeof(double)) == cudaSuccess &&
+         cudaMalloc(&h->adj_err, sizeof(unsigned long long)) == cudaSuccess;
+    for (int i = 0; i < h->nsp && ok; ++i) {
+      for (int d = 0; d < 3 && ok; ++d)
+        ok = cudaMalloc(&h->adj[i].lx[d], ib) == cudaSuccess && cudaMalloc(&h->adj[i].lu[d], ib) == cudaSuccess;
+      ok = ok && cudaMalloc(&h->adj[i].lw, (size_t)id_capacity * sizeof(double)) == cudaSuccess;
+    }
+    if (!ok) {
+      free_adjoint(h);
+      cudaGetLastError();
+      return fail(h, PIC_ENOMEM, "adjoint allocation failed");
+    }
+    h->id_cap = id_capacity;
+    h->adj_ready = true;
+  }
+  const size_t fb = (size_t)h->g.ncell * h->rsize;
+  const size_t ib = (size_t)h->id_cap * h->rsize;
+  for (int d = 0; d < 3; ++d) {
+    CK(h, cudaMemsetAsync(h->lE[d], 0, fb, h->st), "zero");
+    CK(h, cudaMemsetAsync(h->lB[d], 0, fb, h->st), "zero");
+    CK(h, cudaMemsetAsync(h->lJ[d], 0, fb, h->st), "zero");
+  }
+  for (int i = 0; i < h->nsp; ++i) {
+    for (int d = 0; d < 3; ++d) {
+      CK(h, cudaMemsetAsync(h->adj[i].lx[d], 0, ib, h->st), "zero");
+      CK(h, cudaMemsetAsync(h->adj[i].lu[d], 0, ib, h->st), "zero");
+    }
+    CK(h, cudaMemsetAsync(h->adj[i].lw, 0, (size_t)h->id_cap * sizeof(double), h->st), "zero");
+  }
+  CK(h, cudaMemsetAsync(h->da0, 0, sizeof(double), h->st), "zero");
+  CK(h, cudaMemsetAsync(h->objF, 0, sizeof(double), h->st), "zero");
+  CK(h, cudaMemsetAsync(h->adj_err, 0, sizeof(unsigned long long), h->st), "zero");
+  return PIC_OK;
+}
+
+int pic_adjoint_seed_kinetic(pic_handle *h, int species, int col_lo, int col_hi, double *F) {
+  if (!h || !h->adj_ready) return fail(h, PIC_EINVAL, "call pic_adjoint_begin first");
+  if (species < 0 || species >= h->nsp) return fail(h, PIC_EINVAL, "bad species index");
+  if (col_lo < 0 || col_hi > h->g.n[0] || col_lo >= col_hi) return fail(h, PIC_EINVAL, "bad column range");
+  Species &s = h->sp[species];
+  const double dVm = h->g.dx[0] * h->g.dx[1] * h->g.dx[2] * s.m;
+  CK(h, cudaMemsetAsync(h->objF, 0, sizeof(double), h->st), "zero");
+  CK(h,
+     pic::launch_adj_seed(h->g, s.buf[s.cur], s.d_count, s.slots, col_lo, col_hi, dVm, h->adj[species].lu,
+                          h->adj[species].lw, h->objF, h->id_cap, h->adj_err, h->st),
+     "adjoint seed");
+  h->launches++;
+  double v = 0;
+  unsigned long long err = 0;
+  CK(h, cudaMemcpyAsync(&v, h->objF, sizeof(double), cudaMemcpyDeviceToHost, h->st), "D2H");
+  CK(h, cudaMemcpyAsync(&err, h->adj_err, sizeof(err), cudaMemcpyDeviceToHost, h->st), "D2H");
+  CK(h, cudaStreamSynchronize(h->st), "sync");
+  if (err) return fail(h, PIC_EINVAL, "a particle id is not below the adjoint id capacity");
+  if (F) *F = v;
+  return PIC_OK;
+}
+
+int pic_adjoint_step(pic_handle *h, int nsteps) {
+  if (!h || !h->adj_ready) return fail(h, PIC_EINVAL, "call pic_adjoint_begin first");
+  if (nsteps < 0 || nsteps > h->tape_len) return fail(h, PIC_EINVAL, "more adjoint steps than recorded steps");
+  const bool walls = h->g.absorb_lo || h->g.absorb_hi;
+  pic::Laser unit = h->laser;
+  unit.a0 = 1.0;
+  for (int t = 0; t < nsteps; ++t) {
+    Snapshot &en = h->tape[h->tape_len - 1];
+    const double t_old = en.step * h->g.dt, t_new = (en.step + 1) * h->g.dt;
+    CK(h, pic::launch_adj_yee_b(h->g, h->lE, h->lB, 0.5 * h->g.dt, h->st), "adjoint B half");
+    if (walls) CK(h, pic::launch_adj_mur(h->g, h->lE, h->pend, unit, t_old, t_new, h->da0, h->st), "adjoint Mur");
+    CK(h, pic::launch_adj_yee_e(h->g, h->lE, h->lB, h->lJ, h->g.dt, h->st), "adjoint E");
+    if (walls) CK(h, pic::launch_adj_mur_pend(h->g, h->lE, h->pend, h->st), "adjoint Mur");
+    CK(h, pic::launch_adj_yee_b(h->g, h->lE, h->lB, 0.5 * h->g.dt, h->st), "adjoint B half");
+    h->launches += walls ? 5 : 3;
+    for (int i = 0; i < h->nsp; ++i) {
+      Species &s = h->sp[i];
+      CK(h,
+         pic::launch_adj_push(h->g, en.sp[i].p, en.sp[i].count, s.slots, en.E, en.B, h->lJ, h->lE, h->lB,
+                              h->adj[i].lx, h->adj[i].lu, h->adj[i].lw, h->id_cap, h->adj_err, s.q, s.m, h->st),
+         "adjoint push");
+      h->launches++;
+    }
+    h->tape_len--;
+  }
+  return PIC_OK;
+}
+
+int pic_grad(pic_handle *h, double *d_a0, int species, double *d_w, int mem_kind) {
+  if (!h || !h->adj_ready) return fail(h, PIC_EINVAL, "call pic_adjoint_begin first");
+  if (d_w && (species < 0 || species >= h->nsp)) return fail(h, PIC_EINVAL, "bad species index");
+  const cudaMemcpyKind kind = mem_kind == PIC_MEM_HOST ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice;
+  if (d_a0) CK(h, cudaMemcpyAsync(d_a0, h->da0, sizeof(double), kind, h->st), "grad copy");
+  if (d_w) CK(h, cudaMemcpyAsync(d_w, h->adj[species].lw, (size_t)h->id_cap * sizeof(double), kind, h->st), "grad copy");
+  unsigned long long err = 0;
+  CK(h, cudaMemcpyAsync(&err, h->adj_err, sizeof(err), cudaMemcpyDeviceToHost, h->st), "D2H");
+  CK(h, cudaStreamSynchronize(h->st), "sync");
+  if (err) return fail(h, PIC_EINVAL, "a particle id is not below the adjoint id capacity");
   return PIC_OK;
 }
 

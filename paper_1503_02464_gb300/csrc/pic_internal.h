@@ -111,4 +111,23 @@ cudaError_t launch_field_diag(const Grid &g, void *const E[3], void *const B[3],
 cudaError_t launch_particle_diag(const Grid &g, const Particles &p, const int64_t *d_count, int64_t nmax, double m,
                                  double *out, cudaStream_t st);
 
+// ---- adjoint (adjoint.cu) ----
+cudaError_t launch_adj_yee_b(const Grid &g, void *const lE[3], void *const lB[3], double h, cudaStream_t st);
+cudaError_t launch_adj_yee_e(const Grid &g, void *const lE[3], void *const lB[3], void *const lJ[3], double h,
+                             cudaStream_t st);
+cudaError_t launch_adj_mur(const Grid &g, void *const lE[3], double *pend, const Laser &las_unit, double t_old,
+                           double t_new, double *da0, cudaStream_t st);
+cudaError_t launch_adj_mur_pend(const Grid &g, void *const lE[3], const double *pend, cudaStream_t st);
+// Per-particle adjoint of one recorded step (2D3V TSC only): tp/d_count
+// is the particle state at the start of the step, E/B the fields gathered.
+cudaError_t launch_adj_push(const Grid &g, const Particles &tp, const int64_t *d_count, int64_t nmax,
+                            void *const E[3], void *const B[3], void *const lJ[3], void *const lE[3],
+                            void *const lB[3], void *const lx[3], void *const lu[3], double *lw, int64_t id_cap,
+                            unsigned long long *err, double q, double m, cudaStream_t st);
+// Objective sum over particles with x column in [c_lo, c_hi) of
+// w dV m (gamma - 1) into *F; seeds lam_u and dF/dw (by id).
+cudaError_t launch_adj_seed(const Grid &g, const Particles &p, const int64_t *d_count, int64_t nmax, int c_lo,
+                            int c_hi, double dVm, void *const lu[3], double *lw, double *F, int64_t id_cap,
+                            unsigned long long *err, cudaStream_t st);
+
 }  // namespace pic

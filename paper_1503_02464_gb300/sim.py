@@ -194,3 +194,28 @@ class Simulation:
 
     def launch_count(self) -> int:
         return capi.pic_launch_count(self.h)
+
+    # -- differentiable runs (2D3V TSC)
+    def checkpoint(self, slot: int) -> None:
+        capi.pic_checkpoint(self.h, slot)
+
+    def restore(self, slot: int) -> None:
+        capi.pic_restore(self.h, slot)
+
+    def tape_begin(self, nsteps: int) -> None:
+        capi.pic_tape_begin(self.h, nsteps)
+
+    def adjoint_begin(self, id_capacity: int) -> None:
+        capi.pic_adjoint_begin(self.h, id_capacity)
+
+    def adjoint_seed_kinetic(self, species: int, col_lo: int, col_hi: int) -> float:
+        return capi.pic_adjoint_seed_kinetic(self.h, species, col_lo, col_hi)
+
+    def adjoint_step(self, nsteps: int) -> None:
+        capi.pic_adjoint_step(self.h, nsteps)
+
+    def grad(self, species: int, id_capacity: int):
+        """(dF/da0, dF/dw by particle id) after a reverse sweep."""
+        dw = np.zeros(id_capacity, dtype=np.float64)
+        da0 = capi.pic_grad(self.h, species, dw.ctypes.data, capi.PIC_MEM_HOST)
+        return da0, dw
