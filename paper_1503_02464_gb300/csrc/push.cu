@@ -183,18 +183,23 @@ template <> struct WinAcc<double> {
 };
 
 // Esirkepov deposit into the shared J window (compile-time strides).
-// base: window index of the stencil's first node.
+// base: window index of the stencil's first node.  The last running sum of
+// each axis is -DS[last] (the running sum over the whole stencil vanishes),
+// so it is exactly zero for a particle that keeps its nearest node on that
+// axis.  lx, ly, lz: some active lane of the warp uses the last stencil node
+// of that axis (warp-uniform); otherwise every contribution on that outer
+// shell is zero and is skipped with a uniform branch.
 template <class R, int ORDER, int DIM, int SY, int SZ>
 __device__ __forceinline__ void deposit_win(const WinAcc<R> &acc, int base, const DepositAxis<R, ORDER> &X,
                                             const DepositAxis<R, ORDER> &Y, const DepositAxis<R, ORDER> &Z, R cx,
-                                            R cy, R cz, R qwvz) {
+                                            R cy, R cz, R qwvz, bool lx, bool ly, bool lz) {
   constexpr int NW = ORDER + 2;
   constexpr int M = NW - 1;
   R Px[M], Py[M], Pz[M];
   {
     R a = R(0), b = R(0), c = R(0);
 #pragma unroll
-    for (int k = 0; k < M; ++k) {
+    for (int k = 0; k < M - 1; ++k) {
       a += X.DS[k];
       b += Y.DS[k];
       c += Z.DS[k];
@@ -202,6 +207,9 @@ __device__ __forceinline__ void deposit_win(const WinAcc<R> &acc, int base, cons
       Py[k] = cy * b;
       Pz[k] = cz * c;
     }
+    Px[M - 1] = -cx * X.DS[NW - 1];
+    Py[M - 1] = -cy * Y.DS[NW - 1];
+    Pz[M - 1] = -cz * Z.DS[NW - 1];
   }
   if (DIM == 3) {
     // Jx(i+1/2,j,k) += Px[i] (S0y S0z + DSy S0z/2 + S0y DSz/2 + DSy DSz/3), cyclic for y, z
@@ -214,30 +222,47 @@ __device__ __forceinline__ void deposit_win(const WinAcc<R> &acc, int base, cons
       tx[k] = R(0.5) * X.S0[k] + X.DS[k] * R(1.0 / 3.0);
     }
 #pragma unroll
-    for (int c = 0; c < NW; ++c)
+    for (int c = 0; c < NW; ++c) {
+      if (c == NW - 1 && !lz) continue;
 #pragma unroll
       for (int b = 0; b < NW; ++b) {
+        if (b == NW - 1 && !ly) continue;
         const R br = Y.S0[b] * hz[c] + Y.DS[b] * tz[c];
 #pragma unroll
-        for (int a = 0; a < M; ++a) acc.add(0, base + c * SZ + b * SY + a, Px[a] * br);
+        for (int a = 0; a < M; ++a) {
+          if (a == M - 1 && !lx) continue;
+          acc.add(0, base + c * SZ + b * SY + a, Px[a] * br);
+        }
       }
+    }
 #pragma unroll
-    for (int c = 0; c < NW; ++c)
+    for (int c = 0; c < NW; ++c) {
+      if (c == NW - 1 && !lz) continue;
 #pragma unroll
       for (int a = 0; a < NW; ++a) {
+        if (a == NW - 1 && !lx) continue;
         const R br = Z.S0[c] * hx[a] + Z.DS[c] * tx[a];
 #pragma unroll
-        for (int b = 0; b < M; ++b) acc.add(1, base + c * SZ + b * SY + a, Py[b] * br);
+        for (int b = 0; b < M; ++b) {
+          if (b == M - 1 && !ly) continue;
+          acc.add(1, base + c * SZ + b * SY + a, Py[b] * br);
+        }
       }
+    }
 #pragma unroll
     for (int b = 0; b < NW; ++b) {
+      if (b == NW - 1 && !ly) continue;
       const R hy = Y.S0[b] + R(0.5) * Y.DS[b];
       const R ty = R(0.5) * Y.S0[b] + Y.DS[b] * R(1.0 / 3.0);
 #pragma unroll
       for (int a = 0; a < NW; ++a) {
+        if (a == NW - 1 && !lx) continue;
         const R br = X.S0[a] * hy + X.DS[a] * ty;
 #pragma unroll
-        for (int c = 0; c < M; ++c) acc.add(2, base + c * SZ + b * SY + a, Pz[c] * br);
+        for (int c = 0; c < M; ++c) {
+          if (c == M - 1 && !lz) continue;
+          acc.add(2, base + c * SZ + b * SY + a, Pz[c] * br);
+        }
       }
     }
   } else {
@@ -245,18 +270,29 @@ __device__ __forceinline__ void deposit_win(const WinAcc<R> &acc, int base, cons
     //       Jz = q w vz (S0x S0y + DSx S0y/2 + S0x DSy/2 + DSx DSy/3)
 #pragma unroll
     for (int b = 0; b < NW; ++b) {
+      if (b == NW - 1 && !ly) continue;
       const R hy = Y.S0[b] + R(0.5) * Y.DS[b];
       const R ty = R(0.5) * Y.S0[b] + Y.DS[b] * R(1.0 / 3.0);
 #pragma unroll
-      for (int a = 0; a < M; ++a) acc.add(0, base + b * SY + a, Px[a] * hy);
+      for (int a = 0; a < M; ++a) {
+        if (a == M - 1 && !lx) continue;
+        acc.add(0, base + b * SY + a, Px[a] * hy);
+      }
 #pragma unroll
-      for (int a = 0; a < NW; ++a) acc.add(2, base + b * SY + a, qwvz * (X.S0[a] * hy + X.DS[a] * ty));
+      for (int a = 0; a < NW; ++a) {
+        if (a == NW - 1 && !lx) continue;
+        acc.add(2, base + b * SY + a, qwvz * (X.S0[a] * hy + X.DS[a] * ty));
+      }
     }
 #pragma unroll
     for (int a = 0; a < NW; ++a) {
+      if (a == NW - 1 && !lx) continue;
       const R hx = X.S0[a] + R(0.5) * X.DS[a];
 #pragma unroll
-      for (int b = 0; b < M; ++b) acc.add(1, base + b * SY + a, Py[b] * hx);
+      for (int b = 0; b < M; ++b) {
+        if (b == M - 1 && !ly) continue;
+        acc.add(1, base + b * SY + a, Py[b] * hx);
+      }
     }
   }
 }
@@ -474,8 +510,13 @@ __global__ void __launch_bounds__(kThreads, sizeof(R) == 4 ? 2 : 1) k_push(const
           const int jb = (l[0] + dx.rel + oJ) + (l[1] + dy.rel + oJ) * G::JX +
                          (DIM == 3 ? (l[2] + dz.rel + oJ) * G::JX * G::JY : 0);
           const R ws = wq * acc.scale;  // fixed-point units folded into the factors
+          // does some lane of this warp use the last stencil node of an axis?
+          const unsigned act = __activemask();
+          const bool lx = __any_sync(act, dx.S0[G::NW - 1] != R(0) || dx.DS[G::NW - 1] != R(0));
+          const bool ly = __any_sync(act, dy.S0[G::NW - 1] != R(0) || dy.DS[G::NW - 1] != R(0));
+          const bool lz = DIM == 3 && __any_sync(act, dz.S0[G::NW - 1] != R(0) || dz.DS[G::NW - 1] != R(0));
           deposit_win<R, ORDER, DIM, G::JX, G::JX * G::JY>(acc, jb, dx, dy, dz, a.jfac[0] * ws, a.jfac[1] * ws,
-                                                            a.jfac[2] * ws, a.qz * ws * u[2] * ig);
+                                                            a.jfac[2] * ws, a.qz * ws * u[2] * ig, lx, ly, lz);
 
           // ---- new state back into the staging slot ----
           if (outside_walls<R>(a.absorb, ci[0] + s[0], fn[0], a.n[0])) {
@@ -602,10 +643,11 @@ __global__ void __launch_bounds__(kThreads) k_push_escaped(const PushArgs<R> a) 
 #pragma unroll
     for (int d = 0; d < 3; ++d) {
       R run = R(0);
-      for (int k = 0; k < NW - 1; ++k) {
+      for (int k = 0; k < NW - 2; ++k) {
         run += da[d].DS[k];
         P[d][k] = a.jfac[d] * wq * run;
       }
+      P[d][NW - 2] = -a.jfac[d] * wq * da[d].DS[NW - 1];  // the full running sum vanishes
     }
     int gx[NW], gy[NW], gz[NW];
     for (int k = 0; k < NW; ++k) {
