@@ -319,9 +319,14 @@ def run_gpu(args, rank: int, world: int, local: int):
             sim.load(isp, h.arrays)           # pinned host -> device inside the call
         if wl.neutralize:
             sim.neutralize()
+        sim.sync()
+        t_load = time.perf_counter() - t0
+        t_diag = 0.0
         for _ in range(args.steps):
             sim.step(1)
-            dg = sim.diag()                   # FP64 diagnostics read back every step
+            td = time.perf_counter()
+            dg = sim.energy()                 # FP64 energies read back every step
+            t_diag += time.perf_counter() - td
         sim.sync()
         t1 = time.perf_counter()
         _barrier(world)
@@ -331,11 +336,12 @@ def run_gpu(args, rank: int, world: int, local: int):
         for ptr in regs:
             cudart.cudaHostUnregister(ptr)
         h2d = sum(sum(v.nbytes for v in h.arrays.values()) for h in host)
-        d2h = 12 * 8
+        d2h = 5 * 8
         e2e = {"value": world * npart * args.steps / e2e_s, "unit": "particle-steps/s",
                "h2d_bytes_per_step": int(h2d / args.steps), "d2h_bytes_per_step": d2h,
                "pinned": len(regs) == sum(len(h.arrays) for h in host),
-               "note": "load from pinned host + per-step pic_step + pic_diag read-back, wall clock"}
+               "load_s": t_load, "diag_wall_ms_per_step": 1e3 * t_diag / args.steps,
+               "note": "load from pinned host + per-step pic_step + pic_energy read-back, wall clock"}
 
     # ---------------- CPU oracle baseline (rank 0, N = 1 only)
     cpu = None

@@ -127,6 +127,15 @@ typedef struct {
   int64_t step;           /* completed time steps                                 */
 } pic_diag_t;
 
+/* Per-step energy read-back (FP64 sums of storage-precision terms). */
+typedef struct {
+  double energy_e;        /* 1/2 sum E^2 dV                                       */
+  double energy_b;        /* 1/2 sum B^2 dV                                       */
+  double energy_kinetic;  /* sum w dV m (gamma - 1), all species                  */
+  int64_t n_alive;        /* live macro-particles, all species                    */
+  int64_t step;           /* completed time steps                                 */
+} pic_energy_t;
+
 typedef struct pic_handle pic_handle;
 
 /* Create a simulation.  Validates sizes, shape order, precision, boundary
@@ -191,6 +200,11 @@ int pic_particles(pic_handle *h, int species, double *x, double *y, double *z, d
 /* FP64 diagnostics of the current state.  Synchronises; reports device-side
  * errors (PIC_EOVERFLOW, PIC_ENAN). */
 int pic_diag(pic_handle *h, pic_diag_t *out);
+
+/* The field and kinetic energies of the current state without the charge
+ * density, Gauss and continuity checks of pic_diag (so it costs one pass
+ * over the field arrays and one over the particles).  Synchronises. */
+int pic_energy(pic_handle *h, pic_energy_t *out);
 
 /* Wait for all enqueued work and report latched device errors. */
 int pic_sync(pic_handle *h);

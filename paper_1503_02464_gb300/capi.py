@@ -24,7 +24,7 @@ ERROR_NAMES = {0: "PIC_OK", 1: "PIC_EINVAL", 2: "PIC_ECOURANT", 3: "PIC_ENOMEM",
 # every symbol include/pic.h declares
 EXPORTED = ["pic_create", "pic_destroy", "pic_last_error", "pic_add_species", "pic_load_particles",
             "pic_neutralize", "pic_step", "pic_fields", "pic_set_field", "pic_num_particles", "pic_particles",
-            "pic_diag", "pic_sync", "pic_profile", "pic_timings", "pic_launch_count", "pic_checkpoint",
+            "pic_diag", "pic_energy", "pic_sync", "pic_profile", "pic_timings", "pic_launch_count", "pic_checkpoint",
             "pic_restore", "pic_tape_begin", "pic_adjoint_begin", "pic_adjoint_seed_kinetic", "pic_adjoint_step",
             "pic_grad", "pic_field_energy_noalloc"]
 
@@ -48,6 +48,14 @@ class pic_diag_t(ctypes.Structure):
                 ("energy_kinetic", ctypes.c_double), ("charge", ctypes.c_double), ("gauss_max", ctypes.c_double),
                 ("continuity_max", ctypes.c_double), ("n_alive", ctypes.c_int64), ("n_escaped", ctypes.c_int64),
                 ("n_clamped", ctypes.c_int64), ("n_absorbed", ctypes.c_int64), ("step", ctypes.c_int64)]
+
+    def as_dict(self) -> dict:
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+class pic_energy_t(ctypes.Structure):
+    _fields_ = [("energy_e", ctypes.c_double), ("energy_b", ctypes.c_double), ("energy_kinetic", ctypes.c_double),
+                ("n_alive", ctypes.c_int64), ("step", ctypes.c_int64)]
 
     def as_dict(self) -> dict:
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -94,6 +102,7 @@ def load(build_if_missing: bool = True) -> ctypes.CDLL:
         "pic_particles": ([hp, ctypes.c_int] + [vp] * 9 + [ctypes.c_int], ctypes.c_int),
         "pic_diag": ([hp, ctypes.POINTER(pic_diag_t)], ctypes.c_int),
         "pic_sync": ([hp], ctypes.c_int),
+        "pic_energy": ([hp, ctypes.POINTER(pic_energy_t)], ctypes.c_int),
         "pic_profile": ([hp, ctypes.c_int], ctypes.c_int),
         "pic_timings": ([hp, dp, ctypes.POINTER(ctypes.c_int64), ctypes.c_int, ctypes.POINTER(ctypes.c_int)],
                         ctypes.c_int),
@@ -176,6 +185,12 @@ def pic_particles(h, species: int, x, y, z, ux, uy, uz, w, ids, alive, mem_kind:
 def pic_diag(h) -> dict:
     d = pic_diag_t()
     check(h, load().pic_diag(h, ctypes.byref(d)))
+    return d.as_dict()
+
+
+def pic_energy(h) -> dict:
+    d = pic_energy_t()
+    check(h, load().pic_energy(h, ctypes.byref(d)))
     return d.as_dict()
 
 

@@ -210,7 +210,10 @@ int compute_rho(pic_handle *h, double *rho) {
   CK(h, cudaMemcpyAsync(rho, h->rho_bg, sizeof(double) * h->g.ncell, cudaMemcpyDeviceToDevice, h->st), "rho init");
   for (int i = 0; i < h->nsp; ++i) {
     Species &s = h->sp[i];
-    CK(h, pic::launch_rho(h->g, s.buf[s.cur], s.d_count, s.slots, s.q, rho, h->st), "rho deposit");
+    if (s.need_sort)  // slots not grouped by tile yet (just loaded)
+      CK(h, pic::launch_rho(h->g, s.buf[s.cur], s.d_count, s.slots, s.q, rho, h->st), "rho deposit");
+    else
+      CK(h, pic::launch_rho_tiled(h->g, s.buf[s.cur], s.tile_start, s.q, rho, h->st), "rho deposit");
     h->launches++;
   }
   return PIC_OK;
@@ -776,6 +779,29 @@ int pic_diag(pic_handle *h, pic_diag_t *out) {
   out->step = h->step;
   if (c.error) return fail(h, PIC_EOVERFLOW, "device-side error flags set");
   if (red[5] > 0 || red[10] > 0) return fail(h, PIC_ENAN, "non-finite field or momentum values");
+  return PIC_OK;
+}
+
+int pic_energy(pic_handle *h, pic_energy_t *out) {
+  if (!h || !out) return fail(h, PIC_EINVAL, "NULL argument");
+  CK(h, cudaMemsetAsync(h->red, 0, 16 * sizeof(double), h->st), "memset");
+  CK(h, pic::launch_field_energy(h->g, h->E, h->B, h->red, h->st), "field energy");
+  h->launches++;
+  for (int i = 0; i < h->nsp; ++i) {
+    Species &s = h->sp[i];
+    CK(h, pic::launch_particle_diag(h->g, s.buf[s.cur], s.d_count, s.slots, s.m, h->red + 8, h->st), "part diag");
+    h->launches++;
+  }
+  double red[16];
+  CK(h, cudaMemcpyAsync(red, h->red, sizeof red, cudaMemcpyDeviceToHost, h->st), "D2H");
+  CK(h, cudaStreamSynchronize(h->st), "energy sync");
+  const double dV = h->g.dx[0] * h->g.dx[1] * h->g.dx[2];
+  out->energy_e = 0.5 * red[0] * dV;
+  out->energy_b = 0.5 * red[1] * dV;
+  out->energy_kinetic = red[8] * dV;
+  out->n_alive = (int64_t)red[9];
+  out->step = h->step;
+  if (red[10] > 0) return fail(h, PIC_ENAN, "non-finite momenta");
   return PIC_OK;
 }
 

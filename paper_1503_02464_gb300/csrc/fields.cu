@@ -323,6 +323,24 @@ __global__ void __launch_bounds__(256)
   if (threadIdx.x == 0) atomicAdd(out + 5, v);
 }
 
+// sum E^2, sum B^2 (squares in the storage precision, sums in FP64)
+template <class R>
+__global__ void __launch_bounds__(256)
+    k_field_energy(int64_t ncell, const R *Ex, const R *Ey, const R *Ez, const R *Bx, const R *By, const R *Bz,
+                   double *out) {
+  __shared__ double sh[32];
+  double se = 0, sb = 0;
+  for (int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; c < ncell; c += (int64_t)gridDim.x * blockDim.x) {
+    const R ex = Ex[c], ey = Ey[c], ez = Ez[c], bx = Bx[c], by = By[c], bz = Bz[c];
+    se += (double)(ex * ex + ey * ey + ez * ez);
+    sb += (double)(bx * bx + by * by + bz * bz);
+  }
+  double v = block_sum(se, sh);
+  if (threadIdx.x == 0) atomicAdd(out + 0, v);
+  v = block_sum(sb, sh);
+  if (threadIdx.x == 0) atomicAdd(out + 1, v);
+}
+
 template <class R>
 __global__ void __launch_bounds__(256)
     k_particle_diag(Particles p, const int64_t *__restrict__ d_count, double m, double *out) {
@@ -331,16 +349,17 @@ __global__ void __launch_bounds__(256)
   double ek = 0, cnt = 0, nf = 0;
   for (int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; s < n; s += (int64_t)gridDim.x * blockDim.x) {
     if (p.cell[s] < 0) continue;
-    const double ux = static_cast<const R *>(p.u[0])[s], uy = static_cast<const R *>(p.u[1])[s],
-                 uz = static_cast<const R *>(p.u[2])[s];
-    const double u2 = ux * ux + uy * uy + uz * uz;
+    // per-particle terms in the storage precision, sums in FP64
+    const R ux = static_cast<const R *>(p.u[0])[s], uy = static_cast<const R *>(p.u[1])[s],
+            uz = static_cast<const R *>(p.u[2])[s];
+    const R u2 = ux * ux + uy * uy + uz * uz;
     // gamma - 1 = u^2 / (sqrt(1 + u^2) + 1), free of cancellation
-    ek += (double)static_cast<const R *>(p.w)[s] * m * (u2 / (sqrt(1.0 + u2) + 1.0));
+    ek += (double)(static_cast<const R *>(p.w)[s] * (u2 / (sqrt(R(1) + u2) + R(1))));
     cnt += 1;
     if (!isfinite(u2)) nf += 1;
   }
   double v = block_sum(ek, sh);
-  if (threadIdx.x == 0) atomicAdd(out + 0, v);
+  if (threadIdx.x == 0) atomicAdd(out + 0, m * v);
   v = block_sum(cnt, sh);
   if (threadIdx.x == 0) atomicAdd(out + 1, v);
   v = block_sum(nf, sh);
@@ -471,6 +490,18 @@ cudaError_t launch_field_diag(const Grid &g, void *const E[3], void *const B[3],
     k_field_diag<float><<<nb, 256, 0, st>>>(g.dims, g.n[0], g.n[1], g.n[2], r0, r1, r2, rdt, c(E[0]), c(E[1]),
                                             c(E[2]), c(B[0]), c(B[1]), c(B[2]), c(J[0]), c(J[1]), c(J[2]), rho,
                                             rho_prev, out);
+  }
+  return cudaGetLastError();
+}
+
+cudaError_t launch_field_energy(const Grid &g, void *const E[3], void *const B[3], double *out, cudaStream_t st) {
+  const int nb = grid_blocks(g.ncell, 256);
+  if (g.prec == 1) {
+    auto c = [](void *v) { return static_cast<const double *>(v); };
+    k_field_energy<double><<<nb, 256, 0, st>>>(g.ncell, c(E[0]), c(E[1]), c(E[2]), c(B[0]), c(B[1]), c(B[2]), out);
+  } else {
+    auto c = [](void *v) { return static_cast<const float *>(v); };
+    k_field_energy<float><<<nb, 256, 0, st>>>(g.ncell, c(E[0]), c(E[1]), c(E[2]), c(B[0]), c(B[1]), c(B[2]), out);
   }
   return cudaGetLastError();
 }

@@ -73,6 +73,11 @@ cudaError_t launch_push(const Grid &g, void *const E[3], void *const B[3], void 
                         const int64_t *tile_start, int32_t *esc_list, unsigned long long *esc_count, double q,
                         double m, Counters *ctr, cudaStream_t st, int *nlaunch);
 
+// Diagnostics charge density of particles sorted by tile (exact 64-bit
+// fixed-point window sums; adds into rho).
+cudaError_t launch_rho_tiled(const Grid &g, const Particles &p, const int64_t *tile_start, double q, double *rho,
+                             cudaStream_t st);
+
 // ---- sort (sort.cu) ----
 // Counting sort of the slots [0, *d_count) of `src` by (tile, cell-in-tile),
 // dead slots dropped; result in `dst`, *d_count updated, tile_start[ntiles+1]
@@ -107,6 +112,8 @@ cudaError_t launch_rho(const Grid &g, const Particles &p, const int64_t *d_count
 // 4 max|(rho-rho_prev)/dt + div J| (if rho_prev), 5 nonfinite count (fields)
 cudaError_t launch_field_diag(const Grid &g, void *const E[3], void *const B[3], void *const J[3],
                               const double *rho, const double *rho_prev, double *out, cudaStream_t st);
+// out[0] += sum E^2, out[1] += sum B^2
+cudaError_t launch_field_energy(const Grid &g, void *const E[3], void *const B[3], double *out, cudaStream_t st);
 // out[0] += sum w m (gamma-1), out[1] += live count, out[2] += nonfinite count
 cudaError_t launch_particle_diag(const Grid &g, const Particles &p, const int64_t *d_count, int64_t nmax, double m,
                                  double *out, cudaStream_t st);

@@ -750,7 +750,139 @@ cudaError_t launch_t(const Grid &g, void *const E[3], void *const B[3], void *co
   return cudaGetLastError();
 }
 
+// Charge density at the nodes for the diagnostics, rho += q w S(X-i)S(Y-j)S(Z-k),
+// one block per tile like k_push.  The block's window sums are exact 64-bit
+// fixed point (|rho_node| <= sum |q w| over the tile bounds the scale), so
+// the result does not depend on the order of the additions; particles more
+// than one cell outside their tile add to the global array directly.
+template <class R, int DIM, int ORDER>
+__global__ void __launch_bounds__(kThreads)
+    k_rho_tile(int n0, int n1, int n2, int ntile0, int ntile1, FastDiv dn0, FastDiv dn1, const int32_t *__restrict__ cell,
+               const R *__restrict__ off0, const R *__restrict__ off1, const R *__restrict__ off2,
+               const R *__restrict__ w, const int64_t *__restrict__ tile_start, double q, double *rho) {
+  using G = Geo<DIM, ORDER>;
+  constexpr int NS = ORDER + 1;
+  constexpr int RX = G::EX, RY = G::EY, RZ = G::EZ;  // window: cell-1 .. cell+2 around the tile (+ drift)
+  constexpr int RN = RX * RY * RZ;
+  __shared__ unsigned long long win[RN];
+  __shared__ double s_sum;
+  const int t = blockIdx.x;
+  const int64_t pb = tile_start[t], pe = tile_start[t + 1];
+  if (pb >= pe) return;
+  int t0[3];
+  t0[0] = (t % ntile0) * G::TX;
+  t0[1] = ((t / ntile0) % ntile1) * G::TY;
+  t0[2] = (t / ntile0 / ntile1) * G::TZ;
+  for (int i = threadIdx.x; i < RN; i += kThreads) win[i] = 0ull;
+  if (threadIdx.x == 0) s_sum = 0.0;
+  __syncthreads();
+  double part = 0.0;
+  for (int64_t p = pb + threadIdx.x; p < pe; p += kThreads)
+    if (cell[p] >= 0) part += fabs((double)w[p]);
+  atomicAdd(&s_sum, part);
+  __syncthreads();
+  const double Q = fabs(q) * s_sum * 1.0001;
+  int e2 = 0;
+  if (Q > 0.0) frexp(Q, &e2);
+  const double scale = ldexp(1.0, Q > 0.0 ? 61 - e2 : 0);
+  const R *offs[3] = {off0, off1, off2};
+  for (int64_t p = pb + threadIdx.x; p < pe; p += kThreads) {
+    const int c = cell[p];
+    if (c < 0) continue;
+    const uint32_t r0 = dn0.div((uint32_t)c);
+    int ci[3] = {c - (int)r0 * n0, DIM == 3 ? (int)(r0 - dn1.div(r0) * n1) : (int)r0, DIM == 3 ? (int)dn1.div(r0) : 0};
+    const int nn[3] = {n0, n1, n2};
+    constexpr int TT[3] = {G::TX, G::TY, G::TZ};
+    int l[3] = {0, 0, 0};
+    bool inw = true;
+    int base[3] = {0, 0, 0};
+    double wt[3][NS];
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+      if (d >= DIM) {
+        wt[d][0] = 1.0;
+        for (int k = 1; k < NS; ++k) wt[d][k] = 0.0;
+        continue;
+      }
+      int dl = ci[d] - t0[d];
+      if (dl > TT[d] - 1 + G::D) dl -= nn[d];
+      if (dl < -G::D) dl += nn[d];
+      l[d] = dl;
+      inw = inw && dl >= -G::D && dl <= TT[d] - 1 + G::D;
+      const double f = (double)offs[d][p];
+      if (ORDER == 2) {
+        const int h = f >= 0.5;
+        const double dd = f - h, a = 0.5 - dd, b = 0.5 + dd;
+        wt[d][0] = 0.5 * a * a;
+        wt[d][1] = 0.75 - dd * dd;
+        wt[d][NS - 1] = 0.5 * b * b;
+        base[d] = h - 1;
+      } else {
+        wt[d][0] = 1.0 - f;
+        wt[d][NS - 1] = f;
+        base[d] = 0;
+      }
+    }
+    const double qw = q * (double)w[p];
+#pragma unroll
+    for (int kz = 0; kz < (DIM == 3 ? NS : 1); ++kz)
+#pragma unroll
+      for (int ky = 0; ky < NS; ++ky)
+#pragma unroll
+        for (int kx = 0; kx < NS; ++kx) {
+          const double v = qw * wt[0][kx] * wt[1][ky] * wt[2][kz];
+          if (inw) {
+            const int ix = l[0] + base[0] + kx + G::D + G::LOE;
+            const int iy = l[1] + base[1] + ky + G::D + G::LOE;
+            const int iz = DIM == 3 ? l[2] + base[2] + kz + G::D + G::LOE : 0;
+            atomicAdd(&win[ix + RX * (iy + RY * iz)], (unsigned long long)__double2ll_rn(v * scale));
+          } else {
+            const int gi = wrapi(ci[0] + base[0] + kx, n0), gj = wrapi(ci[1] + base[1] + ky, n1);
+            const int gk = DIM == 3 ? wrapi(ci[2] + base[2] + kz, n2) : 0;
+            atomicAdd(rho + gi + (int64_t)n0 * (gj + (int64_t)n1 * gk), v);
+          }
+        }
+  }
+  __syncthreads();
+  for (int i = threadIdx.x; i < RN; i += kThreads) {
+    const long long X = (long long)win[i];
+    if (X == 0) continue;
+    const int x = i % RX, y = (i / RX) % RY, z = i / (RX * RY);
+    const int gi = wrap_near(t0[0] - G::D - G::LOE + x, n0);
+    const int gj = wrap_near(t0[1] - G::D - G::LOE + y, n1);
+    const int gk = DIM == 3 ? wrap_near(t0[2] - G::D - G::LOE + z, n2) : 0;
+    atomicAdd(rho + gi + (int64_t)n0 * (gj + (int64_t)n1 * gk), (double)X / scale);
+  }
+}
+
 }  // namespace
+
+cudaError_t launch_rho_tiled(const Grid &g, const Particles &p, const int64_t *tile_start, double q, double *rho,
+                             cudaStream_t st) {
+  if (g.ntiles > 0x7fffffff) return cudaErrorInvalidValue;
+  const FastDiv d0 = make_fastdiv((uint32_t)g.n[0]), d1 = make_fastdiv((uint32_t)g.n[1]);
+  const unsigned nb = (unsigned)g.ntiles;
+#define PIC_RHO_CASE(K, R, D, O)                                                                                 \
+  case K:                                                                                                        \
+    k_rho_tile<R, D, O><<<nb, kThreads, 0, st>>>(g.n[0], g.n[1], g.n[2], g.ntile[0], g.ntile[1], d0, d1, p.cell, \
+                                                  static_cast<const R *>(p.off[0]), static_cast<const R *>(p.off[1]), \
+                                                  static_cast<const R *>(p.off[2]), static_cast<const R *>(p.w),  \
+                                                  tile_start, q, rho);                                           \
+    break;
+  switch ((g.prec == 1 ? 100 : 0) + g.dims * 10 + g.order) {
+    PIC_RHO_CASE(21, float, 2, 1)
+    PIC_RHO_CASE(22, float, 2, 2)
+    PIC_RHO_CASE(31, float, 3, 1)
+    PIC_RHO_CASE(32, float, 3, 2)
+    PIC_RHO_CASE(121, double, 2, 1)
+    PIC_RHO_CASE(122, double, 2, 2)
+    PIC_RHO_CASE(131, double, 3, 1)
+    PIC_RHO_CASE(132, double, 3, 2)
+    default: return cudaErrorInvalidValue;
+  }
+#undef PIC_RHO_CASE
+  return cudaGetLastError();
+}
 
 // Tile shape compiled into the push kernel for a given dimensionality.
 void push_tile_shape(int dims, int tile[3]) {

@@ -185,6 +185,9 @@ class Simulation:
     def diag(self) -> dict:
         return capi.pic_diag(self.h)
 
+    def energy(self) -> dict:
+        return capi.pic_energy(self.h)
+
     # -- profiling
     def profile(self, enable: bool = True) -> None:
         capi.pic_profile(self.h, enable)

@@ -179,3 +179,16 @@ def test_empty_species_and_zero_steps():
     s.step(3)
     d = s.diag()
     assert d["n_alive"] == 0 and d["energy_field"] == 0.0
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+def test_energy_readback_matches_diag(precision):
+    wl = _wl(3, 2, (12, 12, 12), 2, 0.1, 9)
+    parts = [wl.particles(0)]
+    s = build_gpu(wl, parts, precision)
+    s.step(4)
+    d, e = s.diag(), s.energy()
+    tol = 1e-12 if precision == "fp64" else 1e-6
+    for k in ("energy_e", "energy_b", "energy_kinetic"):
+        assert abs(d[k] - e[k]) <= tol * abs(d[k]), (k, d[k], e[k])
+    assert d["n_alive"] == e["n_alive"] and e["step"] == 4
