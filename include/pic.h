@@ -173,6 +173,15 @@ int pic_load_particles(pic_handle *h, int species, int64_t n, const double *x, c
  * an immobile background carries no current. */
 int pic_neutralize(pic_handle *h);
 
+/* Set the immobile background charge density at the nodes (i, j, k):
+ * rho_bg holds n[0]*n[1]*n[2] doubles, x fastest (host or device memory per
+ * mem_kind, borrowed for the call).  It replaces any earlier background
+ * (pic_neutralize included).  Like pic_neutralize it enters rho and the
+ * Gauss-law diagnostics only; an immobile background carries no current, so
+ * the particle cycle of section 2 is unchanged.  PIC_EINVAL for a NULL
+ * pointer or a non-finite value (the background is then left unchanged). */
+int pic_set_background(pic_handle *h, const double *rho_bg, int mem_kind);
+
 /* Advance nsteps PIC cycles (enqueued on the stream; asynchronous).
  * Per step: sort (every sort_every steps) -> J = 0 -> per species one fused
  * gather/Boris/move/deposit launch -> Yee B half step -> E step -> B half

@@ -72,6 +72,7 @@ def _load():
     lib.oracle_deposit_move.argtypes = [vp, ctypes.c_double, ctypes.c_double, dp, dp, ctypes.c_double]
     lib.oracle_compute_rho.argtypes = [vp]
     lib.oracle_neutralize.argtypes = [vp]
+    lib.oracle_set_background.argtypes = [vp, dp]
     lib.oracle_diag.argtypes = [vp, dp]
     lib.oracle_set_boundary.argtypes = [vp, ctypes.c_int]
     lib.oracle_set_laser.argtypes = [vp, ctypes.c_int] + [ctypes.c_double] * 5 + [ctypes.c_int]
@@ -181,6 +182,11 @@ class OracleSim:
 
     def neutralize(self):
         _load().oracle_neutralize(self._h)
+
+    def set_background(self, rho_bg):
+        """Immobile background charge density at the nodes (shaped like a field)."""
+        a = _f64(np.broadcast_to(rho_bg, self.shape3))
+        _load().oracle_set_background(self._h, _dp(a))
 
     def particles(self, species: int = 0) -> dict:
         lib = _load()

@@ -622,6 +622,12 @@ void oracle_compute_rho(void *h) {
   deposit_rho(s, s->f[ORC_RHO]);
 }
 
+/* Immobile background charge density at the nodes, given explicitly. */
+void oracle_set_background(void *h, const double *rho) {
+  orc_sim *s = (orc_sim *)h;
+  memcpy(s->rho_bg, rho, sizeof(double) * s->ncell);
+}
+
 /* Immobile neutralising background: rho_bg = -rho of the current particles. */
 void oracle_neutralize(void *h) {
   orc_sim *s = (orc_sim *)h;

@@ -23,7 +23,7 @@ ERROR_NAMES = {0: "PIC_OK", 1: "PIC_EINVAL", 2: "PIC_ECOURANT", 3: "PIC_ENOMEM",
 
 # every symbol include/pic.h declares
 EXPORTED = ["pic_create", "pic_destroy", "pic_last_error", "pic_add_species", "pic_load_particles",
-            "pic_neutralize", "pic_step", "pic_fields", "pic_set_field", "pic_num_particles", "pic_particles",
+            "pic_neutralize", "pic_set_background", "pic_step", "pic_fields", "pic_set_field", "pic_num_particles", "pic_particles",
             "pic_diag", "pic_energy", "pic_sync", "pic_profile", "pic_timings", "pic_launch_count", "pic_checkpoint",
             "pic_restore", "pic_tape_begin", "pic_adjoint_begin", "pic_adjoint_seed_kinetic", "pic_adjoint_step",
             "pic_grad", "pic_field_energy_noalloc"]
@@ -95,6 +95,7 @@ def load(build_if_missing: bool = True) -> ctypes.CDLL:
         "pic_add_species": ([hp, ctypes.c_double, ctypes.c_double, i64, ctypes.POINTER(ctypes.c_int)], ctypes.c_int),
         "pic_load_particles": ([hp, ctypes.c_int, i64] + [vp] * 8 + [ctypes.c_int], ctypes.c_int),
         "pic_neutralize": ([hp], ctypes.c_int),
+        "pic_set_background": ([hp, vp, ctypes.c_int], ctypes.c_int),
         "pic_step": ([hp, ctypes.c_int], ctypes.c_int),
         "pic_fields": ([hp, ctypes.c_int, vp, ctypes.c_int], ctypes.c_int),
         "pic_set_field": ([hp, ctypes.c_int, vp, ctypes.c_int], ctypes.c_int),
@@ -158,6 +159,10 @@ def pic_load_particles(h, species: int, n: int, x, y, z, ux, uy, uz, w, ids, mem
 
 def pic_neutralize(h) -> None:
     check(h, load().pic_neutralize(h))
+
+
+def pic_set_background(h, rho_bg_ptr: int, mem_kind: int) -> None:
+    check(h, load().pic_set_background(h, rho_bg_ptr, mem_kind))
 
 
 def pic_step(h, nsteps: int) -> None:

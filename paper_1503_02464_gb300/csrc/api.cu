@@ -9,6 +9,7 @@
 #include <stdio.h>
 #include <string.h>
 
+#include <cmath>
 #include <string>
 #include <vector>
 
@@ -34,6 +35,8 @@ struct Species {
   int64_t h_count = 0;          // host mirror, valid while !stepped_since_count
   int32_t *rank = nullptr;
   int64_t *tile_start = nullptr;
+  float *tq = nullptr;          // per-tile deposit bound carried between pushes
+  bool fresh = true;            // sorted since the last push
   bool need_sort = true;
 };
 
@@ -203,6 +206,7 @@ int sort_species(pic_handle *h, Species &s) {
   h->launches += nl;
   s.cur = 1 - s.cur;
   s.need_sort = false;
+  s.fresh = true;
   return PIC_OK;
 }
 
@@ -479,6 +483,7 @@ int pic_destroy(pic_handle *h) {
     cudaFree(s.d_count);
     cudaFree(s.rank);
     cudaFree(s.tile_start);
+    cudaFree(s.tq);
   }
   for (auto &t : h->timers) {
     cudaEventDestroy(t.a);
@@ -510,12 +515,14 @@ int pic_add_species(pic_handle *h, double q, double m, int64_t capacity, int *sp
   if (e == cudaSuccess) e = cudaMalloc(&s.d_count, sizeof(int64_t));
   if (e == cudaSuccess) e = cudaMalloc(&s.rank, (size_t)(s.slots > 0 ? s.slots : 1) * sizeof(int32_t));
   if (e == cudaSuccess) e = cudaMalloc(&s.tile_start, (size_t)(h->g.ntiles + 1) * sizeof(int64_t));
+  if (e == cudaSuccess) e = cudaMalloc(&s.tq, (size_t)2 * h->g.ntiles * sizeof(float));
   if (e != cudaSuccess) {
     free_particles(s.buf[0]);
     free_particles(s.buf[1]);
     cudaFree(s.d_count);
     cudaFree(s.rank);
     cudaFree(s.tile_start);
+    cudaFree(s.tq);
     s = Species{};
     cudaGetLastError();
     return fail(h, PIC_ENOMEM, "device allocation failed in pic_add_species");
@@ -600,6 +607,25 @@ int pic_neutralize(pic_handle *h) {
   return PIC_OK;
 }
 
+int pic_set_background(pic_handle *h, const double *rho_bg, int mem_kind) {
+  if (!h) return fail(h, PIC_EINVAL, "NULL handle");
+  if (!rho_bg) return fail(h, PIC_EINVAL, "NULL background");
+  if (mem_kind != PIC_MEM_HOST && mem_kind != PIC_MEM_DEVICE) return fail(h, PIC_EINVAL, "bad memory kind");
+  const size_t nb = sizeof(double) * (size_t)h->g.ncell;
+  std::vector<double> tmp((size_t)h->g.ncell);
+  if (mem_kind == PIC_MEM_HOST) {
+    memcpy(tmp.data(), rho_bg, nb);
+  } else {
+    CK(h, cudaMemcpyAsync(tmp.data(), rho_bg, nb, cudaMemcpyDeviceToHost, h->st), "D2H");
+    CK(h, cudaStreamSynchronize(h->st), "sync");
+  }
+  for (double v : tmp)
+    if (!std::isfinite(v)) return fail(h, PIC_EINVAL, "non-finite background");
+  CK(h, cudaMemcpyAsync(h->rho_bg, tmp.data(), nb, cudaMemcpyHostToDevice, h->st), "H2D");
+  CK(h, cudaStreamSynchronize(h->st), "sync");
+  return PIC_OK;
+}
+
 int pic_step(pic_handle *h, int nsteps) {
   if (!h) return fail(h, PIC_EINVAL, "NULL handle");
   if (nsteps < 0) return fail(h, PIC_EINVAL, "negative step count");
@@ -629,9 +655,10 @@ int pic_step(pic_handle *h, int nsteps) {
       Timed tm(h, pic::KC_PUSH);
       int nl = 0;
       CK(h,
-         pic::launch_push(h->g, h->E, h->B, h->J, s.buf[s.cur], s.tile_start, s.rank, h->esc_count, s.q, s.m,
-                          h->ctr, h->st, &nl),
+         pic::launch_push(h->g, h->E, h->B, h->J, s.buf[s.cur], s.tile_start, s.tq, s.fresh ? 1 : 0, s.rank,
+                          h->esc_count, s.q, s.m, h->ctr, h->st, &nl),
          "push");
+      s.fresh = false;
       h->launches += nl;
     }
     {

@@ -67,11 +67,15 @@ enum KernelClass { KC_SORT = 0, KC_ZEROJ = 1, KC_PUSH = 2, KC_YEE_B = 3, KC_YEE_
 // drift allowance is one cell.
 void push_tile_shape(int dims, int tile[3]);
 size_t push_smem_bytes(const Grid &g);
-// Tile kernel + escape kernel.  esc_list (one int per slot) and esc_count
-// are scratch for particles deferred to the escape kernel.
+// Tile kernel + escape kernel.  tq (2 floats per tile) carries the per-tile
+// bound of the FP32 fixed-point deposit from one step to the next; fresh = 1
+// on the first push after a sort (tq is recomputed from the particles).
+// esc_list (one int per slot) and esc_count are scratch for particles
+// deferred to the escape kernel.
 cudaError_t launch_push(const Grid &g, void *const E[3], void *const B[3], void *const J[3], const Particles &p,
-                        const int64_t *tile_start, int32_t *esc_list, unsigned long long *esc_count, double q,
-                        double m, Counters *ctr, cudaStream_t st, int *nlaunch);
+                        const int64_t *tile_start, float *tq, int fresh, int32_t *esc_list,
+                        unsigned long long *esc_count, double q, double m, Counters *ctr, cudaStream_t st,
+                        int *nlaunch);
 
 // Diagnostics charge density of particles sorted by tile (exact 64-bit
 // fixed-point window sums; adds into rho).

@@ -86,6 +86,8 @@ template <class R> struct PushArgs {
   const R *w;
   const int64_t *tile_start;
   double qabs;                      // |q|
+  float *tq;                        // per tile: [2t] sum |w|, [2t+1] sum |w| min(1, |u|) (FP32 runs)
+  int fresh;                        // tile contents changed (sorted) since tq was written
   int32_t *esc_list;                // slots deferred to k_push_escaped
   unsigned long long *esc_count;
   R qmh;      // q dt / (2 m)
@@ -342,7 +344,7 @@ __global__ void __launch_bounds__(kThreads, sizeof(R) == 4 ? 2 : 1) k_push(const
   __shared__ unsigned int s_clamp;
   __shared__ double s_scale;
   __shared__ unsigned int s_emax[3];
-  __shared__ float s_qsum;
+  __shared__ float s_qsum, s_wsum, s_q1;
   float emax[3] = {0.f, 0.f, 0.f};
 
   const int t = blockIdx.x;
@@ -380,6 +382,8 @@ __global__ void __launch_bounds__(kThreads, sizeof(R) == 4 ? 2 : 1) k_push(const
     s_clamp = 0;
     s_emax[0] = s_emax[1] = s_emax[2] = 0u;
     s_qsum = 0.f;
+    s_wsum = 0.f;
+    s_q1 = 0.f;
   }
   __syncthreads();
   if (sizeof(R) == 4) {
@@ -390,14 +394,30 @@ __global__ void __launch_bounds__(kThreads, sizeof(R) == 4 ? 2 : 1) k_push(const
     __syncthreads();
     const float ex = __uint_as_float(s_emax[0]), ey = __uint_as_float(s_emax[1]), ez = __uint_as_float(s_emax[2]);
     const float kick = (float)(2.0 * fabs((double)a.qmh)) * sqrtf(ex * ex + ey * ey + ez * ez);
-    float qs = 0.f;
-    for (int64_t p = pb + tid; p < pe; p += kThreads) {
-      if (a.cell[p] < 0) continue;
-      const float ux = (float)a.u[0][p], uy = (float)a.u[1][p], uz = (float)a.u[2][p];
-      qs += fabsf((float)a.w[p]) * fminf(1.f, sqrtf(ux * ux + uy * uy + uz * uz) + kick);
+    if (a.fresh) {
+      // tile contents are new (sorted): bound from the particles themselves
+      float qs = 0.f, w0 = 0.f;
+      for (int64_t p = pb + tid; p < pe; p += kThreads) {
+        if (a.cell[p] < 0) continue;
+        const float ux = (float)a.u[0][p], uy = (float)a.u[1][p], uz = (float)a.u[2][p];
+        const float aw = fabsf((float)a.w[p]);
+        qs += aw * fminf(1.f, sqrtf(ux * ux + uy * uy + uz * uz) + kick);
+        w0 += aw;
+      }
+      for (int o = 16; o > 0; o >>= 1) {
+        qs += __shfl_down_sync(0xffffffffu, qs, o);
+        w0 += __shfl_down_sync(0xffffffffu, w0, o);
+      }
+      if ((tid & 31) == 0) {
+        if (qs > 0.f) atomicAdd(&s_qsum, qs);
+        if (w0 > 0.f) atomicAdd(&s_wsum, w0);
+      }
+    } else if (tid == 0) {
+      // |u| min'ed at 1 from the previous push, plus the kick of this step:
+      // sum |w| min(1, |u| + kick) <= sum |w| min(1, |u|) + kick sum |w|
+      s_wsum = a.tq[2 * t];
+      s_qsum = a.tq[2 * t + 1] + kick * s_wsum;
     }
-    for (int o = 16; o > 0; o >>= 1) qs += __shfl_down_sync(0xffffffffu, qs, o);
-    if ((tid & 31) == 0 && qs > 0.f) atomicAdd(&s_qsum, qs);
     __syncthreads();
     if (tid == 0) {
       // 1.01: room for the FP32 rounding of the sums above
@@ -423,6 +443,7 @@ __global__ void __launch_bounds__(kThreads, sizeof(R) == 4 ? 2 : 1) k_push(const
   const int lane = tid & 31, warp = tid >> 5;
   const int e = 8 * lane + ((warp + (lane >> 2)) & 7);
   unsigned my_clamp = 0, my_absorbed = 0;
+  float my_q1 = 0.f;
 
   for (int64_t c0 = pb; c0 < pe; c0 += kThreads) {
     const int cn = (int)(pe - c0 < kThreads ? pe - c0 : kThreads);
@@ -468,6 +489,7 @@ __global__ void __launch_bounds__(kThreads, sizeof(R) == 4 ? 2 : 1) k_push(const
           sCell[e] = c | kEscFlag;
           const unsigned long long slot = atomicAdd(a.esc_count, 1ull);
           a.esc_list[slot] = (int32_t)(c0 + e);
+          my_q1 += fabsf((float)sW[e]);  // its new |u| is not known here: bound by 1
         } else {
           R f[3], u[3];
 #pragma unroll
@@ -498,6 +520,8 @@ __global__ void __launch_bounds__(kThreads, sizeof(R) == 4 ? 2 : 1) k_push(const
           R fn[3], ig;
           int s[3];
           push_move<R, ORDER, DIM>(a, u, E, B, f, fn, s, ig, my_clamp);
+          if (sizeof(R) == 4)
+            my_q1 += fabsf((float)sW[e]) * fminf(1.f, sqrtf((float)(u[0] * u[0] + u[1] * u[1] + u[2] * u[2])));
 
           // ---- Esirkepov deposit (§2 eq. 4 + continuity) ----
           DepositAxis<R, ORDER> dx, dy, dz;
@@ -557,7 +581,16 @@ __global__ void __launch_bounds__(kThreads, sizeof(R) == 4 ? 2 : 1) k_push(const
 
   if (my_clamp) atomicAdd(&s_clamp, my_clamp);
   if (my_absorbed) atomicAdd(&a.ctr->absorbed, (unsigned long long)my_absorbed);
+  if (sizeof(R) == 4) {
+    for (int o = 16; o > 0; o >>= 1) my_q1 += __shfl_down_sync(0xffffffffu, my_q1, o);
+    if ((tid & 31) == 0 && my_q1 > 0.f) atomicAdd(&s_q1, my_q1);
+  }
   __syncthreads();
+  if (sizeof(R) == 4 && tid == 0) {
+    // bound inputs for the next step (the tile keeps its slots until the next sort)
+    a.tq[2 * t] = s_wsum;
+    a.tq[2 * t + 1] = s_q1 * 1.0001f;
+  }
 
   // ---- flush the J window into global J ----
   for (int q = tid; q < G::JN; q += kThreads) {
@@ -707,9 +740,12 @@ template <class R, int DIM, int ORDER> constexpr size_t smem_bytes() {
 
 template <class R, int DIM, int ORDER>
 cudaError_t launch_t(const Grid &g, void *const E[3], void *const B[3], void *const J[3], const Particles &p,
-                     const int64_t *tile_start, int32_t *esc_list, unsigned long long *esc_count, double q,
-                     double m, Counters *ctr, cudaStream_t st, int *nlaunch) {
+                     const int64_t *tile_start, float *tq, int fresh, int32_t *esc_list,
+                     unsigned long long *esc_count, double q, double m, Counters *ctr, cudaStream_t st,
+                     int *nlaunch) {
   PushArgs<R> a;
+  a.tq = tq;
+  a.fresh = fresh;
   a.qabs = q < 0 ? -q : q;
   for (int d = 0; d < 3; ++d) {
     a.n[d] = g.n[d];
@@ -907,11 +943,13 @@ size_t push_smem_bytes(const Grid &g) {
 }
 
 cudaError_t launch_push(const Grid &g, void *const E[3], void *const B[3], void *const J[3], const Particles &p,
-                        const int64_t *tile_start, int32_t *esc_list, unsigned long long *esc_count, double q,
-                        double m, Counters *ctr, cudaStream_t st, int *nlaunch) {
+                        const int64_t *tile_start, float *tq, int fresh, int32_t *esc_list,
+                        unsigned long long *esc_count, double q, double m, Counters *ctr, cudaStream_t st,
+                        int *nlaunch) {
   const int key = (g.prec == 1 ? 100 : 0) + g.dims * 10 + g.order;
 #define PIC_PUSH_CASE(K, R, D, O) \
-  case K: return launch_t<R, D, O>(g, E, B, J, p, tile_start, esc_list, esc_count, q, m, ctr, st, nlaunch);
+  case K:                                                                                                    \
+    return launch_t<R, D, O>(g, E, B, J, p, tile_start, tq, fresh, esc_list, esc_count, q, m, ctr, st, nlaunch);
   switch (key) {
     PIC_PUSH_CASE(21, float, 2, 1)
     PIC_PUSH_CASE(22, float, 2, 2)

@@ -143,6 +143,11 @@ class Simulation:
     def neutralize(self) -> None:
         capi.pic_neutralize(self.h)
 
+    def set_background(self, rho_bg) -> None:
+        """Immobile background charge density at the nodes, shaped like a field."""
+        a = np.ascontiguousarray(np.broadcast_to(rho_bg, self.shape3), dtype=np.float64)
+        capi.pic_set_background(self.h, a.ctypes.data, capi.PIC_MEM_HOST)
+
     def num_particles(self, species: int = 0) -> int:
         return capi.pic_num_particles(self.h, species)
 

@@ -14,10 +14,15 @@ the sampled full-size parity tests rely on).  Draws -> uniforms in (0, 1)
 with 53 random bits; normals by the Box-Muller transform.
 
 Workload recipe (section 2 of the paper states the model; the sizes below are
-the synthetic stand-ins for its laser-plasma and thermal-plasma runs):
+the synthetic stand-ins for its laser-plasma and thermal-plasma runs and for
+the two-stream test problem of its scaling study, §4.1):
 positions uniform inside each cell, ``ppc`` particles per cell, momenta
-u = gamma v drawn per component from N(0, u_th) (cold beams/targets have
-u_th = 0), weight w = density / ppc, ids = global index.
+u = gamma v drawn per component from N(0, u_th) plus a species drift (cold
+beams/targets have u_th = 0), weight w = density / ppc, ids = global index.
+A species may instead use a quiet start: its particles sit on a regular
+sub-lattice of each cell (``lattice`` = points per axis), optionally with a
+sinusoidal displacement along x and a sinusoidal change of ux (``perturb``),
+which seeds one Fourier mode far above the discreteness noise.
 """
 from __future__ import annotations
 
@@ -46,11 +51,17 @@ def _normals(u1, u2):
 
 def particles_for_cells(cells: np.ndarray, grid: Sequence[int], d: Sequence[float], ppc: int,
                         u_th: float, w: np.ndarray | float, seed: int, dims: int,
-                        drift: Sequence[float] = (0.0, 0.0, 0.0)) -> dict:
+                        drift: Sequence[float] = (0.0, 0.0, 0.0), lattice: Optional[Sequence[int]] = None,
+                        perturb: Optional[Sequence[float]] = None) -> dict:
     """Particles of the given cells (row-major linear indices).
 
     Returns global positions (physical units), momenta u, weights and ids.
-    ``w`` is a scalar or an array with one weight per listed cell.
+    ``w`` is a scalar or an array with one weight per listed cell.  With
+    ``lattice`` = (lx, ly, lz), lx*ly*lz = ppc, positions are the sub-lattice
+    points ((a + 1/2)/lx, ...) of each cell instead of random draws.  With
+    ``perturb`` = (m, ax, phx, au, phu) and theta = 2 pi m x / Lx at the
+    unperturbed x, x moves by ax cos(theta + phx) (periodic wrap into the
+    box) and ux changes by au cos(theta + phu).
     """
     cells = np.asarray(cells, dtype=np.int64)
     nx, ny = int(grid[0]), int(grid[1])
@@ -68,12 +79,29 @@ def particles_for_cells(cells: np.ndarray, grid: Sequence[int], d: Sequence[floa
     i = cc % nx
     j = (cc // nx) % ny
     k = cc // (nx * ny)
-    x = (i + u[:, 0]) * d[0]
-    y = (j + u[:, 1]) * d[1]
-    z = (k + u[:, 2]) * d[2] if dims == 3 else np.zeros(n)
+    if lattice is None:
+        fx, fy, fz = u[:, 0], u[:, 1], u[:, 2]
+    else:
+        lx, ly, lz = (int(v) for v in lattice)
+        if lx * ly * lz != ppc:
+            raise ValueError("lattice points per cell must multiply to ppc")
+        slot = np.tile(np.arange(ppc), cells.size)
+        fx = (slot % lx + 0.5) / lx
+        fy = ((slot // lx) % ly + 0.5) / ly
+        fz = (slot // (lx * ly) + 0.5) / lz
+    x = (i + fx) * d[0]
+    y = (j + fy) * d[1]
+    z = (k + fz) * d[2] if dims == 3 else np.zeros(n)
+    dux = 0.0
+    if perturb is not None:
+        m, ax, phx, au, phu = (float(v) for v in perturb)
+        lx_box = nx * d[0]
+        theta = TWO_PI * m * x / lx_box
+        x = np.mod(x + ax * np.cos(theta + phx), lx_box)
+        dux = au * np.cos(theta + phu)
     n0, n1 = _normals(u[:, 3], u[:, 4])
     n2, _ = _normals(u[:, 5], u[:, 6])
-    ux = u_th * n0 + drift[0]
+    ux = u_th * n0 + drift[0] + dux
     uy = u_th * n1 + drift[1]
     uz = u_th * n2 + drift[2]
     wa = np.broadcast_to(np.asarray(w, dtype=np.float64), cells.shape)
@@ -93,6 +121,9 @@ class Species:
     # columns [x0, x1) holding the species (None = whole box)
     x_range: Optional[tuple] = None
     seed_offset: int = 0
+    drift: tuple = (0.0, 0.0, 0.0)      # mean momentum u added to every particle
+    lattice: Optional[tuple] = None     # quiet start: sub-lattice points per axis
+    perturb: Optional[tuple] = None     # quiet start: (mode, ax, phase_x, au, phase_u)
 
 
 @dataclass
@@ -133,7 +164,8 @@ class Workload:
         if cells is None:
             cells = self.species_cells(sp)
         return particles_for_cells(cells, self.n, self.d, sp.ppc, sp.u_th, sp.density,
-                                   self.seed * 1000 + sp.seed_offset, self.dims)
+                                   self.seed * 1000 + sp.seed_offset, self.dims, sp.drift, sp.lattice,
+                                   sp.perturb)
 
 
 def courant_limit(d: Sequence[float], dims: int) -> float:
@@ -172,7 +204,33 @@ def preset(name: str) -> Workload:
                          Species("proton", 1.0, 1836.0, 27, 0.0, 50.0, (256, 276), 1)],
                         absorbing_x=True, neutralize=False,
                         laser={"a0": 10.0, "waist": 2 * lam, "duration": 8 * lam, "pol": 1})
+    if name == "twostream3d_512":
+        # the two-stream problem of the paper's scaling runs: 512x512x128
+        # cells, 54 ppc (two counter-streaming electron beams of 27 ppc each,
+        # u = +-0.2 along x, small spread), immobile neutralising ions
+        return Workload(name, 3, (512, 512, 128), (0.05, 0.05, 0.05), 0.028, 2, 50, 1006,
+                        [Species("beam+", -1.0, 1.0, 27, 0.002, 0.5, None, 0, (0.2, 0.0, 0.0)),
+                         Species("beam-", -1.0, 1.0, 27, 0.002, 0.5, None, 1, (-0.2, 0.0, 0.0))])
     raise KeyError(name)
+
+
+def two_stream(n: tuple, d: float, u0: float, ppc_lattice: tuple, seeds=(None, None), order: int = 2,
+               dt_frac: float = 0.9, density: float = 1.0, seed: int = 77) -> Workload:
+    """Two cold counter-streaming electron beams (drift momentum +-u0 along
+    x, each of half the density) on a quiet-start lattice, periodic, 2D3V
+    (len(n) == 2) or 3D3V; ``seeds`` gives each beam's ``perturb`` tuple
+    (see particles_for_cells).  The neutralising background is the
+    caller's (a uniform +density)."""
+    dims = len(n)
+    dd = (d, d, d if dims == 3 else 1.0)
+    dt = dt_frac * courant_limit(dd, dims)
+    nn = tuple(n) + (1,) * (3 - dims)
+    ppc = int(np.prod(ppc_lattice))
+    lat = tuple(ppc_lattice) + (1,) * (3 - len(ppc_lattice))
+    return Workload(f"twostream{dims}d", dims, nn, dd, dt, order, 0, seed,
+                    [Species("beam+", -1.0, 1.0, ppc, 0.0, 0.5 * density, None, 0, (u0, 0.0, 0.0), lat, seeds[0]),
+                     Species("beam-", -1.0, 1.0, ppc, 0.0, 0.5 * density, None, 1, (-u0, 0.0, 0.0), lat,
+                             seeds[1])], neutralize=False)
 
 
 def small(dims: int, n: tuple, order: int, ppc: int, u_th: float, seed: int, dt_frac: float = 0.95,
