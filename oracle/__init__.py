@@ -73,6 +73,9 @@ def _load():
     lib.oracle_compute_rho.argtypes = [vp]
     lib.oracle_neutralize.argtypes = [vp]
     lib.oracle_set_background.argtypes = [vp, dp]
+    lib.oracle_set_filter.argtypes = [vp, ctypes.c_int, ctypes.c_int]
+    lib.oracle_set_gather.argtypes = [vp, ctypes.c_int]
+    lib.oracle_smooth.argtypes = [vp, ctypes.c_int]
     lib.oracle_diag.argtypes = [vp, dp]
     lib.oracle_set_boundary.argtypes = [vp, ctypes.c_int]
     lib.oracle_set_laser.argtypes = [vp, ctypes.c_int] + [ctypes.c_double] * 5 + [ctypes.c_int]
@@ -148,6 +151,19 @@ class OracleSim:
     def add_particles(self, parts: dict, q: float, m: float) -> int:
         return self.add_species(q, m, parts["x"], parts["y"], parts.get("z"), parts["ux"], parts["uy"],
                                 parts["uz"], parts["w"], parts.get("id"))
+
+    def set_filter(self, passes: int, compensate: bool = False):
+        """Smooth J after every deposit: ``passes`` binomial passes per axis,
+        then optionally one compensating pass."""
+        _load().oracle_set_filter(self._h, int(passes), 1 if compensate else 0)
+
+    def set_gather(self, energy_conserving: bool):
+        """Gather variant: one shape order lower at half-integer positions."""
+        _load().oracle_set_gather(self._h, 1 if energy_conserving else 0)
+
+    def smooth(self, which: int):
+        """Apply the configured smoothing to one stored field in place."""
+        _load().oracle_smooth(self._h, int(which))
 
     def set_absorbing_x(self, on: bool = True):
         _load().oracle_set_boundary(self._h, 1 if on else 0)

@@ -85,6 +85,13 @@ typedef struct {
   double a0, waist, duration, yc, zc;
   int pol; /* 1: E along y, 2: E along z */
   double *mur_prev; /* previous boundary samples kept by the Mur condition */
+  /* gather variant: 0 = the same shape at every Yee location; 1 = one order
+   * lower along each axis on which the component sits at a half-integer
+   * position ("energy-conserving" gather) */
+  int gather_ec;
+  /* current smoothing after the deposit: filter_passes three-point binomial
+   * passes per axis, then (filter_comp) one compensating pass */
+  int filter_passes, filter_comp;
 } orc_sim;
 
 /* ------------------------------------------------------------------ */
@@ -133,6 +140,7 @@ double oracle_laser_field(void *h, double x, double y, double z, double t) {
 /* shaped cloud (quadratic B-spline).  xi is measured in cells.        */
 /* ------------------------------------------------------------------ */
 double oracle_shape(int order, double xi) {
+  if (order == 0) return (xi >= -0.5 && xi < 0.5) ? 1.0 : 0.0; /* nearest grid point, half-open cell */
   double a = fabs(xi);
   if (order == 1) return a < 1.0 ? 1.0 - a : 0.0;
   if (a <= 0.5) return 0.75 - a * a;
@@ -260,15 +268,19 @@ long oracle_step_count(void *h) { return ((orc_sim *)h)->step; }
 /* an integer position and 0.5 for a half-integer one along axis a.    */
 /* ------------------------------------------------------------------ */
 static double gather_component(const orc_sim *s, const double *F, const double X[3], const double stag[3]) {
-  int o = s->order;
+  /* shape order per axis: one lower at half-integer positions in the
+   * energy-conserving variant */
+  int ox = s->order - (s->gather_ec && stag[0] != 0.0);
+  int oy = s->order - (s->gather_ec && stag[1] != 0.0);
+  int oz = s->order - (s->gather_ec && stag[2] != 0.0);
   if (s->dims == 2) {
     double sum = 0.0;
     long i0 = (long)floor(X[0] - stag[0]), j0 = (long)floor(X[1] - stag[1]);
     for (long j = j0 - 2; j <= j0 + 3; ++j) {
-      double sy = oracle_shape(o, X[1] - stag[1] - (double)j);
+      double sy = oracle_shape(oy, X[1] - stag[1] - (double)j);
       if (sy == 0.0) continue;
       for (long i = i0 - 2; i <= i0 + 3; ++i) {
-        double sx = oracle_shape(o, X[0] - stag[0] - (double)i);
+        double sx = oracle_shape(ox, X[0] - stag[0] - (double)i);
         if (sx == 0.0) continue;
         sum += F[idx(s, i, j, 0)] * sx * sy;
       }
@@ -278,13 +290,13 @@ static double gather_component(const orc_sim *s, const double *F, const double X
   double sum = 0.0;
   long i0 = (long)floor(X[0] - stag[0]), j0 = (long)floor(X[1] - stag[1]), k0 = (long)floor(X[2] - stag[2]);
   for (long k = k0 - 2; k <= k0 + 3; ++k) {
-    double sz = oracle_shape(o, X[2] - stag[2] - (double)k);
+    double sz = oracle_shape(oz, X[2] - stag[2] - (double)k);
     if (sz == 0.0) continue;
     for (long j = j0 - 2; j <= j0 + 3; ++j) {
-      double sy = oracle_shape(o, X[1] - stag[1] - (double)j);
+      double sy = oracle_shape(oy, X[1] - stag[1] - (double)j);
       if (sy == 0.0) continue;
       for (long i = i0 - 2; i <= i0 + 3; ++i) {
-        double sx = oracle_shape(o, X[0] - stag[0] - (double)i);
+        double sx = oracle_shape(ox, X[0] - stag[0] - (double)i);
         if (sx == 0.0) continue;
         sum += F[idx(s, i, j, k)] * sx * sy * sz;
       }
@@ -520,6 +532,50 @@ static void mur_apply(orc_sim *s, double t_old, double t_new) {
 }
 
 /* Field-only update, exposed for the Yee dispersion and Courant pins. */
+/* ------------------------------------------------------------------ */
+/* Current smoothing (a standard PIC addition; the paper's §2 leaves   */
+/* such details out).  One pass along axis a replaces every value by   */
+/*   alpha f(i) + (1 - alpha)/2 (f(i-1) + f(i+1))   (periodic),        */
+/* which multiplies a Fourier mode exp(i k x) by alpha + (1 - alpha)    */
+/* cos(k dx).  The binomial pass is alpha = 1/2 (factor cos^2(k dx/2)); */
+/* after n of them the compensating pass alpha = 1 + n/2 cancels the    */
+/* k^2 term of the product.                                            */
+/* ------------------------------------------------------------------ */
+static void smooth_axis(orc_sim *s, double *f, int axis, double alpha) {
+  double *tmp = (double *)malloc(sizeof(double) * s->ncell);
+  memcpy(tmp, f, sizeof(double) * s->ncell);
+  double side = 0.5 * (1.0 - alpha);
+  for (long k = 0; k < s->n[2]; ++k)
+    for (long j = 0; j < s->n[1]; ++j)
+      for (long i = 0; i < s->n[0]; ++i) {
+        long lo = axis == 0 ? idx(s, i - 1, j, k) : axis == 1 ? idx(s, i, j - 1, k) : idx(s, i, j, k - 1);
+        long hi = axis == 0 ? idx(s, i + 1, j, k) : axis == 1 ? idx(s, i, j + 1, k) : idx(s, i, j, k + 1);
+        f[idx(s, i, j, k)] = alpha * tmp[idx(s, i, j, k)] + side * (tmp[lo] + tmp[hi]);
+      }
+  free(tmp);
+}
+
+static void smooth_field(orc_sim *s, double *f) {
+  for (int p = 0; p < s->filter_passes; ++p)
+    for (int a = 0; a < s->dims; ++a) smooth_axis(s, f, a, 0.5);
+  if (s->filter_comp && s->filter_passes > 0)
+    for (int a = 0; a < s->dims; ++a) smooth_axis(s, f, a, 1.0 + 0.5 * s->filter_passes);
+}
+
+void oracle_set_filter(void *h, int passes, int compensate) {
+  orc_sim *s = (orc_sim *)h;
+  s->filter_passes = passes;
+  s->filter_comp = compensate;
+}
+
+void oracle_set_gather(void *h, int energy_conserving) { ((orc_sim *)h)->gather_ec = energy_conserving; }
+
+/* Apply the configured smoothing to one stored field (test hook). */
+void oracle_smooth(void *h, int which) {
+  orc_sim *s = (orc_sim *)h;
+  smooth_field(s, s->f[which]);
+}
+
 static void field_cycle(orc_sim *s) {
   double t_old = s->step * s->dt, t_new = (s->step + 1) * s->dt;
   yee_b(s, 0.5 * s->dt);
@@ -580,6 +636,8 @@ void oracle_step(void *h, int nsteps) {
         p->z = r1[2];
       }
     }
+    if (s->filter_passes > 0)
+      for (int c = 0; c < 3; ++c) smooth_field(s, s->f[ORC_JX + c]);
     field_cycle(s);
     s->step++;
   }
@@ -671,6 +729,9 @@ void oracle_diag(void *h, double *out) {
   }
   double *rho = s->f[ORC_RHO];
   deposit_rho(s, rho);
+  /* with current smoothing, Gauss's law holds for the equally smoothed
+   * charge (the filter commutes with the difference operators) */
+  if (s->filter_passes > 0) smooth_field(s, rho);
   double q = 0, gmax = 0;
   for (long k = 0; k < s->n[2]; ++k)
     for (long j = 0; j < s->n[1]; ++j)
