@@ -45,8 +45,9 @@ PUSH_BYTES_PER_PARTICLE = {"fp32": 60, "fp64": 4 + 24 + 24 + 8 + 4 + 24 + 24}
 PUSH_BYTES_PER_CELL = {"fp32": 48, "fp64": 96}
 # DRAM bytes (read + write) per particle of one push launch, from the ncu
 # capture summarised in profiles/k_push_thermal3d_128.md (128^3 case of the
-# same kernel, scaled by the particle count); None once the kernel changes.
-PUSH_TRAFFIC_PER_PARTICLE = {"fp32": 62.7}
+# same plasma, scaled by the particle count); None for workloads and
+# precisions not captured, and once the kernel changes.
+PUSH_TRAFFIC_PER_PARTICLE = {("thermal3d_256", "fp32"): 62.7, ("thermal3d_128", "fp32"): 62.7}
 
 
 def _peaks():
@@ -185,6 +186,12 @@ def generate(wl, isp, nproc):
     return synth.SharedParticles(wl, isp, nproc=nproc)
 
 
+# Above STREAM_PARTICLES the inputs are not held on the host in full: each
+# species is generated and loaded CHUNK_PARTICLES at a time (appending loads).
+STREAM_PARTICLES = 1 << 28
+CHUNK_PARTICLES = 1 << 25
+
+
 def run_gpu(args, rank: int, world: int, local: int):
     import torch
     from paper_1503_02464_gb300 import capi
@@ -193,9 +200,19 @@ def run_gpu(args, rank: int, world: int, local: int):
     wl = synth.preset(args.workload)
     if world > 1:
         wl.seed += 7919 * rank  # independent replica per rank
+    streamed = wl.n_particles() > STREAM_PARTICLES
     # host inputs first (spawned pool, before the first CUDA call)
     t_gen = time.perf_counter()
-    host = [generate(wl, isp, args.nproc) for isp in range(len(wl.species))]
+    pool = None
+    if streamed:
+        import multiprocessing as mp
+        host = []
+        pool = mp.get_context("spawn").Pool(args.nproc or min(16, os.cpu_count() or 1))
+        if not args.no_e2e:
+            print("bench: e2e leg skipped (inputs of this size are generated piece by piece)", file=sys.stderr)
+            args.no_e2e = True
+    else:
+        host = [generate(wl, isp, args.nproc) for isp in range(len(wl.species))]
     t_gen = time.perf_counter() - t_gen
 
     torch.cuda.set_device(local)
@@ -204,18 +221,30 @@ def run_gpu(args, rank: int, world: int, local: int):
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
     capi.load()
     stream = torch.cuda.current_stream()
-    npart = sum(h.n for h in host)
+    npart = wl.n_particles() if streamed else sum(h.n for h in host)
     ncell = wl.ncells
 
     def make_sim(precision):
         return Simulation.from_workload(wl, precision=precision, stream=stream.cuda_stream)
 
     def load_device(sim):
-        for isp, (sp, h) in enumerate(zip(wl.species, host)):
-            s = sim.add_species(sp.q, sp.m, h.n)
-            dev = {k: torch.from_numpy(v).to("cuda") for k, v in h.arrays.items()}
-            sim.load(s, dev)
-            del dev
+        if streamed:
+            for isp, sp in enumerate(wl.species):
+                ncs = int(wl.species_cells(sp).size)
+                s = sim.add_species(sp.q, sp.m, ncs * sp.ppc)
+                step = max(CHUNK_PARTICLES // sp.ppc, 1)
+                for c0 in range(0, ncs, step):
+                    h = synth.SharedParticles(wl, isp, cell_range=(c0, c0 + step), pool=pool)
+                    dev = {k: torch.from_numpy(v).to("cuda") for k, v in h.arrays.items()}
+                    sim.load(s, dev)
+                    del dev
+                    h.close()
+        else:
+            for isp, (sp, h) in enumerate(zip(wl.species, host)):
+                s = sim.add_species(sp.q, sp.m, h.n)
+                dev = {k: torch.from_numpy(v).to("cuda") for k, v in h.arrays.items()}
+                sim.load(s, dev)
+                del dev
         if wl.neutralize:
             sim.neutralize()
 
@@ -235,7 +264,10 @@ def run_gpu(args, rank: int, world: int, local: int):
     results = {}
     # ---------------- FP32 device-resident run (the headline value)
     sim = make_sim(args.precision)
+    t_load = time.perf_counter()
     load_device(sim)
+    torch.cuda.synchronize()
+    t_load = time.perf_counter() - t_load
     sim.step(args.warmup)
     torch.cuda.synchronize()
     l0 = sim.launch_count()
@@ -257,7 +289,12 @@ def run_gpu(args, rank: int, world: int, local: int):
 
     # ---------------- FP64 path on the same workload (fewer steps)
     fp64 = None
-    if args.fp64_steps > 0:
+    # FP64 record: cell 4 + offsets 24 + u 24 + w 8 + id 4 = 64 B, double-buffered, + a 4 B sort rank
+    fp64_bytes = npart * (2 * 64 + 4)
+    if args.fp64_steps > 0 and fp64_bytes > 0.8 * torch.cuda.get_device_properties(local).total_memory:
+        fp64 = {"skipped": f"FP64 particle storage of this workload ({fp64_bytes / 1e9:.0f} GB) exceeds 80 % "
+                           f"of device memory"}
+    elif args.fp64_steps > 0:
         sim = make_sim("fp64")
         load_device(sim)
         sim.step(min(args.warmup, 3))
@@ -354,6 +391,9 @@ def run_gpu(args, rank: int, world: int, local: int):
 
     for h in host:
         h.close()
+    if pool is not None:
+        pool.close()
+        pool.join()
 
     if rank != 0:
         return
@@ -369,16 +409,16 @@ def run_gpu(args, rank: int, world: int, local: int):
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * r["dt"] / args.steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": "f32" if args.precision == "fp32" else "f64", "data": "synthetic",
-        "config": {"workload": f"{wl.name}: {wl.dims}D3V periodic thermal plasma "
-                               f"{'x'.join(map(str, wl.n[:wl.dims]))} cells, {wl.species[0].ppc} ppc, "
-                               f"{npart} electrons, u_th={wl.species[0].u_th}, "
-                               f"{'TSC' if wl.order == 2 else 'CIC'}, dx={wl.d[0]}, dt={wl.dt}, "
+        "config": {"workload": f"{wl.name}: {wl.note}, "
+                               f"{'x'.join(map(str, wl.n[:wl.dims]))} cells, "
+                               f"{sum(sp.ppc for sp in wl.species)} ppc, {npart} particles, "
+                               f"u_th={wl.species[0].u_th}, dx={wl.d[0]}, dt={wl.dt}, "
                                f"sort every {wl.sort_every}",
                    "particles": npart, "cells": ncell, "precision": args.precision,
                    "l2": "inputs larger than L2 (particle arrays > 4 GB, fields 0.6 GB)",
                    "parallelism": "replicas" if world > 1 else "single GPU"},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-                     "traffic": (PUSH_TRAFFIC_PER_PARTICLE.get(args.precision) or 0) * npart or None,
+                     "traffic": (PUSH_TRAFFIC_PER_PARTICLE.get((wl.name, args.precision)) or 0) * npart or None,
                      "kernel": "k_push (fused gather/Boris/move/Esirkepov)",
                      "peak_kind": f"{peak_kind} HBM copy bandwidth",
                      "bytes_per_launch": alg_bytes, "ms_per_launch": push_avg_s * 1e3},
@@ -387,7 +427,8 @@ def run_gpu(args, rank: int, world: int, local: int):
         "clocks": r["clocks"],
         "diag_after": {k: r["diag"][k] for k in ("energy_field", "energy_kinetic", "n_alive", "n_escaped",
                                                    "gauss_max")},
-        "setup_s": {"generate": t_gen},
+        "setup_s": {"generate": t_gen, "load": t_load,
+                    "note": "load = generate + copy piece by piece" if streamed else "load = device copy"},
     }
     if fp64 is not None:
         line["fp64"] = fp64

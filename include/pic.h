@@ -108,7 +108,26 @@ typedef struct {
                           and still use the tile's shared-memory window (0 = 1) */
   pic_laser laser;
   void *stream;        /* cudaStream_t                                         */
+  /* Current smoothing after the deposit, before the E update (a standard
+   * PIC step the paper's §2 does not detail): filter_passes three-point
+   * binomial passes J(i) <- J(i)/2 + (J(i-1) + J(i+1))/4 along every axis
+   * (periodic), each multiplying a Fourier mode by cos^2(k dx/2); with
+   * filter_compensate one more pass with weights alpha = 1 + passes/2 and
+   * (1 - alpha)/2 cancels the k^2 term.  0..8 passes; 0 = off.  The FP64
+   * diagnostics then test Gauss's law and continuity on the equally smoothed
+   * charge (the filter commutes with the Yee differences). */
+  int filter_passes;
+  int filter_compensate;
+  /* Field gather (§2: the g-weighted average of the grid fields):
+   * PIC_GATHER_MOMENTUM uses the shape of order shape_order at every Yee
+   * location; PIC_GATHER_ENERGY lowers the order by one along each axis on
+   * which a component sits at a half-integer position (CIC -> nearest grid
+   * point, TSC -> CIC there), the energy-conserving variant. */
+  int gather;
 } pic_config;
+
+#define PIC_GATHER_MOMENTUM 0
+#define PIC_GATHER_ENERGY 1
 
 /* FP64 diagnostics (all reductions accumulate in double). */
 typedef struct {
@@ -222,7 +241,8 @@ int pic_sync(pic_handle *h);
  * starts recording (clearing previous records).  pic_timings synchronises
  * and writes, for up to nmax kernel classes, total milliseconds and launch
  * counts; class order: 0 sort, 1 zero J, 2 push, 3 Yee B, 4 Yee E,
- * 5 boundary.  Returns the number of classes written in *ncls. */
+ * 5 boundary, 6 current smoothing.  Returns the number of classes written
+ * in *ncls. */
 int pic_profile(pic_handle *h, int enable);
 int pic_timings(pic_handle *h, double *ms, int64_t *launches, int nmax, int *ncls);
 

@@ -14,9 +14,10 @@ from typing import Optional
 PIC_OK, PIC_EINVAL, PIC_ECOURANT, PIC_ENOMEM, PIC_ECUDA, PIC_EOVERFLOW, PIC_ETIMEOUT, PIC_ENAN = range(8)
 PIC_FP32, PIC_FP64 = 0, 1
 PIC_BC_PERIODIC, PIC_BC_ABSORBING = 0, 1
+PIC_GATHER_MOMENTUM, PIC_GATHER_ENERGY = 0, 1
 PIC_MEM_HOST, PIC_MEM_DEVICE = 0, 1
 PIC_EX, PIC_EY, PIC_EZ, PIC_BX, PIC_BY, PIC_BZ, PIC_JX, PIC_JY, PIC_JZ, PIC_RHO = range(10)
-KERNEL_CLASSES = ["sort", "zero_j", "push", "yee_b", "yee_e", "boundary"]
+KERNEL_CLASSES = ["sort", "zero_j", "push", "yee_b", "yee_e", "boundary", "filter"]
 
 ERROR_NAMES = {0: "PIC_OK", 1: "PIC_EINVAL", 2: "PIC_ECOURANT", 3: "PIC_ENOMEM", 4: "PIC_ECUDA",
                5: "PIC_EOVERFLOW", 6: "PIC_ETIMEOUT", 7: "PIC_ENAN"}
@@ -40,7 +41,8 @@ class pic_config(ctypes.Structure):
                 ("dt", ctypes.c_double), ("shape_order", ctypes.c_int), ("precision", ctypes.c_int),
                 ("bc_lo", ctypes.c_int * 3), ("bc_hi", ctypes.c_int * 3), ("sort_every", ctypes.c_int),
                 ("tile", ctypes.c_int * 3), ("drift_guard", ctypes.c_int), ("laser", pic_laser),
-                ("stream", ctypes.c_void_p)]
+                ("stream", ctypes.c_void_p), ("filter_passes", ctypes.c_int), ("filter_compensate", ctypes.c_int),
+                ("gather", ctypes.c_int)]
 
 
 class pic_diag_t(ctypes.Structure):

@@ -356,6 +356,10 @@ int pic_create(const pic_config *cfg, pic_handle **out) {
       return fail(nullptr, PIC_EINVAL, "bad laser parameters");
   }
   if (c.dims == 2 && c.n[2] != 1 && c.n[2] != 0) return fail(nullptr, PIC_EINVAL, "2D needs n[2] = 1");
+  if (c.filter_passes < 0 || c.filter_passes > 8 || (c.filter_compensate != 0 && c.filter_compensate != 1))
+    return fail(nullptr, PIC_EINVAL, "filter_passes must be 0..8 and filter_compensate 0 or 1");
+  if (c.gather != PIC_GATHER_MOMENTUM && c.gather != PIC_GATHER_ENERGY)
+    return fail(nullptr, PIC_EINVAL, "gather must be PIC_GATHER_MOMENTUM or PIC_GATHER_ENERGY");
   if (!(c.dt > 0)) return fail(nullptr, PIC_EINVAL, "dt must be positive");
   double s = 0;
   for (int d = 0; d < c.dims; ++d) s += 1.0 / (c.dx[d] * c.dx[d]);
@@ -391,6 +395,7 @@ int pic_create(const pic_config *cfg, pic_handle **out) {
   g.ncell = ncell;
   g.drift = 1;
   g.absorb_lo = c.bc_lo[0] == PIC_BC_ABSORBING;
+  g.gather_ec = c.gather == PIC_GATHER_ENERGY;
   g.absorb_hi = c.bc_hi[0] == PIC_BC_ABSORBING;
   g.ntiles = 1;
   for (int d = 0; d < 3; ++d) {
@@ -661,6 +666,17 @@ int pic_step(pic_handle *h, int nsteps) {
       s.fresh = false;
       h->launches += nl;
     }
+    if (h->cfg.filter_passes > 0) {
+      Timed tm(h, pic::KC_FILTER);
+      for (int d = 0; d < 3; ++d) {
+        int nl = 0;
+        CK(h,
+           pic::launch_smooth(h->g, h->J[d], false, h->f64, h->cfg.filter_passes, h->cfg.filter_compensate, h->st,
+                              &nl),
+           "smooth J");
+        h->launches += nl;
+      }
+    }
     {
       Timed tm(h, pic::KC_YEE_B);
       CK(h, pic::launch_yee_b(h->g, h->E, h->B, 0.5 * h->g.dt, h->st), "yee B");
@@ -774,6 +790,13 @@ int pic_diag(pic_handle *h, pic_diag_t *out) {
   memset(out, 0, sizeof(*out));
   int r = compute_rho(h, h->rho);
   if (r) return r;
+  if (h->cfg.filter_passes > 0) {
+    // Gauss's law and continuity hold for the equally smoothed charge
+    int nl = 0;
+    CK(h, pic::launch_smooth(h->g, h->rho, true, h->f64, h->cfg.filter_passes, h->cfg.filter_compensate, h->st, &nl),
+       "smooth rho");
+    h->launches += nl;
+  }
   CK(h, cudaMemsetAsync(h->red, 0, 16 * sizeof(double), h->st), "memset");
   const bool have_prev = h->rho_prev_step == h->step - 1;
   CK(h, pic::launch_field_diag(h->g, h->E, h->B, h->J, h->rho, have_prev ? h->rho_prev : nullptr, h->red, h->st),
@@ -922,6 +945,8 @@ int pic_adjoint_begin(pic_handle *h, int64_t id_capacity) {
   if (!h) return fail(h, PIC_EINVAL, "NULL handle");
   if (h->g.dims != 2 || h->g.order != 2)
     return fail(h, PIC_EINVAL, "adjoint kernels exist for 2D3V with the TSC shape only");
+  if (h->cfg.filter_passes > 0 || h->cfg.gather != PIC_GATHER_MOMENTUM)
+    return fail(h, PIC_EINVAL, "adjoint kernels cover the unfiltered momentum-conserving cycle only");
   if (id_capacity <= 0 || id_capacity > 0x7fffffffLL) return fail(h, PIC_EINVAL, "bad id capacity");
   if (!h->adj_ready || h->id_cap != id_capacity) {
     free_adjoint(h);

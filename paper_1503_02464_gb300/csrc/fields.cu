@@ -366,7 +366,65 @@ __global__ void __launch_bounds__(256)
   if (threadIdx.x == 0) atomicAdd(out + 2, v);
 }
 
+// One smoothing pass along `axis`: out = alpha in + side (in[-1] + in[+1]),
+// periodic (side = (1 - alpha)/2).  A Fourier mode exp(i k x) is multiplied
+// by alpha + (1 - alpha) cos(k dx).
+template <class R>
+__global__ void __launch_bounds__(256)
+    k_smooth_axis(const R *__restrict__ in, R *__restrict__ out, int n0, int n1, int n2, int axis, R alpha, R side) {
+  const int64_t ncell = (int64_t)n0 * n1 * n2;
+  const int64_t sy = n0, sz = (int64_t)n0 * n1;
+  for (int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; c < ncell; c += (int64_t)gridDim.x * blockDim.x) {
+    int64_t lo, hi;
+    if (axis == 0) {
+      const int i = (int)(c % n0);
+      lo = c + (i > 0 ? -1 : n0 - 1);
+      hi = c + (i + 1 < n0 ? 1 : 1 - n0);
+    } else if (axis == 1) {
+      const int j = (int)((c / n0) % n1);
+      lo = c + (j > 0 ? -sy : sy * (n1 - 1));
+      hi = c + (j + 1 < n1 ? sy : sy - sy * n1);
+    } else {
+      const int k = (int)(c / sz);
+      lo = c + (k > 0 ? -sz : sz * (n2 - 1));
+      hi = c + (k + 1 < n2 ? sz : sz - sz * n2);
+    }
+    out[c] = alpha * in[c] + side * (in[lo] + in[hi]);
+  }
+}
+
+template <class R>
+cudaError_t smooth_t(const Grid &g, R *f, R *tmp, int passes, int compensate, cudaStream_t st, int *nlaunch) {
+  const int nb = grid_blocks(g.ncell, 256);
+  R *src = f, *dst = tmp;
+  int nl = 0;
+  auto pass = [&](int axis, double alpha) {
+    k_smooth_axis<R><<<nb, 256, 0, st>>>(src, dst, g.n[0], g.n[1], g.n[2], axis, (R)alpha, (R)(0.5 * (1.0 - alpha)));
+    R *t = src;
+    src = dst;
+    dst = t;
+    ++nl;
+  };
+  for (int p = 0; p < passes; ++p)
+    for (int a = 0; a < g.dims; ++a) pass(a, 0.5);
+  if (compensate && passes > 0)
+    for (int a = 0; a < g.dims; ++a) pass(a, 1.0 + 0.5 * passes);
+  if (nlaunch) *nlaunch = nl;
+  if (src != f) {
+    const cudaError_t e = cudaMemcpyAsync(f, src, sizeof(R) * (size_t)g.ncell, cudaMemcpyDeviceToDevice, st);
+    if (e != cudaSuccess) return e;
+  }
+  return cudaGetLastError();
+}
+
 }  // namespace
+
+cudaError_t launch_smooth(const Grid &g, void *f, bool f64, void *tmp, int passes, int compensate, cudaStream_t st,
+                          int *nlaunch) {
+  if (f64 || g.prec == 1)
+    return smooth_t<double>(g, static_cast<double *>(f), static_cast<double *>(tmp), passes, compensate, st, nlaunch);
+  return smooth_t<float>(g, static_cast<float *>(f), static_cast<float *>(tmp), passes, compensate, st, nlaunch);
+}
 
 cudaError_t launch_yee_b(const Grid &g, void *const E[3], void *const B[3], double h, cudaStream_t st) {
   const int nb = grid_blocks(g.ncell, 256);

@@ -32,29 +32,46 @@ template <class R> __device__ __forceinline__ void tsc3(R d, R w[3]) {
 // Gather stencil along one axis for a particle at cell-relative offset f.
 // Integer ("primal") positions m sit at m; half-integer ("dual") positions m
 // sit at m + 1/2.  `rel` is the first node relative to the particle's cell.
+// With `lower` (the energy-conserving gather) the half-integer weights use
+// the shape one order lower: CIC instead of TSC, the nearest grid point (the
+// half-integer node of the particle's own cell) instead of CIC.
 template <class R, int ORDER> struct GatherAxis {
   static constexpr int NS = ORDER + 1;
   int relp, reld;
   R wp[NS], wd[NS];
-  __device__ __forceinline__ void set(R f) {
+  __device__ __forceinline__ void cic_dual(R f) {
+    if (f >= R(0.5)) {
+      reld = 0;
+      wd[0] = R(1.5) - f;
+      wd[1] = f - R(0.5);
+    } else {
+      reld = -1;
+      wd[0] = R(0.5) - f;
+      wd[1] = R(0.5) + f;
+    }
+  }
+  __device__ __forceinline__ void set(R f, bool lower = false) {
     if (ORDER == 2) {
       const int h = f >= R(0.5);
       relp = h - 1;
       tsc3<R>(f - R(h), wp);
-      reld = -1;
-      tsc3<R>(f - R(0.5), wd);
+      if (lower) {
+        cic_dual(f);
+        wd[2] = R(0);
+      } else {
+        reld = -1;
+        tsc3<R>(f - R(0.5), wd);
+      }
     } else {
       relp = 0;
       wp[0] = R(1) - f;
       wp[1] = f;
-      if (f >= R(0.5)) {
+      if (lower) {
         reld = 0;
-        wd[0] = R(1.5) - f;
-        wd[1] = f - R(0.5);
+        wd[0] = R(1);
+        wd[1] = R(0);
       } else {
-        reld = -1;
-        wd[0] = R(0.5) - f;
-        wd[1] = R(0.5) + f;
+        cic_dual(f);
       }
     }
   }

@@ -23,6 +23,7 @@ struct Grid {
   int drift;       // cells a particle may leave its tile and still use the window
   int64_t ncell;
   int absorb_lo, absorb_hi;  // x walls absorbing
+  int gather_ec;             // energy-conserving gather (lower order at half-integer positions)
 };
 
 // Laser entering through the x = 0 wall (copied from pic_config).
@@ -60,7 +61,9 @@ void set_global_error(const std::string &msg);
 
 constexpr int kTilePad = 4;
 
-enum KernelClass { KC_SORT = 0, KC_ZEROJ = 1, KC_PUSH = 2, KC_YEE_B = 3, KC_YEE_E = 4, KC_BOUNDARY = 5, KC_N = 6 };
+enum KernelClass {
+  KC_SORT = 0, KC_ZEROJ = 1, KC_PUSH = 2, KC_YEE_B = 3, KC_YEE_E = 4, KC_BOUNDARY = 5, KC_FILTER = 6, KC_N = 7
+};
 
 // ---- push (push.cu) ----
 // Tile shape compiled into the push kernel (8x8x4 in 3D, 16x16 in 2D); the
@@ -109,6 +112,12 @@ cudaError_t launch_unload(const Grid &g, const Particles &p, const int64_t *d_co
                           double *y, double *z, double *ux, double *uy, double *uz, double *w, uint32_t *id,
                           int32_t *alive, cudaStream_t st);
 cudaError_t launch_field_to_f64(const Grid &g, const void *src, double *dst, cudaStream_t st);
+// Current smoothing of one field in place: `passes` binomial passes along
+// every axis, then (compensate) one compensating pass.  f64 selects the
+// element type (double, else the grid's precision); tmp holds ncell elements
+// of that type.  *nlaunch receives the kernels launched.
+cudaError_t launch_smooth(const Grid &g, void *f, bool f64, void *tmp, int passes, int compensate, cudaStream_t st,
+                          int *nlaunch);
 cudaError_t launch_field_from_f64(const Grid &g, const double *src, void *dst, cudaStream_t st);
 cudaError_t launch_rho(const Grid &g, const Particles &p, const int64_t *d_count, int64_t nmax, double q,
                        double *rho, cudaStream_t st);

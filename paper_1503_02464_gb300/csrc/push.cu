@@ -95,6 +95,7 @@ template <class R> struct PushArgs {
   R jfac[3];  // -q dx_a / dt  (Esirkepov running-sum scale, times w)
   R qz;       // q            (2D3V: Jz = q w vz S)
   int absorb;  // absorbing x walls: remove particles leaving [kWallLo, n0 - kWallHiMargin)
+  int ec;      // energy-conserving gather
   Counters *ctr;
 };
 
@@ -499,9 +500,9 @@ __global__ void __launch_bounds__(kThreads, sizeof(R) == 4 ? 2 : 1) k_push(const
           }
           // ---- gather (§2: g-weighted average of the grid fields) ----
           GatherAxis<R, ORDER> gx, gy, gz;
-          gx.set(f[0]);
-          gy.set(f[1]);
-          gz.set(f[2]);
+          gx.set(f[0], a.ec);
+          gy.set(f[1], a.ec);
+          gz.set(f[2], a.ec);
           constexpr int oE = G::D + G::LOE;
           const int xp = l[0] + gx.relp + oE, xd = l[0] + gx.reld + oE;
           const int yp = (l[1] + gy.relp + oE) * G::EX, yd = (l[1] + gy.reld + oE) * G::EX;
@@ -635,7 +636,7 @@ __global__ void __launch_bounds__(kThreads) k_push_escaped(const PushArgs<R> a) 
     }
     GatherAxis<R, ORDER> ga[3];
 #pragma unroll
-    for (int d = 0; d < 3; ++d) ga[d].set(f[d]);
+    for (int d = 0; d < 3; ++d) ga[d].set(f[d], a.ec);
     const int64_t sy = a.n[0], sz = (int64_t)a.n[0] * a.n[1];
     auto fetch = [&](const R *F, const bool dual[3]) {
       R acc = R(0);
@@ -769,6 +770,7 @@ cudaError_t launch_t(const Grid &g, void *const E[3], void *const B[3], void *co
   a.qmh = (R)(q * g.dt / (2.0 * m));
   a.qz = (R)q;
   a.absorb = g.absorb_lo || g.absorb_hi;
+  a.ec = g.gather_ec;
   a.ctr = ctr;
   constexpr size_t smem = smem_bytes<R, DIM, ORDER>();
   auto fn = k_push<R, DIM, ORDER>;

@@ -30,7 +30,8 @@ def _ptr(a):
 
 def make_config(dims: int, n, d, dt: float, order: int, precision: str = "fp32", sort_every: int = 20,
                 tile=None, drift_guard: int = 0, absorbing_x: bool = False, laser: Optional[dict] = None,
-                stream: Optional[int] = None) -> capi.pic_config:
+                stream: Optional[int] = None, filter_passes: int = 0, filter_compensate: bool = False,
+                gather: str = "momentum") -> capi.pic_config:
     cfg = capi.pic_config()
     cfg.dims = dims
     nn = list(n) + [1] * (3 - len(n))
@@ -59,6 +60,9 @@ def make_config(dims: int, n, d, dt: float, order: int, precision: str = "fp32",
         cfg.laser.z_center = float(laser.get("z_center", 0.5 * nn[2] * dd[2]))
         cfg.laser.polarization = int(laser.get("pol", 1))
     cfg.stream = stream
+    cfg.filter_passes = int(filter_passes)
+    cfg.filter_compensate = 1 if filter_compensate else 0
+    cfg.gather = {"momentum": capi.PIC_GATHER_MOMENTUM, "energy": capi.PIC_GATHER_ENERGY}[gather]
     return cfg
 
 
@@ -67,13 +71,13 @@ class Simulation:
 
     def __init__(self, dims: int, n, d, dt: float, order: int, precision: str = "fp32", sort_every: int = 20,
                  tile=None, drift_guard: int = 0, absorbing_x: bool = False, laser: Optional[dict] = None,
-                 stream=None):
+                 stream=None, filter_passes: int = 0, filter_compensate: bool = False, gather: str = "momentum"):
         capi.load()
         if stream is None:
             import torch
             stream = torch.cuda.current_stream().cuda_stream
         self.cfg = make_config(dims, n, d, dt, order, precision, sort_every, tile, drift_guard, absorbing_x,
-                               laser, stream)
+                               laser, stream, filter_passes, filter_compensate, gather)
         self.dims = dims
         self.n = tuple(self.cfg.n)
         self.d = tuple(self.cfg.dx)

@@ -142,6 +142,7 @@ class Workload:
     absorbing_x: bool = False
     laser: Optional[dict] = None
     neutralize: bool = True
+    note: str = ""                      # one-line description of the plasma
 
     @property
     def ncells(self) -> int:
@@ -173,8 +174,26 @@ def courant_limit(d: Sequence[float], dims: int) -> float:
     return 1.0 / math.sqrt(sum(1.0 / (x * x) for x in d[:dims]))
 
 
+_NOTES = {
+    "thermal2d_64": "2D3V periodic thermal plasma, electrons over immobile ions, CIC",
+    "thermal3d_256": "3D3V periodic thermal plasma, electrons over immobile ions, TSC",
+    "thermal3d_128": "3D3V periodic thermal plasma, electrons over immobile ions, TSC",
+    "laser_slab2d": "2D3V p-polarised laser on an overdense electron-proton slab, absorbing x, TSC",
+    "laser_foil3d": "3D3V linearly polarised laser on a thin electron-proton foil, absorbing x, TSC",
+    "twostream3d_512": "3D3V two counter-streaming electron beams (u=+-0.2 along x) over immobile ions, "
+                       "periodic, TSC (the paper's scaling test problem)",
+}
+
+
 def preset(name: str) -> Workload:
-    """The synthetic workloads (sizes of the paper's laser/thermal plasma runs)."""
+    """The synthetic workloads (sizes of the paper's laser/thermal plasma runs
+    and of the two-stream problem of its scaling study)."""
+    wl = _preset(name)
+    wl.note = _NOTES.get(name, "")
+    return wl
+
+
+def _preset(name: str) -> Workload:
     lam = TWO_PI  # laser wavelength in c/omega_0 units
     if name == "thermal2d_64":
         # 2D3V periodic plasma 64x64, dx=dy=0.05, dt=0.035, 16 ppc, u_th=0.01, CIC
@@ -251,13 +270,13 @@ _FIELDS = (("x", np.float64), ("y", np.float64), ("z", np.float64), ("ux", np.fl
 
 
 def _fill_chunk(args):
-    wl, isp, c0, c1, paths, n_total = args
+    wl, isp, c0, c1, base, paths, n_total = args
     sp = wl.species[isp]
     cells = wl.species_cells(sp)[c0:c1]
     p = wl.particles(isp, cells)
     for (key, dt), path in zip(_FIELDS, paths):
         arr = np.memmap(path, dtype=dt, mode="r+", shape=(n_total,))
-        arr[c0 * sp.ppc:c1 * sp.ppc] = p[key]
+        arr[(c0 - base) * sp.ppc:(c1 - base) * sp.ppc] = p[key]
         arr.flush()
         del arr
     return c1 - c0
@@ -266,28 +285,37 @@ def _fill_chunk(args):
 class SharedParticles:
     """Particle arrays of one species in memory-mapped temporary files, filled
     by a pool of worker processes (spawned, so it is safe after CUDA has
-    started).  ``arrays`` maps x, y, z, ux, uy, uz, w, id to numpy views."""
+    started).  ``arrays`` maps x, y, z, ux, uy, uz, w, id to numpy views.
+    ``cell_range`` = (c0, c1) restricts it to the species' cells c0 .. c1-1
+    (positions in ``Workload.species_cells`` order), so that a very large
+    species can be generated and loaded piece by piece; ``pool`` reuses a
+    caller's process pool."""
 
-    def __init__(self, wl: Workload, isp: int, nproc: int = 0, chunk_cells: int = 65536):
+    def __init__(self, wl: Workload, isp: int, nproc: int = 0, chunk_cells: int = 65536,
+                 cell_range: Optional[tuple] = None, pool=None):
         import multiprocessing as mp
         import os
         import tempfile
         sp = wl.species[isp]
         ncells = int(wl.species_cells(sp).size)
-        self.n = ncells * sp.ppc
+        c0, c1 = (0, ncells) if cell_range is None else (int(cell_range[0]), int(min(cell_range[1], ncells)))
+        self.n = max(c1 - c0, 0) * sp.ppc
         self._dir = tempfile.mkdtemp(prefix="picsynth_")
         self.paths = [os.path.join(self._dir, key + ".bin") for key, _ in _FIELDS]
         for (key, dt), path in zip(_FIELDS, self.paths):
             with open(path, "wb") as f:
                 f.truncate(max(self.n, 1) * np.dtype(dt).itemsize)
-        jobs = [(wl, isp, c, min(c + chunk_cells, ncells), self.paths, self.n) for c in range(0, ncells, chunk_cells)]
+        jobs = [(wl, isp, c, min(c + chunk_cells, c1), c0, self.paths, self.n) for c in range(c0, c1, chunk_cells)]
         nproc = nproc or min(16, os.cpu_count() or 1)
-        if nproc <= 1 or len(jobs) == 1:
+        if pool is not None and len(jobs) > 1:
+            for _ in pool.imap_unordered(_fill_chunk, jobs):
+                pass
+        elif nproc <= 1 or len(jobs) <= 1:
             for j in jobs:
                 _fill_chunk(j)
         else:
-            with mp.get_context("spawn").Pool(nproc) as pool:
-                for _ in pool.imap_unordered(_fill_chunk, jobs):
+            with mp.get_context("spawn").Pool(nproc) as own:
+                for _ in own.imap_unordered(_fill_chunk, jobs):
                     pass
         self.arrays = {key: np.memmap(path, dtype=dt, mode="r+", shape=(max(self.n, 1),))[:self.n]
                        for (key, dt), path in zip(_FIELDS, self.paths)}

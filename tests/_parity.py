@@ -50,19 +50,22 @@ def j_floor(wl, parts_list):
     return 4.0 * qw * max(wl.d[:wl.dims]) / wl.dt * 2 * np.spacing(float(n)) * ppc * 4 ** wl.dims
 
 
-def compare_fields(o, s, names=FIELDS, j_abs=0.0):
+def compare_fields(o, s, names=FIELDS, j_abs=0.0, joint_eb=False):
     """Error of each component relative to the max norm of its vector field
     (max over Ex, Ey, Ez for E; likewise B and J), so that a component that
     is zero up to round-off in some geometry is judged against the field it
-    belongs to.  For J the difference is first reduced by the absolute floor
-    j_abs (see j_floor)."""
+    belongs to.  With joint_eb, E and B share one norm, max(|E|, |B|) (same
+    units for c = 1): for electrostatic problems, where B is round-off.  For
+    J the difference is first reduced by the absolute floor j_abs (see
+    j_floor)."""
     got = {name: s.field(i) for i, name in enumerate(FIELDS)}
     ref = {name: o.get_field(i) for i, name in enumerate(FIELDS)}
     out = {}
     for name in FIELDS:
         if name not in names:
             continue
-        group = [g + c for g in (name[0],) for c in "xyz"]
+        heads = ("E", "B") if joint_eb and name[0] in "EB" else (name[0],)
+        group = [g + c for g in heads for c in "xyz"]
         norm = max(np.abs(ref[g]).max() for g in group)
         d = np.abs(got[name] - ref[name]).max()
         if name.startswith("J"):
