@@ -291,6 +291,70 @@ int pic_adjoint_step(pic_handle *h, int nsteps);
  * Synchronises. */
 int pic_grad(pic_handle *h, double *d_a0, int species, double *d_w, int mem_kind);
 
+/* ---- output manager (§3.1) --------------------------------------------
+ * The paper's output manager writes reduced-dimension outputs (a plane of a
+ * 3D run, a line of a multidimensional one) and sub-domain outputs (a small
+ * box of a large run), restricted in time to a window and a frequency.  A
+ * request here captures frames on the device, inside pic_step, into a
+ * device buffer it owns (reserved by pic_output_add); pic_output_read copies
+ * one frame out.  Frames are taken after a step completes: after step s
+ * (s = completed steps, 1, 2, ...) when first <= s <= last and
+ * (s - first) % every == 0 (pic_output_due).
+ *
+ * PIC_OUT_FIELD: field `which` (PIC_EX .. PIC_RHO) at the grid positions
+ *   (i, j, k) with lo <= (i, j, k) < hi (each component at its own Yee
+ *   location, index (i, j, k) as in pic_fields), FP64, x fastest;
+ *   count = box size.  PIC_RHO deposits the charge first.
+ * PIC_OUT_PARTICLES: the live particles of species `which` whose cell
+ *   (i, j, k) lies in the box, as records of 8 doubles (x, y, z, ux, uy, uz,
+ *   w, id) in the units of pic_load_particles; the record order is not
+ *   defined.  count = particles found; when it exceeds max_particles only
+ *   max_particles records are kept and pic_output_read returns
+ *   PIC_EOVERFLOW (the frame's count still says how many there were).
+ * In 2D lo[2] = 0, hi[2] = 1.  Frames past max_frames are dropped and
+ * counted (pic_output_count). */
+#define PIC_OUT_FIELD 0
+#define PIC_OUT_PARTICLES 1
+
+typedef struct {
+  int kind;              /* PIC_OUT_FIELD or PIC_OUT_PARTICLES                  */
+  int which;             /* field id or species index                           */
+  int lo[3], hi[3];      /* box [lo, hi), 0 <= lo < hi <= n per axis            */
+  int64_t first, last;   /* window of completed steps, 1 <= first <= last       */
+  int64_t every;         /* frame period in steps, >= 1                         */
+  int64_t max_frames;    /* frames reserved, >= 1                               */
+  int64_t max_particles; /* PIC_OUT_PARTICLES: records per frame, >= 1          */
+} pic_output_t;
+
+/* 1 if the request's schedule takes a frame after `step` completed steps,
+ * else 0.  Pure host function (no handle, no device). */
+int pic_output_due(const pic_output_t *req, int64_t step);
+
+/* Register a request and reserve its device buffer (max_frames frames of
+ * box-size doubles, or of 8 * max_particles doubles); *id receives its
+ * handle.  PIC_EINVAL for a bad kind, field, species, box or schedule;
+ * PIC_ENOMEM when the buffer cannot be reserved. */
+int pic_output_add(pic_handle *h, const pic_output_t *req, int *id);
+
+/* Take one frame of request id now, at the current step, outside the
+ * schedule (e.g. the initial state). */
+int pic_output_capture(pic_handle *h, int id);
+
+/* Frames held (*nframes) and frames dropped for lack of room (*dropped,
+ * may be NULL).  Synchronises. */
+int pic_output_count(pic_handle *h, int id, int64_t *nframes, int64_t *dropped);
+
+/* Copy frame `frame` (0 = oldest) of request id into out (host or device
+ * per mem_kind; room for the box size, or 8 * max_particles doubles);
+ * *count receives the values' count (FIELD) or the particles found
+ * (PARTICLES), *step (may be NULL) the completed steps at capture.
+ * Synchronises.  PIC_EOVERFLOW when a particle frame lost records. */
+int pic_output_read(pic_handle *h, int id, int64_t frame, double *out, int64_t *count, int64_t *step,
+                    int mem_kind);
+
+/* Release request id and its buffer (its id is not reused). */
+int pic_output_remove(pic_handle *h, int id);
+
 /* FP64 field energies without any device allocation.  The paper has no
  * counterpart: this is a library service for callers that must not call
  * cudaMalloc/cudaFree (which can synchronise the device), e.g. code embedded

@@ -15,6 +15,7 @@ PIC_OK, PIC_EINVAL, PIC_ECOURANT, PIC_ENOMEM, PIC_ECUDA, PIC_EOVERFLOW, PIC_ETIM
 PIC_FP32, PIC_FP64 = 0, 1
 PIC_BC_PERIODIC, PIC_BC_ABSORBING = 0, 1
 PIC_GATHER_MOMENTUM, PIC_GATHER_ENERGY = 0, 1
+PIC_OUT_FIELD, PIC_OUT_PARTICLES = 0, 1
 PIC_MEM_HOST, PIC_MEM_DEVICE = 0, 1
 PIC_EX, PIC_EY, PIC_EZ, PIC_BX, PIC_BY, PIC_BZ, PIC_JX, PIC_JY, PIC_JZ, PIC_RHO = range(10)
 KERNEL_CLASSES = ["sort", "zero_j", "push", "yee_b", "yee_e", "boundary", "filter"]
@@ -27,7 +28,8 @@ EXPORTED = ["pic_create", "pic_destroy", "pic_last_error", "pic_add_species", "p
             "pic_neutralize", "pic_set_background", "pic_step", "pic_fields", "pic_set_field", "pic_num_particles", "pic_particles",
             "pic_diag", "pic_energy", "pic_sync", "pic_profile", "pic_timings", "pic_launch_count", "pic_checkpoint",
             "pic_restore", "pic_tape_begin", "pic_adjoint_begin", "pic_adjoint_seed_kinetic", "pic_adjoint_step",
-            "pic_grad", "pic_field_energy_noalloc"]
+            "pic_grad", "pic_output_due", "pic_output_add", "pic_output_capture", "pic_output_count",
+            "pic_output_read", "pic_output_remove", "pic_field_energy_noalloc"]
 
 
 class pic_laser(ctypes.Structure):
@@ -43,6 +45,12 @@ class pic_config(ctypes.Structure):
                 ("tile", ctypes.c_int * 3), ("drift_guard", ctypes.c_int), ("laser", pic_laser),
                 ("stream", ctypes.c_void_p), ("filter_passes", ctypes.c_int), ("filter_compensate", ctypes.c_int),
                 ("gather", ctypes.c_int)]
+
+
+class pic_output_t(ctypes.Structure):
+    _fields_ = [("kind", ctypes.c_int), ("which", ctypes.c_int), ("lo", ctypes.c_int * 3), ("hi", ctypes.c_int * 3),
+                ("first", ctypes.c_int64), ("last", ctypes.c_int64), ("every", ctypes.c_int64),
+                ("max_frames", ctypes.c_int64), ("max_particles", ctypes.c_int64)]
 
 
 class pic_diag_t(ctypes.Structure):
@@ -119,6 +127,14 @@ def load(build_if_missing: bool = True) -> ctypes.CDLL:
         "pic_grad": ([hp, dp, ctypes.c_int, vp, ctypes.c_int], ctypes.c_int),
         "pic_field_energy_noalloc": ([ctypes.c_int, ctypes.c_void_p * 3, ctypes.c_void_p * 3, i64, ctypes.c_double,
                                       vp, ctypes.c_int, vp], ctypes.c_int),
+        "pic_output_due": ([ctypes.POINTER(pic_output_t), i64], ctypes.c_int),
+        "pic_output_add": ([hp, ctypes.POINTER(pic_output_t), ctypes.POINTER(ctypes.c_int)], ctypes.c_int),
+        "pic_output_capture": ([hp, ctypes.c_int], ctypes.c_int),
+        "pic_output_count": ([hp, ctypes.c_int, ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_int64)],
+                             ctypes.c_int),
+        "pic_output_read": ([hp, ctypes.c_int, i64, vp, ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_int64),
+                             ctypes.c_int], ctypes.c_int),
+        "pic_output_remove": ([hp, ctypes.c_int], ctypes.c_int),
     }
     for name, (args, res) in sig.items():
         fn = getattr(lib, name)
@@ -247,6 +263,51 @@ def pic_grad(h, species: int, dw_ptr, mem_kind: int) -> float:
     d_a0 = ctypes.c_double()
     check(h, load().pic_grad(h, ctypes.byref(d_a0), int(species), dw_ptr, int(mem_kind)))
     return d_a0.value
+
+
+def make_output(kind: int, which: int, lo, hi, first: int, last: int, every: int = 1, max_frames: int = 1,
+                max_particles: int = 1) -> pic_output_t:
+    r = pic_output_t()
+    r.kind, r.which = int(kind), int(which)
+    for a in range(3):
+        r.lo[a] = int(lo[a]) if a < len(lo) else 0
+        r.hi[a] = int(hi[a]) if a < len(hi) else 1
+    r.first, r.last, r.every = int(first), int(last), int(every)
+    r.max_frames, r.max_particles = int(max_frames), int(max_particles)
+    return r
+
+
+def pic_output_due(req: pic_output_t, step: int) -> bool:
+    return bool(load().pic_output_due(ctypes.byref(req), int(step)))
+
+
+def pic_output_add(h, req: pic_output_t) -> int:
+    i = ctypes.c_int()
+    check(h, load().pic_output_add(h, ctypes.byref(req), ctypes.byref(i)))
+    return i.value
+
+
+def pic_output_capture(h, oid: int) -> None:
+    check(h, load().pic_output_capture(h, int(oid)))
+
+
+def pic_output_count(h, oid: int):
+    n, d = ctypes.c_int64(), ctypes.c_int64()
+    check(h, load().pic_output_count(h, int(oid), ctypes.byref(n), ctypes.byref(d)))
+    return n.value, d.value
+
+
+def pic_output_read(h, oid: int, frame: int, out_ptr, mem_kind: int):
+    """Returns (count, step); raises PicError (PIC_EOVERFLOW) for a particle
+    frame that lost records."""
+    n, st = ctypes.c_int64(), ctypes.c_int64()
+    check(h, load().pic_output_read(h, int(oid), int(frame), out_ptr, ctypes.byref(n), ctypes.byref(st),
+                                    int(mem_kind)))
+    return n.value, st.value
+
+
+def pic_output_remove(h, oid: int) -> None:
+    check(h, load().pic_output_remove(h, int(oid)))
 
 
 def pic_launch_count(h) -> int:

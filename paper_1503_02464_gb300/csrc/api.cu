@@ -67,6 +67,17 @@ struct SpeciesAdjoint {
   double *lw = nullptr;
 };
 
+// One output request (§3.1 output manager) and the frames it holds.
+struct OutputReq {
+  pic_output_t req{};
+  bool active = false;
+  double *buf = nullptr;                  // max_frames * frame_doubles
+  unsigned long long *found = nullptr;    // particles found per frame (device)
+  int64_t frame_doubles = 0;
+  std::vector<int64_t> steps;             // completed steps at each frame
+  int64_t dropped = 0;
+};
+
 std::string g_create_error;
 
 }  // namespace
@@ -105,6 +116,8 @@ struct pic_handle {
   double *pend = nullptr, *da0 = nullptr, *objF = nullptr;
   unsigned long long *adj_err = nullptr;
   SpeciesAdjoint adj[kMaxSpecies];
+  // output manager
+  std::vector<OutputReq> outputs;
 };
 
 namespace {
@@ -490,6 +503,10 @@ int pic_destroy(pic_handle *h) {
     cudaFree(s.tile_start);
     cudaFree(s.tq);
   }
+  for (auto &o : h->outputs) {
+    cudaFree(o.buf);
+    cudaFree(o.found);
+  }
   for (auto &t : h->timers) {
     cudaEventDestroy(t.a);
     cudaEventDestroy(t.b);
@@ -631,6 +648,148 @@ int pic_set_background(pic_handle *h, const double *rho_bg, int mem_kind) {
   return PIC_OK;
 }
 
+namespace {
+
+// Take one frame of an output request at the current state (or count it as
+// dropped when its buffer is full).
+int output_capture(pic_handle *h, OutputReq &o) {
+  if ((int64_t)o.steps.size() >= o.req.max_frames) {
+    o.dropped++;
+    return PIC_OK;
+  }
+  const int64_t f = (int64_t)o.steps.size();
+  double *dst = o.buf + f * o.frame_doubles;
+  pic::OutBox b;
+  for (int a = 0; a < 3; ++a) {
+    b.lo[a] = o.req.lo[a];
+    b.hi[a] = o.req.hi[a];
+  }
+  if (o.req.kind == PIC_OUT_FIELD) {
+    const int w = o.req.which;
+    if (w == PIC_RHO) {
+      const int r = compute_rho(h, h->rho);
+      if (r) return r;
+      CK(h, pic::launch_out_field(h->g, h->rho, true, b, dst, h->st), "output field");
+    } else {
+      const void *src = w < 3 ? h->E[w] : w < 6 ? h->B[w - 3] : h->J[w - 6];
+      CK(h, pic::launch_out_field(h->g, src, false, b, dst, h->st), "output field");
+    }
+  } else {
+    Species &s = h->sp[o.req.which];
+    CK(h,
+       pic::launch_out_particles(h->g, s.buf[s.cur], s.d_count, s.slots, b, dst, o.found + f, o.req.max_particles,
+                                 h->st),
+       "output particles");
+  }
+  h->launches++;
+  o.steps.push_back(h->step);
+  return PIC_OK;
+}
+
+OutputReq *output_get(pic_handle *h, int id) {
+  if (!h || id < 0 || id >= (int)h->outputs.size() || !h->outputs[id].active) return nullptr;
+  return &h->outputs[id];
+}
+
+}  // namespace
+
+int pic_output_due(const pic_output_t *req, int64_t step) {
+  if (!req || req->every < 1) return 0;
+  return step >= req->first && step <= req->last && (step - req->first) % req->every == 0;
+}
+
+int pic_output_add(pic_handle *h, const pic_output_t *req, int *id) {
+  if (!h || !req || !id) return fail(h, PIC_EINVAL, "NULL argument");
+  const pic_output_t &q = *req;
+  if (q.kind == PIC_OUT_FIELD) {
+    if (q.which < PIC_EX || q.which > PIC_RHO) return fail(h, PIC_EINVAL, "bad field id");
+  } else if (q.kind == PIC_OUT_PARTICLES) {
+    if (q.which < 0 || q.which >= h->nsp) return fail(h, PIC_EINVAL, "bad species index");
+    if (q.max_particles < 1) return fail(h, PIC_EINVAL, "max_particles must be >= 1");
+  } else {
+    return fail(h, PIC_EINVAL, "kind must be PIC_OUT_FIELD or PIC_OUT_PARTICLES");
+  }
+  int64_t box = 1;
+  for (int a = 0; a < 3; ++a) {
+    if (q.lo[a] < 0 || q.hi[a] > h->g.n[a] || q.lo[a] >= q.hi[a]) return fail(h, PIC_EINVAL, "bad output box");
+    box *= q.hi[a] - q.lo[a];
+  }
+  if (q.first < 0 || q.last < q.first || q.every < 1 || q.max_frames < 1)
+    return fail(h, PIC_EINVAL, "bad output schedule (0 <= first <= last, every >= 1, max_frames >= 1)");
+  OutputReq o;
+  o.req = q;
+  o.frame_doubles = q.kind == PIC_OUT_FIELD ? box : 8 * q.max_particles;
+  if (q.max_frames > (int64_t)1 << 40 || o.frame_doubles > ((int64_t)1 << 40) / q.max_frames)
+    return fail(h, PIC_ENOMEM, "output buffer too large");
+  if (cudaMalloc(&o.buf, sizeof(double) * (size_t)(o.frame_doubles * q.max_frames)) != cudaSuccess ||
+      cudaMalloc(&o.found, sizeof(unsigned long long) * (size_t)q.max_frames) != cudaSuccess) {
+    cudaFree(o.buf);
+    cudaFree(o.found);
+    cudaGetLastError();
+    return fail(h, PIC_ENOMEM, "device allocation failed in pic_output_add");
+  }
+  CK(h, cudaMemsetAsync(o.found, 0, sizeof(unsigned long long) * (size_t)q.max_frames, h->st), "memset");
+  o.active = true;
+  h->outputs.push_back(std::move(o));
+  *id = (int)h->outputs.size() - 1;
+  return PIC_OK;
+}
+
+int pic_output_capture(pic_handle *h, int id) {
+  OutputReq *o = output_get(h, id);
+  if (!o) return fail(h, PIC_EINVAL, "no such output request");
+  return output_capture(h, *o);
+}
+
+int pic_output_count(pic_handle *h, int id, int64_t *nframes, int64_t *dropped) {
+  OutputReq *o = output_get(h, id);
+  if (!o || !nframes) return fail(h, PIC_EINVAL, "no such output request or NULL argument");
+  *nframes = (int64_t)o->steps.size();
+  if (dropped) *dropped = o->dropped;
+  return check_device_errors(h);
+}
+
+int pic_output_read(pic_handle *h, int id, int64_t frame, double *out, int64_t *count, int64_t *step,
+                    int mem_kind) {
+  OutputReq *o = output_get(h, id);
+  if (!o || !out || !count) return fail(h, PIC_EINVAL, "no such output request or NULL argument");
+  if (frame < 0 || frame >= (int64_t)o->steps.size()) return fail(h, PIC_EINVAL, "no such frame");
+  if (mem_kind != PIC_MEM_HOST && mem_kind != PIC_MEM_DEVICE) return fail(h, PIC_EINVAL, "bad memory kind");
+  const double *src = o->buf + frame * o->frame_doubles;
+  int64_t n = o->frame_doubles, found = o->frame_doubles;
+  if (o->req.kind == PIC_OUT_PARTICLES) {
+    unsigned long long f = 0;
+    CK(h, cudaMemcpyAsync(&f, o->found + frame, sizeof(f), cudaMemcpyDeviceToHost, h->st), "D2H");
+    CK(h, cudaStreamSynchronize(h->st), "sync");
+    found = (int64_t)f;
+    n = 8 * (found < o->req.max_particles ? found : o->req.max_particles);
+  }
+  if (n > 0)
+    CK(h,
+       cudaMemcpyAsync(out, src, sizeof(double) * (size_t)n,
+                       mem_kind == PIC_MEM_HOST ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice, h->st),
+       "output copy");
+  CK(h, cudaStreamSynchronize(h->st), "sync");
+  *count = found;
+  if (step) *step = o->steps[(size_t)frame];
+  if (o->req.kind == PIC_OUT_PARTICLES && found > o->req.max_particles)
+    return fail(h, PIC_EOVERFLOW, "more particles in the box than max_particles");
+  return check_device_errors(h);
+}
+
+int pic_output_remove(pic_handle *h, int id) {
+  OutputReq *o = output_get(h, id);
+  if (!o) return fail(h, PIC_EINVAL, "no such output request");
+  cudaStreamSynchronize(h->st);
+  cudaFree(o->buf);
+  cudaFree(o->found);
+  o->buf = nullptr;
+  o->found = nullptr;
+  o->steps.clear();
+  o->active = false;
+  return PIC_OK;
+}
+
 int pic_step(pic_handle *h, int nsteps) {
   if (!h) return fail(h, PIC_EINVAL, "NULL handle");
   if (nsteps < 0) return fail(h, PIC_EINVAL, "negative step count");
@@ -703,6 +862,11 @@ int pic_step(pic_handle *h, int nsteps) {
     }
     h->launches += 3;
     h->step++;
+    for (auto &o : h->outputs)
+      if (o.active && pic_output_due(&o.req, h->step)) {
+        const int r = output_capture(h, o);
+        if (r) return r;
+      }
   }
   return PIC_OK;
 }

@@ -112,6 +112,19 @@ cudaError_t launch_unload(const Grid &g, const Particles &p, const int64_t *d_co
                           double *y, double *z, double *ux, double *uy, double *uz, double *w, uint32_t *id,
                           int32_t *alive, cudaStream_t st);
 cudaError_t launch_field_to_f64(const Grid &g, const void *src, double *dst, cudaStream_t st);
+// Box [lo, hi) of grid positions or cells (output capture).
+struct OutBox {
+  int lo[3], hi[3];
+};
+// Copy a box of one field (FP64 if f64, else the grid's precision) into an
+// FP64 frame, x fastest.
+cudaError_t launch_out_field(const Grid &g, const void *f, bool f64, const OutBox &b, double *out, cudaStream_t st);
+// Records (x, y, z, ux, uy, uz, w, id as doubles) of the particles whose cell
+// is in the box; *count (zeroed by the caller) receives how many were found,
+// at most cap are written.
+cudaError_t launch_out_particles(const Grid &g, const Particles &p, const int64_t *d_count, int64_t nmax,
+                                 const OutBox &b, double *out, unsigned long long *count, int64_t cap,
+                                 cudaStream_t st);
 // Current smoothing of one field in place: `passes` binomial passes along
 // every axis, then (compensate) one compensating pass.  f64 selects the
 // element type (double, else the grid's precision); tmp holds ncell elements

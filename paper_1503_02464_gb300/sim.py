@@ -191,6 +191,45 @@ class Simulation:
         a = np.ascontiguousarray(np.broadcast_to(arr, self.shape3), dtype=np.float64)
         capi.pic_set_field(self.h, which, a.ctypes.data, capi.PIC_MEM_HOST)
 
+    # -- output manager (reduced-dimension / sub-domain frames in a time window)
+    def output_add(self, kind: str, which, lo, hi, first: int, last: int, every: int = 1, max_frames: int = 1,
+                   max_particles: int = 1) -> int:
+        """Register an output request; kind "field" (which = field id) or
+        "particles" (which = species index); box [lo, hi) in cells."""
+        k = {"field": capi.PIC_OUT_FIELD, "particles": capi.PIC_OUT_PARTICLES}[kind]
+        req = capi.make_output(k, which, lo, hi, first, last, every, max_frames, max_particles)
+        oid = capi.pic_output_add(self.h, req)
+        self._outputs = getattr(self, "_outputs", {})
+        self._outputs[oid] = req
+        return oid
+
+    def output_capture(self, oid: int) -> None:
+        capi.pic_output_capture(self.h, oid)
+
+    def output_count(self, oid: int):
+        """(frames held, frames dropped)."""
+        return capi.pic_output_count(self.h, oid)
+
+    def output_read(self, oid: int, frame: int):
+        """(data, step): a (bz, by, bx) FP64 array for a field frame, a dict
+        of x, y, z, ux, uy, uz, w, id arrays for a particle frame."""
+        req = self._outputs[oid]
+        if req.kind == capi.PIC_OUT_FIELD:
+            shape = tuple(req.hi[a] - req.lo[a] for a in (2, 1, 0))
+            out = np.empty(shape, dtype=np.float64)
+            _, step = capi.pic_output_read(self.h, oid, frame, out.ctypes.data, capi.PIC_MEM_HOST)
+            return out, step
+        buf = np.empty((req.max_particles, 8), dtype=np.float64)
+        n, step = capi.pic_output_read(self.h, oid, frame, buf.ctypes.data, capi.PIC_MEM_HOST)
+        rec = buf[:n]
+        names = ("x", "y", "z", "ux", "uy", "uz", "w")
+        d = {k: rec[:, i].copy() for i, k in enumerate(names)}
+        d["id"] = rec[:, 7].astype(np.uint32)
+        return d, step
+
+    def output_remove(self, oid: int) -> None:
+        capi.pic_output_remove(self.h, oid)
+
     def diag(self) -> dict:
         return capi.pic_diag(self.h)
 
