@@ -181,8 +181,11 @@ int pic_add_species(pic_handle *h, double q, double m, int64_t capacity, int *sp
  * t - dt/2 (leap-frog), w the weight (density carried, so rho = sum q w g),
  * id an optional tag (NULL = running index) kept through sorts.  Seven values
  * per particle as in §3.3, converted on the device to an integer cell plus an
- * in-cell offset.  Positions outside the box wrap on periodic axes and are
- * rejected (PIC_EINVAL) on absorbing ones.  Exceeding capacity: PIC_ENOMEM. */
+ * in-cell offset.  Positions outside the box wrap on periodic axes.  A
+ * particle outside the absorbing walls' [3, n[0] - 4) cells, or with a
+ * non-finite position, momentum or weight, is stored dead and the call
+ * returns PIC_EINVAL after loading the others.  Exceeding capacity:
+ * PIC_ENOMEM (nothing loaded). */
 int pic_load_particles(pic_handle *h, int species, int64_t n, const double *x, const double *y,
                        const double *z, const double *ux, const double *uy, const double *uz,
                        const double *w, const uint32_t *id, int mem_kind);

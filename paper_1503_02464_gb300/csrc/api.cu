@@ -6,6 +6,7 @@
 // library's (cell, offset) particle storage.
 #include <cuda_runtime.h>
 #include <math.h>
+#include <nvtx3/nvToolsExt.h>
 #include <stdio.h>
 #include <string.h>
 
@@ -35,7 +36,8 @@ struct Species {
   int64_t h_count = 0;          // host mirror, valid while !stepped_since_count
   int32_t *rank = nullptr;
   int64_t *tile_start = nullptr;
-  float *tq = nullptr;          // per-tile deposit bound carried between pushes
+  pic::WorkSplit work;          // push work items (tile pieces of at most work.chunk slots)
+  float *tq = nullptr;          // per-item deposit bound carried between pushes
   bool fresh = true;            // sorted since the last push
   bool need_sort = true;
 };
@@ -149,11 +151,18 @@ cudaEvent_t take_event(pic_handle *h) {
   return e;
 }
 
+// NVTX range names of the kernel classes (seen by a timeline profiler; the
+// calls cost nothing when none is attached).
+const char *const kClassNames[pic::KC_N] = {"sort", "zero_j", "push", "yee_b", "yee_e", "boundary", "filter"};
+
+// Scope of one kernel class within a step: an NVTX range, and CUDA events
+// on the simulation stream while profiling is on (pic_profile).
 struct Timed {
   pic_handle *h;
   int cls;
   cudaEvent_t a = nullptr;
   Timed(pic_handle *h_, int c) : h(h_), cls(c) {
+    nvtxRangePushA(kClassNames[c]);
     if (h->profiling) {
       a = take_event(h);
       cudaEventRecord(a, h->st);
@@ -165,6 +174,7 @@ struct Timed {
       cudaEventRecord(b, h->st);
       h->timers.push_back({cls, a, b});
     }
+    nvtxRangePop();
   }
 };
 
@@ -214,7 +224,7 @@ int sort_species(pic_handle *h, Species &s) {
   Timed tm(h, pic::KC_SORT);
   CK(h,
      pic::launch_sort(h->g, s.buf[s.cur], s.buf[1 - s.cur], s.d_count, s.slots, h->keys, s.rank, s.tile_start,
-                      h->tile_tmp, h->st, &nl),
+                      h->tile_tmp, s.work, h->st, &nl),
      "sort");
   h->launches += nl;
   s.cur = 1 - s.cur;
@@ -502,6 +512,8 @@ int pic_destroy(pic_handle *h) {
     cudaFree(s.rank);
     cudaFree(s.tile_start);
     cudaFree(s.tq);
+    cudaFree(s.work.work_tile);
+    cudaFree(s.work.work_pb);
   }
   for (auto &o : h->outputs) {
     cudaFree(o.buf);
@@ -537,7 +549,21 @@ int pic_add_species(pic_handle *h, double q, double m, int64_t capacity, int *sp
   if (e == cudaSuccess) e = cudaMalloc(&s.d_count, sizeof(int64_t));
   if (e == cudaSuccess) e = cudaMalloc(&s.rank, (size_t)(s.slots > 0 ? s.slots : 1) * sizeof(int32_t));
   if (e == cudaSuccess) e = cudaMalloc(&s.tile_start, (size_t)(h->g.ntiles + 1) * sizeof(int64_t));
-  if (e == cudaSuccess) e = cudaMalloc(&s.tq, (size_t)2 * h->g.ntiles * sizeof(float));
+  // Work items: pieces of at most `chunk` slots per tile, chunk sized so that
+  // a species spread over few tiles (a thin slab, a small grid) still gives
+  // about 16 blocks per SM, and never below 512 slots.
+  {
+    int dev = 0, nsm = 1;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+    int64_t chunk = s.slots / (16 * (int64_t)(nsm > 0 ? nsm : 1));
+    chunk = (chunk + 255) / 256 * 256;
+    s.work.chunk = chunk < 512 ? 512 : chunk;
+    s.work.nwork = s.slots / s.work.chunk + 1 + h->g.ntiles;
+  }
+  if (e == cudaSuccess) e = cudaMalloc(&s.tq, (size_t)2 * s.work.nwork * sizeof(float));
+  if (e == cudaSuccess) e = cudaMalloc(&s.work.work_tile, (size_t)s.work.nwork * sizeof(int32_t));
+  if (e == cudaSuccess) e = cudaMalloc(&s.work.work_pb, (size_t)s.work.nwork * sizeof(int64_t));
   if (e != cudaSuccess) {
     free_particles(s.buf[0]);
     free_particles(s.buf[1]);
@@ -545,6 +571,8 @@ int pic_add_species(pic_handle *h, double q, double m, int64_t capacity, int *sp
     cudaFree(s.rank);
     cudaFree(s.tile_start);
     cudaFree(s.tq);
+    cudaFree(s.work.work_tile);
+    cudaFree(s.work.work_pb);
     s = Species{};
     cudaGetLastError();
     return fail(h, PIC_ENOMEM, "device allocation failed in pic_add_species");
@@ -610,7 +638,8 @@ int pic_load_particles(pic_handle *h, int species, int64_t n, const double *x, c
   CK(h, cudaStreamSynchronize(h->st), "load sync");
   s.h_count = nn;
   s.need_sort = true;
-  if (bad) return fail(h, PIC_EINVAL, "particles outside an absorbing wall were marked dead");
+  if (bad)
+    return fail(h, PIC_EINVAL, "particles outside an absorbing wall or with non-finite values were marked dead");
   return PIC_OK;
 }
 
@@ -796,6 +825,10 @@ int pic_step(pic_handle *h, int nsteps) {
   const int every = h->cfg.sort_every > 0 ? h->cfg.sort_every : 20;
   const size_t fb = (size_t)h->g.ncell * h->rsize;
   for (int t = 0; t < nsteps; ++t) {
+    struct StepRange {
+      StepRange() { nvtxRangePushA("pic_step"); }
+      ~StepRange() { nvtxRangePop(); }
+    } step_range;
     for (int i = 0; i < h->nsp; ++i) {
       Species &s = h->sp[i];
       if (s.need_sort || h->step % every == 0) {
@@ -819,8 +852,8 @@ int pic_step(pic_handle *h, int nsteps) {
       Timed tm(h, pic::KC_PUSH);
       int nl = 0;
       CK(h,
-         pic::launch_push(h->g, h->E, h->B, h->J, s.buf[s.cur], s.tile_start, s.tq, s.fresh ? 1 : 0, s.rank,
-                          h->esc_count, s.q, s.m, h->ctr, h->st, &nl),
+         pic::launch_push(h->g, h->E, h->B, h->J, s.buf[s.cur], s.tile_start, s.work, s.tq, s.fresh ? 1 : 0,
+                          s.rank, h->esc_count, s.q, s.m, h->ctr, h->st, &nl),
          "push");
       s.fresh = false;
       h->launches += nl;

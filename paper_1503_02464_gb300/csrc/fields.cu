@@ -171,8 +171,13 @@ __global__ void k_load(int dims, int n0, int n1, int n2, double rdx0, double rdx
     const int nn[3] = {n0, n1, n2};
     int ci[3] = {0, 0, 0};
     R off[3] = {R(0), R(0), R(0)};
-    bool ok = true;
+    // non-finite positions, momenta or weights are not loaded (marked dead)
+    bool ok = isfinite(ux[q]) && isfinite(uy[q]) && isfinite(uz[q]) && isfinite(w[q]);
     for (int d = 0; d < dims; ++d) {
+      if (!isfinite(pos[d])) {
+        ok = false;
+        continue;
+      }
       const double fl = floor(pos[d]);
       double f = pos[d] - fl;
       long long i = (long long)fl;

@@ -70,13 +70,25 @@ enum KernelClass {
 // drift allowance is one cell.
 void push_tile_shape(int dims, int tile[3]);
 size_t push_smem_bytes(const Grid &g);
-// Tile kernel + escape kernel.  tq (2 floats per tile) carries the per-tile
-// bound of the FP32 fixed-point deposit from one step to the next; fresh = 1
-// on the first push after a sort (tq is recomputed from the particles).
+// Work items of the push kernel: each tile's slot run is cut into pieces of
+// at most `chunk` slots; item i covers slots [work_pb[i], min(work_pb[i] +
+// chunk, tile_start[t + 1])) of tile t = work_tile[i] (-1: no work).  nwork
+// bounds the item count (slots / chunk + 1 + ntiles).
+struct WorkSplit {
+  int64_t chunk = 0;
+  int64_t nwork = 0;
+  int32_t *work_tile = nullptr;
+  int64_t *work_pb = nullptr;
+};
+
+// Tile kernel (one block per work item) + escape kernel.  tq (2 floats per
+// work item) carries the bound of the FP32 fixed-point deposit from one step
+// to the next; fresh = 1 on the first push after a sort (tq is recomputed
+// from the particles).
 // esc_list (one int per slot) and esc_count are scratch for particles
 // deferred to the escape kernel.
 cudaError_t launch_push(const Grid &g, void *const E[3], void *const B[3], void *const J[3], const Particles &p,
-                        const int64_t *tile_start, float *tq, int fresh, int32_t *esc_list,
+                        const int64_t *tile_start, const WorkSplit &ws, float *tq, int fresh, int32_t *esc_list,
                         unsigned long long *esc_count, double q, double m, Counters *ctr, cudaStream_t st,
                         int *nlaunch);
 
@@ -90,9 +102,10 @@ cudaError_t launch_rho_tiled(const Grid &g, const Particles &p, const int64_t *t
 // dead slots dropped; result in `dst`, *d_count updated, tile_start[ntiles+1]
 // written.  Each tile's run is padded with dead slots to a multiple of
 // kTilePad.  `keys` has ntiles*tile_cells ints, `rank` one int per slot.
+
 cudaError_t launch_sort(const Grid &g, const Particles &src, const Particles &dst, int64_t *d_count,
                         int64_t capacity, int32_t *keys, int32_t *rank, int64_t *tile_start, int64_t *tile_tmp,
-                        cudaStream_t st, int *nlaunch);
+                        const WorkSplit &ws, cudaStream_t st, int *nlaunch);
 
 // ---- fields and particle conversion (fields.cu) ----
 cudaError_t launch_yee_b(const Grid &g, void *const E[3], void *const B[3], double h, cudaStream_t st);

@@ -86,7 +86,10 @@ template <class R> struct PushArgs {
   const R *w;
   const int64_t *tile_start;
   double qabs;                      // |q|
-  float *tq;                        // per tile: [2t] sum |w|, [2t+1] sum |w| min(1, |u|) (FP32 runs)
+  const int32_t *work_tile;         // work item -> tile (-1: none)
+  const int64_t *work_pb;           // work item -> first slot
+  int64_t chunk;                    // slots per work item at most
+  float *tq;                        // per item: [2i] sum |w|, [2i+1] sum |w| min(1, |u|) (FP32 runs)
   int fresh;                        // tile contents changed (sorted) since tq was written
   int32_t *esc_list;                // slots deferred to k_push_escaped
   unsigned long long *esc_count;
@@ -142,9 +145,10 @@ __device__ __forceinline__ R gsum(const R *__restrict__ F, const R *wx, const R 
 //   |J_node| <= Q = sum over the tile's particles of |q w| min(1, |u| + |q/m| dt Emax)
 // with Emax bounding |E| over the tile's field window; 2^K keeps Q 2^K below
 // 2^kLimitLog2.  X is kept as two signed 32-bit words, X = hi * 2^16 + lo
-// with |lo| <= 2^15, both found with FP32 adds only (adding 1.5 * 2^23 rounds
-// a float of magnitude below 2^22 to an integer held in its low mantissa
-// bits), because float-to-64-bit conversions run on the slow FP64 pipe.  With
+// with |lo| <= 2^15, both found with FP32 FMAs and adds only (adding
+// 1.5 * 2^(23 + s) rounds a float of magnitude below 2^(22 + s) to a multiple
+// of 2^s held in the low mantissa bits), because float-to-64-bit conversions
+// run on the slow FP64 pipe.  With
 // |X| < 2^37 the hi sums cannot overflow, and the lo sums cannot overflow for
 // fewer than 65,536 contributions per node.  FP64 runs use plain double
 // shared atomics, keeping FP64 rounding.
@@ -155,15 +159,21 @@ template <> struct WinAcc<float> {
   float scale;  // 2^K
   float unit;   // 2^-K
   static constexpr int kLimitLog2 = 37;
-  static constexpr float kMagic = 12582912.0f;  // 1.5 * 2^23
-  // x: contribution already multiplied by 2^K
-  __device__ __forceinline__ void add(int comp, int idx, float x) const {
-    if (x != 0.f) {
-      const float yh = fmaf(x, 1.0f / 65536.0f, kMagic);  // rint(x / 2^16) + magic
-      const float hf = yh - kMagic;
-      const int hi = __float_as_int(yh) - __float_as_int(kMagic);
-      const float lf = fmaf(-hf, 65536.0f, x);            // exact, |lf| <= 2^15
-      const int lo = __float_as_int(lf + kMagic) - __float_as_int(kMagic);
+  static constexpr float kMagic = 12582912.0f;        // 1.5 * 2^23: ulp 1
+  static constexpr float kMagicHi = 824633720832.0f;  // 1.5 * 2^39: ulp 2^16
+  // Add the contribution p q (already in units of 2^-K): X = p q is split
+  // into hi 2^16 + lo with FP32 operations only.  The first FMA rounds X to
+  // a multiple of 2^16 (|X| < 2^37, so the sum stays in [2^39, 2^40), where
+  // the float spacing is 2^16) and its bit pattern minus the magic's is hi;
+  // the second FMA gives X - hi 2^16 with one rounding, |.| <= 2^15, and the
+  // 2^23 magic rounds that to the integer lo.
+  __device__ __forceinline__ void add(int comp, int idx, float p, float q) const {
+    const float y = fmaf(p, q, kMagicHi);
+    const float r = y - kMagicHi;  // hi 2^16, exact
+    const float lf = fmaf(p, q, -r);
+    const int hi = __float_as_int(y) - __float_as_int(kMagicHi);
+    const int lo = __float_as_int(lf + kMagic) - __float_as_int(kMagic);
+    if (hi | lo) {
       int *b = w + comp * 2 * jn + idx;
       atomicAdd(b, lo);
       atomicAdd(b + jn, hi);
@@ -179,7 +189,8 @@ template <> struct WinAcc<double> {
   int jn;
   double scale;  // 1: contributions are passed unscaled
   double unit;
-  __device__ __forceinline__ void add(int comp, int idx, double x) const {
+  __device__ __forceinline__ void add(int comp, int idx, double p, double q) const {
+    const double x = p * q;
     if (x != 0.0) atomicAdd(w + comp * jn + idx, x);
   }
   __device__ __forceinline__ double get(int comp, int idx) const { return w[comp * jn + idx]; }
@@ -234,7 +245,7 @@ __device__ __forceinline__ void deposit_win(const WinAcc<R> &acc, int base, cons
 #pragma unroll
         for (int a = 0; a < M; ++a) {
           if (a == M - 1 && !lx) continue;
-          acc.add(0, base + c * SZ + b * SY + a, Px[a] * br);
+          acc.add(0, base + c * SZ + b * SY + a, Px[a], br);
         }
       }
     }
@@ -248,7 +259,7 @@ __device__ __forceinline__ void deposit_win(const WinAcc<R> &acc, int base, cons
 #pragma unroll
         for (int b = 0; b < M; ++b) {
           if (b == M - 1 && !ly) continue;
-          acc.add(1, base + c * SZ + b * SY + a, Py[b] * br);
+          acc.add(1, base + c * SZ + b * SY + a, Py[b], br);
         }
       }
     }
@@ -264,7 +275,7 @@ __device__ __forceinline__ void deposit_win(const WinAcc<R> &acc, int base, cons
 #pragma unroll
         for (int c = 0; c < M; ++c) {
           if (c == M - 1 && !lz) continue;
-          acc.add(2, base + c * SZ + b * SY + a, Pz[c] * br);
+          acc.add(2, base + c * SZ + b * SY + a, Pz[c], br);
         }
       }
     }
@@ -279,12 +290,12 @@ __device__ __forceinline__ void deposit_win(const WinAcc<R> &acc, int base, cons
 #pragma unroll
       for (int a = 0; a < M; ++a) {
         if (a == M - 1 && !lx) continue;
-        acc.add(0, base + b * SY + a, Px[a] * hy);
+        acc.add(0, base + b * SY + a, Px[a], hy);
       }
 #pragma unroll
       for (int a = 0; a < NW; ++a) {
         if (a == NW - 1 && !lx) continue;
-        acc.add(2, base + b * SY + a, qwvz * (X.S0[a] * hy + X.DS[a] * ty));
+        acc.add(2, base + b * SY + a, qwvz, X.S0[a] * hy + X.DS[a] * ty);
       }
     }
 #pragma unroll
@@ -294,7 +305,7 @@ __device__ __forceinline__ void deposit_win(const WinAcc<R> &acc, int base, cons
 #pragma unroll
       for (int b = 0; b < M; ++b) {
         if (b == M - 1 && !ly) continue;
-        acc.add(1, base + b * SY + a, Py[b] * hx);
+        acc.add(1, base + b * SY + a, Py[b], hx);
       }
     }
   }
@@ -348,8 +359,11 @@ __global__ void __launch_bounds__(kThreads, sizeof(R) == 4 ? 2 : 1) k_push(const
   __shared__ float s_qsum, s_wsum, s_q1;
   float emax[3] = {0.f, 0.f, 0.f};
 
-  const int t = blockIdx.x;
-  const int64_t pb = a.tile_start[t], pe = a.tile_start[t + 1];
+  const int wi = blockIdx.x;  // work item
+  const int t = a.work_tile[wi];
+  if (t < 0) return;
+  const int64_t pb = a.work_pb[wi];
+  const int64_t pe = pb + a.chunk < a.tile_start[t + 1] ? pb + a.chunk : a.tile_start[t + 1];
   if (pb >= pe) return;
   const int tid = threadIdx.x;
   int t0[3];
@@ -416,8 +430,8 @@ __global__ void __launch_bounds__(kThreads, sizeof(R) == 4 ? 2 : 1) k_push(const
     } else if (tid == 0) {
       // |u| min'ed at 1 from the previous push, plus the kick of this step:
       // sum |w| min(1, |u| + kick) <= sum |w| min(1, |u|) + kick sum |w|
-      s_wsum = a.tq[2 * t];
-      s_qsum = a.tq[2 * t + 1] + kick * s_wsum;
+      s_wsum = a.tq[2 * wi];
+      s_qsum = a.tq[2 * wi + 1] + kick * s_wsum;
     }
     __syncthreads();
     if (tid == 0) {
@@ -588,9 +602,9 @@ __global__ void __launch_bounds__(kThreads, sizeof(R) == 4 ? 2 : 1) k_push(const
   }
   __syncthreads();
   if (sizeof(R) == 4 && tid == 0) {
-    // bound inputs for the next step (the tile keeps its slots until the next sort)
-    a.tq[2 * t] = s_wsum;
-    a.tq[2 * t + 1] = s_q1 * 1.0001f;
+    // bound inputs for the next step (the item keeps its slots until the next sort)
+    a.tq[2 * wi] = s_wsum;
+    a.tq[2 * wi + 1] = s_q1 * 1.0001f;
   }
 
   // ---- flush the J window into global J ----
@@ -741,10 +755,13 @@ template <class R, int DIM, int ORDER> constexpr size_t smem_bytes() {
 
 template <class R, int DIM, int ORDER>
 cudaError_t launch_t(const Grid &g, void *const E[3], void *const B[3], void *const J[3], const Particles &p,
-                     const int64_t *tile_start, float *tq, int fresh, int32_t *esc_list,
+                     const int64_t *tile_start, const WorkSplit &ws, float *tq, int fresh, int32_t *esc_list,
                      unsigned long long *esc_count, double q, double m, Counters *ctr, cudaStream_t st,
                      int *nlaunch) {
   PushArgs<R> a;
+  a.work_tile = ws.work_tile;
+  a.work_pb = ws.work_pb;
+  a.chunk = ws.chunk;
   a.tq = tq;
   a.fresh = fresh;
   a.qabs = q < 0 ? -q : q;
@@ -776,10 +793,10 @@ cudaError_t launch_t(const Grid &g, void *const E[3], void *const B[3], void *co
   auto fn = k_push<R, DIM, ORDER>;
   cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
-  if (g.ntiles > 0x7fffffff) return cudaErrorInvalidValue;
+  if (ws.nwork > 0x7fffffff) return cudaErrorInvalidValue;
   e = cudaMemsetAsync(esc_count, 0, sizeof(unsigned long long), st);
   if (e != cudaSuccess) return e;
-  fn<<<(unsigned)g.ntiles, kThreads, smem, st>>>(a);
+  fn<<<(unsigned)ws.nwork, kThreads, smem, st>>>(a);
   int dev = 0, nsm = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
@@ -945,13 +962,13 @@ size_t push_smem_bytes(const Grid &g) {
 }
 
 cudaError_t launch_push(const Grid &g, void *const E[3], void *const B[3], void *const J[3], const Particles &p,
-                        const int64_t *tile_start, float *tq, int fresh, int32_t *esc_list,
+                        const int64_t *tile_start, const WorkSplit &ws, float *tq, int fresh, int32_t *esc_list,
                         unsigned long long *esc_count, double q, double m, Counters *ctr, cudaStream_t st,
                         int *nlaunch) {
   const int key = (g.prec == 1 ? 100 : 0) + g.dims * 10 + g.order;
 #define PIC_PUSH_CASE(K, R, D, O) \
   case K:                                                                                                    \
-    return launch_t<R, D, O>(g, E, B, J, p, tile_start, tq, fresh, esc_list, esc_count, q, m, ctr, st, nlaunch);
+    return launch_t<R, D, O>(g, E, B, J, p, tile_start, ws, tq, fresh, esc_list, esc_count, q, m, ctr, st, nlaunch);
   switch (key) {
     PIC_PUSH_CASE(21, float, 2, 1)
     PIC_PUSH_CASE(22, float, 2, 2)

@@ -122,6 +122,35 @@ __global__ void k_offsets(int32_t *__restrict__ count, int64_t ntiles, int tc, c
   if (run + lane < tile_start[t + 1]) dst_cell[run + lane] = -1;
 }
 
+// Single block: cut every tile's slot run into items of at most `chunk`
+// slots.  Exclusive scan of the per-tile item counts, then each thread
+// writes the items of its own run of tiles.
+__global__ void k_work_items(const int64_t *__restrict__ tile_start, int64_t ntiles, int64_t chunk,
+                             int32_t *__restrict__ work_tile, int64_t *__restrict__ work_pb) {
+  __shared__ int64_t sh[1024];
+  const int T = blockDim.x;
+  const int64_t per = (ntiles + T - 1) / T;
+  const int64_t b = threadIdx.x * per;
+  const int64_t e = b + per < ntiles ? b + per : ntiles;
+  int64_t local = 0;
+  for (int64_t t = b; t < e; ++t) local += (tile_start[t + 1] - tile_start[t] + chunk - 1) / chunk;
+  sh[threadIdx.x] = local;
+  __syncthreads();
+  for (int o = 1; o < T; o <<= 1) {
+    const int64_t v = threadIdx.x >= o ? sh[threadIdx.x - o] : 0;
+    __syncthreads();
+    sh[threadIdx.x] += v;
+    __syncthreads();
+  }
+  int64_t w = sh[threadIdx.x] - local;
+  for (int64_t t = b; t < e; ++t) {
+    for (int64_t p = tile_start[t]; p < tile_start[t + 1]; p += chunk, ++w) {
+      work_tile[w] = (int32_t)t;
+      work_pb[w] = p;
+    }
+  }
+}
+
 template <class R>
 __global__ void k_scatter(KeyMap km, int dims, Particles src, Particles dst, const int64_t *__restrict__ n_src,
                           const int32_t *__restrict__ count, const int32_t *__restrict__ rank) {
@@ -145,7 +174,7 @@ __global__ void k_scatter(KeyMap km, int dims, Particles src, Particles dst, con
 
 cudaError_t launch_sort(const Grid &g, const Particles &src, const Particles &dst, int64_t *d_count,
                         int64_t capacity, int32_t *keys, int32_t *rank, int64_t *tile_start, int64_t *tile_tmp,
-                        cudaStream_t st, int *nlaunch) {
+                        const WorkSplit &ws, cudaStream_t st, int *nlaunch) {
   KeyMap km;
   km.n0 = g.n[0];
   km.n1 = g.n[1];
@@ -176,7 +205,10 @@ cudaError_t launch_sort(const Grid &g, const Particles &src, const Particles &ds
     k_scatter<double><<<nb, 256, 0, st>>>(km, g.dims, src, dst, tile_tmp + g.ntiles, keys, rank);
   else
     k_scatter<float><<<nb, 256, 0, st>>>(km, g.dims, src, dst, tile_tmp + g.ntiles, keys, rank);
-  if (nlaunch) *nlaunch = 5;
+  e = cudaMemsetAsync(ws.work_tile, 0xff, sizeof(int32_t) * (size_t)ws.nwork, st);  // -1: no work
+  if (e != cudaSuccess) return e;
+  k_work_items<<<1, 1024, 0, st>>>(tile_start, g.ntiles, ws.chunk, ws.work_tile, ws.work_pb);
+  if (nlaunch) *nlaunch = 6;
   return cudaGetLastError();
 }
 
