@@ -278,11 +278,13 @@ def run_gpu(args, rank: int, world: int, local: int):
     clk = clocks.stop()
     tim = sim.timings()
     launches = sim.launch_count() - l0
-    d = sim.diag()
+    td = time.perf_counter()
+    d = sim.diag()  # FP64 diagnostics (charge deposit, Gauss, energies), synchronising
+    diag_ms = 1e3 * (time.perf_counter() - td)
     sim.profile(False)
     dt_max = _barrier_max(world, dt_s)
     push_ms, push_n = tim["push"]
-    results["main"] = dict(dt=dt_max, tim=tim, launches=launches, diag=d, clocks=clk)
+    results["main"] = dict(dt=dt_max, tim=tim, launches=launches, diag=d, clocks=clk, diag_ms=diag_ms)
     sim.close()
     del sim
     torch.cuda.synchronize()
@@ -327,11 +329,20 @@ def run_gpu(args, rank: int, world: int, local: int):
             torch.cuda.synchronize()
             t2 = time.perf_counter()
             sim.close()
+        # one more run with per-kernel-class events, for the breakdown only
+        sim = diff.build_sim(run, 2.0, prof)
+        sim.profile(True)
+        diff.run_forward(run, sim)
+        diff.backward_gradients(run, sim)
+        adj_kernels = {k: {"ms_total": v[0], "launches": v[1]} for k, v in sim.timings().items() if v[1]}
+        sim.profile(False)
+        sim.close()
         adjoint = {"workload": f"2D3V laser slab {run.nx}x{run.ny}, {run.ppc} ppc ({run.nx * run.ny * run.ppc} "
                                f"electron slots), TSC, {run.steps} steps, checkpoint every {run.segment}, FP32 "
                                f"forward/adjoint, FP64 gradients",
                    "forward_s": t1 - t0, "backward_s": t2 - t1, "ratio": (t2 - t1) / (t1 - t0),
                    "note": "backward includes re-running every segment with the tape on",
+                   "kernel_ms": adj_kernels,
                    "objective": F, "dF_da0": da0}
 
     # ---------------- end to end through the C ABI with host buffers
@@ -427,6 +438,7 @@ def run_gpu(args, rank: int, world: int, local: int):
         "clocks": r["clocks"],
         "diag_after": {k: r["diag"][k] for k in ("energy_field", "energy_kinetic", "n_alive", "n_escaped",
                                                    "gauss_max")},
+        "diag_ms": r["diag_ms"],
         "setup_s": {"generate": t_gen, "load": t_load,
                     "note": "load = generate + copy piece by piece" if streamed else "load = device copy"},
     }

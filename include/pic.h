@@ -244,8 +244,8 @@ int pic_sync(pic_handle *h);
  * starts recording (clearing previous records).  pic_timings synchronises
  * and writes, for up to nmax kernel classes, total milliseconds and launch
  * counts; class order: 0 sort, 1 zero J, 2 push, 3 Yee B, 4 Yee E,
- * 5 boundary, 6 current smoothing.  Returns the number of classes written
- * in *ncls. */
+ * 5 boundary, 6 current smoothing, 7 adjoint field updates, 8 adjoint
+ * particle kernel.  Returns the number of classes written in *ncls. */
 int pic_profile(pic_handle *h, int enable);
 int pic_timings(pic_handle *h, double *ms, int64_t *launches, int nmax, int *ncls);
 

@@ -18,7 +18,7 @@ PIC_GATHER_MOMENTUM, PIC_GATHER_ENERGY = 0, 1
 PIC_OUT_FIELD, PIC_OUT_PARTICLES = 0, 1
 PIC_MEM_HOST, PIC_MEM_DEVICE = 0, 1
 PIC_EX, PIC_EY, PIC_EZ, PIC_BX, PIC_BY, PIC_BZ, PIC_JX, PIC_JY, PIC_JZ, PIC_RHO = range(10)
-KERNEL_CLASSES = ["sort", "zero_j", "push", "yee_b", "yee_e", "boundary", "filter"]
+KERNEL_CLASSES = ["sort", "zero_j", "push", "yee_b", "yee_e", "boundary", "filter", "adj_field", "adj_push"]
 
 ERROR_NAMES = {0: "PIC_OK", 1: "PIC_EINVAL", 2: "PIC_ECOURANT", 3: "PIC_ENOMEM", 4: "PIC_ECUDA",
                5: "PIC_EOVERFLOW", 6: "PIC_ETIMEOUT", 7: "PIC_ENAN"}
@@ -226,10 +226,11 @@ def pic_profile(h, enable: bool) -> None:
 
 
 def pic_timings(h) -> dict:
-    ms = (ctypes.c_double * 8)()
-    cnt = (ctypes.c_int64 * 8)()
+    nmax = len(KERNEL_CLASSES)
+    ms = (ctypes.c_double * nmax)()
+    cnt = (ctypes.c_int64 * nmax)()
     nc = ctypes.c_int()
-    check(h, load().pic_timings(h, ms, cnt, 8, ctypes.byref(nc)))
+    check(h, load().pic_timings(h, ms, cnt, nmax, ctypes.byref(nc)))
     return {KERNEL_CLASSES[i]: (ms[i], cnt[i]) for i in range(nc.value)}
 
 

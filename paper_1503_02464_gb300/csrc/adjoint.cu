@@ -118,15 +118,6 @@ __global__ void __launch_bounds__(256)
   }
 }
 
-__device__ double laser_unit(const Laser &L, int dims, double x, double y, double z, double t) {
-  const double tau = t - x;
-  if (tau <= 0.0 || tau >= L.duration) return 0.0;
-  const double env = sin(3.14159265358979323846 * tau / L.duration);
-  double r2 = (y - L.yc) * (y - L.yc);
-  if (dims == 3) r2 += (z - L.zc) * (z - L.zc);
-  return exp(-r2 / (L.waist * L.waist)) * env * env * sin(tau);
-}
-
 // Transpose of the Mur wall update (tangential components y, z):
 //   E0' = L0n + S1o + k (S1n - S0o),  S = E - L     (left wall, laser)
 //   Ez' = E(n0-2)o + k (E(n0-2)n - E(n0-1)o)      (right wall)
@@ -134,8 +125,8 @@ __device__ double laser_unit(const Laser &L, int dims, double x, double y, doubl
 // the neighbour at the new time, and g, -k g are kept in `pend` for the old
 // time (added after R3).  dF/da0 += g dE0'/da0 (the laser terms over a0).
 template <class R>
-__global__ void k_adj_mur(int dims, int n0, int n1, int n2, double dx, double dy, double dz, double dt, R *lEy,
-                          R *lEz, double *pend, Laser las, double t_old, double t_new, double *da0) {
+__global__ void k_adj_mur(int n0, int n1, int n2, double dx, double dt, R *lEy, R *lEz, double *pend, LaserStep ls,
+                          double *da0) {
   __shared__ double sh[32];
   const int64_t nyz = (int64_t)n1 * n2;
   const double kc = (dt - dx) / (dt + dx);
@@ -143,7 +134,6 @@ __global__ void k_adj_mur(int dims, int n0, int n1, int n2, double dx, double dy
   for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < 2 * nyz; q += (int64_t)gridDim.x * blockDim.x) {
     const int c = (int)(q / nyz);
     const int64_t jk = q % nyz;
-    const int j = (int)(jk % n1), k = (int)(jk / n1);
     R *E = c == 0 ? lEy : lEz;
     double *pd = pend + (int64_t)c * 4 * nyz;  // slots: node 0, 1, n0-2, n0-1
     const int64_t row = (int64_t)n0 * jk;
@@ -152,10 +142,10 @@ __global__ void k_adj_mur(int dims, int n0, int n1, int n2, double dx, double dy
     E[row + 1] += (R)(kc * g0);
     pd[0 * nyz + jk] = -kc * g0;
     pd[1 * nyz + jk] = g0;
-    if (las.enabled && las.pol == c + 1) {
-      const double y = (j + (c == 0 ? 0.5 : 0.0)) * dy, z = (k + (c == 1 ? 0.5 : 0.0)) * dz;
-      const double l0n = laser_unit(las, dims, 0.0, y, z, t_new), l1o = laser_unit(las, dims, dx, y, z, t_old);
-      const double l1n = laser_unit(las, dims, dx, y, z, t_new), l0o = laser_unit(las, dims, 0.0, y, z, t_old);
+    if (ls.pol == c + 1) {
+      // unit-amplitude laser terms at the wall row: P(row) times the waveform
+      const double p = ls.prof[jk];
+      const double l0o = p * ls.amp[0], l1o = p * ls.amp[1], l0n = p * ls.amp[2], l1n = p * ls.amp[3];
       acc += g0 * (l0n - l1o - kc * l1n + kc * l0o);
     }
     const double gr = (double)E[row + n0 - 1];
@@ -262,8 +252,11 @@ template <> __device__ __forceinline__ float inv_sqrt_fwd<float>(float x) { retu
 template <> __device__ __forceinline__ double inv_sqrt_fwd<double>(double x) { return 1.0 / sqrt(x); }
 
 // Per-particle adjoint of gather -> Boris -> move -> Esirkepov (2D3V, TSC).
+// The kernel is latency-bound (scattered field and adjoint reads), so the
+// register cap (3 blocks of 256 per SM for FP32, 2 for FP64) trades a few
+// spills for occupancy.
 template <class R>
-__global__ void __launch_bounds__(256) k_adj_push2d(const AdjPushArgs<R> a) {
+__global__ void __launch_bounds__(256, sizeof(R) == 4 ? 3 : 2) k_adj_push2d(const AdjPushArgs<R> a) {
   const int n0 = a.n[0], n1 = a.n[1];
   const int64_t nslots = *a.d_count;
   for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < nslots; p += (int64_t)gridDim.x * blockDim.x) {
@@ -622,17 +615,15 @@ cudaError_t launch_adj_yee_e(const Grid &g, void *const lE[3], void *const lB[3]
   return cudaGetLastError();
 }
 
-cudaError_t launch_adj_mur(const Grid &g, void *const lE[3], double *pend, const Laser &las, double t_old,
-                           double t_new, double *da0, cudaStream_t st) {
+cudaError_t launch_adj_mur(const Grid &g, void *const lE[3], double *pend, const LaserStep &ls_unit, double *da0,
+                           cudaStream_t st) {
   const int nb = nblocks(2LL * g.n[1] * g.n[2]);
   if (g.prec == 1)
-    k_adj_mur<double><<<nb, 256, 0, st>>>(g.dims, g.n[0], g.n[1], g.n[2], g.dx[0], g.dx[1], g.dx[2], g.dt,
-                                          static_cast<double *>(lE[1]), static_cast<double *>(lE[2]), pend, las, t_old,
-                                          t_new, da0);
+    k_adj_mur<double><<<nb, 256, 0, st>>>(g.n[0], g.n[1], g.n[2], g.dx[0], g.dt, static_cast<double *>(lE[1]),
+                                          static_cast<double *>(lE[2]), pend, ls_unit, da0);
   else
-    k_adj_mur<float><<<nb, 256, 0, st>>>(g.dims, g.n[0], g.n[1], g.n[2], g.dx[0], g.dx[1], g.dx[2], g.dt,
-                                         static_cast<float *>(lE[1]), static_cast<float *>(lE[2]), pend, las, t_old,
-                                         t_new, da0);
+    k_adj_mur<float><<<nb, 256, 0, st>>>(g.n[0], g.n[1], g.n[2], g.dx[0], g.dt, static_cast<float *>(lE[1]),
+                                         static_cast<float *>(lE[2]), pend, ls_unit, da0);
   return cudaGetLastError();
 }
 

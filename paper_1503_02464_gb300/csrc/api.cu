@@ -95,6 +95,7 @@ struct pic_handle {
   int32_t *keys = nullptr;
   int64_t *tile_tmp = nullptr;
   double *mur = nullptr;  // Mur wall planes (8 * n1 * n2)
+  double *laser_prof = nullptr;  // laser profile P at the wall rows of the polarised component (n1 * n2)
   pic::Laser laser{};
   unsigned long long *esc_count = nullptr;
   Counters *ctr = nullptr;
@@ -153,7 +154,8 @@ cudaEvent_t take_event(pic_handle *h) {
 
 // NVTX range names of the kernel classes (seen by a timeline profiler; the
 // calls cost nothing when none is attached).
-const char *const kClassNames[pic::KC_N] = {"sort", "zero_j", "push", "yee_b", "yee_e", "boundary", "filter"};
+const char *const kClassNames[pic::KC_N] = {"sort",     "zero_j", "push",      "yee_b",   "yee_e",
+                                            "boundary", "filter", "adj_field", "adj_push"};
 
 // Scope of one kernel class within a step: an NVTX range, and CUDA events
 // on the simulation stream while profiling is on (pic_profile).
@@ -178,27 +180,34 @@ struct Timed {
   }
 };
 
+// A particle buffer is one allocation holding the SoA arrays back to back
+// (cell, off[0..dims), u[0..3), w, id, each 256-byte aligned), so that a
+// checkpoint or tape copy is one memcpy.  `cell` is the allocation's base.
+size_t align256(size_t b) { return (b + 255) / 256 * 256; }
+
+size_t particles_bytes(int64_t cap, size_t rs, int dims) {
+  const size_t n = (size_t)(cap > 0 ? cap : 1);
+  return align256(n * sizeof(int32_t)) + (size_t)(dims + 4) * align256(n * rs) + align256(n * sizeof(uint32_t));
+}
+
 void free_particles(Particles &p) {
   cudaFree(p.cell);
-  for (int d = 0; d < 3; ++d) {
-    cudaFree(p.off[d]);
-    cudaFree(p.u[d]);
-  }
-  cudaFree(p.w);
-  cudaFree(p.id);
   p = Particles{};
 }
 
 cudaError_t alloc_particles(Particles &p, int64_t cap, size_t rs, int dims) {
-  cudaError_t e;
   const size_t n = (size_t)(cap > 0 ? cap : 1);
-  if ((e = cudaMalloc(&p.cell, n * sizeof(int32_t))) != cudaSuccess) return e;
-  for (int d = 0; d < 3; ++d) {
-    if (d < dims && (e = cudaMalloc(&p.off[d], n * rs)) != cudaSuccess) return e;
-    if ((e = cudaMalloc(&p.u[d], n * rs)) != cudaSuccess) return e;
-  }
-  if ((e = cudaMalloc(&p.w, n * rs)) != cudaSuccess) return e;
-  if ((e = cudaMalloc(&p.id, n * sizeof(uint32_t))) != cudaSuccess) return e;
+  char *base = nullptr;
+  const cudaError_t e = cudaMalloc(&base, particles_bytes(cap, rs, dims));
+  if (e != cudaSuccess) return e;
+  p = Particles{};
+  p.cell = reinterpret_cast<int32_t *>(base);
+  char *q = base + align256(n * sizeof(int32_t));
+  for (int d = 0; d < dims; ++d, q += align256(n * rs)) p.off[d] = q;
+  for (int d = 0; d < 3; ++d, q += align256(n * rs)) p.u[d] = q;
+  p.w = q;
+  q += align256(n * rs);
+  p.id = reinterpret_cast<uint32_t *>(q);
   return cudaSuccess;
 }
 
@@ -260,11 +269,13 @@ cudaError_t alloc_snapshot(pic_handle *h, Snapshot &sn) {
   if (sn.allocated && sn.nsp == h->nsp) return cudaSuccess;
   if (sn.allocated) free_snapshot(sn);
   const size_t fb = (size_t)h->g.ncell * h->rsize;
-  cudaError_t e = cudaSuccess;
-  for (int d = 0; d < 3 && e == cudaSuccess; ++d) {
-    e = cudaMalloc(&sn.E[d], fb);
-    if (e == cudaSuccess) e = cudaMalloc(&sn.B[d], fb);
-  }
+  // E and B back to back, like the live fields (one copy)
+  cudaError_t e = cudaMalloc(&sn.E[0], 6 * fb);
+  if (e == cudaSuccess)
+    for (int d = 0; d < 3; ++d) {
+      sn.E[d] = static_cast<char *>(sn.E[0]) + d * fb;
+      sn.B[d] = static_cast<char *>(sn.E[0]) + (3 + d) * fb;
+    }
   for (int i = 0; i < h->nsp && e == cudaSuccess; ++i) {
     e = alloc_particles(sn.sp[i].p, h->sp[i].slots, h->rsize, h->g.dims);
     if (e == cudaSuccess) e = cudaMalloc(&sn.sp[i].count, sizeof(int64_t));
@@ -275,10 +286,7 @@ cudaError_t alloc_snapshot(pic_handle *h, Snapshot &sn) {
 }
 
 void free_snapshot(Snapshot &sn) {
-  for (int d = 0; d < 3; ++d) {
-    cudaFree(sn.E[d]);
-    cudaFree(sn.B[d]);
-  }
+  cudaFree(sn.E[0]);  // E and B share one allocation
   for (int i = 0; i < kMaxSpecies; ++i) {
     free_particles(sn.sp[i].p);
     cudaFree(sn.sp[i].count);
@@ -286,17 +294,11 @@ void free_snapshot(Snapshot &sn) {
   sn = Snapshot{};
 }
 
+// Both buffers were made by alloc_particles with `slots` slots.
 cudaError_t copy_particles(pic_handle *h, const Particles &dst, int64_t *dcount, const Particles &src,
                            const int64_t *scount, int64_t slots) {
-  const size_t n = (size_t)slots;
-  const size_t rs = h->rsize;
-  cudaError_t e = cudaMemcpyAsync(dst.cell, src.cell, n * sizeof(int32_t), cudaMemcpyDeviceToDevice, h->st);
-  for (int d = 0; d < 3 && e == cudaSuccess; ++d) {
-    if (d < h->g.dims) e = cudaMemcpyAsync(dst.off[d], src.off[d], n * rs, cudaMemcpyDeviceToDevice, h->st);
-    if (e == cudaSuccess) e = cudaMemcpyAsync(dst.u[d], src.u[d], n * rs, cudaMemcpyDeviceToDevice, h->st);
-  }
-  if (e == cudaSuccess) e = cudaMemcpyAsync(dst.w, src.w, n * rs, cudaMemcpyDeviceToDevice, h->st);
-  if (e == cudaSuccess) e = cudaMemcpyAsync(dst.id, src.id, n * sizeof(uint32_t), cudaMemcpyDeviceToDevice, h->st);
+  cudaError_t e = cudaMemcpyAsync(dst.cell, src.cell, particles_bytes(slots, h->rsize, h->g.dims),
+                                  cudaMemcpyDeviceToDevice, h->st);
   if (e == cudaSuccess) e = cudaMemcpyAsync(dcount, scount, sizeof(int64_t), cudaMemcpyDeviceToDevice, h->st);
   return e;
 }
@@ -305,10 +307,7 @@ cudaError_t copy_particles(pic_handle *h, const Particles &dst, int64_t *dcount,
 cudaError_t save_snapshot(pic_handle *h, Snapshot &sn) {
   cudaError_t e = alloc_snapshot(h, sn);
   const size_t fb = (size_t)h->g.ncell * h->rsize;
-  for (int d = 0; d < 3 && e == cudaSuccess; ++d) {
-    e = cudaMemcpyAsync(sn.E[d], h->E[d], fb, cudaMemcpyDeviceToDevice, h->st);
-    if (e == cudaSuccess) e = cudaMemcpyAsync(sn.B[d], h->B[d], fb, cudaMemcpyDeviceToDevice, h->st);
-  }
+  if (e == cudaSuccess) e = cudaMemcpyAsync(sn.E[0], h->E[0], 6 * fb, cudaMemcpyDeviceToDevice, h->st);
   for (int i = 0; i < h->nsp && e == cudaSuccess; ++i) {
     Species &s = h->sp[i];
     e = copy_particles(h, sn.sp[i].p, sn.sp[i].count, s.buf[s.cur], s.d_count, s.slots);
@@ -450,11 +449,15 @@ int pic_create(const pic_config *cfg, pic_handle **out) {
     return fail(nullptr, PIC_EINVAL, "tile + guard window does not fit in shared memory; use a smaller tile");
   }
   const size_t fb = (size_t)ncell * h->rsize;
-  bool ok = true;
-  for (int d = 0; d < 3 && ok; ++d) {
-    ok = ok && cudaMalloc(&h->E[d], fb) == cudaSuccess && cudaMalloc(&h->B[d], fb) == cudaSuccess &&
-         cudaMalloc(&h->J[d], fb) == cudaSuccess;
-  }
+  // E, B in one block (a checkpoint copies them with one memcpy) and the
+  // three J components in another (one memset clears J)
+  bool ok = cudaMalloc(&h->E[0], 6 * fb) == cudaSuccess && cudaMalloc(&h->J[0], 3 * fb) == cudaSuccess;
+  if (ok)
+    for (int d = 0; d < 3; ++d) {
+      h->E[d] = static_cast<char *>(h->E[0]) + d * fb;
+      h->B[d] = static_cast<char *>(h->E[0]) + (3 + d) * fb;
+      h->J[d] = static_cast<char *>(h->J[0]) + d * fb;
+    }
   const size_t db = (size_t)ncell * sizeof(double);
   const int64_t nkeys = g.ntiles * g.tile[0] * g.tile[1] * g.tile[2];
   ok = ok && cudaMalloc(&h->rho_bg, db) == cudaSuccess && cudaMalloc(&h->rho, db) == cudaSuccess &&
@@ -469,14 +472,28 @@ int pic_create(const pic_config *cfg, pic_handle **out) {
     pic_destroy(h);
     return fail(nullptr, PIC_ENOMEM, "device allocation failed in pic_create");
   }
-  for (int d = 0; d < 3; ++d) {
-    cudaMemsetAsync(h->E[d], 0, fb, h->st);
-    cudaMemsetAsync(h->B[d], 0, fb, h->st);
-    cudaMemsetAsync(h->J[d], 0, fb, h->st);
-  }
+  cudaMemsetAsync(h->E[0], 0, 6 * fb, h->st);
+  cudaMemsetAsync(h->J[0], 0, 3 * fb, h->st);
   cudaMemsetAsync(h->rho_bg, 0, db, h->st);
   cudaMemsetAsync(h->ctr, 0, sizeof(Counters), h->st);
-  e = cudaStreamSynchronize(h->st);
+  // laser profile P = exp(-r^2/waist^2) at the wall rows of the polarised
+  // component (Ey at (j + 1/2, k), Ez at (j, k + 1/2)), once for the run
+  const int64_t nyz = (int64_t)g.n[1] * g.n[2];
+  std::vector<double> prof((size_t)nyz, 0.0);
+  if (h->laser.enabled) {
+    const bool ey = h->laser.pol == 1;
+    for (int64_t jk = 0; jk < nyz; ++jk) {
+      const int j = (int)(jk % g.n[1]), k = (int)(jk / g.n[1]);
+      const double y = (j + (ey ? 0.5 : 0.0)) * g.dx[1], z = (k + (ey ? 0.0 : 0.5)) * g.dx[2];
+      double r2 = (y - h->laser.yc) * (y - h->laser.yc);
+      if (g.dims == 3) r2 += (z - h->laser.zc) * (z - h->laser.zc);
+      prof[(size_t)jk] = exp(-r2 / (h->laser.waist * h->laser.waist));
+    }
+  }
+  e = cudaMalloc(&h->laser_prof, sizeof(double) * (size_t)nyz);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(h->laser_prof, prof.data(), sizeof(double) * (size_t)nyz, cudaMemcpyHostToDevice, h->st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(h->st);
   if (e != cudaSuccess) {
     pic_destroy(h);
     return fail(nullptr, PIC_ECUDA, std::string("pic_create: ") + cudaGetErrorString(e));
@@ -488,11 +505,8 @@ int pic_create(const pic_config *cfg, pic_handle **out) {
 int pic_destroy(pic_handle *h) {
   if (!h) return PIC_OK;
   cudaStreamSynchronize(h->st);
-  for (int d = 0; d < 3; ++d) {
-    cudaFree(h->E[d]);
-    cudaFree(h->B[d]);
-    cudaFree(h->J[d]);
-  }
+  cudaFree(h->E[0]);  // E and B share one block
+  cudaFree(h->J[0]);  // so do the three J components
   cudaFree(h->rho_bg);
   cudaFree(h->rho);
   cudaFree(h->rho_prev);
@@ -504,6 +518,7 @@ int pic_destroy(pic_handle *h) {
   cudaFree(h->bad);
   cudaFree(h->esc_count);
   cudaFree(h->mur);
+  cudaFree(h->laser_prof);
   for (int i = 0; i < h->nsp; ++i) {
     Species &s = h->sp[i];
     free_particles(s.buf[0]);
@@ -845,7 +860,7 @@ int pic_step(pic_handle *h, int nsteps) {
     }
     {
       Timed tm(h, pic::KC_ZEROJ);
-      for (int d = 0; d < 3; ++d) CK(h, cudaMemsetAsync(h->J[d], 0, fb, h->st), "zero J");
+      CK(h, cudaMemsetAsync(h->J[0], 0, 3 * fb, h->st), "zero J");
     }
     for (int i = 0; i < h->nsp; ++i) {
       Species &s = h->sp[i];
@@ -885,7 +900,11 @@ int pic_step(pic_handle *h, int nsteps) {
     }
     if (walls) {
       Timed tm(h, pic::KC_BOUNDARY);
-      CK(h, pic::launch_mur_apply(h->g, h->E, h->mur, h->laser, h->step * h->g.dt, (h->step + 1) * h->g.dt, h->st),
+      CK(h,
+         pic::launch_mur_apply(h->g, h->E, h->mur,
+                               pic::laser_step(h->laser, h->laser_prof, h->laser.a0, h->g.dx[0], h->step * h->g.dt,
+                                               (h->step + 1) * h->g.dt),
+                               h->st),
          "mur apply");
       h->launches++;
     }
@@ -1106,10 +1125,7 @@ int pic_restore(pic_handle *h, int slot) {
     return fail(h, PIC_EINVAL, "no such checkpoint");
   Snapshot &sn = h->ckpt[slot];
   const size_t fb = (size_t)h->g.ncell * h->rsize;
-  for (int d = 0; d < 3; ++d) {
-    CK(h, cudaMemcpyAsync(h->E[d], sn.E[d], fb, cudaMemcpyDeviceToDevice, h->st), "restore");
-    CK(h, cudaMemcpyAsync(h->B[d], sn.B[d], fb, cudaMemcpyDeviceToDevice, h->st), "restore");
-  }
+  CK(h, cudaMemcpyAsync(h->E[0], sn.E[0], 6 * fb, cudaMemcpyDeviceToDevice, h->st), "restore");
   for (int i = 0; i < h->nsp; ++i) {
     Species &s = h->sp[i];
     CK(h, copy_particles(h, s.buf[s.cur], s.d_count, sn.sp[i].p, sn.sp[i].count, s.slots), "restore");
@@ -1215,19 +1231,25 @@ int pic_adjoint_step(pic_handle *h, int nsteps) {
   if (!h || !h->adj_ready) return fail(h, PIC_EINVAL, "call pic_adjoint_begin first");
   if (nsteps < 0 || nsteps > h->tape_len) return fail(h, PIC_EINVAL, "more adjoint steps than recorded steps");
   const bool walls = h->g.absorb_lo || h->g.absorb_hi;
-  pic::Laser unit = h->laser;
-  unit.a0 = 1.0;
   for (int t = 0; t < nsteps; ++t) {
     Snapshot &en = h->tape[h->tape_len - 1];
     const double t_old = en.step * h->g.dt, t_new = (en.step + 1) * h->g.dt;
-    CK(h, pic::launch_adj_yee_b(h->g, h->lE, h->lB, 0.5 * h->g.dt, h->st), "adjoint B half");
-    if (walls) CK(h, pic::launch_adj_mur(h->g, h->lE, h->pend, unit, t_old, t_new, h->da0, h->st), "adjoint Mur");
-    CK(h, pic::launch_adj_yee_e(h->g, h->lE, h->lB, h->lJ, h->g.dt, h->st), "adjoint E");
-    if (walls) CK(h, pic::launch_adj_mur_pend(h->g, h->lE, h->pend, h->st), "adjoint Mur");
-    CK(h, pic::launch_adj_yee_b(h->g, h->lE, h->lB, 0.5 * h->g.dt, h->st), "adjoint B half");
+    {
+      Timed tm(h, pic::KC_ADJ_FIELD);
+      CK(h, pic::launch_adj_yee_b(h->g, h->lE, h->lB, 0.5 * h->g.dt, h->st), "adjoint B half");
+      if (walls)
+        CK(h,
+           pic::launch_adj_mur(h->g, h->lE, h->pend,
+                               pic::laser_step(h->laser, h->laser_prof, 1.0, h->g.dx[0], t_old, t_new), h->da0, h->st),
+           "adjoint Mur");
+      CK(h, pic::launch_adj_yee_e(h->g, h->lE, h->lB, h->lJ, h->g.dt, h->st), "adjoint E");
+      if (walls) CK(h, pic::launch_adj_mur_pend(h->g, h->lE, h->pend, h->st), "adjoint Mur");
+      CK(h, pic::launch_adj_yee_b(h->g, h->lE, h->lB, 0.5 * h->g.dt, h->st), "adjoint B half");
+    }
     h->launches += walls ? 5 : 3;
     for (int i = 0; i < h->nsp; ++i) {
       Species &s = h->sp[i];
+      Timed tm(h, pic::KC_ADJ_PUSH);
       CK(h,
          pic::launch_adj_push(h->g, en.sp[i].p, en.sp[i].count, s.slots, en.E, en.B, h->lJ, h->lE, h->lB,
                               h->adj[i].lx, h->adj[i].lu, h->adj[i].lw, h->id_cap, h->adj_err, s.q, s.m, h->st),

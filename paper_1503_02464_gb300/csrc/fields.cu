@@ -88,18 +88,6 @@ __global__ void __launch_bounds__(256) k_yee_e(YeeArgs<R> a) {
   }
 }
 
-// Incoming laser field (polarised component) at (x, y, z, t):
-// a0 exp(-r^2/waist^2) sin^2(pi tau/duration) sin(tau), tau = t - x, on
-// 0 < tau < duration (carrier frequency 1).
-__device__ double laser_at(const Laser &L, int dims, double x, double y, double z, double t) {
-  const double tau = t - x;
-  if (tau <= 0.0 || tau >= L.duration) return 0.0;
-  const double env = sin(3.14159265358979323846 * tau / L.duration);
-  double r2 = (y - L.yc) * (y - L.yc);
-  if (dims == 3) r2 += (z - L.zc) * (z - L.zc);
-  return L.a0 * exp(-r2 / (L.waist * L.waist)) * env * env * sin(tau);
-}
-
 template <class R>
 __global__ void k_mur_save(int n0, int n1, int n2, const R *Ey, const R *Ez, double *buf) {
   const int64_t nyz = (int64_t)n1 * n2;
@@ -114,25 +102,19 @@ __global__ void k_mur_save(int n0, int n1, int n2, const R *Ey, const R *Ez, dou
 
 // E(0)^{n+1} = L(0)^{n+1} + S(1)^n + k (S(1)^{n+1} - S(0)^n), S = E - L the
 // scattered field, k = (dt - dx)/(dt + dx); the same without L at x = n0-1.
+// L = P(row) times the step's four waveform values (LaserStep).
 template <class R>
-__global__ void k_mur_apply(int dims, int n0, int n1, int n2, double dx, double dy, double dz, double dt, R *Ey,
-                            R *Ez, const double *buf, Laser las, double t_old, double t_new) {
+__global__ void k_mur_apply(int n0, int n1, int n2, double dx, double dt, R *Ey, R *Ez, const double *buf,
+                            LaserStep ls) {
   const int64_t nyz = (int64_t)n1 * n2;
   const double kc = (dt - dx) / (dt + dx);
   for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < 2 * nyz; q += (int64_t)gridDim.x * blockDim.x) {
     const int c = (int)(q / nyz);  // 0: Ey, 1: Ez
     const int64_t jk = q % nyz;
-    const int j = (int)(jk % n1), k = (int)(jk / n1);
     R *E = c == 0 ? Ey : Ez;
     const double *o = buf + (int64_t)c * 4 * nyz;
-    const bool lit = las.enabled && las.pol == c + 1;
-    // Ey sits at (i, j+1/2, k), Ez at (i, j, k+1/2)
-    const double y = (j + (c == 0 ? 0.5 : 0.0)) * dy;
-    const double z = (k + (c == 1 ? 0.5 : 0.0)) * dz;
-    const double l0o = lit ? laser_at(las, dims, 0.0, y, z, t_old) : 0.0;
-    const double l1o = lit ? laser_at(las, dims, dx, y, z, t_old) : 0.0;
-    const double l0n = lit ? laser_at(las, dims, 0.0, y, z, t_new) : 0.0;
-    const double l1n = lit ? laser_at(las, dims, dx, y, z, t_new) : 0.0;
+    const double p = ls.pol == c + 1 ? ls.prof[jk] : 0.0;
+    const double l0o = p * ls.amp[0], l1o = p * ls.amp[1], l0n = p * ls.amp[2], l1n = p * ls.amp[3];
     const int64_t row = (int64_t)n0 * jk;
     const double s0o = o[0 * nyz + jk] - l0o;
     const double s1o = o[1 * nyz + jk] - l1o;
@@ -471,17 +453,32 @@ cudaError_t launch_mur_save(const Grid &g, void *const E[3], double *buf, cudaSt
   return cudaGetLastError();
 }
 
-cudaError_t launch_mur_apply(const Grid &g, void *const E[3], const double *buf, const Laser &las, double t_old,
-                             double t_new, cudaStream_t st) {
+double laser_waveform(const Laser &L, double tau) {
+  if (tau <= 0.0 || tau >= L.duration) return 0.0;
+  const double env = sin(3.14159265358979323846 * tau / L.duration);
+  return env * env * sin(tau);
+}
+
+LaserStep laser_step(const Laser &L, const double *prof, double amplitude, double dx, double t_old, double t_new) {
+  LaserStep ls;
+  ls.pol = L.enabled ? L.pol : 0;
+  ls.prof = prof;
+  ls.amp[0] = amplitude * laser_waveform(L, t_old);
+  ls.amp[1] = amplitude * laser_waveform(L, t_old - dx);
+  ls.amp[2] = amplitude * laser_waveform(L, t_new);
+  ls.amp[3] = amplitude * laser_waveform(L, t_new - dx);
+  return ls;
+}
+
+cudaError_t launch_mur_apply(const Grid &g, void *const E[3], const double *buf, const LaserStep &ls,
+                             cudaStream_t st) {
   const int nb = grid_blocks(2LL * g.n[1] * g.n[2], 256);
   if (g.prec == 1)
-    k_mur_apply<double><<<nb, 256, 0, st>>>(g.dims, g.n[0], g.n[1], g.n[2], g.dx[0], g.dx[1], g.dx[2], g.dt,
-                                            static_cast<double *>(E[1]), static_cast<double *>(E[2]), buf, las,
-                                            t_old, t_new);
+    k_mur_apply<double><<<nb, 256, 0, st>>>(g.n[0], g.n[1], g.n[2], g.dx[0], g.dt, static_cast<double *>(E[1]),
+                                            static_cast<double *>(E[2]), buf, ls);
   else
-    k_mur_apply<float><<<nb, 256, 0, st>>>(g.dims, g.n[0], g.n[1], g.n[2], g.dx[0], g.dx[1], g.dx[2], g.dt,
-                                           static_cast<float *>(E[1]), static_cast<float *>(E[2]), buf, las, t_old,
-                                           t_new);
+    k_mur_apply<float><<<nb, 256, 0, st>>>(g.n[0], g.n[1], g.n[2], g.dx[0], g.dt, static_cast<float *>(E[1]),
+                                           static_cast<float *>(E[2]), buf, ls);
   return cudaGetLastError();
 }
 

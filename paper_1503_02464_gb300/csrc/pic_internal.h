@@ -26,12 +26,31 @@ struct Grid {
   int gather_ec;             // energy-conserving gather (lower order at half-integer positions)
 };
 
-// Laser entering through the x = 0 wall (copied from pic_config).
+// Laser entering through the x = 0 wall (copied from pic_config).  Its
+// polarised field is a0 P(y, z) T(t - x): the transverse profile
+// P = exp(-r^2 / waist^2), r measured from the spot centre (yc, zc), times
+// the waveform T(tau) = sin^2(pi tau / duration) sin(tau) on 0 < tau <
+// duration (carrier frequency 1), 0 elsewhere.
 struct Laser {
   int enabled;
   double a0, waist, duration, yc, zc;
   int pol;  // 1: E along y, 2: E along z
 };
+
+// The waveform T(tau) (host).
+double laser_waveform(const Laser &L, double tau);
+
+// What the Mur kernels need of the laser for one step from t_old to t_new:
+// amp = {T(t_old), T(t_old - dx), T(t_new), T(t_new - dx)} times the
+// amplitude (a0 for the forward update, 1 for the adjoint's dF/da0), and
+// prof = P at the wall rows of the polarised component (n1 * n2 doubles:
+// Ey rows at (j + 1/2, k), Ez rows at (j, k + 1/2)); pol = 0: no laser.
+struct LaserStep {
+  int pol;
+  double amp[4];
+  const double *prof;
+};
+LaserStep laser_step(const Laser &L, const double *prof, double amplitude, double dx, double t_old, double t_new);
 
 // Particles whose new position leaves [kWallLo, n0 - kWallHiMargin) cells in
 // x are removed at absorbing walls (after depositing their move).
@@ -62,7 +81,8 @@ void set_global_error(const std::string &msg);
 constexpr int kTilePad = 4;
 
 enum KernelClass {
-  KC_SORT = 0, KC_ZEROJ = 1, KC_PUSH = 2, KC_YEE_B = 3, KC_YEE_E = 4, KC_BOUNDARY = 5, KC_FILTER = 6, KC_N = 7
+  KC_SORT = 0, KC_ZEROJ = 1, KC_PUSH = 2, KC_YEE_B = 3, KC_YEE_E = 4, KC_BOUNDARY = 5, KC_FILTER = 6,
+  KC_ADJ_FIELD = 7, KC_ADJ_PUSH = 8, KC_N = 9
 };
 
 // ---- push (push.cu) ----
@@ -115,8 +135,8 @@ cudaError_t launch_yee_e(const Grid &g, void *const E[3], void *const B[3], void
 // `buf` (8 * n1 * n2 values) before the E update; apply afterwards, with the
 // incoming laser wave at x = 0 (times t_old = n dt, t_new = (n+1) dt).
 cudaError_t launch_mur_save(const Grid &g, void *const E[3], double *buf, cudaStream_t st);
-cudaError_t launch_mur_apply(const Grid &g, void *const E[3], const double *buf, const Laser &las, double t_old,
-                             double t_new, cudaStream_t st);
+cudaError_t launch_mur_apply(const Grid &g, void *const E[3], const double *buf, const LaserStep &ls,
+                             cudaStream_t st);
 // Load n particles into slots [offset, offset+n).
 cudaError_t launch_load(const Grid &g, const Particles &p, int64_t offset, int64_t n, const double *x,
                         const double *y, const double *z, const double *ux, const double *uy, const double *uz,
@@ -161,8 +181,8 @@ cudaError_t launch_particle_diag(const Grid &g, const Particles &p, const int64_
 cudaError_t launch_adj_yee_b(const Grid &g, void *const lE[3], void *const lB[3], double h, cudaStream_t st);
 cudaError_t launch_adj_yee_e(const Grid &g, void *const lE[3], void *const lB[3], void *const lJ[3], double h,
                              cudaStream_t st);
-cudaError_t launch_adj_mur(const Grid &g, void *const lE[3], double *pend, const Laser &las_unit, double t_old,
-                           double t_new, double *da0, cudaStream_t st);
+cudaError_t launch_adj_mur(const Grid &g, void *const lE[3], double *pend, const LaserStep &ls_unit, double *da0,
+                           cudaStream_t st);
 cudaError_t launch_adj_mur_pend(const Grid &g, void *const lE[3], const double *pend, cudaStream_t st);
 // Per-particle adjoint of one recorded step (2D3V TSC only): tp/d_count
 // is the particle state at the start of the step, E/B the fields gathered.

@@ -809,7 +809,13 @@ cudaError_t launch_t(const Grid &g, void *const E[3], void *const B[3], void *co
 // one block per tile like k_push.  The block's window sums are exact 64-bit
 // fixed point (|rho_node| <= sum |q w| over the tile bounds the scale), so
 // the result does not depend on the order of the additions; particles more
-// than one cell outside their tile add to the global array directly.
+// than one cell outside their tile add to the global array directly.  The
+// 1D weights are FP64 in both precisions.  FP64 runs scale the tile's charge
+// bound to 2^61 and convert each product with a float-to-integer
+// conversion; FP32 runs, whose currents carry FP32 rounding anyway, scale it
+// to 2^50 and take the integer from one FMA against 1.5 * 2^52 (the bit
+// pattern of a double in [2^52, 2^53) holds an integer), sparing the slow
+// FP64 conversions.
 template <class R, int DIM, int ORDER>
 __global__ void __launch_bounds__(kThreads)
     k_rho_tile(int n0, int n1, int n2, int ntile0, int ntile1, FastDiv dn0, FastDiv dn1, const int32_t *__restrict__ cell,
@@ -839,7 +845,10 @@ __global__ void __launch_bounds__(kThreads)
   const double Q = fabs(q) * s_sum * 1.0001;
   int e2 = 0;
   if (Q > 0.0) frexp(Q, &e2);
-  const double scale = ldexp(1.0, Q > 0.0 ? 61 - e2 : 0);
+  constexpr bool kFma = sizeof(R) == 4;
+  constexpr int kBits = kFma ? 50 : 61;
+  constexpr double kMagic = 6755399441055744.0;  // 1.5 * 2^52
+  const double scale = ldexp(1.0, Q > 0.0 ? kBits - e2 : 0);
   const R *offs[3] = {off0, off1, off2};
   for (int64_t p = pb + threadIdx.x; p < pe; p += kThreads) {
     const int c = cell[p];
@@ -879,24 +888,34 @@ __global__ void __launch_bounds__(kThreads)
       }
     }
     const double qw = q * (double)w[p];
+    double qwx[NS];  // q w S_x, pre-scaled for the window
+#pragma unroll
+    for (int kx = 0; kx < NS; ++kx) qwx[kx] = (inw ? qw * scale : qw) * wt[0][kx];
 #pragma unroll
     for (int kz = 0; kz < (DIM == 3 ? NS : 1); ++kz)
 #pragma unroll
-      for (int ky = 0; ky < NS; ++ky)
+      for (int ky = 0; ky < NS; ++ky) {
+        const double wyz = wt[1][ky] * wt[2][kz];
 #pragma unroll
         for (int kx = 0; kx < NS; ++kx) {
-          const double v = qw * wt[0][kx] * wt[1][ky] * wt[2][kz];
           if (inw) {
             const int ix = l[0] + base[0] + kx + G::D + G::LOE;
             const int iy = l[1] + base[1] + ky + G::D + G::LOE;
             const int iz = DIM == 3 ? l[2] + base[2] + kz + G::D + G::LOE : 0;
-            atomicAdd(&win[ix + RX * (iy + RY * iz)], (unsigned long long)__double2ll_rn(v * scale));
+            long long X;
+            if (kFma)
+              X = __double_as_longlong(fma(qwx[kx], wyz, kMagic)) - __double_as_longlong(kMagic);
+            else
+              X = __double2ll_rn(qwx[kx] * wyz);
+            atomicAdd(&win[ix + RX * (iy + RY * iz)], (unsigned long long)X);
           } else {
+            const double v = qwx[kx] * wyz;
             const int gi = wrapi(ci[0] + base[0] + kx, n0), gj = wrapi(ci[1] + base[1] + ky, n1);
             const int gk = DIM == 3 ? wrapi(ci[2] + base[2] + kz, n2) : 0;
             atomicAdd(rho + gi + (int64_t)n0 * (gj + (int64_t)n1 * gk), v);
           }
         }
+      }
   }
   __syncthreads();
   for (int i = threadIdx.x; i < RN; i += kThreads) {
