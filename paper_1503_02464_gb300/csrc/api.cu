@@ -24,7 +24,6 @@ using pic::Particles;
 namespace {
 
 constexpr int kMaxSpecies = 8;
-constexpr int kBlock = 256;
 
 struct Species {
   double q = 0, m = 1;
