@@ -389,7 +389,8 @@ def run_gpu(args, rank: int, world: int, local: int):
                "h2d_bytes_per_step": int(h2d / args.steps), "d2h_bytes_per_step": d2h,
                "pinned": len(regs) == sum(len(h.arrays) for h in host),
                "load_s": t_load, "diag_wall_ms_per_step": 1e3 * t_diag / args.steps,
-               "note": "load from pinned host + per-step pic_step + pic_energy read-back, wall clock"}
+               "note": "load from pinned host (read in place by the load kernel) + per-step pic_step + "
+                       "pic_energy read-back, wall clock"}
 
     # ---------------- CPU oracle baseline (rank 0, N = 1 only)
     cpu = None

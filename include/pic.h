@@ -185,7 +185,9 @@ int pic_add_species(pic_handle *h, double q, double m, int64_t capacity, int *sp
  * particle outside the absorbing walls' [3, n[0] - 4) cells, or with a
  * non-finite position, momentum or weight, is stored dead and the call
  * returns PIC_EINVAL after loading the others.  Exceeding capacity:
- * PIC_ENOMEM (nothing loaded). */
+ * PIC_ENOMEM (nothing loaded).  Host arrays that are page-locked and mapped
+ * for the device (e.g. registered with cudaHostRegister) are read in place by
+ * the load kernel; other host arrays go through device staging copies. */
 int pic_load_particles(pic_handle *h, int species, int64_t n, const double *x, const double *y,
                        const double *z, const double *ux, const double *uy, const double *uz,
                        const double *w, const uint32_t *id, int mem_kind);

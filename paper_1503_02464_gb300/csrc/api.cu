@@ -612,7 +612,24 @@ int pic_load_particles(pic_handle *h, int species, int64_t n, const double *x, c
   const double *src[7] = {x, y, z, ux, uy, uz, w};
   const double *dsrc[7] = {};
   std::vector<void *> tmp;
-  if (mem_kind == PIC_MEM_HOST) {
+  // Host arrays that the device can address (page-locked and mapped, e.g.
+  // registered with cudaHostRegister) are read in place by the load kernel
+  // over the host link: no staging buffers, no separate copies.
+  auto mapped = [](const void *p) -> const void * {
+    cudaPointerAttributes at;
+    if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+      cudaGetLastError();
+      return nullptr;
+    }
+    return at.type == cudaMemoryTypeHost ? at.devicePointer : nullptr;
+  };
+  bool direct = mem_kind == PIC_MEM_HOST && (!id || mapped(id));
+  for (int a = 0; a < 7 && direct; ++a) direct = !src[a] || mapped(src[a]);
+  const uint32_t *did = id;
+  if (mem_kind == PIC_MEM_HOST && direct) {
+    for (int a = 0; a < 7; ++a) dsrc[a] = src[a] ? static_cast<const double *>(mapped(src[a])) : nullptr;
+    if (id) did = static_cast<const uint32_t *>(mapped(id));
+  } else if (mem_kind == PIC_MEM_HOST) {
     for (int a = 0; a < 7; ++a) {
       if (!src[a]) continue;
       void *p = nullptr;
@@ -624,14 +641,13 @@ int pic_load_particles(pic_handle *h, int species, int64_t n, const double *x, c
   } else {
     for (int a = 0; a < 7; ++a) dsrc[a] = src[a];
   }
-  const uint32_t *did = id;
   std::vector<uint32_t> gen;
   if (!id) {
     gen.resize((size_t)n);
     for (int64_t i = 0; i < n; ++i) gen[(size_t)i] = (uint32_t)(cur + i);
     did = gen.data();
   }
-  if (mem_kind == PIC_MEM_HOST || !id) {
+  if ((mem_kind == PIC_MEM_HOST && !direct) || !id) {
     void *p = nullptr;
     CK(h, cudaMallocAsync(&p, (size_t)n * sizeof(uint32_t), h->st), "load staging alloc");
     tmp.push_back(p);
@@ -659,15 +675,16 @@ int pic_load_particles(pic_handle *h, int species, int64_t n, const double *x, c
 
 int pic_neutralize(pic_handle *h) {
   if (!h) return fail(h, PIC_EINVAL, "NULL handle");
+  // rho_bg = -rho of the particles: deposit them with the opposite charge
   CK(h, cudaMemsetAsync(h->rho_bg, 0, sizeof(double) * h->g.ncell, h->st), "memset");
-  int r = compute_rho(h, h->rho);
-  if (r) return r;
-  // rho_bg = -rho
-  std::vector<double> tmp((size_t)h->g.ncell);
-  CK(h, cudaMemcpyAsync(tmp.data(), h->rho, sizeof(double) * h->g.ncell, cudaMemcpyDeviceToHost, h->st), "D2H");
-  CK(h, cudaStreamSynchronize(h->st), "sync");
-  for (auto &v : tmp) v = -v;
-  CK(h, cudaMemcpyAsync(h->rho_bg, tmp.data(), sizeof(double) * h->g.ncell, cudaMemcpyHostToDevice, h->st), "H2D");
+  for (int i = 0; i < h->nsp; ++i) {
+    Species &s = h->sp[i];
+    if (s.need_sort)
+      CK(h, pic::launch_rho(h->g, s.buf[s.cur], s.d_count, s.slots, -s.q, h->rho_bg, h->st), "rho deposit");
+    else
+      CK(h, pic::launch_rho_tiled(h->g, s.buf[s.cur], s.tile_start, -s.q, h->rho_bg, h->st), "rho deposit");
+    h->launches++;
+  }
   CK(h, cudaStreamSynchronize(h->st), "sync");
   return PIC_OK;
 }
