@@ -3,11 +3,13 @@
 // ref [8], the charge-conserving deposit for the continuity requirement it
 // states in §2).
 //
-// One thread block owns one cell tile (8x8x8 in 3D, 16x16 in 2D).  The sort
-// keeps each tile's particles in one contiguous, 4-aligned slot range.  The
+// Cell tiles are 8x8x4 in 3D, 16x16 in 2D.  The sort keeps each tile's
+// particles in one contiguous, 4-aligned slot range and cuts that range into
+// work items of bounded size; one thread block takes one work item.  The
 // block stages E and B of the tile plus guard cells in shared memory and
-// accumulates J of the tile plus guard with shared-memory atomics, then adds
-// its J window to the global J (one atomic per non-zero value).
+// accumulates J of the tile plus guard with shared-memory atomics (fixed
+// point in FP32 runs), then adds its J window to the global J (one atomic per
+// non-zero value).
 //
 // Particles stream through a 256-slot shared staging chunk: loaded and stored
 // with coalesced accesses in slot order, but processed in a permuted order
