@@ -167,13 +167,29 @@ def _dist_setup(args):
 
 
 def _barrier_max(world, value: float) -> float:
+    """Max of `value` over the ranks (the slowest replica sets the time)."""
     if world == 1:
         return value
     import torch
     import torch.distributed as dist
-    t = torch.tensor([value], dtype=torch.float64, device="cuda")
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([value], dtype=torch.float64, device=dev)
     dist.all_reduce(t, op=dist.ReduceOp.MAX)
     return float(t.item())
+
+
+def replica_workload(name: str, rank: int, world: int):
+    """The workload of one rank: the same preset, an independent seed per
+    replica (the path does not shard: N GPUs run N replicas)."""
+    wl = synth.preset(name)
+    if world > 1:
+        wl.seed += 7919 * rank
+    return wl
+
+
+def aggregate_rate(world: int, npart: int, steps: int, seconds: float) -> float:
+    """Whole-job particle-steps/s: every rank's particles over the max time."""
+    return world * npart * steps / seconds
 
 
 def _barrier(world):
@@ -197,9 +213,7 @@ def run_gpu(args, rank: int, world: int, local: int):
     from paper_1503_02464_gb300 import capi
     from paper_1503_02464_gb300.sim import Simulation
 
-    wl = synth.preset(args.workload)
-    if world > 1:
-        wl.seed += 7919 * rank  # independent replica per rank
+    wl = replica_workload(args.workload, rank, world)
     streamed = wl.n_particles() > STREAM_PARTICLES
     # host inputs first (spawned pool, before the first CUDA call)
     t_gen = time.perf_counter()
@@ -307,7 +321,7 @@ def run_gpu(args, rank: int, world: int, local: int):
         sim.close()
         del sim
         p64_ms, p64_n = t64["push"]
-        fp64 = {"value": world * npart * args.fp64_steps / dt64, "unit": "particle-steps/s",
+        fp64 = {"value": aggregate_rate(world, npart, args.fp64_steps, dt64), "unit": "particle-steps/s",
                 "ms_per_step": 1e3 * dt64 / args.fp64_steps, "steps": args.fp64_steps,
                 "push_ms_per_launch": p64_ms / max(p64_n, 1)}
         torch.cuda.synchronize()
@@ -385,7 +399,7 @@ def run_gpu(args, rank: int, world: int, local: int):
             cudart.cudaHostUnregister(ptr)
         h2d = sum(sum(v.nbytes for v in h.arrays.values()) for h in host)
         d2h = 5 * 8
-        e2e = {"value": world * npart * args.steps / e2e_s, "unit": "particle-steps/s",
+        e2e = {"value": aggregate_rate(world, npart, args.steps, e2e_s), "unit": "particle-steps/s",
                "h2d_bytes_per_step": int(h2d / args.steps), "d2h_bytes_per_step": d2h,
                "pinned": len(regs) == sum(len(h.arrays) for h in host),
                "load_s": t_load, "diag_wall_ms_per_step": 1e3 * t_diag / args.steps,
@@ -410,7 +424,7 @@ def run_gpu(args, rank: int, world: int, local: int):
     if rank != 0:
         return
     r = results["main"]
-    value = world * npart * args.steps / r["dt"]
+    value = aggregate_rate(world, npart, args.steps, r["dt"])
     peak, peak_kind = _peaks()
     push_avg_s = push_ms / max(push_n, 1) / 1e3
     alg_bytes = npart * PUSH_BYTES_PER_PARTICLE[args.precision] + ncell * PUSH_BYTES_PER_CELL[args.precision]
