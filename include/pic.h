@@ -296,6 +296,28 @@ int pic_adjoint_step(pic_handle *h, int nsteps);
  * Synchronises. */
 int pic_grad(pic_handle *h, double *d_a0, int species, double *d_w, int mem_kind);
 
+/* ---- state save / resume ----------------------------------------------
+ * A run's complete state as one byte blob: fields E, B, J, the background
+ * charge, every species' particle storage (in the library's own cell +
+ * offset form, so a resumed run continues exactly where the saved one
+ * stopped), the step count and the device counters.  The blob starts with a
+ * header recording the configuration; pic_state_load accepts it only into a
+ * handle created with the same configuration and the same species (charge,
+ * mass, capacity) added in the same order.  Output requests, checkpoints and
+ * adjoint state are not part of it. */
+
+/* Bytes of the state blob of this handle. */
+int pic_state_size(pic_handle *h, int64_t *bytes);
+
+/* Write the state into buf (host or device memory per mem_kind, `bytes` =
+ * pic_state_size).  Synchronises.  PIC_EINVAL for a short buffer. */
+int pic_state_save(pic_handle *h, void *buf, int64_t bytes, int mem_kind);
+
+/* Replace the state by a saved one.  PIC_EINVAL (state unchanged) when the
+ * blob's header does not match this handle.  The species are re-sorted at
+ * the next step. */
+int pic_state_load(pic_handle *h, const void *buf, int64_t bytes, int mem_kind);
+
 /* ---- output manager (§3.1) --------------------------------------------
  * The paper's output manager writes reduced-dimension outputs (a plane of a
  * 3D run, a line of a multidimensional one) and sub-domain outputs (a small

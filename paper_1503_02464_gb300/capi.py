@@ -28,7 +28,7 @@ EXPORTED = ["pic_create", "pic_destroy", "pic_last_error", "pic_add_species", "p
             "pic_neutralize", "pic_set_background", "pic_step", "pic_fields", "pic_set_field", "pic_num_particles", "pic_particles",
             "pic_diag", "pic_energy", "pic_sync", "pic_profile", "pic_timings", "pic_launch_count", "pic_checkpoint",
             "pic_restore", "pic_tape_begin", "pic_adjoint_begin", "pic_adjoint_seed_kinetic", "pic_adjoint_step",
-            "pic_grad", "pic_output_due", "pic_output_add", "pic_output_capture", "pic_output_count",
+            "pic_grad", "pic_state_size", "pic_state_save", "pic_state_load", "pic_output_due", "pic_output_add", "pic_output_capture", "pic_output_count",
             "pic_output_read", "pic_output_remove", "pic_field_energy_noalloc"]
 
 
@@ -127,6 +127,9 @@ def load(build_if_missing: bool = True) -> ctypes.CDLL:
         "pic_grad": ([hp, dp, ctypes.c_int, vp, ctypes.c_int], ctypes.c_int),
         "pic_field_energy_noalloc": ([ctypes.c_int, ctypes.c_void_p * 3, ctypes.c_void_p * 3, i64, ctypes.c_double,
                                       vp, ctypes.c_int, vp], ctypes.c_int),
+        "pic_state_size": ([hp, ctypes.POINTER(ctypes.c_int64)], ctypes.c_int),
+        "pic_state_save": ([hp, vp, i64, ctypes.c_int], ctypes.c_int),
+        "pic_state_load": ([hp, vp, i64, ctypes.c_int], ctypes.c_int),
         "pic_output_due": ([ctypes.POINTER(pic_output_t), i64], ctypes.c_int),
         "pic_output_add": ([hp, ctypes.POINTER(pic_output_t), ctypes.POINTER(ctypes.c_int)], ctypes.c_int),
         "pic_output_capture": ([hp, ctypes.c_int], ctypes.c_int),
@@ -264,6 +267,20 @@ def pic_grad(h, species: int, dw_ptr, mem_kind: int) -> float:
     d_a0 = ctypes.c_double()
     check(h, load().pic_grad(h, ctypes.byref(d_a0), int(species), dw_ptr, int(mem_kind)))
     return d_a0.value
+
+
+def pic_state_size(h) -> int:
+    n = ctypes.c_int64()
+    check(h, load().pic_state_size(h, ctypes.byref(n)))
+    return n.value
+
+
+def pic_state_save(h, buf_ptr, nbytes: int, mem_kind: int) -> None:
+    check(h, load().pic_state_save(h, buf_ptr, int(nbytes), int(mem_kind)))
+
+
+def pic_state_load(h, buf_ptr, nbytes: int, mem_kind: int) -> None:
+    check(h, load().pic_state_load(h, buf_ptr, int(nbytes), int(mem_kind)))
 
 
 def make_output(kind: int, which: int, lo, hi, first: int, last: int, every: int = 1, max_frames: int = 1,

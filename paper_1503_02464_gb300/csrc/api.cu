@@ -753,6 +753,148 @@ OutputReq *output_get(pic_handle *h, int id) {
 
 }  // namespace
 
+// ---- state blob: header, then E B | J | rho_bg | per species particle block
+namespace {
+
+struct StateHeader {
+  char magic[8];
+  int32_t version, dims, n[3], order, prec, nsp, bc_lo0, bc_hi0, laser_on, filter_passes, filter_comp, gather, pad;
+  double dx[3], dt, laser_a0, laser_waist, laser_duration;
+  int64_t step, ncell;
+  int64_t slots[kMaxSpecies], count[kMaxSpecies];
+  double q[kMaxSpecies], m[kMaxSpecies];
+  Counters ctr;
+};
+constexpr char kStateMagic[8] = {'P', 'I', 'C', 'S', 'T', 'A', 'T', 'E'};
+
+StateHeader state_header(pic_handle *h) {
+  StateHeader hd;
+  memset(&hd, 0, sizeof hd);
+  memcpy(hd.magic, kStateMagic, 8);
+  hd.version = 1;
+  hd.dims = h->g.dims;
+  for (int d = 0; d < 3; ++d) {
+    hd.n[d] = h->g.n[d];
+    hd.dx[d] = h->g.dx[d];
+  }
+  hd.order = h->g.order;
+  hd.prec = h->g.prec;
+  hd.nsp = h->nsp;
+  hd.bc_lo0 = h->g.absorb_lo;
+  hd.bc_hi0 = h->g.absorb_hi;
+  hd.laser_on = h->laser.enabled;
+  hd.filter_passes = h->cfg.filter_passes;
+  hd.filter_comp = h->cfg.filter_compensate;
+  hd.gather = h->cfg.gather;
+  hd.dt = h->g.dt;
+  hd.laser_a0 = h->laser.enabled ? h->laser.a0 : 0.0;
+  hd.laser_waist = h->laser.enabled ? h->laser.waist : 0.0;
+  hd.laser_duration = h->laser.enabled ? h->laser.duration : 0.0;
+  hd.step = h->step;
+  hd.ncell = h->g.ncell;
+  for (int i = 0; i < h->nsp; ++i) {
+    hd.slots[i] = h->sp[i].slots;
+    hd.q[i] = h->sp[i].q;
+    hd.m[i] = h->sp[i].m;
+  }
+  return hd;
+}
+
+int64_t state_bytes(pic_handle *h) {
+  const int64_t fb = h->g.ncell * (int64_t)h->rsize;
+  int64_t b = (int64_t)sizeof(StateHeader) + 9 * fb + h->g.ncell * (int64_t)sizeof(double);
+  for (int i = 0; i < h->nsp; ++i) b += (int64_t)particles_bytes(h->sp[i].slots, h->rsize, h->g.dims);
+  return b;
+}
+
+}  // namespace
+
+int pic_state_size(pic_handle *h, int64_t *bytes) {
+  if (!h || !bytes) return fail(h, PIC_EINVAL, "NULL argument");
+  *bytes = state_bytes(h);
+  return PIC_OK;
+}
+
+int pic_state_save(pic_handle *h, void *buf, int64_t bytes, int mem_kind) {
+  if (!h || !buf) return fail(h, PIC_EINVAL, "NULL argument");
+  if (mem_kind != PIC_MEM_HOST && mem_kind != PIC_MEM_DEVICE) return fail(h, PIC_EINVAL, "bad memory kind");
+  if (bytes < state_bytes(h)) return fail(h, PIC_EINVAL, "state buffer too small");
+  StateHeader hd = state_header(h);
+  for (int i = 0; i < h->nsp; ++i) hd.count[i] = read_count(h, h->sp[i]);
+  CK(h, cudaMemcpyAsync(&hd.ctr, h->ctr, sizeof(Counters), cudaMemcpyDeviceToHost, h->st), "D2H");
+  CK(h, cudaStreamSynchronize(h->st), "sync");
+  const cudaMemcpyKind to = mem_kind == PIC_MEM_HOST ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice;
+  char *p = static_cast<char *>(buf);
+  CK(h, cudaMemcpyAsync(p, &hd, sizeof hd, mem_kind == PIC_MEM_HOST ? cudaMemcpyHostToHost : cudaMemcpyHostToDevice,
+                        h->st),
+     "state header");
+  p += sizeof hd;
+  const size_t fb = (size_t)h->g.ncell * h->rsize;
+  CK(h, cudaMemcpyAsync(p, h->E[0], 6 * fb, to, h->st), "state fields");
+  p += 6 * fb;
+  CK(h, cudaMemcpyAsync(p, h->J[0], 3 * fb, to, h->st), "state J");
+  p += 3 * fb;
+  CK(h, cudaMemcpyAsync(p, h->rho_bg, sizeof(double) * (size_t)h->g.ncell, to, h->st), "state background");
+  p += sizeof(double) * (size_t)h->g.ncell;
+  for (int i = 0; i < h->nsp; ++i) {
+    Species &s = h->sp[i];
+    const size_t pb = particles_bytes(s.slots, h->rsize, h->g.dims);
+    CK(h, cudaMemcpyAsync(p, s.buf[s.cur].cell, pb, to, h->st), "state particles");
+    p += pb;
+  }
+  CK(h, cudaStreamSynchronize(h->st), "sync");
+  return check_device_errors(h);
+}
+
+int pic_state_load(pic_handle *h, const void *buf, int64_t bytes, int mem_kind) {
+  if (!h || !buf) return fail(h, PIC_EINVAL, "NULL argument");
+  if (mem_kind != PIC_MEM_HOST && mem_kind != PIC_MEM_DEVICE) return fail(h, PIC_EINVAL, "bad memory kind");
+  if (bytes < (int64_t)sizeof(StateHeader)) return fail(h, PIC_EINVAL, "state blob too small");
+  StateHeader hd;
+  CK(h,
+     cudaMemcpyAsync(&hd, buf, sizeof hd, mem_kind == PIC_MEM_HOST ? cudaMemcpyHostToHost : cudaMemcpyDeviceToHost,
+                     h->st),
+     "state header");
+  CK(h, cudaStreamSynchronize(h->st), "sync");
+  // the blob must come from a handle of the same configuration and species
+  StateHeader me = state_header(h);
+  bool same = memcmp(hd.magic, kStateMagic, 8) == 0 && hd.version == me.version && hd.dims == me.dims &&
+              hd.order == me.order && hd.prec == me.prec && hd.nsp == me.nsp && hd.bc_lo0 == me.bc_lo0 &&
+              hd.bc_hi0 == me.bc_hi0 && hd.laser_on == me.laser_on && hd.filter_passes == me.filter_passes &&
+              hd.filter_comp == me.filter_comp && hd.gather == me.gather && hd.dt == me.dt &&
+              hd.laser_a0 == me.laser_a0 && hd.laser_waist == me.laser_waist &&
+              hd.laser_duration == me.laser_duration && hd.ncell == me.ncell;
+  for (int d = 0; d < 3; ++d) same = same && hd.n[d] == me.n[d] && hd.dx[d] == me.dx[d];
+  for (int i = 0; i < me.nsp && same; ++i)
+    same = hd.slots[i] == me.slots[i] && hd.q[i] == me.q[i] && hd.m[i] == me.m[i] && hd.count[i] >= 0 &&
+           hd.count[i] <= me.slots[i];
+  if (!same) return fail(h, PIC_EINVAL, "state blob does not match this simulation's configuration and species");
+  if (bytes < state_bytes(h)) return fail(h, PIC_EINVAL, "state blob too small");
+  const cudaMemcpyKind from = mem_kind == PIC_MEM_HOST ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice;
+  const char *p = static_cast<const char *>(buf) + sizeof hd;
+  const size_t fb = (size_t)h->g.ncell * h->rsize;
+  CK(h, cudaMemcpyAsync(h->E[0], p, 6 * fb, from, h->st), "state fields");
+  p += 6 * fb;
+  CK(h, cudaMemcpyAsync(h->J[0], p, 3 * fb, from, h->st), "state J");
+  p += 3 * fb;
+  CK(h, cudaMemcpyAsync(h->rho_bg, p, sizeof(double) * (size_t)h->g.ncell, from, h->st), "state background");
+  p += sizeof(double) * (size_t)h->g.ncell;
+  for (int i = 0; i < h->nsp; ++i) {
+    Species &s = h->sp[i];
+    const size_t pb = particles_bytes(s.slots, h->rsize, h->g.dims);
+    CK(h, cudaMemcpyAsync(s.buf[s.cur].cell, p, pb, from, h->st), "state particles");
+    p += pb;
+    CK(h, cudaMemcpyAsync(s.d_count, &hd.count[i], sizeof(int64_t), cudaMemcpyHostToDevice, h->st), "count");
+    s.h_count = hd.count[i];
+    s.need_sort = true;
+  }
+  CK(h, cudaMemcpyAsync(h->ctr, &hd.ctr, sizeof(Counters), cudaMemcpyHostToDevice, h->st), "counters");
+  CK(h, cudaStreamSynchronize(h->st), "sync");
+  h->step = hd.step;
+  h->rho_prev_step = -2;
+  return PIC_OK;
+}
+
 int pic_output_due(const pic_output_t *req, int64_t step) {
   if (!req || req->every < 1) return 0;
   return step >= req->first && step <= req->last && (step - req->first) % req->every == 0;

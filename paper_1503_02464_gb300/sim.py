@@ -191,6 +191,27 @@ class Simulation:
         a = np.ascontiguousarray(np.broadcast_to(arr, self.shape3), dtype=np.float64)
         capi.pic_set_field(self.h, which, a.ctypes.data, capi.PIC_MEM_HOST)
 
+    # -- state save / resume
+    def state(self) -> np.ndarray:
+        """The complete state (fields, background, particles, step, counters)
+        as a byte array."""
+        buf = np.empty(capi.pic_state_size(self.h), dtype=np.uint8)
+        capi.pic_state_save(self.h, buf.ctypes.data, buf.nbytes, capi.PIC_MEM_HOST)
+        return buf
+
+    def load_state(self, buf) -> None:
+        """Resume from a state() of a simulation with the same configuration
+        and species."""
+        b = np.ascontiguousarray(buf, dtype=np.uint8)
+        capi.pic_state_load(self.h, b.ctypes.data, b.nbytes, capi.PIC_MEM_HOST)
+
+    def save_state(self, path: str) -> None:
+        with open(path, "wb") as f:
+            f.write(self.state().tobytes())
+
+    def resume(self, path: str) -> None:
+        self.load_state(np.fromfile(path, dtype=np.uint8))
+
     # -- output manager (reduced-dimension / sub-domain frames in a time window)
     def output_add(self, kind: str, which, lo, hi, first: int, last: int, every: int = 1, max_frames: int = 1,
                    max_particles: int = 1) -> int:
