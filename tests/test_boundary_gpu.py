@@ -86,11 +86,17 @@ def test_laser_slab_fp64(dims):
     assert np.abs(s.particles(0)["ux"]).max() > 1e-3
 
 
-def test_laser_slab_fp32():
-    wl = _laser_slab(2, 96, 24)
+@pytest.mark.parametrize("dims,order", [(2, 2), (2, 1), (3, 2), (3, 1)])
+def test_laser_slab_fp32(dims, order):
+    if dims == 2:
+        wl = _laser_slab(2, 96, 24, order=order)
+        before = 50
+    else:
+        wl = _laser_slab(3, 64, 16, 8, slab=(10, 16), order=order)
+        before = 20
     o, s, _ = _pair(wl, "fp32")
-    o.step(50)
-    s.step(50)
+    o.step(before)
+    s.step(before)
     o.step(10)
     s.step(10)
     fe = compare_fields(o, s, ["Ex", "Ey", "Ez", "Bx", "By", "Bz"])
