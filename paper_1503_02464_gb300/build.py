@@ -3,6 +3,13 @@
 Each .cu file is compiled to an object in parallel, then linked into
 ``paper_1503_02464_gb300/_build/libpic.so``.  Objects are rebuilt when their
 source or any header changed.  No GPU is needed to build.
+
+``build(checked=True)`` makes ``_build/libpic_checked.so``: the same code
+with every shared-memory window index, sort slot and capture slot checked
+on the device (``PIC_CHECKED``).  A failed check skips the access and sets
+an error bit that the next synchronising call reports, in place of a
+memory checker, which this toolchain's GPUs do not offer.  Select it with
+``PIC_LIBRARY=checked`` in the environment.
 """
 from __future__ import annotations
 
@@ -18,6 +25,7 @@ CSRC = os.path.join(PKG, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 OUT_DIR = os.path.join(PKG, "_build")
 LIB = os.path.join(OUT_DIR, "libpic.so")
+LIB_CHECKED = os.path.join(OUT_DIR, "libpic_checked.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr",
               "-I", INCLUDE, "-I", CSRC]
@@ -43,15 +51,17 @@ def _compile(src: str, obj: str, extra: list[str]) -> None:
         raise RuntimeError(f"nvcc failed for {os.path.basename(src)}:\n{r.stdout}\n{r.stderr}")
 
 
-def build(force: bool = False, verbose: bool = False, extra: list[str] | None = None) -> str:
-    os.makedirs(OUT_DIR, exist_ok=True)
-    extra = list(extra or [])
+def build(force: bool = False, verbose: bool = False, extra: list[str] | None = None, checked: bool = False) -> str:
+    obj_dir = os.path.join(OUT_DIR, "checked") if checked else OUT_DIR
+    lib = LIB_CHECKED if checked else LIB
+    os.makedirs(obj_dir, exist_ok=True)
+    extra = list(extra or []) + (["-DPIC_CHECKED"] if checked else [])
     srcs = sorted(glob.glob(os.path.join(CSRC, "*.cu")))
     hm = _headers_mtime()
     jobs = []
     objs = []
     for s in srcs:
-        o = os.path.join(OUT_DIR, os.path.basename(s)[:-3] + ".o")
+        o = os.path.join(obj_dir, os.path.basename(s)[:-3] + ".o")
         objs.append(o)
         if force or not os.path.exists(o) or os.path.getmtime(o) < max(os.path.getmtime(s), hm):
             jobs.append((s, o))
@@ -60,18 +70,18 @@ def build(force: bool = False, verbose: bool = False, extra: list[str] | None = 
             futs = [ex.submit(_compile, s, o, extra) for s, o in jobs]
             for f in futs:
                 f.result()
-    if force or jobs or not os.path.exists(LIB) or os.path.getmtime(LIB) < max(os.path.getmtime(o) for o in objs):
-        tmp = LIB + f".tmp{os.getpid()}"
-        cmd = [nvcc()] + ARCH + ["-shared", "-o", tmp] + objs + ["-lcudart_static" if False else "-cudart=static"]
+    if force or jobs or not os.path.exists(lib) or os.path.getmtime(lib) < max(os.path.getmtime(o) for o in objs):
+        tmp = lib + f".tmp{os.getpid()}"
+        cmd = [nvcc()] + ARCH + ["-shared", "-o", tmp] + objs + ["-cudart=static"]
         r = subprocess.run(cmd, capture_output=True, text=True)
         if r.returncode != 0:
             raise RuntimeError(f"link failed:\n{r.stdout}\n{r.stderr}")
-        os.replace(tmp, LIB)
+        os.replace(tmp, lib)
     if verbose:
-        print(LIB)
-    return LIB
+        print(lib)
+    return lib
 
 
 if __name__ == "__main__":
     import sys
-    build(force="--force" in sys.argv, verbose=True)
+    build(force="--force" in sys.argv, verbose=True, checked="--checked" in sys.argv)

@@ -81,7 +81,10 @@ _lib: Optional[ctypes.CDLL] = None
 
 
 def library_path() -> str:
-    return os.path.join(os.path.dirname(os.path.abspath(__file__)), "_build", "libpic.so")
+    """The release library, or with PIC_LIBRARY=checked the build whose
+    kernels check every window and slot index (build.py)."""
+    name = "libpic_checked.so" if os.environ.get("PIC_LIBRARY") == "checked" else "libpic.so"
+    return os.path.join(os.path.dirname(os.path.abspath(__file__)), "_build", name)
 
 
 def load(build_if_missing: bool = True) -> ctypes.CDLL:
@@ -94,7 +97,7 @@ def load(build_if_missing: bool = True) -> ctypes.CDLL:
         if not build_if_missing:
             raise RuntimeError(f"libpic.so not built ({path}); run paper_1503_02464_gb300/build.py")
         from . import build as _build
-        _build.build()
+        _build.build(checked=os.environ.get("PIC_LIBRARY") == "checked")
     lib = ctypes.CDLL(path)
     vp, dp, i64 = ctypes.c_void_p, ctypes.POINTER(ctypes.c_double), ctypes.c_int64
     hp = ctypes.c_void_p

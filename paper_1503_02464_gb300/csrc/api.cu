@@ -214,6 +214,7 @@ int check_device_errors(pic_handle *h) {
   Counters c;
   CK(h, cudaMemcpyAsync(&c, h->ctr, sizeof(Counters), cudaMemcpyDeviceToHost, h->st), "read counters");
   CK(h, cudaStreamSynchronize(h->st), "stream sync");
+  if (c.error & pic::kErrBounds) return fail(h, PIC_EOVERFLOW, "an index outside its buffer was caught (checked build)");
   if (c.error) return fail(h, PIC_EOVERFLOW, "device-side error flags set");
   return PIC_OK;
 }
@@ -232,7 +233,7 @@ int sort_species(pic_handle *h, Species &s) {
   Timed tm(h, pic::KC_SORT);
   CK(h,
      pic::launch_sort(h->g, s.buf[s.cur], s.buf[1 - s.cur], s.d_count, s.slots, h->keys, s.rank, s.tile_start,
-                      h->tile_tmp, s.work, h->st, &nl),
+                      h->tile_tmp, s.work, h->ctr, h->st, &nl),
      "sort");
   h->launches += nl;
   s.cur = 1 - s.cur;
@@ -248,7 +249,7 @@ int compute_rho(pic_handle *h, double *rho) {
     if (s.need_sort)  // slots not grouped by tile yet (just loaded)
       CK(h, pic::launch_rho(h->g, s.buf[s.cur], s.d_count, s.slots, s.q, rho, h->st), "rho deposit");
     else
-      CK(h, pic::launch_rho_tiled(h->g, s.buf[s.cur], s.tile_start, s.q, rho, h->st), "rho deposit");
+      CK(h, pic::launch_rho_tiled(h->g, s.buf[s.cur], s.tile_start, s.q, rho, h->ctr, h->st), "rho deposit");
     h->launches++;
   }
   return PIC_OK;
@@ -682,7 +683,7 @@ int pic_neutralize(pic_handle *h) {
     if (s.need_sort)
       CK(h, pic::launch_rho(h->g, s.buf[s.cur], s.d_count, s.slots, -s.q, h->rho_bg, h->st), "rho deposit");
     else
-      CK(h, pic::launch_rho_tiled(h->g, s.buf[s.cur], s.tile_start, -s.q, h->rho_bg, h->st), "rho deposit");
+      CK(h, pic::launch_rho_tiled(h->g, s.buf[s.cur], s.tile_start, -s.q, h->rho_bg, h->ctr, h->st), "rho deposit");
     h->launches++;
   }
   CK(h, cudaStreamSynchronize(h->st), "sync");
@@ -1201,6 +1202,7 @@ int pic_diag(pic_handle *h, pic_diag_t *out) {
   out->n_clamped = (int64_t)c.clamped;
   out->n_absorbed = (int64_t)c.absorbed;
   out->step = h->step;
+  if (c.error & pic::kErrBounds) return fail(h, PIC_EOVERFLOW, "an index outside its buffer was caught (checked build)");
   if (c.error) return fail(h, PIC_EOVERFLOW, "device-side error flags set");
   if (red[5] > 0 || red[10] > 0) return fail(h, PIC_ENAN, "non-finite field or momentum values");
   return PIC_OK;

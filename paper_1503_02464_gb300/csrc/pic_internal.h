@@ -75,6 +75,18 @@ struct Counters {
   unsigned long long error;     // bit flags of device-side errors
 };
 
+// Device-side error bits of Counters::error.
+constexpr unsigned long long kErrBounds = 2ull;  // an index outside its buffer (checked builds)
+
+// Index checks of the checked build (PIC_CHECKED): a failed check sets
+// kErrBounds in *ctr and evaluates to false, so the caller skips the access;
+// release builds compile the check away (always true).
+#ifdef PIC_CHECKED
+#define PIC_CHECK(cond, ctr) ((cond) || (atomicOr(&(ctr)->error, ::pic::kErrBounds), false))
+#else
+#define PIC_CHECK(cond, ctr) true
+#endif
+
 // Error text reported by pic_last_error(NULL) (entry points without a handle).
 void set_global_error(const std::string &msg);
 
@@ -115,7 +127,7 @@ cudaError_t launch_push(const Grid &g, void *const E[3], void *const B[3], void 
 // Diagnostics charge density of particles sorted by tile (exact 64-bit
 // fixed-point window sums; adds into rho).
 cudaError_t launch_rho_tiled(const Grid &g, const Particles &p, const int64_t *tile_start, double q, double *rho,
-                             cudaStream_t st);
+                             Counters *ctr, cudaStream_t st);
 
 // ---- sort (sort.cu) ----
 // Counting sort of the slots [0, *d_count) of `src` by (tile, cell-in-tile),
@@ -125,7 +137,7 @@ cudaError_t launch_rho_tiled(const Grid &g, const Particles &p, const int64_t *t
 
 cudaError_t launch_sort(const Grid &g, const Particles &src, const Particles &dst, int64_t *d_count,
                         int64_t capacity, int32_t *keys, int32_t *rank, int64_t *tile_start, int64_t *tile_tmp,
-                        const WorkSplit &ws, cudaStream_t st, int *nlaunch);
+                        const WorkSplit &ws, Counters *ctr, cudaStream_t st, int *nlaunch);
 
 // ---- fields and particle conversion (fields.cu) ----
 cudaError_t launch_yee_b(const Grid &g, void *const E[3], void *const B[3], double h, cudaStream_t st);

@@ -507,7 +507,7 @@ __global__ void __launch_bounds__(kThreads, sizeof(R) == 4 ? 2 : 1) k_push(const
           const unsigned long long slot = atomicAdd(a.esc_count, 1ull);
           a.esc_list[slot] = (int32_t)(c0 + e);
           my_q1 += fabsf((float)sW[e]);  // its new |u| is not known here: bound by 1
-        } else {
+        } else do {  // (a single pass: the checked build leaves it early on a bad index)
           R f[3], u[3];
 #pragma unroll
           for (int d = 0; d < 3; ++d) {
@@ -520,6 +520,22 @@ __global__ void __launch_bounds__(kThreads, sizeof(R) == 4 ? 2 : 1) k_push(const
           gy.set(f[1], a.ec);
           gz.set(f[2], a.ec);
           constexpr int oE = G::D + G::LOE;
+#ifdef PIC_CHECKED
+          {
+            // every gather stencil inside the E/B window, every deposit
+            // stencil inside the J window (checked builds)
+            const GatherAxis<R, ORDER> *ga[3] = {&gx, &gy, &gz};
+            constexpr int EW[3] = {G::EX, G::EY, G::EZ};
+            bool ok = true;
+#pragma unroll
+            for (int d = 0; d < DIM; ++d) {
+              const int lo = l[d] + (ga[d]->relp < ga[d]->reld ? ga[d]->relp : ga[d]->reld) + oE;
+              const int hi = l[d] + (ga[d]->relp > ga[d]->reld ? ga[d]->relp : ga[d]->reld) + oE + NS - 1;
+              ok = ok && lo >= 0 && hi < EW[d];
+            }
+            if (!PIC_CHECK(ok, a.ctr)) break;  // leaves the particle as it was
+          }
+#endif
           const int xp = l[0] + gx.relp + oE, xd = l[0] + gx.reld + oE;
           const int yp = (l[1] + gy.relp + oE) * G::EX, yd = (l[1] + gy.reld + oE) * G::EX;
           const int zp = DIM == 3 ? (l[2] + gz.relp + oE) * G::EX * G::EY : 0;
@@ -548,6 +564,16 @@ __global__ void __launch_bounds__(kThreads, sizeof(R) == 4 ? 2 : 1) k_push(const
           else dz.zero();
           const R wq = sW[e];
           constexpr int oJ = G::D + G::LOJ;
+#ifdef PIC_CHECKED
+          {
+            const int rel[3] = {dx.rel, dy.rel, dz.rel};
+            constexpr int JW[3] = {G::JX, G::JY, G::JZ};
+            bool ok = true;
+#pragma unroll
+            for (int d = 0; d < DIM; ++d) ok = ok && l[d] + rel[d] + oJ >= 0 && l[d] + rel[d] + oJ + G::NW - 1 < JW[d];
+            if (!PIC_CHECK(ok, a.ctr)) break;  // leaves the particle as it was
+          }
+#endif
           const int jb = (l[0] + dx.rel + oJ) + (l[1] + dy.rel + oJ) * G::JX +
                          (DIM == 3 ? (l[2] + dz.rel + oJ) * G::JX * G::JY : 0);
           const R ws = wq * acc.scale;  // fixed-point units folded into the factors
@@ -581,7 +607,7 @@ __global__ void __launch_bounds__(kThreads, sizeof(R) == 4 ? 2 : 1) k_push(const
 #pragma unroll
           for (int d = 0; d < 3; ++d) sU[d * kThreads + e] = u[d];
           }
-        }
+        } while (0);
       }
     }
     __syncthreads();
@@ -822,7 +848,8 @@ template <class R, int DIM, int ORDER>
 __global__ void __launch_bounds__(kThreads)
     k_rho_tile(int n0, int n1, int n2, int ntile0, int ntile1, FastDiv dn0, FastDiv dn1, const int32_t *__restrict__ cell,
                const R *__restrict__ off0, const R *__restrict__ off1, const R *__restrict__ off2,
-               const R *__restrict__ w, const int64_t *__restrict__ tile_start, double q, double *rho) {
+               const R *__restrict__ w, const int64_t *__restrict__ tile_start, double q, double *rho,
+               Counters *ctr) {
   using G = Geo<DIM, ORDER>;
   constexpr int NS = ORDER + 1;
   constexpr int RX = G::EX, RY = G::EY, RZ = G::EZ;  // window: cell-1 .. cell+2 around the tile (+ drift)
@@ -904,6 +931,7 @@ __global__ void __launch_bounds__(kThreads)
             const int ix = l[0] + base[0] + kx + G::D + G::LOE;
             const int iy = l[1] + base[1] + ky + G::D + G::LOE;
             const int iz = DIM == 3 ? l[2] + base[2] + kz + G::D + G::LOE : 0;
+            if (!PIC_CHECK(ix >= 0 && ix < RX && iy >= 0 && iy < RY && iz >= 0 && iz < RZ, ctr)) continue;
             long long X;
             if (kFma)
               X = __double_as_longlong(fma(qwx[kx], wyz, kMagic)) - __double_as_longlong(kMagic);
@@ -934,7 +962,7 @@ __global__ void __launch_bounds__(kThreads)
 }  // namespace
 
 cudaError_t launch_rho_tiled(const Grid &g, const Particles &p, const int64_t *tile_start, double q, double *rho,
-                             cudaStream_t st) {
+                             Counters *ctr, cudaStream_t st) {
   if (g.ntiles > 0x7fffffff) return cudaErrorInvalidValue;
   const FastDiv d0 = make_fastdiv((uint32_t)g.n[0]), d1 = make_fastdiv((uint32_t)g.n[1]);
   const unsigned nb = (unsigned)g.ntiles;
@@ -943,7 +971,7 @@ cudaError_t launch_rho_tiled(const Grid &g, const Particles &p, const int64_t *t
     k_rho_tile<R, D, O><<<nb, kThreads, 0, st>>>(g.n[0], g.n[1], g.n[2], g.ntile[0], g.ntile[1], d0, d1, p.cell, \
                                                   static_cast<const R *>(p.off[0]), static_cast<const R *>(p.off[1]), \
                                                   static_cast<const R *>(p.off[2]), static_cast<const R *>(p.w),  \
-                                                  tile_start, q, rho);                                           \
+                                                  tile_start, q, rho, ctr);                                      \
     break;
   switch ((g.prec == 1 ? 100 : 0) + g.dims * 10 + g.order) {
     PIC_RHO_CASE(21, float, 2, 1)

@@ -159,21 +159,25 @@ __global__ void k_work_items(const int64_t *__restrict__ tile_start, int64_t nti
 
 __global__ void k_permute(KeyMap km, const int32_t *__restrict__ cell, const int64_t *__restrict__ n_src,
                           const int32_t *__restrict__ count, const int32_t *__restrict__ rank,
-                          int32_t *__restrict__ dst_cell) {
+                          int32_t *__restrict__ dst_cell, int64_t capacity, Counters *ctr) {
   const int64_t n = *n_src;
   for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < n; p += (int64_t)gridDim.x * blockDim.x) {
     const int r = rank[p];
     if (r < 0) continue;
-    dst_cell[(int64_t)count[km.key(cell[p])] + r] = (int32_t)p;  // slots stay below 2^31
+    const int64_t q = (int64_t)count[km.key(cell[p])] + r;
+    if (!PIC_CHECK(q >= 0 && q < capacity, ctr)) continue;
+    dst_cell[q] = (int32_t)p;  // slots stay below 2^31
   }
 }
 
 template <class R>
-__global__ void k_gather(int dims, Particles src, Particles dst, const int64_t *__restrict__ n_dst) {
+__global__ void k_gather(int dims, Particles src, Particles dst, const int64_t *__restrict__ n_dst,
+                         const int64_t *__restrict__ n_src, Counters *ctr) {
   const int64_t n = *n_dst;
   for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < n; q += (int64_t)gridDim.x * blockDim.x) {
     const int p = dst.cell[q];
     if (p < 0) continue;  // tile padding: stays a dead slot
+    if (!PIC_CHECK(p < *n_src, ctr)) continue;
     dst.cell[q] = src.cell[p];
     dst.id[q] = src.id[p];
     static_cast<R *>(dst.w)[q] = static_cast<const R *>(src.w)[p];
@@ -188,7 +192,7 @@ __global__ void k_gather(int dims, Particles src, Particles dst, const int64_t *
 
 cudaError_t launch_sort(const Grid &g, const Particles &src, const Particles &dst, int64_t *d_count,
                         int64_t capacity, int32_t *keys, int32_t *rank, int64_t *tile_start, int64_t *tile_tmp,
-                        const WorkSplit &ws, cudaStream_t st, int *nlaunch) {
+                        const WorkSplit &ws, Counters *ctr, cudaStream_t st, int *nlaunch) {
   KeyMap km;
   km.n0 = g.n[0];
   km.n1 = g.n[1];
@@ -215,11 +219,11 @@ cudaError_t launch_sort(const Grid &g, const Particles &src, const Particles &ds
   if (e != cudaSuccess) return e;
   k_scan_tiles<<<1, 1024, 0, st>>>(tile_tmp, g.ntiles, tile_start, d_count);
   k_offsets<<<wb, 256, 0, st>>>(keys, g.ntiles, km.tc, tile_start, dst.cell);
-  k_permute<<<nb, 256, 0, st>>>(km, src.cell, tile_tmp + g.ntiles, keys, rank, dst.cell);
+  k_permute<<<nb, 256, 0, st>>>(km, src.cell, tile_tmp + g.ntiles, keys, rank, dst.cell, capacity, ctr);
   if (g.prec == 1)
-    k_gather<double><<<nb, 256, 0, st>>>(g.dims, src, dst, d_count);
+    k_gather<double><<<nb, 256, 0, st>>>(g.dims, src, dst, d_count, tile_tmp + g.ntiles, ctr);
   else
-    k_gather<float><<<nb, 256, 0, st>>>(g.dims, src, dst, d_count);
+    k_gather<float><<<nb, 256, 0, st>>>(g.dims, src, dst, d_count, tile_tmp + g.ntiles, ctr);
   e = cudaMemsetAsync(ws.work_tile, 0xff, sizeof(int32_t) * (size_t)ws.nwork, st);  // -1: no work
   if (e != cudaSuccess) return e;
   k_work_items<<<1, 1024, 0, st>>>(tile_start, g.ntiles, ws.chunk, ws.work_tile, ws.work_pb);
