@@ -198,7 +198,10 @@ def _barrier(world):
         dist.barrier()
 
 
-def generate(wl, isp, nproc):
+def generate(wl, isp, nproc, world=1):
+    """Host inputs of one species; with N replicas on one host the
+    generator processes are shared out between the ranks."""
+    nproc = nproc or max(1, min(16, (os.cpu_count() or 1) // max(world, 1)))
     return synth.SharedParticles(wl, isp, nproc=nproc)
 
 
@@ -226,7 +229,7 @@ def run_gpu(args, rank: int, world: int, local: int):
             print("bench: e2e leg skipped (inputs of this size are generated piece by piece)", file=sys.stderr)
             args.no_e2e = True
     else:
-        host = [generate(wl, isp, args.nproc) for isp in range(len(wl.species))]
+        host = [generate(wl, isp, args.nproc, world) for isp in range(len(wl.species))]
     t_gen = time.perf_counter() - t_gen
 
     torch.cuda.set_device(local)

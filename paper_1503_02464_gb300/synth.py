@@ -282,6 +282,21 @@ def _fill_chunk(args):
     return c1 - c0
 
 
+def _scratch_dir(nbytes: int):
+    """A directory with room for nbytes of scratch files: the temporary
+    directory, else /dev/shm; None (the default) when neither has room."""
+    import os
+    import shutil
+    import tempfile
+    for d in (tempfile.gettempdir(), "/dev/shm"):
+        try:
+            if os.path.isdir(d) and shutil.disk_usage(d).free > 1.2 * nbytes:
+                return d
+        except OSError:
+            continue
+    return None
+
+
 class SharedParticles:
     """Particle arrays of one species in memory-mapped temporary files, filled
     by a pool of worker processes (spawned, so it is safe after CUDA has
@@ -300,7 +315,7 @@ class SharedParticles:
         ncells = int(wl.species_cells(sp).size)
         c0, c1 = (0, ncells) if cell_range is None else (int(cell_range[0]), int(min(cell_range[1], ncells)))
         self.n = max(c1 - c0, 0) * sp.ppc
-        self._dir = tempfile.mkdtemp(prefix="picsynth_")
+        self._dir = tempfile.mkdtemp(prefix="picsynth_", dir=_scratch_dir(self.n * 60))
         self.paths = [os.path.join(self._dir, key + ".bin") for key, _ in _FIELDS]
         for (key, dt), path in zip(_FIELDS, self.paths):
             with open(path, "wb") as f:
