@@ -430,7 +430,9 @@ def run_gpu(args, rank: int, world: int, local: int):
     value = aggregate_rate(world, npart, args.steps, r["dt"])
     peak, peak_kind = _peaks()
     push_avg_s = push_ms / max(push_n, 1) / 1e3
-    alg_bytes = npart * PUSH_BYTES_PER_PARTICLE[args.precision] + ncell * PUSH_BYTES_PER_CELL[args.precision]
+    # one push launch moves one species (equal sizes here) and its windows of every tile
+    alg_bytes = (npart // max(len(wl.species), 1)) * PUSH_BYTES_PER_PARTICLE[args.precision] + \
+        ncell * PUSH_BYTES_PER_CELL[args.precision]
     achieved = alg_bytes / push_avg_s / 1e9
     tim_out = {k: {"ms_total": v[0], "launches": v[1]} for k, v in r["tim"].items() if v[1]}
     line = {
@@ -447,7 +449,8 @@ def run_gpu(args, rank: int, world: int, local: int):
                    "l2": "inputs larger than L2 (particle arrays > 4 GB, fields 0.6 GB)",
                    "parallelism": "replicas" if world > 1 else "single GPU"},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-                     "traffic": (PUSH_TRAFFIC_PER_PARTICLE.get((wl.name, args.precision)) or 0) * npart or None,
+                     "traffic": (PUSH_TRAFFIC_PER_PARTICLE.get((wl.name, args.precision)) or 0) *
+                                (npart // max(len(wl.species), 1)) or None,
                      "kernel": "k_push (fused gather/Boris/move/Esirkepov)",
                      "peak_kind": f"{peak_kind} HBM copy bandwidth",
                      "bytes_per_launch": alg_bytes, "ms_per_launch": push_avg_s * 1e3},
