@@ -13,6 +13,10 @@ draws, so any subset of cells can be regenerated on its own (this is what
 the sampled full-size parity tests rely on).  Draws -> uniforms in (0, 1)
 with 53 random bits; normals by the Box-Muller transform.
 
+In the laser-target presets electrons and protons share their draws (the
+same seed), so they start at the same positions: the target is neutral
+node by node and E = 0 satisfies Gauss's law at t = 0.
+
 Workload recipe (section 2 of the paper states the model; the sizes below are
 the synthetic stand-ins for its laser-plasma and thermal-plasma runs and for
 the two-stream test problem of its scaling study, §4.1):
@@ -212,7 +216,7 @@ def _preset(name: str) -> Workload:
         dt = 0.9 * courant_limit((d, d), 2)
         return Workload(name, 2, (2048, 1024, 1), (d, d, 1.0), dt, 2, 2000, 1002,
                         [Species("electron", -1.0, 1.0, 64, 0.0, 40.0, (1024, 1064), 0),
-                         Species("proton", 1.0, 1836.0, 64, 0.0, 40.0, (1024, 1064), 1)],
+                         Species("proton", 1.0, 1836.0, 64, 0.0, 40.0, (1024, 1064), 0)],
                         absorbing_x=True, neutralize=False,
                         laser={"a0": 3.0, "waist": 3 * lam, "duration": 10 * lam, "pol": 1})
     if name == "laser_foil3d":
@@ -220,7 +224,7 @@ def _preset(name: str) -> Workload:
         dt = 0.9 * courant_limit((d, d, d), 3)
         return Workload(name, 3, (512, 256, 256), (d, d, d), dt, 2, 1000, 1004,
                         [Species("electron", -1.0, 1.0, 27, 0.0, 50.0, (256, 276), 0),
-                         Species("proton", 1.0, 1836.0, 27, 0.0, 50.0, (256, 276), 1)],
+                         Species("proton", 1.0, 1836.0, 27, 0.0, 50.0, (256, 276), 0)],
                         absorbing_x=True, neutralize=False,
                         laser={"a0": 10.0, "waist": 2 * lam, "duration": 8 * lam, "pol": 1})
     if name == "twostream3d_512":
