@@ -102,7 +102,9 @@ typedef struct {
   int precision;       /* PIC_FP32 or PIC_FP64                                 */
   int bc_lo[3];        /* PIC_BC_* per axis; only x may be absorbing           */
   int bc_hi[3];
-  int sort_every;      /* steps between particle sorts (0 = 20)                */
+  int sort_every;      /* steps between particle sorts (0 = 20); a species is also
+                          sorted early when its last push sent more than 0.5 %
+                          of its particles down the escape path               */
   int tile[3];         /* cell-tile shape of the push kernel (0 = default)     */
   int drift_guard;     /* cells a particle may stray from its tile between sorts
                           and still use the tile's shared-memory window (0 = 1) */
@@ -143,6 +145,9 @@ typedef struct {
   int64_t n_escaped;      /* particle-steps that left their tile window (slow path)*/
   int64_t n_clamped;      /* FP32 offsets clamped below 1 after a cell carry      */
   int64_t n_absorbed;     /* particles removed at absorbing walls                 */
+  int64_t n_sorts_adaptive; /* sorts made ahead of the sort_every cadence because
+                             a push sent more than 0.5 % of a species (at least
+                             1024 particles) down the escape path              */
   int64_t step;           /* completed time steps                                 */
 } pic_diag_t;
 

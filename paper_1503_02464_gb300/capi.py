@@ -57,7 +57,8 @@ class pic_diag_t(ctypes.Structure):
     _fields_ = [("energy_field", ctypes.c_double), ("energy_e", ctypes.c_double), ("energy_b", ctypes.c_double),
                 ("energy_kinetic", ctypes.c_double), ("charge", ctypes.c_double), ("gauss_max", ctypes.c_double),
                 ("continuity_max", ctypes.c_double), ("n_alive", ctypes.c_int64), ("n_escaped", ctypes.c_int64),
-                ("n_clamped", ctypes.c_int64), ("n_absorbed", ctypes.c_int64), ("step", ctypes.c_int64)]
+                ("n_clamped", ctypes.c_int64), ("n_absorbed", ctypes.c_int64), ("n_sorts_adaptive", ctypes.c_int64),
+                ("step", ctypes.c_int64)]
 
     def as_dict(self) -> dict:
         return {k: getattr(self, k) for k, _ in self._fields_}

@@ -37,6 +37,10 @@ struct Species {
   int64_t *tile_start = nullptr;
   pic::WorkSplit work;          // push work items (tile pieces of at most work.chunk slots)
   float *tq = nullptr;          // per-item deposit bound carried between pushes
+  // escapes of the last push, read back without blocking (adaptive sort)
+  unsigned long long *esc_host = nullptr;  // page-locked
+  cudaEvent_t esc_ev = nullptr;
+  bool esc_pending = false;
   bool fresh = true;            // sorted since the last push
   bool need_sort = true;
 };
@@ -103,6 +107,7 @@ struct pic_handle {
   int nsp = 0;
   int64_t step = 0;
   int64_t launches = 0;
+  int64_t adaptive_sorts = 0;  // sorts triggered by escapes rather than by the cadence
   std::string err;
   bool profiling = false;
   std::vector<TimerRec> timers;
@@ -529,6 +534,8 @@ int pic_destroy(pic_handle *h) {
     cudaFree(s.tq);
     cudaFree(s.work.work_tile);
     cudaFree(s.work.work_pb);
+    cudaFreeHost(s.esc_host);
+    if (s.esc_ev) cudaEventDestroy(s.esc_ev);
   }
   for (auto &o : h->outputs) {
     cudaFree(o.buf);
@@ -577,6 +584,8 @@ int pic_add_species(pic_handle *h, double q, double m, int64_t capacity, int *sp
     s.work.nwork = s.slots / s.work.chunk + 1 + h->g.ntiles;
   }
   if (e == cudaSuccess) e = cudaMalloc(&s.tq, (size_t)2 * s.work.nwork * sizeof(float));
+  if (e == cudaSuccess) e = cudaMallocHost(&s.esc_host, sizeof(unsigned long long));
+  if (e == cudaSuccess) e = cudaEventCreateWithFlags(&s.esc_ev, cudaEventDisableTiming);
   if (e == cudaSuccess) e = cudaMalloc(&s.work.work_tile, (size_t)s.work.nwork * sizeof(int32_t));
   if (e == cudaSuccess) e = cudaMalloc(&s.work.work_pb, (size_t)s.work.nwork * sizeof(int64_t));
   if (e != cudaSuccess) {
@@ -588,6 +597,8 @@ int pic_add_species(pic_handle *h, double q, double m, int64_t capacity, int *sp
     cudaFree(s.tq);
     cudaFree(s.work.work_tile);
     cudaFree(s.work.work_pb);
+    cudaFreeHost(s.esc_host);
+    if (s.esc_ev) cudaEventDestroy(s.esc_ev);
     s = Species{};
     cudaGetLastError();
     return fail(h, PIC_ENOMEM, "device allocation failed in pic_add_species");
@@ -1005,7 +1016,23 @@ int pic_step(pic_handle *h, int nsteps) {
     } step_range;
     for (int i = 0; i < h->nsp; ++i) {
       Species &s = h->sp[i];
-      if (s.need_sort || h->step % every == 0) {
+      // Sort on the cadence, or early when the last push sent more than
+      // 0.5 % of the particles down the escape path (they drifted beyond
+      // their tile's guard cells).  The escape count is read without
+      // blocking: a push whose count has not arrived yet does not trigger.
+      bool many_escapes = false;
+      if (s.esc_pending) {
+        const cudaError_t q = cudaEventQuery(s.esc_ev);
+        if (q == cudaSuccess) {
+          s.esc_pending = false;
+          const unsigned long long lim = (unsigned long long)(s.h_count / 200 > 1024 ? s.h_count / 200 : 1024);
+          many_escapes = *s.esc_host > lim;
+        } else {
+          cudaGetLastError();  // not ready: not an error
+        }
+      }
+      if (s.need_sort || h->step % every == 0 || many_escapes) {
+        if (many_escapes) h->adaptive_sorts++;
         int r = sort_species(h, s);
         if (r) return r;
       }
@@ -1031,6 +1058,12 @@ int pic_step(pic_handle *h, int nsteps) {
          "push");
       s.fresh = false;
       h->launches += nl;
+      if (s.esc_host && !s.esc_pending) {
+        CK(h, cudaMemcpyAsync(s.esc_host, h->esc_count, sizeof(unsigned long long), cudaMemcpyDeviceToHost, h->st),
+           "escape count");
+        CK(h, cudaEventRecord(s.esc_ev, h->st), "escape event");
+        s.esc_pending = true;
+      }
     }
     if (h->cfg.filter_passes > 0) {
       Timed tm(h, pic::KC_FILTER);
@@ -1201,6 +1234,7 @@ int pic_diag(pic_handle *h, pic_diag_t *out) {
   out->n_escaped = (int64_t)c.escaped;
   out->n_clamped = (int64_t)c.clamped;
   out->n_absorbed = (int64_t)c.absorbed;
+  out->n_sorts_adaptive = h->adaptive_sorts;
   out->step = h->step;
   if (c.error & pic::kErrBounds) return fail(h, PIC_EOVERFLOW, "an index outside its buffer was caught (checked build)");
   if (c.error) return fail(h, PIC_EOVERFLOW, "device-side error flags set");

@@ -192,3 +192,28 @@ def test_energy_readback_matches_diag(precision):
     for k in ("energy_e", "energy_b", "energy_kinetic"):
         assert abs(d[k] - e[k]) <= tol * abs(d[k]), (k, d[k], e[k])
     assert d["n_alive"] == e["n_alive"] and e["step"] == 4
+
+
+def test_adaptive_sort_for_fast_particles():
+    """A relativistic plasma (u_th = 1) drifts out of the tile windows long
+    before a sort_every = 1000 cadence: the library sorts early once a push
+    sends more than 0.5 % of the particles down the escape path, and the run
+    stays at FP64 parity with the oracle throughout."""
+    wl = _wl(3, 2, (16, 16, 8), 4, 1.0, 45)
+    parts = [wl.particles(0)]
+    o = build_oracle(wl, parts)
+    s = build_gpu(wl, parts, "fp64", sort_every=1000)
+    for step in range(1, 31):
+        o.step(1)
+        s.step(1)
+        if step % 10 == 0:
+            s.sync()
+            fe = compare_fields(o, s, ["Ex", "Ey", "Ez", "Bx", "By", "Bz"])
+            for k, v in fe.items():
+                assert v <= 1e-12 * step, (step, k, v)
+            du, _ = compare_particles(o, s, wl, 0)
+            assert du <= 1e-12 * step, (step, du)
+    d = s.diag()
+    assert d["n_sorts_adaptive"] > 0
+    # without the early sorts most particles would take the escape path by now
+    assert d["n_escaped"] < 0.2 * 30 * wl.n_particles()
