@@ -53,7 +53,13 @@ template <int DIM, int ORDER> struct Geo {
   static constexpr int JY = TY + 2 * D + LOJ + HIJ;
   static constexpr int JZ = DIM == 3 ? TZ + 2 * D + LOJ + HIJ : 1;
   static constexpr int EN = EX * EY * EZ;
-  static constexpr int JN = JX * JY * JZ;
+  // J window plane stride.  For 3D TSC it is padded from 15 x 15 = 225 to 231
+  // nodes: the deposit's atomics come from 32 lanes in 32 neighbouring cells,
+  // each offset by its particle's stencil start, and with 231 those addresses
+  // fall on fewer shared banks twice (a count over thermal-plasma tiles: 2.6
+  // -> 2.2 wavefronts per atomic instruction).  The padding nodes stay zero.
+  static constexpr int JP = (DIM == 3 && ORDER == 2) ? JX * JY + 6 : JX * JY;
+  static constexpr int JN = JP * JZ;
   static constexpr int NS = ORDER + 1;  // gather stencil width
   static constexpr int NW = ORDER + 2;  // deposit stencil width
 };
@@ -175,11 +181,13 @@ template <> struct WinAcc<float> {
     const float lf = fmaf(p, q, -r);
     const int hi = __float_as_int(y) - __float_as_int(kMagicHi);
     const int lo = __float_as_int(lf + kMagic) - __float_as_int(kMagic);
-    if (hi | lo) {
-      int *b = w + comp * 2 * jn + idx;
-      atomicAdd(b, lo);
-      atomicAdd(b + jn, hi);
-    }
+    // Both words are added unconditionally: a zero adds nothing, and a
+    // branch around the pair (or a predicate on it) cost more than the
+    // zero adds do.  Warps whose particles all deposit nothing skip the
+    // whole stencil instead (deposit_particle).
+    const unsigned s = (unsigned)__cvta_generic_to_shared(w + comp * 2 * jn + idx);
+    asm volatile("red.shared.add.s32 [%0], %1;\n\tred.shared.add.s32 [%2], %3;" ::"r"(s), "r"(lo),
+                 "r"(s + 4u * (unsigned)jn), "r"(hi));
   }
   __device__ __forceinline__ float get(int comp, int idx) const {
     const int *b = w + comp * 2 * jn + idx;
@@ -313,6 +321,21 @@ __device__ __forceinline__ void deposit_win(const WinAcc<R> &acc, int base, cons
   }
 }
 
+// A deposit job: the particle's cell relative to the tile (l in [-1, 16] on
+// every axis) and its cell shift (s in {-1, 0, 1}), 5 + 2 bits per axis, and
+// bit 30 set so that a job is never 0.
+__device__ __forceinline__ int pack_job(const int l[3], const int s[3]) {
+  return (1 << 30) | (l[0] + 1) | ((l[1] + 1) << 5) | ((l[2] + 1) << 10) | ((s[0] + 1) << 15) |
+         ((s[1] + 1) << 17) | ((s[2] + 1) << 19);
+}
+__device__ __forceinline__ void unpack_job(int j, int l[3], int s[3]) {
+#pragma unroll
+  for (int d = 0; d < 3; ++d) {
+    l[d] = ((j >> (5 * d)) & 31) - 1;
+    s[d] = ((j >> (15 + 2 * d)) & 3) - 1;
+  }
+}
+
 // The per-particle physics shared by the tile kernel and the escape kernel:
 // given gathered E, B, advance u, move, and build the deposit stencils.
 template <class R, int ORDER, int DIM>
@@ -343,6 +366,51 @@ __device__ __forceinline__ void push_move(const PushArgs<R> &a, R u[3], const R 
   }
 }
 
+// Esirkepov deposit of one particle's move into the J window (§2 eq. 4 and
+// the continuity equation): l is its cell relative to the tile, s its cell
+// shift, f -> fn its offsets before and after the move, w its weight, vz its
+// velocity along z (the 2D3V Jz term).  Returns false when the checked build
+// finds the stencil outside the window (nothing deposited).
+template <class R, int DIM, int ORDER>
+__device__ __forceinline__ bool deposit_particle(const PushArgs<R> &a, const WinAcc<R> &acc, const int l[3],
+                                                 const int s[3], const R f[3], const R fn[3], R w, R vz) {
+  using G = Geo<DIM, ORDER>;
+  // A particle that keeps its place (and, in 2D3V, has vz = 0) or has no
+  // weight deposits nothing; a warp of such particles (a cold target before
+  // the pulse reaches it) skips the stencil with a uniform branch.
+  const unsigned act = __activemask();
+  const bool moves = w != R(0) && ((s[0] | s[1] | s[2]) != 0 || f[0] != fn[0] || f[1] != fn[1] ||
+                                   (DIM == 3 ? f[2] != fn[2] : vz != R(0)));
+  if (!__any_sync(act, moves)) return true;
+  DepositAxis<R, ORDER> dx, dy, dz;
+  dx.set(f[0], s[0], fn[0]);
+  dy.set(f[1], s[1], fn[1]);
+  if (DIM == 3) dz.set(f[2], s[2], fn[2]);
+  else dz.zero();
+  constexpr int oJ = G::D + G::LOJ;
+#ifdef PIC_CHECKED
+  {
+    // every deposit stencil inside the J window (checked builds)
+    const int rel[3] = {dx.rel, dy.rel, dz.rel};
+    constexpr int JW[3] = {G::JX, G::JY, G::JZ};
+    bool ok = true;
+#pragma unroll
+    for (int d = 0; d < DIM; ++d) ok = ok && l[d] + rel[d] + oJ >= 0 && l[d] + rel[d] + oJ + G::NW - 1 < JW[d];
+    if (!PIC_CHECK(ok, a.ctr)) return false;
+  }
+#endif
+  const int jb = (l[0] + dx.rel + oJ) + (l[1] + dy.rel + oJ) * G::JX +
+                 (DIM == 3 ? (l[2] + dz.rel + oJ) * G::JP : 0);
+  const R ws = w * acc.scale;  // fixed-point units folded into the factors
+  // does some lane of this warp use the last stencil node of an axis?
+  const bool lx = __any_sync(act, dx.S0[G::NW - 1] != R(0) || dx.DS[G::NW - 1] != R(0));
+  const bool ly = __any_sync(act, dy.S0[G::NW - 1] != R(0) || dy.DS[G::NW - 1] != R(0));
+  const bool lz = DIM == 3 && __any_sync(act, dz.S0[G::NW - 1] != R(0) || dz.DS[G::NW - 1] != R(0));
+  deposit_win<R, ORDER, DIM, G::JX, G::JP>(acc, jb, dx, dy, dz, a.jfac[0] * ws, a.jfac[1] * ws,
+                                                    a.jfac[2] * ws, a.qz * ws * vz, lx, ly, lz);
+  return true;
+}
+
 template <class R, int DIM, int ORDER>
 // Blocks per SM the register allocation is held to: FP32 3D TSC windows
 // fill half the shared memory (two blocks); the 3D CIC windows leave room for
@@ -354,6 +422,7 @@ __global__ void __launch_bounds__(kThreads, sizeof(R) == 4 ? (DIM == 2 ? 4 : (OR
     k_push(const PushArgs<R> a) {
   using G = Geo<DIM, ORDER>;
   constexpr int NS = G::NS;
+  static_assert(G::TX + G::D < 31 && G::TY + G::D < 31 && G::TZ + G::D < 31, "deposit job packing");
   extern __shared__ __align__(16) unsigned char smem_raw[];
   R *sF = reinterpret_cast<R *>(smem_raw);    // 6 * EN: Ex Ey Ez Bx By Bz
   // J window: 24 bytes per node (3 components x 8 bytes of fixed point)
@@ -362,6 +431,8 @@ __global__ void __launch_bounds__(kThreads, sizeof(R) == 4 ? (DIM == 2 ? 4 : (OR
   R *sU = sOff + DIM * kThreads;              // 3 x 256
   R *sW = sU + 3 * kThreads;                  // 256
   int32_t *sCell = reinterpret_cast<int32_t *>(sW + kThreads);  // 256
+  R *sFo = reinterpret_cast<R *>(sCell + kThreads);                 // FP32 3D: 3 x 256 old offsets
+  int32_t *sJob = reinterpret_cast<int32_t *>(sFo + 3 * kThreads);  // FP32 3D: 256 deposit jobs
   __shared__ unsigned int s_clamp;
   __shared__ double s_scale;
   __shared__ unsigned int s_emax[3];
@@ -462,10 +533,22 @@ __global__ void __launch_bounds__(kThreads, sizeof(R) == 4 ? (DIM == 2 ? 4 : (OR
   acc.scale = (R)s_scale;
   acc.unit = (R)(1.0 / s_scale);
 
-  // lane-spreading permutation of the 256 staging slots (bijective; the
-  // eight warps' lanes land on 32 distinct banks)
+  // Slot assignment.  The deposit runs on the lane-spreading permutation e
+  // (bijective; lane l of warp w takes slot 8l + ((w + l/4) mod 8)): the
+  // slots are cell-sorted, so a warp's lanes sit about one cell apart and
+  // their atomics hit different nodes.  In 3D the gather and push run first
+  // on slot tid instead, where a warp's lanes sit in a few neighbouring cells
+  // and mostly read the same field nodes (shared-memory broadcasts instead of
+  // bank conflicts on the 162-node TSC gather); each pushed particle then
+  // leaves a deposit job behind (old offsets in sFo, new ones in sOff, tile
+  // cell and cell shift packed in sJob) for the deposit phase after a block
+  // barrier.  In 2D the gather is a third of that, and FP64 runs are bound by
+  // the FP64 pipe: there the extra barrier and staging traffic cost more than
+  // they save, so one thread pushes and deposits slot e.
+  constexpr bool kSplit = DIM == 3 && sizeof(R) == 4;
   const int lane = tid & 31, warp = tid >> 5;
   const int e = 8 * lane + ((warp + (lane >> 2)) & 7);
+  const int ep = kSplit ? tid : e;  // slot gathered and pushed by this thread
   unsigned my_clamp = 0, my_absorbed = 0;
   float my_q1 = 0.f;
 
@@ -482,8 +565,10 @@ __global__ void __launch_bounds__(kThreads, sizeof(R) == 4 ? (DIM == 2 ? 4 : (OR
       sW[tid] = a.w[p];
     }
     __syncthreads();
-    if (e < cn) {
-      const int c = sCell[e];
+    // ---- gather, Boris, move (and, in 2D, deposit) of slot ep ----
+    if (ep < cn) {
+      int job = 0;
+      const int c = sCell[ep];
       if (c >= 0) {
         // decode the cell and its position relative to the tile
         const uint32_t r0 = a.dn0.div((uint32_t)c);
@@ -510,16 +595,16 @@ __global__ void __launch_bounds__(kThreads, sizeof(R) == 4 ? (DIM == 2 ? 4 : (OR
         }
         if (!inw) {
           // defer to k_push_escaped (state left untouched)
-          sCell[e] = c | kEscFlag;
+          sCell[ep] = c | kEscFlag;
           const unsigned long long slot = atomicAdd(a.esc_count, 1ull);
-          a.esc_list[slot] = (int32_t)(c0 + e);
-          my_q1 += fabsf((float)sW[e]);  // its new |u| is not known here: bound by 1
+          a.esc_list[slot] = (int32_t)(c0 + ep);
+          my_q1 += fabsf((float)sW[ep]);  // its new |u| is not known here: bound by 1
         } else do {  // (a single pass: the checked build leaves it early on a bad index)
           R f[3], u[3];
 #pragma unroll
           for (int d = 0; d < 3; ++d) {
-            f[d] = d < DIM ? sOff[d * kThreads + e] : R(0);
-            u[d] = sU[d * kThreads + e];
+            f[d] = d < DIM ? sOff[d * kThreads + ep] : R(0);
+            u[d] = sU[d * kThreads + ep];
           }
           // ---- gather (§2: g-weighted average of the grid fields) ----
           GatherAxis<R, ORDER> gx, gy, gz;
@@ -529,8 +614,7 @@ __global__ void __launch_bounds__(kThreads, sizeof(R) == 4 ? (DIM == 2 ? 4 : (OR
           constexpr int oE = G::D + G::LOE;
 #ifdef PIC_CHECKED
           {
-            // every gather stencil inside the E/B window, every deposit
-            // stencil inside the J window (checked builds)
+            // every gather stencil inside the E/B window (checked builds)
             const GatherAxis<R, ORDER> *ga[3] = {&gx, &gy, &gz};
             constexpr int EW[3] = {G::EX, G::EY, G::EZ};
             bool ok = true;
@@ -561,45 +645,28 @@ __global__ void __launch_bounds__(kThreads, sizeof(R) == 4 ? (DIM == 2 ? 4 : (OR
           int s[3];
           push_move<R, ORDER, DIM>(a, u, E, B, f, fn, s, ig, my_clamp);
           if (sizeof(R) == 4)
-            my_q1 += fabsf((float)sW[e]) * fminf(1.f, sqrtf((float)(u[0] * u[0] + u[1] * u[1] + u[2] * u[2])));
+            my_q1 += fabsf((float)sW[ep]) * fminf(1.f, sqrtf((float)(u[0] * u[0] + u[1] * u[1] + u[2] * u[2])));
 
-          // ---- Esirkepov deposit (§2 eq. 4 + continuity) ----
-          DepositAxis<R, ORDER> dx, dy, dz;
-          dx.set(f[0], s[0], fn[0]);
-          dy.set(f[1], s[1], fn[1]);
-          if (DIM == 3) dz.set(f[2], s[2], fn[2]);
-          else dz.zero();
-          const R wq = sW[e];
-          constexpr int oJ = G::D + G::LOJ;
-#ifdef PIC_CHECKED
-          {
-            const int rel[3] = {dx.rel, dy.rel, dz.rel};
-            constexpr int JW[3] = {G::JX, G::JY, G::JZ};
-            bool ok = true;
+          if (kSplit) {
+            // the deposit job; the old offsets stay readable in sFo
 #pragma unroll
-            for (int d = 0; d < DIM; ++d) ok = ok && l[d] + rel[d] + oJ >= 0 && l[d] + rel[d] + oJ + G::NW - 1 < JW[d];
-            if (!PIC_CHECK(ok, a.ctr)) break;  // leaves the particle as it was
+            for (int d = 0; d < DIM; ++d) sFo[d * kThreads + ep] = f[d];
+            job = pack_job(l, s);
+          } else if (!deposit_particle<R, DIM, ORDER>(a, acc, l, s, f, fn, sW[ep], u[2] * ig)) {
+            break;  // (checked build) leaves the particle as it was
           }
-#endif
-          const int jb = (l[0] + dx.rel + oJ) + (l[1] + dy.rel + oJ) * G::JX +
-                         (DIM == 3 ? (l[2] + dz.rel + oJ) * G::JX * G::JY : 0);
-          const R ws = wq * acc.scale;  // fixed-point units folded into the factors
-          // does some lane of this warp use the last stencil node of an axis?
-          const unsigned act = __activemask();
-          const bool lx = __any_sync(act, dx.S0[G::NW - 1] != R(0) || dx.DS[G::NW - 1] != R(0));
-          const bool ly = __any_sync(act, dy.S0[G::NW - 1] != R(0) || dy.DS[G::NW - 1] != R(0));
-          const bool lz = DIM == 3 && __any_sync(act, dz.S0[G::NW - 1] != R(0) || dz.DS[G::NW - 1] != R(0));
-          deposit_win<R, ORDER, DIM, G::JX, G::JX * G::JY>(acc, jb, dx, dy, dz, a.jfac[0] * ws, a.jfac[1] * ws,
-                                                            a.jfac[2] * ws, a.qz * ws * u[2] * ig, lx, ly, lz);
 
           // ---- new state back into the staging slot ----
+#pragma unroll
+          for (int d = 0; d < DIM; ++d) sOff[d * kThreads + ep] = fn[d];
+#pragma unroll
+          for (int d = 0; d < 3; ++d) sU[d * kThreads + ep] = u[d];
           if (outside_walls<R>(a.absorb, ci[0] + s[0], fn[0], a.n[0])) {
-            sCell[e] = -1;  // removed at an absorbing wall after depositing its move
+            sCell[ep] = -1;  // removed at an absorbing wall after depositing its move
             ++my_absorbed;
           } else {
-          int nc = c;
-          {
-            int i0 = ci[0] + s[0];
+            int nc = c;
+            const int i0 = ci[0] + s[0];
             nc += s[0] + (i0 < 0 ? a.n[0] : (i0 >= a.n[0] ? -a.n[0] : 0));
             const int i1 = ci[1] + s[1];
             nc += (s[1] + (i1 < 0 ? a.n[1] : (i1 >= a.n[1] ? -a.n[1] : 0))) * a.n[0];
@@ -607,14 +674,28 @@ __global__ void __launch_bounds__(kThreads, sizeof(R) == 4 ? (DIM == 2 ? 4 : (OR
               const int i2 = ci[2] + s[2];
               nc += (s[2] + (i2 < 0 ? a.n[2] : (i2 >= a.n[2] ? -a.n[2] : 0))) * a.n[0] * a.n[1];
             }
-          }
-          sCell[e] = nc;
-#pragma unroll
-          for (int d = 0; d < DIM; ++d) sOff[d * kThreads + e] = fn[d];
-#pragma unroll
-          for (int d = 0; d < 3; ++d) sU[d * kThreads + e] = u[d];
+            sCell[ep] = nc;
           }
         } while (0);
+      }
+      if (kSplit) sJob[ep] = job;
+    }
+    if (kSplit) {
+      __syncthreads();
+      // ---- Esirkepov deposit of slot e (3D) ----
+      if (e < cn) {
+        const int job = sJob[e];
+        if (job) {
+          int l[3], s[3];
+          unpack_job(job, l, s);
+          R f[3], fn[3];
+#pragma unroll
+          for (int d = 0; d < 3; ++d) {
+            f[d] = sFo[d * kThreads + e];
+            fn[d] = sOff[d * kThreads + e];
+          }
+          deposit_particle<R, DIM, ORDER>(a, acc, l, s, f, fn, sW[e], R(0));
+        }
       }
     }
     __syncthreads();
@@ -644,9 +725,10 @@ __global__ void __launch_bounds__(kThreads, sizeof(R) == 4 ? (DIM == 2 ? 4 : (OR
 
   // ---- flush the J window into global J ----
   for (int q = tid; q < G::JN; q += kThreads) {
-    const int x = q % G::JX;
-    const int y = (q / G::JX) % G::JY;
-    const int z = q / (G::JX * G::JY);
+    const int z = q / G::JP;
+    const int x = (q - z * G::JP) % G::JX;
+    const int y = (q - z * G::JP) / G::JX;
+    if (y >= G::JY) continue;  // plane padding
     const int gi = wrap_near(t0[0] - G::D - G::LOJ + x, a.n[0]);
     const int gj = wrap_near(t0[1] - G::D - G::LOJ + y, a.n[1]);
     const int gk = DIM == 3 ? wrap_near(t0[2] - G::D - G::LOJ + z, a.n[2]) : 0;
@@ -785,7 +867,11 @@ __global__ void __launch_bounds__(kThreads) k_push_escaped(const PushArgs<R> a) 
 
 template <class R, int DIM, int ORDER> constexpr size_t smem_bytes() {
   using G = Geo<DIM, ORDER>;
-  return (size_t)(6 * G::EN + (DIM + 4) * kThreads) * sizeof(R) + 24 * (size_t)G::JN + kThreads * sizeof(int32_t);
+  // E, B window; J window; staging of cell, offsets, u, w; for FP32 3D the
+  // deposit jobs (old offsets and a packed int per slot)
+  constexpr bool split = DIM == 3 && sizeof(R) == 4;
+  return (size_t)(6 * G::EN + (DIM + 4 + (split ? 3 : 0)) * kThreads) * sizeof(R) + 24 * (size_t)G::JN +
+         (split ? 2 : 1) * kThreads * sizeof(int32_t);
 }
 
 template <class R, int DIM, int ORDER>
