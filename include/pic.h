@@ -190,16 +190,20 @@ int pic_add_species(pic_handle *h, double q, double m, int64_t capacity, int *sp
  * particle outside the absorbing walls' [3, n[0] - 4) cells, or with a
  * non-finite position, momentum or weight, is stored dead and the call
  * returns PIC_EINVAL after loading the others.  Exceeding capacity:
- * PIC_ENOMEM (nothing loaded).  Host arrays that are page-locked and mapped
- * for the device (e.g. registered with cudaHostRegister) are read in place by
- * the load kernel; other host arrays go through device staging copies. */
+ * PIC_ENOMEM (nothing loaded).  Host arrays are copied in chunks of 4M
+ * particles through two device staging buffers (about 0.5 GB, freed before
+ * the call returns), copy engine and conversion kernel overlapped; page-locked
+ * arrays (cudaHostAlloc, cudaHostRegister) move at the host link's DMA rate.
+ * Synchronises. */
 int pic_load_particles(pic_handle *h, int species, int64_t n, const double *x, const double *y,
                        const double *z, const double *ux, const double *uy, const double *uz,
                        const double *w, const uint32_t *id, int mem_kind);
 
 /* Immobile neutralising background: rho_bg = -rho of the particles loaded so
  * far (so that E = 0 satisfies Gauss's law).  Used by the diagnostics only:
- * an immobile background carries no current. */
+ * an immobile background carries no current.  Species loaded since their
+ * last sort are sorted first, as the next pic_step would do (slot order
+ * changes, dead slots are dropped). */
 int pic_neutralize(pic_handle *h);
 
 /* Set the immobile background charge density at the nodes (i, j, k):

@@ -43,6 +43,7 @@ struct Species {
   bool esc_pending = false;
   bool fresh = true;            // sorted since the last push
   bool need_sort = true;
+  int64_t sorted_at = -1;  // step count at the last sort
 };
 
 struct TimerRec {
@@ -243,6 +244,7 @@ int sort_species(pic_handle *h, Species &s) {
   h->launches += nl;
   s.cur = 1 - s.cur;
   s.need_sort = false;
+  s.sorted_at = h->step;
   s.fresh = true;
   return PIC_OK;
 }
@@ -609,6 +611,28 @@ int pic_add_species(pic_handle *h, double q, double m, int64_t capacity, int *sp
   return PIC_OK;
 }
 
+namespace {
+// Particles per chunk of a host load (two staging buffers of 60 B each).
+constexpr int64_t kLoadChunk = int64_t(1) << 22;
+
+// The copy stream, events and staging buffers of a chunked host load.  On
+// every exit the copies in flight finish before the buffers are released
+// (stream-ordered on the simulation stream, after the kernels that read them).
+struct LoadPipe {
+  cudaStream_t st = nullptr, cs = nullptr;
+  cudaEvent_t ev[5] = {};  // copied[2], converted[2], allocated
+  void *stage[2] = {};
+  ~LoadPipe() {
+    if (cs) cudaStreamSynchronize(cs);
+    for (void *p : stage)
+      if (p) cudaFreeAsync(p, st);
+    for (cudaEvent_t e : ev)
+      if (e) cudaEventDestroy(e);
+    if (cs) cudaStreamDestroy(cs);
+  }
+};
+}  // namespace
+
 int pic_load_particles(pic_handle *h, int species, int64_t n, const double *x, const double *y, const double *z,
                        const double *ux, const double *uy, const double *uz, const double *w, const uint32_t *id,
                        int mem_kind) {
@@ -622,61 +646,62 @@ int pic_load_particles(pic_handle *h, int species, int64_t n, const double *x, c
   const int64_t cur = read_count(h, s);
   if (cur + n > s.capacity) return fail(h, PIC_ENOMEM, "species capacity exceeded");
   const double *src[7] = {x, y, z, ux, uy, uz, w};
-  const double *dsrc[7] = {};
-  std::vector<void *> tmp;
-  // Host arrays that the device can address (page-locked and mapped, e.g.
-  // registered with cudaHostRegister) are read in place by the load kernel
-  // over the host link: no staging buffers, no separate copies.
-  auto mapped = [](const void *p) -> const void * {
-    cudaPointerAttributes at;
-    if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
-      cudaGetLastError();
-      return nullptr;
-    }
-    return at.type == cudaMemoryTypeHost ? at.devicePointer : nullptr;
-  };
-  bool direct = mem_kind == PIC_MEM_HOST && (!id || mapped(id));
-  for (int a = 0; a < 7 && direct; ++a) direct = !src[a] || mapped(src[a]);
-  const uint32_t *did = id;
-  if (mem_kind == PIC_MEM_HOST && direct) {
-    for (int a = 0; a < 7; ++a) dsrc[a] = src[a] ? static_cast<const double *>(mapped(src[a])) : nullptr;
-    if (id) did = static_cast<const uint32_t *>(mapped(id));
-  } else if (mem_kind == PIC_MEM_HOST) {
-    for (int a = 0; a < 7; ++a) {
-      if (!src[a]) continue;
-      void *p = nullptr;
-      CK(h, cudaMallocAsync(&p, (size_t)n * sizeof(double), h->st), "load staging alloc");
-      tmp.push_back(p);
-      CK(h, cudaMemcpyAsync(p, src[a], (size_t)n * sizeof(double), cudaMemcpyHostToDevice, h->st), "load H2D");
-      dsrc[a] = static_cast<const double *>(p);
+  CK(h, cudaMemsetAsync(h->bad, 0, sizeof(unsigned long long), h->st), "memset");
+  if (mem_kind == PIC_MEM_HOST) {
+    // Host arrays travel in chunks through two device staging buffers: the
+    // copy engine fills one (cudaMemcpyAsync on a copy stream) while the
+    // load kernel converts the other on the simulation stream.  From
+    // page-locked memory this runs at the host link's DMA rate (about three
+    // times what the load kernel reaches reading mapped host memory in place).
+    LoadPipe lp;
+    lp.st = h->st;
+    const int64_t chunk = n < kLoadChunk ? n : kLoadChunk;
+    const size_t stride = (size_t)chunk * sizeof(double);  // one array of a chunk
+    const size_t bytes = 7 * stride + (size_t)chunk * sizeof(uint32_t);
+    const int nbuf = n > chunk ? 2 : 1;
+    CK(h, cudaStreamCreateWithFlags(&lp.cs, cudaStreamNonBlocking), "copy stream");
+    for (auto &e : lp.ev) CK(h, cudaEventCreateWithFlags(&e, cudaEventDisableTiming), "event");
+    for (int b = 0; b < nbuf; ++b) CK(h, cudaMallocAsync(&lp.stage[b], bytes, h->st), "load staging alloc");
+    CK(h, cudaEventRecord(lp.ev[4], h->st), "event");
+    CK(h, cudaStreamWaitEvent(lp.cs, lp.ev[4], 0), "event wait");  // staging allocated
+    for (int64_t c0 = 0, k = 0; c0 < n; c0 += chunk, ++k) {
+      const int b = (int)(k & 1);
+      const int64_t m = n - c0 < chunk ? n - c0 : chunk;
+      unsigned char *d = static_cast<unsigned char *>(lp.stage[b]);
+      if (k >= 2) CK(h, cudaStreamWaitEvent(lp.cs, lp.ev[2 + b], 0), "event wait");  // buffer converted
+      const double *ds[7] = {};
+      for (int a = 0; a < 7; ++a) {
+        if (!src[a]) continue;
+        CK(h, cudaMemcpyAsync(d + a * stride, src[a] + c0, (size_t)m * sizeof(double), cudaMemcpyHostToDevice, lp.cs),
+           "load H2D");
+        ds[a] = reinterpret_cast<const double *>(d + a * stride);
+      }
+      const uint32_t *did = nullptr;
+      if (id) {
+        CK(h, cudaMemcpyAsync(d + 7 * stride, id + c0, (size_t)m * sizeof(uint32_t), cudaMemcpyHostToDevice, lp.cs),
+           "load H2D");
+        did = reinterpret_cast<const uint32_t *>(d + 7 * stride);
+      }
+      CK(h, cudaEventRecord(lp.ev[b], lp.cs), "event");
+      CK(h, cudaStreamWaitEvent(h->st, lp.ev[b], 0), "event wait");  // chunk arrived
+      CK(h,
+         pic::launch_load(h->g, s.buf[s.cur], cur + c0, m, ds[0], ds[1], ds[2], ds[3], ds[4], ds[5], ds[6], did,
+                          (uint32_t)(cur + c0), h->bad, h->st),
+         "load kernel");
+      h->launches++;
+      CK(h, cudaEventRecord(lp.ev[2 + b], h->st), "event");
     }
   } else {
-    for (int a = 0; a < 7; ++a) dsrc[a] = src[a];
+    CK(h,
+       pic::launch_load(h->g, s.buf[s.cur], cur, n, src[0], src[1], src[2], src[3], src[4], src[5], src[6], id,
+                        (uint32_t)cur, h->bad, h->st),
+       "load kernel");
+    h->launches++;
   }
-  std::vector<uint32_t> gen;
-  if (!id) {
-    gen.resize((size_t)n);
-    for (int64_t i = 0; i < n; ++i) gen[(size_t)i] = (uint32_t)(cur + i);
-    did = gen.data();
-  }
-  if ((mem_kind == PIC_MEM_HOST && !direct) || !id) {
-    void *p = nullptr;
-    CK(h, cudaMallocAsync(&p, (size_t)n * sizeof(uint32_t), h->st), "load staging alloc");
-    tmp.push_back(p);
-    CK(h, cudaMemcpyAsync(p, did, (size_t)n * sizeof(uint32_t), cudaMemcpyHostToDevice, h->st), "load H2D");
-    did = static_cast<const uint32_t *>(p);
-  }
-  CK(h, cudaMemsetAsync(h->bad, 0, sizeof(unsigned long long), h->st), "memset");
-  CK(h,
-     pic::launch_load(h->g, s.buf[s.cur], cur, n, dsrc[0], dsrc[1], dsrc[2], dsrc[3], dsrc[4], dsrc[5], dsrc[6], did,
-                      h->bad, h->st),
-     "load kernel");
-  h->launches++;
   const int64_t nn = cur + n;
   CK(h, cudaMemcpyAsync(s.d_count, &nn, sizeof(int64_t), cudaMemcpyHostToDevice, h->st), "count");
   unsigned long long bad = 0;
   CK(h, cudaMemcpyAsync(&bad, h->bad, sizeof(bad), cudaMemcpyDeviceToHost, h->st), "bad count");
-  for (void *p : tmp) cudaFreeAsync(p, h->st);
   CK(h, cudaStreamSynchronize(h->st), "load sync");
   s.h_count = nn;
   s.need_sort = true;
@@ -687,14 +712,18 @@ int pic_load_particles(pic_handle *h, int species, int64_t n, const double *x, c
 
 int pic_neutralize(pic_handle *h) {
   if (!h) return fail(h, PIC_EINVAL, "NULL handle");
-  // rho_bg = -rho of the particles: deposit them with the opposite charge
+  // rho_bg = -rho of the particles: deposit them with the opposite charge.
+  // Freshly loaded species are sorted first (the next step would sort them
+  // anyway), so that the tiled fixed-point deposit serves: input in cell
+  // order sends a warp's global atomics to the same nodes.
   CK(h, cudaMemsetAsync(h->rho_bg, 0, sizeof(double) * h->g.ncell, h->st), "memset");
   for (int i = 0; i < h->nsp; ++i) {
     Species &s = h->sp[i];
-    if (s.need_sort)
-      CK(h, pic::launch_rho(h->g, s.buf[s.cur], s.d_count, s.slots, -s.q, h->rho_bg, h->st), "rho deposit");
-    else
-      CK(h, pic::launch_rho_tiled(h->g, s.buf[s.cur], s.tile_start, -s.q, h->rho_bg, h->ctr, h->st), "rho deposit");
+    if (s.need_sort) {
+      const int r = sort_species(h, s);
+      if (r) return r;
+    }
+    CK(h, pic::launch_rho_tiled(h->g, s.buf[s.cur], s.tile_start, -s.q, h->rho_bg, h->ctr, h->st), "rho deposit");
     h->launches++;
   }
   CK(h, cudaStreamSynchronize(h->st), "sync");
@@ -1031,7 +1060,8 @@ int pic_step(pic_handle *h, int nsteps) {
           cudaGetLastError();  // not ready: not an error
         }
       }
-      if (s.need_sort || h->step % every == 0 || many_escapes) {
+      // (a species sorted since the last push, e.g. by pic_neutralize, is not sorted again)
+      if (s.need_sort || (h->step % every == 0 && s.sorted_at != h->step) || many_escapes) {
         if (many_escapes) h->adaptive_sorts++;
         int r = sort_species(h, s);
         if (r) return r;

@@ -147,7 +147,7 @@ __global__ void k_load(int dims, int n0, int n1, int n2, double rdx0, double rdx
                        int64_t offset, int64_t n, const double *__restrict__ x, const double *__restrict__ y,
                        const double *__restrict__ z, const double *__restrict__ ux, const double *__restrict__ uy,
                        const double *__restrict__ uz, const double *__restrict__ w, const uint32_t *__restrict__ id,
-                       unsigned long long *bad) {
+                       uint32_t id_base, unsigned long long *bad) {
   for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < n; q += (int64_t)gridDim.x * blockDim.x) {
     const double pos[3] = {x[q] * rdx0, y[q] * rdx1, dims == 3 ? z[q] * rdx2 : 0.0};
     const int nn[3] = {n0, n1, n2};
@@ -188,7 +188,7 @@ __global__ void k_load(int dims, int n0, int n1, int n2, double rdx0, double rdx
     static_cast<R *>(p.u[1])[s] = (R)uy[q];
     static_cast<R *>(p.u[2])[s] = (R)uz[q];
     static_cast<R *>(p.w)[s] = (R)w[q];
-    p.id[s] = id ? id[q] : (uint32_t)q;
+    p.id[s] = id ? id[q] : id_base + (uint32_t)q;  // no tags given: running index
   }
 }
 
@@ -310,21 +310,41 @@ __global__ void __launch_bounds__(256)
   if (threadIdx.x == 0) atomicAdd(out + 5, v);
 }
 
-// sum E^2, sum B^2 (squares in the storage precision, sums in FP64)
+// A thread's running sum of per-element terms computed in R.  FP64 runs add
+// in FP64.  FP32 runs keep a compensated FP32 sum (Neumaier's variant of
+// Kahan summation), which stays off the slow FP64 pipe and is exact to a few
+// FP32 ulps of the summed magnitudes; block and grid sums are FP64.
+template <class R> struct ThreadSum;
+template <> struct ThreadSum<double> {
+  double s = 0.0;
+  __device__ __forceinline__ void add(double x) { s += x; }
+  __device__ __forceinline__ double value() const { return s; }
+};
+template <> struct ThreadSum<float> {
+  float s = 0.f, c = 0.f;
+  __device__ __forceinline__ void add(float x) {
+    const float t = s + x;
+    c += fabsf(s) >= fabsf(x) ? (s - t) + x : (x - t) + s;  // the rounding error of s + x, exactly
+    s = t;
+  }
+  __device__ __forceinline__ double value() const { return (double)s + (double)c; }
+};
+
+// sum E^2, sum B^2 (squares in the storage precision)
 template <class R>
 __global__ void __launch_bounds__(256)
     k_field_energy(int64_t ncell, const R *Ex, const R *Ey, const R *Ez, const R *Bx, const R *By, const R *Bz,
                    double *out) {
   __shared__ double sh[32];
-  double se = 0, sb = 0;
+  ThreadSum<R> se, sb;
   for (int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; c < ncell; c += (int64_t)gridDim.x * blockDim.x) {
     const R ex = Ex[c], ey = Ey[c], ez = Ez[c], bx = Bx[c], by = By[c], bz = Bz[c];
-    se += (double)(ex * ex + ey * ey + ez * ez);
-    sb += (double)(bx * bx + by * by + bz * bz);
+    se.add(ex * ex + ey * ey + ez * ez);
+    sb.add(bx * bx + by * by + bz * bz);
   }
-  double v = block_sum(se, sh);
+  double v = block_sum(se.value(), sh);
   if (threadIdx.x == 0) atomicAdd(out + 0, v);
-  v = block_sum(sb, sh);
+  v = block_sum(sb.value(), sh);
   if (threadIdx.x == 0) atomicAdd(out + 1, v);
 }
 
@@ -333,23 +353,24 @@ __global__ void __launch_bounds__(256)
     k_particle_diag(Particles p, const int64_t *__restrict__ d_count, double m, double *out) {
   __shared__ double sh[32];
   const int64_t n = *d_count;
-  double ek = 0, cnt = 0, nf = 0;
+  ThreadSum<R> ek;
+  int64_t cnt = 0, nf = 0;
   for (int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; s < n; s += (int64_t)gridDim.x * blockDim.x) {
     if (p.cell[s] < 0) continue;
-    // per-particle terms in the storage precision, sums in FP64
+    // per-particle terms in the storage precision
     const R ux = static_cast<const R *>(p.u[0])[s], uy = static_cast<const R *>(p.u[1])[s],
             uz = static_cast<const R *>(p.u[2])[s];
     const R u2 = ux * ux + uy * uy + uz * uz;
     // gamma - 1 = u^2 / (sqrt(1 + u^2) + 1), free of cancellation
-    ek += (double)(static_cast<const R *>(p.w)[s] * (u2 / (sqrt(R(1) + u2) + R(1))));
-    cnt += 1;
-    if (!isfinite(u2)) nf += 1;
+    ek.add(static_cast<const R *>(p.w)[s] * (u2 / (sqrt(R(1) + u2) + R(1))));
+    ++cnt;
+    nf += !isfinite(u2);
   }
-  double v = block_sum(ek, sh);
+  double v = block_sum(ek.value(), sh);
   if (threadIdx.x == 0) atomicAdd(out + 0, m * v);
-  v = block_sum(cnt, sh);
+  v = block_sum((double)cnt, sh);
   if (threadIdx.x == 0) atomicAdd(out + 1, v);
-  v = block_sum(nf, sh);
+  v = block_sum((double)nf, sh);
   if (threadIdx.x == 0) atomicAdd(out + 2, v);
 }
 
@@ -484,16 +505,17 @@ cudaError_t launch_mur_apply(const Grid &g, void *const E[3], const double *buf,
 
 cudaError_t launch_load(const Grid &g, const Particles &p, int64_t offset, int64_t n, const double *x,
                         const double *y, const double *z, const double *ux, const double *uy, const double *uz,
-                        const double *w, const uint32_t *id, unsigned long long *bad, cudaStream_t st) {
+                        const double *w, const uint32_t *id, uint32_t id_base, unsigned long long *bad,
+                        cudaStream_t st) {
   if (n <= 0) return cudaSuccess;
   const int nb = grid_blocks(n, 256);
   const int absorb = g.absorb_lo || g.absorb_hi;
   if (g.prec == 1)
     k_load<double><<<nb, 256, 0, st>>>(g.dims, g.n[0], g.n[1], g.n[2], 1.0 / g.dx[0], 1.0 / g.dx[1], 1.0 / g.dx[2],
-                                       absorb, p, offset, n, x, y, z, ux, uy, uz, w, id, bad);
+                                       absorb, p, offset, n, x, y, z, ux, uy, uz, w, id, id_base, bad);
   else
     k_load<float><<<nb, 256, 0, st>>>(g.dims, g.n[0], g.n[1], g.n[2], 1.0 / g.dx[0], 1.0 / g.dx[1], 1.0 / g.dx[2],
-                                      absorb, p, offset, n, x, y, z, ux, uy, uz, w, id, bad);
+                                      absorb, p, offset, n, x, y, z, ux, uy, uz, w, id, id_base, bad);
   return cudaGetLastError();
 }
 

@@ -152,7 +152,8 @@ cudaError_t launch_mur_apply(const Grid &g, void *const E[3], const double *buf,
 // Load n particles into slots [offset, offset+n).
 cudaError_t launch_load(const Grid &g, const Particles &p, int64_t offset, int64_t n, const double *x,
                         const double *y, const double *z, const double *ux, const double *uy, const double *uz,
-                        const double *w, const uint32_t *id, unsigned long long *bad, cudaStream_t st);
+                        const double *w, const uint32_t *id, uint32_t id_base, unsigned long long *bad,
+                        cudaStream_t st);
 cudaError_t launch_unload(const Grid &g, const Particles &p, const int64_t *d_count, int64_t nmax, double *x,
                           double *y, double *z, double *ux, double *uy, double *uz, double *w, uint32_t *id,
                           int32_t *alive, cudaStream_t st);
