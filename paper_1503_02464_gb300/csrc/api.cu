@@ -575,14 +575,16 @@ int pic_add_species(pic_handle *h, double q, double m, int64_t capacity, int *sp
   if (e == cudaSuccess) e = cudaMalloc(&s.tile_start, (size_t)(h->g.ntiles + 1) * sizeof(int64_t));
   // Work items: pieces of at most `chunk` slots per tile, chunk sized so that
   // a species spread over few tiles (a thin slab, a small grid) still gives
-  // about 16 blocks per SM, and never below 512 slots.
+  // about 16 blocks per SM, never below 512 slots and never above the
+  // fixed-point window's limit (kMaxWindowSlots).
   {
     int dev = 0, nsm = 1;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
     int64_t chunk = s.slots / (16 * (int64_t)(nsm > 0 ? nsm : 1));
     chunk = (chunk + 255) / 256 * 256;
-    s.work.chunk = chunk < 512 ? 512 : chunk;
+    chunk = chunk < 512 ? 512 : chunk;
+    s.work.chunk = chunk > pic::kMaxWindowSlots ? pic::kMaxWindowSlots : chunk;
     s.work.nwork = s.slots / s.work.chunk + 1 + h->g.ntiles;
   }
   if (e == cudaSuccess) e = cudaMalloc(&s.tq, (size_t)2 * s.work.nwork * sizeof(float));

@@ -92,6 +92,12 @@ void set_global_error(const std::string &msg);
 
 constexpr int kTilePad = 4;
 
+// Most particle slots one block accumulates into a shared window: FP32 runs
+// keep each node's fixed-point sum as a pair of int32 words, and the low word
+// (at most 2^15 in magnitude per contribution, one contribution per particle
+// and node) cannot overflow below 65,536 contributions.
+constexpr int64_t kMaxWindowSlots = 65280;
+
 enum KernelClass {
   KC_SORT = 0, KC_ZEROJ = 1, KC_PUSH = 2, KC_YEE_B = 3, KC_YEE_E = 4, KC_BOUNDARY = 5, KC_FILTER = 6,
   KC_ADJ_FIELD = 7, KC_ADJ_PUSH = 8, KC_N = 9

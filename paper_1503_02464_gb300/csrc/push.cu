@@ -60,6 +60,7 @@ template <int DIM, int ORDER> struct Geo {
   // -> 2.2 wavefronts per atomic instruction).  The padding nodes stay zero.
   static constexpr int JP = (DIM == 3 && ORDER == 2) ? JX * JY + 6 : JX * JY;
   static constexpr int JN = JP * JZ;
+  static constexpr int JS = JN + (ORDER == 2 ? 32 : 0);  // word-array stride of the shared J window (TSC: + 32 scratch words)
   static constexpr int NS = ORDER + 1;  // gather stencil width
   static constexpr int NW = ORDER + 2;  // deposit stencil width
 };
@@ -162,8 +163,9 @@ __device__ __forceinline__ R gsum(const R *__restrict__ F, const R *wx, const R 
 // shared atomics, keeping FP64 rounding.
 template <class R> struct WinAcc;
 template <> struct WinAcc<float> {
-  int *w;       // [3][2][JN]: per component lo words, then hi words
-  int jn;
+  int *w;       // [3][2][jn]: per component lo words, then hi words
+  int jn;       // word stride: the window's nodes (then, for TSC, 32 scratch words)
+  int dummy;    // TSC: this lane's scratch word (past the nodes, bank = lane)
   float scale;  // 2^K
   float unit;   // 2^-K
   static constexpr int kLimitLog2 = 37;
@@ -175,17 +177,22 @@ template <> struct WinAcc<float> {
   // the float spacing is 2^16) and its bit pattern minus the magic's is hi;
   // the second FMA gives X - hi 2^16 with one rounding, |.| <= 2^15, and the
   // 2^23 magic rounds that to the integer lo.
+  template <bool kScratch>
   __device__ __forceinline__ void add(int comp, int idx, float p, float q) const {
     const float y = fmaf(p, q, kMagicHi);
     const float r = y - kMagicHi;  // hi 2^16, exact
     const float lf = fmaf(p, q, -r);
     const int hi = __float_as_int(y) - __float_as_int(kMagicHi);
     const int lo = __float_as_int(lf + kMagic) - __float_as_int(kMagic);
-    // Both words are added unconditionally: a zero adds nothing, and a
-    // branch around the pair (or a predicate on it) cost more than the
-    // zero adds do.  Warps whose particles all deposit nothing skip the
-    // whole stencil instead (deposit_particle).
-    const unsigned s = (unsigned)__cvta_generic_to_shared(w + comp * 2 * jn + idx);
+    // Both words are added unconditionally: a branch around the pair (or a
+    // predicate on it) cost more than the adds.  With kScratch (TSC) a zero
+    // contribution goes to the lane's own scratch word instead of the node,
+    // so that it does not collide with the other lanes' nodes in their
+    // banks (for CIC's smaller stencils the select costs more than it
+    // saves).  Warps whose particles all deposit nothing skip the whole
+    // stencil instead (deposit_particle).
+    const int at = (!kScratch || (hi | lo)) ? idx : dummy;
+    const unsigned s = (unsigned)__cvta_generic_to_shared(w + comp * 2 * jn + at);
     asm volatile("red.shared.add.s32 [%0], %1;\n\tred.shared.add.s32 [%2], %3;" ::"r"(s), "r"(lo),
                  "r"(s + 4u * (unsigned)jn), "r"(hi));
   }
@@ -195,10 +202,12 @@ template <> struct WinAcc<float> {
   }
 };
 template <> struct WinAcc<double> {
-  double *w;  // [3][JN], plain double sums (the FP64 path keeps FP64 rounding)
+  double *w;  // [3][jn], plain double sums (the FP64 path keeps FP64 rounding)
   int jn;
+  int dummy;  // (unused)
   double scale;  // 1: contributions are passed unscaled
   double unit;
+  template <bool kScratch>
   __device__ __forceinline__ void add(int comp, int idx, double p, double q) const {
     const double x = p * q;
     if (x != 0.0) atomicAdd(w + comp * jn + idx, x);
@@ -255,7 +264,7 @@ __device__ __forceinline__ void deposit_win(const WinAcc<R> &acc, int base, cons
 #pragma unroll
         for (int a = 0; a < M; ++a) {
           if (a == M - 1 && !lx) continue;
-          acc.add(0, base + c * SZ + b * SY + a, Px[a], br);
+          acc.template add<ORDER == 2>(0, base + c * SZ + b * SY + a, Px[a], br);
         }
       }
     }
@@ -269,7 +278,7 @@ __device__ __forceinline__ void deposit_win(const WinAcc<R> &acc, int base, cons
 #pragma unroll
         for (int b = 0; b < M; ++b) {
           if (b == M - 1 && !ly) continue;
-          acc.add(1, base + c * SZ + b * SY + a, Py[b], br);
+          acc.template add<ORDER == 2>(1, base + c * SZ + b * SY + a, Py[b], br);
         }
       }
     }
@@ -285,7 +294,7 @@ __device__ __forceinline__ void deposit_win(const WinAcc<R> &acc, int base, cons
 #pragma unroll
         for (int c = 0; c < M; ++c) {
           if (c == M - 1 && !lz) continue;
-          acc.add(2, base + c * SZ + b * SY + a, Pz[c], br);
+          acc.template add<ORDER == 2>(2, base + c * SZ + b * SY + a, Pz[c], br);
         }
       }
     }
@@ -300,12 +309,12 @@ __device__ __forceinline__ void deposit_win(const WinAcc<R> &acc, int base, cons
 #pragma unroll
       for (int a = 0; a < M; ++a) {
         if (a == M - 1 && !lx) continue;
-        acc.add(0, base + b * SY + a, Px[a], hy);
+        acc.template add<ORDER == 2>(0, base + b * SY + a, Px[a], hy);
       }
 #pragma unroll
       for (int a = 0; a < NW; ++a) {
         if (a == NW - 1 && !lx) continue;
-        acc.add(2, base + b * SY + a, qwvz, X.S0[a] * hy + X.DS[a] * ty);
+        acc.template add<ORDER == 2>(2, base + b * SY + a, qwvz, X.S0[a] * hy + X.DS[a] * ty);
       }
     }
 #pragma unroll
@@ -315,7 +324,7 @@ __device__ __forceinline__ void deposit_win(const WinAcc<R> &acc, int base, cons
 #pragma unroll
       for (int b = 0; b < M; ++b) {
         if (b == M - 1 && !ly) continue;
-        acc.add(1, base + b * SY + a, Py[b], hx);
+        acc.template add<ORDER == 2>(1, base + b * SY + a, Py[b], hx);
       }
     }
   }
@@ -427,12 +436,11 @@ __global__ void __launch_bounds__(kThreads, sizeof(R) == 4 ? (DIM == 2 ? 4 : (OR
   R *sF = reinterpret_cast<R *>(smem_raw);    // 6 * EN: Ex Ey Ez Bx By Bz
   // J window: 24 bytes per node (3 components x 8 bytes of fixed point)
   unsigned char *sJraw = smem_raw + 6 * G::EN * sizeof(R);
-  R *sOff = reinterpret_cast<R *>(sJraw + 24 * G::JN);  // DIM x 256
+  R *sOff = reinterpret_cast<R *>(sJraw + 24 * G::JS);  // DIM x 256
   R *sU = sOff + DIM * kThreads;              // 3 x 256
   R *sW = sU + 3 * kThreads;                  // 256
   int32_t *sCell = reinterpret_cast<int32_t *>(sW + kThreads);  // 256
-  R *sFo = reinterpret_cast<R *>(sCell + kThreads);                 // FP32 3D: 3 x 256 old offsets
-  int32_t *sJob = reinterpret_cast<int32_t *>(sFo + 3 * kThreads);  // FP32 3D: 256 deposit jobs
+  int32_t *sJob = sCell + kThreads;  // FP32 3D: 256 deposit jobs
   __shared__ unsigned int s_clamp;
   __shared__ double s_scale;
   __shared__ unsigned int s_emax[3];
@@ -472,7 +480,7 @@ __global__ void __launch_bounds__(kThreads, sizeof(R) == 4 ? (DIM == 2 ? 4 : (OR
       emax[c] = fmax(emax[c], fabs((float)ev));
     }
   }
-  for (int q = tid; q < 6 * G::JN; q += kThreads) reinterpret_cast<int *>(sJraw)[q] = 0;  // 24 B per node
+  for (int q = tid; q < 6 * G::JS; q += kThreads) reinterpret_cast<int *>(sJraw)[q] = 0;  // 24 B per node
   if (tid == 0) {
     s_clamp = 0;
     s_emax[0] = s_emax[1] = s_emax[2] = 0u;
@@ -529,7 +537,8 @@ __global__ void __launch_bounds__(kThreads, sizeof(R) == 4 ? (DIM == 2 ? 4 : (OR
   __syncthreads();
   WinAcc<R> acc;
   acc.w = reinterpret_cast<decltype(acc.w)>(sJraw);
-  acc.jn = G::JN;
+  acc.jn = G::JS;
+  acc.dummy = G::JN + (tid & 31);
   acc.scale = (R)s_scale;
   acc.unit = (R)(1.0 / s_scale);
 
@@ -540,9 +549,9 @@ __global__ void __launch_bounds__(kThreads, sizeof(R) == 4 ? (DIM == 2 ? 4 : (OR
   // on slot tid instead, where a warp's lanes sit in a few neighbouring cells
   // and mostly read the same field nodes (shared-memory broadcasts instead of
   // bank conflicts on the 162-node TSC gather); each pushed particle then
-  // leaves a deposit job behind (old offsets in sFo, new ones in sOff, tile
-  // cell and cell shift packed in sJob) for the deposit phase after a block
-  // barrier.  In 2D the gather is a third of that, and FP64 runs are bound by
+  // writes its new state to global memory and leaves a deposit job behind
+  // (old offsets in sU, new ones in sOff, tile cell and cell shift packed in
+  // sJob) for the deposit phase after a block barrier.  In 2D the gather is a third of that, and FP64 runs are bound by
   // the FP64 pipe: there the extra barrier and staging traffic cost more than
   // they save, so one thread pushes and deposits slot e.
   constexpr bool kSplit = DIM == 3 && sizeof(R) == 4;
@@ -595,7 +604,8 @@ __global__ void __launch_bounds__(kThreads, sizeof(R) == 4 ? (DIM == 2 ? 4 : (OR
         }
         if (!inw) {
           // defer to k_push_escaped (state left untouched)
-          sCell[ep] = c | kEscFlag;
+          if (kSplit) a.cell[c0 + ep] = c | kEscFlag;
+          else sCell[ep] = c | kEscFlag;
           const unsigned long long slot = atomicAdd(a.esc_count, 1ull);
           a.esc_list[slot] = (int32_t)(c0 + ep);
           my_q1 += fabsf((float)sW[ep]);  // its new |u| is not known here: bound by 1
@@ -647,25 +657,15 @@ __global__ void __launch_bounds__(kThreads, sizeof(R) == 4 ? (DIM == 2 ? 4 : (OR
           if (sizeof(R) == 4)
             my_q1 += fabsf((float)sW[ep]) * fminf(1.f, sqrtf((float)(u[0] * u[0] + u[1] * u[1] + u[2] * u[2])));
 
-          if (kSplit) {
-            // the deposit job; the old offsets stay readable in sFo
-#pragma unroll
-            for (int d = 0; d < DIM; ++d) sFo[d * kThreads + ep] = f[d];
-            job = pack_job(l, s);
-          } else if (!deposit_particle<R, DIM, ORDER>(a, acc, l, s, f, fn, sW[ep], u[2] * ig)) {
+          if (!kSplit && !deposit_particle<R, DIM, ORDER>(a, acc, l, s, f, fn, sW[ep], u[2] * ig))
             break;  // (checked build) leaves the particle as it was
-          }
 
-          // ---- new state back into the staging slot ----
-#pragma unroll
-          for (int d = 0; d < DIM; ++d) sOff[d * kThreads + ep] = fn[d];
-#pragma unroll
-          for (int d = 0; d < 3; ++d) sU[d * kThreads + ep] = u[d];
+          // ---- the new state ----
+          int nc = -1;  // removed at an absorbing wall after depositing its move
           if (outside_walls<R>(a.absorb, ci[0] + s[0], fn[0], a.n[0])) {
-            sCell[ep] = -1;  // removed at an absorbing wall after depositing its move
             ++my_absorbed;
           } else {
-            int nc = c;
+            nc = c;
             const int i0 = ci[0] + s[0];
             nc += s[0] + (i0 < 0 ? a.n[0] : (i0 >= a.n[0] ? -a.n[0] : 0));
             const int i1 = ci[1] + s[1];
@@ -674,6 +674,29 @@ __global__ void __launch_bounds__(kThreads, sizeof(R) == 4 ? (DIM == 2 ? 4 : (OR
               const int i2 = ci[2] + s[2];
               nc += (s[2] + (i2 < 0 ? a.n[2] : (i2 >= a.n[2] ? -a.n[2] : 0))) * a.n[0] * a.n[1];
             }
+          }
+          if (kSplit) {
+            // Slot ep is this thread's own index: the state goes straight to
+            // global memory (coalesced).  The deposit job keeps the old
+            // offsets in sU (u is no longer needed there) and the new ones
+            // in sOff.
+            const int64_t p = c0 + ep;
+            a.cell[p] = nc;
+#pragma unroll
+            for (int d = 0; d < DIM; ++d) {
+              a.off[d][p] = fn[d];
+              sU[d * kThreads + ep] = f[d];
+              sOff[d * kThreads + ep] = fn[d];
+            }
+#pragma unroll
+            for (int d = 0; d < 3; ++d) a.u[d][p] = u[d];
+            job = pack_job(l, s);
+          } else {
+            // back into the staging slot, stored after the chunk
+#pragma unroll
+            for (int d = 0; d < DIM; ++d) sOff[d * kThreads + ep] = fn[d];
+#pragma unroll
+            for (int d = 0; d < 3; ++d) sU[d * kThreads + ep] = u[d];
             sCell[ep] = nc;
           }
         } while (0);
@@ -691,7 +714,7 @@ __global__ void __launch_bounds__(kThreads, sizeof(R) == 4 ? (DIM == 2 ? 4 : (OR
           R f[3], fn[3];
 #pragma unroll
           for (int d = 0; d < 3; ++d) {
-            f[d] = sFo[d * kThreads + e];
+            f[d] = sU[d * kThreads + e];
             fn[d] = sOff[d * kThreads + e];
           }
           deposit_particle<R, DIM, ORDER>(a, acc, l, s, f, fn, sW[e], R(0));
@@ -699,8 +722,8 @@ __global__ void __launch_bounds__(kThreads, sizeof(R) == 4 ? (DIM == 2 ? 4 : (OR
       }
     }
     __syncthreads();
-    // coalesced store of the chunk (w is unchanged)
-    if (tid < cn) {
+    // coalesced store of the chunk (w is unchanged; 3D FP32 stored its state in phase 1)
+    if (!kSplit && tid < cn) {
       const int64_t p = c0 + tid;
       a.cell[p] = sCell[tid];
 #pragma unroll
@@ -868,9 +891,9 @@ __global__ void __launch_bounds__(kThreads) k_push_escaped(const PushArgs<R> a) 
 template <class R, int DIM, int ORDER> constexpr size_t smem_bytes() {
   using G = Geo<DIM, ORDER>;
   // E, B window; J window; staging of cell, offsets, u, w; for FP32 3D the
-  // deposit jobs (old offsets and a packed int per slot)
+  // deposit jobs (a packed int per slot)
   constexpr bool split = DIM == 3 && sizeof(R) == 4;
-  return (size_t)(6 * G::EN + (DIM + 4 + (split ? 3 : 0)) * kThreads) * sizeof(R) + 24 * (size_t)G::JN +
+  return (size_t)(6 * G::EN + (DIM + 4) * kThreads) * sizeof(R) + 24 * (size_t)G::JS +
          (split ? 2 : 1) * kThreads * sizeof(int32_t);
 }
 
@@ -927,16 +950,22 @@ cudaError_t launch_t(const Grid &g, void *const E[3], void *const B[3], void *co
 }
 
 // Charge density at the nodes for the diagnostics, rho += q w S(X-i)S(Y-j)S(Z-k),
-// one block per tile like k_push.  The block's window sums are exact 64-bit
-// fixed point (|rho_node| <= sum |q w| over the tile bounds the scale), so
-// the result does not depend on the order of the additions; particles more
-// than one cell outside their tile add to the global array directly.  The
-// 1D weights are FP64 in both precisions.  FP64 runs scale the tile's charge
-// bound to 2^61 and convert each product with a float-to-integer
-// conversion; FP32 runs, whose currents carry FP32 rounding anyway, scale it
-// to 2^50 and take the integer from one FMA against 1.5 * 2^52 (the bit
-// pattern of a double in [2^52, 2^53) holds an integer), sparing the slow
-// FP64 conversions.
+// one block per tile like k_push, particles taken in the same lane-spread
+// order (a warp's lanes about one cell apart, so that their atomics hit
+// different nodes).  The block's window sums are exact fixed point, scaled
+// from a bound on the tile's charge (|rho_node| <= sum |q w|), so the window
+// does not depend on the order of the additions; each node then receives
+// one FP64 add per tile that reaches it.  Particles more than one cell
+// outside their tile add to the global array directly.
+//  FP32 runs: weights and products in FP32 (their positions carry FP32
+//   rounding anyway), the tile's bound scaled to 2^37 and each product split
+//   into int32 words hi 2^16 + lo by FP32 FMAs, as in the push's current
+//   window; each particle's contributions sum exactly to its charge (the
+//   last node takes the remainder), so the total charge is conserved; a
+//   tile of more than kMaxWindowSlots particles is flushed in pieces so that
+//   the lo sums cannot overflow.
+//  FP64 runs: weights in FP64, the bound scaled to 2^61, one 64-bit word per
+//   node.
 template <class R, int DIM, int ORDER>
 __global__ void __launch_bounds__(kThreads)
     k_rho_tile(int n0, int n1, int n2, int ntile0, int ntile1, FastDiv dn0, FastDiv dn1, const int32_t *__restrict__ cell,
@@ -947,108 +976,166 @@ __global__ void __launch_bounds__(kThreads)
   constexpr int NS = ORDER + 1;
   constexpr int RX = G::EX, RY = G::EY, RZ = G::EZ;  // window: cell-1 .. cell+2 around the tile (+ drift)
   constexpr int RN = RX * RY * RZ;
-  __shared__ unsigned long long win[RN];
+  constexpr bool kF32 = sizeof(R) == 4;
+  __shared__ unsigned long long win[RN];  // FP32: int32 lo words [0, RN), hi words [RN, 2 RN)
+  int *wlo = reinterpret_cast<int *>(win);
   __shared__ double s_sum;
   const int t = blockIdx.x;
   const int64_t pb = tile_start[t], pe = tile_start[t + 1];
   if (pb >= pe) return;
+  const int tid = threadIdx.x;
   int t0[3];
   t0[0] = (t % ntile0) * G::TX;
   t0[1] = ((t / ntile0) % ntile1) * G::TY;
   t0[2] = (t / ntile0 / ntile1) * G::TZ;
-  for (int i = threadIdx.x; i < RN; i += kThreads) win[i] = 0ull;
-  if (threadIdx.x == 0) s_sum = 0.0;
+  if (tid == 0) s_sum = 0.0;
   __syncthreads();
-  double part = 0.0;
-  for (int64_t p = pb + threadIdx.x; p < pe; p += kThreads)
-    if (cell[p] >= 0) part += fabs((double)w[p]);
-  atomicAdd(&s_sum, part);
-  __syncthreads();
-  const double Q = fabs(q) * s_sum * 1.0001;
-  int e2 = 0;
-  if (Q > 0.0) frexp(Q, &e2);
-  constexpr bool kFma = sizeof(R) == 4;
-  constexpr int kBits = kFma ? 50 : 61;
-  constexpr double kMagic = 6755399441055744.0;  // 1.5 * 2^52
-  const double scale = ldexp(1.0, Q > 0.0 ? kBits - e2 : 0);
-  const R *offs[3] = {off0, off1, off2};
-  for (int64_t p = pb + threadIdx.x; p < pe; p += kThreads) {
-    const int c = cell[p];
-    if (c < 0) continue;
-    const uint32_t r0 = dn0.div((uint32_t)c);
-    int ci[3] = {c - (int)r0 * n0, DIM == 3 ? (int)(r0 - dn1.div(r0) * n1) : (int)r0, DIM == 3 ? (int)dn1.div(r0) : 0};
-    const int nn[3] = {n0, n1, n2};
-    constexpr int TT[3] = {G::TX, G::TY, G::TZ};
-    int l[3] = {0, 0, 0};
-    bool inw = true;
-    int base[3] = {0, 0, 0};
-    double wt[3][NS];
-#pragma unroll
-    for (int d = 0; d < 3; ++d) {
-      if (d >= DIM) {
-        wt[d][0] = 1.0;
-        for (int k = 1; k < NS; ++k) wt[d][k] = 0.0;
-        continue;
-      }
-      int dl = ci[d] - t0[d];
-      if (dl > TT[d] - 1 + G::D) dl -= nn[d];
-      if (dl < -G::D) dl += nn[d];
-      l[d] = dl;
-      inw = inw && dl >= -G::D && dl <= TT[d] - 1 + G::D;
-      const double f = (double)offs[d][p];
-      if (ORDER == 2) {
-        const int h = f >= 0.5;
-        const double dd = f - h, a = 0.5 - dd, b = 0.5 + dd;
-        wt[d][0] = 0.5 * a * a;
-        wt[d][1] = 0.75 - dd * dd;
-        wt[d][NS - 1] = 0.5 * b * b;
-        base[d] = h - 1;
-      } else {
-        wt[d][0] = 1.0 - f;
-        wt[d][NS - 1] = f;
-        base[d] = 0;
-      }
-    }
-    const double qw = q * (double)w[p];
-    double qwx[NS];  // q w S_x, pre-scaled for the window
-#pragma unroll
-    for (int kx = 0; kx < NS; ++kx) qwx[kx] = (inw ? qw * scale : qw) * wt[0][kx];
-#pragma unroll
-    for (int kz = 0; kz < (DIM == 3 ? NS : 1); ++kz)
-#pragma unroll
-      for (int ky = 0; ky < NS; ++ky) {
-        const double wyz = wt[1][ky] * wt[2][kz];
-#pragma unroll
-        for (int kx = 0; kx < NS; ++kx) {
-          if (inw) {
-            const int ix = l[0] + base[0] + kx + G::D + G::LOE;
-            const int iy = l[1] + base[1] + ky + G::D + G::LOE;
-            const int iz = DIM == 3 ? l[2] + base[2] + kz + G::D + G::LOE : 0;
-            if (!PIC_CHECK(ix >= 0 && ix < RX && iy >= 0 && iy < RY && iz >= 0 && iz < RZ, ctr)) continue;
-            long long X;
-            if (kFma)
-              X = __double_as_longlong(fma(qwx[kx], wyz, kMagic)) - __double_as_longlong(kMagic);
-            else
-              X = __double2ll_rn(qwx[kx] * wyz);
-            atomicAdd(&win[ix + RX * (iy + RY * iz)], (unsigned long long)X);
-          } else {
-            const double v = qwx[kx] * wyz;
-            const int gi = wrapi(ci[0] + base[0] + kx, n0), gj = wrapi(ci[1] + base[1] + ky, n1);
-            const int gk = DIM == 3 ? wrapi(ci[2] + base[2] + kz, n2) : 0;
-            atomicAdd(rho + gi + (int64_t)n0 * (gj + (int64_t)n1 * gk), v);
-          }
-        }
-      }
+  {
+    R part = R(0);
+    for (int64_t p = pb + tid; p < pe; p += kThreads)
+      if (cell[p] >= 0) part += fabs(w[p]);
+    for (int o = 16; o > 0; o >>= 1) part += __shfl_down_sync(0xffffffffu, part, o);
+    if ((tid & 31) == 0 && part > R(0)) atomicAdd(&s_sum, (double)part);
   }
   __syncthreads();
-  for (int i = threadIdx.x; i < RN; i += kThreads) {
-    const long long X = (long long)win[i];
-    if (X == 0) continue;
-    const int x = i % RX, y = (i / RX) % RY, z = i / (RX * RY);
-    const int gi = wrap_near(t0[0] - G::D - G::LOE + x, n0);
-    const int gj = wrap_near(t0[1] - G::D - G::LOE + y, n1);
-    const int gk = DIM == 3 ? wrap_near(t0[2] - G::D - G::LOE + z, n2) : 0;
-    atomicAdd(rho + gi + (int64_t)n0 * (gj + (int64_t)n1 * gk), (double)X / scale);
+  // 1.01: room for the rounding of the sum above
+  const double Q = fabs(q) * s_sum * 1.01;
+  int e2 = 0;
+  if (Q > 0.0) frexp(Q, &e2);  // Q < 2^e2
+  int K = Q > 0.0 ? (kF32 ? WinAcc<float>::kLimitLog2 : 61) - e2 : 0;
+  K = K > 100 ? 100 : (K < -100 ? -100 : K);
+  const double scale = ldexp(1.0, K);
+  const R *offs[3] = {off0, off1, off2};
+  const int nn[3] = {n0, n1, n2};
+  constexpr int TT[3] = {G::TX, G::TY, G::TZ};
+  const int lane = tid & 31, warp = tid >> 5;
+  const int e = 8 * lane + ((warp + (lane >> 2)) & 7);  // lane-spread slot of a 256-slot chunk
+  for (int64_t s0 = pb; s0 < pe; s0 += kMaxWindowSlots) {
+    const int64_t se = pe - s0 < kMaxWindowSlots ? pe : s0 + kMaxWindowSlots;
+    for (int i = tid; i < (kF32 ? 2 * RN : RN); i += kThreads) {
+      if (kF32) wlo[i] = 0;
+      else win[i] = 0ull;
+    }
+    __syncthreads();
+    for (int64_t c0 = s0; c0 < se; c0 += kThreads) {
+      const int64_t p = c0 + e;
+      if (p >= se) continue;
+      const int c = cell[p];
+      if (c < 0) continue;
+      const uint32_t r0 = dn0.div((uint32_t)c);
+      const int ci[3] = {c - (int)r0 * n0, DIM == 3 ? (int)(r0 - dn1.div(r0) * n1) : (int)r0,
+                         DIM == 3 ? (int)dn1.div(r0) : 0};
+      int l[3] = {0, 0, 0};
+      bool inw = true;
+      int base[3] = {0, 0, 0};
+      R wt[3][NS];
+#pragma unroll
+      for (int d = 0; d < 3; ++d) {
+        if (d >= DIM) {
+          wt[d][0] = R(1);
+          for (int k = 1; k < NS; ++k) wt[d][k] = R(0);
+          continue;
+        }
+        int dl = ci[d] - t0[d];
+        if (dl > TT[d] - 1 + G::D) dl -= nn[d];
+        if (dl < -G::D) dl += nn[d];
+        l[d] = dl;
+        inw = inw && dl >= -G::D && dl <= TT[d] - 1 + G::D;
+        const R f = offs[d][p];
+        if (ORDER == 2) {
+          const int h = f >= R(0.5);
+          const R dd = f - R(h), a = R(0.5) - dd, b = R(0.5) + dd;
+          wt[d][0] = R(0.5) * a * a;
+          wt[d][1] = R(0.75) - dd * dd;
+          wt[d][NS - 1] = R(0.5) * b * b;
+          base[d] = h - 1;
+        } else {
+          wt[d][0] = R(1) - f;
+          wt[d][NS - 1] = f;
+          base[d] = 0;
+        }
+      }
+      // q w S_x, in window units (2^K) for particles in the window
+      const R qw = inw ? (R)(q * scale) * w[p] : (R)q * w[p];
+      R qwx[NS];
+#pragma unroll
+      for (int kx = 0; kx < NS; ++kx) qwx[kx] = qw * wt[0][kx];
+      // FP32 runs: the particle's last node takes its whole charge minus what
+      // the other nodes received, so that its integer contributions sum to
+      // the integer q w 2^K exactly (and a particle outside the window adds
+      // q w minus the other FP64 products): the FP32 weights need not sum to
+      // one exactly for the total charge to be conserved.
+      int hi_t = 0, lo_t = 0;
+      double v_t = 0.0;
+      if (kF32) {
+        if (inw) {
+          const float y = qw + WinAcc<float>::kMagicHi;  // |q w 2^K| < 2^37: hi 2^16 + lo as below
+          hi_t = __float_as_int(y) - __float_as_int(WinAcc<float>::kMagicHi);
+          lo_t = __float_as_int((qw - (y - WinAcc<float>::kMagicHi)) + WinAcc<float>::kMagic) -
+                 __float_as_int(WinAcc<float>::kMagic);
+        } else {
+          v_t = (double)qw;
+        }
+      }
+#pragma unroll
+      for (int kz = 0; kz < (DIM == 3 ? NS : 1); ++kz)
+#pragma unroll
+        for (int ky = 0; ky < NS; ++ky) {
+          const R wyz = wt[1][ky] * wt[2][kz];
+#pragma unroll
+          for (int kx = 0; kx < NS; ++kx) {
+            const bool last = kF32 && kx == NS - 1 && ky == NS - 1 && kz == (DIM == 3 ? NS - 1 : 0);
+            if (inw) {
+              const int ix = l[0] + base[0] + kx + G::D + G::LOE;
+              const int iy = l[1] + base[1] + ky + G::D + G::LOE;
+              const int iz = DIM == 3 ? l[2] + base[2] + kz + G::D + G::LOE : 0;
+              if (!PIC_CHECK(ix >= 0 && ix < RX && iy >= 0 && iy < RY && iz >= 0 && iz < RZ, ctr)) continue;
+              const int at = ix + RX * (iy + RY * iz);
+              if constexpr (kF32) {
+                // X = qwx wyz 2^K < 2^37 as hi 2^16 + lo, the push's split
+                int hi, lo;
+                if (last) {
+                  hi = hi_t;
+                  lo = lo_t;
+                  const int carry = (lo + 32768) >> 16;  // back to |lo| <= 2^15
+                  hi += carry;
+                  lo -= carry * 65536;
+                } else {
+                  const float y = fmaf(qwx[kx], wyz, WinAcc<float>::kMagicHi);
+                  const float r = y - WinAcc<float>::kMagicHi;
+                  const float lf = fmaf(qwx[kx], wyz, -r);
+                  hi = __float_as_int(y) - __float_as_int(WinAcc<float>::kMagicHi);
+                  lo = __float_as_int(lf + WinAcc<float>::kMagic) - __float_as_int(WinAcc<float>::kMagic);
+                  hi_t -= hi;
+                  lo_t -= lo;
+                }
+                atomicAdd(wlo + at, lo);
+                atomicAdd(wlo + RN + at, hi);
+              } else {
+                atomicAdd(&win[at], (unsigned long long)__double2ll_rn(qwx[kx] * wyz));
+              }
+            } else {
+              double v = (double)qwx[kx] * (double)wyz;
+              if (last) v = v_t;
+              else v_t -= v;
+              const int gi = wrapi(ci[0] + base[0] + kx, n0), gj = wrapi(ci[1] + base[1] + ky, n1);
+              const int gk = DIM == 3 ? wrapi(ci[2] + base[2] + kz, n2) : 0;
+              atomicAdd(rho + gi + (int64_t)n0 * (gj + (int64_t)n1 * gk), v);
+            }
+          }
+        }
+    }
+    __syncthreads();
+    for (int i = tid; i < RN; i += kThreads) {
+      const long long X = kF32 ? (long long)wlo[RN + i] * 65536 + wlo[i] : (long long)win[i];
+      if (X == 0) continue;
+      const int x = i % RX, y = (i / RX) % RY, z = i / (RX * RY);
+      const int gi = wrap_near(t0[0] - G::D - G::LOE + x, n0);
+      const int gj = wrap_near(t0[1] - G::D - G::LOE + y, n1);
+      const int gk = DIM == 3 ? wrap_near(t0[2] - G::D - G::LOE + z, n2) : 0;
+      atomicAdd(rho + gi + (int64_t)n0 * (gj + (int64_t)n1 * gk), (double)X / scale);
+    }
+    __syncthreads();
   }
 }
 
