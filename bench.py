@@ -47,6 +47,14 @@ PUSH_BYTES_PER_CELL = {"fp32": 48, "fp64": 96}
 # capture summarised in profiles/k_push_thermal3d_128.md (128^3 case of the
 # same plasma, scaled by the particle count); None for workloads and
 # precisions not captured, and once the kernel changes.
+# Algorithmic flops of the fused push per particle-step, by (dims, shape
+# order): gather weights and staggered sums, Boris and move, Esirkepov
+# weights, brackets and the products of the full compact stencil (NW = order
+# + 2 nodes per axis, no data-dependent skipping); an FMA counts as 2.  The
+# breakdown is in the design notes (section 5).
+PUSH_FLOPS_PER_PARTICLE = {(3, 2): 1117, (3, 1): 496, (2, 2): 445, (2, 1): 251}
+FP32_LANES_PER_SM = 128  # FP32 FMA lanes per SM
+FP64_NOMINAL_TFLOPS = 1.25  # GB300 FP64 (nominal)
 PUSH_TRAFFIC_PER_PARTICLE = {("thermal3d_256", "fp32"): 62.8, ("thermal3d_128", "fp32"): 62.8}
 
 
@@ -435,6 +443,17 @@ def run_gpu(args, rank: int, world: int, local: int):
     alg_bytes = (npart // max(len(wl.species), 1)) * PUSH_BYTES_PER_PARTICLE[args.precision] + \
         ncell * PUSH_BYTES_PER_CELL[args.precision]
     achieved = alg_bytes / push_avg_s / 1e9
+    # the FP32 ALU roof of the same launch: nominal lanes x max SM clock sampled during the run
+    flops_pp = PUSH_FLOPS_PER_PARTICLE[(wl.dims, wl.order)]
+    nsm = torch.cuda.get_device_properties(local).multi_processor_count
+    sm_max_mhz = (r["clocks"] or {}).get("sm_max_mhz") or 2070.0
+    peak_alu = nsm * FP32_LANES_PER_SM * 2 * sm_max_mhz * 1e6 / 1e12
+    flops_launch = (npart // max(len(wl.species), 1)) * flops_pp
+    achieved_alu = flops_launch / push_avg_s / 1e12
+    if fp64 is not None and "push_ms_per_launch" in fp64:
+        a64 = flops_launch / (fp64["push_ms_per_launch"] / 1e3) / 1e12
+        fp64["alu"] = {"achieved": a64, "peak": FP64_NOMINAL_TFLOPS, "unit": "TFLOP/s",
+                       "frac": a64 / FP64_NOMINAL_TFLOPS, "peak_kind": "nominal GB300 FP64"}
     tim_out = {k: {"ms_total": v[0], "launches": v[1]} for k, v in r["tim"].items() if v[1]}
     line = {
         "metric": "particle-steps/s", "value": value, "unit": "particle-steps/s", "n_gpus": world,
@@ -455,6 +474,13 @@ def run_gpu(args, rank: int, world: int, local: int):
                      "kernel": "k_push (fused gather/Boris/move/Esirkepov)",
                      "peak_kind": f"{peak_kind} HBM copy bandwidth",
                      "bytes_per_launch": alg_bytes, "ms_per_launch": push_avg_s * 1e3},
+        # the same launch against the FP32 ALU roof (by arithmetic intensity the
+        # 3D TSC push is ALU-bound, not HBM-bound)
+        "roofline_alu": {"bound": "alu", "achieved": achieved_alu, "peak": peak_alu, "unit": "TFLOP/s",
+                         "frac": achieved_alu / peak_alu, "flops_per_particle": flops_pp,
+                         "flops_per_launch": flops_launch,
+                         "peak_kind": f"nominal: {nsm} SMs x {FP32_LANES_PER_SM} FP32 lanes x 2 flop x "
+                                      f"{sm_max_mhz:.0f} MHz max SM clock"},
         "kernel_times": tim_out,
         "gpu_launches": int(r["launches"]),
         "clocks": r["clocks"],
