@@ -11,11 +11,14 @@
 // point in FP32 runs), then adds its J window to the global J (one atomic per
 // non-zero value).
 //
-// Particles stream through a 256-slot shared staging chunk: loaded and stored
-// with coalesced accesses in slot order, but processed in a permuted order
-// that gives the 32 lanes of a warp particles eight slots apart.  Slots are
+// Particles stream through a 256-slot shared staging chunk, loaded with
+// coalesced accesses in slot order.  The deposit runs in a permuted order that
+// gives the 32 lanes of a warp particles eight slots apart: slots are
 // cell-sorted, so lanes then sit in different cells and their shared atomics
-// hit different addresses and banks.
+// hit different addresses and banks.  FP32 3D runs gather and push in slot
+// order first (lanes of a warp in a few cells read the same field nodes),
+// write the new state to global memory and leave a deposit job for the
+// permuted phase after a block barrier (see k_push).
 //
 // A particle that has drifted more than D = 1 cell outside its tile since the
 // last sort is not handled here: its slot is appended to an escape list and
