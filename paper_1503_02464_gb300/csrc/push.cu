@@ -175,18 +175,19 @@ template <> struct WinAcc<float> {
   static constexpr float kMagic = 12582912.0f;        // 1.5 * 2^23: ulp 1
   static constexpr float kMagicHi = 824633720832.0f;  // 1.5 * 2^39: ulp 2^16
   // Add the contribution p q (already in units of 2^-K): X = p q is split
-  // into hi 2^16 + lo with FP32 operations only.  The first FMA rounds X to
-  // a multiple of 2^16 (|X| < 2^37, so the sum stays in [2^39, 2^40), where
+  // into hi 2^16 + lo without the FP64 pipe.  The first FMA rounds X to a
+  // multiple of 2^16 (|X| < 2^37, so the sum stays in [2^39, 2^40), where
   // the float spacing is 2^16) and its bit pattern minus the magic's is hi;
-  // the second FMA gives X - hi 2^16 with one rounding, |.| <= 2^15, and the
-  // 2^23 magic rounds that to the integer lo.
+  // the second FMA gives X - hi 2^16 with one rounding, |.| <= 2^15, and a
+  // round-to-nearest conversion gives the integer lo (one instruction where
+  // adding and removing the 1.5 * 2^23 magic took two).
   template <bool kScratch>
   __device__ __forceinline__ void add(int comp, int idx, float p, float q) const {
     const float y = fmaf(p, q, kMagicHi);
     const float r = y - kMagicHi;  // hi 2^16, exact
     const float lf = fmaf(p, q, -r);
     const int hi = __float_as_int(y) - __float_as_int(kMagicHi);
-    const int lo = __float_as_int(lf + kMagic) - __float_as_int(kMagic);
+    const int lo = __float2int_rn(lf);  // round to nearest even, as the 2^23 magic would
     // Both words are added unconditionally: a branch around the pair (or a
     // predicate on it) cost more than the adds.  With kScratch (TSC) a zero
     // contribution goes to the lane's own scratch word instead of the node,
