@@ -131,7 +131,10 @@ typedef struct {
 #define PIC_GATHER_MOMENTUM 0
 #define PIC_GATHER_ENERGY 1
 
-/* FP64 diagnostics (all reductions accumulate in double). */
+/* FP64 diagnostics.  Sums across threads accumulate in double; FP32 runs sum
+ * each thread's terms with compensated FP32 sums, and rho is deposited in
+ * exact fixed point per cell tile (each particle's contributions adding up
+ * to its charge exactly) before the FP64 adds. */
 typedef struct {
   double energy_field;    /* 1/2 sum (E^2 + B^2) dV at the current integer time  */
   double energy_e;        /* electric part                                        */
@@ -151,7 +154,9 @@ typedef struct {
   int64_t step;           /* completed time steps                                 */
 } pic_diag_t;
 
-/* Per-step energy read-back (FP64 sums of storage-precision terms). */
+/* Per-step energy read-back: per-element terms in the storage precision,
+ * summed per thread (FP32 runs: compensated FP32 sums, exact to a few FP32
+ * ulps of the summed magnitudes) and across threads in FP64. */
 typedef struct {
   double energy_e;        /* 1/2 sum E^2 dV                                       */
   double energy_b;        /* 1/2 sum B^2 dV                                       */
