@@ -82,7 +82,15 @@ extern "C" {
  * notes).  Field amplitude a0 (normalised vector potential), Gaussian
  * transverse profile exp(-r^2/waist^2) about (y_center, z_center), sin^2
  * envelope of total length `duration`, carrier frequency 1 (omega_r = omega
- * of the laser).  polarization 1 = E along y, 2 = E along z. */
+ * of the laser).  polarization 1 = E in the x-y plane (E along y at normal
+ * incidence), 2 = E along z.  angle tilts the propagation direction in the
+ * x-y plane to (cos angle, sin angle, 0), |angle| < pi/2: the incoming wave
+ * is a0 A exp(-r^2/waist^2) T(tau) with r the distance from the beam axis
+ * through (0, y_center, z_center), tau = t - x cos(angle) - (y - y0)
+ * sin(angle), y0 the wall edge the tilted fronts reach first (0 for
+ * angle > 0, the box height for angle < 0), and A = cos(angle) on Ey
+ * (polarization 1) or 1 on Ez (polarization 2).  angle = 0 is normal
+ * incidence. */
 typedef struct {
   int enabled;
   double a0;
@@ -91,6 +99,7 @@ typedef struct {
   double y_center;
   double z_center;
   int polarization;
+  double angle;
 } pic_laser;
 
 typedef struct {

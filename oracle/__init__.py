@@ -78,7 +78,7 @@ def _load():
     lib.oracle_smooth.argtypes = [vp, ctypes.c_int]
     lib.oracle_diag.argtypes = [vp, dp]
     lib.oracle_set_boundary.argtypes = [vp, ctypes.c_int]
-    lib.oracle_set_laser.argtypes = [vp, ctypes.c_int] + [ctypes.c_double] * 5 + [ctypes.c_int]
+    lib.oracle_set_laser.argtypes = [vp, ctypes.c_int] + [ctypes.c_double] * 5 + [ctypes.c_int, ctypes.c_double]
     lib.oracle_laser_field.restype = ctypes.c_double
     lib.oracle_laser_field.argtypes = [vp] + [ctypes.c_double] * 4
     _lib = lib
@@ -168,11 +168,11 @@ class OracleSim:
     def set_absorbing_x(self, on: bool = True):
         _load().oracle_set_boundary(self._h, 1 if on else 0)
 
-    def set_laser(self, a0, waist, duration, y_center=None, z_center=None, pol=1):
+    def set_laser(self, a0, waist, duration, y_center=None, z_center=None, pol=1, angle=0.0):
         yc = 0.5 * self.n[1] * self.d[1] if y_center is None else y_center
         zc = 0.5 * self.n[2] * self.d[2] if z_center is None else z_center
         _load().oracle_set_laser(self._h, 1, float(a0), float(waist), float(duration), float(yc), float(zc),
-                                 int(pol))
+                                 int(pol), float(angle))
 
     def laser_field(self, x, y, z, t) -> float:
         return _load().oracle_laser_field(self._h, float(x), float(y), float(z), float(t))

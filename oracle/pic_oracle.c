@@ -83,7 +83,8 @@ typedef struct {
   /* laser entering through x = 0 (section on boundary readings) */
   int laser_on;
   double a0, waist, duration, yc, zc;
-  int pol; /* 1: E along y, 2: E along z */
+  int pol; /* 1: E in the x-y plane (Ey at the wall), 2: E along z */
+  double angle; /* propagation direction (cos angle, sin angle, 0) */
   double *mur_prev; /* previous boundary samples kept by the Mur condition */
   /* gather variant: 0 = the same shape at every Yee location; 1 = one order
    * lower along each axis on which the component sits at a half-integer
@@ -109,10 +110,17 @@ typedef struct {
 
 void oracle_set_boundary(void *h, int absorb_x) { ((orc_sim *)h)->absorb_x = absorb_x; }
 
-/* Laser through x = 0: field a0 exp(-r^2/waist^2) env(t - x) sin(t - x)
- * along y (pol 1) or z (pol 2), env(tau) = sin^2(pi tau / duration) on
- * [0, duration] (carrier frequency 1: times are in 1/omega_laser). */
-void oracle_set_laser(void *h, int on, double a0, double waist, double duration, double yc, double zc, int pol) {
+/* Laser through x = 0, travelling along k = (cos a, sin a, 0) (a = angle,
+ * 0 for normal incidence): a Gaussian beam of waist `waist` about the axis
+ * through (0, yc, zc) along k, times the waveform env(tau) sin(tau),
+ * env(tau) = sin^2(pi tau / duration) on [0, duration] (carrier frequency
+ * 1: times are in 1/omega_laser).  The phase tau = t - k.(x, y - y0) counts
+ * time from the wall edge y0 the tilted fronts reach first (y0 = 0 for
+ * a > 0, the box height for a < 0).  The field is the component tangential
+ * to the wall: along z (pol 2, amplitude a0) or, for E in the x-y plane
+ * (pol 1, E along (-sin a, cos a, 0)), its y component a0 cos a. */
+void oracle_set_laser(void *h, int on, double a0, double waist, double duration, double yc, double zc, int pol,
+                      double angle) {
   orc_sim *s = (orc_sim *)h;
   s->laser_on = on;
   s->a0 = a0;
@@ -121,17 +129,23 @@ void oracle_set_laser(void *h, int on, double a0, double waist, double duration,
   s->yc = yc;
   s->zc = zc;
   s->pol = pol;
+  s->angle = angle;
 }
 
 /* Incoming laser field at (x, y, z, t) for the polarised component. */
 double oracle_laser_field(void *h, double x, double y, double z, double t) {
   orc_sim *s = (orc_sim *)h;
   if (!s->laser_on) return 0.0;
-  double tau = t - x;
+  double ca = cos(s->angle), sa = sin(s->angle);
+  double y0 = s->angle > 0.0 ? 0.0 : s->n[1] * s->d[1];
+  double tau = t - (x * ca + (y - y0) * sa);
   if (tau <= 0.0 || tau >= s->duration) return 0.0;
   double env = sin(M_PI * tau / s->duration);
-  double r2 = (y - s->yc) * (y - s->yc) + (s->dims == 3 ? (z - s->zc) * (z - s->zc) : 0.0);
-  return s->a0 * exp(-r2 / (s->waist * s->waist)) * env * env * sin(tau);
+  /* distance from the beam axis: the part of (x, y - yc, z - zc) across k */
+  double across = (y - s->yc) * ca - x * sa;
+  double r2 = across * across + (s->dims == 3 ? (z - s->zc) * (z - s->zc) : 0.0);
+  double amp = s->pol == 1 ? s->a0 * ca : s->a0;
+  return amp * exp(-r2 / (s->waist * s->waist)) * env * env * sin(tau);
 }
 
 /* ------------------------------------------------------------------ */

@@ -35,7 +35,7 @@ EXPORTED = ["pic_create", "pic_destroy", "pic_last_error", "pic_add_species", "p
 class pic_laser(ctypes.Structure):
     _fields_ = [("enabled", ctypes.c_int), ("a0", ctypes.c_double), ("waist", ctypes.c_double),
                 ("duration", ctypes.c_double), ("y_center", ctypes.c_double), ("z_center", ctypes.c_double),
-                ("polarization", ctypes.c_int)]
+                ("polarization", ctypes.c_int), ("angle", ctypes.c_double)]
 
 
 class pic_config(ctypes.Structure):

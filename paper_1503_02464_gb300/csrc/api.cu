@@ -381,8 +381,8 @@ int pic_create(const pic_config *cfg, pic_handle **out) {
   if (c.laser.enabled) {
     if (!absorb) return fail(nullptr, PIC_EINVAL, "the laser enters through an absorbing x = 0 wall");
     if (!(c.laser.duration > 0) || !(c.laser.waist > 0) || (c.laser.polarization != 1 && c.laser.polarization != 2) ||
-        (c.dims == 2 && c.laser.polarization == 2 && false))
-      return fail(nullptr, PIC_EINVAL, "bad laser parameters");
+        !(fabs(c.laser.angle) < 0.5 * 3.14159265358979323846))
+      return fail(nullptr, PIC_EINVAL, "bad laser parameters (duration, waist > 0; polarization 1 or 2; |angle| < pi/2)");
   }
   if (c.dims == 2 && c.n[2] != 1 && c.n[2] != 0) return fail(nullptr, PIC_EINVAL, "2D needs n[2] = 1");
   if (c.filter_passes < 0 || c.filter_passes > 8 || (c.filter_compensate != 0 && c.filter_compensate != 1))
@@ -441,6 +441,7 @@ int pic_create(const pic_config *cfg, pic_handle **out) {
   h->laser.yc = c.laser.y_center;
   h->laser.zc = c.laser.z_center;
   h->laser.pol = c.laser.polarization;
+  h->laser.angle = c.laser.enabled ? c.laser.angle : 0.0;
   h->st = static_cast<cudaStream_t>(c.stream);
 
   int dev = 0;
@@ -802,7 +803,7 @@ namespace {
 struct StateHeader {
   char magic[8];
   int32_t version, dims, n[3], order, prec, nsp, bc_lo0, bc_hi0, laser_on, filter_passes, filter_comp, gather, pad;
-  double dx[3], dt, laser_a0, laser_waist, laser_duration;
+  double dx[3], dt, laser_a0, laser_waist, laser_duration, laser_angle;
   int64_t step, ncell;
   int64_t slots[kMaxSpecies], count[kMaxSpecies];
   double q[kMaxSpecies], m[kMaxSpecies];
@@ -814,7 +815,7 @@ StateHeader state_header(pic_handle *h) {
   StateHeader hd;
   memset(&hd, 0, sizeof hd);
   memcpy(hd.magic, kStateMagic, 8);
-  hd.version = 1;
+  hd.version = 2;
   hd.dims = h->g.dims;
   for (int d = 0; d < 3; ++d) {
     hd.n[d] = h->g.n[d];
@@ -833,6 +834,7 @@ StateHeader state_header(pic_handle *h) {
   hd.laser_a0 = h->laser.enabled ? h->laser.a0 : 0.0;
   hd.laser_waist = h->laser.enabled ? h->laser.waist : 0.0;
   hd.laser_duration = h->laser.enabled ? h->laser.duration : 0.0;
+  hd.laser_angle = h->laser.enabled ? h->laser.angle : 0.0;
   hd.step = h->step;
   hd.ncell = h->g.ncell;
   for (int i = 0; i < h->nsp; ++i) {
@@ -906,7 +908,7 @@ int pic_state_load(pic_handle *h, const void *buf, int64_t bytes, int mem_kind) 
               hd.bc_hi0 == me.bc_hi0 && hd.laser_on == me.laser_on && hd.filter_passes == me.filter_passes &&
               hd.filter_comp == me.filter_comp && hd.gather == me.gather && hd.dt == me.dt &&
               hd.laser_a0 == me.laser_a0 && hd.laser_waist == me.laser_waist &&
-              hd.laser_duration == me.laser_duration && hd.ncell == me.ncell;
+              hd.laser_duration == me.laser_duration && hd.laser_angle == me.laser_angle && hd.ncell == me.ncell;
   for (int d = 0; d < 3; ++d) same = same && hd.n[d] == me.n[d] && hd.dx[d] == me.dx[d];
   for (int i = 0; i < me.nsp && same; ++i)
     same = hd.slots[i] == me.slots[i] && hd.q[i] == me.q[i] && hd.m[i] == me.m[i] && hd.count[i] >= 0 &&
@@ -1126,7 +1128,7 @@ int pic_step(pic_handle *h, int nsteps) {
       Timed tm(h, pic::KC_BOUNDARY);
       CK(h,
          pic::launch_mur_apply(h->g, h->E, h->mur,
-                               pic::laser_step(h->laser, h->laser_prof, h->laser.a0, h->g.dx[0], h->step * h->g.dt,
+                               pic::laser_step(h->laser, h->laser_prof, h->laser.a0, h->g, h->step * h->g.dt,
                                                (h->step + 1) * h->g.dt),
                                h->st),
          "mur apply");
@@ -1386,6 +1388,8 @@ int pic_adjoint_begin(pic_handle *h, int64_t id_capacity) {
     return fail(h, PIC_EINVAL, "adjoint kernels exist for 2D3V with the TSC shape only");
   if (h->cfg.filter_passes > 0 || h->cfg.gather != PIC_GATHER_MOMENTUM)
     return fail(h, PIC_EINVAL, "adjoint kernels cover the unfiltered momentum-conserving cycle only");
+  if (h->laser.enabled && h->laser.angle != 0.0)
+    return fail(h, PIC_EINVAL, "adjoint kernels cover a laser at normal incidence only");
   if (id_capacity <= 0 || id_capacity > 0x7fffffffLL) return fail(h, PIC_EINVAL, "bad id capacity");
   if (!h->adj_ready || h->id_cap != id_capacity) {
     free_adjoint(h);
@@ -1466,7 +1470,7 @@ int pic_adjoint_step(pic_handle *h, int nsteps) {
       if (walls)
         CK(h,
            pic::launch_adj_mur(h->g, h->lE, h->pend,
-                               pic::laser_step(h->laser, h->laser_prof, 1.0, h->g.dx[0], t_old, t_new), h->da0, h->st),
+                               pic::laser_step(h->laser, h->laser_prof, 1.0, h->g, t_old, t_new), h->da0, h->st),
            "adjoint Mur");
       CK(h, pic::launch_adj_yee_e(h->g, h->lE, h->lB, h->lJ, h->g.dt, h->st), "adjoint E");
       if (walls) CK(h, pic::launch_adj_mur_pend(h->g, h->lE, h->pend, h->st), "adjoint Mur");

@@ -113,8 +113,24 @@ __global__ void k_mur_apply(int n0, int n1, int n2, double dx, double dt, R *Ey,
     const int64_t jk = q % nyz;
     R *E = c == 0 ? Ey : Ez;
     const double *o = buf + (int64_t)c * 4 * nyz;
-    const double p = ls.pol == c + 1 ? ls.prof[jk] : 0.0;
-    const double l0o = p * ls.amp[0], l1o = p * ls.amp[1], l0n = p * ls.amp[2], l1n = p * ls.amp[3];
+    double l0o = 0.0, l1o = 0.0, l0n = 0.0, l1n = 0.0;
+    if (ls.pol == c + 1) {
+      if (ls.oblique) {
+        // the wall row's own delay and profile (Ey rows at (j + 1/2, k), Ez rows at (j, k + 1/2))
+        const int j = (int)(jk % n1), k = (int)(jk / n1);
+        const double y = (j + (c == 0 ? 0.5 : 0.0)) * ls.dy, z = (k + (c == 1 ? 0.5 : 0.0)) * ls.dz;
+        l0o = laser_wave(ls, 0.0, y, z, ls.t_old);
+        l1o = laser_wave(ls, ls.dx, y, z, ls.t_old);
+        l0n = laser_wave(ls, 0.0, y, z, ls.t_new);
+        l1n = laser_wave(ls, ls.dx, y, z, ls.t_new);
+      } else {
+        const double p = ls.prof[jk];
+        l0o = p * ls.amp[0];
+        l1o = p * ls.amp[1];
+        l0n = p * ls.amp[2];
+        l1n = p * ls.amp[3];
+      }
+    }
     const int64_t row = (int64_t)n0 * jk;
     const double s0o = o[0 * nyz + jk] - l0o;
     const double s1o = o[1 * nyz + jk] - l1o;
@@ -480,14 +496,33 @@ double laser_waveform(const Laser &L, double tau) {
   return env * env * sin(tau);
 }
 
-LaserStep laser_step(const Laser &L, const double *prof, double amplitude, double dx, double t_old, double t_new) {
-  LaserStep ls;
+LaserStep laser_step(const Laser &L, const double *prof, double amplitude, const Grid &g, double t_old, double t_new) {
+  LaserStep ls{};
+  const double dx = g.dx[0];
   ls.pol = L.enabled ? L.pol : 0;
   ls.prof = prof;
   ls.amp[0] = amplitude * laser_waveform(L, t_old);
   ls.amp[1] = amplitude * laser_waveform(L, t_old - dx);
   ls.amp[2] = amplitude * laser_waveform(L, t_new);
   ls.amp[3] = amplitude * laser_waveform(L, t_new - dx);
+  ls.oblique = L.enabled && L.angle != 0.0;
+  if (ls.oblique) {
+    ls.dims = g.dims;
+    ls.cos_t = cos(L.angle);
+    ls.sin_t = sin(L.angle);
+    // E in the x-y plane: its y component is cos(angle) of the amplitude
+    ls.a = amplitude * (L.pol == 1 ? ls.cos_t : 1.0);
+    ls.y0 = L.angle > 0.0 ? 0.0 : g.n[1] * g.dx[1];  // the wall edge the tilted fronts reach first
+    ls.yc = L.yc;
+    ls.zc = L.zc;
+    ls.inv_w2 = 1.0 / (L.waist * L.waist);
+    ls.duration = L.duration;
+    ls.t_old = t_old;
+    ls.t_new = t_new;
+    ls.dx = dx;
+    ls.dy = g.dx[1];
+    ls.dz = g.dx[2];
+  }
   return ls;
 }
 

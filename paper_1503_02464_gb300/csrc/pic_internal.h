@@ -26,31 +26,49 @@ struct Grid {
   int gather_ec;             // energy-conserving gather (lower order at half-integer positions)
 };
 
-// Laser entering through the x = 0 wall (copied from pic_config).  Its
-// polarised field is a0 P(y, z) T(t - x): the transverse profile
-// P = exp(-r^2 / waist^2), r measured from the spot centre (yc, zc), times
-// the waveform T(tau) = sin^2(pi tau / duration) sin(tau) on 0 < tau <
-// duration (carrier frequency 1), 0 elsewhere.
+// Laser entering through the x = 0 wall (copied from pic_config).  At normal
+// incidence its polarised field is a0 P(y, z) T(t - x): the transverse
+// profile P = exp(-r^2 / waist^2), r measured from the spot centre (yc, zc),
+// times the waveform T(tau) = sin^2(pi tau / duration) sin(tau) on
+// 0 < tau < duration (carrier frequency 1), 0 elsewhere.  A tilt `angle` in
+// the x-y plane delays the wall rows along y and tilts the profile with the
+// beam axis (laser_wave).
 struct Laser {
   int enabled;
   double a0, waist, duration, yc, zc;
-  int pol;  // 1: E along y, 2: E along z
+  int pol;       // 1: E in the x-y plane (Ey at the wall), 2: E along z
+  double angle;  // propagation direction (cos, sin, 0) in the x-y plane
 };
 
 // The waveform T(tau) (host).
 double laser_waveform(const Laser &L, double tau);
 
-// What the Mur kernels need of the laser for one step from t_old to t_new:
-// amp = {T(t_old), T(t_old - dx), T(t_new), T(t_new - dx)} times the
-// amplitude (a0 for the forward update, 1 for the adjoint's dF/da0), and
-// prof = P at the wall rows of the polarised component (n1 * n2 doubles:
-// Ey rows at (j + 1/2, k), Ez rows at (j, k + 1/2)); pol = 0: no laser.
+// What the Mur kernels need of the laser for one step from t_old to t_new.
+// Normal incidence: amp = {T(t_old), T(t_old - dx), T(t_new), T(t_new - dx)}
+// times the amplitude (a0 for the forward update, 1 for the adjoint's
+// dF/da0), and prof = P at the wall rows of the polarised component (n1 * n2
+// doubles: Ey rows at (j + 1/2, k), Ez rows at (j, k + 1/2)); pol = 0: no
+// laser.  Oblique incidence (oblique = 1): the wave's delay and profile vary
+// along the wall, so the kernel evaluates it per row from the parameters
+// below (laser_wave).
 struct LaserStep {
   int pol;
   double amp[4];
   const double *prof;
+  int oblique, dims;
+  double a, cos_t, sin_t, y0, yc, zc, inv_w2, duration, t_old, t_new, dx, dy, dz;
 };
-LaserStep laser_step(const Laser &L, const double *prof, double amplitude, double dx, double t_old, double t_new);
+LaserStep laser_step(const Laser &L, const double *prof, double amplitude, const Grid &g, double t_old, double t_new);
+
+// The incoming oblique wave's polarised component at (x, y, z, t) (device).
+__host__ __device__ inline double laser_wave(const LaserStep &ls, double x, double y, double z, double t) {
+  const double tau = t - x * ls.cos_t - (y - ls.y0) * ls.sin_t;
+  if (tau <= 0.0 || tau >= ls.duration) return 0.0;
+  const double env = sin(3.14159265358979323846 * tau / ls.duration);
+  const double rp = (y - ls.yc) * ls.cos_t - x * ls.sin_t;  // distance from the beam axis in the x-y plane
+  const double r2 = rp * rp + (ls.dims == 3 ? (z - ls.zc) * (z - ls.zc) : 0.0);
+  return ls.a * exp(-r2 * ls.inv_w2) * env * env * sin(tau);
+}
 
 // Particles whose new position leaves [kWallLo, n0 - kWallHiMargin) cells in
 // x are removed at absorbing walls (after depositing their move).

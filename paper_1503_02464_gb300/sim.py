@@ -59,6 +59,7 @@ def make_config(dims: int, n, d, dt: float, order: int, precision: str = "fp32",
         cfg.laser.y_center = float(laser.get("y_center", 0.5 * nn[1] * dd[1]))
         cfg.laser.z_center = float(laser.get("z_center", 0.5 * nn[2] * dd[2]))
         cfg.laser.polarization = int(laser.get("pol", 1))
+        cfg.laser.angle = float(laser.get("angle", 0.0))
     cfg.stream = stream
     cfg.filter_passes = int(filter_passes)
     cfg.filter_compensate = 1 if filter_compensate else 0

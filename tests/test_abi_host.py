@@ -77,3 +77,38 @@ def test_create_fails_loudly_without_device(lib):
     h = ctypes.c_void_p()
     rc = lib.pic_create(ctypes.byref(cfg), ctypes.byref(h))
     assert rc == 4
+
+
+def test_struct_layouts_match_header(tmp_path):
+    """Every struct the binding mirrors has the size and field offsets the C
+    compiler gives it from include/pic.h (a field added on one side only
+    shifts everything after it)."""
+    import shutil
+    import subprocess
+    from paper_1503_02464_gb300 import capi
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if cc is None:
+        pytest.skip("no C compiler")
+    structs = [capi.pic_laser, capi.pic_config, capi.pic_output_t, capi.pic_diag_t, capi.pic_energy_t]
+    lines = ["#include <stdio.h>", "#include <stddef.h>", '#include "pic.h"', "int main(void) {"]
+    for st in structs:
+        name = st.__name__
+        lines.append(f'  printf("{name} size %zu\\n", sizeof({name}));')
+        for field, _ in st._fields_:
+            lines.append(f'  printf("{name} {field} %zu\\n", offsetof({name}, {field}));')
+    lines += ["  return 0;", "}"]
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines) + "\n")
+    exe = tmp_path / "layout"
+    subprocess.run([cc, "-std=c99", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)], check=True)
+    out = subprocess.run([str(exe)], check=True, capture_output=True, text=True).stdout.split("\n")
+    got = {}
+    for ln in out:
+        parts = ln.split()
+        if len(parts) == 3:
+            got[(parts[0], parts[1])] = int(parts[2])
+    for st in structs:
+        name = st.__name__
+        assert got[(name, "size")] == ctypes.sizeof(st), name
+        for field, _ in st._fields_:
+            assert got[(name, field)] == getattr(st, field).offset, (name, field)

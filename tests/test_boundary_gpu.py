@@ -20,7 +20,7 @@ pytestmark = pytest.mark.gpu
 TAU = 2 * math.pi
 
 
-def _laser_slab(dims, nx, ny, nz=1, d=0.1, a0=2.0, slab=(20, 28), ppc=2, density=4.0, order=2):
+def _laser_slab(dims, nx, ny, nz=1, d=0.1, a0=2.0, slab=(20, 28), ppc=2, density=4.0, order=2, angle=0.0, pol=1):
     dd = (d, d, d if dims == 3 else 1.0)
     dt = 0.9 * synth.courant_limit(dd, dims)
     n = (nx, ny, nz if dims == 3 else 1)
@@ -28,7 +28,7 @@ def _laser_slab(dims, nx, ny, nz=1, d=0.1, a0=2.0, slab=(20, 28), ppc=2, density
                         [synth.Species("electron", -1.0, 1.0, ppc, 0.0, density, slab, 0),
                          synth.Species("proton", 1.0, 1836.0, ppc, 0.0, density, slab, 1)],
                         absorbing_x=True, neutralize=False,
-                        laser={"a0": a0, "waist": 0.25 * ny * d, "duration": TAU, "pol": 1})
+                        laser={"a0": a0, "waist": 0.25 * ny * d, "duration": TAU, "pol": pol, "angle": angle})
     return wl
 
 
@@ -38,7 +38,7 @@ def _pair(wl, precision):
     o = oracle.OracleSim(wl.dims, wl.n, wl.d, wl.dt, wl.order)
     o.set_absorbing_x(True)
     L = wl.laser
-    o.set_laser(L["a0"], L["waist"], L["duration"], pol=L["pol"])
+    o.set_laser(L["a0"], L["waist"], L["duration"], pol=L["pol"], angle=L.get("angle", 0.0))
     s = Simulation.from_workload(wl, precision=precision)
     parts = []
     for isp, sp in enumerate(wl.species):
@@ -104,6 +104,74 @@ def test_laser_slab_fp32(dims, order):
         assert v <= 1e-5, (k, v)
     du, _ = compare_particles(o, s, wl, 0)
     assert du <= 1e-4, du
+
+
+OBLIQUE = [(2, 1, math.radians(20.0)), (2, 2, math.radians(-15.0)), (3, 1, math.radians(25.0)),
+           (3, 2, math.radians(-20.0))]
+
+
+@pytest.mark.parametrize("dims,pol,angle", OBLIQUE)
+def test_oblique_laser_slab_fp64(dims, pol, angle):
+    """A laser tilted in the x-y plane: each wall row carries its own delay
+    and profile, evaluated on the device; FP64 parity per step."""
+    if dims == 3:
+        wl = _laser_slab(3, 64, 16, 8, slab=(10, 16), angle=angle, pol=pol)
+    else:
+        wl = _laser_slab(2, 96, 24, angle=angle, pol=pol)
+    o, s, jf = _pair(wl, "fp64")
+    nsteps = 40 if dims == 3 else 80
+    for step in range(1, nsteps + 1):
+        o.step(1)
+        s.step(1)
+        if step % 10 == 0:
+            fe = compare_fields(o, s, j_abs=jf)
+            for k, v in fe.items():
+                assert v <= 1e-12 * step, (step, k, v)
+            emax = max(np.abs(o.get_field(c)).max() for c in range(3))
+            for isp, sp in enumerate(wl.species):
+                us = abs(sp.q) / sp.m * emax * wl.dt * step
+                du, dx = compare_particles(o, s, wl, isp, u_scale=us)
+                assert du <= 1e-12 * step, (step, isp, du)
+    # the tilted wave reached the slab and pushed electrons (along z for s-polarisation)
+    p0 = s.particles(0)
+    assert max(np.abs(p0[k]).max() for k in ("ux", "uy", "uz")) > 1e-3
+    comp = 1 if pol == 1 else 2
+    wall = s.field(comp)[0, :, 1] if dims == 2 else s.field(comp)[wl.n[2] // 2, :, 1]
+    assert np.abs(wall).max() > 0
+
+
+@pytest.mark.parametrize("dims", [2, 3])
+def test_oblique_laser_slab_fp32(dims):
+    angle = math.radians(20.0)
+    if dims == 2:
+        wl = _laser_slab(2, 96, 24, angle=angle)
+        before = 50
+    else:
+        wl = _laser_slab(3, 64, 16, 8, slab=(10, 16), angle=angle)
+        before = 20
+    o, s, _ = _pair(wl, "fp32")
+    o.step(before)
+    s.step(before)
+    o.step(10)
+    s.step(10)
+    fe = compare_fields(o, s, ["Ex", "Ey", "Ez", "Bx", "By", "Bz"])
+    for k, v in fe.items():
+        assert v <= 1e-5, (k, v)
+    du, _ = compare_particles(o, s, wl, 0)
+    assert du <= 1e-4, du
+
+
+def test_oblique_laser_limits():
+    """|angle| must stay below pi/2, and the adjoint covers normal incidence only."""
+    from paper_1503_02464_gb300 import capi
+    wl = _laser_slab(2, 96, 24, angle=0.5 * math.pi)
+    with pytest.raises(capi.PicError):
+        Simulation.from_workload(wl, precision="fp64")
+    wl = _laser_slab(2, 96, 24, angle=0.3)
+    s = Simulation.from_workload(wl, precision="fp64")
+    with pytest.raises(capi.PicError):
+        s.adjoint_begin(16)
+    s.close()
 
 
 @pytest.mark.parametrize("precision", ["fp64", "fp32"])
