@@ -128,6 +128,9 @@ class Species:
     drift: tuple = (0.0, 0.0, 0.0)      # mean momentum u added to every particle
     lattice: Optional[tuple] = None     # quiet start: sub-lattice points per axis
     perturb: Optional[tuple] = None     # quiet start: (mode, ax, phase_x, au, phase_u)
+    # density structure inside x_range (see structure_mask): None (uniform),
+    # ("grating", period, depth) or ("foam", fill, seed)
+    structure: Optional[tuple] = None
 
 
 @dataclass
@@ -156,10 +159,14 @@ class Workload:
         nx, ny = self.n[0], self.n[1]
         nz = self.n[2] if self.dims == 3 else 1
         if sp.x_range is None:
-            return np.arange(nx * ny * nz, dtype=np.int64)
-        i = np.arange(sp.x_range[0], sp.x_range[1])
-        jk = np.arange(ny * nz)
-        return (i[None, :] + nx * jk[:, None]).reshape(-1)
+            cells = np.arange(nx * ny * nz, dtype=np.int64)
+        else:
+            i = np.arange(sp.x_range[0], sp.x_range[1])
+            jk = np.arange(ny * nz)
+            cells = (i[None, :] + nx * jk[:, None]).reshape(-1)
+        if sp.structure is not None:
+            cells = cells[structure_mask(sp.structure, cells, self.n, sp.x_range)]
+        return cells
 
     def n_particles(self) -> int:
         return sum(int(self.species_cells(s).size) * s.ppc for s in self.species)
@@ -171,6 +178,42 @@ class Workload:
         return particles_for_cells(cells, self.n, self.d, sp.ppc, sp.u_th, sp.density,
                                    self.seed * 1000 + sp.seed_offset, self.dims, sp.drift, sp.lattice,
                                    sp.perturb)
+
+
+def structure_mask(structure: tuple, cells: np.ndarray, n: Sequence[int], x_range) -> np.ndarray:
+    """Which of the listed cells (row-major linear indices) a structured
+    target fills.  The paper shows structured targets (foams, gratings) but
+    gives no specification, so these are generic shapes:
+
+    ("grating", period, depth): the target's front surface is modulated
+    along y, x_front(j) = x0 + floor(depth (1 + sin(2 pi (j + 1/2) / period)) / 2)
+    cells, x0 the first column of x_range; cells in front of it are empty.
+
+    ("foam", fill, seed): each cell is filled with probability `fill`, drawn
+    once per cell from Philox (key `seed`, counter 2 * cell), so any subset
+    of cells gets the same mask.
+    """
+    cells = np.asarray(cells, dtype=np.int64)
+    kind = structure[0]
+    nx, ny = int(n[0]), int(n[1])
+    if kind == "grating":
+        period, depth = float(structure[1]), float(structure[2])
+        x0 = x_range[0] if x_range is not None else 0
+        i = cells % nx
+        j = (cells // nx) % ny
+        front = x0 + np.floor(depth * (1.0 + np.sin(TWO_PI * (j + 0.5) / period)) / 2.0).astype(np.int64)
+        return i >= front
+    if kind == "foam":
+        fill, seed = float(structure[1]), int(structure[2])
+        u = np.empty(cells.size)
+        if cells.size:
+            breaks = np.nonzero(np.diff(cells) != 1)[0] + 1
+            starts = np.concatenate([[0], breaks])
+            ends = np.concatenate([breaks, [cells.size]])
+            for a, b in zip(starts, ends):
+                u[a:b] = philox_uniforms(seed, int(cells[a]), int(b - a))[:, 0]
+        return u < fill
+    raise ValueError(f"unknown target structure {kind!r}")
 
 
 def courant_limit(d: Sequence[float], dims: int) -> float:
@@ -186,6 +229,10 @@ _NOTES = {
     "laser_foil3d": "3D3V linearly polarised laser on a thin electron-proton foil, absorbing x, TSC",
     "twostream3d_512": "3D3V two counter-streaming electron beams (u=+-0.2 along x) over immobile ions, "
                        "periodic, TSC (the paper's scaling test problem)",
+    "grating_foil2d": "2D3V p-polarised laser at 30 degrees on a grating-fronted electron-proton foil, "
+                      "absorbing x, TSC (generic grating: the paper gives no target specification)",
+    "foam_foil2d": "2D3V laser on a near-critical foam layer (cells filled at random) in front of a dense foil, "
+                   "absorbing x, TSC (generic foam: the paper gives no target specification)",
 }
 
 
@@ -227,6 +274,32 @@ def _preset(name: str) -> Workload:
                          Species("proton", 1.0, 1836.0, 27, 0.0, 50.0, (256, 276), 0)],
                         absorbing_x=True, neutralize=False,
                         laser={"a0": 10.0, "waist": 2 * lam, "duration": 8 * lam, "pol": 1})
+    if name == "grating_foil2d":
+        # foil 40 cells (0.8 lambda) thick at 40 n_c, front surface a sine
+        # grating of period 1 lambda (50 cells) and depth 0.2 lambda
+        d = 0.02 * lam
+        dt = 0.9 * courant_limit((d, d), 2)
+        grating = ("grating", 50, 10)
+        return Workload(name, 2, (1024, 512, 1), (d, d, 1.0), dt, 2, 2000, 1007,
+                        [Species("electron", -1.0, 1.0, 16, 0.0, 40.0, (512, 552), 0, structure=grating),
+                         Species("proton", 1.0, 1836.0, 16, 0.0, 40.0, (512, 552), 0, structure=grating)],
+                        absorbing_x=True, neutralize=False,
+                        laser={"a0": 3.0, "waist": 3 * lam, "duration": 10 * lam, "pol": 1,
+                               "angle": math.radians(30.0)})
+    if name == "foam_foil2d":
+        # a foam layer 2.2 lambda thick whose cells are filled with
+        # probability 1/4 at 5 n_c (1.25 n_c on average), then a 0.4 lambda
+        # foil at 40 n_c
+        d = 0.02 * lam
+        dt = 0.9 * courant_limit((d, d), 2)
+        foam = ("foam", 0.25, 4242)
+        return Workload(name, 2, (1024, 512, 1), (d, d, 1.0), dt, 2, 2000, 1008,
+                        [Species("foam_e", -1.0, 1.0, 16, 0.0, 5.0, (400, 512), 0, structure=foam),
+                         Species("foam_p", 1.0, 1836.0, 16, 0.0, 5.0, (400, 512), 0, structure=foam),
+                         Species("foil_e", -1.0, 1.0, 16, 0.0, 40.0, (512, 532), 1),
+                         Species("foil_p", 1.0, 1836.0, 16, 0.0, 40.0, (512, 532), 1)],
+                        absorbing_x=True, neutralize=False,
+                        laser={"a0": 5.0, "waist": 3 * lam, "duration": 10 * lam, "pol": 1})
     if name == "twostream3d_512":
         # the two-stream problem of the paper's scaling runs: 512x512x128
         # cells, 54 ppc (two counter-streaming electron beams of 27 ppc each,

@@ -161,6 +161,34 @@ def test_oblique_laser_slab_fp32(dims):
     assert du <= 1e-4, du
 
 
+@pytest.mark.parametrize("structure", [("grating", 12, 4), ("foam", 0.4, 99)], ids=["grating", "foam"])
+def test_structured_target_fp64(structure):
+    """A laser at 30 degrees on a structured target (a grating front or a
+    randomly filled foam): FP64 parity per step."""
+    d = 0.1
+    dt = 0.9 * synth.courant_limit((d, d), 2)
+    species = [synth.Species("electron", -1.0, 1.0, 2, 0.0, 4.0, (20, 30), 0, structure=structure),
+               synth.Species("proton", 1.0, 1836.0, 2, 0.0, 4.0, (20, 30), 0, structure=structure)]
+    wl = synth.Workload("target_small", 2, (96, 48, 1), (d, d, 1.0), dt, 2, 60, 91, species, absorbing_x=True,
+                        neutralize=False, laser={"a0": 2.0, "waist": 1.2, "duration": TAU, "pol": 1,
+                                                 "angle": math.radians(30.0)})
+    o, s, jf = _pair(wl, "fp64")
+    for step in range(1, 61):
+        o.step(1)
+        s.step(1)
+        if step % 10 == 0:
+            fe = compare_fields(o, s, j_abs=jf)
+            for k, v in fe.items():
+                assert v <= 1e-12 * step, (step, k, v)
+            emax = max(np.abs(o.get_field(c)).max() for c in range(3))
+            for isp, sp in enumerate(wl.species):
+                us = abs(sp.q) / sp.m * emax * wl.dt * step
+                du, dx = compare_particles(o, s, wl, isp, u_scale=us)
+                assert du <= 1e-12 * step, (step, isp, du)
+    p0 = s.particles(0)
+    assert max(np.abs(p0[k]).max() for k in ("ux", "uy")) > 1e-3
+
+
 def test_oblique_laser_limits():
     """|angle| must stay below pi/2, and the adjoint covers normal incidence only."""
     from paper_1503_02464_gb300 import capi
