@@ -17,7 +17,6 @@ from __future__ import annotations
 import ctypes
 import os
 import subprocess
-import sys
 
 import numpy as np
 

@@ -8,7 +8,7 @@ import pytest
 
 import oracle
 from oracle import OracleSim
-from paper_1503_02464_gb300 import capi, synth
+from paper_1503_02464_gb300 import synth
 from paper_1503_02464_gb300.sim import Simulation
 
 from _parity import compare_fields, compare_particles, j_floor
