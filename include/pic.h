@@ -266,11 +266,13 @@ int pic_energy(pic_handle *h, pic_energy_t *out);
 int pic_sync(pic_handle *h);
 
 /* Per-kernel timing with CUDA events on the simulation stream.  enable = 1
- * starts recording (clearing previous records).  pic_timings synchronises
- * and writes, for up to nmax kernel classes, total milliseconds and launch
- * counts; class order: 0 sort, 1 zero J, 2 push, 3 Yee B, 4 Yee E,
- * 5 boundary, 6 current smoothing, 7 adjoint field updates, 8 adjoint
- * particle kernel.  Returns the number of classes written in *ncls. */
+ * starts recording (clearing previous records), 0 stops.  pic_timings
+ * synchronises and writes, for up to nmax kernel classes, total milliseconds
+ * (ms) and launch counts (launches) into caller-owned arrays of nmax
+ * entries (either may be NULL); class order: 0 sort, 1 zero J, 2 push,
+ * 3 Yee B, 4 Yee E, 5 boundary, 6 current smoothing, 7 adjoint field
+ * updates, 8 adjoint particle kernel.  The number of classes written goes
+ * to *ncls (NULL allowed).  PIC_EINVAL for a NULL handle. */
 int pic_profile(pic_handle *h, int enable);
 int pic_timings(pic_handle *h, double *ms, int64_t *launches, int nmax, int *ncls);
 
@@ -290,8 +292,10 @@ int pic_launch_count(pic_handle *h, int64_t *count);
  * added so far; add all species first. */
 
 /* Save (restore) the full state -- fields, particles of every species, step
- * count -- in slot `slot` (0..4096; device memory allocated on first use).
- * pic_restore marks the species for a sort at the next step. */
+ * count -- in slot `slot` (0..4096; device memory, owned by the handle,
+ * allocated on first use).  pic_restore marks the species for a sort at the
+ * next step; it returns PIC_EINVAL for a slot never saved, PIC_ENOMEM when
+ * pic_checkpoint cannot allocate the slot. */
 int pic_checkpoint(pic_handle *h, int slot);
 int pic_restore(pic_handle *h, int slot);
 
@@ -329,7 +333,8 @@ int pic_grad(pic_handle *h, double *d_a0, int species, double *d_w, int mem_kind
  * mass, capacity) added in the same order.  Output requests, checkpoints and
  * adjoint state are not part of it. */
 
-/* Bytes of the state blob of this handle. */
+/* Bytes of the state blob of this handle (header, fields, every species'
+ * storage, counters) into *bytes.  PIC_EINVAL for a NULL argument. */
 int pic_state_size(pic_handle *h, int64_t *bytes);
 
 /* Write the state into buf (host or device memory per mem_kind, `bytes` =
