@@ -169,19 +169,31 @@ def run_reference(args, rank: int, world: int):
 
 
 # --------------------------------------------------------------------------- GPU arm
+def parse_cpulist(spec: str) -> set:
+    """CPUs of a sysfs list such as "0-3,8,10-11"."""
+    cpus = set()
+    for part in spec.strip().split(","):
+        if not part:
+            continue
+        a, _, b = part.partition("-")
+        cpus.update(range(int(a), int(b or a) + 1))
+    return cpus
+
+
+def pci_sysfs_name(bus_id: str) -> str:
+    """sysfs device name of an nvidia-smi PCI bus id ("00000009:01:00.0" ->
+    "0009:01:00.0")."""
+    dom, rest = bus_id.strip().split(":", 1)
+    return f"{int(dom, 16):04x}:{rest.lower()}"
+
+
 def _gpu_local_cpus(gpu: int):
     """CPUs on the NUMA node of the GPU (from sysfs), or None."""
     try:
         bus = subprocess.run(["nvidia-smi", "-i", str(gpu), "--query-gpu=pci.bus_id", "--format=csv,noheader"],
-                             capture_output=True, text=True, timeout=30).stdout.strip()
-        dom, rest = bus.split(":", 1)
-        with open(f"/sys/bus/pci/devices/{int(dom, 16):04x}:{rest.lower()}/local_cpulist") as f:
-            spec = f.read().strip()
-        cpus = set()
-        for part in spec.split(","):
-            a, _, b = part.partition("-")
-            cpus.update(range(int(a), int(b or a) + 1))
-        return cpus or None
+                             capture_output=True, text=True, timeout=30).stdout
+        with open(f"/sys/bus/pci/devices/{pci_sysfs_name(bus)}/local_cpulist") as f:
+            return parse_cpulist(f.read()) or None
     except Exception:
         return None
 
