@@ -67,6 +67,24 @@ def test_create_rejects_bad_config(lib, kw, code):
         assert "Yee limit" in msg
 
 
+@pytest.mark.parametrize("laser", [
+    dict(angle=0.5 * 3.141592653589793),   # grazing: |angle| must stay below pi/2
+    dict(angle=float("nan")),
+    dict(pol=3),
+    dict(waist=0.0),
+])
+def test_create_rejects_bad_laser(lib, laser):
+    """Laser parameters are checked on the host before any device work."""
+    from paper_1503_02464_gb300.sim import make_config
+    L = dict(a0=1.0, waist=1.0, duration=6.0, pol=1, angle=0.3)
+    L.update(laser)
+    cfg = make_config(2, (32, 8), (0.1, 0.1), 0.05, 2, absorbing_x=True, laser=L)
+    h = ctypes.c_void_p()
+    rc = lib.pic_create(ctypes.byref(cfg), ctypes.byref(h))
+    assert rc == 1 and h.value is None
+    assert "laser" in lib.pic_last_error(None).decode()
+
+
 def test_create_fails_loudly_without_device(lib):
     """A valid configuration on a machine without a GPU reports PIC_ECUDA
     (no CPU fallback)."""
