@@ -53,7 +53,9 @@ extern "C" {
 #define PIC_ENOMEM 3    /* device allocation failed or capacity exceeded         */
 #define PIC_ECUDA 4     /* a CUDA runtime call or kernel launch failed           */
 #define PIC_EOVERFLOW 5 /* an internal bound was exceeded on the device          */
-#define PIC_ETIMEOUT 6  /* a bounded device-side wait gave up                    */
+#define PIC_ETIMEOUT 6  /* a bounded device-side wait gave up (reserved: no
+                           kernel of this library waits on another block or
+                           on an asynchronous copy)                          */
 #define PIC_ENAN 7      /* a non-finite value was found by a diagnostic          */
 
 /* ---- enumerations ---- */
