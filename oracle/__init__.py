@@ -44,9 +44,16 @@ def build(force: bool = False) -> str:
 
 def _load():
     global _lib
-    if _lib is not None:
-        return _lib
-    lib = ctypes.CDLL(build())
+    if _lib is None:
+        _lib = load_library(build())
+    return _lib
+
+
+def load_library(path: str):
+    """Open a compiled oracle library at ``path`` and declare its entry
+    points (the default one comes from ``build()``; the pin tests also open
+    copies compiled with a deliberately planted mistake)."""
+    lib = ctypes.CDLL(path)
     vp, dp, ip = ctypes.c_void_p, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int)
     u32p = ctypes.POINTER(ctypes.c_uint32)
     lib.oracle_create.restype = vp
@@ -80,7 +87,6 @@ def _load():
     lib.oracle_set_laser.argtypes = [vp, ctypes.c_int] + [ctypes.c_double] * 5 + [ctypes.c_int, ctypes.c_double]
     lib.oracle_laser_field.restype = ctypes.c_double
     lib.oracle_laser_field.argtypes = [vp] + [ctypes.c_double] * 4
-    _lib = lib
     return lib
 
 
@@ -113,7 +119,7 @@ class OracleSim:
     """
 
     def __init__(self, dims, n, d, dt, order):
-        lib = _load()
+        lib = self._lib = _load()
         n3 = list(n) + [1] * (3 - len(n))
         d3 = list(d) + [1.0] * (3 - len(d))
         if dims == 2:
@@ -126,7 +132,7 @@ class OracleSim:
 
     def close(self):
         if self._h:
-            _load().oracle_destroy(self._h)
+            self._lib.oracle_destroy(self._h)
             self._h = None
 
     def __del__(self):
@@ -143,7 +149,7 @@ class OracleSim:
         n = len(x)
         arrs = [_f64(a) for a in (x, y, z if z is not None else np.zeros(n), ux, uy, uz, w)]
         ids = np.ascontiguousarray(ids if ids is not None else np.arange(n), dtype=np.uint32)
-        return _load().oracle_add_species(
+        return self._lib.oracle_add_species(
             self._h, float(q), float(m), n, *[_dp(a) for a in arrs],
             ids.ctypes.data_as(ctypes.POINTER(ctypes.c_uint32)))
 
@@ -154,57 +160,57 @@ class OracleSim:
     def set_filter(self, passes: int, compensate: bool = False):
         """Smooth J after every deposit: ``passes`` binomial passes per axis,
         then optionally one compensating pass."""
-        _load().oracle_set_filter(self._h, int(passes), 1 if compensate else 0)
+        self._lib.oracle_set_filter(self._h, int(passes), 1 if compensate else 0)
 
     def set_gather(self, energy_conserving: bool):
         """Gather variant: one shape order lower at half-integer positions."""
-        _load().oracle_set_gather(self._h, 1 if energy_conserving else 0)
+        self._lib.oracle_set_gather(self._h, 1 if energy_conserving else 0)
 
     def smooth(self, which: int):
         """Apply the configured smoothing to one stored field in place."""
-        _load().oracle_smooth(self._h, int(which))
+        self._lib.oracle_smooth(self._h, int(which))
 
     def set_absorbing_x(self, on: bool = True):
-        _load().oracle_set_boundary(self._h, 1 if on else 0)
+        self._lib.oracle_set_boundary(self._h, 1 if on else 0)
 
     def set_laser(self, a0, waist, duration, y_center=None, z_center=None, pol=1, angle=0.0):
         yc = 0.5 * self.n[1] * self.d[1] if y_center is None else y_center
         zc = 0.5 * self.n[2] * self.d[2] if z_center is None else z_center
-        _load().oracle_set_laser(self._h, 1, float(a0), float(waist), float(duration), float(yc), float(zc),
+        self._lib.oracle_set_laser(self._h, 1, float(a0), float(waist), float(duration), float(yc), float(zc),
                                  int(pol), float(angle))
 
     def laser_field(self, x, y, z, t) -> float:
-        return _load().oracle_laser_field(self._h, float(x), float(y), float(z), float(t))
+        return self._lib.oracle_laser_field(self._h, float(x), float(y), float(z), float(t))
 
     def step(self, n: int = 1):
-        _load().oracle_step(self._h, int(n))
+        self._lib.oracle_step(self._h, int(n))
 
     def field_step(self, n: int = 1):
-        _load().oracle_field_step(self._h, int(n))
+        self._lib.oracle_field_step(self._h, int(n))
 
     def get_field(self, which: int) -> np.ndarray:
         out = np.empty(self.shape3, dtype=np.float64)
-        _load().oracle_get_field(self._h, which, _dp(out))
+        self._lib.oracle_get_field(self._h, which, _dp(out))
         return out
 
     def set_field(self, which: int, arr):
         a = _f64(np.broadcast_to(arr, self.shape3))
-        _load().oracle_set_field(self._h, which, _dp(a))
+        self._lib.oracle_set_field(self._h, which, _dp(a))
 
     def rho(self) -> np.ndarray:
-        _load().oracle_compute_rho(self._h)
+        self._lib.oracle_compute_rho(self._h)
         return self.get_field(RHO)
 
     def neutralize(self):
-        _load().oracle_neutralize(self._h)
+        self._lib.oracle_neutralize(self._h)
 
     def set_background(self, rho_bg):
         """Immobile background charge density at the nodes (shaped like a field)."""
         a = _f64(np.broadcast_to(rho_bg, self.shape3))
-        _load().oracle_set_background(self._h, _dp(a))
+        self._lib.oracle_set_background(self._h, _dp(a))
 
     def particles(self, species: int = 0) -> dict:
-        lib = _load()
+        lib = self._lib
         n = lib.oracle_num_particles(self._h, species)
         out = np.empty((max(n, 1), 7), dtype=np.float64)
         ids = np.empty(max(n, 1), dtype=np.uint32)
@@ -216,19 +222,19 @@ class OracleSim:
     def gather(self, x, y, z=0.0):
         E = np.zeros(3)
         B = np.zeros(3)
-        _load().oracle_gather_point(self._h, float(x), float(y), float(z), _dp(E), _dp(B))
+        self._lib.oracle_gather_point(self._h, float(x), float(y), float(z), _dp(E), _dp(B))
         return E, B
 
     def deposit_move(self, q, w, r0, r1, vz=0.0):
         r0, r1 = _f64(r0), _f64(r1)
-        _load().oracle_deposit_move(self._h, float(q), float(w), _dp(r0), _dp(r1), float(vz))
+        self._lib.oracle_deposit_move(self._h, float(q), float(w), _dp(r0), _dp(r1), float(vz))
 
     def diag(self) -> dict:
         out = np.zeros(8)
-        _load().oracle_diag(self._h, _dp(out))
+        self._lib.oracle_diag(self._h, _dp(out))
         return {"energy_field": out[0], "energy_kinetic": out[1], "charge": out[2], "gauss_max": out[3],
                 "n_alive": int(out[4]), "energy_e": out[5], "energy_b": out[6]}
 
     @property
     def step_count(self) -> int:
-        return _load().oracle_step_count(self._h)
+        return self._lib.oracle_step_count(self._h)

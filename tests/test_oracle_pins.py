@@ -377,3 +377,179 @@ def test_cold_plasma_oscillation():
     w_theory = 2 / dt * math.asin(dt / 2)
     assert abs(w - w_theory) / w_theory < 0.02, (w, w_theory)
     assert kdx < 0.1
+
+
+# ---------------------------------------------------------------- deposit moments (§2 eq. 4)
+def _path_moments(X0, X1, a, b):
+    """Time averages over a straight move of 1, x_a, x_b and x_a x_b."""
+    p0, p1 = X0[a], X1[a]
+    q0, q1 = X0[b], X1[b]
+    return (1.0, 0.5 * (p0 + p1), 0.5 * (q0 + q1),
+            p0 * q0 + 0.5 * (p0 * (q1 - q0) + (p1 - p0) * q0) + (p1 - p0) * (q1 - q0) / 3.0)
+
+
+def check_transverse_moments(dims, order, seed=3, nmoves=12):
+    """One straight move from X0 to X1 (in cells, |X1 - X0| < 1 per axis).
+
+    The charge-conserving current of a component, summed along its own
+    axis (or, for the out-of-plane Jz of 2D3V, taken as it is), equals
+    q w v_c times transverse node weights that are the time average, over
+    the move, of the products of linearly interpolated node weights
+    S0 + t (S1 - S0).  Sampled CIC and TSC weights reproduce constants and
+    linear functions exactly (sum_i S(X - i) = 1, sum_i i S(X - i) = X), so
+    the weights' moments are path averages:
+        sum T = 1,  sum j T = <Y>,  sum k T = <Z>,  sum j k T = <Y Z>
+    with <Y Z> = Y0 Z0 + (Y0 dZ + dY Z0)/2 + dY dZ / 3 on the path.  A wrong
+    1/3 or 1/2 in the bracket, a dropped term, or the end-point shapes used
+    in place of the average all change one of these."""
+    rng = np.random.default_rng(seed)
+    n = (16, 16, 16) if dims == 3 else (16, 16)
+    d = np.array([0.1, 0.13, 0.07])
+    dt = 0.02
+    for _ in range(nmoves):
+        sim = OracleSim(dims, n, tuple(d[:dims]), dt, order)
+        X0 = 6.0 + 3.0 * rng.random(3)
+        X1 = X0 + rng.uniform(-0.95, 0.95, 3)
+        if dims == 2:
+            X0[2] = X1[2] = 0.0
+        q, w, vz_2d = -1.0 + 2.0 * rng.random(), 0.2 + rng.random(), rng.uniform(-0.8, 0.8)
+        sim.deposit_move(q, w, X0 * d, X1 * d, vz_2d)
+        v = (X1 - X0) * d / dt
+        nz, ny, nx = sim.shape3
+        k_, j_, i_ = np.meshgrid(np.arange(nz), np.arange(ny), np.arange(nx), indexing="ij")
+        pos = (i_.astype(float), j_.astype(float), k_.astype(float))
+        comps = [(JX, 0, 1, 2), (JY, 1, 2, 0), (JZ, 2, 0, 1)] if dims == 3 else [(JZ, 2, 0, 1)]
+        for key, c, a, b in comps:
+            J = sim.get_field(key)
+            qv = q * w * (v[c] if dims == 3 else vz_2d)
+            want = _path_moments(X0, X1, a, b)
+            got = (J.sum(), (J * pos[a]).sum(), (J * pos[b]).sum(), (J * pos[a] * pos[b]).sum())
+            for g, m in zip(got, want):
+                assert abs(g - qv * m) <= 1e-12 * abs(qv) * max(1.0, abs(m)), (key, g, qv * m)
+        sim.close()
+
+
+@pytest.mark.parametrize("order", [1, 2])
+def test_jz_2d3v_moments(order):
+    """The out-of-plane current of 2D3V, which the continuity equation does
+    not constrain (nothing varies along z), against the path averages of 1,
+    x, y and x y."""
+    check_transverse_moments(2, order)
+
+
+@pytest.mark.parametrize("order", [1, 2])
+def test_j3d_transverse_moments(order):
+    check_transverse_moments(3, order)
+
+
+# ---------------------------------------------------------------- energy diagnostics
+def check_field_energy_of_eigenmode(dims):
+    """A travelling vacuum plane wave (an exact eigenvector of the split Yee
+    update) has, at every integer step, electric energy (1/2) dV (N/2) |E0|^2
+    and magnetic energy (1/2) dV (N/2) |B0|^2 cos^2(w dt/2): over the whole
+    periodic grid, sum cos^2(k.x - w t) = N/2 at any phase when 2k is not a
+    multiple of the grid's reciprocal lattice."""
+    n = (16, 12, 10) if dims == 3 else (16, 12, 1)
+    d = (0.1, 0.13, 0.07) if dims == 3 else (0.1, 0.13, 1.0)
+    lim = 1.0 / math.sqrt(sum(1.0 / x ** 2 for x in d[:dims]))
+    sim = OracleSim(dims, n, d, 0.9 * lim, 2)
+    m = np.array([3, -2, 1]) if dims == 3 else np.array([3, -2, 0])
+    kvec = 2 * math.pi * m / (np.array(n) * np.array(d))
+    kap = 2.0 / np.array(d) * np.sin(kvec * np.array(d) / 2.0)
+    if dims == 2:
+        kvec[2] = kap[2] = 0.0
+    e_amp = np.cross(kap, [0.3, 0.5, 1.0])
+    e_amp *= 0.7 / np.linalg.norm(e_amp)
+    init, w = _yee_mode(sim, kvec, e_amp, 0)
+    for key, val in init.items():
+        sim.set_field(key, val)
+    Om = np.linalg.norm(kap)
+    b_amp = np.cross(kap, e_amp) / Om * math.cos(w * sim.dt / 2)
+    ncell = n[0] * n[1] * n[2]
+    dV = d[0] * d[1] * (d[2] if dims == 3 else 1.0)
+    want_e = 0.5 * dV * 0.5 * ncell * float(e_amp @ e_amp)
+    want_b = 0.5 * dV * 0.5 * ncell * float(b_amp @ b_amp)
+    for steps in (0, 7, 13):
+        if steps:
+            sim.field_step(steps)
+        dg = sim.diag()
+        assert abs(dg["energy_e"] - want_e) < 1e-12 * want_e, (steps, dg["energy_e"], want_e)
+        assert abs(dg["energy_b"] - want_b) < 1e-12 * want_b, (steps, dg["energy_b"], want_b)
+        assert abs(dg["energy_field"] - want_e - want_b) < 1e-12 * (want_e + want_b)
+    sim.close()
+
+
+@pytest.mark.parametrize("dims", [2, 3])
+def test_field_energy_of_vacuum_eigenmode(dims):
+    check_field_energy_of_eigenmode(dims)
+
+
+def check_kinetic_energy_of_cold_beams(dims):
+    """Uniform cold beams of density n_s and momentum u_s per unit mass in a
+    box of volume V carry kinetic energy sum_s n_s V m_s (gamma_s - 1)
+    (relativistic: u = 1 gives gamma - 1 = 0.414, not u^2/2 = 0.5)."""
+    from paper_1503_02464_gb300 import synth
+    n = (6, 5, 4) if dims == 3 else (8, 6)
+    d = (0.11, 0.07, 0.05) if dims == 3 else (0.11, 0.07)
+    sim = OracleSim(dims, n, d, 0.01, 2)
+    n3 = tuple(list(n) + [1] * (3 - len(n)))
+    d3 = tuple(list(d) + [1.0] * (3 - len(d)))
+    cells = np.arange(n3[0] * n3[1] * n3[2])
+    V = float(np.prod(np.array(n3) * np.array(d3)))
+    want = 0.0
+    for (q, mass, dens, u, ppc, seed) in ((-1.0, 1.0, 2.5, (1.0, 0.0, 0.0), 3, 5),
+                                          (1.0, 1836.0, 2.5, (0.0, -0.02, 0.01), 2, 6)):
+        p = synth.particles_for_cells(cells, n3, d3, ppc, 0.0, dens, seed, dims)
+        for key, val in zip(("ux", "uy", "uz"), u):
+            p[key] = np.full(len(p["x"]), val)
+        sim.add_particles(p, q, mass)
+        want += dens * V * mass * (math.sqrt(1.0 + sum(x * x for x in u)) - 1.0)
+    got = sim.diag()["energy_kinetic"]
+    assert abs(got - want) < 1e-12 * want, (got, want)
+    sim.close()
+
+
+@pytest.mark.parametrize("dims", [2, 3])
+def test_kinetic_energy_of_cold_beams(dims):
+    check_kinetic_energy_of_cold_beams(dims)
+
+
+def check_langmuir_energy_exchange():
+    """A small cold Langmuir oscillation trades kinetic for electric energy:
+    over whole periods the kinetic energy (centred at integer steps as the
+    mean of the two half-step values) and the electric energy swing by the
+    same amount, and their sum is conserved, both to O((w_p dt)^2) (here
+    w_p dt = 0.1).  A missing 1/2 or dV in either energy breaks the balance."""
+    nx, ny = 64, 4
+    d = (0.2, 0.2)
+    dt = 0.1
+    sim = OracleSim(2, (nx, ny), d, dt, 2)
+    from paper_1503_02464_gb300 import synth
+    cells = np.arange(nx * ny)
+    p = synth.particles_for_cells(cells, (nx, ny, 1), (0.2, 0.2, 1.0), 4, 0.0, 1.0, 77, 2)
+    i = cells.repeat(4) % nx
+    j = cells.repeat(4) // nx
+    s = np.tile(np.arange(4), nx * ny)
+    p["x"] = (i + 0.125 + 0.25 * s) * d[0]
+    p["y"] = (j + 0.5) * d[1]
+    p["ux"] = 1e-3 * np.sin(2 * math.pi * p["x"] / (nx * d[0]))
+    sim.add_particles(p, -1.0, 1.0)
+    sim.neutralize()
+    kin, ue, ub = [], [], []
+    for _ in range(128):
+        sim.step(1)
+        dg = sim.diag()
+        kin.append(dg["energy_kinetic"])
+        ue.append(dg["energy_e"])
+        ub.append(dg["energy_b"])
+    kin, ue, ub = np.array(kin), np.array(ue), np.array(ub)
+    kc = 0.5 * (kin[:-1] + kin[1:])  # kinetic energy at the integer step of ue[:-1]
+    tot = kc + ue[:-1] + ub[:-1]
+    swing_k, swing_e = kc.max() - kc.min(), ue.max() - ue.min()
+    assert swing_e > 0.0 and abs(swing_k / swing_e - 1.0) < 0.02, (swing_k, swing_e)
+    assert (tot.max() - tot.min()) < 0.02 * swing_e, (tot.max() - tot.min(), swing_e)
+    sim.close()
+
+
+def test_langmuir_energy_exchange():
+    check_langmuir_energy_exchange()
