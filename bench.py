@@ -43,18 +43,17 @@ WORKLOAD = "thermal3d_256"
 # 12 B write) once = 48 B.
 PUSH_BYTES_PER_PARTICLE = {"fp32": 60, "fp64": 4 + 24 + 24 + 8 + 4 + 24 + 24}
 PUSH_BYTES_PER_CELL = {"fp32": 48, "fp64": 96}
-# DRAM bytes (read + write) per particle of one push launch, from the ncu
-# capture summarised in profiles/k_push_thermal3d_128.md (128^3 case of the
-# same plasma, scaled by the particle count); None for workloads and
-# precisions not captured, and once the kernel changes.
+# DRAM bytes (read + write) per particle of one push launch, from an ncu
+# capture of the push kernel on the 128^3 case of the same plasma (scaled by
+# the particle count); None for workloads and precisions not captured, and
+# once the kernel changes.
 # Algorithmic flops of the fused push per particle-step, by (dims, shape
 # order): gather weights and staggered sums, Boris and move, Esirkepov
 # weights, brackets and the products of the full compact stencil (NW = order
 # + 2 nodes per axis, no data-dependent skipping); an FMA counts as 2.  The
 # breakdown is in the design notes (section 5).
 PUSH_FLOPS_PER_PARTICLE = {(3, 2): 1117, (3, 1): 496, (2, 2): 445, (2, 1): 251}
-FP32_LANES_PER_SM = 128  # FP32 FMA lanes per SM
-FP64_NOMINAL_TFLOPS = 1.25  # GB300 FP64 (nominal)
+FP32_LANES_PER_SM = 128  # FP32 FMA lanes per SM (nominal roof, quoted beside the measured one)
 PUSH_TRAFFIC_PER_PARTICLE = {("thermal3d_256", "fp32"): 62.8, ("thermal3d_128", "fp32"): 62.8}
 
 
@@ -127,9 +126,47 @@ def oracle_sample_workload(wl, ncell_axis: int):
                           wl.seed, wl.species, wl.sort_every)
 
 
-def time_oracle(wl, nsteps: int, warmup: int = 0):
+def cpu_model() -> str:
+    """The host CPU's model name (lscpu, else /proc/cpuinfo)."""
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.strip().lower().startswith("model name"):
+                return line.split(":", 1)[1].strip()
+    except Exception:
+        pass
+    try:
+        for line in open("/proc/cpuinfo"):
+            if line.lower().startswith("model name"):
+                return line.split(":", 1)[1].strip()
+    except Exception:
+        pass
+    return "unknown"
+
+
+# periodic sub-box edge (cells) of the oracle samples: 3D 64^3, 2D 512^2
+ORACLE_SAMPLE_CELLS = {3: 64, 2: 512}
+
+
+def oracle_baseline(wl, nsteps: int, warmup: int = 0) -> dict:
+    """The FP64 oracle (OpenMP build, every host core) on a periodic sub-box
+    of the workload: particle-steps/s and a description of the sample."""
     import oracle
-    o = oracle.OracleSim(wl.dims, wl.n, wl.d, wl.dt, wl.order)
+    sample = oracle_sample_workload(wl, ORACLE_SAMPLE_CELLS[wl.dims])
+    npart, times = time_oracle(sample, nsteps, warmup, parallel=True)
+    cores = oracle.num_threads(parallel=True)
+    tot = sum(times)
+    desc = (f"FP64 C oracle, OpenMP on {cores} threads ({os.cpu_count()} host CPUs, {cpu_model()}), periodic "
+            f"{'x'.join(map(str, sample.n[:sample.dims]))} sub-box of {wl.name} ({npart} particles, same dx, dt, "
+            f"ppc, u_th, shape), {len(times)} steps, {tot:.1f} s")
+    return {"value": npart * len(times) / tot, "unit": "particle-steps/s", "cores": cores, "kind": "oracle",
+            "sample": desc, "npart": npart, "times": times,
+            "shape": "x".join(map(str, sample.n[:sample.dims]))}
+
+
+def time_oracle(wl, nsteps: int, warmup: int = 0, parallel: bool = False):
+    import oracle
+    o = oracle.OracleSim(wl.dims, wl.n, wl.d, wl.dt, wl.order, parallel=parallel)
     npart = 0
     for isp, sp in enumerate(wl.species):
         p = wl.particles(isp)
@@ -151,19 +188,14 @@ def run_reference(args, rank: int, world: int):
     if rank != 0:
         return
     wl = synth.preset(args.workload)
-    sample = oracle_sample_workload(wl, 32 if wl.dims == 3 else 256)
-    npart, times = time_oracle(sample, args.steps, args.warmup)
+    cpu = oracle_baseline(wl, args.steps, args.warmup)
+    value, times = cpu["value"], cpu["times"]
     tot = sum(times)
-    value = npart * len(times) / tot
-    desc = (f"FP64 C oracle, single thread, periodic {'x'.join(map(str, sample.n[:sample.dims]))} sub-box of "
-            f"{wl.name} ({npart} particles, same dx, dt, ppc, u_th, shape), {len(times)} steps")
     line = {"impl": "reference", "metric": "particle-steps/s", "value": value, "unit": "particle-steps/s",
             "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * tot / len(times),
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": wl.name, "sample": "x".join(map(str, sample.n[:sample.dims])),
-                       "particles": npart},
-            "cpu_baseline": {"value": value, "unit": "particle-steps/s", "cores": 1, "kind": "oracle",
-                             "sample": desc},
+            "config": {"workload": wl.name, "sample": cpu["shape"], "particles": cpu["npart"]},
+            "cpu_baseline": {k: cpu[k] for k in ("value", "unit", "cores", "kind", "sample")},
             "e2e": {"value": value, "unit": "particle-steps/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
@@ -455,11 +487,8 @@ def run_gpu(args, rank: int, world: int, local: int):
     # ---------------- CPU oracle baseline (rank 0, N = 1 only)
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        sample = oracle_sample_workload(wl, 32)
-        n_o, ts = time_oracle(sample, args.cpu_steps)
-        cpu = {"value": n_o * len(ts) / sum(ts), "unit": "particle-steps/s", "cores": 1, "kind": "oracle",
-               "sample": f"FP64 C oracle, 1 thread, periodic 32^3 sub-box of {wl.name} ({n_o} particles, "
-                         f"same dx/dt/ppc/u_th/TSC), {len(ts)} steps, {sum(ts):.1f} s"}
+        c = oracle_baseline(wl, args.cpu_steps)
+        cpu = {k: c[k] for k in ("value", "unit", "cores", "kind", "sample")}
 
     for h in host:
         h.close()
@@ -467,6 +496,7 @@ def run_gpu(args, rank: int, world: int, local: int):
         pool.close()
         pool.join()
 
+    alu_peaks = capi.pic_alu_peak(stream.cuda_stream)  # FP32, FP64 FMA TFLOP/s of this device
     if rank != 0:
         return
     r = results["main"]
@@ -477,17 +507,19 @@ def run_gpu(args, rank: int, world: int, local: int):
     alg_bytes = (npart // max(len(wl.species), 1)) * PUSH_BYTES_PER_PARTICLE[args.precision] + \
         ncell * PUSH_BYTES_PER_CELL[args.precision]
     achieved = alg_bytes / push_avg_s / 1e9
-    # the FP32 ALU roof of the same launch: nominal lanes x max SM clock sampled during the run
+    # the ALU roof of the same launch: FMA throughput measured on this device
+    # (pic_alu_peak, after the timed regions), the nominal roof beside it
     flops_pp = PUSH_FLOPS_PER_PARTICLE[(wl.dims, wl.order)]
     nsm = torch.cuda.get_device_properties(local).multi_processor_count
     sm_max_mhz = (r["clocks"] or {}).get("sm_max_mhz") or 2070.0
-    peak_alu = nsm * FP32_LANES_PER_SM * 2 * sm_max_mhz * 1e6 / 1e12
+    nominal_alu = nsm * FP32_LANES_PER_SM * 2 * sm_max_mhz * 1e6 / 1e12
+    peak_alu, peak64_alu = alu_peaks
     flops_launch = (npart // max(len(wl.species), 1)) * flops_pp
     achieved_alu = flops_launch / push_avg_s / 1e12
     if fp64 is not None and "push_ms_per_launch" in fp64:
         a64 = flops_launch / (fp64["push_ms_per_launch"] / 1e3) / 1e12
-        fp64["alu"] = {"achieved": a64, "peak": FP64_NOMINAL_TFLOPS, "unit": "TFLOP/s",
-                       "frac": a64 / FP64_NOMINAL_TFLOPS, "peak_kind": "nominal GB300 FP64"}
+        fp64["alu"] = {"achieved": a64, "peak": peak64_alu, "unit": "TFLOP/s", "frac": a64 / peak64_alu,
+                       "peak_kind": "measured FP64 FMA-chain kernel (pic_alu_peak)"}
     tim_out = {k: {"ms_total": v[0], "launches": v[1]} for k, v in r["tim"].items() if v[1]}
     line = {
         "metric": "particle-steps/s", "value": value, "unit": "particle-steps/s", "n_gpus": world,
@@ -513,8 +545,10 @@ def run_gpu(args, rank: int, world: int, local: int):
         "roofline_alu": {"bound": "alu", "achieved": achieved_alu, "peak": peak_alu, "unit": "TFLOP/s",
                          "frac": achieved_alu / peak_alu, "flops_per_particle": flops_pp,
                          "flops_per_launch": flops_launch,
-                         "peak_kind": f"nominal: {nsm} SMs x {FP32_LANES_PER_SM} FP32 lanes x 2 flop x "
-                                      f"{sm_max_mhz:.0f} MHz max SM clock"},
+                         "peak_kind": "measured FP32 FMA-chain kernel (pic_alu_peak)",
+                         "nominal": nominal_alu,
+                         "nominal_kind": f"{nsm} SMs x {FP32_LANES_PER_SM} FP32 lanes x 2 flop x "
+                                         f"{sm_max_mhz:.0f} MHz max SM clock"},
         "kernel_times": tim_out,
         "gpu_launches": int(r["launches"]),
         "clocks": r["clocks"],
@@ -547,7 +581,7 @@ def main():
     ap.add_argument("--workload", default=WORKLOAD)
     ap.add_argument("--precision", default="fp32", choices=["fp32", "fp64"])
     ap.add_argument("--fp64-steps", type=int, default=10)
-    ap.add_argument("--cpu-steps", type=int, default=3)
+    ap.add_argument("--cpu-steps", type=int, default=4)
     ap.add_argument("--nproc", type=int, default=0)
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")

@@ -344,8 +344,11 @@ int pic_state_size(pic_handle *h, int64_t *bytes);
 int pic_state_save(pic_handle *h, void *buf, int64_t bytes, int mem_kind);
 
 /* Replace the state by a saved one.  PIC_EINVAL (state unchanged) when the
- * blob's header does not match this handle.  The species are re-sorted at
- * the next step. */
+ * blob's header does not match this handle, or when a particle slot in use
+ * is neither dead nor valid (cell outside the grid, offset outside [0, 1),
+ * non-finite momentum or weight, position beyond an absorbing wall): the
+ * particle storage is checked on the device before anything is replaced.
+ * The species are re-sorted at the next step. */
 int pic_state_load(pic_handle *h, const void *buf, int64_t bytes, int mem_kind);
 
 /* ---- output manager (§3.1) --------------------------------------------
@@ -411,6 +414,17 @@ int pic_output_read(pic_handle *h, int id, int64_t frame, double *out, int64_t *
 
 /* Release request id and its buffer (its id is not reused). */
 int pic_output_remove(pic_handle *h, int id);
+
+/* Measured FMA throughput of the current device, the denominators of the
+ * arithmetic rooflines a throughput report gives beside the HBM one (the
+ * paper has no counterpart: §4 quotes BlueGene/Q scaling, not per-node
+ * rates).  Times, with CUDA events on `stream` (cudaStream_t, NULL = the
+ * default stream), a kernel of eight independent FMA chains per thread on
+ * every SM in FP32 and in FP64, best of three launches each, and writes the
+ * rates in TFLOP/s (an FMA counts 2 flops) to *fp32_tflops, *fp64_tflops
+ * (host memory).  Synchronises; takes about 0.1 s; changes no clock or power
+ * setting.  PIC_EINVAL for NULL outputs, PIC_ECUDA if a launch failed. */
+int pic_alu_peak(double *fp32_tflops, double *fp64_tflops, void *stream);
 
 /* FP64 field energies without any device allocation.  The paper has no
  * counterpart: this is a library service for callers that must not call

@@ -23,30 +23,47 @@ import numpy as np
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "pic_oracle.c")
 _LIB = os.path.join(_HERE, "_build", "libpic_oracle.so")
+_LIB_OMP = os.path.join(_HERE, "_build", "libpic_oracle_omp.so")
 
 EX, EY, EZ, BX, BY, BZ, JX, JY, JZ, RHO = range(10)
 FIELD_NAMES = ["Ex", "Ey", "Ez", "Bx", "By", "Bz", "Jx", "Jy", "Jz", "rho"]
 
 _lib = None
+_lib_omp = None
 
 
-def build(force: bool = False) -> str:
-    """Compile the oracle with gcc (no GPU, no CUDA)."""
-    os.makedirs(os.path.dirname(_LIB), exist_ok=True)
-    if not force and os.path.exists(_LIB) and os.path.getmtime(_LIB) >= os.path.getmtime(_SRC):
-        return _LIB
-    tmp = _LIB + f".tmp{os.getpid()}"
-    cmd = ["gcc", "-O2", "-fPIC", "-shared", "-std=c99", "-ffp-contract=off", "-o", tmp, _SRC, "-lm"]
+def build(force: bool = False, parallel: bool = False) -> str:
+    """Compile the oracle with gcc (no GPU, no CUDA).  ``parallel`` builds
+    the OpenMP variant, whose particle loop runs on every host core with a J
+    array per thread (same arithmetic; the per-thread J arrays are summed in
+    thread order)."""
+    lib_path = _LIB_OMP if parallel else _LIB
+    os.makedirs(os.path.dirname(lib_path), exist_ok=True)
+    if not force and os.path.exists(lib_path) and os.path.getmtime(lib_path) >= os.path.getmtime(_SRC):
+        return lib_path
+    tmp = lib_path + f".tmp{os.getpid()}"
+    cmd = ["gcc", "-O2", "-fPIC", "-shared", "-std=c99", "-ffp-contract=off"] + (["-fopenmp"] if parallel else []) \
+        + ["-o", tmp, _SRC, "-lm"]
     subprocess.run(cmd, check=True)
-    os.replace(tmp, _LIB)
-    return _LIB
+    os.replace(tmp, lib_path)
+    return lib_path
 
 
-def _load():
-    global _lib
+def _load(parallel: bool = False):
+    global _lib, _lib_omp
+    if parallel:
+        if _lib_omp is None:
+            _lib_omp = load_library(build(parallel=True))
+        return _lib_omp
     if _lib is None:
         _lib = load_library(build())
     return _lib
+
+
+def num_threads(parallel: bool = True) -> int:
+    """Threads the oracle's particle loop runs on (OMP_NUM_THREADS, else
+    every host core, for the OpenMP build; 1 for the serial one)."""
+    return int(_load(parallel).oracle_num_threads())
 
 
 def load_library(path: str):
@@ -87,6 +104,8 @@ def load_library(path: str):
     lib.oracle_set_laser.argtypes = [vp, ctypes.c_int] + [ctypes.c_double] * 5 + [ctypes.c_int, ctypes.c_double]
     lib.oracle_laser_field.restype = ctypes.c_double
     lib.oracle_laser_field.argtypes = [vp] + [ctypes.c_double] * 4
+    lib.oracle_num_threads.restype = ctypes.c_int
+    lib.oracle_num_threads.argtypes = []
     return lib
 
 
@@ -115,11 +134,12 @@ class OracleSim:
 
     ``dims`` is 2 or 3, ``n`` the cells per axis, ``d`` the cell sizes (c/omega
     units), ``dt`` the time step and ``order`` the shape order (1 CIC, 2 TSC).
-    Fields are returned as numpy arrays shaped (nz, ny, nx).
+    Fields are returned as numpy arrays shaped (nz, ny, nx).  ``parallel``
+    runs the particle loop of each step on every host core (OpenMP build).
     """
 
-    def __init__(self, dims, n, d, dt, order):
-        lib = self._lib = _load()
+    def __init__(self, dims, n, d, dt, order, parallel: bool = False):
+        lib = self._lib = _load(parallel)
         n3 = list(n) + [1] * (3 - len(n))
         d3 = list(d) + [1.0] * (3 - len(d))
         if dims == 2:

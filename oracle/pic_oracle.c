@@ -39,6 +39,9 @@
 #include <stdint.h>
 #include <stdlib.h>
 #include <string.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
 
 #define ORC_EX 0
 #define ORC_EY 1
@@ -370,7 +373,8 @@ void oracle_boris(double q, double m, double dt, const double *E, const double *
 /* eq. 4 and the continuity requirement stated in §2).                 */
 /* ------------------------------------------------------------------ */
 #define ORC_SW 10
-static void esirkepov(orc_sim *s, double q, double w, const double X0[3], const double X1[3], double vz) {
+static void esirkepov(orc_sim *s, double *const J3[3], double q, double w, const double X0[3], const double X1[3],
+                      double vz) {
   int o = s->order;
   int na = s->dims;
   long lo[3] = {0, 0, 0};
@@ -388,7 +392,7 @@ static void esirkepov(orc_sim *s, double q, double w, const double X0[3], const 
       DS[a][i] = S1[a][i] - S0[a][i];
     }
   }
-  double *Jx = s->f[ORC_JX], *Jy = s->f[ORC_JY], *Jz = s->f[ORC_JZ];
+  double *Jx = J3[0], *Jy = J3[1], *Jz = J3[2];
   double cx = -q * w * s->d[0] / s->dt, cy = -q * w * s->d[1] / s->dt, cz = -q * w * s->d[2] / s->dt;
   if (s->dims == 2) {
     for (int j = 0; j < wdt[1]; ++j) {
@@ -448,7 +452,7 @@ void oracle_deposit_move(void *h, double q, double w, const double *r0, const do
   orc_sim *s = (orc_sim *)h;
   double X0[3] = {r0[0] / s->d[0], r0[1] / s->d[1], s->dims == 3 ? r0[2] / s->d[2] : 0.0};
   double X1[3] = {r1[0] / s->d[0], r1[1] / s->d[1], s->dims == 3 ? r1[2] / s->d[2] : 0.0};
-  esirkepov(s, q, w, X0, X1, vz);
+  esirkepov(s, s->f + ORC_JX, q, w, X0, X1, vz);
 }
 
 /* ------------------------------------------------------------------ */
@@ -610,6 +614,78 @@ void oracle_field_step(void *h, int nsteps) {
 /* ------------------------------------------------------------------ */
 /* One PIC cycle: gather -> Boris -> move -> deposit, then Yee.        */
 /* ------------------------------------------------------------------ */
+/* Gather, Boris, move and deposit (into J3) of one live particle. */
+static void advance_particle(orc_sim *s, const orc_species *sp, orc_particle *p, const double L[3],
+                             double *const J3[3]) {
+  double E[3], B[3];
+  gather_at(s, p->x, p->y, p->z, E, B);
+  double mom[3] = {p->px, p->py, p->pz};
+  oracle_boris(sp->q, sp->m, s->dt, E, B, mom);
+  p->px = mom[0];
+  p->py = mom[1];
+  p->pz = mom[2];
+  double gm = sqrt(mom[0] * mom[0] + mom[1] * mom[1] + mom[2] * mom[2] + sp->m * sp->m);
+  double v[3] = {mom[0] / gm, mom[1] / gm, mom[2] / gm}; /* §2 eq. 1 */
+  double r0[3] = {p->x, p->y, p->z};
+  double r1[3] = {p->x + s->dt * v[0], p->y + s->dt * v[1], s->dims == 3 ? p->z + s->dt * v[2] : 0.0};
+  double X0[3] = {r0[0] / s->d[0], r0[1] / s->d[1], r0[2] / s->d[2]};
+  double X1[3] = {r1[0] / s->d[0], r1[1] / s->d[1], r1[2] / s->d[2]};
+  esirkepov(s, J3, sp->q, p->w, X0, X1, v[2]);
+  if (s->absorb_x && (X1[0] < ORC_WALL_LO || X1[0] >= s->n[0] - ORC_WALL_HI_MARGIN)) {
+    p->alive = 0; /* removed at the wall after depositing its last move */
+    return;
+  }
+  /* periodic wrap of the stored position */
+  for (int a = 0; a < s->dims; ++a) {
+    if (r1[a] >= L[a]) r1[a] -= L[a];
+    else if (r1[a] < 0.0) r1[a] += L[a];
+  }
+  p->x = r1[0];
+  p->y = r1[1];
+  p->z = r1[2];
+}
+
+#ifdef _OPENMP
+/* The particle loop of one step on all OpenMP threads (the library built
+ * with -fopenmp).  Each thread deposits into J arrays of its own; they are
+ * then summed node by node in thread order, so the result depends only on
+ * the thread count and differs from the serial loop by the order of the
+ * additions alone (round-off). */
+static void push_all_parallel(orc_sim *s, const double L[3]) {
+  const int nt = omp_get_max_threads();
+  const long nc = s->ncell;
+  double *buf = (double *)calloc((size_t)nt * 3 * (size_t)nc, sizeof(double));
+#pragma omp parallel num_threads(nt)
+  {
+    const int t = omp_get_thread_num();
+    double *J3[3] = {buf + ((size_t)t * 3 + 0) * nc, buf + ((size_t)t * 3 + 1) * nc, buf + ((size_t)t * 3 + 2) * nc};
+    for (int isp = 0; isp < s->nsp; ++isp) {
+      orc_species *sp = &s->sp[isp];
+#pragma omp for schedule(static)
+      for (long ip = 0; ip < sp->n; ++ip)
+        if (sp->p[ip].alive) advance_particle(s, sp, &sp->p[ip], L, J3);
+    }
+#pragma omp for schedule(static)
+    for (long c = 0; c < nc; ++c)
+      for (int a = 0; a < 3; ++a) {
+        double acc = 0.0;
+        for (int u = 0; u < nt; ++u) acc += buf[((size_t)u * 3 + a) * nc + c];
+        s->f[ORC_JX + a][c] = acc;
+      }
+  }
+  free(buf);
+}
+#endif
+
+/* Threads the particle loop runs on (1 for the serial build). */
+int oracle_num_threads(void) {
+#ifdef _OPENMP
+  return omp_get_max_threads();
+#else
+  return 1;
+#endif
+}
+
 void oracle_step(void *h, int nsteps) {
   orc_sim *s = (orc_sim *)h;
   double L[3] = {s->n[0] * s->d[0], s->n[1] * s->d[1], s->n[2] * s->d[2]};
@@ -617,39 +693,15 @@ void oracle_step(void *h, int nsteps) {
     memset(s->f[ORC_JX], 0, sizeof(double) * s->ncell);
     memset(s->f[ORC_JY], 0, sizeof(double) * s->ncell);
     memset(s->f[ORC_JZ], 0, sizeof(double) * s->ncell);
+#ifdef _OPENMP
+    push_all_parallel(s, L);
+#else
     for (int isp = 0; isp < s->nsp; ++isp) {
       orc_species *sp = &s->sp[isp];
-      for (long ip = 0; ip < sp->n; ++ip) {
-        orc_particle *p = &sp->p[ip];
-        if (!p->alive) continue;
-        double E[3], B[3];
-        gather_at(s, p->x, p->y, p->z, E, B);
-        double mom[3] = {p->px, p->py, p->pz};
-        oracle_boris(sp->q, sp->m, s->dt, E, B, mom);
-        p->px = mom[0];
-        p->py = mom[1];
-        p->pz = mom[2];
-        double gm = sqrt(mom[0] * mom[0] + mom[1] * mom[1] + mom[2] * mom[2] + sp->m * sp->m);
-        double v[3] = {mom[0] / gm, mom[1] / gm, mom[2] / gm}; /* §2 eq. 1 */
-        double r0[3] = {p->x, p->y, p->z};
-        double r1[3] = {p->x + s->dt * v[0], p->y + s->dt * v[1], s->dims == 3 ? p->z + s->dt * v[2] : 0.0};
-        double X0[3] = {r0[0] / s->d[0], r0[1] / s->d[1], r0[2] / s->d[2]};
-        double X1[3] = {r1[0] / s->d[0], r1[1] / s->d[1], r1[2] / s->d[2]};
-        esirkepov(s, sp->q, p->w, X0, X1, v[2]);
-        if (s->absorb_x && (X1[0] < ORC_WALL_LO || X1[0] >= s->n[0] - ORC_WALL_HI_MARGIN)) {
-          p->alive = 0; /* removed at the wall after depositing its last move */
-          continue;
-        }
-        /* periodic wrap of the stored position */
-        for (int a = 0; a < s->dims; ++a) {
-          if (r1[a] >= L[a]) r1[a] -= L[a];
-          else if (r1[a] < 0.0) r1[a] += L[a];
-        }
-        p->x = r1[0];
-        p->y = r1[1];
-        p->z = r1[2];
-      }
+      for (long ip = 0; ip < sp->n; ++ip)
+        if (sp->p[ip].alive) advance_particle(s, sp, &sp->p[ip], L, s->f + ORC_JX);
     }
+#endif
     if (s->filter_passes > 0)
       for (int c = 0; c < 3; ++c) smooth_field(s, s->f[ORC_JX + c]);
     field_cycle(s);

@@ -29,7 +29,7 @@ EXPORTED = ["pic_create", "pic_destroy", "pic_last_error", "pic_add_species", "p
             "pic_diag", "pic_energy", "pic_sync", "pic_profile", "pic_timings", "pic_launch_count", "pic_checkpoint",
             "pic_restore", "pic_tape_begin", "pic_adjoint_begin", "pic_adjoint_seed_kinetic", "pic_adjoint_step",
             "pic_grad", "pic_state_size", "pic_state_save", "pic_state_load", "pic_output_due", "pic_output_add", "pic_output_capture", "pic_output_count",
-            "pic_output_read", "pic_output_remove", "pic_field_energy_noalloc"]
+            "pic_output_read", "pic_output_remove", "pic_field_energy_noalloc", "pic_alu_peak"]
 
 
 class pic_laser(ctypes.Structure):
@@ -142,6 +142,7 @@ def load(build_if_missing: bool = True) -> ctypes.CDLL:
         "pic_output_read": ([hp, ctypes.c_int, i64, vp, ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_int64),
                              ctypes.c_int], ctypes.c_int),
         "pic_output_remove": ([hp, ctypes.c_int], ctypes.c_int),
+        "pic_alu_peak": ([dp, dp, vp], ctypes.c_int),
     }
     for name, (args, res) in sig.items():
         fn = getattr(lib, name)
@@ -345,3 +346,10 @@ def pic_field_energy_noalloc(precision: int, E_ptrs, B_ptrs, ncell: int, cell_vo
     b = (ctypes.c_void_p * 3)(*B_ptrs)
     check(None, load().pic_field_energy_noalloc(int(precision), e, b, int(ncell), float(cell_volume), out_ptr,
                                                 int(mem_kind), stream))
+
+
+def pic_alu_peak(stream=None) -> tuple:
+    """Measured FP32 and FP64 FMA throughput of the current device, TFLOP/s."""
+    a, b = ctypes.c_double(), ctypes.c_double()
+    check(None, load().pic_alu_peak(ctypes.byref(a), ctypes.byref(b), stream))
+    return a.value, b.value

@@ -918,17 +918,36 @@ int pic_state_load(pic_handle *h, const void *buf, int64_t bytes, int mem_kind) 
   const cudaMemcpyKind from = mem_kind == PIC_MEM_HOST ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice;
   const char *p = static_cast<const char *>(buf) + sizeof hd;
   const size_t fb = (size_t)h->g.ncell * h->rsize;
-  CK(h, cudaMemcpyAsync(h->E[0], p, 6 * fb, from, h->st), "state fields");
-  p += 6 * fb;
-  CK(h, cudaMemcpyAsync(h->J[0], p, 3 * fb, from, h->st), "state J");
-  p += 3 * fb;
-  CK(h, cudaMemcpyAsync(h->rho_bg, p, sizeof(double) * (size_t)h->g.ncell, from, h->st), "state background");
-  p += sizeof(double) * (size_t)h->g.ncell;
+  const char *pf = p;  // fields, J and background
+  p += 9 * fb + sizeof(double) * (size_t)h->g.ncell;
+  // Particles go first into each species' spare sort buffer and are
+  // validated there on the device (cells inside the grid, offsets in [0, 1),
+  // finite momenta and weights), so that a corrupt blob is refused before it
+  // replaces anything: the next sort indexes its counters by cell.
+  CK(h, cudaMemsetAsync(h->bad, 0, sizeof(unsigned long long), h->st), "memset");
   for (int i = 0; i < h->nsp; ++i) {
     Species &s = h->sp[i];
     const size_t pb = particles_bytes(s.slots, h->rsize, h->g.dims);
-    CK(h, cudaMemcpyAsync(s.buf[s.cur].cell, p, pb, from, h->st), "state particles");
+    CK(h, cudaMemcpyAsync(s.buf[1 - s.cur].cell, p, pb, from, h->st), "state particles");
     p += pb;
+    CK(h, pic::launch_check_particles(h->g, s.buf[1 - s.cur], hd.count[i], h->bad, h->st), "state check");
+  }
+  unsigned long long bad = 0;
+  CK(h, cudaMemcpyAsync(&bad, h->bad, sizeof(bad), cudaMemcpyDeviceToHost, h->st), "bad count");
+  CK(h, cudaStreamSynchronize(h->st), "sync");
+  if (bad)
+    return fail(h, PIC_EINVAL,
+                "state blob holds " + std::to_string(bad) +
+                    " invalid particle slot(s) (cell outside the grid, offset outside [0, 1), non-finite momentum "
+                    "or weight, or beyond an absorbing wall); nothing was loaded");
+  CK(h, cudaMemcpyAsync(h->E[0], pf, 6 * fb, from, h->st), "state fields");
+  pf += 6 * fb;
+  CK(h, cudaMemcpyAsync(h->J[0], pf, 3 * fb, from, h->st), "state J");
+  pf += 3 * fb;
+  CK(h, cudaMemcpyAsync(h->rho_bg, pf, sizeof(double) * (size_t)h->g.ncell, from, h->st), "state background");
+  for (int i = 0; i < h->nsp; ++i) {
+    Species &s = h->sp[i];
+    s.cur = 1 - s.cur;
     CK(h, cudaMemcpyAsync(s.d_count, &hd.count[i], sizeof(int64_t), cudaMemcpyHostToDevice, h->st), "count");
     s.h_count = hd.count[i];
     s.need_sort = true;

@@ -208,6 +208,32 @@ __global__ void k_load(int dims, int n0, int n1, int n2, double rdx0, double rdx
   }
 }
 
+// ---- validation of particle storage copied in from outside (state resume) ----
+// A slot below n is valid when it is dead (cell -1) or when its cell lies in
+// the grid (and, with absorbing x walls, its position between them), its
+// offsets on the grid's axes are in [0, 1) and its momenta and weight are
+// finite.  Invalid slots are counted in *bad.
+template <class R>
+__global__ void k_check_particles(int dims, int n0, int64_t ncell, int absorb, Particles p, int64_t n,
+                                  unsigned long long *bad) {
+  for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < n; q += (int64_t)gridDim.x * blockDim.x) {
+    const int c = p.cell[q];
+    if (c == -1) continue;
+    bool ok = c >= 0 && (int64_t)c < ncell;
+    for (int d = 0; d < dims; ++d) {
+      const R f = static_cast<const R *>(p.off[d])[q];
+      ok = ok && f >= R(0) && f < R(1);  // false for NaN
+    }
+    for (int d = 0; d < 3; ++d) ok = ok && isfinite(static_cast<const R *>(p.u[d])[q]);
+    ok = ok && isfinite(static_cast<const R *>(p.w)[q]);
+    if (ok && absorb) {
+      const double X = (double)(c % n0) + (double)static_cast<const R *>(p.off[0])[q];
+      ok = X >= kWallLo && X < n0 - kWallHiMargin;
+    }
+    if (!ok) atomicAdd(bad, 1ull);
+  }
+}
+
 // ---- particle unload: (cell, offset) -> global FP64 ----
 template <class R>
 __global__ void k_unload(int dims, int n0, int n1, double dx0, double dx1, double dx2, Particles p,
@@ -551,6 +577,18 @@ cudaError_t launch_load(const Grid &g, const Particles &p, int64_t offset, int64
   else
     k_load<float><<<nb, 256, 0, st>>>(g.dims, g.n[0], g.n[1], g.n[2], 1.0 / g.dx[0], 1.0 / g.dx[1], 1.0 / g.dx[2],
                                       absorb, p, offset, n, x, y, z, ux, uy, uz, w, id, id_base, bad);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_check_particles(const Grid &g, const Particles &p, int64_t n, unsigned long long *bad,
+                                  cudaStream_t st) {
+  if (n <= 0) return cudaSuccess;
+  const int nb = grid_blocks(n, 256);
+  const int absorb = g.absorb_lo || g.absorb_hi;
+  if (g.prec == 1)
+    k_check_particles<double><<<nb, 256, 0, st>>>(g.dims, g.n[0], g.ncell, absorb, p, n, bad);
+  else
+    k_check_particles<float><<<nb, 256, 0, st>>>(g.dims, g.n[0], g.ncell, absorb, p, n, bad);
   return cudaGetLastError();
 }
 

@@ -178,6 +178,11 @@ cudaError_t launch_load(const Grid &g, const Particles &p, int64_t offset, int64
                         const double *y, const double *z, const double *ux, const double *uy, const double *uz,
                         const double *w, const uint32_t *id, uint32_t id_base, unsigned long long *bad,
                         cudaStream_t st);
+// Count (into *bad) the slots below n of p that are neither dead nor a valid
+// particle of the grid: cell outside it, offsets outside [0, 1), non-finite
+// momenta or weight, or a position beyond absorbing walls.
+cudaError_t launch_check_particles(const Grid &g, const Particles &p, int64_t n, unsigned long long *bad,
+                                  cudaStream_t st);
 cudaError_t launch_unload(const Grid &g, const Particles &p, const int64_t *d_count, int64_t nmax, double *x,
                           double *y, double *z, double *ux, double *uy, double *uz, double *w, uint32_t *id,
                           int32_t *alive, cudaStream_t st);

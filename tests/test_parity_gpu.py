@@ -10,7 +10,7 @@ import pytest
 
 from paper_1503_02464_gb300 import synth
 
-from _parity import build_gpu, build_oracle, compare_fields, compare_particles
+from _parity import build_gpu, build_oracle, compare_fields, compare_particles, j_floor
 
 pytestmark = pytest.mark.gpu
 
@@ -60,7 +60,9 @@ def test_fp32_after_10_steps(dims, order, n, tile, ppc, uth):
     s = build_gpu(wl, parts, "fp32", tile=tile)
     o.step(10)
     s.step(10)
-    fe = compare_fields(o, s, ["Ex", "Ey", "Ez", "Bx", "By", "Bz"])
+    # every field, J included (the fixed-point deposit window is what sets
+    # the FP32 current apart from the oracle's FP64 one)
+    fe = compare_fields(o, s, j_abs=j_floor(wl, parts))
     du, dx = compare_particles(o, s, wl)
     print("fp32 after 10 steps:", fe, du, dx)
     for k, v in fe.items():
@@ -103,14 +105,14 @@ def test_escape_path(precision):
     for step in range(1, 9):
         o.step(1)
         s.step(1)
-    fe = compare_fields(o, s)
+    fe = compare_fields(o, s, j_abs=j_floor(wl, parts))
     du, dx = compare_particles(o, s, wl)
     d = s.diag()
     assert d["n_escaped"] > 0
     tol = FP64_TOL_PER_STEP * 8 if precision == "fp64" else FP32_TOL
+    print(precision, "escape path after 8 steps:", fe, du)
     for k, v in fe.items():
-        if precision == "fp64" or not k.startswith("J"):
-            assert v <= tol, (k, v)
+        assert v <= tol, (k, v)
     assert du <= tol
 
 

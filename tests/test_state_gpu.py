@@ -96,3 +96,60 @@ def test_state_rejects_a_different_configuration():
         c.load_state(blob)
     with pytest.raises(capi.PicError):
         a.load_state(blob[:100])
+
+
+def _species0_arrays(blob, ncell, dims, rsize):
+    """Byte offsets of the cell array and the first offset array of the only
+    species in a state blob: the particle storage is the blob's tail, one
+    allocation of 256-byte aligned arrays (cell, offsets, u, w, id), and the
+    header stores the species' slot count right after the cell count."""
+    head = blob[:1024].tobytes()
+    at = head.find(np.int64(ncell).tobytes())
+    assert at > 0
+    slots = int(np.frombuffer(head[at + 8:at + 16], dtype=np.int64)[0])
+    a256 = lambda b: (b + 255) // 256 * 256  # noqa: E731
+    pb = a256(slots * 4) + (dims + 4) * a256(slots * rsize) + a256(slots * 4)
+    cell0 = len(blob) - pb
+    return cell0, cell0 + a256(slots * 4)
+
+
+@pytest.mark.parametrize("precision", ["fp32", "fp64"])
+def test_state_rejects_invalid_particles(precision):
+    """A blob whose particle storage holds a cell outside the grid or a
+    non-finite offset is refused (PIC_EINVAL) before it replaces anything:
+    the simulation keeps its own state and steps on."""
+    wl = synth.small(2, (32, 32), 2, 2, 0.1, 3)
+    a = _make(wl, precision)
+    a.load(0, wl.particles(0))
+    a.step(2)
+    blob = a.state()
+    rsize = 4 if precision == "fp32" else 8
+    cell0, off0 = _species0_arrays(blob, 32 * 32, 2, rsize)
+    cells = np.frombuffer(blob[cell0:cell0 + 4 * 64].tobytes(), dtype=np.int32)
+    live = int(np.nonzero(cells >= 0)[0][0])
+
+    b = _make(wl, precision)
+    pb = wl.particles(0)
+    pb["ux"] = pb["ux"] * 0.5
+    b.load(0, pb)
+    b.step(1)
+    before = b.diag()
+    for corrupt in ("cell", "offset"):
+        bad = blob.copy()
+        if corrupt == "cell":
+            bad[cell0 + 4 * live:cell0 + 4 * live + 4] = np.frombuffer(np.int32(32 * 32 + 5).tobytes(), np.uint8)
+        else:
+            nan = np.float32(np.nan) if rsize == 4 else np.float64(np.nan)
+            bad[off0 + rsize * live:off0 + rsize * (live + 1)] = np.frombuffer(nan.tobytes(), np.uint8)
+        with pytest.raises(capi.PicError) as ei:
+            b.load_state(bad)
+        assert ei.value.code == capi.PIC_EINVAL
+        assert "invalid particle" in str(ei.value)
+        after = b.diag()
+        assert after["step"] == before["step"] and after["n_alive"] == before["n_alive"]
+        # FP64 sums taken with atomics: equal to round-off
+        assert abs(after["energy_kinetic"] - before["energy_kinetic"]) <= 1e-13 * before["energy_kinetic"]
+        assert abs(after["energy_field"] - before["energy_field"]) <= 1e-13 * before["energy_field"]
+    b.step(1)
+    b.load_state(blob)  # the intact blob still loads
+    assert b.diag()["step"] == 2
