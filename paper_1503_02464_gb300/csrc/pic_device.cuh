@@ -80,44 +80,100 @@ template <class R, int ORDER> struct GatherAxis {
 // Deposit stencil along one axis (Esirkepov, compact form): the shapes
 // before (S0, offset f in the old cell) and after (S1, offset fn in the cell
 // shifted by s) a move, on NW = ORDER + 2 consecutive nodes starting at `rel`
-// (relative to the old cell).
+// (relative to the old cell); DS = S1 - S0.
+//
+// DS is taken in factored form, never as the difference of the two shape
+// values, so that it keeps the precision of the offsets however small the
+// move (the difference would lose it: a particle moving 1e-4 cells changes
+// its weights by 1e-4, and S1 - S0 in FP32 then carries a 1e-3 relative
+// error).  With the nearest node N0 of the old position (TSC) and the
+// offsets d0, d1 of the two positions from it:
+//  - support unchanged: DS = (D (s - 1)/2, -D s, D (s + 1)/2) on N0-1..N0+1,
+//    D = d1 - d0, s = d0 + d1 (differences of squares of the quadratic
+//    pieces);
+//  - nearest node moves up to N0 + 1: with g0, g1 the distances of the two
+//    positions below and above the half-integer N0 + 1/2 they straddle,
+//    DS = (-g0^2/2, -g1 (2 - g1)/2 - g0 (1 - g0), g1 (1 - g1) + g0 (2 - g0)/2,
+//    g1^2/2) on N0-1..N0+2 (each piece of the shape changed from its value
+//    at the half-integer, where the pieces meet);
+//  - down to N0 - 1: the mirror image on N0-2..N0+1.
+// CIC: DS = (-D, D) within a cell; across the face c+1 (down: c) with g0,
+// g1 the distances to it, (-g0, g0 - g1, g1) (mirror: (g1, g0 - g1, -g0)).
+// Each form equals S1 - S0 exactly in real arithmetic.
 template <class R, int ORDER> struct DepositAxis {
   static constexpr int NW = ORDER + 2;
   int rel;
   R S0[NW], DS[NW];
   __device__ __forceinline__ void set(R f, int s, R fn) {
-    R w0[ORDER + 1], w1[ORDER + 1];
-    int n0, n1;
     if (ORDER == 2) {
       const int h0 = f >= R(0.5), h1 = fn >= R(0.5);
-      tsc3<R>(f - R(h0), w0);
-      tsc3<R>(fn - R(h1), w1);
-      n0 = h0 - 1;      // first node of the old support
-      n1 = s + h1 - 1;  // first node of the new support
+      const int k = s + h1 - h0;  // nearest node moves by k (|k| <= 1 under the Courant limit)
+      const R d0 = f - R(h0);     // old position from N0, in [-1/2, 1/2)
+      const R e1 = fn - R(h1);    // new position from its own nearest node
+      R w0[3];
+      tsc3<R>(d0, w0);
+      if (k == 0) {
+        rel = h0 - 1;
+        const R dl = e1 - d0, sg = d0 + e1, hd = R(0.5) * dl;
+        S0[0] = w0[0];
+        S0[1] = w0[1];
+        S0[2] = w0[2];
+        DS[0] = hd * (sg - R(1));
+        DS[1] = -dl * sg;
+        DS[2] = hd * (sg + R(1));
+        S0[NW - 1] = DS[NW - 1] = R(0);
+      } else if (k > 0) {
+        rel = h0 - 1;
+        const R g0 = R(0.5) - d0, g1 = e1 + R(0.5);
+        S0[0] = w0[0];
+        S0[1] = w0[1];
+        S0[2] = w0[2];
+        S0[NW - 1] = R(0);
+        DS[0] = R(-0.5) * g0 * g0;
+        DS[1] = R(-0.5) * g1 * (R(2) - g1) - g0 * (R(1) - g0);
+        DS[2] = g1 * (R(1) - g1) + R(0.5) * g0 * (R(2) - g0);
+        DS[3] = R(0.5) * g1 * g1;
+      } else {
+        rel = h0 - 2;
+        const R g0 = R(0.5) + d0, g1 = R(0.5) - e1;
+        S0[0] = R(0);
+        S0[1] = w0[0];
+        S0[2] = w0[1];
+        S0[3] = w0[2];
+        DS[0] = R(0.5) * g1 * g1;
+        DS[1] = g1 * (R(1) - g1) + R(0.5) * g0 * (R(2) - g0);
+        DS[2] = R(-0.5) * g1 * (R(2) - g1) - g0 * (R(1) - g0);
+        DS[3] = R(-0.5) * g0 * g0;
+      }
     } else {
-      w0[0] = R(1) - f;
-      w0[1] = f;
-      w1[0] = R(1) - fn;
-      w1[1] = fn;
-      n0 = 0;
-      n1 = s;
-    }
-    rel = n0 < n1 ? n0 : n1;
-    // each support starts at offset 0 or 1 inside the NW-node run; pad the
-    // weights with a zero on either side and pick the window
-    R p0[NW + 1], p1[NW + 1];
-    p0[0] = p1[0] = R(0);
-    p0[NW] = p1[NW] = R(0);
-#pragma unroll
-    for (int q = 0; q <= ORDER; ++q) {
-      p0[q + 1] = w0[q];
-      p1[q + 1] = w1[q];
-    }
-    const bool o0 = n0 != rel, o1 = n1 != rel;
-#pragma unroll
-    for (int k = 0; k < NW; ++k) {
-      S0[k] = o0 ? p0[k] : p0[k + 1];
-      DS[k] = (o1 ? p1[k] : p1[k + 1]) - S0[k];
+      if (s == 0) {
+        rel = 0;
+        const R dl = fn - f;
+        S0[0] = R(1) - f;
+        S0[1] = f;
+        S0[2] = R(0);
+        DS[0] = -dl;
+        DS[1] = dl;
+        DS[2] = R(0);
+      } else if (s > 0) {
+        rel = 0;
+        const R g0 = R(1) - f, g1 = fn;
+        S0[0] = g0;
+        S0[1] = f;
+        S0[2] = R(0);
+        DS[0] = -g0;
+        DS[1] = g0 - g1;
+        DS[2] = g1;
+      } else {
+        rel = -1;
+        const R g0 = f, g1 = R(1) - fn;
+        S0[0] = R(0);
+        S0[1] = R(1) - f;
+        S0[2] = f;
+        DS[0] = g1;
+        DS[1] = g0 - g1;
+        DS[2] = -g0;
+      }
     }
   }
   __device__ __forceinline__ void zero() {

@@ -349,6 +349,236 @@ __device__ __forceinline__ void unpack_job(int j, int l[3], int s[3]) {
   }
 }
 
+// ---- settled deposit (FP32) -------------------------------------------
+// Most particles keep their shape support over a step: for TSC the nearest
+// node does not change, for CIC the cell does not.  For them the Esirkepov
+// stencil shrinks from ORDER + 2 to ORDER + 1 nodes per axis (3D TSC: 54
+// contributions instead of up to 144).  The shape change DS = S1 - S0 is
+// taken in the factored form of DepositAxis (TSC, offsets d0, d1 of the two
+// positions from their common nearest node, D = d1 - d0, sg = d0 + d1:
+//   DS = (D (sg - 1) / 2, -D sg, D (sg + 1) / 2);  CIC: DS = (-D, D)),
+// which keeps FP32's relative precision however small the move, where the
+// difference of the two shapes would lose it.  The factored values equal
+// S1 - S0 in exact arithmetic, so the current still satisfies the discrete
+// continuity equation with rho = sum q w S (to FP32 round-off of S).
+template <int ORDER> struct SettledAxis {
+  static constexpr int NS = ORDER + 1;
+  int rel;    // first support node relative to the old cell
+  float S0[NS], DS[NS];
+  float dl;   // displacement in cells
+  // false when the support changes (then nothing is set)
+  __device__ __forceinline__ bool set(float f0, int s, float f1) {
+    if (ORDER == 2) {
+      const int h0 = f0 >= 0.5f, h1 = f1 >= 0.5f;
+      if (s + h1 != h0) return false;
+      rel = h0 - 1;
+      const float d0 = f0 - (float)h0, d1 = f1 - (float)h1;  // both from the same node
+      dl = d1 - d0;
+      const float sg = d0 + d1;
+      tsc3<float>(d0, S0);
+      const float hd = 0.5f * dl;
+      DS[0] = hd * (sg - 1.0f);
+      DS[1] = -dl * sg;
+      DS[2] = hd * (sg + 1.0f);
+    } else {
+      if (s != 0) return false;
+      rel = 0;
+      S0[0] = 1.0f - f0;
+      S0[1] = f0;
+      dl = f1 - f0;
+      DS[0] = -dl;
+      DS[NS - 1] = dl;
+    }
+    return true;
+  }
+  __device__ __forceinline__ void zero() {
+    rel = 0;
+    dl = 0.0f;
+#pragma unroll
+    for (int k = 0; k < NS; ++k) S0[k] = DS[k] = 0.0f;
+    S0[0] = 1.0f;
+  }
+};
+
+// Add the contribution p q (window units) at the shared byte address sa of
+// its low word; the high word lies JS words further.  Same split as
+// WinAcc<float>::add, without the scratch-word select, so that the address
+// is one base register plus a compile-time offset for the whole stencil.
+template <int JS> __device__ __forceinline__ void fx_add(unsigned sa, float p, float q) {
+  const float y = fmaf(p, q, WinAcc<float>::kMagicHi);
+  const float r = y - WinAcc<float>::kMagicHi;
+  const float lf = fmaf(p, q, -r);
+  const int hi = __float_as_int(y) - __float_as_int(WinAcc<float>::kMagicHi);
+  const int lo = __float2int_rn(lf);
+  asm volatile("red.shared.add.s32 [%0], %1;\n\tred.shared.add.s32 [%2], %3;" ::"r"(sa), "r"(lo),
+               "r"(sa + 4u * (unsigned)JS), "r"(hi));
+}
+
+// Esirkepov deposit of a settled particle on its ORDER + 1 support nodes per
+// axis (compile-time strides SY, SZ in nodes; sb = byte address of the Jx low
+// word of the stencil's first node).  Same brackets as deposit_win: Jx gets
+// Px (S0y S0z + DSy S0z/2 + S0y DSz/2 + DSy DSz/3), cyclic; in 2D3V
+// Jz = q w vz (S0x S0y + DSx S0y/2 + S0x DSy/2 + DSx DSy/3).  The running
+// sums of DS along an axis end at -DS[last] (the whole sum vanishes).
+template <int ORDER, int DIM, int SY, int SZ, int JS>
+__device__ __forceinline__ void deposit_settled_win(unsigned sb, const SettledAxis<ORDER> &X,
+                                                    const SettledAxis<ORDER> &Y, const SettledAxis<ORDER> &Z,
+                                                    float cx, float cy, float cz, float qwvz) {
+  constexpr int NS = ORDER + 1, M = ORDER;
+  constexpr unsigned CY = 8u * JS, CZ = 16u * JS;  // byte offsets of the Jy, Jz low words
+  float Px[M], Py[M], Pz[M];
+  {
+    float ra = 0.0f, rb = 0.0f, rc = 0.0f;
+#pragma unroll
+    for (int k = 0; k < M - 1; ++k) {
+      ra += X.DS[k];
+      rb += Y.DS[k];
+      rc += Z.DS[k];
+      Px[k] = cx * ra;
+      Py[k] = cy * rb;
+      Pz[k] = cz * rc;
+    }
+    Px[M - 1] = -cx * X.DS[NS - 1];
+    Py[M - 1] = -cy * Y.DS[NS - 1];
+    Pz[M - 1] = -cz * Z.DS[NS - 1];
+  }
+  if (DIM == 3) {
+    float hz[NS], tz[NS], hx[NS], tx[NS];
+#pragma unroll
+    for (int k = 0; k < NS; ++k) {
+      hz[k] = Z.S0[k] + 0.5f * Z.DS[k];
+      tz[k] = 0.5f * Z.S0[k] + Z.DS[k] * (1.0f / 3.0f);
+      hx[k] = X.S0[k] + 0.5f * X.DS[k];
+      tx[k] = 0.5f * X.S0[k] + X.DS[k] * (1.0f / 3.0f);
+    }
+#pragma unroll
+    for (int c = 0; c < NS; ++c)
+#pragma unroll
+      for (int b = 0; b < NS; ++b) {
+        const float br = Y.S0[b] * hz[c] + Y.DS[b] * tz[c];
+#pragma unroll
+        for (int a = 0; a < M; ++a) fx_add<JS>(sb + 4u * (unsigned)(c * SZ + b * SY + a), Px[a], br);
+      }
+#pragma unroll
+    for (int c = 0; c < NS; ++c)
+#pragma unroll
+      for (int a = 0; a < NS; ++a) {
+        const float br = Z.S0[c] * hx[a] + Z.DS[c] * tx[a];
+#pragma unroll
+        for (int b = 0; b < M; ++b) fx_add<JS>(sb + CY + 4u * (unsigned)(c * SZ + b * SY + a), Py[b], br);
+      }
+#pragma unroll
+    for (int b = 0; b < NS; ++b) {
+      const float hy = Y.S0[b] + 0.5f * Y.DS[b];
+      const float ty = 0.5f * Y.S0[b] + Y.DS[b] * (1.0f / 3.0f);
+#pragma unroll
+      for (int a = 0; a < NS; ++a) {
+        const float br = X.S0[a] * hy + X.DS[a] * ty;
+#pragma unroll
+        for (int c = 0; c < M; ++c) fx_add<JS>(sb + CZ + 4u * (unsigned)(c * SZ + b * SY + a), Pz[c], br);
+      }
+    }
+  } else {
+#pragma unroll
+    for (int b = 0; b < NS; ++b) {
+      const float hy = Y.S0[b] + 0.5f * Y.DS[b];
+      const float ty = 0.5f * Y.S0[b] + Y.DS[b] * (1.0f / 3.0f);
+#pragma unroll
+      for (int a = 0; a < M; ++a) fx_add<JS>(sb + 4u * (unsigned)(b * SY + a), Px[a], hy);
+#pragma unroll
+      for (int a = 0; a < NS; ++a)
+        fx_add<JS>(sb + CZ + 4u * (unsigned)(b * SY + a), qwvz, X.S0[a] * hy + X.DS[a] * ty);
+    }
+#pragma unroll
+    for (int a = 0; a < NS; ++a) {
+      const float hx = X.S0[a] + 0.5f * X.DS[a];
+#pragma unroll
+      for (int b = 0; b < M; ++b) fx_add<JS>(sb + CY + 4u * (unsigned)(b * SY + a), Py[b], hx);
+    }
+  }
+}
+
+// Deposit of a particle whose support did not change (FP32 runs).  Returns
+// false, depositing nothing, when the support changes on some axis: such a
+// particle takes the general ORDER + 2 node stencil (deposit_particle),
+// through the block's queue of deferred jobs.
+template <int DIM, int ORDER>
+__device__ __forceinline__ bool deposit_settled(const PushArgs<float> &a, const WinAcc<float> &acc, const int l[3],
+                                                const int s[3], const float f[3], const float fn[3], float w,
+                                                float vz) {
+  using G = Geo<DIM, ORDER>;
+  SettledAxis<ORDER> X, Y, Z;
+  bool ok = X.set(f[0], s[0], fn[0]);
+  ok = Y.set(f[1], s[1], fn[1]) && ok;
+  if (DIM == 3) ok = Z.set(f[2], s[2], fn[2]) && ok;
+  else Z.zero();
+  if (!ok) return false;
+  // a warp whose settled particles neither move nor (2D3V) carry vz deposits nothing
+  const bool moves = w != 0.0f && (X.dl != 0.0f || Y.dl != 0.0f || (DIM == 3 ? Z.dl != 0.0f : vz != 0.0f));
+  if (!__any_sync(__activemask(), moves)) return true;
+  constexpr int oJ = G::D + G::LOJ;
+#ifdef PIC_CHECKED
+  {
+    const int rel[3] = {X.rel, Y.rel, Z.rel};
+    constexpr int JW[3] = {G::JX, G::JY, G::JZ};
+    bool in = true;
+#pragma unroll
+    for (int d = 0; d < DIM; ++d) in = in && l[d] + rel[d] + oJ >= 0 && l[d] + rel[d] + oJ + ORDER < JW[d];
+    if (!PIC_CHECK(in, a.ctr)) return true;
+  }
+#endif
+  const int jb = (l[0] + X.rel + oJ) + (l[1] + Y.rel + oJ) * G::JX + (DIM == 3 ? (l[2] + Z.rel + oJ) * G::JP : 0);
+  const unsigned sb = (unsigned)__cvta_generic_to_shared(acc.w) + 4u * (unsigned)jb;
+  const float ws = w * acc.scale;
+  deposit_settled_win<ORDER, DIM, G::JX, G::JP, G::JS>(sb, X, Y, Z, a.jfac[0] * ws, a.jfac[1] * ws,
+                                                        a.jfac[2] * ws, a.qz * ws * vz);
+  return true;
+}
+
+// Deferred deposit jobs of particles whose support changes (FP32 runs): up
+// to kQCap entries in shared memory, appended by warps through a shared
+// counter and deposited once, at the end of the work item, by all threads
+// together (dq_drain), so that the general stencil runs on full warps
+// instead of on the few lanes of every warp that hold such a particle.  A
+// job that finds the queue full is deposited on the spot.
+constexpr int kQCap = 224;
+struct DepQueue {
+  int *job;    // [kQCap] packed cell and shift (pack_job) | axes whose support changes << 22
+  float *f;    // [7][kQCap]: old offsets x y z, new offsets x y z, weight (2D3V: vz in the old z slot)
+  int *tail;   // shared counter of appended jobs
+};
+
+// Append this lane's job; false when the queue is full.
+__device__ __forceinline__ bool dq_push(const DepQueue &q, int job, const float f[3], const float fn[3], float w,
+                                        float vz, bool twod) {
+  const unsigned act = __activemask();
+  const int lane = threadIdx.x & 31, leader = __ffs(act) - 1;
+  int base = 0;
+  if (lane == leader) base = atomicAdd(q.tail, __popc(act));
+  base = __shfl_sync(act, base, leader);
+  const int at = base + __popc(act & ((1u << lane) - 1u));
+  if (at >= kQCap) return false;
+  q.job[at] = job;
+#pragma unroll
+  for (int d = 0; d < 3; ++d) {
+    q.f[d * kQCap + at] = (twod && d == 2) ? vz : f[d];
+    q.f[(3 + d) * kQCap + at] = fn[d];
+  }
+  q.f[6 * kQCap + at] = w;
+  return true;
+}
+
+// The axes (bit d) on which a particle's shape support changes over a move.
+template <int ORDER> __device__ __forceinline__ int support_change(const float f[3], const int s[3], const float fn[3]) {
+  int m = 0;
+#pragma unroll
+  for (int d = 0; d < 3; ++d) {
+    const bool ch = ORDER == 2 ? (s[d] + (fn[d] >= 0.5f) != (f[d] >= 0.5f)) : s[d] != 0;
+    m |= ch ? 1 << d : 0;
+  }
+  return m;
+}
+
 // The per-particle physics shared by the tile kernel and the escape kernel:
 // given gathered E, B, advance u, move, and build the deposit stencils.
 template <class R, int ORDER, int DIM>
@@ -424,6 +654,46 @@ __device__ __forceinline__ bool deposit_particle(const PushArgs<R> &a, const Win
   return true;
 }
 
+// Deposit the n <= kQCap queued jobs on the general stencil, one per thread.
+// The jobs are first ordered by the axes on which their support changes
+// (a counting sort into `order`, kQCap ints of shared memory), so that the
+// lanes of a warp mostly share that set and the warp-uniform skip of the
+// outer stencil shell in deposit_particle drops the axes that did not
+// change.  Block-wide: every thread of the block calls it.
+template <int DIM, int ORDER>
+__device__ __forceinline__ void dq_drain(const PushArgs<float> &a, const WinAcc<float> &acc, const DepQueue &q, int n,
+                                         int *order) {
+  __shared__ int s_cls[8];
+  const int i = threadIdx.x;
+  if (i < 8) s_cls[i] = 0;
+  __syncthreads();
+  int cls = 0, rank = 0;
+  if (i < n) {
+    cls = (q.job[i] >> 22) & 7;
+    rank = atomicAdd(&s_cls[cls], 1);
+  }
+  __syncthreads();
+  if (i < n) {
+    int start = 0;
+#pragma unroll
+    for (int c = 0; c < 8; ++c) start += c < cls ? s_cls[c] : 0;
+    order[start + rank] = i;
+  }
+  __syncthreads();
+  if (i >= n) return;
+  const int at = order[i];
+  int l[3], sh[3];
+  unpack_job(q.job[at] & ((1 << 22) - 1), l, sh);
+  float f[3], fn[3];
+#pragma unroll
+  for (int d = 0; d < 3; ++d) {
+    f[d] = (DIM == 2 && d == 2) ? 0.0f : q.f[d * kQCap + at];
+    fn[d] = q.f[(3 + d) * kQCap + at];
+  }
+  const float vz = DIM == 2 ? q.f[2 * kQCap + at] : 0.0f;
+  deposit_particle<float, DIM, ORDER>(a, acc, l, sh, f, fn, q.f[6 * kQCap + at], vz);
+}
+
 template <class R, int DIM, int ORDER>
 // Blocks per SM the register allocation is held to: FP32 3D TSC windows
 // fill half the shared memory (two blocks); the 3D CIC windows leave room for
@@ -445,6 +715,13 @@ __global__ void __launch_bounds__(kThreads, sizeof(R) == 4 ? (DIM == 2 ? 4 : (OR
   R *sW = sU + 3 * kThreads;                  // 256
   int32_t *sCell = reinterpret_cast<int32_t *>(sW + kThreads);  // 256
   int32_t *sJob = sCell + kThreads;  // FP32 3D: 256 deposit jobs
+  // FP32: queue of deferred deposit jobs (after the jobs in 3D, after the cells in 2D)
+  constexpr bool kSettled = sizeof(R) == 4;
+  DepQueue dq;
+  dq.job = sCell + (DIM == 3 ? 2 : 1) * kThreads;
+  dq.f = reinterpret_cast<float *>(dq.job + kQCap);
+  __shared__ int s_qtail;
+  dq.tail = &s_qtail;
   __shared__ unsigned int s_clamp;
   __shared__ double s_scale;
   __shared__ unsigned int s_emax[3];
@@ -487,6 +764,7 @@ __global__ void __launch_bounds__(kThreads, sizeof(R) == 4 ? (DIM == 2 ? 4 : (OR
   for (int q = tid; q < 6 * G::JS; q += kThreads) reinterpret_cast<int *>(sJraw)[q] = 0;  // 24 B per node
   if (tid == 0) {
     s_clamp = 0;
+    s_qtail = 0;
     s_emax[0] = s_emax[1] = s_emax[2] = 0u;
     s_qsum = 0.f;
     s_wsum = 0.f;
@@ -661,8 +939,17 @@ __global__ void __launch_bounds__(kThreads, sizeof(R) == 4 ? (DIM == 2 ? 4 : (OR
           if (sizeof(R) == 4)
             my_q1 += fabsf((float)sW[ep]) * fminf(1.f, sqrtf((float)(u[0] * u[0] + u[1] * u[1] + u[2] * u[2])));
 
-          if (!kSplit && !deposit_particle<R, DIM, ORDER>(a, acc, l, s, f, fn, sW[ep], u[2] * ig))
-            break;  // (checked build) leaves the particle as it was
+          if (!kSplit) {
+            bool done = false;
+            if constexpr (kSettled) {
+              const R vz = u[2] * ig;
+              done = deposit_settled<DIM, ORDER>(a, acc, l, s, f, fn, sW[ep], vz) ||
+                     dq_push(dq, pack_job(l, s) | support_change<ORDER>(f, s, fn) << 22, f, fn, sW[ep], vz,
+                             DIM == 2);
+            }
+            if (!done && !deposit_particle<R, DIM, ORDER>(a, acc, l, s, f, fn, sW[ep], u[2] * ig))
+              break;  // (checked build) leaves the particle as it was
+          }
 
           // ---- the new state ----
           int nc = -1;  // removed at an absorbing wall after depositing its move
@@ -721,7 +1008,11 @@ __global__ void __launch_bounds__(kThreads, sizeof(R) == 4 ? (DIM == 2 ? 4 : (OR
             f[d] = sU[d * kThreads + e];
             fn[d] = sOff[d * kThreads + e];
           }
-          deposit_particle<R, DIM, ORDER>(a, acc, l, s, f, fn, sW[e], R(0));
+          bool done = false;
+          if constexpr (kSettled)
+            done = deposit_settled<DIM, ORDER>(a, acc, l, s, f, fn, sW[e], 0.0f) ||
+                   dq_push(dq, job | support_change<ORDER>(f, s, fn) << 22, f, fn, sW[e], 0.0f, false);
+          if (!done) deposit_particle<R, DIM, ORDER>(a, acc, l, s, f, fn, sW[e], R(0));
         }
       }
     }
@@ -735,6 +1026,11 @@ __global__ void __launch_bounds__(kThreads, sizeof(R) == 4 ? (DIM == 2 ? 4 : (OR
 #pragma unroll
       for (int d = 0; d < 3; ++d) a.u[d][p] = sU[d * kThreads + tid];
     }
+  }
+  if constexpr (kSettled) {
+    // the deferred jobs of the whole work item (the chunk loop ended on a barrier)
+    const int nq = *(volatile int *)dq.tail;
+    dq_drain<DIM, ORDER>(a, acc, dq, nq > kQCap ? kQCap : nq, sCell);
   }
 
   if (my_clamp) atomicAdd(&s_clamp, my_clamp);
@@ -898,7 +1194,7 @@ template <class R, int DIM, int ORDER> constexpr size_t smem_bytes() {
   // deposit jobs (a packed int per slot)
   constexpr bool split = DIM == 3 && sizeof(R) == 4;
   return (size_t)(6 * G::EN + (DIM + 4) * kThreads) * sizeof(R) + 24 * (size_t)G::JS +
-         (split ? 2 : 1) * kThreads * sizeof(int32_t);
+         (split ? 2 : 1) * kThreads * sizeof(int32_t) + (sizeof(R) == 4 ? 8 * kQCap * sizeof(int32_t) : 0);
 }
 
 template <class R, int DIM, int ORDER>

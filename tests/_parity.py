@@ -50,6 +50,27 @@ def j_floor(wl, parts_list):
     return 4.0 * qw * max(wl.d[:wl.dims]) / wl.dt * 2 * np.spacing(float(n)) * ppc * 4 ** wl.dims
 
 
+def j_floor_fp32(wl, parts_list):
+    """Absolute floor of the FP32 path's current density against an exact
+    trajectory.
+
+    The FP32 path stores each in-cell offset in FP32, so every stored
+    position is rounded by up to half an ulp of the offset, 2^-25 cells, and
+    the discrete continuity equation ties the current to the stored
+    displacement: a contribution q w (dx/dt) (a running sum of S1 - S0, at
+    most the displacement in cells) times a bracket of at most 1 moves by up
+    to q w (dx/dt) 2^-25 against the current of the unrounded move.  A node
+    sums at most ppc * (order + 2)^dims such contributions.  For particles
+    that barely move (a cold target that a pulse has just reached) this
+    rounding, not the arithmetic, separates the FP32 current from the
+    oracle's; the arithmetic itself is checked on the stored moves
+    (test_fp32_deposit_of_stored_moves)."""
+    qw = max((abs(sp.q) * np.abs(p["w"]).max() for sp, p in zip(wl.species, parts_list) if len(p["w"])),
+             default=0.0)
+    ppc = max((sp.ppc for sp in wl.species), default=1)
+    return qw * max(wl.d[:wl.dims]) / wl.dt * 2.0 ** -25 * ppc * (wl.order + 2) ** wl.dims
+
+
 def compare_fields(o, s, names=FIELDS, j_abs=0.0, joint_eb=False):
     """Error of each component relative to the max norm of its vector field
     (max over Ex, Ey, Ez for E; likewise B and J), so that a component that
