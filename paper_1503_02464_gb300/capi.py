@@ -82,9 +82,13 @@ _lib: Optional[ctypes.CDLL] = None
 
 
 def library_path() -> str:
-    """The release library, or with PIC_LIBRARY=checked the build whose
-    kernels check every window and slot index (build.py)."""
-    name = "libpic_checked.so" if os.environ.get("PIC_LIBRARY") == "checked" else "libpic.so"
+    """The release library; with PIC_LIBRARY=checked the build whose kernels
+    check every window and slot index (build.py); with PIC_LIBRARY set to the
+    path of a .so file, that build of the library."""
+    sel = os.environ.get("PIC_LIBRARY", "")
+    if sel.endswith(".so"):
+        return os.path.abspath(sel)
+    name = "libpic_checked.so" if sel == "checked" else "libpic.so"
     return os.path.join(os.path.dirname(os.path.abspath(__file__)), "_build", name)
 
 

@@ -88,6 +88,137 @@ __global__ void __launch_bounds__(256) k_yee_e(YeeArgs<R> a) {
   }
 }
 
+// The same two updates with 16-byte vector accesses along x: a thread takes
+// W = 16 / sizeof(R) consecutive cells of one row (four FP32 or two FP64
+// values per component), on a 3D grid of (x groups, rows, planes), so there
+// is no division per cell and every load and store of a warp is 512
+// contiguous bytes.  The neighbour across the group's end in x is one extra
+// scalar load (cached; the adjacent thread reads it too), with the periodic
+// wrap at the ends of the row.  Used when the row length is a multiple of W
+// (so every component array is 16-byte aligned); the scalar kernels above
+// take the other grids.
+template <class R> struct alignas(16) Pack {
+  R v[16 / sizeof(R)];
+};
+template <class R> __device__ __forceinline__ Pack<R> ldp(const R *p) { return *reinterpret_cast<const Pack<R> *>(p); }
+template <class R> __device__ __forceinline__ void stp(R *p, const Pack<R> &v) { *reinterpret_cast<Pack<R> *>(p) = v; }
+
+template <class R, int DIM>
+__global__ void __launch_bounds__(256) k_yee_b_vec(YeeArgs<R> a) {
+  constexpr int W = 16 / sizeof(R);
+  const int n0 = a.n[0], n1 = a.n[1], n2 = a.n[2];
+  const int nq = n0 / W;
+  const int iq = blockIdx.x * blockDim.x + threadIdx.x;
+  const int j = blockIdx.y * blockDim.y + threadIdx.y;
+  const int k = blockIdx.z;
+  if (iq >= nq || j >= n1) return;
+  const int64_t sy = n0, sz = (int64_t)n0 * n1;
+  const int64_t row = (int64_t)j * sy + (int64_t)k * sz;
+  const int64_t c = row + (int64_t)iq * W;
+  const int64_t cyp = j + 1 < n1 ? c + sy : c + sy - sy * n1;
+  const int64_t cxn = iq + 1 < nq ? c + W : row;  // x + 1 of the group's last cell
+  const Pack<R> ex = ldp(a.E[0] + c), ey = ldp(a.E[1] + c), ez = ldp(a.E[2] + c);
+  const Pack<R> ex_yp = ldp(a.E[0] + cyp), ez_yp = ldp(a.E[2] + cyp);
+  const R ey_xn = a.E[1][cxn], ez_xn = a.E[2][cxn];
+  Pack<R> ex_zp, ey_zp;
+  if (DIM == 3) {
+    const int64_t czp = k + 1 < n2 ? c + sz : c + sz - sz * n2;
+    ex_zp = ldp(a.E[0] + czp);
+    ey_zp = ldp(a.E[1] + czp);
+  }
+  Pack<R> bx = ldp(a.B[0] + c), by = ldp(a.B[1] + c), bz = ldp(a.B[2] + c);
+  // By, Bz half a cell beyond the last node stay as they are at absorbing walls
+  const bool last = a.absorb && iq == nq - 1;
+#pragma unroll
+  for (int w = 0; w < W; ++w) {
+    const R eyx = w + 1 < W ? ey.v[w + 1] : ey_xn, ezx = w + 1 < W ? ez.v[w + 1] : ez_xn;
+    R cx = (ez_yp.v[w] - ez.v[w]) * a.rdx[1];
+    R cy = -(ezx - ez.v[w]) * a.rdx[0];
+    const R cz = (eyx - ey.v[w]) * a.rdx[0] - (ex_yp.v[w] - ex.v[w]) * a.rdx[1];
+    if (DIM == 3) {
+      cx -= (ey_zp.v[w] - ey.v[w]) * a.rdx[2];
+      cy += (ex_zp.v[w] - ex.v[w]) * a.rdx[2];
+    }
+    bx.v[w] -= a.h * cx;
+    if (!(last && w == W - 1)) {
+      by.v[w] -= a.h * cy;
+      bz.v[w] -= a.h * cz;
+    }
+  }
+  stp(a.B[0] + c, bx);
+  stp(a.B[1] + c, by);
+  stp(a.B[2] + c, bz);
+}
+
+template <class R, int DIM>
+__global__ void __launch_bounds__(256) k_yee_e_vec(YeeArgs<R> a) {
+  constexpr int W = 16 / sizeof(R);
+  const int n0 = a.n[0], n1 = a.n[1], n2 = a.n[2];
+  const int nq = n0 / W;
+  const int iq = blockIdx.x * blockDim.x + threadIdx.x;
+  const int j = blockIdx.y * blockDim.y + threadIdx.y;
+  const int k = blockIdx.z;
+  if (iq >= nq || j >= n1) return;
+  const int64_t sy = n0, sz = (int64_t)n0 * n1;
+  const int64_t row = (int64_t)j * sy + (int64_t)k * sz;
+  const int64_t c = row + (int64_t)iq * W;
+  const int64_t cym = j > 0 ? c - sy : c - sy + sy * n1;
+  const int64_t cxp = iq > 0 ? c - 1 : row + n0 - 1;  // x - 1 of the group's first cell
+  const Pack<R> bx = ldp(a.B[0] + c), by = ldp(a.B[1] + c), bz = ldp(a.B[2] + c);
+  const Pack<R> bx_ym = ldp(a.B[0] + cym), bz_ym = ldp(a.B[2] + cym);
+  const R by_xp = a.B[1][cxp], bz_xp = a.B[2][cxp];
+  Pack<R> bx_zm, by_zm;
+  if (DIM == 3) {
+    const int64_t czm = k > 0 ? c - sz : c - sz + sz * n2;
+    bx_zm = ldp(a.B[0] + czm);
+    by_zm = ldp(a.B[1] + czm);
+  }
+  const Pack<R> jx = ldp(a.J[0] + c), jy = ldp(a.J[1] + c), jz = ldp(a.J[2] + c);
+  Pack<R> ex = ldp(a.E[0] + c), ey = ldp(a.E[1] + c), ez = ldp(a.E[2] + c);
+  // at absorbing walls the wall nodes belong to the Mur kernels, and Ex
+  // half a cell beyond the last node is not updated
+  const bool first = a.absorb && iq == 0, last = a.absorb && iq == nq - 1;
+#pragma unroll
+  for (int w = 0; w < W; ++w) {
+    const R byx = w > 0 ? by.v[w - 1] : by_xp, bzx = w > 0 ? bz.v[w - 1] : bz_xp;
+    R cx = (bz.v[w] - bz_ym.v[w]) * a.rdx[1];
+    R cy = -(bz.v[w] - bzx) * a.rdx[0];
+    const R cz = (by.v[w] - byx) * a.rdx[0] - (bx.v[w] - bx_ym.v[w]) * a.rdx[1];
+    if (DIM == 3) {
+      cx -= (by.v[w] - by_zm.v[w]) * a.rdx[2];
+      cy += (bx.v[w] - bx_zm.v[w]) * a.rdx[2];
+    }
+    const bool wall_hi = last && w == W - 1, wall_lo = first && w == 0;
+    if (!wall_hi) ex.v[w] += a.h * (cx - jx.v[w]);
+    if (!wall_hi && !wall_lo) {
+      ey.v[w] += a.h * (cy - jy.v[w]);
+      ez.v[w] += a.h * (cz - jz.v[w]);
+    }
+  }
+  stp(a.E[0] + c, ex);
+  stp(a.E[1] + c, ey);
+  stp(a.E[2] + c, ez);
+}
+
+// Vector path when the row length is a multiple of W and every array is
+// 16-byte aligned; block (x groups, rows) with 256 threads.
+template <class R> bool yee_vec_ok(const Grid &g, const YeeArgs<R> &a, bool with_j) {
+  constexpr int W = 16 / sizeof(R);
+  if (g.n[0] % W != 0 || g.n[2] > 65535) return false;
+  for (int d = 0; d < 3; ++d) {
+    if (reinterpret_cast<uintptr_t>(a.E[d]) % 16 || reinterpret_cast<uintptr_t>(a.B[d]) % 16) return false;
+    if (with_j && reinterpret_cast<uintptr_t>(a.J[d]) % 16) return false;
+  }
+  return true;
+}
+template <class R> void yee_vec_shape(const Grid &g, dim3 &grid, dim3 &block) {
+  constexpr int W = 16 / sizeof(R);
+  const int nq = g.n[0] / W;
+  const int bx = nq >= 64 ? 64 : 32;
+  block = dim3(bx, 256 / bx, 1);
+  grid = dim3((nq + bx - 1) / bx, (g.n[1] + block.y - 1) / block.y, g.n[2]);
+}
+
 template <class R>
 __global__ void k_mur_save(int n0, int n1, int n2, const R *Ey, const R *Ez, double *buf) {
   const int64_t nyz = (int64_t)n1 * n2;
@@ -476,32 +607,45 @@ cudaError_t launch_smooth(const Grid &g, void *f, bool f64, void *tmp, int passe
   return smooth_t<float>(g, static_cast<float *>(f), static_cast<float *>(tmp), passes, compensate, st, nlaunch);
 }
 
-cudaError_t launch_yee_b(const Grid &g, void *const E[3], void *const B[3], double h, cudaStream_t st) {
-  const int nb = grid_blocks(g.ncell, 256);
-  if (g.prec == 1) {
-    auto a = yee_args<double>(g, E, B, nullptr, h);
-    if (g.dims == 3) k_yee_b<double, 3><<<nb, 256, 0, st>>>(a);
-    else k_yee_b<double, 2><<<nb, 256, 0, st>>>(a);
+template <class R> void yee_b_t(const Grid &g, void *const E[3], void *const B[3], double h, cudaStream_t st) {
+  auto a = yee_args<R>(g, E, B, nullptr, h);
+  if (yee_vec_ok<R>(g, a, false)) {
+    dim3 grid, block;
+    yee_vec_shape<R>(g, grid, block);
+    if (g.dims == 3) k_yee_b_vec<R, 3><<<grid, block, 0, st>>>(a);
+    else k_yee_b_vec<R, 2><<<grid, block, 0, st>>>(a);
   } else {
-    auto a = yee_args<float>(g, E, B, nullptr, h);
-    if (g.dims == 3) k_yee_b<float, 3><<<nb, 256, 0, st>>>(a);
-    else k_yee_b<float, 2><<<nb, 256, 0, st>>>(a);
+    const int nb = grid_blocks(g.ncell, 256);
+    if (g.dims == 3) k_yee_b<R, 3><<<nb, 256, 0, st>>>(a);
+    else k_yee_b<R, 2><<<nb, 256, 0, st>>>(a);
   }
+}
+
+template <class R>
+void yee_e_t(const Grid &g, void *const E[3], void *const B[3], void *const J[3], double h, cudaStream_t st) {
+  auto a = yee_args<R>(g, E, B, J, h);
+  if (yee_vec_ok<R>(g, a, true)) {
+    dim3 grid, block;
+    yee_vec_shape<R>(g, grid, block);
+    if (g.dims == 3) k_yee_e_vec<R, 3><<<grid, block, 0, st>>>(a);
+    else k_yee_e_vec<R, 2><<<grid, block, 0, st>>>(a);
+  } else {
+    const int nb = grid_blocks(g.ncell, 256);
+    if (g.dims == 3) k_yee_e<R, 3><<<nb, 256, 0, st>>>(a);
+    else k_yee_e<R, 2><<<nb, 256, 0, st>>>(a);
+  }
+}
+
+cudaError_t launch_yee_b(const Grid &g, void *const E[3], void *const B[3], double h, cudaStream_t st) {
+  if (g.prec == 1) yee_b_t<double>(g, E, B, h, st);
+  else yee_b_t<float>(g, E, B, h, st);
   return cudaGetLastError();
 }
 
 cudaError_t launch_yee_e(const Grid &g, void *const E[3], void *const B[3], void *const J[3], double h,
                          cudaStream_t st) {
-  const int nb = grid_blocks(g.ncell, 256);
-  if (g.prec == 1) {
-    auto a = yee_args<double>(g, E, B, J, h);
-    if (g.dims == 3) k_yee_e<double, 3><<<nb, 256, 0, st>>>(a);
-    else k_yee_e<double, 2><<<nb, 256, 0, st>>>(a);
-  } else {
-    auto a = yee_args<float>(g, E, B, J, h);
-    if (g.dims == 3) k_yee_e<float, 3><<<nb, 256, 0, st>>>(a);
-    else k_yee_e<float, 2><<<nb, 256, 0, st>>>(a);
-  }
+  if (g.prec == 1) yee_e_t<double>(g, E, B, J, h, st);
+  else yee_e_t<float>(g, E, B, J, h, st);
   return cudaGetLastError();
 }
 
