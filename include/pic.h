@@ -325,6 +325,30 @@ int pic_adjoint_step(pic_handle *h, int nsteps);
  * Synchronises. */
 int pic_grad(pic_handle *h, double *d_a0, int species, double *d_w, int mem_kind);
 
+/* Adjoint state, for objectives of the caller's own and for checks of the
+ * transposes (the adjoint of §2's cycle as above; this access has no
+ * counterpart in the paper).  All need pic_adjoint_begin first and
+ * synchronise.  The adjoint arrays are of the run's precision; values pass
+ * as FP64.  Errors: PIC_EINVAL for NULL arguments, a bad selector, species
+ * or memory kind, or no pic_adjoint_begin; PIC_ECUDA.
+ *
+ * pic_adjoint_field: the adjoint of field component `which` (PIC_EX ..
+ *   PIC_BZ: of E, B at the current adjoint time; PIC_JX .. PIC_JZ: of the
+ *   current density of the last reversed step) into out (ncell doubles,
+ *   index i + n0 (j + n1 k) as in pic_fields), host or device per mem_kind.
+ * pic_adjoint_set_field: replace the adjoint of E or B component `which`
+ *   (PIC_EX .. PIC_BZ) by in (ncell doubles): dF/dE, dF/dB of an objective
+ *   F of the fields at the last recorded step.
+ * pic_adjoint_momenta / pic_adjoint_set_momenta: the adjoint of the
+ *   momenta u of a species, one array per component of id_capacity doubles
+ *   indexed by particle id (a NULL pointer skips that component): dF/du of
+ *   an objective of the particles' momenta at the last recorded step. */
+int pic_adjoint_field(pic_handle *h, int which, double *out, int mem_kind);
+int pic_adjoint_set_field(pic_handle *h, int which, const double *in, int mem_kind);
+int pic_adjoint_momenta(pic_handle *h, int species, double *lux, double *luy, double *luz, int mem_kind);
+int pic_adjoint_set_momenta(pic_handle *h, int species, const double *lux, const double *luy, const double *luz,
+                            int mem_kind);
+
 /* ---- state save / resume ----------------------------------------------
  * A run's complete state as one byte blob: fields E, B, J, the background
  * charge, every species' particle storage (in the library's own cell +

@@ -29,7 +29,8 @@ EXPORTED = ["pic_create", "pic_destroy", "pic_last_error", "pic_add_species", "p
             "pic_diag", "pic_energy", "pic_sync", "pic_profile", "pic_timings", "pic_launch_count", "pic_checkpoint",
             "pic_restore", "pic_tape_begin", "pic_adjoint_begin", "pic_adjoint_seed_kinetic", "pic_adjoint_step",
             "pic_grad", "pic_state_size", "pic_state_save", "pic_state_load", "pic_output_due", "pic_output_add", "pic_output_capture", "pic_output_count",
-            "pic_output_read", "pic_output_remove", "pic_field_energy_noalloc", "pic_alu_peak"]
+            "pic_output_read", "pic_output_remove", "pic_field_energy_noalloc", "pic_alu_peak",
+            "pic_adjoint_field", "pic_adjoint_set_field", "pic_adjoint_momenta", "pic_adjoint_set_momenta"]
 
 
 class pic_laser(ctypes.Structure):
@@ -147,6 +148,10 @@ def load(build_if_missing: bool = True) -> ctypes.CDLL:
                              ctypes.c_int], ctypes.c_int),
         "pic_output_remove": ([hp, ctypes.c_int], ctypes.c_int),
         "pic_alu_peak": ([dp, dp, vp], ctypes.c_int),
+        "pic_adjoint_field": ([hp, ctypes.c_int, vp, ctypes.c_int], ctypes.c_int),
+        "pic_adjoint_set_field": ([hp, ctypes.c_int, vp, ctypes.c_int], ctypes.c_int),
+        "pic_adjoint_momenta": ([hp, ctypes.c_int, vp, vp, vp, ctypes.c_int], ctypes.c_int),
+        "pic_adjoint_set_momenta": ([hp, ctypes.c_int, vp, vp, vp, ctypes.c_int], ctypes.c_int),
     }
     for name, (args, res) in sig.items():
         fn = getattr(lib, name)
@@ -357,3 +362,19 @@ def pic_alu_peak(stream=None) -> tuple:
     a, b = ctypes.c_double(), ctypes.c_double()
     check(None, load().pic_alu_peak(ctypes.byref(a), ctypes.byref(b), stream))
     return a.value, b.value
+
+
+def pic_adjoint_field(h, which: int, out_ptr, mem_kind: int) -> None:
+    check(h, load().pic_adjoint_field(h, int(which), out_ptr, int(mem_kind)))
+
+
+def pic_adjoint_set_field(h, which: int, in_ptr, mem_kind: int) -> None:
+    check(h, load().pic_adjoint_set_field(h, int(which), in_ptr, int(mem_kind)))
+
+
+def pic_adjoint_momenta(h, species: int, ptrs, mem_kind: int) -> None:
+    check(h, load().pic_adjoint_momenta(h, int(species), *ptrs, int(mem_kind)))
+
+
+def pic_adjoint_set_momenta(h, species: int, ptrs, mem_kind: int) -> None:
+    check(h, load().pic_adjoint_set_momenta(h, int(species), *ptrs, int(mem_kind)))

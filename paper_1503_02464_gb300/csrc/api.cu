@@ -122,6 +122,7 @@ struct pic_handle {
   int64_t id_cap = 0;
   void *lE[3] = {}, *lB[3] = {}, *lJ[3] = {};
   double *pend = nullptr, *da0 = nullptr, *objF = nullptr;
+  double *adj_stage = nullptr;  // FP64 staging of id-indexed adjoint arrays (id_cap doubles)
   unsigned long long *adj_err = nullptr;
   SpeciesAdjoint adj[kMaxSpecies];
   // output manager
@@ -334,7 +335,8 @@ void free_adjoint(pic_handle *h) {
   cudaFree(h->da0);
   cudaFree(h->objF);
   cudaFree(h->adj_err);
-  h->pend = h->da0 = h->objF = nullptr;
+  cudaFree(h->adj_stage);
+  h->pend = h->da0 = h->objF = h->adj_stage = nullptr;
   h->adj_err = nullptr;
   for (int i = 0; i < kMaxSpecies; ++i) {
     for (int d = 0; d < 3; ++d) {
@@ -1420,7 +1422,8 @@ int pic_adjoint_begin(pic_handle *h, int64_t id_capacity) {
            cudaMalloc(&h->lJ[d], fb) == cudaSuccess;
     ok = ok && cudaMalloc(&h->pend, 8 * sizeof(double) * (size_t)h->g.n[1] * h->g.n[2]) == cudaSuccess &&
          cudaMalloc(&h->da0, sizeof(double)) == cudaSuccess && cudaMalloc(&h->objF, sizeof(double)) == cudaSuccess &&
-         cudaMalloc(&h->adj_err, sizeof(unsigned long long)) == cudaSuccess;
+         cudaMalloc(&h->adj_err, sizeof(unsigned long long)) == cudaSuccess &&
+         cudaMalloc(&h->adj_stage, (size_t)id_capacity * sizeof(double)) == cudaSuccess;
     for (int i = 0; i < h->nsp && ok; ++i) {
       for (int d = 0; d < 3 && ok; ++d)
         ok = cudaMalloc(&h->adj[i].lx[d], ib) == cudaSuccess && cudaMalloc(&h->adj[i].lu[d], ib) == cudaSuccess;
@@ -1520,6 +1523,69 @@ int pic_grad(pic_handle *h, double *d_a0, int species, double *d_w, int mem_kind
   CK(h, cudaMemcpyAsync(&err, h->adj_err, sizeof(err), cudaMemcpyDeviceToHost, h->st), "D2H");
   CK(h, cudaStreamSynchronize(h->st), "sync");
   if (err) return fail(h, PIC_EINVAL, "a particle id is not below the adjoint id capacity");
+  return PIC_OK;
+}
+
+int pic_adjoint_field(pic_handle *h, int which, double *out, int mem_kind) {
+  if (!h || !out) return fail(h, PIC_EINVAL, "NULL argument");
+  if (!h->adj_ready) return fail(h, PIC_EINVAL, "call pic_adjoint_begin first");
+  if (which < PIC_EX || which > PIC_JZ) return fail(h, PIC_EINVAL, "bad field selector (PIC_EX .. PIC_JZ)");
+  if (mem_kind != PIC_MEM_HOST && mem_kind != PIC_MEM_DEVICE) return fail(h, PIC_EINVAL, "bad memory kind");
+  const void *src = which < 3 ? h->lE[which] : which < 6 ? h->lB[which - 3] : h->lJ[which - 6];
+  CK(h, pic::launch_field_to_f64(h->g, src, h->f64, h->st), "convert");
+  int r = copy_out(h, out, h->f64, sizeof(double) * h->g.ncell, mem_kind);
+  if (r) return r;
+  CK(h, cudaStreamSynchronize(h->st), "sync");
+  return PIC_OK;
+}
+
+int pic_adjoint_set_field(pic_handle *h, int which, const double *in, int mem_kind) {
+  if (!h || !in) return fail(h, PIC_EINVAL, "NULL argument");
+  if (!h->adj_ready) return fail(h, PIC_EINVAL, "call pic_adjoint_begin first");
+  if (which < PIC_EX || which > PIC_BZ) return fail(h, PIC_EINVAL, "bad field selector (PIC_EX .. PIC_BZ)");
+  if (mem_kind != PIC_MEM_HOST && mem_kind != PIC_MEM_DEVICE) return fail(h, PIC_EINVAL, "bad memory kind");
+  CK(h,
+     cudaMemcpyAsync(h->f64, in, sizeof(double) * h->g.ncell,
+                     mem_kind == PIC_MEM_HOST ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice, h->st),
+     "copy in");
+  void *dst = which < 3 ? h->lE[which] : h->lB[which - 3];
+  CK(h, pic::launch_field_from_f64(h->g, h->f64, dst, h->st), "convert");
+  CK(h, cudaStreamSynchronize(h->st), "sync");
+  return PIC_OK;
+}
+
+int pic_adjoint_momenta(pic_handle *h, int species, double *lux, double *luy, double *luz, int mem_kind) {
+  if (!h) return fail(h, PIC_EINVAL, "NULL handle");
+  if (!h->adj_ready) return fail(h, PIC_EINVAL, "call pic_adjoint_begin first");
+  if (species < 0 || species >= h->nsp) return fail(h, PIC_EINVAL, "bad species index");
+  if (mem_kind != PIC_MEM_HOST && mem_kind != PIC_MEM_DEVICE) return fail(h, PIC_EINVAL, "bad memory kind");
+  double *outs[3] = {lux, luy, luz};
+  for (int d = 0; d < 3; ++d) {
+    if (!outs[d]) continue;
+    CK(h, pic::launch_to_f64(h->g.prec, h->adj[species].lu[d], h->adj_stage, h->id_cap, h->st), "convert");
+    int r = copy_out(h, outs[d], h->adj_stage, sizeof(double) * (size_t)h->id_cap, mem_kind);
+    if (r) return r;
+  }
+  CK(h, cudaStreamSynchronize(h->st), "sync");
+  return PIC_OK;
+}
+
+int pic_adjoint_set_momenta(pic_handle *h, int species, const double *lux, const double *luy, const double *luz,
+                            int mem_kind) {
+  if (!h) return fail(h, PIC_EINVAL, "NULL handle");
+  if (!h->adj_ready) return fail(h, PIC_EINVAL, "call pic_adjoint_begin first");
+  if (species < 0 || species >= h->nsp) return fail(h, PIC_EINVAL, "bad species index");
+  if (mem_kind != PIC_MEM_HOST && mem_kind != PIC_MEM_DEVICE) return fail(h, PIC_EINVAL, "bad memory kind");
+  const double *ins[3] = {lux, luy, luz};
+  for (int d = 0; d < 3; ++d) {
+    if (!ins[d]) continue;
+    CK(h,
+       cudaMemcpyAsync(h->adj_stage, ins[d], sizeof(double) * (size_t)h->id_cap,
+                       mem_kind == PIC_MEM_HOST ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice, h->st),
+       "copy in");
+    CK(h, pic::launch_from_f64(h->g.prec, h->adj_stage, h->adj[species].lu[d], h->id_cap, h->st), "convert");
+  }
+  CK(h, cudaStreamSynchronize(h->st), "sync");
   return PIC_OK;
 }
 

@@ -765,6 +765,20 @@ cudaError_t launch_field_from_f64(const Grid &g, const double *src, void *dst, c
   return cudaGetLastError();
 }
 
+cudaError_t launch_to_f64(int prec, const void *src, double *dst, int64_t n, cudaStream_t st) {
+  if (n <= 0) return cudaSuccess;
+  if (prec == 1) return cudaMemcpyAsync(dst, src, sizeof(double) * n, cudaMemcpyDeviceToDevice, st);
+  k_convert<float, double><<<grid_blocks(n, 256), 256, 0, st>>>(static_cast<const float *>(src), dst, n);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_from_f64(int prec, const double *src, void *dst, int64_t n, cudaStream_t st) {
+  if (n <= 0) return cudaSuccess;
+  if (prec == 1) return cudaMemcpyAsync(dst, src, sizeof(double) * n, cudaMemcpyDeviceToDevice, st);
+  k_convert<double, float><<<grid_blocks(n, 256), 256, 0, st>>>(src, static_cast<float *>(dst), n);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_rho(const Grid &g, const Particles &p, const int64_t *d_count, int64_t nmax, double q,
                        double *rho, cudaStream_t st) {
   const int nb = grid_blocks(nmax, 256);

@@ -206,6 +206,10 @@ cudaError_t launch_out_particles(const Grid &g, const Particles &p, const int64_
 // of that type.  *nlaunch receives the kernels launched.
 cudaError_t launch_smooth(const Grid &g, void *f, bool f64, void *tmp, int passes, int compensate, cudaStream_t st,
                           int *nlaunch);
+// n values between an array of the run's real type (prec: PIC_FP32 or
+// PIC_FP64) and FP64, on the device.
+cudaError_t launch_to_f64(int prec, const void *src, double *dst, int64_t n, cudaStream_t st);
+cudaError_t launch_from_f64(int prec, const double *src, void *dst, int64_t n, cudaStream_t st);
 cudaError_t launch_field_from_f64(const Grid &g, const double *src, void *dst, cudaStream_t st);
 cudaError_t launch_rho(const Grid &g, const Particles &p, const int64_t *d_count, int64_t nmax, double q,
                        double *rho, cudaStream_t st);

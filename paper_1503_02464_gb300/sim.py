@@ -287,6 +287,29 @@ class Simulation:
     def adjoint_step(self, nsteps: int) -> None:
         capi.pic_adjoint_step(self.h, nsteps)
 
+    def adjoint_field(self, which: int) -> np.ndarray:
+        """The adjoint of field component `which` (EX..BZ, or JX..JZ: of the
+        current of the last reversed step), FP64, shaped like field()."""
+        out = np.empty(self.shape3, dtype=np.float64)
+        capi.pic_adjoint_field(self.h, which, out.ctypes.data, capi.PIC_MEM_HOST)
+        return out
+
+    def adjoint_set_field(self, which: int, values) -> None:
+        """Seed the adjoint of E or B component `which` (dF/dE, dF/dB)."""
+        a = np.ascontiguousarray(np.broadcast_to(values, self.shape3), dtype=np.float64)
+        capi.pic_adjoint_set_field(self.h, which, a.ctypes.data, capi.PIC_MEM_HOST)
+
+    def adjoint_momenta(self, species: int, id_capacity: int) -> np.ndarray:
+        """dF/du of a species by particle id, shape (3, id_capacity)."""
+        out = np.zeros((3, id_capacity), dtype=np.float64)
+        capi.pic_adjoint_momenta(self.h, species, [out[d].ctypes.data for d in range(3)], capi.PIC_MEM_HOST)
+        return out
+
+    def adjoint_set_momenta(self, species: int, lu) -> None:
+        """Seed dF/du of a species by particle id, lu shaped (3, id_capacity)."""
+        a = np.ascontiguousarray(lu, dtype=np.float64)
+        capi.pic_adjoint_set_momenta(self.h, species, [a[d].ctypes.data for d in range(3)], capi.PIC_MEM_HOST)
+
     def grad(self, species: int, id_capacity: int):
         """(dF/da0, dF/dw by particle id) after a reverse sweep."""
         dw = np.zeros(id_capacity, dtype=np.float64)
