@@ -210,14 +210,18 @@ template <class R> struct DAxisD {
     tsc3d<R>(fn - R(h1), w1, d1);
     const int n0 = h0 - 1, n1 = s + h1 - 1;
     rel = n0 < n1 ? n0 : n1;
-    const int o0 = n0 - rel, o1 = n1 - rel;
+    // each support starts at node 0 or 1 of the window: a select between two
+    // compile-time shifts (a run-time array index would put the weights in
+    // local memory)
+    const bool o0 = n0 != rel, o1 = n1 != rel;
 #pragma unroll
     for (int k = 0; k < 4; ++k) {
-      const int q0 = k - o0, q1 = k - o1;
-      S0[k] = (q0 >= 0 && q0 < 3) ? w0[q0 < 3 ? q0 : 0] : R(0);
-      dS0[k] = (q0 >= 0 && q0 < 3) ? d0[q0 < 3 ? q0 : 0] : R(0);
-      S1[k] = (q1 >= 0 && q1 < 3) ? w1[q1 < 3 ? q1 : 0] : R(0);
-      dS1[k] = (q1 >= 0 && q1 < 3) ? d1[q1 < 3 ? q1 : 0] : R(0);
+      const int ka = k < 3 ? k : 2, kb = k > 0 ? k - 1 : 0;
+      const bool ina = k < 3, inb = k > 0;
+      S0[k] = o0 ? (inb ? w0[kb] : R(0)) : (ina ? w0[ka] : R(0));
+      dS0[k] = o0 ? (inb ? d0[kb] : R(0)) : (ina ? d0[ka] : R(0));
+      S1[k] = o1 ? (inb ? w1[kb] : R(0)) : (ina ? w1[ka] : R(0));
+      dS1[k] = o1 ? (inb ? d1[kb] : R(0)) : (ina ? d1[ka] : R(0));
     }
   }
 };
@@ -251,6 +255,28 @@ template <class R> __device__ __forceinline__ R inv_sqrt_fwd(R x);
 template <> __device__ __forceinline__ float inv_sqrt_fwd<float>(float x) { return rsqrtf(x); }
 template <> __device__ __forceinline__ double inv_sqrt_fwd<double>(double x) { return 1.0 / sqrt(x); }
 
+// The forward Boris step (the push's arithmetic) with its intermediates:
+// u- = u0 + h E, t = h B / gamma-, s = 2 t / (1 + t^2), u' = u- + u- x t,
+// u+ = u- + u' x s, uo = u+ + h E.
+template <class R>
+__device__ __forceinline__ void boris_fwd(R h, const R u0[3], const R F[6], R um[3], R t[3], R sv[3], R up[3],
+                                          R uo[3]) {
+#pragma unroll
+  for (int d = 0; d < 3; ++d) um[d] = u0[d] + h * F[d];
+  const R gm = sqrt(R(1) + um[0] * um[0] + um[1] * um[1] + um[2] * um[2]);
+#pragma unroll
+  for (int d = 0; d < 3; ++d) t[d] = h * F[3 + d] / gm;
+  const R den = R(1) + t[0] * t[0] + t[1] * t[1] + t[2] * t[2];
+#pragma unroll
+  for (int d = 0; d < 3; ++d) sv[d] = R(2) * t[d] / den;
+  up[0] = um[0] + (um[1] * t[2] - um[2] * t[1]);
+  up[1] = um[1] + (um[2] * t[0] - um[0] * t[2]);
+  up[2] = um[2] + (um[0] * t[1] - um[1] * t[0]);
+  uo[0] = um[0] + (up[1] * sv[2] - up[2] * sv[1]) + h * F[0];
+  uo[1] = um[1] + (up[2] * sv[0] - up[0] * sv[2]) + h * F[1];
+  uo[2] = um[2] + (up[0] * sv[1] - up[1] * sv[0]) + h * F[2];
+}
+
 // Per-particle adjoint of gather -> Boris -> move -> Esirkepov (2D3V, TSC).
 // The kernel is latency-bound (scattered field and adjoint reads), so the
 // register cap (3 blocks of 256 per SM for FP32, 2 for FP64) trades a few
@@ -271,61 +297,51 @@ __global__ void __launch_bounds__(256, sizeof(R) == 4 ? 3 : 2) k_adj_push2d(cons
     const R f[2] = {a.off[0][p], a.off[1][p]};
     const R u0[3] = {a.u[0][p], a.u[1][p], a.u[2][p]};
     const R wq = a.w[p];
-    // ---- forward recomputation: gather
-    GAxisD<R> gx, gy;
-    gx.set(f[0]);
-    gy.set(f[1]);
-    int ixp[3], ixd[3], iyp[3], iyd[3];
-#pragma unroll
-    for (int k = 0; k < 3; ++k) {
-      ixp[k] = wrapi(i0 + gx.relp + k, n0);
-      ixd[k] = wrapi(i0 + gx.reld + k, n0);
-      iyp[k] = wrapi(j0 + gy.relp + k, n1) * n0;
-      iyd[k] = wrapi(j0 + gy.reld + k, n1) * n0;
-    }
+    // ---- forward recomputation: gather (values only; the weight derivatives
+    // and the field gradients at the particle are recomputed for gather^T at
+    // the end, which keeps them out of the registers of the deposit^T)
     // component c: (dual x?, dual y?) for Ex Ey Ez Bx By Bz
     const bool dx_[6] = {true, false, false, false, true, true};
     const bool dy_[6] = {false, true, false, true, false, true};
-    R F[6], dFx[6], dFy[6];
+    R F[6];
+    {
+      GatherAxis<R, 2> gx, gy;
+      gx.set(f[0]);
+      gy.set(f[1]);
+      int ixp[3], ixd[3], iyp[3], iyd[3];
 #pragma unroll
-    for (int cc = 0; cc < 6; ++cc) {
-      const R *G = cc < 3 ? a.E[cc] : a.B[cc - 3];
-      const int *ix = dx_[cc] ? ixd : ixp;
-      const int *iy = dy_[cc] ? iyd : iyp;
-      const R *wx = dx_[cc] ? gx.wd : gx.wp, *dwx = dx_[cc] ? gx.dwd : gx.dwp;
-      const R *wy = dy_[cc] ? gy.wd : gy.wp, *dwy = dy_[cc] ? gy.dwd : gy.dwp;
-      R s = 0, sx = 0, sy = 0;
+      for (int k = 0; k < 3; ++k) {
+        ixp[k] = wrapi(i0 + gx.relp + k, n0);
+        ixd[k] = wrapi(i0 + gx.reld + k, n0);
+        iyp[k] = wrapi(j0 + gy.relp + k, n1) * n0;
+        iyd[k] = wrapi(j0 + gy.reld + k, n1) * n0;
+      }
 #pragma unroll
-      for (int b = 0; b < 3; ++b)
+      for (int cc = 0; cc < 6; ++cc) {
+        const R *G = cc < 3 ? a.E[cc] : a.B[cc - 3];
+        const int *ix = dx_[cc] ? ixd : ixp;
+        const int *iy = dy_[cc] ? iyd : iyp;
+        const R *wx = dx_[cc] ? gx.wd : gx.wp;
+        const R *wy = dy_[cc] ? gy.wd : gy.wp;
+        R s = 0;
 #pragma unroll
-        for (int aa = 0; aa < 3; ++aa) {
-          const R v = G[ix[aa] + iy[b]];
-          s += v * wx[aa] * wy[b];
-          sx += v * dwx[aa] * wy[b];
-          sy += v * wx[aa] * dwy[b];
+        for (int b = 0; b < 3; ++b) {
+          R r = 0;
+#pragma unroll
+          for (int aa = 0; aa < 3; ++aa) r += G[ix[aa] + iy[b]] * wx[aa];
+          s += r * wy[b];
         }
-      F[cc] = s;
-      dFx[cc] = sx;
-      dFy[cc] = sy;
+        F[cc] = s;
+      }
     }
-    // Boris (forward values kept for the transpose)
+    // Boris.  Its intermediate values are recomputed from u0 and F for the
+    // transpose further down, rather than kept live through deposit^T.
     const R h = a.qmh;
-    R um[3], t[3], sv[3], up[3], uo[3];
-#pragma unroll
-    for (int d = 0; d < 3; ++d) um[d] = u0[d] + h * F[d];
-    const R gm = sqrt(R(1) + um[0] * um[0] + um[1] * um[1] + um[2] * um[2]);
-#pragma unroll
-    for (int d = 0; d < 3; ++d) t[d] = h * F[3 + d] / gm;
-    const R t2 = t[0] * t[0] + t[1] * t[1] + t[2] * t[2];
-    const R den = R(1) + t2;
-#pragma unroll
-    for (int d = 0; d < 3; ++d) sv[d] = R(2) * t[d] / den;
-    up[0] = um[0] + (um[1] * t[2] - um[2] * t[1]);
-    up[1] = um[1] + (um[2] * t[0] - um[0] * t[2]);
-    up[2] = um[2] + (um[0] * t[1] - um[1] * t[0]);
-    uo[0] = um[0] + (up[1] * sv[2] - up[2] * sv[1]) + h * F[0];
-    uo[1] = um[1] + (up[2] * sv[0] - up[0] * sv[2]) + h * F[1];
-    uo[2] = um[2] + (up[0] * sv[1] - up[1] * sv[0]) + h * F[2];
+    R uo[3];
+    {
+      R um[3], t[3], sv[3], up[3];
+      boris_fwd<R>(h, u0, F, um, t, sv, up, uo);
+    }
     // move
     const R ig = inv_sqrt_fwd<R>(R(1) + uo[0] * uo[0] + uo[1] * uo[1] + uo[2] * uo[2]);
     R fn[2];
@@ -427,12 +443,18 @@ __global__ void __launch_bounds__(256, sizeof(R) == 4 ? 3 : 2) k_adj_push2d(cons
     }
     const R lvz = qw * Tz;  // dL/dvz
     R lf_old[2] = {0, 0}, lf_new[2] = {0, 0};
+    {
+      // shape derivatives, set up only now (X, Y are used for their values)
+      DAxisD<R> Xd, Yd;
+      Xd.set(f[0], sh[0], fn[0]);
+      Yd.set(f[1], sh[1], fn[1]);
 #pragma unroll
-    for (int k = 0; k < 4; ++k) {
-      lf_old[0] += dS0x[k] * X.dS0[k];
-      lf_new[0] += dS1x[k] * X.dS1[k];
-      lf_old[1] += dS0y[k] * Y.dS0[k];
-      lf_new[1] += dS1y[k] * Y.dS1[k];
+      for (int k = 0; k < 4; ++k) {
+        lf_old[0] += dS0x[k] * Xd.dS0[k];
+        lf_new[0] += dS1x[k] * Xd.dS1[k];
+        lf_old[1] += dS0y[k] * Yd.dS0[k];
+        lf_new[1] += dS1y[k] * Yd.dS1[k];
+      }
     }
 
     // ---- move^T: x' = x + D(u+), vz = u+_z / gamma
@@ -451,7 +473,14 @@ __global__ void __launch_bounds__(256, sizeof(R) == 4 ? 3 : 2) k_adj_push2d(cons
       for (int d = 0; d < 3; ++d) lu[d] = a.lu[d][pid] + (lD[d] - uo[d] * ud) * ig;
     }
 
-    // ---- Boris^T
+    // ---- Boris^T (the forward intermediates recomputed)
+    R um[3], t[3], sv[3], up[3];
+    {
+      R uo_[3];
+      boris_fwd<R>(h, u0, F, um, t, sv, up, uo_);
+    }
+    const R gm = sqrt(R(1) + um[0] * um[0] + um[1] * um[1] + um[2] * um[2]);
+    const R den = R(1) + t[0] * t[0] + t[1] * t[1] + t[2] * t[2];
     R lF[6];
 #pragma unroll
     for (int d = 0; d < 3; ++d) lF[d] = h * lu[d];  // u_out = u+' + h E
@@ -500,20 +529,42 @@ __global__ void __launch_bounds__(256, sizeof(R) == 4 ? 3 : 2) k_adj_push2d(cons
     }
 
     // ---- gather^T: scatter lamF into lamE, lamB; position derivative
+    // (weights, their derivatives and the field values recomputed here)
+    {
+      GAxisD<R> gx, gy;
+      gx.set(f[0]);
+      gy.set(f[1]);
+      int ixp[3], ixd[3], iyp[3], iyd[3];
 #pragma unroll
-    for (int cc = 0; cc < 6; ++cc) {
-      lX[0] += lF[cc] * dFx[cc];
-      lX[1] += lF[cc] * dFy[cc];
-      if (lF[cc] == R(0)) continue;
-      R *G = cc < 3 ? a.lE[cc] : a.lB[cc - 3];
-      const int *ix = dx_[cc] ? ixd : ixp;
-      const int *iy = dy_[cc] ? iyd : iyp;
-      const R *wx = dx_[cc] ? gx.wd : gx.wp;
-      const R *wy = dy_[cc] ? gy.wd : gy.wp;
+      for (int k = 0; k < 3; ++k) {
+        ixp[k] = wrapi(i0 + gx.relp + k, n0);
+        ixd[k] = wrapi(i0 + gx.reld + k, n0);
+        iyp[k] = wrapi(j0 + gy.relp + k, n1) * n0;
+        iyd[k] = wrapi(j0 + gy.reld + k, n1) * n0;
+      }
 #pragma unroll
-      for (int b = 0; b < 3; ++b)
+      for (int cc = 0; cc < 6; ++cc) {
+        if (lF[cc] == R(0)) continue;
+        const R *G = cc < 3 ? a.E[cc] : a.B[cc - 3];
+        R *LG = cc < 3 ? a.lE[cc] : a.lB[cc - 3];
+        const int *ix = dx_[cc] ? ixd : ixp;
+        const int *iy = dy_[cc] ? iyd : iyp;
+        const R *wx = dx_[cc] ? gx.wd : gx.wp, *dwx = dx_[cc] ? gx.dwd : gx.dwp;
+        const R *wy = dy_[cc] ? gy.wd : gy.wp, *dwy = dy_[cc] ? gy.dwd : gy.dwp;
+        R sx = 0, sy = 0;
 #pragma unroll
-        for (int aa = 0; aa < 3; ++aa) atomicAdd(G + ix[aa] + iy[b], lF[cc] * wx[aa] * wy[b]);
+        for (int b = 0; b < 3; ++b)
+#pragma unroll
+          for (int aa = 0; aa < 3; ++aa) {
+            const int node = ix[aa] + iy[b];
+            const R v = G[node];
+            sx += v * dwx[aa] * wy[b];
+            sy += v * wx[aa] * dwy[b];
+            atomicAdd(LG + node, lF[cc] * wx[aa] * wy[b]);
+          }
+        lX[0] += lF[cc] * sx;
+        lX[1] += lF[cc] * sy;
+      }
     }
 
     // ---- new adjoint state (time n), weight gradient
