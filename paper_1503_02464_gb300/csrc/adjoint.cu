@@ -45,10 +45,14 @@ struct GridIdx {
 // lamE -= h * curl_at_E(M_B lamB): the transpose of "B -= h curl_at_B(E)"
 // over the rows the forward updated (By, Bz of the last x cell are not
 // updated when the x walls absorb).
+//
+// With `pend` (the second B half, R1), the Mur transpose's terms for the
+// old time level (R4, kept in `pend` by k_adj_mur) are added to lamEy,
+// lamEz at the wall nodes in the same pass: both updates only add to lamE.
 template <class R, int DIM>
 __global__ void __launch_bounds__(256)
     k_adj_yee_b(GridIdx g, int absorb, R rdx, R rdy, R rdz, R h, R *lE0, R *lE1, R *lE2, const R *lB0, const R *lB1,
-                const R *lB2) {
+                const R *lB2, const double *pend) {
   const int64_t ncell = (int64_t)g.n0 * g.n1 * g.n2;
   const int64_t sy = g.n0, sz = (int64_t)g.n0 * g.n1;
   for (int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; c < ncell; c += (int64_t)gridDim.x * blockDim.x) {
@@ -71,9 +75,21 @@ __global__ void __launch_bounds__(256)
       cx -= (by - byzm) * rdz;
       cy += (bx - lB0[czm]) * rdz;
     }
+    R py = R(0), pz = R(0);
+    if (pend && (i < 2 || i >= g.n0 - 2)) {
+      // pend slots: nodes 0, 1, n0-2, n0-1 (for Ey, then for Ez), per row
+      const int64_t nyz = (int64_t)g.n1 * g.n2, jk = c / g.n0;
+      const int nodes[4] = {0, 1, g.n0 - 2, g.n0 - 1};
+#pragma unroll
+      for (int q = 0; q < 4; ++q)
+        if (nodes[q] == i) {
+          py += (R)pend[q * nyz + jk];
+          pz += (R)pend[(4 + q) * nyz + jk];
+        }
+    }
     lE0[c] -= h * cx;
-    lE1[c] -= h * cy;
-    lE2[c] -= h * cz;
+    lE1[c] += py - h * cy;
+    lE2[c] += pz - h * cz;
   }
 }
 
@@ -123,7 +139,8 @@ __global__ void __launch_bounds__(256)
 //   Ez' = E(n0-2)o + k (E(n0-2)n - E(n0-1)o)      (right wall)
 // g = lamE(wall) is consumed (the wall value was overwritten), k g goes to
 // the neighbour at the new time, and g, -k g are kept in `pend` for the old
-// time (added after R3).  dF/da0 += g dE0'/da0 (the laser terms over a0).
+// time (added to lamE by the R1 pass of k_adj_yee_b).  dF/da0 += g dE0'/da0
+// (the laser terms over a0).
 template <class R>
 __global__ void k_adj_mur(int n0, int n1, int n2, double dx, double dt, R *lEy, R *lEz, double *pend, LaserStep ls,
                           double *da0) {
@@ -156,21 +173,6 @@ __global__ void k_adj_mur(int n0, int n1, int n2, double dx, double dt, R *lEy, 
   }
   const double v = block_sum(acc, sh);
   if (threadIdx.x == 0 && v != 0.0) atomicAdd(da0, v);
-}
-
-template <class R>
-__global__ void k_adj_mur_pend(int n0, int n1, int n2, R *lEy, R *lEz, const double *pend) {
-  const int64_t nyz = (int64_t)n1 * n2;
-  const int nodes[4] = {0, 1, n0 - 2, n0 - 1};
-  for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < 2 * nyz; q += (int64_t)gridDim.x * blockDim.x) {
-    const int c = (int)(q / nyz);
-    const int64_t jk = q % nyz;
-    R *E = c == 0 ? lEy : lEz;
-    const double *pd = pend + (int64_t)c * 4 * nyz;
-    const int64_t row = (int64_t)n0 * jk;
-#pragma unroll
-    for (int s = 0; s < 4; ++s) E[row + nodes[s]] += (R)pd[s * nyz + jk];
-  }
 }
 
 // ---------------------------------------------------------------- particles
@@ -612,7 +614,8 @@ template <class R> GridIdx gidx(const Grid &g) { return GridIdx{g.n[0], g.n[1], 
 
 }  // namespace
 
-cudaError_t launch_adj_yee_b(const Grid &g, void *const lE[3], void *const lB[3], double h, cudaStream_t st) {
+cudaError_t launch_adj_yee_b(const Grid &g, void *const lE[3], void *const lB[3], double h, const double *pend,
+                             cudaStream_t st) {
   const int nb = nblocks(g.ncell);
   const int absorb = g.absorb_lo || g.absorb_hi;
   if (g.prec == 1) {
@@ -620,19 +623,19 @@ cudaError_t launch_adj_yee_b(const Grid &g, void *const lE[3], void *const lB[3]
     auto B = [&](int c) { return static_cast<const double *>(lB[c]); };
     if (g.dims == 3)
       k_adj_yee_b<double, 3><<<nb, 256, 0, st>>>(gidx<double>(g), absorb, 1.0 / g.dx[0], 1.0 / g.dx[1], 1.0 / g.dx[2],
-                                                 h, E(0), E(1), E(2), B(0), B(1), B(2));
+                                                 h, E(0), E(1), E(2), B(0), B(1), B(2), pend);
     else
       k_adj_yee_b<double, 2><<<nb, 256, 0, st>>>(gidx<double>(g), absorb, 1.0 / g.dx[0], 1.0 / g.dx[1], 1.0 / g.dx[2],
-                                                 h, E(0), E(1), E(2), B(0), B(1), B(2));
+                                                 h, E(0), E(1), E(2), B(0), B(1), B(2), pend);
   } else {
     auto E = [&](int c) { return static_cast<float *>(lE[c]); };
     auto B = [&](int c) { return static_cast<const float *>(lB[c]); };
     if (g.dims == 3)
       k_adj_yee_b<float, 3><<<nb, 256, 0, st>>>(gidx<float>(g), absorb, (float)(1.0 / g.dx[0]), (float)(1.0 / g.dx[1]),
-                                                (float)(1.0 / g.dx[2]), (float)h, E(0), E(1), E(2), B(0), B(1), B(2));
+                                                (float)(1.0 / g.dx[2]), (float)h, E(0), E(1), E(2), B(0), B(1), B(2), pend);
     else
       k_adj_yee_b<float, 2><<<nb, 256, 0, st>>>(gidx<float>(g), absorb, (float)(1.0 / g.dx[0]), (float)(1.0 / g.dx[1]),
-                                                (float)(1.0 / g.dx[2]), (float)h, E(0), E(1), E(2), B(0), B(1), B(2));
+                                                (float)(1.0 / g.dx[2]), (float)h, E(0), E(1), E(2), B(0), B(1), B(2), pend);
   }
   return cudaGetLastError();
 }
@@ -675,17 +678,6 @@ cudaError_t launch_adj_mur(const Grid &g, void *const lE[3], double *pend, const
   else
     k_adj_mur<float><<<nb, 256, 0, st>>>(g.n[0], g.n[1], g.n[2], g.dx[0], g.dt, static_cast<float *>(lE[1]),
                                          static_cast<float *>(lE[2]), pend, ls_unit, da0);
-  return cudaGetLastError();
-}
-
-cudaError_t launch_adj_mur_pend(const Grid &g, void *const lE[3], const double *pend, cudaStream_t st) {
-  const int nb = nblocks(2LL * g.n[1] * g.n[2]);
-  if (g.prec == 1)
-    k_adj_mur_pend<double><<<nb, 256, 0, st>>>(g.n[0], g.n[1], g.n[2], static_cast<double *>(lE[1]),
-                                               static_cast<double *>(lE[2]), pend);
-  else
-    k_adj_mur_pend<float><<<nb, 256, 0, st>>>(g.n[0], g.n[1], g.n[2], static_cast<float *>(lE[1]),
-                                              static_cast<float *>(lE[2]), pend);
   return cudaGetLastError();
 }
 

@@ -1488,17 +1488,18 @@ int pic_adjoint_step(pic_handle *h, int nsteps) {
     const double t_old = en.step * h->g.dt, t_new = (en.step + 1) * h->g.dt;
     {
       Timed tm(h, pic::KC_ADJ_FIELD);
-      CK(h, pic::launch_adj_yee_b(h->g, h->lE, h->lB, 0.5 * h->g.dt, h->st), "adjoint B half");
+      CK(h, pic::launch_adj_yee_b(h->g, h->lE, h->lB, 0.5 * h->g.dt, nullptr, h->st), "adjoint B half");
       if (walls)
         CK(h,
            pic::launch_adj_mur(h->g, h->lE, h->pend,
                                pic::laser_step(h->laser, h->laser_prof, 1.0, h->g, t_old, t_new), h->da0, h->st),
            "adjoint Mur");
       CK(h, pic::launch_adj_yee_e(h->g, h->lE, h->lB, h->lJ, h->g.dt, h->st), "adjoint E");
-      if (walls) CK(h, pic::launch_adj_mur_pend(h->g, h->lE, h->pend, h->st), "adjoint Mur");
-      CK(h, pic::launch_adj_yee_b(h->g, h->lE, h->lB, 0.5 * h->g.dt, h->st), "adjoint B half");
+      // the second B half also adds the Mur transpose's old-time terms
+      CK(h, pic::launch_adj_yee_b(h->g, h->lE, h->lB, 0.5 * h->g.dt, walls ? h->pend : nullptr, h->st),
+         "adjoint B half");
     }
-    h->launches += walls ? 5 : 3;
+    h->launches += walls ? 4 : 3;
     for (int i = 0; i < h->nsp; ++i) {
       Species &s = h->sp[i];
       Timed tm(h, pic::KC_ADJ_PUSH);

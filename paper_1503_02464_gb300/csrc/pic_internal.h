@@ -224,12 +224,14 @@ cudaError_t launch_particle_diag(const Grid &g, const Particles &p, const int64_
                                  double *out, cudaStream_t st);
 
 // ---- adjoint (adjoint.cu) ----
-cudaError_t launch_adj_yee_b(const Grid &g, void *const lE[3], void *const lB[3], double h, cudaStream_t st);
+// pend (may be null): the Mur transpose's old-time terms, added to lamE at the
+// wall nodes in the same pass (the second B half of the reversed step).
+cudaError_t launch_adj_yee_b(const Grid &g, void *const lE[3], void *const lB[3], double h, const double *pend,
+                             cudaStream_t st);
 cudaError_t launch_adj_yee_e(const Grid &g, void *const lE[3], void *const lB[3], void *const lJ[3], double h,
                              cudaStream_t st);
 cudaError_t launch_adj_mur(const Grid &g, void *const lE[3], double *pend, const LaserStep &ls_unit, double *da0,
                            cudaStream_t st);
-cudaError_t launch_adj_mur_pend(const Grid &g, void *const lE[3], const double *pend, cudaStream_t st);
 // Per-particle adjoint of one recorded step (2D3V TSC only): tp/d_count
 // is the particle state at the start of the step, E/B the fields gathered.
 cudaError_t launch_adj_push(const Grid &g, const Particles &tp, const int64_t *d_count, int64_t nmax,
