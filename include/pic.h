@@ -305,6 +305,14 @@ int pic_restore(pic_handle *h, int slot);
  * step loop (after its sort), for pic_adjoint_step.  nsteps = 0 stops. */
 int pic_tape_begin(pic_handle *h, int nsteps);
 
+/* Record the current state as the next tape entry without taking the step
+ * (a reverse sweep needs a step's start state, not its result: the last
+ * step of a recomputed segment need not run).  The entry holds the state as
+ * it is now, before any sort the next step would make; the adjoint kernels
+ * index particles by id, so the slot order does not matter.  PIC_EINVAL
+ * when no tape entry is left (pic_tape_begin). */
+int pic_tape_record(pic_handle *h);
+
 /* Allocate (first call) and zero the adjoint state: field adjoints, and per
  * species particle adjoints indexed by particle id (ids must be below
  * id_capacity), the FP64 weight gradients and dF/da0.  PIC_EINVAL unless

@@ -30,7 +30,8 @@ EXPORTED = ["pic_create", "pic_destroy", "pic_last_error", "pic_add_species", "p
             "pic_restore", "pic_tape_begin", "pic_adjoint_begin", "pic_adjoint_seed_kinetic", "pic_adjoint_step",
             "pic_grad", "pic_state_size", "pic_state_save", "pic_state_load", "pic_output_due", "pic_output_add", "pic_output_capture", "pic_output_count",
             "pic_output_read", "pic_output_remove", "pic_field_energy_noalloc", "pic_alu_peak",
-            "pic_adjoint_field", "pic_adjoint_set_field", "pic_adjoint_momenta", "pic_adjoint_set_momenta"]
+            "pic_adjoint_field", "pic_adjoint_set_field", "pic_adjoint_momenta", "pic_adjoint_set_momenta",
+            "pic_tape_record"]
 
 
 class pic_laser(ctypes.Structure):
@@ -130,6 +131,7 @@ def load(build_if_missing: bool = True) -> ctypes.CDLL:
         "pic_checkpoint": ([hp, ctypes.c_int], ctypes.c_int),
         "pic_restore": ([hp, ctypes.c_int], ctypes.c_int),
         "pic_tape_begin": ([hp, ctypes.c_int], ctypes.c_int),
+        "pic_tape_record": ([hp], ctypes.c_int),
         "pic_adjoint_begin": ([hp, i64], ctypes.c_int),
         "pic_adjoint_seed_kinetic": ([hp, ctypes.c_int, ctypes.c_int, ctypes.c_int, dp], ctypes.c_int),
         "pic_adjoint_step": ([hp, ctypes.c_int], ctypes.c_int),
@@ -378,3 +380,7 @@ def pic_adjoint_momenta(h, species: int, ptrs, mem_kind: int) -> None:
 
 def pic_adjoint_set_momenta(h, species: int, ptrs, mem_kind: int) -> None:
     check(h, load().pic_adjoint_set_momenta(h, int(species), *ptrs, int(mem_kind)))
+
+
+def pic_tape_record(h) -> None:
+    check(h, load().pic_tape_record(h))

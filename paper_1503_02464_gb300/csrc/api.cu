@@ -1403,6 +1403,16 @@ int pic_tape_begin(pic_handle *h, int nsteps) {
   return PIC_OK;
 }
 
+int pic_tape_record(pic_handle *h) {
+  if (!h) return fail(h, PIC_EINVAL, "NULL handle");
+  if (!h->taping || h->tape_len >= (int)h->tape.size())
+    return fail(h, PIC_EINVAL, "no tape entry left to record (pic_tape_begin)");
+  CK(h, save_snapshot(h, h->tape[h->tape_len]), "tape record");
+  h->tape_len++;
+  if (h->tape_len >= (int)h->tape.size()) h->taping = false;
+  return PIC_OK;
+}
+
 int pic_adjoint_begin(pic_handle *h, int64_t id_capacity) {
   if (!h) return fail(h, PIC_EINVAL, "NULL handle");
   if (h->g.dims != 2 || h->g.order != 2)

@@ -119,9 +119,14 @@ def backward_gradients(run: SlabRun, sim: Simulation):
     for k in reversed(range(nseg)):
         sim.restore(k)
         sim.tape_begin(run.segment)
-        sim.step(run.segment)
         if k == nseg - 1:
+            # the objective needs the final state: the last segment runs in full
+            sim.step(run.segment)
             sim.adjoint_seed_kinetic(0, run.obj[0], run.obj[1])
+        else:
+            # only the start state of the segment's last step is needed
+            sim.step(run.segment - 1)
+            sim.tape_record()
         sim.adjoint_step(run.segment)
     da0, dw = sim.grad(0, run.id_capacity)
     ids = np.arange(run.id_capacity)

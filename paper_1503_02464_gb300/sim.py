@@ -278,6 +278,10 @@ class Simulation:
     def tape_begin(self, nsteps: int) -> None:
         capi.pic_tape_begin(self.h, nsteps)
 
+    def tape_record(self) -> None:
+        """Record the current state as the next tape entry without stepping."""
+        capi.pic_tape_record(self.h)
+
     def adjoint_begin(self, id_capacity: int) -> None:
         capi.pic_adjoint_begin(self.h, id_capacity)
 
