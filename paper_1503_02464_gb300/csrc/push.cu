@@ -349,7 +349,7 @@ __device__ __forceinline__ void unpack_job(int j, int l[3], int s[3]) {
   }
 }
 
-// ---- settled deposit (FP32) -------------------------------------------
+// ---- settled deposit ----------------------------------------------------
 // Most particles keep their shape support over a step: for TSC the nearest
 // node does not change, for CIC the cell does not.  For them the Esirkepov
 // stencil shrinks from ORDER + 2 to ORDER + 1 nodes per axis (3D TSC: 54
@@ -361,29 +361,29 @@ __device__ __forceinline__ void unpack_job(int j, int l[3], int s[3]) {
 // difference of the two shapes would lose it.  The factored values equal
 // S1 - S0 in exact arithmetic, so the current still satisfies the discrete
 // continuity equation with rho = sum q w S (to FP32 round-off of S).
-template <int ORDER> struct SettledAxis {
+template <class R, int ORDER> struct SettledAxis {
   static constexpr int NS = ORDER + 1;
   int rel;    // first support node relative to the old cell
-  float S0[NS], DS[NS];
-  float dl;   // displacement in cells
+  R S0[NS], DS[NS];
+  R dl;       // displacement in cells
   // false when the support changes (then nothing is set)
-  __device__ __forceinline__ bool set(float f0, int s, float f1) {
+  __device__ __forceinline__ bool set(R f0, int s, R f1) {
     if (ORDER == 2) {
-      const int h0 = f0 >= 0.5f, h1 = f1 >= 0.5f;
+      const int h0 = f0 >= R(0.5), h1 = f1 >= R(0.5);
       if (s + h1 != h0) return false;
       rel = h0 - 1;
-      const float d0 = f0 - (float)h0, d1 = f1 - (float)h1;  // both from the same node
+      const R d0 = f0 - R(h0), d1 = f1 - R(h1);  // both from the same node
       dl = d1 - d0;
-      const float sg = d0 + d1;
-      tsc3<float>(d0, S0);
-      const float hd = 0.5f * dl;
-      DS[0] = hd * (sg - 1.0f);
+      const R sg = d0 + d1;
+      tsc3<R>(d0, S0);
+      const R hd = R(0.5) * dl;
+      DS[0] = hd * (sg - R(1));
       DS[1] = -dl * sg;
-      DS[2] = hd * (sg + 1.0f);
+      DS[2] = hd * (sg + R(1));
     } else {
       if (s != 0) return false;
       rel = 0;
-      S0[0] = 1.0f - f0;
+      S0[0] = R(1) - f0;
       S0[1] = f0;
       dl = f1 - f0;
       DS[0] = -dl;
@@ -393,10 +393,10 @@ template <int ORDER> struct SettledAxis {
   }
   __device__ __forceinline__ void zero() {
     rel = 0;
-    dl = 0.0f;
+    dl = R(0);
 #pragma unroll
-    for (int k = 0; k < NS; ++k) S0[k] = DS[k] = 0.0f;
-    S0[0] = 1.0f;
+    for (int k = 0; k < NS; ++k) S0[k] = DS[k] = R(0);
+    S0[0] = R(1);
   }
 };
 
@@ -414,21 +414,38 @@ template <int JS> __device__ __forceinline__ void fx_add(unsigned sa, float p, f
                "r"(sa + 4u * (unsigned)JS), "r"(hi));
 }
 
+// One contribution p q to component comp at node offset off (compile-time)
+// from the stencil's first node.  FP32: fixed point at the byte address
+// base + ...; FP64: a double shared atomic at the node (zero skipped), as in
+// WinAcc<double>.
+template <class R, int JS> struct SettledSink;
+template <int JS> struct SettledSink<float, JS> {
+  unsigned sb;  // byte address of the Jx low word of the stencil's first node
+  __device__ __forceinline__ void add(int comp, int off, float p, float q) const {
+    fx_add<JS>(sb + 8u * (unsigned)JS * (unsigned)comp + 4u * (unsigned)off, p, q);
+  }
+};
+template <int JS> struct SettledSink<double, JS> {
+  double *w;  // Jx value of the stencil's first node (components JS doubles apart)
+  __device__ __forceinline__ void add(int comp, int off, double p, double q) const {
+    const double x = p * q;
+    if (x != 0.0) atomicAdd(w + comp * JS + off, x);
+  }
+};
+
 // Esirkepov deposit of a settled particle on its ORDER + 1 support nodes per
-// axis (compile-time strides SY, SZ in nodes; sb = byte address of the Jx low
-// word of the stencil's first node).  Same brackets as deposit_win: Jx gets
-// Px (S0y S0z + DSy S0z/2 + S0y DSz/2 + DSy DSz/3), cyclic; in 2D3V
+// axis (compile-time strides SY, SZ in nodes).  Same brackets as deposit_win:
+// Jx gets Px (S0y S0z + DSy S0z/2 + S0y DSz/2 + DSy DSz/3), cyclic; in 2D3V
 // Jz = q w vz (S0x S0y + DSx S0y/2 + S0x DSy/2 + DSx DSy/3).  The running
 // sums of DS along an axis end at -DS[last] (the whole sum vanishes).
-template <int ORDER, int DIM, int SY, int SZ, int JS>
-__device__ __forceinline__ void deposit_settled_win(unsigned sb, const SettledAxis<ORDER> &X,
-                                                    const SettledAxis<ORDER> &Y, const SettledAxis<ORDER> &Z,
-                                                    float cx, float cy, float cz, float qwvz) {
+template <class R, int ORDER, int DIM, int SY, int SZ, int JS>
+__device__ __forceinline__ void deposit_settled_win(const SettledSink<R, JS> &out, const SettledAxis<R, ORDER> &X,
+                                                    const SettledAxis<R, ORDER> &Y, const SettledAxis<R, ORDER> &Z,
+                                                    R cx, R cy, R cz, R qwvz) {
   constexpr int NS = ORDER + 1, M = ORDER;
-  constexpr unsigned CY = 8u * JS, CZ = 16u * JS;  // byte offsets of the Jy, Jz low words
-  float Px[M], Py[M], Pz[M];
+  R Px[M], Py[M], Pz[M];
   {
-    float ra = 0.0f, rb = 0.0f, rc = 0.0f;
+    R ra = R(0), rb = R(0), rc = R(0);
 #pragma unroll
     for (int k = 0; k < M - 1; ++k) {
       ra += X.DS[k];
@@ -443,78 +460,76 @@ __device__ __forceinline__ void deposit_settled_win(unsigned sb, const SettledAx
     Pz[M - 1] = -cz * Z.DS[NS - 1];
   }
   if (DIM == 3) {
-    float hz[NS], tz[NS], hx[NS], tx[NS];
+    R hz[NS], tz[NS], hx[NS], tx[NS];
 #pragma unroll
     for (int k = 0; k < NS; ++k) {
-      hz[k] = Z.S0[k] + 0.5f * Z.DS[k];
-      tz[k] = 0.5f * Z.S0[k] + Z.DS[k] * (1.0f / 3.0f);
-      hx[k] = X.S0[k] + 0.5f * X.DS[k];
-      tx[k] = 0.5f * X.S0[k] + X.DS[k] * (1.0f / 3.0f);
+      hz[k] = Z.S0[k] + R(0.5) * Z.DS[k];
+      tz[k] = R(0.5) * Z.S0[k] + Z.DS[k] * R(1.0 / 3.0);
+      hx[k] = X.S0[k] + R(0.5) * X.DS[k];
+      tx[k] = R(0.5) * X.S0[k] + X.DS[k] * R(1.0 / 3.0);
     }
 #pragma unroll
     for (int c = 0; c < NS; ++c)
 #pragma unroll
       for (int b = 0; b < NS; ++b) {
-        const float br = Y.S0[b] * hz[c] + Y.DS[b] * tz[c];
+        const R br = Y.S0[b] * hz[c] + Y.DS[b] * tz[c];
 #pragma unroll
-        for (int a = 0; a < M; ++a) fx_add<JS>(sb + 4u * (unsigned)(c * SZ + b * SY + a), Px[a], br);
+        for (int a = 0; a < M; ++a) out.add(0, c * SZ + b * SY + a, Px[a], br);
       }
 #pragma unroll
     for (int c = 0; c < NS; ++c)
 #pragma unroll
       for (int a = 0; a < NS; ++a) {
-        const float br = Z.S0[c] * hx[a] + Z.DS[c] * tx[a];
+        const R br = Z.S0[c] * hx[a] + Z.DS[c] * tx[a];
 #pragma unroll
-        for (int b = 0; b < M; ++b) fx_add<JS>(sb + CY + 4u * (unsigned)(c * SZ + b * SY + a), Py[b], br);
+        for (int b = 0; b < M; ++b) out.add(1, c * SZ + b * SY + a, Py[b], br);
       }
 #pragma unroll
     for (int b = 0; b < NS; ++b) {
-      const float hy = Y.S0[b] + 0.5f * Y.DS[b];
-      const float ty = 0.5f * Y.S0[b] + Y.DS[b] * (1.0f / 3.0f);
+      const R hy = Y.S0[b] + R(0.5) * Y.DS[b];
+      const R ty = R(0.5) * Y.S0[b] + Y.DS[b] * R(1.0 / 3.0);
 #pragma unroll
       for (int a = 0; a < NS; ++a) {
-        const float br = X.S0[a] * hy + X.DS[a] * ty;
+        const R br = X.S0[a] * hy + X.DS[a] * ty;
 #pragma unroll
-        for (int c = 0; c < M; ++c) fx_add<JS>(sb + CZ + 4u * (unsigned)(c * SZ + b * SY + a), Pz[c], br);
+        for (int c = 0; c < M; ++c) out.add(2, c * SZ + b * SY + a, Pz[c], br);
       }
     }
   } else {
 #pragma unroll
     for (int b = 0; b < NS; ++b) {
-      const float hy = Y.S0[b] + 0.5f * Y.DS[b];
-      const float ty = 0.5f * Y.S0[b] + Y.DS[b] * (1.0f / 3.0f);
+      const R hy = Y.S0[b] + R(0.5) * Y.DS[b];
+      const R ty = R(0.5) * Y.S0[b] + Y.DS[b] * R(1.0 / 3.0);
 #pragma unroll
-      for (int a = 0; a < M; ++a) fx_add<JS>(sb + 4u * (unsigned)(b * SY + a), Px[a], hy);
+      for (int a = 0; a < M; ++a) out.add(0, b * SY + a, Px[a], hy);
 #pragma unroll
-      for (int a = 0; a < NS; ++a)
-        fx_add<JS>(sb + CZ + 4u * (unsigned)(b * SY + a), qwvz, X.S0[a] * hy + X.DS[a] * ty);
+      for (int a = 0; a < NS; ++a) out.add(2, b * SY + a, qwvz, X.S0[a] * hy + X.DS[a] * ty);
     }
 #pragma unroll
     for (int a = 0; a < NS; ++a) {
-      const float hx = X.S0[a] + 0.5f * X.DS[a];
+      const R hx = X.S0[a] + R(0.5) * X.DS[a];
 #pragma unroll
-      for (int b = 0; b < M; ++b) fx_add<JS>(sb + CY + 4u * (unsigned)(b * SY + a), Py[b], hx);
+      for (int b = 0; b < M; ++b) out.add(1, b * SY + a, Py[b], hx);
     }
   }
 }
 
-// Deposit of a particle whose support did not change (FP32 runs).  Returns
-// false, depositing nothing, when the support changes on some axis: such a
-// particle takes the general ORDER + 2 node stencil (deposit_particle),
-// through the block's queue of deferred jobs.
-template <int DIM, int ORDER>
-__device__ __forceinline__ bool deposit_settled(const PushArgs<float> &a, const WinAcc<float> &acc, const int l[3],
-                                                const int s[3], const float f[3], const float fn[3], float w,
-                                                float vz) {
+// Deposit of a particle whose support did not change.  Returns false,
+// depositing nothing, when the support changes on some axis: such a particle
+// takes the general ORDER + 2 node stencil (deposit_particle), through the
+// block's queue of deferred jobs.
+template <class R, int DIM, int ORDER>
+__device__ __forceinline__ bool deposit_settled(const PushArgs<R> &a, const WinAcc<R> &acc, const int l[3],
+                                                const int s[3], const R f[3], const R fn[3], R w, R vz) {
   using G = Geo<DIM, ORDER>;
-  SettledAxis<ORDER> X, Y, Z;
+  SettledAxis<R, ORDER> X, Y, Z;
   bool ok = X.set(f[0], s[0], fn[0]);
   ok = Y.set(f[1], s[1], fn[1]) && ok;
   if (DIM == 3) ok = Z.set(f[2], s[2], fn[2]) && ok;
   else Z.zero();
   if (!ok) return false;
   // a warp whose settled particles neither move nor (2D3V) carry vz deposits nothing
-  const bool moves = w != 0.0f && (X.dl != 0.0f || Y.dl != 0.0f || (DIM == 3 ? Z.dl != 0.0f : vz != 0.0f));
+  const bool moves = w != R(0) && (X.dl != R(0) || Y.dl != R(0) || (DIM == 3 ? Z.dl != R(0) : vz != R(0)));
   if (!__any_sync(__activemask(), moves)) return true;
   constexpr int oJ = G::D + G::LOJ;
 #ifdef PIC_CHECKED
@@ -528,29 +543,32 @@ __device__ __forceinline__ bool deposit_settled(const PushArgs<float> &a, const 
   }
 #endif
   const int jb = (l[0] + X.rel + oJ) + (l[1] + Y.rel + oJ) * G::JX + (DIM == 3 ? (l[2] + Z.rel + oJ) * G::JP : 0);
-  const unsigned sb = (unsigned)__cvta_generic_to_shared(acc.w) + 4u * (unsigned)jb;
-  const float ws = w * acc.scale;
-  deposit_settled_win<ORDER, DIM, G::JX, G::JP, G::JS>(sb, X, Y, Z, a.jfac[0] * ws, a.jfac[1] * ws,
-                                                        a.jfac[2] * ws, a.qz * ws * vz);
+  SettledSink<R, G::JS> out;
+  if constexpr (sizeof(R) == 4) out.sb = (unsigned)__cvta_generic_to_shared(acc.w) + 4u * (unsigned)jb;
+  else out.w = acc.w + jb;
+  const R ws = w * acc.scale;
+  deposit_settled_win<R, ORDER, DIM, G::JX, G::JP, G::JS>(out, X, Y, Z, a.jfac[0] * ws, a.jfac[1] * ws,
+                                                           a.jfac[2] * ws, a.qz * ws * vz);
   return true;
 }
 
-// Deferred deposit jobs of particles whose support changes (FP32 runs): up
-// to kQCap entries in shared memory, appended by warps through a shared
-// counter and deposited once, at the end of the work item, by all threads
-// together (dq_drain), so that the general stencil runs on full warps
-// instead of on the few lanes of every warp that hold such a particle.  A
-// job that finds the queue full is deposited on the spot.
+// Deferred deposit jobs of particles whose support changes: up to kQCap
+// entries in shared memory, appended by warps through a shared counter and
+// deposited once, at the end of the work item, by all threads together
+// (dq_drain), so that the general stencil runs on full warps instead of on
+// the few lanes of every warp that hold such a particle.  A job that finds
+// the queue full is deposited on the spot.
 constexpr int kQCap = 224;
-struct DepQueue {
-  int *job;    // [kQCap] packed cell and shift (pack_job) | axes whose support changes << 22
-  float *f;    // [7][kQCap]: old offsets x y z, new offsets x y z, weight (2D3V: vz in the old z slot)
-  int *tail;   // shared counter of appended jobs
+template <class R> struct DepQueue {
+  int *job;  // [kQCap] packed cell and shift (pack_job) | axes whose support changes << 22
+  R *f;      // [7][kQCap]: old offsets x y z, new offsets x y z, weight (2D3V: vz in the old z slot)
+  int *tail;  // shared counter of appended jobs
 };
 
 // Append this lane's job; false when the queue is full.
-__device__ __forceinline__ bool dq_push(const DepQueue &q, int job, const float f[3], const float fn[3], float w,
-                                        float vz, bool twod) {
+template <class R>
+__device__ __forceinline__ bool dq_push(const DepQueue<R> &q, int job, const R f[3], const R fn[3], R w, R vz,
+                                        bool twod) {
   const unsigned act = __activemask();
   const int lane = threadIdx.x & 31, leader = __ffs(act) - 1;
   int base = 0;
@@ -569,11 +587,12 @@ __device__ __forceinline__ bool dq_push(const DepQueue &q, int job, const float 
 }
 
 // The axes (bit d) on which a particle's shape support changes over a move.
-template <int ORDER> __device__ __forceinline__ int support_change(const float f[3], const int s[3], const float fn[3]) {
+template <class R, int ORDER>
+__device__ __forceinline__ int support_change(const R f[3], const int s[3], const R fn[3]) {
   int m = 0;
 #pragma unroll
   for (int d = 0; d < 3; ++d) {
-    const bool ch = ORDER == 2 ? (s[d] + (fn[d] >= 0.5f) != (f[d] >= 0.5f)) : s[d] != 0;
+    const bool ch = ORDER == 2 ? (s[d] + (fn[d] >= R(0.5)) != (f[d] >= R(0.5))) : s[d] != 0;
     m |= ch ? 1 << d : 0;
   }
   return m;
@@ -660,8 +679,8 @@ __device__ __forceinline__ bool deposit_particle(const PushArgs<R> &a, const Win
 // lanes of a warp mostly share that set and the warp-uniform skip of the
 // outer stencil shell in deposit_particle drops the axes that did not
 // change.  Block-wide: every thread of the block calls it.
-template <int DIM, int ORDER>
-__device__ __forceinline__ void dq_drain(const PushArgs<float> &a, const WinAcc<float> &acc, const DepQueue &q, int n,
+template <class R, int DIM, int ORDER>
+__device__ __forceinline__ void dq_drain(const PushArgs<R> &a, const WinAcc<R> &acc, const DepQueue<R> &q, int n,
                                          int *order) {
   __shared__ int s_cls[8];
   const int i = threadIdx.x;
@@ -684,14 +703,14 @@ __device__ __forceinline__ void dq_drain(const PushArgs<float> &a, const WinAcc<
   const int at = order[i];
   int l[3], sh[3];
   unpack_job(q.job[at] & ((1 << 22) - 1), l, sh);
-  float f[3], fn[3];
+  R f[3], fn[3];
 #pragma unroll
   for (int d = 0; d < 3; ++d) {
-    f[d] = (DIM == 2 && d == 2) ? 0.0f : q.f[d * kQCap + at];
+    f[d] = (DIM == 2 && d == 2) ? R(0) : q.f[d * kQCap + at];
     fn[d] = q.f[(3 + d) * kQCap + at];
   }
-  const float vz = DIM == 2 ? q.f[2 * kQCap + at] : 0.0f;
-  deposit_particle<float, DIM, ORDER>(a, acc, l, sh, f, fn, q.f[6 * kQCap + at], vz);
+  const R vz = DIM == 2 ? q.f[2 * kQCap + at] : R(0);
+  deposit_particle<R, DIM, ORDER>(a, acc, l, sh, f, fn, q.f[6 * kQCap + at], vz);
 }
 
 template <class R, int DIM, int ORDER>
@@ -715,11 +734,12 @@ __global__ void __launch_bounds__(kThreads, sizeof(R) == 4 ? (DIM == 2 ? 4 : (OR
   R *sW = sU + 3 * kThreads;                  // 256
   int32_t *sCell = reinterpret_cast<int32_t *>(sW + kThreads);  // 256
   int32_t *sJob = sCell + kThreads;  // FP32 3D: 256 deposit jobs
-  // FP32: queue of deferred deposit jobs (after the jobs in 3D, after the cells in 2D)
-  constexpr bool kSettled = sizeof(R) == 4;
-  DepQueue dq;
-  dq.job = sCell + (DIM == 3 ? 2 : 1) * kThreads;
-  dq.f = reinterpret_cast<float *>(dq.job + kQCap);
+  // queue of deferred deposit jobs (after the jobs in 3D FP32, after the cells otherwise)
+  constexpr bool kSplitLayout = DIM == 3 && sizeof(R) == 4;
+  constexpr int kQJobBytes = 4 * kQCap;  // a multiple of 8: the R array that follows stays aligned
+  DepQueue<R> dq;
+  dq.job = sCell + (kSplitLayout ? 2 : 1) * kThreads;
+  dq.f = reinterpret_cast<R *>(reinterpret_cast<char *>(dq.job) + kQJobBytes);
   __shared__ int s_qtail;
   dq.tail = &s_qtail;
   __shared__ unsigned int s_clamp;
@@ -941,11 +961,11 @@ __global__ void __launch_bounds__(kThreads, sizeof(R) == 4 ? (DIM == 2 ? 4 : (OR
 
           if (!kSplit) {
             bool done = false;
-            if constexpr (kSettled) {
+            {
               const R vz = u[2] * ig;
-              done = deposit_settled<DIM, ORDER>(a, acc, l, s, f, fn, sW[ep], vz) ||
-                     dq_push(dq, pack_job(l, s) | support_change<ORDER>(f, s, fn) << 22, f, fn, sW[ep], vz,
-                             DIM == 2);
+              done = deposit_settled<R, DIM, ORDER>(a, acc, l, s, f, fn, sW[ep], vz) ||
+                     dq_push<R>(dq, pack_job(l, s) | support_change<R, ORDER>(f, s, fn) << 22, f, fn, sW[ep], vz,
+                                DIM == 2);
             }
             if (!done && !deposit_particle<R, DIM, ORDER>(a, acc, l, s, f, fn, sW[ep], u[2] * ig))
               break;  // (checked build) leaves the particle as it was
@@ -1009,9 +1029,8 @@ __global__ void __launch_bounds__(kThreads, sizeof(R) == 4 ? (DIM == 2 ? 4 : (OR
             fn[d] = sOff[d * kThreads + e];
           }
           bool done = false;
-          if constexpr (kSettled)
-            done = deposit_settled<DIM, ORDER>(a, acc, l, s, f, fn, sW[e], 0.0f) ||
-                   dq_push(dq, job | support_change<ORDER>(f, s, fn) << 22, f, fn, sW[e], 0.0f, false);
+          done = deposit_settled<R, DIM, ORDER>(a, acc, l, s, f, fn, sW[e], R(0)) ||
+                 dq_push<R>(dq, job | support_change<R, ORDER>(f, s, fn) << 22, f, fn, sW[e], R(0), false);
           if (!done) deposit_particle<R, DIM, ORDER>(a, acc, l, s, f, fn, sW[e], R(0));
         }
       }
@@ -1027,10 +1046,10 @@ __global__ void __launch_bounds__(kThreads, sizeof(R) == 4 ? (DIM == 2 ? 4 : (OR
       for (int d = 0; d < 3; ++d) a.u[d][p] = sU[d * kThreads + tid];
     }
   }
-  if constexpr (kSettled) {
+  {
     // the deferred jobs of the whole work item (the chunk loop ended on a barrier)
     const int nq = *(volatile int *)dq.tail;
-    dq_drain<DIM, ORDER>(a, acc, dq, nq > kQCap ? kQCap : nq, sCell);
+    dq_drain<R, DIM, ORDER>(a, acc, dq, nq > kQCap ? kQCap : nq, sCell);
   }
 
   if (my_clamp) atomicAdd(&s_clamp, my_clamp);
@@ -1194,7 +1213,7 @@ template <class R, int DIM, int ORDER> constexpr size_t smem_bytes() {
   // deposit jobs (a packed int per slot)
   constexpr bool split = DIM == 3 && sizeof(R) == 4;
   return (size_t)(6 * G::EN + (DIM + 4) * kThreads) * sizeof(R) + 24 * (size_t)G::JS +
-         (split ? 2 : 1) * kThreads * sizeof(int32_t) + (sizeof(R) == 4 ? 8 * kQCap * sizeof(int32_t) : 0);
+         (split ? 2 : 1) * kThreads * sizeof(int32_t) + kQCap * (sizeof(int32_t) + 7 * sizeof(R));
 }
 
 template <class R, int DIM, int ORDER>
