@@ -38,9 +38,10 @@ struct Species {
   pic::WorkSplit work;          // push work items (tile pieces of at most work.chunk slots)
   float *tq = nullptr;          // per-item deposit bound carried between pushes
   // escapes of the last push, read back without blocking (adaptive sort)
-  unsigned long long *esc_host = nullptr;  // page-locked
+  unsigned long long *esc_host = nullptr;  // page-locked: [0] escapes, [1] deferred deposit jobs
   cudaEvent_t esc_ev = nullptr;
   bool esc_pending = false;
+  bool mid_drain = false;       // push variant draining its job queue between chunks
   bool fresh = true;            // sorted since the last push
   bool need_sort = true;
   int64_t sorted_at = -1;  // step count at the last sort
@@ -476,7 +477,7 @@ int pic_create(const pic_config *cfg, pic_handle **out) {
        cudaMalloc(&h->keys, (size_t)nkeys * sizeof(int32_t)) == cudaSuccess &&
        cudaMalloc(&h->tile_tmp, (size_t)(g.ntiles + 1) * sizeof(int64_t)) == cudaSuccess &&
        cudaMalloc(&h->ctr, sizeof(Counters)) == cudaSuccess && cudaMalloc(&h->bad, sizeof(unsigned long long)) == cudaSuccess &&
-       cudaMalloc(&h->esc_count, sizeof(unsigned long long)) == cudaSuccess &&
+       cudaMalloc(&h->esc_count, 2 * sizeof(unsigned long long)) == cudaSuccess &&
        cudaMalloc(&h->mur, 8 * sizeof(double) * (size_t)g.n[1] * g.n[2]) == cudaSuccess;
   if (!ok) {
     pic_destroy(h);
@@ -591,7 +592,7 @@ int pic_add_species(pic_handle *h, double q, double m, int64_t capacity, int *sp
     s.work.nwork = s.slots / s.work.chunk + 1 + h->g.ntiles;
   }
   if (e == cudaSuccess) e = cudaMalloc(&s.tq, (size_t)2 * s.work.nwork * sizeof(float));
-  if (e == cudaSuccess) e = cudaMallocHost(&s.esc_host, sizeof(unsigned long long));
+  if (e == cudaSuccess) e = cudaMallocHost(&s.esc_host, 2 * sizeof(unsigned long long));
   if (e == cudaSuccess) e = cudaEventCreateWithFlags(&s.esc_ev, cudaEventDisableTiming);
   if (e == cudaSuccess) e = cudaMalloc(&s.work.work_tile, (size_t)s.work.nwork * sizeof(int32_t));
   if (e == cudaSuccess) e = cudaMalloc(&s.work.work_pb, (size_t)s.work.nwork * sizeof(int64_t));
@@ -1080,7 +1081,10 @@ int pic_step(pic_handle *h, int nsteps) {
         if (q == cudaSuccess) {
           s.esc_pending = false;
           const unsigned long long lim = (unsigned long long)(s.h_count / 200 > 1024 ? s.h_count / 200 : 1024);
-          many_escapes = *s.esc_host > lim;
+          many_escapes = s.esc_host[0] > lim;
+          // many particles changing shape support per step (fast beams): the
+          // push variant that drains its deferred-job queue between chunks
+          s.mid_drain = s.esc_host[1] > (unsigned long long)pic::kPushQueueMidDrain * (unsigned long long)s.work.nwork;
         } else {
           cudaGetLastError();  // not ready: not an error
         }
@@ -1109,12 +1113,13 @@ int pic_step(pic_handle *h, int nsteps) {
       int nl = 0;
       CK(h,
          pic::launch_push(h->g, h->E, h->B, h->J, s.buf[s.cur], s.tile_start, s.work, s.tq, s.fresh ? 1 : 0,
-                          s.rank, h->esc_count, s.q, s.m, h->ctr, h->st, &nl),
+                          s.rank, h->esc_count, s.q, s.m, h->ctr, h->st, &nl, s.mid_drain ? 1 : 0),
          "push");
       s.fresh = false;
       h->launches += nl;
       if (s.esc_host && !s.esc_pending) {
-        CK(h, cudaMemcpyAsync(s.esc_host, h->esc_count, sizeof(unsigned long long), cudaMemcpyDeviceToHost, h->st),
+        CK(h, cudaMemcpyAsync(s.esc_host, h->esc_count, 2 * sizeof(unsigned long long), cudaMemcpyDeviceToHost,
+                              h->st),
            "escape count");
         CK(h, cudaEventRecord(s.esc_ev, h->st), "escape event");
         s.esc_pending = true;

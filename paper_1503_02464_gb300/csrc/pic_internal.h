@@ -141,12 +141,19 @@ struct WorkSplit {
 // work item) carries the bound of the FP32 fixed-point deposit from one step
 // to the next; fresh = 1 on the first push after a sort (tq is recomputed
 // from the particles).
-// esc_list (one int per slot) and esc_count are scratch for particles
-// deferred to the escape kernel.
+// esc_list (one int per slot) is scratch for particles deferred to the
+// escape kernel; esc_count (two counters) receives their number and the
+// number of deferred deposit jobs (particles whose shape support changed)
+// of the launch.  mid_drain selects the kernel variant that deposits those
+// jobs between chunks when its queue fills (3D): the caller turns it on for
+// a species whose last push averaged more than kPushQueueMidDrain jobs per
+// work item.
+constexpr int kPushQueueCap = 224;      // deferred deposit jobs a work item queues at a time
+constexpr int kPushQueueMidDrain = 168;  // 3/4 of the queue
 cudaError_t launch_push(const Grid &g, void *const E[3], void *const B[3], void *const J[3], const Particles &p,
                         const int64_t *tile_start, const WorkSplit &ws, float *tq, int fresh, int32_t *esc_list,
                         unsigned long long *esc_count, double q, double m, Counters *ctr, cudaStream_t st,
-                        int *nlaunch);
+                        int *nlaunch, int mid_drain);
 
 // Diagnostics charge density of particles sorted by tile (exact 64-bit
 // fixed-point window sums; adds into rho).

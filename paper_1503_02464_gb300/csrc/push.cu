@@ -105,6 +105,7 @@ template <class R> struct PushArgs {
   int fresh;                        // tile contents changed (sorted) since tq was written
   int32_t *esc_list;                // slots deferred to k_push_escaped
   unsigned long long *esc_count;
+  unsigned long long *q_jobs;       // deferred deposit jobs of this launch (counted at each drain)
   R qmh;      // q dt / (2 m)
   R dtdx[3];  // dt / dx_a
   R jfac[3];  // -q dx_a / dt  (Esirkepov running-sum scale, times w)
@@ -558,7 +559,13 @@ __device__ __forceinline__ bool deposit_settled(const PushArgs<R> &a, const WinA
 // (dq_drain), so that the general stencil runs on full warps instead of on
 // the few lanes of every warp that hold such a particle.  A job that finds
 // the queue full is deposited on the spot.
-constexpr int kQCap = 224;
+constexpr int kQCap = kPushQueueCap;
+// A chunk after which the queue could not take another chunk's worth of jobs
+// (1.5 times what the last chunk added) drains it, the whole block taking
+// one job per thread, so that plasmas whose particles change support often
+// (fast beams) do not overflow it and deposit in divergent lanes.  A plasma
+// with few such particles drains once, at the end of the work item: every
+// drain costs a partly idle block-wide pass.
 template <class R> struct DepQueue {
   int *job;  // [kQCap] packed cell and shift (pack_job) | axes whose support changes << 22
   R *f;      // [7][kQCap]: old offsets x y z, new offsets x y z, weight (2D3V: vz in the old z slot)
@@ -673,7 +680,8 @@ __device__ __forceinline__ bool deposit_particle(const PushArgs<R> &a, const Win
   return true;
 }
 
-// Deposit the n <= kQCap queued jobs on the general stencil, one per thread.
+// Deposit the n <= kQCap queued jobs on the general stencil, one per thread
+// (with `reset`, the queue is emptied for the jobs of the next chunks).
 // The jobs are first ordered by the axes on which their support changes
 // (a counting sort into `order`, kQCap ints of shared memory), so that the
 // lanes of a warp mostly share that set and the warp-uniform skip of the
@@ -681,11 +689,14 @@ __device__ __forceinline__ bool deposit_particle(const PushArgs<R> &a, const Win
 // change.  Block-wide: every thread of the block calls it.
 template <class R, int DIM, int ORDER>
 __device__ __forceinline__ void dq_drain(const PushArgs<R> &a, const WinAcc<R> &acc, const DepQueue<R> &q, int n,
-                                         int *order) {
+                                         int *order, bool reset) {
   __shared__ int s_cls[8];
   const int i = threadIdx.x;
   if (i < 8) s_cls[i] = 0;
   __syncthreads();
+  // every thread has read the count: the queue may start over (appends
+  // resume only after the next chunk's barriers)
+  if (reset && i == 0) *q.tail = 0;
   int cls = 0, rank = 0;
   if (i < n) {
     cls = (q.job[i] >> 22) & 7;
@@ -713,7 +724,9 @@ __device__ __forceinline__ void dq_drain(const PushArgs<R> &a, const WinAcc<R> &
   deposit_particle<R, DIM, ORDER>(a, acc, l, sh, f, fn, q.f[6 * kQCap + at], vz);
 }
 
-template <class R, int DIM, int ORDER>
+// MID: drain the queue between chunks when it fills (for plasmas whose
+// particles change support often; see the launcher).
+template <class R, int DIM, int ORDER, bool MID>
 // Blocks per SM the register allocation is held to: FP32 3D TSC windows
 // fill half the shared memory (two blocks); the 3D CIC windows leave room for
 // three, which fit at 72 registers (1.27x faster than two); FP32 2D windows
@@ -736,12 +749,18 @@ __global__ void __launch_bounds__(kThreads, sizeof(R) == 4 ? (DIM == 2 ? 4 : (OR
   int32_t *sJob = sCell + kThreads;  // FP32 3D: 256 deposit jobs
   // queue of deferred deposit jobs (after the jobs in 3D FP32, after the cells otherwise)
   constexpr bool kSplitLayout = DIM == 3 && sizeof(R) == 4;
+  // the settled stencils and the queue: all but FP64 2D, whose kernel is
+  // bound by the FP64 pipe in its gather and lost occupancy to the extra
+  // registers and shared memory (measured 2.22 -> 1.91 G particle-steps/s
+  // on the 2D laser slab)
+  constexpr bool kSettled = !(sizeof(R) == 8 && DIM == 2);
   constexpr int kQJobBytes = 4 * kQCap;  // a multiple of 8: the R array that follows stays aligned
   DepQueue<R> dq;
   dq.job = sCell + (kSplitLayout ? 2 : 1) * kThreads;
   dq.f = reinterpret_cast<R *>(reinterpret_cast<char *>(dq.job) + kQJobBytes);
   __shared__ int s_qtail;
   dq.tail = &s_qtail;
+  int q_prev = 0;  // jobs queued at the end of the previous chunk (the same in every thread)
   __shared__ unsigned int s_clamp;
   __shared__ double s_scale;
   __shared__ unsigned int s_emax[3];
@@ -961,7 +980,7 @@ __global__ void __launch_bounds__(kThreads, sizeof(R) == 4 ? (DIM == 2 ? 4 : (OR
 
           if (!kSplit) {
             bool done = false;
-            {
+            if constexpr (kSettled) {
               const R vz = u[2] * ig;
               done = deposit_settled<R, DIM, ORDER>(a, acc, l, s, f, fn, sW[ep], vz) ||
                      dq_push<R>(dq, pack_job(l, s) | support_change<R, ORDER>(f, s, fn) << 22, f, fn, sW[ep], vz,
@@ -1029,8 +1048,9 @@ __global__ void __launch_bounds__(kThreads, sizeof(R) == 4 ? (DIM == 2 ? 4 : (OR
             fn[d] = sOff[d * kThreads + e];
           }
           bool done = false;
-          done = deposit_settled<R, DIM, ORDER>(a, acc, l, s, f, fn, sW[e], R(0)) ||
-                 dq_push<R>(dq, job | support_change<R, ORDER>(f, s, fn) << 22, f, fn, sW[e], R(0), false);
+          if constexpr (kSettled)
+            done = deposit_settled<R, DIM, ORDER>(a, acc, l, s, f, fn, sW[e], R(0)) ||
+                   dq_push<R>(dq, job | support_change<R, ORDER>(f, s, fn) << 22, f, fn, sW[e], R(0), false);
           if (!done) deposit_particle<R, DIM, ORDER>(a, acc, l, s, f, fn, sW[e], R(0));
         }
       }
@@ -1045,11 +1065,23 @@ __global__ void __launch_bounds__(kThreads, sizeof(R) == 4 ? (DIM == 2 ? 4 : (OR
 #pragma unroll
       for (int d = 0; d < 3; ++d) a.u[d][p] = sU[d * kThreads + tid];
     }
+    if constexpr (kSettled && MID) {
+      const int nq = *(volatile int *)dq.tail;  // read by every thread after the barrier above
+      const int inc = nq - q_prev;
+      if (nq + inc + inc / 2 > kQCap) {
+        if (tid == 0) atomicAdd(a.q_jobs, (unsigned long long)nq);
+        dq_drain<R, DIM, ORDER>(a, acc, dq, nq > kQCap ? kQCap : nq, sCell, true);
+        q_prev = 0;
+      } else {
+        q_prev = nq;
+      }
+    }
   }
-  {
-    // the deferred jobs of the whole work item (the chunk loop ended on a barrier)
+  if constexpr (kSettled) {
+    // the deferred jobs still queued (the chunk loop ended on a barrier)
     const int nq = *(volatile int *)dq.tail;
-    dq_drain<R, DIM, ORDER>(a, acc, dq, nq > kQCap ? kQCap : nq, sCell);
+    if (tid == 0 && nq > 0) atomicAdd(a.q_jobs, (unsigned long long)nq);
+    dq_drain<R, DIM, ORDER>(a, acc, dq, nq > kQCap ? kQCap : nq, sCell, false);
   }
 
   if (my_clamp) atomicAdd(&s_clamp, my_clamp);
@@ -1213,14 +1245,15 @@ template <class R, int DIM, int ORDER> constexpr size_t smem_bytes() {
   // deposit jobs (a packed int per slot)
   constexpr bool split = DIM == 3 && sizeof(R) == 4;
   return (size_t)(6 * G::EN + (DIM + 4) * kThreads) * sizeof(R) + 24 * (size_t)G::JS +
-         (split ? 2 : 1) * kThreads * sizeof(int32_t) + kQCap * (sizeof(int32_t) + 7 * sizeof(R));
+         (split ? 2 : 1) * kThreads * sizeof(int32_t) +
+         (sizeof(R) == 8 && DIM == 2 ? 0 : kQCap * (sizeof(int32_t) + 7 * sizeof(R)));
 }
 
 template <class R, int DIM, int ORDER>
 cudaError_t launch_t(const Grid &g, void *const E[3], void *const B[3], void *const J[3], const Particles &p,
                      const int64_t *tile_start, const WorkSplit &ws, float *tq, int fresh, int32_t *esc_list,
                      unsigned long long *esc_count, double q, double m, Counters *ctr, cudaStream_t st,
-                     int *nlaunch) {
+                     int *nlaunch, bool mid_drain) {
   PushArgs<R> a;
   a.work_tile = ws.work_tile;
   a.work_pb = ws.work_pb;
@@ -1247,17 +1280,20 @@ cudaError_t launch_t(const Grid &g, void *const E[3], void *const B[3], void *co
   a.tile_start = tile_start;
   a.esc_list = esc_list;
   a.esc_count = esc_count;
+  a.q_jobs = esc_count + 1;
   a.qmh = (R)(q * g.dt / (2.0 * m));
   a.qz = (R)q;
   a.absorb = g.absorb_lo || g.absorb_hi;
   a.ec = g.gather_ec;
   a.ctr = ctr;
   constexpr size_t smem = smem_bytes<R, DIM, ORDER>();
-  auto fn = k_push<R, DIM, ORDER>;
+  // the variant that drains between chunks only where it can matter (3D;
+  // 2D targets queue few jobs)
+  auto fn = (DIM == 3 && mid_drain) ? k_push<R, DIM, ORDER, DIM == 3> : k_push<R, DIM, ORDER, false>;
   cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   if (ws.nwork > 0x7fffffff) return cudaErrorInvalidValue;
-  e = cudaMemsetAsync(esc_count, 0, sizeof(unsigned long long), st);
+  e = cudaMemsetAsync(esc_count, 0, 2 * sizeof(unsigned long long), st);
   if (e != cudaSuccess) return e;
   fn<<<(unsigned)ws.nwork, kThreads, smem, st>>>(a);
   int dev = 0, nsm = 0;
@@ -1512,11 +1548,12 @@ size_t push_smem_bytes(const Grid &g) {
 cudaError_t launch_push(const Grid &g, void *const E[3], void *const B[3], void *const J[3], const Particles &p,
                         const int64_t *tile_start, const WorkSplit &ws, float *tq, int fresh, int32_t *esc_list,
                         unsigned long long *esc_count, double q, double m, Counters *ctr, cudaStream_t st,
-                        int *nlaunch) {
+                        int *nlaunch, int mid_drain) {
   const int key = (g.prec == 1 ? 100 : 0) + g.dims * 10 + g.order;
-#define PIC_PUSH_CASE(K, R, D, O) \
-  case K:                                                                                                    \
-    return launch_t<R, D, O>(g, E, B, J, p, tile_start, ws, tq, fresh, esc_list, esc_count, q, m, ctr, st, nlaunch);
+#define PIC_PUSH_CASE(K, R, D, O)                                                                        \
+  case K:                                                                                                \
+    return launch_t<R, D, O>(g, E, B, J, p, tile_start, ws, tq, fresh, esc_list, esc_count, q, m, ctr, st, \
+                             nlaunch, mid_drain != 0);
   switch (key) {
     PIC_PUSH_CASE(21, float, 2, 1)
     PIC_PUSH_CASE(22, float, 2, 2)
