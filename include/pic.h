@@ -163,6 +163,16 @@ typedef struct {
                              a push sent more than 0.5 % of a species (at least
                              1024 particles) down the escape path              */
   int64_t step;           /* completed time steps                                 */
+  int64_t n_push_mid_drain; /* species pushes that took the kernel variant which
+                             deposits its deferred shape-changing particles
+                             between chunks (chosen when the previous push of
+                             the species averaged more than 168 of them per
+                             work item, e.g. fast beams)                      */
+  int64_t n_adj_escaped;  /* particle adjoints since pic_adjoint_begin computed
+                             on the global-memory path: the particle had moved
+                             more than 2 cells out of the tile it was sorted
+                             into (the rest use the tile's window in shared
+                             memory)                                          */
 } pic_diag_t;
 
 /* Per-step energy read-back: per-element terms in the storage precision,
@@ -273,7 +283,8 @@ int pic_sync(pic_handle *h);
  * (ms) and launch counts (launches) into caller-owned arrays of nmax
  * entries (either may be NULL); class order: 0 sort, 1 zero J, 2 push,
  * 3 Yee B, 4 Yee E, 5 boundary, 6 current smoothing, 7 adjoint field
- * updates, 8 adjoint particle kernel.  The number of classes written goes
+ * updates, 8 adjoint particle kernel, 9 checkpoint, restore and tape copies
+ * (device-to-device).  The number of classes written goes
  * to *ncls (NULL allowed).  PIC_EINVAL for a NULL handle. */
 int pic_profile(pic_handle *h, int enable);
 int pic_timings(pic_handle *h, double *ms, int64_t *launches, int nmax, int *ncls);
@@ -332,6 +343,20 @@ int pic_adjoint_step(pic_handle *h, int nsteps);
  * particle id (id_capacity doubles, may be NULL) to host or device memory.
  * Synchronises. */
 int pic_grad(pic_handle *h, double *d_a0, int species, double *d_w, int mem_kind);
+
+/* dF/dw of `species` summed over bins of particle ids (row A16: the gradient
+ * with respect to an initial density profile, the bins its columns):
+ * out[b] = sum of dF/dw over the ids i < n_ids with bin_of_id[i] == b, for
+ * b in [0, nbins); ids with a bin outside that range are left out.
+ * bin_of_id (n_ids int32) and out (nbins doubles) are both in host or both
+ * in device memory per mem_kind (a host map is copied to the device per
+ * call).  The sums run on the device in FP64; a warp's ids are summed in
+ * lane order, the warps' partial sums by atomics, so the last bits may
+ * differ between calls.  Synchronises.  PIC_EINVAL: NULL arguments, no
+ * pic_adjoint_begin, bad species or memory kind, n_ids outside
+ * [0, id_capacity], nbins < 1; PIC_ENOMEM, PIC_ECUDA. */
+int pic_grad_binned(pic_handle *h, int species, const int32_t *bin_of_id, int64_t n_ids, int nbins, double *out,
+                    int mem_kind);
 
 /* Adjoint state, for objectives of the caller's own and for checks of the
  * transposes (the adjoint of §2's cycle as above; this access has no

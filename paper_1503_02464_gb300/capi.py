@@ -18,7 +18,8 @@ PIC_GATHER_MOMENTUM, PIC_GATHER_ENERGY = 0, 1
 PIC_OUT_FIELD, PIC_OUT_PARTICLES = 0, 1
 PIC_MEM_HOST, PIC_MEM_DEVICE = 0, 1
 PIC_EX, PIC_EY, PIC_EZ, PIC_BX, PIC_BY, PIC_BZ, PIC_JX, PIC_JY, PIC_JZ, PIC_RHO = range(10)
-KERNEL_CLASSES = ["sort", "zero_j", "push", "yee_b", "yee_e", "boundary", "filter", "adj_field", "adj_push"]
+KERNEL_CLASSES = ["sort", "zero_j", "push", "yee_b", "yee_e", "boundary", "filter", "adj_field", "adj_push",
+                  "tape"]
 
 ERROR_NAMES = {0: "PIC_OK", 1: "PIC_EINVAL", 2: "PIC_ECOURANT", 3: "PIC_ENOMEM", 4: "PIC_ECUDA",
                5: "PIC_EOVERFLOW", 6: "PIC_ETIMEOUT", 7: "PIC_ENAN"}
@@ -31,7 +32,7 @@ EXPORTED = ["pic_create", "pic_destroy", "pic_last_error", "pic_add_species", "p
             "pic_grad", "pic_state_size", "pic_state_save", "pic_state_load", "pic_output_due", "pic_output_add", "pic_output_capture", "pic_output_count",
             "pic_output_read", "pic_output_remove", "pic_field_energy_noalloc", "pic_alu_peak",
             "pic_adjoint_field", "pic_adjoint_set_field", "pic_adjoint_momenta", "pic_adjoint_set_momenta",
-            "pic_tape_record"]
+            "pic_tape_record", "pic_grad_binned"]
 
 
 class pic_laser(ctypes.Structure):
@@ -60,7 +61,8 @@ class pic_diag_t(ctypes.Structure):
                 ("energy_kinetic", ctypes.c_double), ("charge", ctypes.c_double), ("gauss_max", ctypes.c_double),
                 ("continuity_max", ctypes.c_double), ("n_alive", ctypes.c_int64), ("n_escaped", ctypes.c_int64),
                 ("n_clamped", ctypes.c_int64), ("n_absorbed", ctypes.c_int64), ("n_sorts_adaptive", ctypes.c_int64),
-                ("step", ctypes.c_int64)]
+                ("step", ctypes.c_int64), ("n_push_mid_drain", ctypes.c_int64),
+                ("n_adj_escaped", ctypes.c_int64)]
 
     def as_dict(self) -> dict:
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -136,6 +138,7 @@ def load(build_if_missing: bool = True) -> ctypes.CDLL:
         "pic_adjoint_seed_kinetic": ([hp, ctypes.c_int, ctypes.c_int, ctypes.c_int, dp], ctypes.c_int),
         "pic_adjoint_step": ([hp, ctypes.c_int], ctypes.c_int),
         "pic_grad": ([hp, dp, ctypes.c_int, vp, ctypes.c_int], ctypes.c_int),
+        "pic_grad_binned": ([hp, ctypes.c_int, vp, i64, ctypes.c_int, vp, ctypes.c_int], ctypes.c_int),
         "pic_field_energy_noalloc": ([ctypes.c_int, ctypes.c_void_p * 3, ctypes.c_void_p * 3, i64, ctypes.c_double,
                                       vp, ctypes.c_int, vp], ctypes.c_int),
         "pic_state_size": ([hp, ctypes.POINTER(ctypes.c_int64)], ctypes.c_int),
@@ -283,6 +286,10 @@ def pic_grad(h, species: int, dw_ptr, mem_kind: int) -> float:
     d_a0 = ctypes.c_double()
     check(h, load().pic_grad(h, ctypes.byref(d_a0), int(species), dw_ptr, int(mem_kind)))
     return d_a0.value
+
+
+def pic_grad_binned(h, species: int, bin_ptr, n_ids: int, nbins: int, out_ptr, mem_kind: int) -> None:
+    check(h, load().pic_grad_binned(h, int(species), bin_ptr, int(n_ids), int(nbins), out_ptr, int(mem_kind)))
 
 
 def pic_state_size(h) -> int:

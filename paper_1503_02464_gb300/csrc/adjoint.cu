@@ -279,23 +279,54 @@ __device__ __forceinline__ void boris_fwd(R h, const R u0[3], const R F[6], R um
   uo[2] = um[2] + (up[0] * sv[1] - up[1] * sv[0]) + h * F[2];
 }
 
-// Per-particle adjoint of gather -> Boris -> move -> Esirkepov (2D3V, TSC).
-// The kernel is latency-bound (scattered field and adjoint reads), so the
-// register cap (3 blocks of 256 per SM for FP32, 2 for FP64) trades a few
-// spills for occupancy.
-template <class R>
-__global__ void __launch_bounds__(256, sizeof(R) == 4 ? 3 : 2) k_adj_push2d(const AdjPushArgs<R> a) {
-  const int n0 = a.n[0], n1 = a.n[1];
-  const int64_t nslots = *a.d_count;
-  for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < nslots; p += (int64_t)gridDim.x * blockDim.x) {
-    const int c = a.cell[p];
-    if (c < 0) continue;
-    const uint32_t pid = a.id[p];
-    if ((int64_t)pid >= a.id_cap) {
-      atomicOr(a.err, 1ull);  // id outside the adjoint arrays: skipped, reported
-      continue;
-    }
-    const int i0 = c % n0, j0 = c / n0;
+// Where one particle's stencils find their nodes: the node r cells along x
+// and r' along y from the particle's cell has index x(r) + y(r') in the
+// arrays it reads, F (E then B) and J (lamJ), and index sx(r) + sy(r') in the
+// arrays it scatters into, L (lamE then lamB, in global memory: float
+// atomics in shared memory would be compare-and-swap loops, and the lanes
+// of a warp often share nodes).  GridNodes: the whole periodic grid in
+// global memory.  WindowNodes: E, B and lamJ of a cell tile's window staged
+// in shared memory (kAdjWin nodes per axis).
+template <class R> struct GridNodes {
+  int i0, j0, n0, n1;
+  const R *const *F;  // [6]
+  const R *const *J;  // [3]
+  R *const *L;        // [6]
+  __device__ __forceinline__ int x(int r) const { return wrapi(i0 + r, n0); }
+  __device__ __forceinline__ int y(int r) const { return wrapi(j0 + r, n1) * n0; }
+  __device__ __forceinline__ int sx(int r) const { return x(r); }
+  __device__ __forceinline__ int sy(int r) const { return y(r); }
+  __device__ __forceinline__ const R *f(int c) const { return F[c]; }
+  __device__ __forceinline__ const R *j(int c) const { return J[c]; }
+  __device__ __forceinline__ R *l(int c) const { return L[c]; }
+};
+
+constexpr int kAdjTile = 16;                           // largest tile edge of the windowed kernel
+constexpr int kAdjDrift = 4;                           // cells a particle may have left its tile
+constexpr int kAdjGuard = kAdjDrift + 2;               // window nodes below the tile (deposit reaches 2 below)
+constexpr int kAdjWin = kAdjTile + 2 * kAdjGuard + 1;  // window nodes per axis (and 3 above)
+constexpr int kAdjWinN = kAdjWin * kAdjWin;
+constexpr int kAdjSub = 512;                           // slots of a work item one block takes
+
+template <class R> struct WindowNodes {
+  int wi, wj;  // the particle's cell in window coordinates
+  const R *s;  // [9][kAdjWinN]: E, B, lamJ
+  int i0, j0, n0, n1;
+  R *const *L;  // [6]
+  __device__ __forceinline__ int x(int r) const { return wi + r; }
+  __device__ __forceinline__ int y(int r) const { return (wj + r) * kAdjWin; }
+  __device__ __forceinline__ int sx(int r) const { return wrapi(i0 + r, n0); }
+  __device__ __forceinline__ int sy(int r) const { return wrapi(j0 + r, n1) * n0; }
+  __device__ __forceinline__ const R *f(int c) const { return s + c * kAdjWinN; }
+  __device__ __forceinline__ const R *j(int c) const { return s + (6 + c) * kAdjWinN; }
+  __device__ __forceinline__ R *l(int c) const { return L[c]; }
+};
+
+// Per-particle adjoint of gather -> Boris -> move -> Esirkepov (2D3V, TSC)
+// for the particle in slot p (live, id pid), its nodes found through nd.
+template <class R, class Nodes>
+__device__ __forceinline__ void adj_particle(const AdjPushArgs<R> &a, const Nodes &nd, int64_t p, uint32_t pid) {
+  {
     const R f[2] = {a.off[0][p], a.off[1][p]};
     const R u0[3] = {a.u[0][p], a.u[1][p], a.u[2][p]};
     const R wq = a.w[p];
@@ -313,14 +344,14 @@ __global__ void __launch_bounds__(256, sizeof(R) == 4 ? 3 : 2) k_adj_push2d(cons
       int ixp[3], ixd[3], iyp[3], iyd[3];
 #pragma unroll
       for (int k = 0; k < 3; ++k) {
-        ixp[k] = wrapi(i0 + gx.relp + k, n0);
-        ixd[k] = wrapi(i0 + gx.reld + k, n0);
-        iyp[k] = wrapi(j0 + gy.relp + k, n1) * n0;
-        iyd[k] = wrapi(j0 + gy.reld + k, n1) * n0;
+        ixp[k] = nd.x(gx.relp + k);
+        ixd[k] = nd.x(gx.reld + k);
+        iyp[k] = nd.y(gy.relp + k);
+        iyd[k] = nd.y(gy.reld + k);
       }
 #pragma unroll
       for (int cc = 0; cc < 6; ++cc) {
-        const R *G = cc < 3 ? a.E[cc] : a.B[cc - 3];
+        const R *G = nd.f(cc);
         const int *ix = dx_[cc] ? ixd : ixp;
         const int *iy = dy_[cc] ? iyd : iyp;
         const R *wx = dx_[cc] ? gx.wd : gx.wp;
@@ -367,82 +398,100 @@ __global__ void __launch_bounds__(256, sizeof(R) == 4 ? 3 : 2) k_adj_push2d(cons
     int jx[4], jy[4];
 #pragma unroll
     for (int k = 0; k < 4; ++k) {
-      jx[k] = wrapi(i0 + X.rel + k, n0);
-      jy[k] = wrapi(j0 + Y.rel + k, n1) * n0;
+      jx[k] = nd.x(X.rel + k);
+      jy[k] = nd.y(Y.rel + k);
     }
-    R Px[3], Py[3];
-    {
-      R sx = 0, sy = 0;
-#pragma unroll
-      for (int k = 0; k < 3; ++k) {
-        sx += X.S1[k] - X.S0[k];
-        sy += Y.S1[k] - Y.S0[k];
-        Px[k] = sx;
-        Py[k] = sy;
-      }
-    }
-    R Hx[4], Hy[4];
-#pragma unroll
-    for (int k = 0; k < 4; ++k) {
-      Hx[k] = R(0.5) * (X.S0[k] + X.S1[k]);
-      Hy[k] = R(0.5) * (Y.S0[k] + Y.S1[k]);
-    }
-    // Jx: Gx[a] = sum_b Ax[a][b] Hy[b], Ky[b] = sum_a Ax[a][b] Px[a]
-    R Gx[3] = {0, 0, 0}, Ky[4] = {0, 0, 0, 0};
-    R Gy[3] = {0, 0, 0}, Kx[4] = {0, 0, 0, 0};
-    R Zx0[4] = {0, 0, 0, 0}, Zx1[4] = {0, 0, 0, 0}, Zy0[4] = {0, 0, 0, 0}, Zy1[4] = {0, 0, 0, 0};
-#pragma unroll
-    for (int b = 0; b < 4; ++b)
-#pragma unroll
-      for (int aa = 0; aa < 4; ++aa) {
-        const int64_t node = jx[aa] + jy[b];
-        if (aa < 3) {
-          const R Ax = a.lJ[0][node];
-          Gx[aa] += Ax * Hy[b];
-          Ky[b] += Ax * Px[aa];
-        }
-        if (b < 3) {
-          const R Ay = a.lJ[1][node];
-          Gy[b] += Ay * Hx[aa];
-          Kx[aa] += Ay * Py[b];
-        }
-        const R Az = a.lJ[2][node];
-        Zx0[aa] += Az * Y.S0[b];
-        Zx1[aa] += Az * Y.S1[b];
-        Zy0[b] += Az * X.S0[aa];
-        Zy1[b] += Az * X.S1[aa];
-      }
     const R cx = a.cxu[0] * wq, cy = a.cxu[1] * wq, qw = a.q * wq;
-    // suffix sums R[k] = sum_{a>=k, a<3} G[a]
-    R Rx[4], Ry[4];
-    Rx[3] = 0;
-    Ry[3] = 0;
-#pragma unroll
-    for (int k = 2; k >= 0; --k) {
-      Rx[k] = Rx[k + 1] + Gx[k];
-      Ry[k] = Ry[k + 1] + Gy[k];
-    }
-    R Tz = 0;
     R dS0x[4], dS1x[4], dS0y[4], dS1y[4];  // dL/dS
-#pragma unroll
-    for (int k = 0; k < 4; ++k) {
-      Tz += (X.S0[k] * Zx0[k] + X.S1[k] * Zx1[k]) * R(1.0 / 3.0) + (X.S0[k] * Zx1[k] + X.S1[k] * Zx0[k]) * R(1.0 / 6.0);
-      dS1x[k] = cx * Rx[k] + R(0.5) * cy * Kx[k] + qw * vz * (Zx1[k] * R(1.0 / 3.0) + Zx0[k] * R(1.0 / 6.0));
-      dS0x[k] = -cx * Rx[k] + R(0.5) * cy * Kx[k] + qw * vz * (Zx0[k] * R(1.0 / 3.0) + Zx1[k] * R(1.0 / 6.0));
-      dS1y[k] = cy * Ry[k] + R(0.5) * cx * Ky[k] + qw * vz * (Zy1[k] * R(1.0 / 3.0) + Zy0[k] * R(1.0 / 6.0));
-      dS0y[k] = -cy * Ry[k] + R(0.5) * cx * Ky[k] + qw * vz * (Zy0[k] * R(1.0 / 3.0) + Zy1[k] * R(1.0 / 6.0));
-    }
-    // dL/dw (contributions are linear in w)
-    double dLw = 0.0;
+    double dLw;                            // dL/dw (contributions are linear in w)
+    // pass 1, Jx and Jy: Gx[a] = sum_b lamJx[a][b] Hy[b], Ky[b] = sum_a
+    // lamJx[a][b] Px[a] (Px the prefix sums of S1 - S0, H the means of S0
+    // and S1), and the same with x and y exchanged for Jy
     {
+      R Px[3], Py[3];
+      {
+        R sx = 0, sy = 0;
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+          sx += X.S1[k] - X.S0[k];
+          sy += Y.S1[k] - Y.S0[k];
+          Px[k] = sx;
+          Py[k] = sy;
+        }
+      }
+      R Hx[4], Hy[4];
+#pragma unroll
+      for (int k = 0; k < 4; ++k) {
+        Hx[k] = R(0.5) * (X.S0[k] + X.S1[k]);
+        Hy[k] = R(0.5) * (Y.S0[k] + Y.S1[k]);
+      }
+      R Gx[3] = {0, 0, 0}, Ky[4] = {0, 0, 0, 0};
+      R Gy[3] = {0, 0, 0}, Kx[4] = {0, 0, 0, 0};
+#pragma unroll
+      for (int b = 0; b < 4; ++b)
+#pragma unroll
+        for (int aa = 0; aa < 4; ++aa) {
+          const int node = jx[aa] + jy[b];
+          if (aa < 3) {
+            const R Ax = nd.j(0)[node];
+            Gx[aa] += Ax * Hy[b];
+            Ky[b] += Ax * Px[aa];
+          }
+          if (b < 3) {
+            const R Ay = nd.j(1)[node];
+            Gy[b] += Ay * Hx[aa];
+            Kx[aa] += Ay * Py[b];
+          }
+        }
+      // suffix sums R[k] = sum_{a>=k, a<3} G[a]
+      R Rx[4], Ry[4];
+      Rx[3] = 0;
+      Ry[3] = 0;
+#pragma unroll
+      for (int k = 2; k >= 0; --k) {
+        Rx[k] = Rx[k + 1] + Gx[k];
+        Ry[k] = Ry[k + 1] + Gy[k];
+      }
+#pragma unroll
+      for (int k = 0; k < 4; ++k) {
+        dS1x[k] = cx * Rx[k] + R(0.5) * cy * Kx[k];
+        dS0x[k] = -cx * Rx[k] + R(0.5) * cy * Kx[k];
+        dS1y[k] = cy * Ry[k] + R(0.5) * cx * Ky[k];
+        dS0y[k] = -cy * Ry[k] + R(0.5) * cx * Ky[k];
+      }
       R gxp = 0, gyp = 0;
 #pragma unroll
       for (int k = 0; k < 3; ++k) {
         gxp += Gx[k] * Px[k];
         gyp += Gy[k] * Py[k];
       }
-      dLw = (double)(a.cxu[0] * gxp + a.cxu[1] * gyp + a.q * vz * Tz);
+      dLw = (double)(a.cxu[0] * gxp + a.cxu[1] * gyp);
     }
+    // pass 2, Jz: Zx0[a] = sum_b lamJz[a][b] SY0[b] (and with S1), Zy the
+    // same over a
+    R Tz = 0;
+    {
+      R Zx0[4] = {0, 0, 0, 0}, Zx1[4] = {0, 0, 0, 0}, Zy0[4] = {0, 0, 0, 0}, Zy1[4] = {0, 0, 0, 0};
+#pragma unroll
+      for (int b = 0; b < 4; ++b)
+#pragma unroll
+        for (int aa = 0; aa < 4; ++aa) {
+          const R Az = nd.j(2)[jx[aa] + jy[b]];
+          Zx0[aa] += Az * Y.S0[b];
+          Zx1[aa] += Az * Y.S1[b];
+          Zy0[b] += Az * X.S0[aa];
+          Zy1[b] += Az * X.S1[aa];
+        }
+#pragma unroll
+      for (int k = 0; k < 4; ++k) {
+        Tz += (X.S0[k] * Zx0[k] + X.S1[k] * Zx1[k]) * R(1.0 / 3.0) + (X.S0[k] * Zx1[k] + X.S1[k] * Zx0[k]) * R(1.0 / 6.0);
+        dS1x[k] += qw * vz * (Zx1[k] * R(1.0 / 3.0) + Zx0[k] * R(1.0 / 6.0));
+        dS0x[k] += qw * vz * (Zx0[k] * R(1.0 / 3.0) + Zx1[k] * R(1.0 / 6.0));
+        dS1y[k] += qw * vz * (Zy1[k] * R(1.0 / 3.0) + Zy0[k] * R(1.0 / 6.0));
+        dS0y[k] += qw * vz * (Zy0[k] * R(1.0 / 3.0) + Zy1[k] * R(1.0 / 6.0));
+      }
+    }
+    dLw += (double)(a.q * vz * Tz);
     const R lvz = qw * Tz;  // dL/dvz
     R lf_old[2] = {0, 0}, lf_new[2] = {0, 0};
     {
@@ -539,18 +588,19 @@ __global__ void __launch_bounds__(256, sizeof(R) == 4 ? 3 : 2) k_adj_push2d(cons
       int ixp[3], ixd[3], iyp[3], iyd[3];
 #pragma unroll
       for (int k = 0; k < 3; ++k) {
-        ixp[k] = wrapi(i0 + gx.relp + k, n0);
-        ixd[k] = wrapi(i0 + gx.reld + k, n0);
-        iyp[k] = wrapi(j0 + gy.relp + k, n1) * n0;
-        iyd[k] = wrapi(j0 + gy.reld + k, n1) * n0;
+        ixp[k] = nd.x(gx.relp + k);
+        ixd[k] = nd.x(gx.reld + k);
+        iyp[k] = nd.y(gy.relp + k);
+        iyd[k] = nd.y(gy.reld + k);
       }
 #pragma unroll
       for (int cc = 0; cc < 6; ++cc) {
         if (lF[cc] == R(0)) continue;
-        const R *G = cc < 3 ? a.E[cc] : a.B[cc - 3];
-        R *LG = cc < 3 ? a.lE[cc] : a.lB[cc - 3];
+        const R *G = nd.f(cc);
+        R *LG = nd.l(cc);
         const int *ix = dx_[cc] ? ixd : ixp;
         const int *iy = dy_[cc] ? iyd : iyp;
+        const int rx = dx_[cc] ? gx.reld : gx.relp, ry = dy_[cc] ? gy.reld : gy.relp;
         const R *wx = dx_[cc] ? gx.wd : gx.wp, *dwx = dx_[cc] ? gx.dwd : gx.dwp;
         const R *wy = dy_[cc] ? gy.wd : gy.wp, *dwy = dy_[cc] ? gy.dwd : gy.dwp;
         R sx = 0, sy = 0;
@@ -558,11 +608,10 @@ __global__ void __launch_bounds__(256, sizeof(R) == 4 ? 3 : 2) k_adj_push2d(cons
         for (int b = 0; b < 3; ++b)
 #pragma unroll
           for (int aa = 0; aa < 3; ++aa) {
-            const int node = ix[aa] + iy[b];
-            const R v = G[node];
+            const R v = G[ix[aa] + iy[b]];
             sx += v * dwx[aa] * wy[b];
             sy += v * wx[aa] * dwy[b];
-            atomicAdd(LG + node, lF[cc] * wx[aa] * wy[b]);
+            atomicAdd(LG + nd.sx(rx + aa) + nd.sy(ry + b), lF[cc] * wx[aa] * wy[b]);
           }
         lX[0] += lF[cc] * sx;
         lX[1] += lF[cc] * sy;
@@ -575,6 +624,138 @@ __global__ void __launch_bounds__(256, sizeof(R) == 4 ? 3 : 2) k_adj_push2d(cons
 #pragma unroll
     for (int d = 0; d < 3; ++d) a.lu[d][pid] = lu0[d];
     a.lw[pid] += dLw;
+  }
+}
+
+// The particle adjoint over all slots, nodes in global memory (particles
+// not in tile order).  The kernel is latency-bound (scattered field and
+// adjoint reads), so the register cap (3 blocks of 256 per SM for FP32, 2
+// for FP64) trades spills for occupancy.
+template <class R>
+__global__ void __launch_bounds__(256, sizeof(R) == 4 ? 3 : 2) k_adj_push2d(const AdjPushArgs<R> a) {
+  const int n0 = a.n[0], n1 = a.n[1];
+  const int64_t n = *a.d_count;
+  const R *F[6] = {a.E[0], a.E[1], a.E[2], a.B[0], a.B[1], a.B[2]};
+  R *L[6] = {a.lE[0], a.lE[1], a.lE[2], a.lB[0], a.lB[1], a.lB[2]};
+  for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < n; p += (int64_t)gridDim.x * blockDim.x) {
+    const int c = a.cell[p];
+    if (c < 0) continue;
+    const uint32_t pid = a.id[p];
+    if ((int64_t)pid >= a.id_cap) {
+      atomicOr(a.err, 1ull);  // id outside the adjoint arrays: skipped, reported
+      continue;
+    }
+    const GridNodes<R> nd{c % n0, c / n0, n0, n1, F, a.lJ, L};
+    adj_particle<R>(a, nd, p, pid);
+  }
+}
+
+// Work items of a recorded particle buffer (the sort in effect when it was
+// recorded): item i covers slots [work_pb[i], min(work_pb[i] + chunk,
+// tile_start[t + 1])) of tile t = work_tile[i] (-1: none); nsub blocks share
+// an item, kAdjSub slots each.
+struct AdjWork {
+  const int32_t *work_tile;
+  const int64_t *work_pb;
+  const int64_t *tile_start;
+  int64_t chunk;
+  int nsub;
+  int nt0, t0, t1;
+  unsigned long long *esc_total;  // running count of particles on the global path
+};
+
+// The particle adjoint over kAdjSub slots of one work item, one block: E, B
+// and lamJ of the item's tile window are staged in shared memory (lamE and
+// lamB are scattered to global memory).  A particle more than kAdjDrift
+// cells outside its tile since the sort is set aside and done at the end of
+// the block with all its nodes in global memory.
+template <class R>
+__global__ void __launch_bounds__(256, sizeof(R) == 4 ? 3 : 2)
+    k_adj_push2d_win(const AdjPushArgs<R> a, const AdjWork w) {
+  extern __shared__ __align__(16) unsigned char adj_smem[];
+  R *s = reinterpret_cast<R *>(adj_smem);
+  __shared__ int s_esc[kAdjSub];
+  __shared__ int s_nesc;
+  const int item = blockIdx.x / w.nsub;
+  const int t = w.work_tile[item];
+  if (t < 0) return;
+  const int64_t te = w.tile_start[t + 1];
+  const int64_t ib = w.work_pb[item];
+  const int64_t ie = ib + w.chunk < te ? ib + w.chunk : te;
+  const int64_t pb = ib + (int64_t)(blockIdx.x % w.nsub) * kAdjSub;
+  if (pb >= ie) return;
+  const int64_t pe = pb + kAdjSub < ie ? pb + kAdjSub : ie;
+  const int n0 = a.n[0], n1 = a.n[1];
+  const int tx = (t % w.nt0) * w.t0, ty = (t / w.nt0) * w.t1;  // the tile's first cell
+  const int ox = tx - kAdjGuard, oy = ty - kAdjGuard;          // the window's first node
+  const R *src[9] = {a.E[0], a.E[1], a.E[2], a.B[0], a.B[1], a.B[2], a.lJ[0], a.lJ[1], a.lJ[2]};
+  R *L[6] = {a.lE[0], a.lE[1], a.lE[2], a.lB[0], a.lB[1], a.lB[2]};
+  if (threadIdx.x == 0) s_nesc = 0;
+  for (int k = threadIdx.x; k < kAdjWinN; k += blockDim.x) {
+    const int g = wrapi(ox + k % kAdjWin, n0) + wrapi(oy + k / kAdjWin, n1) * n0;
+#pragma unroll
+    for (int c = 0; c < 9; ++c) s[c * kAdjWinN + k] = src[c][g];
+  }
+  __syncthreads();
+  for (int64_t p = pb + threadIdx.x; p < pe; p += blockDim.x) {
+    const int c = a.cell[p];
+    if (c < 0) continue;
+    const uint32_t pid = a.id[p];
+    if ((int64_t)pid >= a.id_cap) {
+      atomicOr(a.err, 1ull);  // id outside the adjoint arrays: skipped, reported
+      continue;
+    }
+    // the cell relative to the tile, across the periodic seam if need be
+    int il = c % n0 - tx, jl = c / n0 - ty;
+    if (il >= w.t0 + kAdjDrift) il -= n0;
+    else if (il < -kAdjDrift) il += n0;
+    if (jl >= w.t1 + kAdjDrift) jl -= n1;
+    else if (jl < -kAdjDrift) jl += n1;
+    if (il < -kAdjDrift || il >= w.t0 + kAdjDrift || jl < -kAdjDrift || jl >= w.t1 + kAdjDrift) {
+      s_esc[atomicAdd(&s_nesc, 1)] = (int)(p - pb);
+      continue;
+    }
+    const WindowNodes<R> nd{il + kAdjGuard, jl + kAdjGuard, s, c % n0, c / n0, n0, n1, L};
+    adj_particle<R>(a, nd, p, pid);
+  }
+  __syncthreads();
+  // the particles set aside, nodes in global memory
+  const int nesc = s_nesc;
+  if (threadIdx.x == 0 && nesc > 0) atomicAdd(w.esc_total, (unsigned long long)nesc);
+  const R *F[6] = {a.E[0], a.E[1], a.E[2], a.B[0], a.B[1], a.B[2]};
+  for (int k = threadIdx.x; k < nesc; k += blockDim.x) {
+    const int64_t p = pb + s_esc[k];
+    const int c = a.cell[p];
+    const GridNodes<R> nd{c % n0, c / n0, n0, n1, F, a.lJ, L};
+    adj_particle<R>(a, nd, p, a.id[p]);
+  }
+}
+
+// out[b] += sum of w[i] over the i < n with bin[i] == b (0 <= b < nbins):
+// the lanes of a warp that share a bin are summed in lane order by their
+// lowest lane, which adds the sum to out[b].
+__global__ void k_sum_by_bin(const double *__restrict__ w, const int32_t *__restrict__ bin, int64_t n, int nbins,
+                             double *__restrict__ out) {
+  const int lane = threadIdx.x & 31;
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  // warp-uniform trip count: every lane takes part in the warp operations
+  for (int64_t base = (int64_t)blockIdx.x * blockDim.x + (threadIdx.x & ~31); base < n; base += stride) {
+    const int64_t i = base + lane;
+    int b = -1;
+    double v = 0.0;
+    if (i < n) {
+      b = bin[i];
+      v = w[i];
+    }
+    if (b < 0 || b >= nbins) b = -1;
+    const unsigned peers = __match_any_sync(0xffffffffu, b);
+    double sum = 0.0;
+#pragma unroll 4
+    for (int l = 0; l < 32; ++l) {
+      const double t = __shfl_sync(0xffffffffu, v, l);
+      if ((peers >> l) & 1u) sum += t;
+    }
+    if (b >= 0 && lane == __ffs(peers) - 1) atomicAdd(out + b, sum);
   }
 }
 
@@ -683,10 +864,10 @@ cudaError_t launch_adj_mur(const Grid &g, void *const lE[3], double *pend, const
 
 template <class R>
 static cudaError_t adj_push_t(const Grid &g, const Particles &tp, const int64_t *d_count, int64_t nmax,
-                              void *const E[3], void *const B[3],
-                              void *const lJ[3], void *const lE[3], void *const lB[3], void *const lx[3],
-                              void *const lu[3], double *lw, int64_t id_cap, unsigned long long *err, double q,
-                              double m, cudaStream_t st) {
+                              void *const E[3], void *const B[3], void *const lJ[3], void *const lE[3],
+                              void *const lB[3], void *const lx[3], void *const lu[3], double *lw, int64_t id_cap,
+                              unsigned long long *err, double q, double m, const AdjTiles *tt, cudaStream_t st,
+                              int *nlaunch) {
   AdjPushArgs<R> a;
   for (int d = 0; d < 3; ++d) {
     a.n[d] = g.n[d];
@@ -712,19 +893,54 @@ static cudaError_t adj_push_t(const Grid &g, const Particles &tp, const int64_t 
   a.err = err;
   a.qmh = (R)(q * g.dt / (2.0 * m));
   a.q = (R)q;
-  k_adj_push2d<R><<<nblocks(nmax), 256, 0, st>>>(a);
+  const bool win = tt && tt->work_tile && tt->nwork > 0 && g.tile[0] <= kAdjTile && g.tile[1] <= kAdjTile;
+  if (!win) {
+    k_adj_push2d<R><<<nblocks(nmax), 256, 0, st>>>(a);
+    if (nlaunch) *nlaunch = 1;
+    return cudaGetLastError();
+  }
+  const size_t smem = (size_t)9 * kAdjWinN * sizeof(R);
+  static bool attr_set = false;  // per R: one instantiation per element type
+  if (!attr_set) {
+    cudaError_t e = cudaFuncSetAttribute(k_adj_push2d_win<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    attr_set = true;
+  }
+  AdjWork w;
+  w.work_tile = tt->work_tile;
+  w.work_pb = tt->work_pb;
+  w.tile_start = tt->tile_start;
+  w.chunk = tt->chunk;
+  w.nsub = (int)((tt->chunk + kAdjSub - 1) / kAdjSub);
+  w.nt0 = g.ntile[0];
+  w.t0 = g.tile[0];
+  w.t1 = g.tile[1];
+  w.esc_total = tt->esc_total;
+  const int64_t nblk = tt->nwork * w.nsub;
+  if (nblk > 0x7fffffffLL) return cudaErrorInvalidValue;
+  k_adj_push2d_win<R><<<(unsigned)nblk, 256, smem, st>>>(a, w);
+  if (nlaunch) *nlaunch = 1;
   return cudaGetLastError();
 }
 
 cudaError_t launch_adj_push(const Grid &g, const Particles &tp, const int64_t *d_count, int64_t nmax,
                             void *const E[3], void *const B[3], void *const lJ[3], void *const lE[3],
                             void *const lB[3], void *const lx[3], void *const lu[3], double *lw, int64_t id_cap,
-                            unsigned long long *err, double q, double m, cudaStream_t st) {
+                            unsigned long long *err, double q, double m, const AdjTiles *tt, cudaStream_t st,
+                            int *nlaunch) {
+  if (nlaunch) *nlaunch = 0;
   if (g.dims != 2 || g.order != 2) return cudaErrorInvalidValue;
   if (nmax <= 0) return cudaSuccess;
   if (g.prec == 1)
-    return adj_push_t<double>(g, tp, d_count, nmax, E, B, lJ, lE, lB, lx, lu, lw, id_cap, err, q, m, st);
-  return adj_push_t<float>(g, tp, d_count, nmax, E, B, lJ, lE, lB, lx, lu, lw, id_cap, err, q, m, st);
+    return adj_push_t<double>(g, tp, d_count, nmax, E, B, lJ, lE, lB, lx, lu, lw, id_cap, err, q, m, tt, st, nlaunch);
+  return adj_push_t<float>(g, tp, d_count, nmax, E, B, lJ, lE, lB, lx, lu, lw, id_cap, err, q, m, tt, st, nlaunch);
+}
+
+cudaError_t launch_sum_by_bin(const double *w, const int32_t *bin, int64_t n, int nbins, double *out,
+                              cudaStream_t st) {
+  if (n <= 0) return cudaSuccess;
+  k_sum_by_bin<<<nblocks(n), 256, 0, st>>>(w, bin, n, nbins, out);
+  return cudaGetLastError();
 }
 
 cudaError_t launch_adj_seed(const Grid &g, const Particles &p, const int64_t *d_count, int64_t nmax, int c_lo,

@@ -45,6 +45,7 @@ struct Species {
   bool fresh = true;            // sorted since the last push
   bool need_sort = true;
   int64_t sorted_at = -1;  // step count at the last sort
+  int64_t sorts = 0;       // sorts so far (names the slot order in effect)
 };
 
 struct TimerRec {
@@ -56,6 +57,16 @@ struct TimerRec {
 struct PCopy {
   Particles p{};
   int64_t *count = nullptr;
+  // Tape entries: the work items of the sort in effect (tiled = false when
+  // the species was unsorted at the copy).  meta is this copy's own buffer;
+  // work_pb, tile_start, work_tile point to it or, when the previous tape
+  // entry was recorded under the same sort, to that entry's arrays.
+  void *meta = nullptr;
+  const int32_t *work_tile = nullptr;
+  const int64_t *work_pb = nullptr;
+  const int64_t *tile_start = nullptr;
+  int64_t nwork = 0, chunk = 0, sorts = -1;
+  bool tiled = false;
 };
 
 // Full simulation state at a step boundary (checkpoint) or at the start of a
@@ -110,6 +121,7 @@ struct pic_handle {
   int64_t step = 0;
   int64_t launches = 0;
   int64_t adaptive_sorts = 0;  // sorts triggered by escapes rather than by the cadence
+  int64_t mid_drain_pushes = 0;  // species pushes launched with the between-chunk drain variant
   std::string err;
   bool profiling = false;
   std::vector<TimerRec> timers;
@@ -125,6 +137,7 @@ struct pic_handle {
   double *pend = nullptr, *da0 = nullptr, *objF = nullptr;
   double *adj_stage = nullptr;  // FP64 staging of id-indexed adjoint arrays (id_cap doubles)
   unsigned long long *adj_err = nullptr;
+  unsigned long long *adj_esc = nullptr;  // particle adjoints on the global-memory path since pic_adjoint_begin
   SpeciesAdjoint adj[kMaxSpecies];
   // output manager
   std::vector<OutputReq> outputs;
@@ -161,8 +174,8 @@ cudaEvent_t take_event(pic_handle *h) {
 
 // NVTX range names of the kernel classes (seen by a timeline profiler; the
 // calls cost nothing when none is attached).
-const char *const kClassNames[pic::KC_N] = {"sort",     "zero_j", "push",      "yee_b",   "yee_e",
-                                            "boundary", "filter", "adj_field", "adj_push"};
+const char *const kClassNames[pic::KC_N] = {"sort",   "zero_j",    "push",     "yee_b", "yee_e",
+                                            "boundary", "filter", "adj_field", "adj_push", "tape"};
 
 // Scope of one kernel class within a step: an NVTX range, and CUDA events
 // on the simulation stream while profiling is on (pic_profile).
@@ -195,6 +208,19 @@ size_t align256(size_t b) { return (b + 255) / 256 * 256; }
 size_t particles_bytes(int64_t cap, size_t rs, int dims) {
   const size_t n = (size_t)(cap > 0 ? cap : 1);
   return align256(n * sizeof(int32_t)) + (size_t)(dims + 4) * align256(n * rs) + align256(n * sizeof(uint32_t));
+}
+
+// A sort's outputs in one allocation: work_pb[nwork], tile_start[ntiles + 1],
+// work_tile[nwork].
+size_t sort_meta_bytes(int64_t nwork, int64_t ntiles) {
+  return sizeof(int64_t) * (size_t)(nwork + ntiles + 1) + sizeof(int32_t) * (size_t)nwork;
+}
+
+void set_sort_meta(void *base, int64_t nwork, int64_t ntiles, int64_t *&work_pb, int64_t *&tile_start,
+                   int32_t *&work_tile) {
+  work_pb = static_cast<int64_t *>(base);
+  tile_start = work_pb + nwork;
+  work_tile = reinterpret_cast<int32_t *>(tile_start + ntiles + 1);
 }
 
 void free_particles(Particles &p) {
@@ -247,6 +273,7 @@ int sort_species(pic_handle *h, Species &s) {
   s.cur = 1 - s.cur;
   s.need_sort = false;
   s.sorted_at = h->step;
+  s.sorts++;
   s.fresh = true;
   return PIC_OK;
 }
@@ -286,8 +313,10 @@ cudaError_t alloc_snapshot(pic_handle *h, Snapshot &sn) {
       sn.B[d] = static_cast<char *>(sn.E[0]) + (3 + d) * fb;
     }
   for (int i = 0; i < h->nsp && e == cudaSuccess; ++i) {
-    e = alloc_particles(sn.sp[i].p, h->sp[i].slots, h->rsize, h->g.dims);
-    if (e == cudaSuccess) e = cudaMalloc(&sn.sp[i].count, sizeof(int64_t));
+    PCopy &c = sn.sp[i];
+    e = alloc_particles(c.p, h->sp[i].slots, h->rsize, h->g.dims);
+    if (e == cudaSuccess) e = cudaMalloc(&c.count, sizeof(int64_t));
+    if (e == cudaSuccess) e = cudaMalloc(&c.meta, sort_meta_bytes(h->sp[i].work.nwork, h->g.ntiles));
   }
   sn.allocated = e == cudaSuccess;
   sn.nsp = h->nsp;
@@ -299,6 +328,7 @@ void free_snapshot(Snapshot &sn) {
   for (int i = 0; i < kMaxSpecies; ++i) {
     free_particles(sn.sp[i].p);
     cudaFree(sn.sp[i].count);
+    cudaFree(sn.sp[i].meta);
   }
   sn = Snapshot{};
 }
@@ -312,14 +342,38 @@ cudaError_t copy_particles(pic_handle *h, const Particles &dst, int64_t *dcount,
   return e;
 }
 
-// Copy the live state (current particle buffers, E, B, step) into sn.
-cudaError_t save_snapshot(pic_handle *h, Snapshot &sn) {
+// Copy the live state (current particle buffers, E, B, step) into sn.  A
+// tape entry (prev: the entry recorded before it, or null) also keeps the
+// work items of the sort in effect, copied unless prev already holds them.
+cudaError_t save_snapshot(pic_handle *h, Snapshot &sn, bool tape = false, const Snapshot *prev = nullptr) {
   cudaError_t e = alloc_snapshot(h, sn);
   const size_t fb = (size_t)h->g.ncell * h->rsize;
   if (e == cudaSuccess) e = cudaMemcpyAsync(sn.E[0], h->E[0], 6 * fb, cudaMemcpyDeviceToDevice, h->st);
   for (int i = 0; i < h->nsp && e == cudaSuccess; ++i) {
     Species &s = h->sp[i];
-    e = copy_particles(h, sn.sp[i].p, sn.sp[i].count, s.buf[s.cur], s.d_count, s.slots);
+    PCopy &c = sn.sp[i];
+    e = copy_particles(h, c.p, c.count, s.buf[s.cur], s.d_count, s.slots);
+    // the slot order is that of the last sort unless a sort is pending
+    c.tiled = tape && !s.need_sort && s.work.nwork > 0;
+    c.nwork = s.work.nwork;
+    c.chunk = s.work.chunk;
+    c.sorts = s.sorts;
+    if (!c.tiled || e != cudaSuccess) continue;
+    const PCopy *q = prev ? &prev->sp[i] : nullptr;
+    if (q && q->tiled && q->sorts == s.sorts) {
+      c.work_pb = q->work_pb;
+      c.tile_start = q->tile_start;
+      c.work_tile = q->work_tile;
+    } else {
+      e = cudaMemcpyAsync(c.meta, s.work.work_pb, sort_meta_bytes(s.work.nwork, h->g.ntiles), cudaMemcpyDeviceToDevice,
+                          h->st);
+      int64_t *pb = nullptr, *ts = nullptr;
+      int32_t *wt = nullptr;
+      set_sort_meta(c.meta, s.work.nwork, h->g.ntiles, pb, ts, wt);
+      c.work_pb = pb;
+      c.tile_start = ts;
+      c.work_tile = wt;
+    }
   }
   sn.step = h->step;
   return e;
@@ -337,8 +391,10 @@ void free_adjoint(pic_handle *h) {
   cudaFree(h->objF);
   cudaFree(h->adj_err);
   cudaFree(h->adj_stage);
+  cudaFree(h->adj_esc);
   h->pend = h->da0 = h->objF = h->adj_stage = nullptr;
   h->adj_err = nullptr;
+  h->adj_esc = nullptr;
   for (int i = 0; i < kMaxSpecies; ++i) {
     for (int d = 0; d < 3; ++d) {
       cudaFree(h->adj[i].lx[d]);
@@ -536,10 +592,8 @@ int pic_destroy(pic_handle *h) {
     free_particles(s.buf[1]);
     cudaFree(s.d_count);
     cudaFree(s.rank);
-    cudaFree(s.tile_start);
+    cudaFree(s.work.work_pb);  // with tile_start and work_tile
     cudaFree(s.tq);
-    cudaFree(s.work.work_tile);
-    cudaFree(s.work.work_pb);
     cudaFreeHost(s.esc_host);
     if (s.esc_ev) cudaEventDestroy(s.esc_ev);
   }
@@ -576,7 +630,6 @@ int pic_add_species(pic_handle *h, double q, double m, int64_t capacity, int *sp
   if (e == cudaSuccess) e = alloc_particles(s.buf[1], s.slots, h->rsize, h->g.dims);
   if (e == cudaSuccess) e = cudaMalloc(&s.d_count, sizeof(int64_t));
   if (e == cudaSuccess) e = cudaMalloc(&s.rank, (size_t)(s.slots > 0 ? s.slots : 1) * sizeof(int32_t));
-  if (e == cudaSuccess) e = cudaMalloc(&s.tile_start, (size_t)(h->g.ntiles + 1) * sizeof(int64_t));
   // Work items: pieces of at most `chunk` slots per tile, chunk sized so that
   // a species spread over few tiles (a thin slab, a small grid) still gives
   // about 16 blocks per SM, never below 512 slots and never above the
@@ -594,17 +647,20 @@ int pic_add_species(pic_handle *h, double q, double m, int64_t capacity, int *sp
   if (e == cudaSuccess) e = cudaMalloc(&s.tq, (size_t)2 * s.work.nwork * sizeof(float));
   if (e == cudaSuccess) e = cudaMallocHost(&s.esc_host, 2 * sizeof(unsigned long long));
   if (e == cudaSuccess) e = cudaEventCreateWithFlags(&s.esc_ev, cudaEventDisableTiming);
-  if (e == cudaSuccess) e = cudaMalloc(&s.work.work_tile, (size_t)s.work.nwork * sizeof(int32_t));
-  if (e == cudaSuccess) e = cudaMalloc(&s.work.work_pb, (size_t)s.work.nwork * sizeof(int64_t));
+  // the sort's outputs in one allocation (one copy for a tape entry):
+  // work_pb[nwork], tile_start[ntiles + 1], work_tile[nwork]
+  if (e == cudaSuccess) {
+    void *meta = nullptr;
+    e = cudaMalloc(&meta, sort_meta_bytes(s.work.nwork, h->g.ntiles));
+    if (e == cudaSuccess) set_sort_meta(meta, s.work.nwork, h->g.ntiles, s.work.work_pb, s.tile_start, s.work.work_tile);
+  }
   if (e != cudaSuccess) {
     free_particles(s.buf[0]);
     free_particles(s.buf[1]);
     cudaFree(s.d_count);
     cudaFree(s.rank);
-    cudaFree(s.tile_start);
+    cudaFree(s.work.work_pb);  // with tile_start and work_tile
     cudaFree(s.tq);
-    cudaFree(s.work.work_tile);
-    cudaFree(s.work.work_pb);
     cudaFreeHost(s.esc_host);
     if (s.esc_ev) cudaEventDestroy(s.esc_ev);
     s = Species{};
@@ -1098,7 +1154,9 @@ int pic_step(pic_handle *h, int nsteps) {
     }
     if (h->taping) {
       if (h->tape_len < (int)h->tape.size()) {
-        CK(h, save_snapshot(h, h->tape[h->tape_len]), "tape record");
+        Timed tm(h, pic::KC_TAPE);
+        CK(h, save_snapshot(h, h->tape[h->tape_len], true, h->tape_len > 0 ? &h->tape[h->tape_len - 1] : nullptr),
+           "tape record");
         h->tape_len++;
       }
       if (h->tape_len >= (int)h->tape.size()) h->taping = false;
@@ -1117,6 +1175,7 @@ int pic_step(pic_handle *h, int nsteps) {
          "push");
       s.fresh = false;
       h->launches += nl;
+      if (s.mid_drain) h->mid_drain_pushes++;
       if (s.esc_host && !s.esc_pending) {
         CK(h, cudaMemcpyAsync(s.esc_host, h->esc_count, 2 * sizeof(unsigned long long), cudaMemcpyDeviceToHost,
                               h->st),
@@ -1279,6 +1338,8 @@ int pic_diag(pic_handle *h, pic_diag_t *out) {
   Counters c;
   CK(h, cudaMemcpyAsync(red, h->red, sizeof red, cudaMemcpyDeviceToHost, h->st), "D2H");
   CK(h, cudaMemcpyAsync(&c, h->ctr, sizeof c, cudaMemcpyDeviceToHost, h->st), "D2H");
+  unsigned long long adj_esc = 0;
+  if (h->adj_esc) CK(h, cudaMemcpyAsync(&adj_esc, h->adj_esc, sizeof adj_esc, cudaMemcpyDeviceToHost, h->st), "D2H");
   CK(h, cudaMemcpyAsync(h->rho_prev, h->rho, sizeof(double) * h->g.ncell, cudaMemcpyDeviceToDevice, h->st), "copy");
   CK(h, cudaStreamSynchronize(h->st), "diag sync");
   h->rho_prev_step = h->step;
@@ -1295,6 +1356,8 @@ int pic_diag(pic_handle *h, pic_diag_t *out) {
   out->n_clamped = (int64_t)c.clamped;
   out->n_absorbed = (int64_t)c.absorbed;
   out->n_sorts_adaptive = h->adaptive_sorts;
+  out->n_push_mid_drain = h->mid_drain_pushes;
+  out->n_adj_escaped = (int64_t)adj_esc;
   out->step = h->step;
   if (c.error & pic::kErrBounds) return fail(h, PIC_EOVERFLOW, "an index outside its buffer was caught (checked build)");
   if (c.error) return fail(h, PIC_EOVERFLOW, "device-side error flags set");
@@ -1365,6 +1428,7 @@ int pic_timings(pic_handle *h, double *ms, int64_t *launches, int nmax, int *ncl
 int pic_checkpoint(pic_handle *h, int slot) {
   if (!h || slot < 0 || slot > 4096) return fail(h, PIC_EINVAL, "bad checkpoint slot");
   if ((int)h->ckpt.size() <= slot) h->ckpt.resize(slot + 1);
+  Timed tm(h, pic::KC_TAPE);
   cudaError_t e = save_snapshot(h, h->ckpt[slot]);
   if (e != cudaSuccess) {
     cudaGetLastError();
@@ -1379,6 +1443,7 @@ int pic_restore(pic_handle *h, int slot) {
     return fail(h, PIC_EINVAL, "no such checkpoint");
   Snapshot &sn = h->ckpt[slot];
   const size_t fb = (size_t)h->g.ncell * h->rsize;
+  Timed tm(h, pic::KC_TAPE);
   CK(h, cudaMemcpyAsync(h->E[0], sn.E[0], 6 * fb, cudaMemcpyDeviceToDevice, h->st), "restore");
   for (int i = 0; i < h->nsp; ++i) {
     Species &s = h->sp[i];
@@ -1412,7 +1477,11 @@ int pic_tape_record(pic_handle *h) {
   if (!h) return fail(h, PIC_EINVAL, "NULL handle");
   if (!h->taping || h->tape_len >= (int)h->tape.size())
     return fail(h, PIC_EINVAL, "no tape entry left to record (pic_tape_begin)");
-  CK(h, save_snapshot(h, h->tape[h->tape_len]), "tape record");
+  {
+    Timed tm(h, pic::KC_TAPE);
+    CK(h, save_snapshot(h, h->tape[h->tape_len], true, h->tape_len > 0 ? &h->tape[h->tape_len - 1] : nullptr),
+       "tape record");
+  }
   h->tape_len++;
   if (h->tape_len >= (int)h->tape.size()) h->taping = false;
   return PIC_OK;
@@ -1438,6 +1507,7 @@ int pic_adjoint_begin(pic_handle *h, int64_t id_capacity) {
     ok = ok && cudaMalloc(&h->pend, 8 * sizeof(double) * (size_t)h->g.n[1] * h->g.n[2]) == cudaSuccess &&
          cudaMalloc(&h->da0, sizeof(double)) == cudaSuccess && cudaMalloc(&h->objF, sizeof(double)) == cudaSuccess &&
          cudaMalloc(&h->adj_err, sizeof(unsigned long long)) == cudaSuccess &&
+         cudaMalloc(&h->adj_esc, sizeof(unsigned long long)) == cudaSuccess &&
          cudaMalloc(&h->adj_stage, (size_t)id_capacity * sizeof(double)) == cudaSuccess;
     for (int i = 0; i < h->nsp && ok; ++i) {
       for (int d = 0; d < 3 && ok; ++d)
@@ -1452,6 +1522,7 @@ int pic_adjoint_begin(pic_handle *h, int64_t id_capacity) {
     h->id_cap = id_capacity;
     h->adj_ready = true;
   }
+  CK(h, cudaMemsetAsync(h->adj_esc, 0, sizeof(unsigned long long), h->st), "zero");
   const size_t fb = (size_t)h->g.ncell * h->rsize;
   const size_t ib = (size_t)h->id_cap * h->rsize;
   for (int d = 0; d < 3; ++d) {
@@ -1518,11 +1589,21 @@ int pic_adjoint_step(pic_handle *h, int nsteps) {
     for (int i = 0; i < h->nsp; ++i) {
       Species &s = h->sp[i];
       Timed tm(h, pic::KC_ADJ_PUSH);
+      const PCopy &c = en.sp[i];
+      pic::AdjTiles tt;
+      tt.work_tile = c.work_tile;
+      tt.work_pb = c.work_pb;
+      tt.tile_start = c.tile_start;
+      tt.nwork = c.nwork;
+      tt.chunk = c.chunk;
+      tt.esc_total = h->adj_esc;
+      int nl = 0;
       CK(h,
-         pic::launch_adj_push(h->g, en.sp[i].p, en.sp[i].count, s.slots, en.E, en.B, h->lJ, h->lE, h->lB,
-                              h->adj[i].lx, h->adj[i].lu, h->adj[i].lw, h->id_cap, h->adj_err, s.q, s.m, h->st),
+         pic::launch_adj_push(h->g, c.p, c.count, s.slots, en.E, en.B, h->lJ, h->lE, h->lB, h->adj[i].lx,
+                              h->adj[i].lu, h->adj[i].lw, h->id_cap, h->adj_err, s.q, s.m, c.tiled ? &tt : nullptr,
+                              h->st, &nl),
          "adjoint push");
-      h->launches++;
+      h->launches += nl;
     }
     h->tape_len--;
   }
@@ -1537,6 +1618,46 @@ int pic_grad(pic_handle *h, double *d_a0, int species, double *d_w, int mem_kind
   if (d_w) CK(h, cudaMemcpyAsync(d_w, h->adj[species].lw, (size_t)h->id_cap * sizeof(double), kind, h->st), "grad copy");
   unsigned long long err = 0;
   CK(h, cudaMemcpyAsync(&err, h->adj_err, sizeof(err), cudaMemcpyDeviceToHost, h->st), "D2H");
+  CK(h, cudaStreamSynchronize(h->st), "sync");
+  if (err) return fail(h, PIC_EINVAL, "a particle id is not below the adjoint id capacity");
+  return PIC_OK;
+}
+
+int pic_grad_binned(pic_handle *h, int species, const int32_t *bin_of_id, int64_t n_ids, int nbins, double *out,
+                    int mem_kind) {
+  if (!h || !bin_of_id || !out) return fail(h, PIC_EINVAL, "NULL argument");
+  if (!h->adj_ready) return fail(h, PIC_EINVAL, "call pic_adjoint_begin first");
+  if (species < 0 || species >= h->nsp) return fail(h, PIC_EINVAL, "bad species index");
+  if (mem_kind != PIC_MEM_HOST && mem_kind != PIC_MEM_DEVICE) return fail(h, PIC_EINVAL, "bad memory kind");
+  if (n_ids < 0 || n_ids > h->id_cap) return fail(h, PIC_EINVAL, "n_ids outside [0, id capacity]");
+  if (nbins < 1) return fail(h, PIC_EINVAL, "nbins < 1");
+  const bool host = mem_kind == PIC_MEM_HOST;
+  int32_t *dbin = nullptr;
+  double *dout = nullptr;
+  bool ok = cudaMallocAsync(&dout, sizeof(double) * (size_t)nbins, h->st) == cudaSuccess;
+  if (ok && host && n_ids > 0) ok = cudaMallocAsync(&dbin, sizeof(int32_t) * (size_t)n_ids, h->st) == cudaSuccess;
+  int r = PIC_OK;
+  if (!ok) {
+    cudaGetLastError();
+    r = fail(h, PIC_ENOMEM, "gradient bins allocation failed");
+  }
+  cudaError_t e = cudaSuccess;
+  if (!r) e = cudaMemsetAsync(dout, 0, sizeof(double) * (size_t)nbins, h->st);
+  if (!r && e == cudaSuccess && dbin)
+    e = cudaMemcpyAsync(dbin, bin_of_id, sizeof(int32_t) * (size_t)n_ids, cudaMemcpyHostToDevice, h->st);
+  if (!r && e == cudaSuccess)
+    e = pic::launch_sum_by_bin(h->adj[species].lw, host ? dbin : bin_of_id, n_ids, nbins, dout, h->st);
+  if (!r && e == cudaSuccess) {
+    h->launches++;
+    e = cudaMemcpyAsync(out, dout, sizeof(double) * (size_t)nbins,
+                        host ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice, h->st);
+  }
+  unsigned long long err = 0;
+  if (!r && e == cudaSuccess) e = cudaMemcpyAsync(&err, h->adj_err, sizeof(err), cudaMemcpyDeviceToHost, h->st);
+  if (dbin) cudaFreeAsync(dbin, h->st);
+  if (dout) cudaFreeAsync(dout, h->st);
+  if (!r && e != cudaSuccess) r = cuda_fail(h, e, "gradient bins");
+  if (r) return r;
   CK(h, cudaStreamSynchronize(h->st), "sync");
   if (err) return fail(h, PIC_EINVAL, "a particle id is not below the adjoint id capacity");
   return PIC_OK;

@@ -118,7 +118,7 @@ constexpr int64_t kMaxWindowSlots = 65280;
 
 enum KernelClass {
   KC_SORT = 0, KC_ZEROJ = 1, KC_PUSH = 2, KC_YEE_B = 3, KC_YEE_E = 4, KC_BOUNDARY = 5, KC_FILTER = 6,
-  KC_ADJ_FIELD = 7, KC_ADJ_PUSH = 8, KC_N = 9
+  KC_ADJ_FIELD = 7, KC_ADJ_PUSH = 8, KC_TAPE = 9, KC_N = 10
 };
 
 // ---- push (push.cu) ----
@@ -239,14 +239,32 @@ cudaError_t launch_adj_yee_e(const Grid &g, void *const lE[3], void *const lB[3]
                              cudaStream_t st);
 cudaError_t launch_adj_mur(const Grid &g, void *const lE[3], double *pend, const LaserStep &ls_unit, double *da0,
                            cudaStream_t st);
+// Work items of a recorded particle buffer (those of the sort in effect when
+// it was recorded, see WorkSplit) for the windowed adjoint kernel;
+// esc_total counts the particles that had drifted beyond their tile window
+// (a running sum).
+struct AdjTiles {
+  const int32_t *work_tile = nullptr;
+  const int64_t *work_pb = nullptr;
+  const int64_t *tile_start = nullptr;
+  int64_t nwork = 0, chunk = 0;
+  unsigned long long *esc_total = nullptr;
+};
 // Per-particle adjoint of one recorded step (2D3V TSC only): tp/d_count
 // is the particle state at the start of the step, E/B the fields gathered.
+// With tt (and tiles of at most 16x16 cells) one block per work item stages
+// its tile window in shared memory; without, one pass over all slots with
+// the nodes in global memory.  *nlaunch receives the kernel launches.
 cudaError_t launch_adj_push(const Grid &g, const Particles &tp, const int64_t *d_count, int64_t nmax,
                             void *const E[3], void *const B[3], void *const lJ[3], void *const lE[3],
                             void *const lB[3], void *const lx[3], void *const lu[3], double *lw, int64_t id_cap,
-                            unsigned long long *err, double q, double m, cudaStream_t st);
+                            unsigned long long *err, double q, double m, const AdjTiles *tt, cudaStream_t st,
+                            int *nlaunch);
 // Objective sum over particles with x column in [c_lo, c_hi) of
 // w dV m (gamma - 1) into *F; seeds lam_u and dF/dw (by id).
+// out[b] += sum of w[i] over i < n with bin[i] == b in [0, nbins).
+cudaError_t launch_sum_by_bin(const double *w, const int32_t *bin, int64_t n, int nbins, double *out,
+                              cudaStream_t st);
 cudaError_t launch_adj_seed(const Grid &g, const Particles &p, const int64_t *d_count, int64_t nmax, int c_lo,
                             int c_hi, double dVm, void *const lu[3], double *lw, double *F, int64_t id_cap,
                             unsigned long long *err, cudaStream_t st);

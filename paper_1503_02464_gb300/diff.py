@@ -80,6 +80,20 @@ class SlabRun:
         return (ids // self.ppc) % self.nx
 
 
+_BINS = {}
+
+
+def _column_bins(run: SlabRun):
+    """The initial column of every particle id (int32), kept in device memory
+    (a CUDA tensor) once made."""
+    key = (run.nx, run.ppc, run.id_capacity)
+    if key not in _BINS:
+        bins = run.column_of_id(np.arange(run.id_capacity)).astype(np.int32)
+        import torch
+        _BINS[key] = torch.from_numpy(bins).cuda() if torch.cuda.is_available() else bins
+    return _BINS[key]
+
+
 def build_sim(run: SlabRun, a0: float, profile: np.ndarray) -> Simulation:
     """Simulation of the run with its electrons loaded (no steps taken)."""
     wl = run.workload(a0)
@@ -128,10 +142,10 @@ def backward_gradients(run: SlabRun, sim: Simulation):
             sim.step(run.segment - 1)
             sim.tape_record()
         sim.adjoint_step(run.segment)
-    da0, dw = sim.grad(0, run.id_capacity)
-    ids = np.arange(run.id_capacity)
-    dprof = np.bincount(run.column_of_id(ids), weights=dw, minlength=run.nx) / run.ppc
-    return da0, dprof
+    # dF/dprofile[k] = sum of dF/dw over the electrons of column k / ppc,
+    # summed on the device
+    dprof = sim.grad_binned(0, _column_bins(run), run.nx) / run.ppc
+    return sim.grad_a0(), dprof
 
 
 def make_function():

@@ -314,6 +314,27 @@ class Simulation:
         a = np.ascontiguousarray(lu, dtype=np.float64)
         capi.pic_adjoint_set_momenta(self.h, species, [a[d].ctypes.data for d in range(3)], capi.PIC_MEM_HOST)
 
+    def grad_binned(self, species: int, bin_of_id, nbins: int) -> np.ndarray:
+        """dF/dw summed over bins of particle ids on the device: out[b] =
+        sum of dF/dw_i over ids i with bin_of_id[i] == b.  bin_of_id is an
+        int32 numpy array (copied per call) or a CUDA int32 tensor."""
+        if hasattr(bin_of_id, "data_ptr"):
+            import torch
+            if bin_of_id.dtype != torch.int32 or not bin_of_id.is_cuda or not bin_of_id.is_contiguous():
+                raise ValueError("bin_of_id: a contiguous CUDA int32 tensor")
+            out = torch.zeros(nbins, dtype=torch.float64, device=bin_of_id.device)
+            capi.pic_grad_binned(self.h, species, bin_of_id.data_ptr(), bin_of_id.numel(), nbins, out.data_ptr(),
+                                 capi.PIC_MEM_DEVICE)
+            return out.cpu().numpy()
+        b = np.ascontiguousarray(bin_of_id, dtype=np.int32)
+        out = np.zeros(nbins, dtype=np.float64)
+        capi.pic_grad_binned(self.h, species, b.ctypes.data, len(b), nbins, out.ctypes.data, capi.PIC_MEM_HOST)
+        return out
+
+    def grad_a0(self) -> float:
+        """dF/da0 after a reverse sweep."""
+        return capi.pic_grad(self.h, 0, None, capi.PIC_MEM_HOST)
+
     def grad(self, species: int, id_capacity: int):
         """(dF/da0, dF/dw by particle id) after a reverse sweep."""
         dw = np.zeros(id_capacity, dtype=np.float64)

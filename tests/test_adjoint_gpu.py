@@ -67,6 +67,35 @@ def test_adjoint_fp64_matches_central_differences():
     assert abs(dprof @ v - fd_v) <= 1e-6 * _dir_scale(fd_v, dprof, v), (dprof @ v, fd_v)
 
 
+def test_binned_gradient_matches_per_id_sums():
+    """pic_grad_binned (the profile gradient's column sums, on the device)
+    against a bincount of the per-id weight gradient of pic_grad, with the
+    bin map in host and in device memory; ids with a bin outside [0, nbins)
+    are left out."""
+    import torch
+    run, prof = _tiny("fp64")
+    F, sim = diff.forward_objective(run, 0.8, prof, keep=True)
+    diff.backward_gradients(run, sim)
+    _, dw = sim.grad(0, run.id_capacity)
+    ids = np.arange(run.id_capacity)
+    bins = run.column_of_id(ids).astype(np.int32)
+    ref = np.bincount(bins, weights=dw, minlength=run.nx)
+    scale = np.abs(dw).sum()
+    assert scale > 0
+    host = sim.grad_binned(0, bins, run.nx)
+    dev = sim.grad_binned(0, torch.from_numpy(bins).cuda(), run.nx)
+    for got in (host, dev):
+        assert np.abs(got - ref).max() <= 1e-13 * scale, np.abs(got - ref).max() / scale
+    # bins past the end (and negative ones) drop out
+    odd = bins.copy()
+    odd[::3] = -1
+    odd[1::3] += run.nx
+    keep = np.bincount(bins[2::3], weights=dw[2::3], minlength=run.nx)
+    got = sim.grad_binned(0, odd, run.nx)
+    assert np.abs(got - keep).max() <= 1e-13 * scale
+    sim.close()
+
+
 def test_adjoint_fp64_matches_oracle_gradient():
     """Central differences of the CPU oracle's objective on the same run."""
     import oracle

@@ -13,7 +13,11 @@ are linear in some input, and a Jacobian check where the step is not.
   * Gather and rotation in B: u' is not linear in B, so the directional
     derivative of <u'(B), y> is compared with central differences (h = 1e-5).
 
-The 2D3V TSC cycle is the one the adjoint kernels cover.
+The 2D3V TSC cycle is the one the adjoint kernels cover.  The particle
+transposes run twice: with the particles in the tiles they were sorted into
+(the windowed kernel, nodes in shared memory), and after twelve unsorted
+steps of a hot plasma, when some have drifted beyond their tile windows and
+take the global-memory kernel.
 """
 import numpy as np
 import pytest
@@ -44,6 +48,26 @@ def _particles(s, npart, seed, u_th=0.2, walls=False):
     k = s.add_species(-1.0, 1.0, npart)
     s.load(k, p)
     return p
+
+
+def _drift(s, drifted):
+    """Twelve steps without a sort (sort_every = 1000), so that a hot plasma
+    leaves its tiles, then fields back to zero: the next step starts from
+    drifted particles and no field."""
+    if not drifted:
+        return
+    s.step(12)
+    zero = np.zeros(s.shape3)
+    for c in EB:
+        s.set_field(c, zero)
+
+
+def _check_paths(s, npart, drifted):
+    n_esc = s.diag()["n_adj_escaped"]
+    if drifted:
+        assert 0 < n_esc < npart, n_esc
+    else:
+        assert n_esc == 0, n_esc
 
 
 def _momenta_by_id(s, npart):
@@ -86,10 +110,12 @@ def test_yee_transpose_dot_product(walls):
     s.close()
 
 
-def test_deposit_transpose_in_weights():
+@pytest.mark.parametrize("drifted", [False, True], ids=["in_tiles", "drifted"])
+def test_deposit_transpose_in_weights(drifted):
     s = _sim()
     npart = 400
-    p = _particles(s, npart, 12)
+    p = _particles(s, npart, 12, u_th=0.8 if drifted else 0.2)
+    _drift(s, drifted)
     s.tape_begin(1)
     s.step(1)
     Lw = [s.field(c) for c in EB]
@@ -105,20 +131,21 @@ def test_deposit_transpose_in_weights():
     scale = _scale(Lw, y) + float(np.abs(p["w"] * lw[p["id"]]).sum())
     print("deposit", lhs, rhs, abs(lhs - rhs) / scale)
     assert abs(lhs - rhs) <= TOL * scale, (lhs, rhs)
+    _check_paths(s, npart, drifted)
     s.close()
 
 
-def test_gather_transpose_in_E():
+@pytest.mark.parametrize("drifted", [False, True], ids=["in_tiles", "drifted"])
+def test_gather_transpose_in_E(drifted):
     s = _sim()
     npart = 400
-    p = _particles(s, npart, 14)
+    _particles(s, npart, 14, u_th=0.8 if drifted else 0.2)
+    _drift(s, drifted)
     rng = np.random.default_rng(15)
     E0 = [rng.normal(size=s.shape3) for _ in range(3)]
     for c in range(3):
         s.set_field(c, E0[c])
-    u0 = np.stack([np.zeros(npart)] * 3)
-    for d, key in enumerate(("ux", "uy", "uz")):
-        u0[d, p["id"]] = p[key]
+    u0 = _momenta_by_id(s, npart)
     s.tape_begin(1)
     s.step(1)
     du = _momenta_by_id(s, npart) - u0  # (q dt/m) G E0, linear in E0
@@ -131,6 +158,7 @@ def test_gather_transpose_in_E():
     scale = float(np.abs(du * y).sum()) + _scale(E0, lE)
     print("gather E", lhs, rhs, abs(lhs - rhs) / scale)
     assert abs(lhs - rhs) <= TOL * scale, (lhs, rhs)
+    _check_paths(s, npart, drifted)
     s.close()
 
 

@@ -116,6 +116,34 @@ def test_escape_path(precision):
     assert du <= tol
 
 
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+@pytest.mark.parametrize("order", [1, 2])
+def test_fast_plasma_between_chunk_drain(precision, order):
+    """A relativistic 3D plasma (u_th = 1) changes the shape support of about
+    half its particles every step, more than the deferred-deposit queue of a
+    work item holds: the first push overflows the queue (the overflowing
+    particles deposit on the general stencil), the later ones take the
+    variant that drains the queue between chunks.  Both stay at parity with
+    the oracle, J included."""
+    wl = _wl(3, order, (32, 16, 16), 16, 1.0, 61 + order)
+    parts = [wl.particles(0)]
+    o = build_oracle(wl, parts)
+    s = build_gpu(wl, parts, precision)
+    for step in range(1, 11):
+        o.step(1)
+        s.step(1)
+        s.sync()  # the job count of each push is read back before the next
+    fe = compare_fields(o, s, j_abs=j_floor(wl, parts))
+    du, dx = compare_particles(o, s, wl)
+    d = s.diag()
+    print(precision, order, "fast plasma after 10 steps:", fe, du, d["n_push_mid_drain"])
+    assert d["n_push_mid_drain"] >= 5, d
+    tol = FP64_TOL_PER_STEP * 10 if precision == "fp64" else FP32_TOL
+    for k, v in fe.items():
+        assert v <= tol, (k, v)
+    assert du <= tol
+
+
 def test_thermal2d_64_full_fp64():
     """The 2D3V periodic plasma: 64x64 cells, 16 ppc (65,536 electrons),
     CIC, dt = 0.035, 100 steps in FP64 against the oracle."""
