@@ -421,24 +421,41 @@ def run_gpu(args, rank: int, world: int, local: int):
     # ---------------- adjoint / forward time of the differentiable run
     adjoint = None
     if not args.no_adjoint and rank == 0:
+        import dataclasses
+
         from paper_1503_02464_gb300 import diff
         run = diff.SlabRun(precision="fp32")
         prof = run.default_profile()
-        reps = []
-        for rep in range(4):  # the first repetition warms up; the median of the other three is reported
-            sim = diff.build_sim(run, 2.0, prof)
-            torch.cuda.synchronize()
-            t0 = time.perf_counter()
-            F = diff.run_forward(run, sim)
-            torch.cuda.synchronize()
-            t1 = time.perf_counter()
-            da0, dprof = diff.backward_gradients(run, sim)
-            torch.cuda.synchronize()
-            t2 = time.perf_counter()
-            sim.close()
-            if rep:
-                reps.append((t1 - t0, t2 - t1))
+
+        def timed_runs(r):
+            reps = []
+            for rep in range(4):  # the first repetition warms up; the median of the other three is reported
+                sim = diff.build_sim(r, 2.0, prof)
+                torch.cuda.synchronize()
+                t0 = time.perf_counter()
+                F = diff.run_forward(r, sim)
+                torch.cuda.synchronize()
+                t1 = time.perf_counter()
+                da0, dprof = diff.backward_gradients(r, sim)
+                torch.cuda.synchronize()
+                t2 = time.perf_counter()
+                sim.close()
+                if rep:
+                    reps.append((t1 - t0, t2 - t1))
+            return reps, F, da0
+
+        reps, F, da0 = timed_runs(run)
         fwd_s, bwd_s = sorted(reps, key=lambda r: r[1] / r[0])[len(reps) // 2]
+        # every forward step recorded instead (no recomputation), memory permitting
+        store_all = None
+        free_b, _ = torch.cuda.mem_get_info()
+        tape_b = run.steps * run.id_capacity * (4 * 4 + 4 * 4) + run.steps * 6 * 4 * run.nx * run.ny
+        if tape_b < 0.5 * free_b:
+            reps_a, _, da0_a = timed_runs(dataclasses.replace(run, store_all=True))
+            f_a, b_a = sorted(reps_a, key=lambda r: r[1] / r[0])[len(reps_a) // 2]
+            store_all = {"forward_s": f_a, "backward_s": b_a, "ratio": b_a / f_a, "ratios": [b / f for f, b in reps_a],
+                         "tape_bytes": tape_b, "dF_da0": da0_a,
+                         "note": "forward records all steps (device memory), reverse sweep without recomputation"}
         # one more run with per-kernel-class events, for the breakdown only
         sim = diff.build_sim(run, 2.0, prof)
         sim.profile(True)
@@ -455,7 +472,7 @@ def run_gpu(args, rank: int, world: int, local: int):
                    "note": "backward includes re-running every segment with the tape on; median of three "
                            "repetitions after a warm-up",
                    "kernel_ms": adj_kernels,
-                   "objective": F, "dF_da0": da0}
+                   "objective": F, "dF_da0": da0, "store_all": store_all}
 
     # ---------------- end to end through the C ABI with host buffers
     e2e = None

@@ -192,7 +192,12 @@ typedef struct pic_handle pic_handle;
  * kinds and the Courant condition of the Yee scheme (§2 states dx_i >= c dt;
  * the limit enforced is the sharper (sum dx_i^-2)^(-1/2)).  Allocates and
  * zeroes E, B, J.  Returns PIC_EINVAL / PIC_ECOURANT / PIC_ENOMEM / PIC_ECUDA.
- * On failure *out is NULL. */
+ * On failure *out is NULL.  Checkpoints, tape entries and load staging are
+ * stream-ordered allocations from the device's default memory pool; the
+ * first pic_create of the process lets that pool keep up to a quarter of
+ * the device's memory after frees, for reuse (a process-wide pool
+ * attribute), and a particle allocation that finds the device full returns
+ * the kept memory first. */
 int pic_create(const pic_config *cfg, pic_handle **out);
 
 /* Release every device buffer and the handle (NULL is accepted). */

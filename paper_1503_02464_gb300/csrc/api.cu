@@ -72,6 +72,7 @@ struct PCopy {
 // Full simulation state at a step boundary (checkpoint) or at the start of a
 // recorded step after its sort (tape entry).
 struct Snapshot {
+  void *mem = nullptr;  // the one allocation holding everything below
   PCopy sp[kMaxSpecies];
   void *E[3] = {}, *B[3] = {};
   int64_t step = -1;
@@ -228,11 +229,9 @@ void free_particles(Particles &p) {
   p = Particles{};
 }
 
-cudaError_t alloc_particles(Particles &p, int64_t cap, size_t rs, int dims) {
+// The SoA arrays of `cap` slots laid out from base (particles_bytes).
+void carve_particles(Particles &p, char *base, int64_t cap, size_t rs, int dims) {
   const size_t n = (size_t)(cap > 0 ? cap : 1);
-  char *base = nullptr;
-  const cudaError_t e = cudaMalloc(&base, particles_bytes(cap, rs, dims));
-  if (e != cudaSuccess) return e;
   p = Particles{};
   p.cell = reinterpret_cast<int32_t *>(base);
   char *q = base + align256(n * sizeof(int32_t));
@@ -241,6 +240,46 @@ cudaError_t alloc_particles(Particles &p, int64_t cap, size_t rs, int dims) {
   p.w = q;
   q += align256(n * rs);
   p.id = reinterpret_cast<uint32_t *>(q);
+}
+
+// Stream-ordered allocations (snapshots, load staging) that are freed stay
+// in the device's default memory pool, up to a quarter of the device's
+// memory, for reuse by later ones of this process (a process-wide pool
+// attribute, set once).
+void keep_pooled_memory(int dev) {
+  static bool done = false;
+  if (done) return;
+  done = true;
+  cudaMemPool_t pool;
+  size_t free_b = 0, total_b = 0;
+  if (cudaDeviceGetDefaultMemPool(&pool, dev) != cudaSuccess || cudaMemGetInfo(&free_b, &total_b) != cudaSuccess) {
+    cudaGetLastError();
+    return;
+  }
+  uint64_t keep = total_b / 4;
+  cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &keep);
+  cudaGetLastError();
+}
+
+// cudaMalloc that, when the device is full, first returns the memory kept
+// in the default pool and tries once more.
+cudaError_t dev_malloc(void **p, size_t bytes) {
+  cudaError_t e = cudaMalloc(p, bytes);
+  if (e != cudaErrorMemoryAllocation) return e;
+  cudaGetLastError();
+  int dev = 0;
+  cudaMemPool_t pool;
+  if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetDefaultMemPool(&pool, dev) != cudaSuccess) return e;
+  cudaDeviceSynchronize();
+  cudaMemPoolTrimTo(pool, 0);
+  return cudaMalloc(p, bytes);
+}
+
+cudaError_t alloc_particles(Particles &p, int64_t cap, size_t rs, int dims) {
+  char *base = nullptr;
+  const cudaError_t e = dev_malloc(reinterpret_cast<void **>(&base), particles_bytes(cap, rs, dims));
+  if (e != cudaSuccess) return e;
+  carve_particles(p, base, cap, rs, dims);
   return cudaSuccess;
 }
 
@@ -299,37 +338,47 @@ int64_t read_count(pic_handle *h, Species &s) {
   return n;
 }
 
-void free_snapshot(Snapshot &sn);
+void free_snapshot(Snapshot &sn, cudaStream_t st);
 
+// One stream-ordered allocation per snapshot: E and B back to back (like
+// the live fields, one copy), then per species its particle buffer, slot
+// count and sort work items.  Freed snapshots return to the device's
+// memory pool (kept for reuse, see pic_create), so that recording many
+// steps again in a later run costs no fresh allocation.
 cudaError_t alloc_snapshot(pic_handle *h, Snapshot &sn) {
   if (sn.allocated && sn.nsp == h->nsp) return cudaSuccess;
-  if (sn.allocated) free_snapshot(sn);
+  if (sn.allocated) free_snapshot(sn, h->st);
   const size_t fb = (size_t)h->g.ncell * h->rsize;
-  // E and B back to back, like the live fields (one copy)
-  cudaError_t e = cudaMalloc(&sn.E[0], 6 * fb);
-  if (e == cudaSuccess)
-    for (int d = 0; d < 3; ++d) {
-      sn.E[d] = static_cast<char *>(sn.E[0]) + d * fb;
-      sn.B[d] = static_cast<char *>(sn.E[0]) + (3 + d) * fb;
-    }
-  for (int i = 0; i < h->nsp && e == cudaSuccess; ++i) {
-    PCopy &c = sn.sp[i];
-    e = alloc_particles(c.p, h->sp[i].slots, h->rsize, h->g.dims);
-    if (e == cudaSuccess) e = cudaMalloc(&c.count, sizeof(int64_t));
-    if (e == cudaSuccess) e = cudaMalloc(&c.meta, sort_meta_bytes(h->sp[i].work.nwork, h->g.ntiles));
+  size_t total = align256(6 * fb);
+  for (int i = 0; i < h->nsp; ++i)
+    total += particles_bytes(h->sp[i].slots, h->rsize, h->g.dims) + 256 +
+             align256(sort_meta_bytes(h->sp[i].work.nwork, h->g.ntiles));
+  char *base = nullptr;
+  const cudaError_t e = cudaMallocAsync(reinterpret_cast<void **>(&base), total, h->st);
+  if (e != cudaSuccess) return e;
+  sn.mem = base;
+  sn.E[0] = base;
+  for (int d = 0; d < 3; ++d) {
+    sn.E[d] = base + d * fb;
+    sn.B[d] = base + (3 + d) * fb;
   }
-  sn.allocated = e == cudaSuccess;
+  char *q = base + align256(6 * fb);
+  for (int i = 0; i < h->nsp; ++i) {
+    PCopy &c = sn.sp[i];
+    carve_particles(c.p, q, h->sp[i].slots, h->rsize, h->g.dims);
+    q += particles_bytes(h->sp[i].slots, h->rsize, h->g.dims);
+    c.count = reinterpret_cast<int64_t *>(q);
+    q += 256;
+    c.meta = q;
+    q += align256(sort_meta_bytes(h->sp[i].work.nwork, h->g.ntiles));
+  }
+  sn.allocated = true;
   sn.nsp = h->nsp;
-  return e;
+  return cudaSuccess;
 }
 
-void free_snapshot(Snapshot &sn) {
-  cudaFree(sn.E[0]);  // E and B share one allocation
-  for (int i = 0; i < kMaxSpecies; ++i) {
-    free_particles(sn.sp[i].p);
-    cudaFree(sn.sp[i].count);
-    cudaFree(sn.sp[i].meta);
-  }
+void free_snapshot(Snapshot &sn, cudaStream_t st) {
+  if (sn.mem) cudaFreeAsync(sn.mem, st);
   sn = Snapshot{};
 }
 
@@ -511,6 +560,7 @@ int pic_create(const pic_config *cfg, pic_handle **out) {
     delete h;
     return fail(nullptr, PIC_ECUDA, std::string("no CUDA device: ") + cudaGetErrorString(e));
   }
+  keep_pooled_memory(dev);
   if (pic::push_smem_bytes(g) > (size_t)maxsm) {
     delete h;
     return fail(nullptr, PIC_EINVAL, "tile + guard window does not fit in shared memory; use a smaller tile");
@@ -606,8 +656,9 @@ int pic_destroy(pic_handle *h) {
     cudaEventDestroy(t.b);
   }
   for (auto e : h->event_pool) cudaEventDestroy(e);
-  for (auto &sn : h->ckpt) free_snapshot(sn);
-  for (auto &sn : h->tape) free_snapshot(sn);
+  for (auto &sn : h->ckpt) free_snapshot(sn, h->st);
+  for (auto &sn : h->tape) free_snapshot(sn, h->st);
+  cudaStreamSynchronize(h->st);
   free_adjoint(h);
   delete h;
   return PIC_OK;
@@ -1457,7 +1508,7 @@ int pic_restore(pic_handle *h, int slot) {
 int pic_tape_begin(pic_handle *h, int nsteps) {
   if (!h || nsteps < 0 || nsteps > 100000) return fail(h, PIC_EINVAL, "bad tape length");
   while ((int)h->tape.size() > nsteps) {
-    free_snapshot(h->tape.back());
+    free_snapshot(h->tape.back(), h->st);
     h->tape.pop_back();
   }
   h->tape.resize(nsteps);

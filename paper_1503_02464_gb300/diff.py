@@ -42,6 +42,11 @@ class SlabRun:
     duration: float = 4 * TAU
     seed: int = 1005
     precision: str = "fp32"
+    # True: the forward records every step (no recomputation in the reverse
+    # sweep; about 38 MB per step at the default size, FP32); False: a
+    # checkpoint every `segment` steps, each segment recomputed with its
+    # steps recorded during the reverse sweep
+    store_all: bool = False
 
     @property
     def d(self) -> float:
@@ -106,11 +111,16 @@ def build_sim(run: SlabRun, a0: float, profile: np.ndarray) -> Simulation:
 
 
 def run_forward(run: SlabRun, sim: Simulation) -> float:
-    """The forward steps with a checkpoint at every segment start; returns F."""
-    nseg = run.steps // run.segment
-    for k in range(nseg):
-        sim.checkpoint(k)
-        sim.step(run.segment)
+    """The forward steps, with a checkpoint at every segment start (or every
+    step recorded, run.store_all); returns F (and leaves the adjoint seeded)."""
+    if run.store_all:
+        sim.tape_begin(run.steps)
+        sim.step(run.steps)
+    else:
+        nseg = run.steps // run.segment
+        for k in range(nseg):
+            sim.checkpoint(k)
+            sim.step(run.segment)
     sim.adjoint_begin(run.id_capacity)
     return sim.adjoint_seed_kinetic(0, run.obj[0], run.obj[1])
 
@@ -126,8 +136,13 @@ def forward_objective(run: SlabRun, a0: float, profile: np.ndarray, keep: bool =
 
 
 def backward_gradients(run: SlabRun, sim: Simulation):
-    """Reverse sweep over the checkpointed segments; returns
-    (dF/da0, dF/dprofile[nx])."""
+    """Reverse sweep over the recorded steps (run.store_all) or the
+    checkpointed segments; returns (dF/da0, dF/dprofile[nx])."""
+    if run.store_all:
+        # the adjoint was seeded at the end of the forward pass
+        sim.adjoint_step(run.steps)
+        dprof = sim.grad_binned(0, _column_bins(run), run.nx) / run.ppc
+        return sim.grad_a0(), dprof
     nseg = run.steps // run.segment
     sim.adjoint_begin(run.id_capacity)
     for k in reversed(range(nseg)):
@@ -183,8 +198,9 @@ def main(argv=None):
     ap.add_argument("--precision", default="fp32", choices=["fp32", "fp64"])
     ap.add_argument("--a0", type=float, default=2.0)
     ap.add_argument("--repeat", type=int, default=2, help="runs (the first warms up)")
+    ap.add_argument("--store-all", action="store_true", help="record every forward step (no recomputation)")
     args = ap.parse_args(argv)
-    run = SlabRun(precision=args.precision)
+    run = SlabRun(precision=args.precision, store_all=args.store_all)
     prof = run.default_profile()
     for _ in range(args.repeat):
         sim = build_sim(run, args.a0, prof)

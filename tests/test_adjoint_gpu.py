@@ -138,6 +138,22 @@ def test_adjoint_fp32_matches_fp64_differences():
     assert abs(dprof @ v - fd_v) <= 1e-4 * _dir_scale(fd_v, dprof, v), (dprof @ v, fd_v)
 
 
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+def test_store_all_matches_checkpoints(precision):
+    """Recording every forward step (no recomputation in the reverse sweep)
+    gives the gradients of the checkpointed sweep: to round-off in FP64; in
+    FP32 to the level at which a recomputed segment differs from the first
+    run (float atomics in the shared windows change the order of additions)."""
+    import dataclasses
+    run, prof = _tiny(precision)
+    F1, da1, dp1 = _adjoint(run, 0.8, prof)
+    F2, da2, dp2 = _adjoint(dataclasses.replace(run, store_all=True), 0.8, prof)
+    tol = 1e-11 if precision == "fp64" else 1e-4
+    assert abs(F2 - F1) <= 1e-12 * abs(F1)
+    assert abs(da2 - da1) <= tol * abs(da1), (da1, da2)
+    assert np.abs(dp2 - dp1).max() <= tol * np.abs(dp1).max(), np.abs(dp2 - dp1).max() / np.abs(dp1).max()
+
+
 def test_autograd_function():
     import torch
     run, prof = _tiny("fp64")
