@@ -444,29 +444,32 @@ __global__ void __launch_bounds__(256)
                  const R *Ey, const R *Ez, const R *Bx, const R *By, const R *Bz, const R *Jx, const R *Jy,
                  const R *Jz, const double *rho, const double *rho_prev, double *out) {
   __shared__ double sh[32];
-  const int64_t ncell = (int64_t)n0 * n1 * n2;
   double se = 0, sb = 0, sq = 0, gm = 0, cm = 0, nf = 0;
-  for (int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; c < ncell; c += (int64_t)gridDim.x * blockDim.x) {
-    const int i = (int)(c % n0);
-    const int64_t r = c / n0;
-    const int j = (int)(r % n1);
-    const int k = (int)(r / n1);
-    const double ex = Ex[c], ey = Ey[c], ez = Ez[c], bx = Bx[c], by = By[c], bz = Bz[c];
-    se += ex * ex + ey * ey + ez * ez;
-    sb += bx * bx + by * by + bz * bz;
-    if (!isfinite(ex) || !isfinite(ey) || !isfinite(ez) || !isfinite(bx) || !isfinite(by) || !isfinite(bz)) nf += 1;
-    const int64_t cxm = c - (i > 0 ? 1 : 1 - n0);
-    const int64_t cym = c - (j > 0 ? n0 : (int64_t)n0 - (int64_t)n0 * n1);
-    const int64_t czm = c - (k > 0 ? (int64_t)n0 * n1 : (int64_t)n0 * n1 - (int64_t)n0 * n1 * n2);
-    double div = ((double)Ex[c] - (double)Ex[cxm]) * rdx0 + ((double)Ey[c] - (double)Ey[cym]) * rdx1;
-    double dj = ((double)Jx[c] - (double)Jx[cxm]) * rdx0 + ((double)Jy[c] - (double)Jy[cym]) * rdx1;
-    if (dims == 3) {
-      div += ((double)Ez[c] - (double)Ez[czm]) * rdx2;
-      dj += ((double)Jz[c] - (double)Jz[czm]) * rdx2;
+  // one x row per block and pass (no per-cell index division)
+  const int64_t nrows = (int64_t)n1 * n2;
+  for (int64_t r = blockIdx.x; r < nrows; r += gridDim.x) {
+    const int j = (int)(r % n1), k = (int)(r / n1);
+    const int64_t dy = j > 0 ? n0 : (int64_t)n0 - (int64_t)n0 * n1;  // to the y - 1 row, periodic
+    const int64_t dz = k > 0 ? (int64_t)n0 * n1 : (int64_t)n0 * n1 - (int64_t)n0 * n1 * n2;
+    for (int i = threadIdx.x; i < n0; i += blockDim.x) {
+      const int64_t c = r * n0 + i;
+      const double ex = Ex[c], ey = Ey[c], ez = Ez[c], bx = Bx[c], by = By[c], bz = Bz[c];
+      se += ex * ex + ey * ey + ez * ez;
+      sb += bx * bx + by * by + bz * bz;
+      if (!isfinite(ex) || !isfinite(ey) || !isfinite(ez) || !isfinite(bx) || !isfinite(by) || !isfinite(bz)) nf += 1;
+      const int64_t cxm = c - (i > 0 ? 1 : 1 - n0);
+      const int64_t cym = c - dy;
+      const int64_t czm = c - dz;
+      double div = ((double)Ex[c] - (double)Ex[cxm]) * rdx0 + ((double)Ey[c] - (double)Ey[cym]) * rdx1;
+      double dj = ((double)Jx[c] - (double)Jx[cxm]) * rdx0 + ((double)Jy[c] - (double)Jy[cym]) * rdx1;
+      if (dims == 3) {
+        div += ((double)Ez[c] - (double)Ez[czm]) * rdx2;
+        dj += ((double)Jz[c] - (double)Jz[czm]) * rdx2;
+      }
+      sq += rho[c];
+      gm = fmax(gm, fabs(div - rho[c]));
+      if (rho_prev) cm = fmax(cm, fabs((rho[c] - rho_prev[c]) * rdt + dj));
     }
-    sq += rho[c];
-    gm = fmax(gm, fabs(div - rho[c]));
-    if (rho_prev) cm = fmax(cm, fabs((rho[c] - rho_prev[c]) * rdt + dj));
   }
   double v;
   v = block_sum(se, sh);
@@ -526,18 +529,41 @@ __global__ void __launch_bounds__(256)
     k_particle_diag(Particles p, const int64_t *__restrict__ d_count, double m, double *out) {
   __shared__ double sh[32];
   const int64_t n = *d_count;
+  const int32_t *__restrict__ cell = p.cell;
+  const R *__restrict__ u0 = static_cast<const R *>(p.u[0]);
+  const R *__restrict__ u1 = static_cast<const R *>(p.u[1]);
+  const R *__restrict__ u2p = static_cast<const R *>(p.u[2]);
+  const R *__restrict__ w = static_cast<const R *>(p.w);
   ThreadSum<R> ek;
   int64_t cnt = 0, nf = 0;
-  for (int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; s < n; s += (int64_t)gridDim.x * blockDim.x) {
-    if (p.cell[s] < 0) continue;
-    // per-particle terms in the storage precision
-    const R ux = static_cast<const R *>(p.u[0])[s], uy = static_cast<const R *>(p.u[1])[s],
-            uz = static_cast<const R *>(p.u[2])[s];
-    const R u2 = ux * ux + uy * uy + uz * uz;
-    // gamma - 1 = u^2 / (sqrt(1 + u^2) + 1), free of cancellation
-    ek.add(static_cast<const R *>(p.w)[s] * (u2 / (sqrt(R(1) + u2) + R(1))));
-    ++cnt;
-    nf += !isfinite(u2);
+  // four slots per thread and pass, every load issued before any is used
+  // (a dead slot's momenta are read and dropped rather than skipped, so
+  // the loads do not wait for the cell index)
+  constexpr int kU = 4;
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t s0 = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; s0 < n; s0 += kU * stride) {
+    int c[kU];
+    R ux[kU], uy[kU], uz[kU], wq[kU];
+#pragma unroll
+    for (int k = 0; k < kU; ++k) {
+      const int64_t s = s0 + k * stride;
+      const bool in = s < n;
+      c[k] = in ? cell[s] : -1;
+      ux[k] = in ? u0[s] : R(0);
+      uy[k] = in ? u1[s] : R(0);
+      uz[k] = in ? u2p[s] : R(0);
+      wq[k] = in ? w[s] : R(0);
+    }
+#pragma unroll
+    for (int k = 0; k < kU; ++k) {
+      if (c[k] < 0) continue;
+      // per-particle terms in the storage precision
+      const R u2 = ux[k] * ux[k] + uy[k] * uy[k] + uz[k] * uz[k];
+      // gamma - 1 = u^2 / (sqrt(1 + u^2) + 1), free of cancellation
+      ek.add(wq[k] * (u2 / (sqrt(R(1) + u2) + R(1))));
+      ++cnt;
+      nf += !isfinite(u2);
+    }
   }
   double v = block_sum(ek.value(), sh);
   if (threadIdx.x == 0) atomicAdd(out + 0, m * v);
