@@ -1098,19 +1098,53 @@ __global__ void __launch_bounds__(kThreads, sizeof(R) == 4 ? (DIM == 2 ? 4 : (OR
   }
 
   // ---- flush the J window into global J ----
-  for (int q = tid; q < G::JN; q += kThreads) {
-    const int z = q / G::JP;
-    const int x = (q - z * G::JP) % G::JX;
-    const int y = (q - z * G::JP) / G::JX;
-    if (y >= G::JY) continue;  // plane padding
-    const int gi = wrap_near(t0[0] - G::D - G::LOJ + x, a.n[0]);
-    const int gj = wrap_near(t0[1] - G::D - G::LOJ + y, a.n[1]);
-    const int gk = DIM == 3 ? wrap_near(t0[2] - G::D - G::LOJ + z, a.n[2]) : 0;
-    const int64_t g = gi + (int64_t)a.n[0] * (gj + (int64_t)a.n[1] * gk);
+  if (sizeof(R) == 4 && (a.n[0] & 3) == 0) {
+    // FP32 with rows of a multiple of four cells: runs of four nodes along x
+    // aligned in global memory, one vector reduction each (every element
+    // added atomically); a run reaching past the window's x ends adds zeros
+    // there.  A run never straddles the periodic seam.
+    const int xs = t0[0] - G::D - G::LOJ;          // the window's first node, global x (unwrapped)
+    const int a0 = xs - (((xs % 4) + 4) & 3);      // the multiple of 4 at or below it
+    constexpr int NG = (G::JX + 6) / 4;            // runs per window row (the last may start past it)
+    for (int q = tid; q < NG * G::JY * G::JZ; q += kThreads) {
+      const int m = q % NG, row = q / NG;
+      const int y = row % G::JY, z = row / G::JY;
+      const int wx0 = a0 + 4 * m - xs;  // window x of the run's first node
+      if (wx0 >= G::JX) continue;
+      const int gi = wrap_near(a0 + 4 * m, a.n[0]);
+      const int gj = wrap_near(t0[1] - G::D - G::LOJ + y, a.n[1]);
+      const int gk = DIM == 3 ? wrap_near(t0[2] - G::D - G::LOJ + z, a.n[2]) : 0;
+      const int64_t g = gi + (int64_t)a.n[0] * (gj + (int64_t)a.n[1] * gk);
+      const int wrow = z * G::JP + y * G::JX;
 #pragma unroll
-    for (int c = 0; c < 3; ++c) {
-      const R v = acc.get(c, q);
-      if (v != R(0)) atomicAdd(a.J[c] + g, v);
+      for (int c = 0; c < 3; ++c) {
+        float v[4];
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+          const int wx = wx0 + e;
+          v[e] = (wx >= 0 && wx < G::JX) ? (float)acc.get(c, wrow + wx) : 0.f;
+        }
+        if (v[0] != 0.f || v[1] != 0.f || v[2] != 0.f || v[3] != 0.f)
+          asm volatile("red.global.add.v4.f32 [%0], {%1, %2, %3, %4};" ::"l"(a.J[c] + g), "f"(v[0]), "f"(v[1]),
+                       "f"(v[2]), "f"(v[3])
+                       : "memory");
+      }
+    }
+  } else {
+    for (int q = tid; q < G::JN; q += kThreads) {
+      const int z = q / G::JP;
+      const int x = (q - z * G::JP) % G::JX;
+      const int y = (q - z * G::JP) / G::JX;
+      if (y >= G::JY) continue;  // plane padding
+      const int gi = wrap_near(t0[0] - G::D - G::LOJ + x, a.n[0]);
+      const int gj = wrap_near(t0[1] - G::D - G::LOJ + y, a.n[1]);
+      const int gk = DIM == 3 ? wrap_near(t0[2] - G::D - G::LOJ + z, a.n[2]) : 0;
+      const int64_t g = gi + (int64_t)a.n[0] * (gj + (int64_t)a.n[1] * gk);
+#pragma unroll
+      for (int c = 0; c < 3; ++c) {
+        const R v = acc.get(c, q);
+        if (v != R(0)) atomicAdd(a.J[c] + g, v);
+      }
     }
   }
   if (tid == 0 && s_clamp) atomicAdd(&a.ctr->clamped, (unsigned long long)s_clamp);
