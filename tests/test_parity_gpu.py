@@ -52,7 +52,15 @@ def test_fp64_per_step(dims, order, n, tile, ppc, uth):
     print("fp64 worst per step:", worst)
 
 
-@pytest.mark.parametrize("dims,order,n,tile,ppc,uth", CASES)
+# rows of a multiple of four cells take the four-node vector reductions of
+# the FP32 J flush; these x sizes take the scalar one
+ODD_ROW_CASES = [
+    (2, 2, (41, 24), (16, 16), 4, 0.2),
+    (3, 2, (13, 10, 9), None, 3, 0.2),
+]
+
+
+@pytest.mark.parametrize("dims,order,n,tile,ppc,uth", CASES + ODD_ROW_CASES)
 def test_fp32_after_10_steps(dims, order, n, tile, ppc, uth):
     wl = _wl(dims, order, n, ppc, uth, 41 + dims * 10 + order)
     parts = [wl.particles(0)]
