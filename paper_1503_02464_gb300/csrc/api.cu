@@ -42,6 +42,9 @@ struct Species {
   cudaEvent_t esc_ev = nullptr;
   bool esc_pending = false;
   bool mid_drain = false;       // push variant draining its job queue between chunks
+  bool fast = false;            // the last escape count read was above 1/8 of the early-sort threshold
+  int count_age = 0;            // steps since an escape count was last read
+  int64_t esc_step = -1;        // step of the push whose escape count is being read back
   bool fresh = true;            // sorted since the last push
   bool need_sort = true;
   int64_t sorted_at = -1;  // step count at the last sort
@@ -1180,20 +1183,36 @@ int pic_step(pic_handle *h, int nsteps) {
       Species &s = h->sp[i];
       // Sort on the cadence, or early when the last push sent more than
       // 0.5 % of the particles down the escape path (they drifted beyond
-      // their tile's guard cells).  The escape count is read without
-      // blocking: a push whose count has not arrived yet does not trigger.
+      // their tile's guard cells).  The escape count of a push is read back
+      // asynchronously.  A species whose last count was above 1/8 of that
+      // threshold waits for the count of its previous push; the others wait
+      // once four steps have passed without a count, so that a long
+      // pic_step call, whose host loop runs ahead of the device, still
+      // learns how the particles drift.  (On large grids a wait costs no
+      // device time: the last step's field updates are still queued behind
+      // the push when it ends.)
       bool many_escapes = false;
       if (s.esc_pending) {
-        const cudaError_t q = cudaEventQuery(s.esc_ev);
+        cudaError_t q;
+        if (s.fast || s.count_age >= 4) {
+          CK(h, cudaEventSynchronize(s.esc_ev), "escape count");
+          q = cudaSuccess;
+        } else {
+          q = cudaEventQuery(s.esc_ev);
+        }
         if (q == cudaSuccess) {
           s.esc_pending = false;
+          s.count_age = 0;
           const unsigned long long lim = (unsigned long long)(s.h_count / 200 > 1024 ? s.h_count / 200 : 1024);
-          many_escapes = s.esc_host[0] > lim;
+          // (a count from before the last sort says nothing about the order now)
+          many_escapes = s.esc_step >= s.sorted_at && s.esc_host[0] > lim;
+          s.fast = s.esc_host[0] > lim / 8;
           // many particles changing shape support per step (fast beams): the
           // push variant that drains its deferred-job queue between chunks
           s.mid_drain = s.esc_host[1] > (unsigned long long)pic::kPushQueueMidDrain * (unsigned long long)s.work.nwork;
         } else {
           cudaGetLastError();  // not ready: not an error
+          s.count_age++;
         }
       }
       // (a species sorted since the last push, e.g. by pic_neutralize, is not sorted again)
@@ -1233,6 +1252,7 @@ int pic_step(pic_handle *h, int nsteps) {
            "escape count");
         CK(h, cudaEventRecord(s.esc_ev, h->st), "escape event");
         s.esc_pending = true;
+        s.esc_step = h->step;
       }
     }
     if (h->cfg.filter_passes > 0) {
