@@ -152,6 +152,22 @@ def test_fast_plasma_between_chunk_drain(precision, order):
     assert du <= tol
 
 
+def test_adaptive_sort_within_one_step_call():
+    """The same early sorts when all the steps are enqueued by one pic_step
+    call: the host loop runs ahead of the device (2M particles, a push takes
+    longer than enqueueing a step), so the escape counts must be waited for
+    rather than only polled."""
+    wl = _wl(3, 2, (64, 64, 32), 16, 1.0, 47)
+    parts = [wl.particles(0)]
+    s = build_gpu(wl, parts, "fp32", sort_every=1000)
+    s.step(30)
+    d = s.diag()
+    print("adaptive sorts", d["n_sorts_adaptive"], "escaped", d["n_escaped"])
+    assert d["n_sorts_adaptive"] > 0
+    assert d["n_escaped"] < 0.2 * 30 * wl.n_particles()
+    assert np.isfinite(d["energy_kinetic"]) and d["n_alive"] == wl.n_particles()
+
+
 def test_thermal2d_64_full_fp64():
     """The 2D3V periodic plasma: 64x64 cells, 16 ppc (65,536 electrons),
     CIC, dt = 0.035, 100 steps in FP64 against the oracle."""
