@@ -900,11 +900,9 @@ static cudaError_t adj_push_t(const Grid &g, const Particles &tp, const int64_t 
     return cudaGetLastError();
   }
   const size_t smem = (size_t)9 * kAdjWinN * sizeof(R);
-  static bool attr_set = false;  // per R: one instantiation per element type
-  if (!attr_set) {
+  if (smem > 48 * 1024) {  // (set on every launch: the attribute belongs to the current device)
     cudaError_t e = cudaFuncSetAttribute(k_adj_push2d_win<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    attr_set = true;
   }
   AdjWork w;
   w.work_tile = tt->work_tile;
