@@ -111,16 +111,21 @@ def build_sim(run: SlabRun, a0: float, profile: np.ndarray) -> Simulation:
 
 
 def run_forward(run: SlabRun, sim: Simulation) -> float:
-    """The forward steps, with a checkpoint at every segment start (or every
-    step recorded, run.store_all); returns F (and leaves the adjoint seeded)."""
+    """The forward steps, with a checkpoint at the start of every segment but
+    the last, whose steps are recorded (or every step recorded,
+    run.store_all); returns F (and leaves the adjoint seeded)."""
     if run.store_all:
         sim.tape_begin(run.steps)
         sim.step(run.steps)
     else:
         nseg = run.steps // run.segment
-        for k in range(nseg):
+        for k in range(nseg - 1):
             sim.checkpoint(k)
             sim.step(run.segment)
+        # the last segment is recorded as it runs, so that the reverse sweep
+        # starts without recomputing it
+        sim.tape_begin(run.segment)
+        sim.step(run.segment)
     sim.adjoint_begin(run.id_capacity)
     return sim.adjoint_seed_kinetic(0, run.obj[0], run.obj[1])
 
@@ -144,18 +149,15 @@ def backward_gradients(run: SlabRun, sim: Simulation):
         dprof = sim.grad_binned(0, _column_bins(run), run.nx) / run.ppc
         return sim.grad_a0(), dprof
     nseg = run.steps // run.segment
-    sim.adjoint_begin(run.id_capacity)
-    for k in reversed(range(nseg)):
+    # the last segment was recorded by the forward pass, which also seeded
+    # the adjoint at the final state
+    sim.adjoint_step(run.segment)
+    for k in reversed(range(nseg - 1)):
         sim.restore(k)
         sim.tape_begin(run.segment)
-        if k == nseg - 1:
-            # the objective needs the final state: the last segment runs in full
-            sim.step(run.segment)
-            sim.adjoint_seed_kinetic(0, run.obj[0], run.obj[1])
-        else:
-            # only the start state of the segment's last step is needed
-            sim.step(run.segment - 1)
-            sim.tape_record()
+        # only the start state of the segment's last step is needed
+        sim.step(run.segment - 1)
+        sim.tape_record()
         sim.adjoint_step(run.segment)
     # dF/dprofile[k] = sum of dF/dw over the electrons of column k / ppc,
     # summed on the device
