@@ -403,7 +403,7 @@ __device__ __forceinline__ void adj_particle(const AdjPushArgs<R> &a, const Node
     }
     const R cx = a.cxu[0] * wq, cy = a.cxu[1] * wq, qw = a.q * wq;
     R dS0x[4], dS1x[4], dS0y[4], dS1y[4];  // dL/dS
-    double dLw;                            // dL/dw (contributions are linear in w)
+    R dLw;  // dL/dw of this step (contributions are linear in w); summed over steps in FP64
     // pass 1, Jx and Jy: Gx[a] = sum_b lamJx[a][b] Hy[b], Ky[b] = sum_a
     // lamJx[a][b] Px[a] (Px the prefix sums of S1 - S0, H the means of S0
     // and S1), and the same with x and y exchanged for Jy
@@ -465,7 +465,7 @@ __device__ __forceinline__ void adj_particle(const AdjPushArgs<R> &a, const Node
         gxp += Gx[k] * Px[k];
         gyp += Gy[k] * Py[k];
       }
-      dLw = (double)(a.cxu[0] * gxp + a.cxu[1] * gyp);
+      dLw = a.cxu[0] * gxp + a.cxu[1] * gyp;
     }
     // pass 2, Jz: Zx0[a] = sum_b lamJz[a][b] SY0[b] (and with S1), Zy the
     // same over a
@@ -491,7 +491,7 @@ __device__ __forceinline__ void adj_particle(const AdjPushArgs<R> &a, const Node
         dS0y[k] += qw * vz * (Zy0[k] * R(1.0 / 3.0) + Zy1[k] * R(1.0 / 6.0));
       }
     }
-    dLw += (double)(a.q * vz * Tz);
+    dLw += a.q * vz * Tz;
     const R lvz = qw * Tz;  // dL/dvz
     R lf_old[2] = {0, 0}, lf_new[2] = {0, 0};
     {
@@ -623,7 +623,7 @@ __device__ __forceinline__ void adj_particle(const AdjPushArgs<R> &a, const Node
     a.lx[1][pid] = lX[1];
 #pragma unroll
     for (int d = 0; d < 3; ++d) a.lu[d][pid] = lu0[d];
-    a.lw[pid] += dLw;
+    a.lw[pid] += (double)dLw;
   }
 }
 
