@@ -79,3 +79,42 @@ def test_thermal3d_256_first_step_sampled():
         s.close()
     finally:
         host.close()
+
+
+def test_thermal3d_256_fp32_tracks_fp64_over_a_sort_cycle():
+    """The bench workload over 25 steps (a cadence sort at step 20, particles
+    on the escape path before it) in FP32 and in FP64 from the same inputs:
+    the FP64 path holds the oracle to 1e-12 per step on the small cases, so
+    the FP32 run's energies must follow it, and in both runs the discrete
+    continuity equation and Gauss's law hold at the last step."""
+    wl = synth.preset("thermal3d_256")
+    host = synth.SharedParticles(wl, 0)
+    out = {}
+    try:
+        for precision in ("fp32", "fp64"):
+            s = Simulation.from_workload(wl, precision=precision)
+            k = s.add_species(-1.0, 1.0, host.n)
+            s.load(k, host.arrays)
+            s.neutralize()
+            s.step(24)
+            s.diag()  # the previous step's charge, for the continuity check
+            s.step(1)
+            d = s.diag()
+            jmax = max(np.abs(s.field(6 + c)).max() for c in range(3))
+            out[precision] = d
+            print(precision, {key: d[key] for key in ("energy_e", "energy_b", "energy_kinetic", "gauss_max",
+                                                       "continuity_max", "n_escaped")}, "jmax", jmax)
+            assert d["n_alive"] == host.n
+            tol = 1e-5 if precision == "fp32" else 1e-12
+            assert 0 <= d["continuity_max"] <= tol * jmax / wl.d[0], (precision, d["continuity_max"], jmax)
+            assert d["n_escaped"] > 0  # the escape path ran
+            s.close()
+    finally:
+        host.close()
+    # measured on GB300: kinetic 1e-10, electric 3e-8, magnetic 4e-8 relative
+    a, b = out["fp32"], out["fp64"]
+    assert a["n_escaped"] == b["n_escaped"]  # the same particles left their windows
+    assert abs(a["energy_kinetic"] / b["energy_kinetic"] - 1) <= 1e-8, (a["energy_kinetic"], b["energy_kinetic"])
+    assert abs(a["energy_e"] / b["energy_e"] - 1) <= 1e-6, (a["energy_e"], b["energy_e"])
+    assert abs(a["energy_b"] / b["energy_b"] - 1) <= 1e-6, (a["energy_b"], b["energy_b"])
+    assert a["gauss_max"] <= 1e-6 and b["gauss_max"] <= 1e-12
