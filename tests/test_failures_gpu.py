@@ -93,6 +93,13 @@ def test_bad_arguments():
     assert _code(s.adjoint_step, 1) == capi.PIC_EINVAL
     assert _code(s.set_background, np.full(s.shape3, np.nan)) == capi.PIC_EINVAL
     assert "background" in capi.load().pic_last_error(h).decode()
+    bins = np.zeros(10, dtype=np.int32)
+    assert _code(s.grad_binned, 0, bins, 4) == capi.PIC_EINVAL      # no pic_adjoint_begin
+    s.adjoint_begin(10)
+    assert _code(s.grad_binned, 3, bins, 4) == capi.PIC_EINVAL      # no such species
+    assert _code(s.grad_binned, 0, bins, 0) == capi.PIC_EINVAL      # no bins
+    assert _code(s.grad_binned, 0, np.zeros(11, dtype=np.int32), 4) == capi.PIC_EINVAL  # more ids than the capacity
+    np.testing.assert_array_equal(s.grad_binned(0, bins, 4), np.zeros(4))  # nothing accumulated yet
     # still usable
     s.load(k, {key: v[:10] for key, v in wl.particles(0).items()})
     s.step(1)
