@@ -601,6 +601,18 @@ def run_gpu(args, rank: int, world: int, local: int):
                          "nominal_kind": f"{nsm} SMs x {FP32_LANES_PER_SM} FP32 lanes x 2 flop x "
                                          f"{sm_max_mhz:.0f} MHz max SM clock"},
         "kernel_times": tim_out,
+        # the Yee updates against the same copy bandwidth: a B half reads E, B
+        # and writes B (9 arrays of the grid), the E update reads E, B, J and
+        # writes E (12 arrays)
+        "roofline_fields": {
+            k: {"bound": "hbm", "achieved": nb * ncell * (4 if args.precision == "fp32" else 8) /
+                (r["tim"][k][0] / r["tim"][k][1] / 1e3) / 1e9,
+                "peak": peak, "unit": "GB/s",
+                "frac": nb * ncell * (4 if args.precision == "fp32" else 8) /
+                (r["tim"][k][0] / r["tim"][k][1] / 1e3) / 1e9 / peak,
+                "bytes_per_launch": nb * ncell * (4 if args.precision == "fp32" else 8),
+                "ms_per_launch": r["tim"][k][0] / r["tim"][k][1]}
+            for k, nb in (("yee_b", 9), ("yee_e", 12)) if r["tim"].get(k, (0, 0))[1]},
         "gpu_launches": int(r["launches"]),
         "clocks": r["clocks"],
         "diag_after": {k: r["diag"][k] for k in ("energy_field", "energy_kinetic", "n_alive", "n_escaped",
