@@ -169,17 +169,24 @@ def test_oblique_laser_slab_fp32(dims):
     _check_fp32(wl, before)
 
 
-@pytest.mark.parametrize("structure", [("grating", 12, 4), ("foam", 0.4, 99)], ids=["grating", "foam"])
-def test_structured_target_fp64(structure):
-    """A laser at 30 degrees on a structured target (a grating front or a
-    randomly filled foam): FP64 parity per step."""
+def _structured_target(structure):
     d = 0.1
     dt = 0.9 * synth.courant_limit((d, d), 2)
     species = [synth.Species("electron", -1.0, 1.0, 2, 0.0, 4.0, (20, 30), 0, structure=structure),
                synth.Species("proton", 1.0, 1836.0, 2, 0.0, 4.0, (20, 30), 0, structure=structure)]
-    wl = synth.Workload("target_small", 2, (96, 48, 1), (d, d, 1.0), dt, 2, 60, 91, species, absorbing_x=True,
-                        neutralize=False, laser={"a0": 2.0, "waist": 1.2, "duration": TAU, "pol": 1,
-                                                 "angle": math.radians(30.0)})
+    return synth.Workload("target_small", 2, (96, 48, 1), (d, d, 1.0), dt, 2, 60, 91, species, absorbing_x=True,
+                          neutralize=False, laser={"a0": 2.0, "waist": 1.2, "duration": TAU, "pol": 1,
+                                                   "angle": math.radians(30.0)})
+
+
+STRUCTURES = [("grating", 12, 4), ("foam", 0.4, 99)]
+
+
+@pytest.mark.parametrize("structure", STRUCTURES, ids=["grating", "foam"])
+def test_structured_target_fp64(structure):
+    """A laser at 30 degrees on a structured target (a grating front or a
+    randomly filled foam): FP64 parity per step."""
+    wl = _structured_target(structure)
     o, s, jf = _pair(wl, "fp64")
     for step in range(1, 61):
         o.step(1)
@@ -195,6 +202,14 @@ def test_structured_target_fp64(structure):
                 assert du <= 1e-12 * step, (step, isp, du)
     p0 = s.particles(0)
     assert max(np.abs(p0[k]).max() for k in ("ux", "uy")) > 1e-3
+
+
+@pytest.mark.parametrize("structure", STRUCTURES, ids=["grating", "foam"])
+def test_structured_target_fp32(structure):
+    """The same targets on the FP32 path: 1e-5 on fields (J above the
+    position-rounding floor) and on momenta relative to the field-imparted
+    momentum, ten steps after the pulse has reached the target."""
+    _check_fp32(_structured_target(structure), 50)
 
 
 def test_oblique_laser_limits():
