@@ -118,3 +118,73 @@ def test_thermal3d_256_fp32_tracks_fp64_over_a_sort_cycle():
     assert abs(a["energy_e"] / b["energy_e"] - 1) <= 1e-6, (a["energy_e"], b["energy_e"])
     assert abs(a["energy_b"] / b["energy_b"] - 1) <= 1e-6, (a["energy_b"], b["energy_b"])
     assert a["gauss_max"] <= 1e-6 and b["gauss_max"] <= 1e-12
+
+
+def _run_laser(wl, precision, nsteps, hosts):
+    """Load the workload's species from the shared host arrays, record the
+    Gauss residual div E - rho at the start (E = 0), run nsteps, return the
+    residual's change away from the injection wall (relative to max|E|/dx),
+    the final diagnostics and max|J|."""
+    s = Simulation.from_workload(wl, precision=precision)
+    for sp, h in zip(wl.species, hosts):
+        k = s.add_species(sp.q, sp.m, h.n)
+        s.load(k, h.arrays)
+
+    def gauss():
+        E = [s.field(c) for c in range(wl.dims)]
+        rho = s.field(9)
+        div = np.zeros_like(rho)
+        for a in range(wl.dims):
+            ax = 2 - a  # arrays are (z, y, x)
+            div += (E[a] - np.roll(E[a], 1, axis=ax)) / wl.d[a]
+        return div - rho, max(np.abs(e).max() for e in E)
+
+    g0, _ = gauss()
+    s.step(nsteps - 1)
+    s.diag()  # charge of the step before the last, for the continuity check
+    s.step(1)
+    d = s.diag()
+    g1, emax = gauss()
+    jmax = max(np.abs(s.field(6 + c)).max() for c in range(3))
+    # the wall cells: the incoming wave is injected as its transverse
+    # component alone (§2 reading), so div E changes there by design
+    inner = np.abs(g1 - g0)[..., 2:wl.n[0] - 2].max() / (emax / min(wl.d[:wl.dims]))
+    s.close()
+    return inner, d, jmax, emax
+
+
+# steps: the slab's full 2000 (the pulse reaches it near step 1600); the
+# foil until the front of the pulse has reached it (near step 490)
+@pytest.mark.parametrize("name,nsteps,fp64_steps", [("laser_slab2d", 2000, 2000), ("laser_foil3d", 650, 650)])
+def test_laser_workloads_full_size(name, nsteps, fp64_steps):
+    """The laser workloads at full size (2D slab 2048x1024 with 5.2M
+    particles, 3D foil 512x256^2 with 70.8M), in the launch configuration
+    the bench times, FP32 and FP64 from the same inputs, checked by
+    properties that hold at any size: the charge-conserving cycle keeps
+    div E - rho at its initial value away from the injection wall, the
+    discrete continuity equation holds at the last step, and the FP32 run's
+    energies follow the FP64 run's (FP64 parity with the oracle is per step
+    on the small cases)."""
+    wl = synth.preset(name)
+    hosts = [synth.SharedParticles(wl, i) for i in range(len(wl.species))]
+    out = {}
+    try:
+        for precision, n in (("fp32", nsteps), ("fp64", fp64_steps)):
+            inner, d, jmax, emax = _run_laser(wl, precision, n, hosts)
+            out[precision] = d
+            print(name, precision, "gauss change / (max|E|/dx) %.2e" % inner, "continuity", d["continuity_max"],
+                  "jmax", jmax, "emax", emax, {k: d[k] for k in ("energy_e", "energy_b", "energy_kinetic",
+                                                               "n_absorbed")})
+            assert emax > 0.1 and jmax > 0  # the pulse is in the box and has reached the target
+            tol = 2e-5 if precision == "fp32" else 1e-11
+            assert inner <= tol, (precision, inner)
+            ctol = 1e-5 if precision == "fp32" else 1e-12
+            assert 0 <= d["continuity_max"] <= ctol * max(jmax, 1e-30) / min(wl.d[:wl.dims]) or jmax == 0.0, \
+                (precision, d["continuity_max"], jmax)
+    finally:
+        for h in hosts:
+            h.close()
+    a, b = out["fp32"], out["fp64"]
+    for k in ("energy_e", "energy_b"):
+        assert abs(a[k] / b[k] - 1) <= 1e-5, (k, a[k], b[k])
+    assert abs(a["energy_kinetic"] - b["energy_kinetic"]) <= 1e-5 * (b["energy_e"] + b["energy_b"] + b["energy_kinetic"])
