@@ -132,9 +132,16 @@ struct pic_handle {
   std::vector<cudaEvent_t> event_pool;
   // differentiable runs
   std::vector<Snapshot> ckpt;
-  std::vector<Snapshot> tape;
+  // Two tape buffers: the reverse sweep of one segment (on st_adj) runs
+  // while the next segment is recomputed and recorded into the other (on st).
+  std::vector<Snapshot> tapes[2];
+  int tape_buf = 1;  // the buffer last begun (recorded, then reversed)
   int tape_len = 0;
   bool taping = false;
+  cudaStream_t st_adj = nullptr;  // the adjoint kernels' stream
+  cudaEvent_t tape_free[2] = {};  // on st_adj: the last reversal of each tape buffer has run
+  cudaEvent_t ev_main = nullptr;  // on st: what an adjoint step must wait for
+  cudaEvent_t ev_adj = nullptr;   // on st_adj: what work on st touching the adjoint state must wait for
   bool adj_ready = false;
   int64_t id_cap = 0;
   void *lE[3] = {}, *lB[3] = {}, *lJ[3] = {};
@@ -186,23 +193,46 @@ const char *const kClassNames[pic::KC_N] = {"sort",   "zero_j",    "push",     "
 struct Timed {
   pic_handle *h;
   int cls;
+  cudaStream_t st;
   cudaEvent_t a = nullptr;
-  Timed(pic_handle *h_, int c) : h(h_), cls(c) {
+  Timed(pic_handle *h_, int c, cudaStream_t s = nullptr) : h(h_), cls(c), st(s ? s : h_->st) {
     nvtxRangePushA(kClassNames[c]);
     if (h->profiling) {
       a = take_event(h);
-      cudaEventRecord(a, h->st);
+      cudaEventRecord(a, st);
     }
   }
   ~Timed() {
     if (h->profiling) {
       cudaEvent_t b = take_event(h);
-      cudaEventRecord(b, h->st);
+      cudaEventRecord(b, st);
       h->timers.push_back({cls, a, b});
     }
     nvtxRangePop();
   }
 };
+
+// The tape buffer being recorded or reversed.
+std::vector<Snapshot> &cur_tape(pic_handle *h) { return h->tapes[h->tape_buf]; }
+
+// Work about to be enqueued on st that reads or writes the adjoint state
+// waits for the adjoint kernels enqueued so far on st_adj.
+cudaError_t join_adj(pic_handle *h) {
+  if (!h->st_adj) return cudaSuccess;
+  cudaError_t e = cudaEventRecord(h->ev_adj, h->st_adj);
+  if (e == cudaSuccess) e = cudaStreamWaitEvent(h->st, h->ev_adj, 0);
+  return e;
+}
+
+// The ordering events (created once).
+cudaError_t make_tape_events(pic_handle *h) {
+  cudaError_t e = cudaSuccess;
+  for (auto &ev : h->tape_free)
+    if (!ev && e == cudaSuccess) e = cudaEventCreateWithFlags(&ev, cudaEventDisableTiming);
+  if (!h->ev_main && e == cudaSuccess) e = cudaEventCreateWithFlags(&h->ev_main, cudaEventDisableTiming);
+  if (!h->ev_adj && e == cudaSuccess) e = cudaEventCreateWithFlags(&h->ev_adj, cudaEventDisableTiming);
+  return e;
+}
 
 // A particle buffer is one allocation holding the SoA arrays back to back
 // (cell, off[0..dims), u[0..3), w, id, each 256-byte aligned), so that a
@@ -660,9 +690,16 @@ int pic_destroy(pic_handle *h) {
   }
   for (auto e : h->event_pool) cudaEventDestroy(e);
   for (auto &sn : h->ckpt) free_snapshot(sn, h->st);
-  for (auto &sn : h->tape) free_snapshot(sn, h->st);
+  join_adj(h);
+  for (auto &tb : h->tapes)
+    for (auto &sn : tb) free_snapshot(sn, h->st);
   cudaStreamSynchronize(h->st);
   free_adjoint(h);
+  if (h->st_adj) cudaStreamDestroy(h->st_adj);
+  for (cudaEvent_t ev : h->tape_free)
+    if (ev) cudaEventDestroy(ev);
+  if (h->ev_main) cudaEventDestroy(h->ev_main);
+  if (h->ev_adj) cudaEventDestroy(h->ev_adj);
   delete h;
   return PIC_OK;
 }
@@ -1223,13 +1260,14 @@ int pic_step(pic_handle *h, int nsteps) {
       }
     }
     if (h->taping) {
-      if (h->tape_len < (int)h->tape.size()) {
+      std::vector<Snapshot> &tape = cur_tape(h);
+      if (h->tape_len < (int)tape.size()) {
         Timed tm(h, pic::KC_TAPE);
-        CK(h, save_snapshot(h, h->tape[h->tape_len], true, h->tape_len > 0 ? &h->tape[h->tape_len - 1] : nullptr),
+        CK(h, save_snapshot(h, tape[h->tape_len], true, h->tape_len > 0 ? &tape[h->tape_len - 1] : nullptr),
            "tape record");
         h->tape_len++;
       }
-      if (h->tape_len >= (int)h->tape.size()) h->taping = false;
+      if (h->tape_len >= (int)tape.size()) h->taping = false;
     }
     {
       Timed tm(h, pic::KC_ZEROJ);
@@ -1461,11 +1499,13 @@ int pic_energy(pic_handle *h, pic_energy_t *out) {
 
 int pic_sync(pic_handle *h) {
   if (!h) return fail(h, PIC_EINVAL, "NULL handle");
+  CK(h, join_adj(h), "adjoint join");
   return check_device_errors(h);
 }
 
 int pic_profile(pic_handle *h, int enable) {
   if (!h) return fail(h, PIC_EINVAL, "NULL handle");
+  join_adj(h);
   cudaStreamSynchronize(h->st);
   for (auto &t : h->timers) {
     h->event_pool.push_back(t.a);
@@ -1478,6 +1518,7 @@ int pic_profile(pic_handle *h, int enable) {
 
 int pic_timings(pic_handle *h, double *ms, int64_t *launches, int nmax, int *ncls) {
   if (!h) return fail(h, PIC_EINVAL, "NULL handle");
+  CK(h, join_adj(h), "adjoint join");
   CK(h, cudaStreamSynchronize(h->st), "sync");
   double acc[pic::KC_N] = {};
   int64_t cnt[pic::KC_N] = {};
@@ -1527,13 +1568,18 @@ int pic_restore(pic_handle *h, int slot) {
 
 int pic_tape_begin(pic_handle *h, int nsteps) {
   if (!h || nsteps < 0 || nsteps > 100000) return fail(h, PIC_EINVAL, "bad tape length");
-  while ((int)h->tape.size() > nsteps) {
-    free_snapshot(h->tape.back(), h->st);
-    h->tape.pop_back();
+  CK(h, make_tape_events(h), "events");
+  // the other buffer, once its last reversal (on st_adj) has run
+  h->tape_buf ^= 1;
+  CK(h, cudaStreamWaitEvent(h->st, h->tape_free[h->tape_buf], 0), "tape buffer wait");
+  std::vector<Snapshot> &tape = cur_tape(h);
+  while ((int)tape.size() > nsteps) {
+    free_snapshot(tape.back(), h->st);
+    tape.pop_back();
   }
-  h->tape.resize(nsteps);
+  tape.resize(nsteps);
   for (int k = 0; k < nsteps; ++k) {
-    cudaError_t e = alloc_snapshot(h, h->tape[k]);
+    cudaError_t e = alloc_snapshot(h, tape[k]);
     if (e != cudaSuccess) {
       cudaGetLastError();
       return fail(h, PIC_ENOMEM, "tape allocation failed");
@@ -1546,20 +1592,24 @@ int pic_tape_begin(pic_handle *h, int nsteps) {
 
 int pic_tape_record(pic_handle *h) {
   if (!h) return fail(h, PIC_EINVAL, "NULL handle");
-  if (!h->taping || h->tape_len >= (int)h->tape.size())
+  std::vector<Snapshot> &tape = cur_tape(h);
+  if (!h->taping || h->tape_len >= (int)tape.size())
     return fail(h, PIC_EINVAL, "no tape entry left to record (pic_tape_begin)");
   {
     Timed tm(h, pic::KC_TAPE);
-    CK(h, save_snapshot(h, h->tape[h->tape_len], true, h->tape_len > 0 ? &h->tape[h->tape_len - 1] : nullptr),
+    CK(h, save_snapshot(h, tape[h->tape_len], true, h->tape_len > 0 ? &tape[h->tape_len - 1] : nullptr),
        "tape record");
   }
   h->tape_len++;
-  if (h->tape_len >= (int)h->tape.size()) h->taping = false;
+  if (h->tape_len >= (int)tape.size()) h->taping = false;
   return PIC_OK;
 }
 
 int pic_adjoint_begin(pic_handle *h, int64_t id_capacity) {
   if (!h) return fail(h, PIC_EINVAL, "NULL handle");
+  CK(h, make_tape_events(h), "events");
+  if (!h->st_adj) CK(h, cudaStreamCreateWithFlags(&h->st_adj, cudaStreamNonBlocking), "adjoint stream");
+  CK(h, join_adj(h), "adjoint join");
   if (h->g.dims != 2 || h->g.order != 2)
     return fail(h, PIC_EINVAL, "adjoint kernels exist for 2D3V with the TSC shape only");
   if (h->cfg.filter_passes > 0 || h->cfg.gather != PIC_GATHER_MOMENTUM)
@@ -1620,6 +1670,7 @@ int pic_adjoint_seed_kinetic(pic_handle *h, int species, int col_lo, int col_hi,
   if (col_lo < 0 || col_hi > h->g.n[0] || col_lo >= col_hi) return fail(h, PIC_EINVAL, "bad column range");
   Species &s = h->sp[species];
   const double dVm = h->g.dx[0] * h->g.dx[1] * h->g.dx[2] * s.m;
+  CK(h, join_adj(h), "adjoint join");
   CK(h, cudaMemsetAsync(h->objF, 0, sizeof(double), h->st), "zero");
   CK(h,
      pic::launch_adj_seed(h->g, s.buf[s.cur], s.d_count, s.slots, col_lo, col_hi, dVm, h->adj[species].lu,
@@ -1640,26 +1691,33 @@ int pic_adjoint_step(pic_handle *h, int nsteps) {
   if (!h || !h->adj_ready) return fail(h, PIC_EINVAL, "call pic_adjoint_begin first");
   if (nsteps < 0 || nsteps > h->tape_len) return fail(h, PIC_EINVAL, "more adjoint steps than recorded steps");
   const bool walls = h->g.absorb_lo || h->g.absorb_hi;
+  // The reversal runs on st_adj after everything enqueued on st so far (the
+  // tape's recording, seeds, adjoint writes), so that st can go on with the
+  // next segment's recomputation meanwhile.
+  cudaStream_t sa = h->st_adj;
+  CK(h, cudaEventRecord(h->ev_main, h->st), "event");
+  CK(h, cudaStreamWaitEvent(sa, h->ev_main, 0), "event wait");
+  std::vector<Snapshot> &tape = cur_tape(h);
   for (int t = 0; t < nsteps; ++t) {
-    Snapshot &en = h->tape[h->tape_len - 1];
+    Snapshot &en = tape[h->tape_len - 1];
     const double t_old = en.step * h->g.dt, t_new = (en.step + 1) * h->g.dt;
     {
-      Timed tm(h, pic::KC_ADJ_FIELD);
-      CK(h, pic::launch_adj_yee_b(h->g, h->lE, h->lB, 0.5 * h->g.dt, nullptr, h->st), "adjoint B half");
+      Timed tm(h, pic::KC_ADJ_FIELD, sa);
+      CK(h, pic::launch_adj_yee_b(h->g, h->lE, h->lB, 0.5 * h->g.dt, nullptr, sa), "adjoint B half");
       if (walls)
         CK(h,
            pic::launch_adj_mur(h->g, h->lE, h->pend,
-                               pic::laser_step(h->laser, h->laser_prof, 1.0, h->g, t_old, t_new), h->da0, h->st),
+                               pic::laser_step(h->laser, h->laser_prof, 1.0, h->g, t_old, t_new), h->da0, sa),
            "adjoint Mur");
-      CK(h, pic::launch_adj_yee_e(h->g, h->lE, h->lB, h->lJ, h->g.dt, h->st), "adjoint E");
+      CK(h, pic::launch_adj_yee_e(h->g, h->lE, h->lB, h->lJ, h->g.dt, sa), "adjoint E");
       // the second B half also adds the Mur transpose's old-time terms
-      CK(h, pic::launch_adj_yee_b(h->g, h->lE, h->lB, 0.5 * h->g.dt, walls ? h->pend : nullptr, h->st),
+      CK(h, pic::launch_adj_yee_b(h->g, h->lE, h->lB, 0.5 * h->g.dt, walls ? h->pend : nullptr, sa),
          "adjoint B half");
     }
     h->launches += walls ? 4 : 3;
     for (int i = 0; i < h->nsp; ++i) {
       Species &s = h->sp[i];
-      Timed tm(h, pic::KC_ADJ_PUSH);
+      Timed tm(h, pic::KC_ADJ_PUSH, sa);
       const PCopy &c = en.sp[i];
       pic::AdjTiles tt;
       tt.work_tile = c.work_tile;
@@ -1672,18 +1730,21 @@ int pic_adjoint_step(pic_handle *h, int nsteps) {
       CK(h,
          pic::launch_adj_push(h->g, c.p, c.count, s.slots, en.E, en.B, h->lJ, h->lE, h->lB, h->adj[i].lx,
                               h->adj[i].lu, h->adj[i].lw, h->id_cap, h->adj_err, s.q, s.m, c.tiled ? &tt : nullptr,
-                              h->st, &nl),
+                              sa, &nl),
          "adjoint push");
       h->launches += nl;
     }
     h->tape_len--;
   }
+  // the tape buffer may be recorded into again once this has run
+  CK(h, cudaEventRecord(h->tape_free[h->tape_buf], sa), "event");
   return PIC_OK;
 }
 
 int pic_grad(pic_handle *h, double *d_a0, int species, double *d_w, int mem_kind) {
   if (!h || !h->adj_ready) return fail(h, PIC_EINVAL, "call pic_adjoint_begin first");
   if (d_w && (species < 0 || species >= h->nsp)) return fail(h, PIC_EINVAL, "bad species index");
+  CK(h, join_adj(h), "adjoint join");
   const cudaMemcpyKind kind = mem_kind == PIC_MEM_HOST ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice;
   if (d_a0) CK(h, cudaMemcpyAsync(d_a0, h->da0, sizeof(double), kind, h->st), "grad copy");
   if (d_w) CK(h, cudaMemcpyAsync(d_w, h->adj[species].lw, (size_t)h->id_cap * sizeof(double), kind, h->st), "grad copy");
@@ -1702,6 +1763,7 @@ int pic_grad_binned(pic_handle *h, int species, const int32_t *bin_of_id, int64_
   if (mem_kind != PIC_MEM_HOST && mem_kind != PIC_MEM_DEVICE) return fail(h, PIC_EINVAL, "bad memory kind");
   if (n_ids < 0 || n_ids > h->id_cap) return fail(h, PIC_EINVAL, "n_ids outside [0, id capacity]");
   if (nbins < 1) return fail(h, PIC_EINVAL, "nbins < 1");
+  CK(h, join_adj(h), "adjoint join");
   const bool host = mem_kind == PIC_MEM_HOST;
   int32_t *dbin = nullptr;
   double *dout = nullptr;
@@ -1739,6 +1801,7 @@ int pic_adjoint_field(pic_handle *h, int which, double *out, int mem_kind) {
   if (!h->adj_ready) return fail(h, PIC_EINVAL, "call pic_adjoint_begin first");
   if (which < PIC_EX || which > PIC_JZ) return fail(h, PIC_EINVAL, "bad field selector (PIC_EX .. PIC_JZ)");
   if (mem_kind != PIC_MEM_HOST && mem_kind != PIC_MEM_DEVICE) return fail(h, PIC_EINVAL, "bad memory kind");
+  CK(h, join_adj(h), "adjoint join");
   const void *src = which < 3 ? h->lE[which] : which < 6 ? h->lB[which - 3] : h->lJ[which - 6];
   CK(h, pic::launch_field_to_f64(h->g, src, h->f64, h->st), "convert");
   int r = copy_out(h, out, h->f64, sizeof(double) * h->g.ncell, mem_kind);
@@ -1752,6 +1815,7 @@ int pic_adjoint_set_field(pic_handle *h, int which, const double *in, int mem_ki
   if (!h->adj_ready) return fail(h, PIC_EINVAL, "call pic_adjoint_begin first");
   if (which < PIC_EX || which > PIC_BZ) return fail(h, PIC_EINVAL, "bad field selector (PIC_EX .. PIC_BZ)");
   if (mem_kind != PIC_MEM_HOST && mem_kind != PIC_MEM_DEVICE) return fail(h, PIC_EINVAL, "bad memory kind");
+  CK(h, join_adj(h), "adjoint join");
   CK(h,
      cudaMemcpyAsync(h->f64, in, sizeof(double) * h->g.ncell,
                      mem_kind == PIC_MEM_HOST ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice, h->st),
@@ -1767,6 +1831,7 @@ int pic_adjoint_momenta(pic_handle *h, int species, double *lux, double *luy, do
   if (!h->adj_ready) return fail(h, PIC_EINVAL, "call pic_adjoint_begin first");
   if (species < 0 || species >= h->nsp) return fail(h, PIC_EINVAL, "bad species index");
   if (mem_kind != PIC_MEM_HOST && mem_kind != PIC_MEM_DEVICE) return fail(h, PIC_EINVAL, "bad memory kind");
+  CK(h, join_adj(h), "adjoint join");
   double *outs[3] = {lux, luy, luz};
   for (int d = 0; d < 3; ++d) {
     if (!outs[d]) continue;
@@ -1784,6 +1849,7 @@ int pic_adjoint_set_momenta(pic_handle *h, int species, const double *lux, const
   if (!h->adj_ready) return fail(h, PIC_EINVAL, "call pic_adjoint_begin first");
   if (species < 0 || species >= h->nsp) return fail(h, PIC_EINVAL, "bad species index");
   if (mem_kind != PIC_MEM_HOST && mem_kind != PIC_MEM_DEVICE) return fail(h, PIC_EINVAL, "bad memory kind");
+  CK(h, join_adj(h), "adjoint join");
   const double *ins[3] = {lux, luy, luz};
   for (int d = 0; d < 3; ++d) {
     if (!ins[d]) continue;
