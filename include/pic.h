@@ -318,7 +318,11 @@ int pic_checkpoint(pic_handle *h, int slot);
 int pic_restore(pic_handle *h, int slot);
 
 /* Record the state at the start of each of the next nsteps calls to the
- * step loop (after its sort), for pic_adjoint_step.  nsteps = 0 stops. */
+ * step loop (after its sort), for pic_adjoint_step.  nsteps = 0 stops.  The
+ * handle keeps two tape buffers and alternates between them at each call, so
+ * that a segment can be recorded while the previous one is being reversed;
+ * the recording waits (on the device) for the last reversal of the buffer it
+ * reuses. */
 int pic_tape_begin(pic_handle *h, int nsteps);
 
 /* Record the current state as the next tape entry without taking the step
@@ -341,7 +345,12 @@ int pic_adjoint_begin(pic_handle *h, int64_t id_capacity);
 int pic_adjoint_seed_kinetic(pic_handle *h, int species, int col_lo, int col_hi, double *F);
 
 /* Reverse the last nsteps recorded steps (most recent first), accumulating
- * dF/da0 and dF/dw.  PIC_EINVAL if fewer steps are on the tape. */
+ * dF/da0 and dF/dw.  PIC_EINVAL if fewer steps are on the tape.  The
+ * adjoint kernels run on a stream of the handle's own, after the work
+ * enqueued on the simulation stream so far; the call returns once they are
+ * enqueued, so the next pic_restore / pic_step calls overlap them.  Every
+ * call that reads or writes the adjoint state (pic_adjoint_*, pic_grad,
+ * pic_grad_binned, pic_sync, pic_timings) first waits for them. */
 int pic_adjoint_step(pic_handle *h, int nsteps);
 
 /* Copy dF/da0 (one double, may be NULL) and dF/dw of `species` indexed by
