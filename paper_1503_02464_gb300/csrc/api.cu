@@ -1448,7 +1448,10 @@ int pic_diag(pic_handle *h, pic_diag_t *out) {
   CK(h, cudaMemcpyAsync(red, h->red, sizeof red, cudaMemcpyDeviceToHost, h->st), "D2H");
   CK(h, cudaMemcpyAsync(&c, h->ctr, sizeof c, cudaMemcpyDeviceToHost, h->st), "D2H");
   unsigned long long adj_esc = 0;
-  if (h->adj_esc) CK(h, cudaMemcpyAsync(&adj_esc, h->adj_esc, sizeof adj_esc, cudaMemcpyDeviceToHost, h->st), "D2H");
+  if (h->adj_esc) {
+    CK(h, join_adj(h), "adjoint join");  // the count is kept by the adjoint stream
+    CK(h, cudaMemcpyAsync(&adj_esc, h->adj_esc, sizeof adj_esc, cudaMemcpyDeviceToHost, h->st), "D2H");
+  }
   CK(h, cudaMemcpyAsync(h->rho_prev, h->rho, sizeof(double) * h->g.ncell, cudaMemcpyDeviceToDevice, h->st), "copy");
   CK(h, cudaStreamSynchronize(h->st), "diag sync");
   h->rho_prev_step = h->step;
